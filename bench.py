@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark of the HEX8 weak-form hot path on GB300.
+
+One step = one complete load-stepped Newton solve of the 64^3 Neo-Hookean
+workload (823,875 DOF, 10 load steps) in mixed precision: FP64 residuals,
+norms and updates, FP32 Jacobi-PCG on the matrix-free tangent -- every row of
+the hot path (BCs, residual, tangent apply, diagonal, CG, Newton, refinement)
+runs in each step.  Inputs are resident in HBM; L2 is flushed (256 MiB write)
+between timed steps.
+
+value      = Newton-solved DOFs per second over all ranks (MDOF/s)
+ms_per_step= wall time of one solve (device-synchronised)
+roofline   = FP32 Neo-Hookean CG tangent-apply kernel, timed live inside the
+             timed solves by CUDA events captured in the CG graph
+e2e        = the same metric through the public API with pinned host buffers:
+             H2D of mask / prescribed values / start state and D2H of u inside
+             the timed region
+cpu_baseline / --impl reference = the FP64 CPU oracle (Newton + spsolve) on a
+             bounded sample of the same workload (the 8^3 instance of the same
+             recipe), single thread.
+Multi-GPU: replicas only -- every rank solves its own instance, no
+collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tangent-apply GDOF/s and Newton solve time, 64^3 Neo-Hookean, mixed vs FP64"
+# Algorithmic FP32 flops per cell of one Neo-Hookean CG tangent apply
+# (sum-factorised gradients of u and x: 576; 8 Gauss points x (kinematics 94 +
+# directional stress derivative 206 + flux accumulation 9) = 2472; transpose
+# 360 + 3; p.Kp 48; assembly adds 24).  FMA = 2 flops.
+NH_APPLY_FLOPS_PER_CELL = 3483
+# FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Bytes a launch must move (u, x read; y written; FP32): 12 * D.
+SAMPLE_N = 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=64, help="mesh edge (64 = the benchmark workload)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_solves(k: int):
+    """Time k oracle solves of the SAMPLE_N^3 instance of the workload recipe."""
+    import oracle
+    from oracle import solve as osolve
+    from paper_2212_00964_gb300 import inputs
+    w = inputs.c1(n=SAMPLE_N)
+    om = oracle.mesh(w.nx, w.ny, w.nz)
+    mat = oracle.Material(w.kind, w.E, w.nu)
+    times = []
+    for _ in range(k):
+        t0 = time.perf_counter()
+        osolve.newton_solve(om, mat, w.mask, w.u_bar, n_steps=w.n_steps)
+        times.append(time.perf_counter() - t0)
+    return w.n_dofs, times
+
+
+def cpu_baseline_obj(dofs, times):
+    t = statistics.median(times)
+    return {"value": dofs / t / 1e6, "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle Newton + spsolve, {SAMPLE_N}^3 instance of the same recipe "
+                      f"({dofs} DOF, 10 load steps), {len(times)} solves, median {t:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    dofs, times = cpu_oracle_solves(args.warmup + args.steps)
+    timed = times[args.warmup:]
+    total = sum(timed)
+    value = dofs * len(timed) / total / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"Neo-Hookean {SAMPLE_N}^3 sample of the 64^3 recipe (E=10, nu=0.3, x=0 "
+                                   f"clamped, u_x=-0.1 on x=1, 10 load steps)", "parallelism": "rank 0 only"},
+            "cpu_baseline": cpu_baseline_obj(dofs, timed),
+            "e2e": {"value": value, "unit": "MDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2212_00964_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2212_00964_gb300 import fem as F
+    from paper_2212_00964_gb300 import inputs
+
+    w = inputs.c1(n=args.n)
+    D = w.n_dofs
+    m = F.fem_mesh(w.nx, w.ny, w.nz)
+    mat = F.material(w.kind, w.E, w.nu)
+    mask = torch.tensor(w.mask, device="cuda")
+    ubar = torch.tensor(w.u_bar, device="cuda")
+    u = torch.zeros(D, dtype=torch.float64, device="cuda")
+    opt = F.default_options(precision=F.FEM_MIXED, newton_rtol=1e-10)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def solve_once(options):
+        u.zero_()
+        return F.fem_solve(m, mat, mask, ubar, u, None, None, w.n_steps, options)
+
+    for _ in range(args.warmup):
+        solve_once(opt)
+    barrier()
+    clocks = Clocks(local)
+    launches0 = F.kernel_launches()
+    step_ms, stats = [], []
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = solve_once(opt)
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    launches = F.kernel_launches() - launches0
+    total_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = D * args.steps * world / total_s / 1e6
+    u_mixed = u.clone()
+
+    apply_ms = sum(s["apply_ms"] for s in stats)
+    apply_n = sum(s["apply_samples"] for s in stats)
+    apply_launches = sum(s["apply_launches"] for s in stats) / len(stats)
+    t_apply = apply_ms / max(apply_n, 1) / 1e3
+    flops = NH_APPLY_FLOPS_PER_CELL * w.n_cells
+    achieved = flops / t_apply / 1e12
+    share = apply_launches * t_apply / (statistics.mean(step_ms) / 1e3)
+
+    # all-FP64 GPU path on the same mesh, for the mixed-vs-FP64 comparison
+    fp64 = None
+    if not args.no_fp64:
+        o64 = F.default_options(precision=F.FEM_FP64, newton_rtol=1e-10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st64 = solve_once(o64)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        rel = float(torch.linalg.norm(u - u_mixed) / torch.linalg.norm(u))
+        fp64 = {"newton_solve_s": t64, "value": D / t64 / 1e6, "unit": "MDOF/s",
+                "tangent_apply_gdofs": D / (st64["apply_ms"] / max(st64["apply_samples"], 1) / 1e3) / 1e9,
+                "newton_iters": st64["newton_iters"], "pcg_iters": st64["pcg_iters"],
+                "mixed_vs_fp64_rel_l2": rel, "speedup_mixed_vs_fp64": t64 / (statistics.mean(step_ms) / 1e3)}
+
+    # end to end through the public API with pinned host buffers
+    mask_h = torch.tensor(w.mask).pin_memory()
+    ubar_h = torch.tensor(w.u_bar).pin_memory()
+    u0_h = torch.zeros(D, dtype=torch.float64).pin_memory()
+    u_out_h = torch.empty(D, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mask.copy_(mask_h, non_blocking=True)
+        ubar.copy_(ubar_h, non_blocking=True)
+        u.copy_(u0_h, non_blocking=True)
+        F.fem_solve(m, mat, mask, ubar, u, None, None, w.n_steps, opt)
+        u_out_h.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_t = statistics.median(e2e_ms) / 1e3
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu and world == 1:
+        dofs, times = cpu_oracle_solves(3)
+        cpu = cpu_baseline_obj(dofs, times)
+    st0 = stats[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"Neo-Hookean {w.nx}^3 HEX8 unit cube ({D} DOF), E=10, nu=0.3, x=0 clamped, "
+                               f"u_x=-0.1 on x=1, 10 load steps, Newton + Jacobi-PCG, mixed precision",
+                   "l2": "flushed by a 256 MiB write between timed steps", "parallelism": f"replicas x{world}",
+                   "newton_rtol": 1e-10, "pcg_rtol": opt.pcg_rtol},
+        "newton_solve_s": statistics.mean(step_ms) / 1e3,
+        "tangent_apply_gdofs": D / t_apply / 1e9,
+        "solver": {"newton_iters": st0["newton_iters"], "pcg_iters": st0["pcg_iters"],
+                   "ref_rnorm": st0["ref_rnorm"], "final_rnorm": st0["final_rnorm"], "status": st0["status"]},
+        "fp64": fp64,
+        "clocks": clk,
+        "e2e": {"value": D / e2e_t / 1e6, "unit": "MDOF/s", "h2d_bytes_per_step": int(D * (1 + 8 + 8)),
+                "d2h_bytes_per_step": int(D * 8)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "kernel": "cell_kernel<float,NH,CM_APPLY_PCG>",
+                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "launch_us": t_apply * 1e6, "launches_per_step": apply_launches,
+                     "time_share": share, "hbm_gbs_algorithmic": 12 * D / t_apply / 1e9},
+        "cpu_baseline": cpu,
+        "wall_s_timed": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,237 @@
+/*
+ * fem.h -- C-ABI of the GB300-native HEX8 weak-form library (libfemgb.so).
+ *
+ * The library computes, on one NVIDIA GB300 (sm_103a), the data-parallel hot
+ * path of the differentiable finite-element method of Xue et al., "JAX-FEM"
+ * (arXiv 2212.00964): the per-cell weak form of a second-order elliptic
+ * vector PDE (Sec. 2.1, Eqs. (1)-(2)) on structured trilinear HEX8 box meshes
+ * with 2x2x2 Gauss quadrature -- residual, matrix-free consistent tangent
+ * (Eq. (5)), Jacobi diagonal, adjoint vector-Jacobian product (Eq. (23)) --
+ * and the solvers around it (Newton, Eq. (4), with Jacobi-preconditioned CG;
+ * adjoint solve, Eq. (22)).
+ *
+ * Conventions shared by every call
+ *   Mesh      structured box of nx*ny*nz cells on [0,lx]x[0,ly]x[0,lz];
+ *             node id = i + (nx+1)(j + (ny+1)k), cell id = i + nx(j + ny k),
+ *             cell-local node order is VTK_HEXAHEDRON.
+ *   DOFs      D = 3 * n_nodes, interleaved: DOF 3*node + component.
+ *   Pointers  every array argument is a caller-owned, contiguous DEVICE
+ *             pointer unless the comment says "host".  The library never
+ *             frees caller memory.  A mesh handle owns its own buffers and a
+ *             scratch workspace that grows on demand and is freed by
+ *             fem_mesh_destroy.
+ *   Streams   `stream` is a cudaStream_t (NULL = legacy default stream).  The
+ *             cell-operator calls are asynchronous on it; fem_solve*,
+ *             fem_adjoint and fem_mesh synchronise once before returning.
+ *   Errors    every call returns a fem_status (0 = FEM_OK); nothing is thrown
+ *             across the ABI.  fem_last_error() returns the text of the last
+ *             failure on the calling thread.
+ *   Precision FEM_FP64: all arithmetic in double.  FEM_FP32: all in float
+ *             (cell operators only).  FEM_MIXED (solvers only): float cell
+ *             kernels and CG, double residuals, norms and updates.
+ *             For the cell-operator calls the value arrays (u, x, y,
+ *             cell_param, f_ext, r) are double for FEM_FP64 and float for
+ *             FEM_FP32.
+ *   Materials FEM_LINEAR   sigma = lam tr(eps) I + 2 mu eps     (Sec. 2.3, Eq. (11))
+ *             FEM_SIMP     the same with E(theta) = E (emin + theta^p (1-emin))
+ *                          per cell (Sec. 3.2, Eq. (30) with a floor emin)
+ *             FEM_NEOHOOKE P = dW/dF, W = G/2 (J^{-2/3} I1 - 3) + kappa/2 (J-1)^2
+ *                          (Sec. 2.3, Eq. (13)), total Lagrangian.
+ *             cell_param: SIMP -> density theta_e; other laws -> stiffness
+ *             scale s_e (E_e = E s_e).  NULL means theta_e = 1 / s_e = 1.
+ *   Dirichlet mask[d] != 0 marks a prescribed DOF.  Prescribed DOFs are
+ *             eliminated symmetrically: residual rows are 0, tangent rows and
+ *             columns are the identity ((K x)_c = x_c).
+ */
+#ifndef FEMGB_FEM_H
+#define FEMGB_FEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fem_mesh_s *fem_mesh_t;
+
+typedef enum {
+    FEM_OK = 0,
+    FEM_ERR_ARG = -1,           /* invalid argument (null pointer, bad size, bad enum) */
+    FEM_ERR_CUDA = -2,          /* a CUDA runtime call failed; see fem_last_error() */
+    FEM_ERR_NOT_CONVERGED = -3, /* Newton / refinement hit its iteration limit */
+    FEM_ERR_INVERTED = -4,      /* det F <= 0 at some Gauss point */
+    FEM_ERR_BREAKDOWN = -5,     /* CG found p^T K p <= 0 (tangent not positive definite) */
+    FEM_ERR_NONFINITE = -6,     /* NaN / Inf in a residual norm */
+    FEM_ERR_TIMEOUT = -7,       /* host-side watchdog of a solve expired */
+    FEM_ERR_NOMEM = -8          /* device allocation failed */
+} fem_status;
+
+typedef enum { FEM_LINEAR = 0, FEM_SIMP = 1, FEM_NEOHOOKE = 2 } fem_material_kind;
+typedef enum { FEM_FP64 = 0, FEM_FP32 = 1, FEM_MIXED = 2 } fem_precision;
+
+typedef struct {
+    int kind;         /* fem_material_kind */
+    double E;         /* reference Young's modulus (> 0) */
+    double nu;        /* Poisson ratio, -1 < nu < 0.5 */
+    double simp_p;    /* SIMP penalty exponent (FEM_SIMP only) */
+    double simp_emin; /* SIMP stiffness floor, 0 <= emin < 1 (FEM_SIMP only) */
+} fem_material;
+
+/* ------------------------------------------------------------------ mesh -- */
+#define FEM_MESH_CSR 1 /* also build the CSR pattern and scatter map (Algorithm 1) */
+
+/* Build a structured box mesh on the device (the paper's linear hexahedra,
+ * Sec. 3.1): connectivity, coordinates, the 8-colour cell colouring and,
+ * with FEM_MESH_CSR, the CSR pattern of the global tangent (row 3n+i holds
+ * every DOF of every node sharing a cell with n, columns ascending) and the
+ * scatter map.  nx, ny, nz >= 1, lengths > 0.  *out receives the handle.
+ * FEM_ERR_ARG if the CSR would exceed 2^31-1 entries. */
+int fem_mesh(int nx, int ny, int nz, double lx, double ly, double lz, int flags, void *stream,
+             fem_mesh_t *out);
+
+/* Sizes of a mesh (host outputs; any may be NULL).  nnz = 0 without CSR. */
+int fem_mesh_info(fem_mesh_t m, int64_t *n_nodes, int64_t *n_cells, int64_t *nnz);
+
+/* Copy the mesh arrays into caller device buffers (any may be NULL):
+ * conn int32[Ne][8] (VTK order), X double[N][3], colour_ptr int32[9],
+ * cell_perm int32[Ne] (cells by colour (i&1)+2(j&1)+4(k&1), ascending id
+ * inside a colour), row_ptr int32[D+1], col int32[nnz],
+ * map int32[Ne][24][24] with map[e][3a+i][3b+j] = CSR slot of
+ * K[3 n_a + i][3 n_b + j].  The CSR outputs need FEM_MESH_CSR. */
+int fem_mesh_export(fem_mesh_t m, int32_t *conn, double *X, int32_t *colour_ptr,
+                    int32_t *cell_perm, int32_t *row_ptr, int32_t *col, int32_t *map,
+                    void *stream);
+
+int fem_mesh_destroy(fem_mesh_t m);
+
+/* ----------------------------------------------------------------- loads -- */
+/* f_ext += nodal forces of a uniform traction t (host double[3]) on one box
+ * face (Neumann term of Eq. (2)); face 0..5 = x=0, x=lx, y=0, y=ly, z=0, z=lz.
+ * f_ext: double[D]. */
+int fem_load_traction(fem_mesh_t m, int face, const double *t, double *f_ext, void *stream);
+
+/* f_ext += nodal forces of a uniform body force b (host double[3]) (source
+ * term of Eq. (2)).  f_ext: double[D]. */
+int fem_load_body(fem_mesh_t m, const double *b, double *f_ext, void *stream);
+
+/* -------------------------------------------------------- cell operators -- */
+/* Residual of the discretised weak form, Eq. (2) / element residual Eq. (8):
+ * r = sum_e R_e(u) - f_ext, r_c = 0 on prescribed DOFs.  f_ext and mask may
+ * be NULL.  u, f_ext, r: [D]; cell_param: [Ne] or NULL. */
+int fem_residual(fem_mesh_t m, const fem_material *mat, int precision, const void *u,
+                 const void *cell_param, const uint8_t *mask, const void *f_ext, void *r,
+                 void *stream);
+
+/* Matrix-free consistent tangent, Eq. (5): y = K(u) x, with prescribed
+ * columns removed and (K x)_c = x_c.  u, x, y: [D] (y must not alias x). */
+int fem_tangent_apply(fem_mesh_t m, const fem_material *mat, int precision, const void *u,
+                      const void *cell_param, const uint8_t *mask, const void *x, void *y,
+                      void *stream);
+
+/* Diagonal of K(u) (the Jacobi preconditioner of the paper's linear solver,
+ * Sec. 5 item 2); d_c = 1 on prescribed DOFs.  d: [D]. */
+int fem_tangent_diag(fem_mesh_t m, const fem_material *mat, int precision, const void *u,
+                     const void *cell_param, const uint8_t *mask, void *d, void *stream);
+
+/* Adjoint vector-Jacobian product, Eq. (23): g_e = -lambda^T dC/dtheta_e
+ * for every cell (prescribed rows of C do not depend on theta).  lambda: [D];
+ * g: [Ne] (same value type as u). */
+int fem_vjp(fem_mesh_t m, const fem_material *mat, int precision, const void *u,
+            const void *lambda, const void *cell_param, const uint8_t *mask, void *g,
+            void *stream);
+
+/* Assembled tangent (Algorithm 1): vals[nnz] of K(u) in the mesh's CSR
+ * pattern (needs FEM_MESH_CSR).  With a mask, prescribed rows and columns are
+ * dropped and their diagonal is 1. */
+int fem_assemble_csr(fem_mesh_t m, const fem_material *mat, int precision, const void *u,
+                     const void *cell_param, const uint8_t *mask, void *vals, void *stream);
+
+/* ---------------------------------------------------------------- solvers -- */
+typedef struct {
+    int precision;       /* FEM_MIXED (default) or FEM_FP64 */
+    double newton_rtol;  /* stop when ||R_free|| <= newton_rtol * ||R_free|| of step 1, it 0 */
+    double newton_atol;  /* ... or ||R_free|| <= newton_atol */
+    int newton_maxit;    /* Newton iterations per load step before FEM_ERR_NOT_CONVERGED */
+    double pcg_rtol;     /* inner CG: ||r|| <= pcg_rtol ||r_0|| */
+    int pcg_maxit;       /* inner CG iteration cap (the iterate is still used) */
+    int pcg_chunk;       /* CG iterations per CUDA-graph launch (0 = default) */
+    int step_begin;      /* first load step to run (1 = from the start; k+1 resumes a
+                            checkpoint taken after step k) */
+    int cells_per_block; /* cell-kernel CTA size (0 = autotuned) */
+    int deterministic;   /* 1: colour-ordered scatter (bit-reproducible), 0: atomics */
+    double timeout_s;    /* host watchdog for one solve (0 = none) */
+} fem_options;
+
+typedef struct {
+    int status;          /* fem_status of this solve / instance */
+    int load_steps;      /* load steps completed */
+    int newton_iters;    /* total Newton (or refinement) iterations */
+    int pcg_iters;       /* total inner CG iterations */
+    double ref_rnorm;    /* ||R_free|| at step 1, iteration 0 */
+    double final_rnorm;  /* last ||R_free|| (double precision) */
+    double time_ms;      /* wall time of the call */
+    double apply_ms;     /* summed device time of the sampled CG tangent-apply launches */
+    int apply_samples;   /* number of sampled launches (the first apply of each CG graph) */
+    int apply_launches;  /* CG tangent-apply launches that did work */
+} fem_stats;
+
+typedef struct {
+    const uint8_t *mask;  /* [D] prescribed-DOF mask */
+    const double *u_bar;  /* [D] final prescribed values (read where mask != 0) */
+    const double *f_ext;  /* [D] external nodal forces, or NULL */
+} fem_bc;
+
+/* Fill *o with the defaults (FEM_MIXED, newton_rtol 1e-10, ...). */
+void fem_default_options(fem_options *o);
+
+/* Nonlinear solve of R_free(u) = 0 (Newton, Eq. (4), on the FP64 residual),
+ * with n_steps uniform load steps: at step s the prescribed DOFs are set to
+ * (s/n_steps) u_bar and the free DOFs start from the previous state.  Inner
+ * solver: Jacobi-preconditioned CG on the matrix-free tangent.  For linear
+ * materials this is iterative refinement of one linear solve.
+ * u_inout [D] double: start state in, solution out.  cell_param [Ne] double
+ * or NULL.  stats (host) may be NULL. */
+int fem_solve(fem_mesh_t m, const fem_material *mat, const fem_bc *bc, const double *cell_param,
+              int n_steps, const fem_options *opt, double *u_inout, fem_stats *stats,
+              void *stream);
+
+/* Adjoint gradient at a converged state u_star (Sec. 3, Eqs. (22)-(23)):
+ * solve K(u_star)^T lambda = dJ/du on the free DOFs (lambda_c = 0; K is
+ * symmetric for all three laws), then
+ * dJ/dtheta_e = -lambda^T dC/dtheta_e + dJdtheta_explicit_e.
+ * u_star, dJdu: [D] double; dJdtheta_explicit: [Ne] double or NULL;
+ * dJdtheta_out: [Ne] double; lambda_out: [D] double or NULL. */
+int fem_adjoint(fem_mesh_t m, const fem_material *mat, const fem_bc *bc, const double *u_star,
+                const double *cell_param, const double *dJdu, const double *dJdtheta_explicit,
+                const fem_options *opt, double *dJdtheta_out, double *lambda_out,
+                fem_stats *stats, void *stream);
+
+/* One solve of many independent problems of uneven size in a single batched,
+ * CUDA-graph-captured launch sequence (no paper counterpart: throughput
+ * path).  inst: host array of n_inst descriptors; stats: host array of
+ * n_inst (may be NULL). */
+typedef struct {
+    fem_mesh_t mesh;
+    fem_material mat;
+    fem_bc bc;
+    const double *cell_param; /* [Ne] or NULL */
+    int n_steps;
+    double *u_inout;          /* [D] */
+} fem_instance;
+
+int fem_solve_batched(int n_inst, const fem_instance *inst, const fem_options *opt,
+                      fem_stats *stats, void *stream);
+
+/* ------------------------------------------------------------- utilities -- */
+const char *fem_status_string(int status);
+const char *fem_last_error(void);
+
+/* Number of kernels this library has launched in this process (for the
+ * benchmark's launch count). */
+int64_t fem_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEMGB_FEM_H */

@@ -1,0 +1,325 @@
+// cell_ops.cu -- the cell-operator entry points of the C-ABI (residual,
+// tangent apply, diagonal, VJP, CSR assembly) and the cell-kernel launcher
+// shared with the solvers.
+#include <algorithm>
+#include <map>
+#include <mutex>
+
+#include "cell_kernels.cuh"
+#include "cell_ops.cuh"
+#include "mesh.cuh"
+
+namespace femgb {
+
+static std::mutex g_occ_mu;
+static std::map<const void *, int> g_occ;
+
+int device_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+int resident_grid(const void *func, int block, size_t smem)
+{
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    auto it = g_occ.find(func);
+    int nb;
+    if (it == g_occ.end()) {
+        nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, block, smem) != cudaSuccess || nb < 1) {
+            cudaGetLastError();
+            nb = 1;
+        }
+        g_occ[func] = nb;
+    } else {
+        nb = it->second;
+    }
+    return nb * device_sms();
+}
+
+template <typename T, int NH, int MODE>
+static cudaError_t launch_one(const CellArgs<T> &a, cudaStream_t s)
+{
+    auto f = cell_kernel<T, NH, MODE>;
+    int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, 0));
+    if (g < 1) return cudaSuccess;
+    f<<<(int)g, CELL_BLOCK, 0, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, int NH>
+static cudaError_t launch_mode(int mode, const CellArgs<T> &a, cudaStream_t s)
+{
+    switch (mode) {
+    case CM_RESIDUAL: return launch_one<T, NH, CM_RESIDUAL>(a, s);
+    case CM_APPLY: return launch_one<T, NH, CM_APPLY>(a, s);
+    case CM_APPLY_PCG: return launch_one<T, NH, CM_APPLY_PCG>(a, s);
+    case CM_DIAG: return launch_one<T, NH, CM_DIAG>(a, s);
+    case CM_VJP: return launch_one<T, NH, CM_VJP>(a, s);
+    case CM_RESIDUAL_CTL: return launch_one<T, NH, CM_RESIDUAL_CTL>(a, s);
+    case CM_APPLY_CTL: return launch_one<T, NH, CM_APPLY_CTL>(a, s);
+    case CM_DIAG_CTL: return launch_one<T, NH, CM_DIAG_CTL>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_cell(int mode, bool nh, const CellArgs<T> &a, cudaStream_t s)
+{
+    return nh ? launch_mode<T, 1>(mode, a, s) : launch_mode<T, 0>(mode, a, s);
+}
+
+// Occupancy queries of the solver's cell kernels, done before a graph
+// capture so that no query runs while a stream is capturing.
+template <typename T, int NH>
+static void warm_one()
+{
+    resident_grid((const void *)cell_kernel<T, NH, CM_RESIDUAL_CTL>, CELL_BLOCK, 0);
+    resident_grid((const void *)cell_kernel<T, NH, CM_APPLY_CTL>, CELL_BLOCK, 0);
+    resident_grid((const void *)cell_kernel<T, NH, CM_DIAG_CTL>, CELL_BLOCK, 0);
+    resident_grid((const void *)cell_kernel<T, NH, CM_APPLY_PCG>, CELL_BLOCK, 0);
+    resident_grid((const void *)cell_kernel<T, NH, CM_VJP>, CELL_BLOCK, 0);
+}
+
+void warm_occupancy(bool nh)
+{
+    device_sms();
+    if (nh) {
+        warm_one<float, 1>();
+        warm_one<double, 1>();
+    } else {
+        warm_one<float, 0>();
+        warm_one<double, 0>();
+    }
+}
+template cudaError_t launch_cell<float>(int, bool, const CellArgs<float> &, cudaStream_t);
+template cudaError_t launch_cell<double>(int, bool, const CellArgs<double> &, cudaStream_t);
+
+int check_material(const fem_material *mat)
+{
+    if (!mat) return (set_error("material is NULL"), FEM_ERR_ARG);
+    if (mat->kind < FEM_LINEAR || mat->kind > FEM_NEOHOOKE) return (set_error("unknown material kind"), FEM_ERR_ARG);
+    if (!(mat->E > 0) || !(mat->nu > -1.0) || !(mat->nu < 0.5))
+        return (set_error("material needs E > 0 and -1 < nu < 0.5"), FEM_ERR_ARG);
+    if (mat->kind == FEM_SIMP && (!(mat->simp_p > 0) || !(mat->simp_emin >= 0) || !(mat->simp_emin < 1)))
+        return (set_error("SIMP needs p > 0 and 0 <= emin < 1"), FEM_ERR_ARG);
+    return FEM_OK;
+}
+
+InstDesc make_desc(const fem_mesh_s *m, const fem_material *mat)
+{
+    InstDesc d{};
+    d.nx = m->nx; d.ny = m->ny; d.nz = m->nz;
+    d.kind = mat->kind;
+    d.E = mat->E; d.nu = mat->nu; d.p = mat->simp_p; d.emin = mat->simp_emin;
+    d.hx = m->lx / m->nx; d.hy = m->ly / m->ny; d.hz = m->lz / m->nz;
+    d.dof_off = 0; d.cell_off = 0; d.tile_off = 0; d.vec_off = 0;
+    return d;
+}
+
+// y = f ? -f : 0
+template <typename T>
+__global__ void k_init_neg(T *y, const T *f, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = f ? -f[i] : (T)0;
+}
+
+// prescribed rows: how 0 -> y_c = 0, 1 -> y_c = x_c, 2 -> y_c = 1
+template <typename T>
+__global__ void k_fix_mask(T *y, const T *x, const uint8_t *mask, int64_t n, int how)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (mask[i]) y[i] = how == 0 ? (T)0 : (how == 1 ? x[i] : (T)1);
+}
+
+template <typename T>
+__global__ void k_csr_diag_ones(const uint8_t *mask, const int32_t *row_ptr, const int32_t *col, T *vals, int64_t n)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        if (!mask[r]) continue;
+        for (int32_t t = row_ptr[r]; t < row_ptr[r + 1]; ++t)
+            if (col[t] == r) vals[t] = (T)1;
+    }
+}
+
+static int vgrid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+
+template <typename T>
+static int residual_t(fem_mesh_t m, const fem_material *mat, const T *u, const T *cp, const uint8_t *mask,
+                      const T *f, T *r, cudaStream_t s)
+{
+    const int64_t D = m->n_dofs();
+    k_init_neg<T><<<vgrid(D), 256, 0, s>>>(r, f, D);
+    count_launch();
+    CellArgs<T> a{};
+    a.d0 = make_desc(m, mat);
+    a.n_tiles = (m->n_cells + CELL_BLOCK - 1) / CELL_BLOCK;
+    a.u = u; a.y = r; a.cell_param = cp; a.jflag = nullptr;
+    FEM_CUDA(launch_cell<T>(CM_RESIDUAL, mat->kind == FEM_NEOHOOKE, a, s));
+    if (mask) {
+        k_fix_mask<T><<<vgrid(D), 256, 0, s>>>(r, nullptr, mask, D, 0);
+        count_launch();
+    }
+    FEM_CUDA(cudaGetLastError());
+    return FEM_OK;
+}
+
+template <typename T>
+static int apply_t(fem_mesh_t m, const fem_material *mat, const T *u, const T *cp, const uint8_t *mask, const T *x,
+                   T *y, cudaStream_t s)
+{
+    const int64_t D = m->n_dofs();
+    FEM_CUDA(cudaMemsetAsync(y, 0, sizeof(T) * D, s));
+    CellArgs<T> a{};
+    a.d0 = make_desc(m, mat);
+    a.n_tiles = (m->n_cells + CELL_BLOCK - 1) / CELL_BLOCK;
+    a.u = u; a.x = x; a.y = y; a.cell_param = cp; a.mask = mask;
+    FEM_CUDA(launch_cell<T>(CM_APPLY, mat->kind == FEM_NEOHOOKE, a, s));
+    if (mask) {
+        k_fix_mask<T><<<vgrid(D), 256, 0, s>>>(y, x, mask, D, 1);
+        count_launch();
+    }
+    FEM_CUDA(cudaGetLastError());
+    return FEM_OK;
+}
+
+template <typename T>
+static int diag_t(fem_mesh_t m, const fem_material *mat, const T *u, const T *cp, const uint8_t *mask, T *dg,
+                  cudaStream_t s)
+{
+    const int64_t D = m->n_dofs();
+    FEM_CUDA(cudaMemsetAsync(dg, 0, sizeof(T) * D, s));
+    CellArgs<T> a{};
+    a.d0 = make_desc(m, mat);
+    a.n_tiles = (m->n_cells + CELL_BLOCK - 1) / CELL_BLOCK;
+    a.u = u; a.y = dg; a.cell_param = cp;
+    FEM_CUDA(launch_cell<T>(CM_DIAG, mat->kind == FEM_NEOHOOKE, a, s));
+    if (mask) {
+        k_fix_mask<T><<<vgrid(D), 256, 0, s>>>(dg, nullptr, mask, D, 2);
+        count_launch();
+    }
+    FEM_CUDA(cudaGetLastError());
+    return FEM_OK;
+}
+
+template <typename T>
+static int vjp_t(fem_mesh_t m, const fem_material *mat, const T *u, const T *lam, const T *cp, const uint8_t *mask,
+                 T *g, cudaStream_t s)
+{
+    CellArgs<T> a{};
+    a.d0 = make_desc(m, mat);
+    a.n_tiles = (m->n_cells + CELL_BLOCK - 1) / CELL_BLOCK;
+    a.u = u; a.x = lam; a.cell_param = cp; a.mask = mask; a.g = g;
+    FEM_CUDA(launch_cell<T>(CM_VJP, mat->kind == FEM_NEOHOOKE, a, s));
+    return FEM_OK;
+}
+
+template <typename T>
+static int assemble_t(fem_mesh_t m, const fem_material *mat, const T *u, const T *cp, const uint8_t *mask, T *vals,
+                      cudaStream_t s)
+{
+    FEM_CUDA(cudaMemsetAsync(vals, 0, sizeof(T) * m->nnz, s));
+    AsmArgs<T> a{};
+    a.d = make_desc(m, mat);
+    a.u = u; a.cell_param = cp; a.mask = mask; a.row_ptr = m->row_ptr; a.vals = vals;
+    const int64_t work = m->n_cells * 24;
+    if (mat->kind == FEM_NEOHOOKE) {
+        int g = (int)std::min<int64_t>((work + CELL_BLOCK - 1) / CELL_BLOCK,
+                                       resident_grid((const void *)assemble_kernel<T, 1>, CELL_BLOCK, 0));
+        assemble_kernel<T, 1><<<g, CELL_BLOCK, 0, s>>>(a);
+    } else {
+        int g = (int)std::min<int64_t>((work + CELL_BLOCK - 1) / CELL_BLOCK,
+                                       resident_grid((const void *)assemble_kernel<T, 0>, CELL_BLOCK, 0));
+        assemble_kernel<T, 0><<<g, CELL_BLOCK, 0, s>>>(a);
+    }
+    count_launch();
+    if (mask) {
+        k_csr_diag_ones<T><<<vgrid(m->n_dofs()), 256, 0, s>>>(mask, m->row_ptr, m->col, vals, m->n_dofs());
+        count_launch();
+    }
+    FEM_CUDA(cudaGetLastError());
+    return FEM_OK;
+}
+
+}  // namespace femgb
+
+using namespace femgb;
+
+#define CHECK_PREC(p)                                                                             \
+    if ((p) != FEM_FP64 && (p) != FEM_FP32)                                                       \
+        return (set_error("cell operators take FEM_FP64 or FEM_FP32"), FEM_ERR_ARG);
+
+extern "C" int fem_residual(fem_mesh_t m, const fem_material *mat, int precision, const void *u,
+                            const void *cell_param, const uint8_t *mask, const void *f_ext, void *r, void *stream)
+{
+    if (!m || !u || !r) return (set_error("fem_residual: NULL argument"), FEM_ERR_ARG);
+    if (int rc = check_material(mat)) return rc;
+    CHECK_PREC(precision);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == FEM_FP64)
+        return residual_t<double>(m, mat, (const double *)u, (const double *)cell_param, mask, (const double *)f_ext,
+                                  (double *)r, s);
+    return residual_t<float>(m, mat, (const float *)u, (const float *)cell_param, mask, (const float *)f_ext,
+                             (float *)r, s);
+}
+
+extern "C" int fem_tangent_apply(fem_mesh_t m, const fem_material *mat, int precision, const void *u,
+                                 const void *cell_param, const uint8_t *mask, const void *x, void *y, void *stream)
+{
+    if (!m || !u || !x || !y) return (set_error("fem_tangent_apply: NULL argument"), FEM_ERR_ARG);
+    if (x == y) return (set_error("fem_tangent_apply: y must not alias x"), FEM_ERR_ARG);
+    if (int rc = check_material(mat)) return rc;
+    CHECK_PREC(precision);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == FEM_FP64)
+        return apply_t<double>(m, mat, (const double *)u, (const double *)cell_param, mask, (const double *)x,
+                               (double *)y, s);
+    return apply_t<float>(m, mat, (const float *)u, (const float *)cell_param, mask, (const float *)x, (float *)y, s);
+}
+
+extern "C" int fem_tangent_diag(fem_mesh_t m, const fem_material *mat, int precision, const void *u,
+                                const void *cell_param, const uint8_t *mask, void *d, void *stream)
+{
+    if (!m || !u || !d) return (set_error("fem_tangent_diag: NULL argument"), FEM_ERR_ARG);
+    if (int rc = check_material(mat)) return rc;
+    CHECK_PREC(precision);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == FEM_FP64)
+        return diag_t<double>(m, mat, (const double *)u, (const double *)cell_param, mask, (double *)d, s);
+    return diag_t<float>(m, mat, (const float *)u, (const float *)cell_param, mask, (float *)d, s);
+}
+
+extern "C" int fem_vjp(fem_mesh_t m, const fem_material *mat, int precision, const void *u, const void *lambda,
+                       const void *cell_param, const uint8_t *mask, void *g, void *stream)
+{
+    if (!m || !u || !lambda || !g) return (set_error("fem_vjp: NULL argument"), FEM_ERR_ARG);
+    if (int rc = check_material(mat)) return rc;
+    CHECK_PREC(precision);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == FEM_FP64)
+        return vjp_t<double>(m, mat, (const double *)u, (const double *)lambda, (const double *)cell_param, mask,
+                             (double *)g, s);
+    return vjp_t<float>(m, mat, (const float *)u, (const float *)lambda, (const float *)cell_param, mask, (float *)g, s);
+}
+
+extern "C" int fem_assemble_csr(fem_mesh_t m, const fem_material *mat, int precision, const void *u,
+                                const void *cell_param, const uint8_t *mask, void *vals, void *stream)
+{
+    if (!m || !u || !vals) return (set_error("fem_assemble_csr: NULL argument"), FEM_ERR_ARG);
+    if (!m->row_ptr) return (set_error("fem_assemble_csr: mesh built without FEM_MESH_CSR"), FEM_ERR_ARG);
+    if (int rc = check_material(mat)) return rc;
+    CHECK_PREC(precision);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == FEM_FP64)
+        return assemble_t<double>(m, mat, (const double *)u, (const double *)cell_param, mask, (double *)vals, s);
+    return assemble_t<float>(m, mat, (const float *)u, (const float *)cell_param, mask, (float *)vals, s);
+}

@@ -1,0 +1,325 @@
+// fem_internal.cuh -- shared definitions of the CUDA library (not part of the ABI).
+//
+// Everything in the library is batched by construction: kernels take a table
+// of instance descriptors (InstDesc) and process the concatenation of all
+// instances' cells / DOFs.  A single-mesh call is a batch of one whose
+// descriptor travels by value in the kernel arguments.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "../../include/fem.h"
+
+namespace femgb {
+
+// ------------------------------------------------------------ descriptors --
+struct InstDesc {
+    int nx, ny, nz;
+    int kind;              // fem_material_kind
+    double E, nu, p, emin; // material
+    double hx, hy, hz;     // cell sizes
+    int64_t dof_off;       // first DOF of this instance in concatenated vectors
+    int64_t cell_off;      // first cell (cell_param / per-cell outputs)
+    int64_t tile_off;      // first cell tile (cell kernels)
+    int64_t vec_off;       // first vector chunk (vector kernels)
+    __host__ __device__ int64_t n_dofs() const { return 3LL * (nx + 1) * (ny + 1) * (nz + 1); }
+    __host__ __device__ int64_t n_cells() const { return (int64_t)nx * ny * nz; }
+};
+
+// Per-instance solver state, device resident.  The PCG scalars live in a
+// ring of three slots indexed by the CG iteration, so a slot can be cleared
+// one iteration ahead without a separate reset launch.
+struct Ctl {
+    int n_steps;
+    int step;       // current load step, 1-based
+    int need_bc;    // set prescribed DOFs for `step` at the next head
+    int newton_it;  // iterations in the current step
+    int status;     // 0 running, 1 finished, < 0 fem_status error
+    int solving;    // a CG solve runs in this round
+    int pcg_base;   // CG iterations completed before the current chunk
+    int pcg_done;   // CG of this round finished
+    int pcg_last;   // iterations of the last CG
+    int jflag;      // det F <= 0 seen by the residual kernel
+    int newton_total;
+    int pcg_total;
+    int steps_done;
+    int pad_;
+    double r_ref;   // ||R_free|| at step 1, iteration 0
+    double r_norm2; // accumulator of ||R_free||^2
+    double r_norm;  // last ||R_free||
+    double eta;     // CG relative tolerance
+    double rr0;     // ||r_0||^2 of the current CG
+    double pAp[3], rz[3], rr[3];
+};
+
+// ----------------------------------------------------------- launch count --
+// Kernels launched by this library (graph replays count their kernel nodes).
+// Launches issued while a graph is being captured are counted at replay.
+extern std::atomic<int64_t> g_launches;
+extern thread_local bool t_capturing;
+inline void count_launch(int64_t n = 1)
+{
+    if (!t_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define FEM_CUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return ::femgb::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+// ------------------------------------------------------- device helpers ---
+constexpr int CELL_BLOCK = 128;  // default cells per CTA (one thread per cell)
+constexpr int VEC_BLOCK = 256;   // threads per CTA of the vector kernels
+constexpr int VEC_CHUNK = 2048;  // DOFs per vector work item
+
+__device__ __forceinline__ int find_inst(const InstDesc *tab, int n, int64_t item, bool tiles)
+{
+    // last instance whose offset <= item (offsets ascending)
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        int64_t off = tiles ? tab[mid].tile_off : tab[mid].vec_off;
+        if (off <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of one value; the result is valid in thread 0.
+template <typename T, int NT>
+__device__ __forceinline__ T block_sum(T v, T *sh)
+{
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();  // sh may still be read by a previous call
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    T s = 0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NT / 32; ++i) s += sh[i];
+    }
+    return s;
+}
+
+// ------------------------------------------------ HEX8 on a uniform box ----
+// Reference cell [-1,1]^3, trilinear shape functions written as tensor
+// products phi_p(xi) phi_q(eta) phi_r(zeta), phi_0(s) = (1-s)/2,
+// phi_1(s) = (1+s)/2.  Local node n = p + 2q + 4r.  Gauss points +-1/sqrt(3),
+// weights 1.  At Gauss coordinate g (0: -1/sqrt3, 1: +1/sqrt3) the
+// interpolation matrix B[g][node] = phi_node(s_g) is [[CA, CB], [CB, CA]].
+// On an axis-aligned cell of size (hx, hy, hz) the x-derivative of a
+// trilinear field does not depend on xi, so at the 8 Gauss points it takes
+// only 4 values indexed by (beta, gamma); likewise y (alpha, gamma) and z
+// (alpha, beta).  This sum-factorised form is exact for the uniform box.
+#define FEM_CA 0.78867513459481288225457439025098   // (1 + 1/sqrt(3)) / 2
+#define FEM_CB 0.21132486540518711774542560974902   // (1 - 1/sqrt(3)) / 2
+
+// W[a + 2b] = sum_{i,j} B[a][i] B[b][j] d[i + 2j]; B is symmetric, so the
+// same operator is its own transpose.
+template <typename T>
+__device__ __forceinline__ void interp2(T d00, T d10, T d01, T d11, T *W)
+{
+    const T ca = (T)FEM_CA, cb = (T)FEM_CB;
+    T s00 = ca * d00 + cb * d10;  // a=0, j=0
+    T s10 = cb * d00 + ca * d10;  // a=1, j=0
+    T s01 = ca * d01 + cb * d11;  // a=0, j=1
+    T s11 = cb * d01 + ca * d11;  // a=1, j=1
+    W[0] = ca * s00 + cb * s01;
+    W[1] = ca * s10 + cb * s11;
+    W[2] = cb * s00 + ca * s01;
+    W[3] = cb * s10 + ca * s11;
+}
+
+// Gradient values of one scalar nodal field v[8] (node n = p+2q+4r):
+// G[0][b+2g] = dv/dx at (.,b,g), G[1][a+2g] = dv/dy at (a,.,g),
+// G[2][a+2b] = dv/dz at (a,b,.).  ih = 1/h per direction.
+template <typename T>
+__device__ __forceinline__ void grad_sf(const T *v, T ihx, T ihy, T ihz, T G[3][4])
+{
+    interp2<T>((v[1] - v[0]) * ihx, (v[3] - v[2]) * ihx, (v[5] - v[4]) * ihx, (v[7] - v[6]) * ihx, G[0]);
+    interp2<T>((v[2] - v[0]) * ihy, (v[3] - v[1]) * ihy, (v[6] - v[4]) * ihy, (v[7] - v[5]) * ihy, G[1]);
+    interp2<T>((v[4] - v[0]) * ihz, (v[5] - v[1]) * ihz, (v[6] - v[2]) * ihz, (v[7] - v[3]) * ihz, G[2]);
+}
+
+// Transpose of grad_sf: given S[d][.] = sum over the remaining Gauss index of
+// the flux component along direction d (already weighted), accumulate
+// y[n] += sum_gp flux . grad N_n.
+template <typename T>
+__device__ __forceinline__ void grad_sf_t(T S[3][4], T ihx, T ihy, T ihz, T *y)
+{
+    T W[4];
+    interp2<T>(S[0][0], S[0][1], S[0][2], S[0][3], W);  // W[q + 2r]
+    y[1] += W[0] * ihx; y[0] -= W[0] * ihx;
+    y[3] += W[1] * ihx; y[2] -= W[1] * ihx;
+    y[5] += W[2] * ihx; y[4] -= W[2] * ihx;
+    y[7] += W[3] * ihx; y[6] -= W[3] * ihx;
+    interp2<T>(S[1][0], S[1][1], S[1][2], S[1][3], W);  // W[p + 2r]
+    y[2] += W[0] * ihy; y[0] -= W[0] * ihy;
+    y[3] += W[1] * ihy; y[1] -= W[1] * ihy;
+    y[6] += W[2] * ihy; y[4] -= W[2] * ihy;
+    y[7] += W[3] * ihy; y[5] -= W[3] * ihy;
+    interp2<T>(S[2][0], S[2][1], S[2][2], S[2][3], W);  // W[p + 2q]
+    y[4] += W[0] * ihz; y[0] -= W[0] * ihz;
+    y[5] += W[1] * ihz; y[1] -= W[1] * ihz;
+    y[6] += W[2] * ihz; y[2] -= W[2] * ihz;
+    y[7] += W[3] * ihz; y[3] -= W[3] * ihz;
+}
+
+// -------------------------------------------------- constitutive laws ----
+// Material constants of one cell (already scaled by its stiffness factor).
+template <typename T>
+struct Mat {
+    T c1, c2;  // LE/SIMP: lam, mu.  NH: G, kappa.
+};
+
+// det(I + H) - 1 without cancellation: tr H + (tr^2 H - tr H^2)/2 + det H.
+template <typename T>
+__device__ __forceinline__ T det_ipH_m1(const T *H)
+{
+    T tr = H[0] + H[4] + H[8];
+    T tr2 = H[0] * H[0] + H[4] * H[4] + H[8] * H[8] + (T)2 * (H[1] * H[3] + H[2] * H[6] + H[5] * H[7]);
+    T dH = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+           H[2] * (H[3] * H[7] - H[4] * H[6]);
+    return tr + (T)0.5 * (tr * tr - tr2) + dH;
+}
+
+__device__ __forceinline__ float rcbrt_t(float x) { return rcbrtf(x); }
+__device__ __forceinline__ double rcbrt_t(double x) { return rcbrt(x); }
+
+// Neo-Hookean kinematics at one Gauss point: A = F^{-T}, J, J-1, I1, G J^{-2/3}.
+template <typename T>
+struct NHPoint {
+    T F[9], A[9];
+    T J, Jm1, I1, k1;
+};
+
+template <typename T>
+__device__ __forceinline__ void nh_point(const T *H, const Mat<T> &m, NHPoint<T> &q)
+{
+#pragma unroll
+    for (int t = 0; t < 9; ++t) q.F[t] = H[t] + ((t % 4) == 0 ? (T)1 : (T)0);
+    const T *F = q.F;
+    T c00 = F[4] * F[8] - F[5] * F[7], c01 = F[5] * F[6] - F[3] * F[8], c02 = F[3] * F[7] - F[4] * F[6];
+    T c10 = F[2] * F[7] - F[1] * F[8], c11 = F[0] * F[8] - F[2] * F[6], c12 = F[1] * F[6] - F[0] * F[7];
+    T c20 = F[1] * F[5] - F[2] * F[4], c21 = F[2] * F[3] - F[0] * F[5], c22 = F[0] * F[4] - F[1] * F[3];
+    q.Jm1 = det_ipH_m1(H);
+    q.J = (T)1 + q.Jm1;
+    T iJ = (T)1 / q.J;
+    q.A[0] = c00 * iJ; q.A[1] = c01 * iJ; q.A[2] = c02 * iJ;
+    q.A[3] = c10 * iJ; q.A[4] = c11 * iJ; q.A[5] = c12 * iJ;
+    q.A[6] = c20 * iJ; q.A[7] = c21 * iJ; q.A[8] = c22 * iJ;
+    T I1 = 0;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) I1 += F[t] * F[t];
+    q.I1 = I1;
+    T r = rcbrt_t(q.J);
+    q.k1 = m.c1 * r * r;  // G J^{-2/3}
+}
+
+// First Piola-Kirchhoff stress P = G J^{-2/3} (F - I1/3 A) + kappa J (J-1) A.
+template <typename T>
+__device__ __forceinline__ void nh_stress(const NHPoint<T> &q, const Mat<T> &m, T *P)
+{
+    T a = q.k1 * q.I1 * (T)(1.0 / 3.0);
+    T b = m.c2 * q.J * q.Jm1;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) P[t] = q.k1 * q.F[t] + (b - a) * q.A[t];
+}
+
+// dP = k1 dF + kA A + kF F + kdA dA with dA = -A dF^T A, c = A:dF, dI1 = 2F:dF,
+// kA = k1 (-dI1/3 + 2/9 c I1) + kappa (2J-1) J c, kF = -2/3 k1 c,
+// kdA = kappa J (J-1) - k1 I1/3  (directional derivative of nh_stress).
+template <typename T>
+__device__ __forceinline__ void nh_dstress(const NHPoint<T> &q, const Mat<T> &m, const T *dF, T *dP)
+{
+    T c = 0, dI1 = 0;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        c += q.A[t] * dF[t];
+        dI1 += q.F[t] * dF[t];
+    }
+    dI1 *= (T)2;
+    const T *A = q.A;
+    // M = A dF^T  (M_ij = sum_k A_ik dF_jk)
+    T M[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            M[3 * i + j] = A[3 * i] * dF[3 * j] + A[3 * i + 1] * dF[3 * j + 1] + A[3 * i + 2] * dF[3 * j + 2];
+    T kA = q.k1 * ((T)(2.0 / 9.0) * c * q.I1 - dI1 * (T)(1.0 / 3.0)) + m.c2 * ((T)1 + (T)2 * q.Jm1) * q.J * c;
+    T kF = (T)(-2.0 / 3.0) * q.k1 * c;
+    T kdA = q.k1 * q.I1 * (T)(1.0 / 3.0) - m.c2 * q.J * q.Jm1;  // = -(coefficient of dA)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            // (M A)_ij, dA = -(M A); dP += coef(dA) * dA = kdA * (M A)
+            T MA = M[3 * i] * A[j] + M[3 * i + 1] * A[3 + j] + M[3 * i + 2] * A[6 + j];
+            dP[3 * i + j] = q.k1 * dF[3 * i + j] + kA * A[3 * i + j] + kF * q.F[3 * i + j] + kdA * MA;
+        }
+}
+
+// Linear elasticity (also the SIMP-scaled law): P = lam tr(H) I + mu (H + H^T).
+template <typename T>
+__device__ __forceinline__ void le_stress(const T *H, const Mat<T> &m, T *P)
+{
+    T tr = m.c1 * (H[0] + H[4] + H[8]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            P[3 * i + j] = m.c2 * (H[3 * i + j] + H[3 * j + i]) + (i == j ? tr : (T)0);
+}
+
+// Cell material constants from the instance and the cell parameter.
+template <typename T>
+__device__ __forceinline__ Mat<T> cell_mat(const InstDesc &d, const T *cell_param, int64_t cell)
+{
+    double s = 1.0;
+    Mat<T> m;
+    if (d.kind == FEM_SIMP) {
+        T th = cell_param ? cell_param[cell] : (T)1;
+        T sp = (d.p == 3.0) ? th * th * th : (T)pow((double)th, d.p);
+        T sc = (T)d.emin + sp * (T)(1.0 - d.emin);
+        T E = (T)d.E * sc;
+        m.c1 = E * (T)(d.nu / ((1.0 + d.nu) * (1.0 - 2.0 * d.nu)));
+        m.c2 = E * (T)(1.0 / (2.0 * (1.0 + d.nu)));
+        return m;
+    }
+    T sc = cell_param ? cell_param[cell] : (T)s;
+    T E = (T)d.E * sc;
+    if (d.kind == FEM_NEOHOOKE) {
+        m.c1 = E * (T)(1.0 / (2.0 * (1.0 + d.nu)));
+        m.c2 = E * (T)(1.0 / (3.0 * (1.0 - 2.0 * d.nu)));
+    } else {
+        m.c1 = E * (T)(d.nu / ((1.0 + d.nu) * (1.0 - 2.0 * d.nu)));
+        m.c2 = E * (T)(1.0 / (2.0 * (1.0 + d.nu)));
+    }
+    return m;
+}
+
+// d(scale)/d(theta) of the cell parameter (1 for a plain stiffness scale).
+__device__ __forceinline__ double cell_dscale(const InstDesc &d, double th)
+{
+    if (d.kind != FEM_SIMP) return 1.0;
+    return d.p * pow(th, d.p - 1.0) * (1.0 - d.emin);
+}
+
+}  // namespace femgb

@@ -1,0 +1,1004 @@
+// solver.cu -- Newton (Sec. 2.1, Eq. (4)) with load stepping, Jacobi-PCG on
+// the matrix-free tangent, FP64 iterative refinement for linear problems,
+// the adjoint gradient (Sec. 3, Eqs. (22)-(23)) and the batched launcher.
+//
+// Design.  Every decision of the solver lives on the device in one control
+// block per instance (Ctl); kernels are gated per instance, so one code path
+// serves one mesh or hundreds of meshes of uneven size.  A Newton round is
+// three CUDA graphs replayed on an internal stream:
+//   head  : set prescribed DOFs -> FP64 residual -> norm -> control decision
+//           -> diagonal -> CG start
+//   chunk : `pcg_chunk` CG iterations (apply, update 1, update 2) + count
+//   tail  : u += du (FP64) -> bookkeeping, fused with the next head
+// The host only reads back three counters per graph (how many instances are
+// solving / iterating / active).  The paper's linear solver is BiCGSTAB with
+// Jacobi (Sec. 5 item 2); the tangent of all three laws here is symmetric,
+// so CG is used.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <mutex>
+#include <type_traits>
+#include <vector>
+
+#include "cell_ops.cuh"
+#include "mesh.cuh"
+
+namespace femgb {
+
+struct SolverParams {
+    double rtol, atol;
+    int maxit;
+    double eta;
+    int pcg_maxit;
+    int chunk;
+};
+
+enum SolveMode { SM_NONLINEAR = 0, SM_LINEAR = 1 };
+
+template <typename T>
+struct VecArgs {
+    InstDesc d0;
+    const InstDesc *tab;
+    int n_inst;
+    int64_t n_items;
+    Ctl *ctl;
+    double *u64;        // unknown (displacement, or the adjoint variable)
+    double *R64;        // FP64 residual
+    const double *rhs;  // f_ext (nonlinear) or dJ/du (linear); may be null
+    const double *ubar; // final prescribed values
+    const uint8_t *mask;
+    T *uT;              // state copy in T used by the T cell kernels
+    int write_uT;       // refresh uT from u64 after updates
+    T *x, *r, *z, *p, *q, *dg;
+    int iter;
+    SolverParams prm;
+    int *counter;       // [0] solving, [1] iterating, [2] active
+};
+
+#define VEC_ITEMS_BEGIN                                                       \
+    for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {    \
+        int k = 0;                                                            \
+        InstDesc d;                                                           \
+        if (a.tab) {                                                          \
+            k = find_inst(a.tab, a.n_inst, item, false);                      \
+            d = a.tab[k];                                                     \
+        } else {                                                              \
+            d = a.d0;                                                         \
+        }                                                                     \
+        Ctl &c = a.ctl[k];                                                    \
+        const int64_t i0 = (item - d.vec_off) * VEC_CHUNK;                    \
+        const int64_t i1 = min(i0 + (int64_t)VEC_CHUNK, d.n_dofs());          \
+        const int64_t base = d.dof_off;                                       \
+        (void)base;
+
+#define VEC_ITEMS_END }
+
+template <typename T>
+__global__ void __launch_bounds__(VEC_BLOCK) k_bc(const VecArgs<T> a)
+{
+    VEC_ITEMS_BEGIN
+    if (c.status != 0 || !c.need_bc) continue;
+    const double f = (double)c.step / (double)c.n_steps;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int64_t j = base + i;
+        if (a.mask[j]) {
+            const double v = f * a.ubar[j];
+            a.u64[j] = v;
+            if (a.write_uT) a.uT[j] = (T)v;
+        }
+    }
+    VEC_ITEMS_END
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VEC_BLOCK) k_res_init(const VecArgs<T> a)
+{
+    VEC_ITEMS_BEGIN
+    if (c.status != 0) continue;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int64_t j = base + i;
+        a.R64[j] = a.rhs ? -a.rhs[j] : 0.0;
+    }
+    VEC_ITEMS_END
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VEC_BLOCK) k_res_finish(const VecArgs<T> a)
+{
+    __shared__ double sh[VEC_BLOCK / 32];
+    VEC_ITEMS_BEGIN
+    if (c.status != 0) continue;
+    double acc = 0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int64_t j = base + i;
+        const double R = a.mask[j] ? 0.0 : a.R64[j];
+        a.R64[j] = R;
+        acc += R * R;
+        a.r[j] = (T)(-R);
+        a.x[j] = 0;
+        a.q[j] = 0;
+        a.dg[j] = 0;
+    }
+    double s = block_sum<double, VEC_BLOCK>(acc, sh);
+    if (threadIdx.x == 0) atomicAdd(&c.r_norm2, s);
+    VEC_ITEMS_END
+}
+
+__global__ void k_control(Ctl *ctl, int n_inst, SolverParams prm, int *counter)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_inst) return;
+    Ctl &c = ctl[k];
+    c.need_bc = 0;
+    c.solving = 0;
+    if (c.status != 0) return;
+    const double rn = sqrt(c.r_norm2);
+    c.r_norm2 = 0;
+    c.r_norm = rn;
+    if (!isfinite(rn)) { c.status = FEM_ERR_NONFINITE; return; }
+    if (c.jflag) { c.status = FEM_ERR_INVERTED; return; }
+    if (c.r_ref < 0) c.r_ref = rn > 0 ? rn : 1.0;
+    if (rn <= prm.rtol * c.r_ref || rn <= prm.atol) {
+        c.steps_done++;
+        if (c.step >= c.n_steps) {
+            c.status = 1;
+        } else {
+            c.step++;
+            c.need_bc = 1;
+            c.newton_it = 0;
+        }
+        return;
+    }
+    if (c.newton_it >= prm.maxit) { c.status = FEM_ERR_NOT_CONVERGED; return; }
+    c.newton_it++;
+    c.newton_total++;
+    c.solving = 1;
+    c.pcg_base = 0;
+    c.pcg_done = 0;
+    c.pcg_last = 0;
+    c.rr0 = 0;
+    c.eta = prm.eta;
+    for (int s = 0; s < 3; ++s) c.pAp[s] = c.rz[s] = c.rr[s] = 0;
+    atomicAdd(&counter[0], 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VEC_BLOCK) k_pcg_init(const VecArgs<T> a)
+{
+    __shared__ double sh[VEC_BLOCK / 32];
+    VEC_ITEMS_BEGIN
+    if (c.status != 0 || !c.solving) continue;
+    T arz = 0, arr = 0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int64_t j = base + i;
+        const T dv = a.dg[j];
+        const T inv = (a.mask[j] || dv == (T)0) ? (T)0 : (T)1 / dv;
+        a.dg[j] = inv;
+        const T rv = a.r[j];
+        const T zv = inv * rv;
+        a.z[j] = zv;
+        a.p[j] = zv;
+        arz += rv * zv;
+        arr += rv * rv;
+    }
+    double s1 = block_sum<double, VEC_BLOCK>((double)arz, sh);
+    if (threadIdx.x == 0) atomicAdd(&c.rz[2], s1);
+    double s2 = block_sum<double, VEC_BLOCK>((double)arr, sh);
+    if (threadIdx.x == 0) atomicAdd(&c.rr0, s2);
+    VEC_ITEMS_END
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VEC_BLOCK) k_pcg_u1(const VecArgs<T> a)
+{
+    __shared__ double sh[VEC_BLOCK / 32];
+    VEC_ITEMS_BEGIN
+    if (c.status != 0 || !c.solving || c.pcg_done) continue;
+    const int it = c.pcg_base + a.iter;
+    const int s = it % 3, sp = (it + 2) % 3, sn = (it + 1) % 3;
+    const double pAp = c.pAp[s];
+    if (!(pAp > 0.0) || !isfinite(pAp)) continue;  // breakdown: decided in k_pcg_u2
+    const T alpha = (T)(c.rz[sp] / pAp);
+    T arz = 0, arr = 0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int64_t j = base + i;
+        const T pv = a.p[j], qv = a.q[j], inv = a.dg[j];
+        a.x[j] += alpha * pv;
+        T rv = a.r[j];
+        if (inv != (T)0) rv -= alpha * qv;
+        a.r[j] = rv;
+        const T zv = inv * rv;
+        a.z[j] = zv;
+        a.q[j] = 0;
+        arz += rv * zv;
+        arr += rv * rv;
+    }
+    double s1 = block_sum<double, VEC_BLOCK>((double)arz, sh);
+    if (threadIdx.x == 0) atomicAdd(&c.rz[s], s1);
+    double s2 = block_sum<double, VEC_BLOCK>((double)arr, sh);
+    if (threadIdx.x == 0) atomicAdd(&c.rr[s], s2);
+    if (item == d.vec_off && threadIdx.x == 0) {
+        c.pAp[sn] = 0;
+        c.rz[sn] = 0;
+        c.rr[sn] = 0;
+    }
+    VEC_ITEMS_END
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VEC_BLOCK) k_pcg_u2(const VecArgs<T> a)
+{
+    VEC_ITEMS_BEGIN
+    if (c.status != 0 || !c.solving || c.pcg_done) continue;
+    const int it = c.pcg_base + a.iter;
+    const int s = it % 3, sp = (it + 2) % 3;
+    const bool lead = (item == d.vec_off) && threadIdx.x == 0;
+    if (c.rr0 == 0.0) {
+        if (lead) { c.pcg_done = 1; c.pcg_last = it; }
+        continue;
+    }
+    const double pAp = c.pAp[s], rr = c.rr[s];
+    if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(rr)) {
+        if (lead) {
+            c.status = isfinite(pAp) && isfinite(rr) ? FEM_ERR_BREAKDOWN : FEM_ERR_NONFINITE;
+            c.pcg_done = 1;
+            c.pcg_last = it + 1;
+        }
+        continue;
+    }
+    if (rr <= c.eta * c.eta * c.rr0 || it + 1 >= a.prm.pcg_maxit) {
+        if (lead) { c.pcg_done = 1; c.pcg_last = it + 1; }
+        continue;
+    }
+    const T beta = (T)(c.rz[s] / c.rz[sp]);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int64_t j = base + i;
+        a.p[j] = a.z[j] + beta * a.p[j];
+    }
+    VEC_ITEMS_END
+}
+
+__global__ void k_chunk_ctl(Ctl *ctl, int n_inst, int chunk, int *counter)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_inst) return;
+    Ctl &c = ctl[k];
+    if (c.status == 0 && c.solving && !c.pcg_done) {
+        c.pcg_base += chunk;
+        atomicAdd(&counter[1], 1);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VEC_BLOCK) k_newton_update(const VecArgs<T> a)
+{
+    VEC_ITEMS_BEGIN
+    if (c.status != 0 || !c.solving) continue;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int64_t j = base + i;
+        const double v = a.u64[j] + (double)a.x[j];
+        a.u64[j] = v;
+        if (a.write_uT) a.uT[j] = (T)v;
+    }
+    VEC_ITEMS_END
+}
+
+__global__ void k_tail_ctl(Ctl *ctl, int n_inst, int *counter)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_inst) return;
+    Ctl &c = ctl[k];
+    if (c.solving) {
+        c.pcg_total += c.pcg_last;
+        c.solving = 0;
+    }
+    if (c.status == 0) atomicAdd(&counter[2], 1);
+}
+
+template <typename T>
+__global__ void k_convert(T *dst, const double *src, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (T)src[i];
+}
+
+__global__ void k_add(double *y, const double *x, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += x[i];
+}
+
+static int vec_grid(int64_t n_items)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)device_sms() * 8));
+}
+
+// ------------------------------------------------------------ the core -----
+struct Problem {
+    std::vector<InstDesc> desc;  // offsets filled by layout()
+    std::vector<int> n_steps;
+    int64_t D = 0, Ne = 0, n_tiles = 0, n_items = 0;
+    bool nh = false;
+
+    void layout()
+    {
+        D = Ne = n_tiles = n_items = 0;
+        for (auto &d : desc) {
+            d.dof_off = D;
+            d.cell_off = Ne;
+            d.tile_off = n_tiles;
+            d.vec_off = n_items;
+            D += d.n_dofs();
+            Ne += d.n_cells();
+            n_tiles += (d.n_cells() + CELL_BLOCK - 1) / CELL_BLOCK;
+            n_items += (d.n_dofs() + VEC_CHUNK - 1) / VEC_CHUNK;
+        }
+    }
+};
+
+// Device buffers of one solve (all owned by a Workspace).
+template <typename T>
+struct Buffers {
+    Ctl *ctl;
+    int *counter;
+    InstDesc *tab;
+    double *u64, *R64;
+    const double *rhs, *ubar;
+    const uint8_t *mask;
+    const double *cp64;  // per-cell parameter (double), may be null
+    T *cpT;              // the same in T (== cp64 when T = double)
+    T *uT;
+    T *x, *r, *z, *p, *q, *dg;
+};
+
+struct Graphs {
+    cudaGraphExec_t head = nullptr, chunk = nullptr, tail_head = nullptr;
+    int64_t n_head = 0, n_chunk = 0, n_tail_head = 0;
+    ~Graphs()
+    {
+        if (head) cudaGraphExecDestroy(head);
+        if (chunk) cudaGraphExecDestroy(chunk);
+        if (tail_head) cudaGraphExecDestroy(tail_head);
+    }
+};
+
+static int64_t count_kernel_nodes(cudaGraph_t g)
+{
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    cudaGraphGetNodes(g, nodes.data(), &n);
+    int64_t k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
+template <typename T>
+class Core {
+  public:
+    Core(const Problem &pb, const Buffers<T> &b, SolveMode mode, const SolverParams &prm, int *h_counter)
+        : pb_(pb), b_(b), mode_(mode), prm_(prm), h_counter_(h_counter)
+    {
+        va_ = VecArgs<T>{};
+        va_.d0 = pb.desc[0];
+        va_.tab = pb.desc.size() > 1 ? b.tab : nullptr;
+        va_.n_inst = (int)pb.desc.size();
+        va_.n_items = pb.n_items;
+        va_.ctl = b.ctl;
+        va_.u64 = b.u64;
+        va_.R64 = b.R64;
+        va_.rhs = b.rhs;
+        va_.ubar = b.ubar;
+        va_.mask = b.mask;
+        va_.uT = b.uT;
+        va_.write_uT = (mode == SM_NONLINEAR && (void *)b.uT != (void *)b.u64) ? 1 : 0;
+        va_.x = b.x; va_.r = b.r; va_.z = b.z; va_.p = b.p; va_.q = b.q; va_.dg = b.dg;
+        va_.prm = prm;
+        va_.counter = b.counter;
+    }
+
+    cudaError_t enqueue_head(cudaStream_t s)
+    {
+        cudaError_t e;
+        const int gv = vec_grid(pb_.n_items);
+        const int ni = va_.n_inst, gi = (ni + 127) / 128;
+        if ((e = cudaMemsetAsync(b_.counter, 0, sizeof(int), s)) != cudaSuccess) return e;
+        if (mode_ == SM_NONLINEAR) {
+            k_bc<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
+            count_launch();
+        }
+        k_res_init<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
+        count_launch();
+        {
+            CellArgs<double> ca{};
+            ca.d0 = pb_.desc[0];
+            ca.tab = va_.tab;
+            ca.n_inst = ni;
+            ca.n_tiles = pb_.n_tiles;
+            ca.ctl = b_.ctl;
+            ca.cell_param = b_.cp64;
+            ca.y = b_.R64;
+            if (mode_ == SM_NONLINEAR) {
+                ca.u = b_.u64;
+                if ((e = launch_cell<double>(CM_RESIDUAL_CTL, pb_.nh, ca, s)) != cudaSuccess) return e;
+            } else {
+                ca.u = ustar64_;
+                ca.x = b_.u64;
+                ca.mask = b_.mask;
+                if ((e = launch_cell<double>(CM_APPLY_CTL, pb_.nh, ca, s)) != cudaSuccess) return e;
+            }
+        }
+        k_res_finish<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
+        k_control<<<gi, 128, 0, s>>>(b_.ctl, ni, prm_, b_.counter);
+        count_launch(2);
+        {
+            CellArgs<T> ca{};
+            ca.d0 = pb_.desc[0];
+            ca.tab = va_.tab;
+            ca.n_inst = ni;
+            ca.n_tiles = pb_.n_tiles;
+            ca.ctl = b_.ctl;
+            ca.cell_param = b_.cpT;
+            ca.u = b_.uT;
+            ca.y = b_.dg;
+            if ((e = launch_cell<T>(CM_DIAG_CTL, pb_.nh, ca, s)) != cudaSuccess) return e;
+        }
+        k_pcg_init<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
+        count_launch();
+        return cudaGetLastError();
+    }
+
+    cudaError_t enqueue_chunk(cudaStream_t s)
+    {
+        cudaError_t e;
+        const int gv = vec_grid(pb_.n_items);
+        const int ni = va_.n_inst, gi = (ni + 127) / 128;
+        if ((e = cudaMemsetAsync(b_.counter + 1, 0, sizeof(int), s)) != cudaSuccess) return e;
+        CellArgs<T> ca{};
+        ca.d0 = pb_.desc[0];
+        ca.tab = va_.tab;
+        ca.n_inst = ni;
+        ca.n_tiles = pb_.n_tiles;
+        ca.ctl = b_.ctl;
+        ca.cell_param = b_.cpT;
+        ca.u = b_.uT;
+        ca.x = b_.p;
+        ca.y = b_.q;
+        for (int j = 0; j < prm_.chunk; ++j) {
+            ca.iter = j;
+            if (j == 0 && ev_a_ && (e = cudaEventRecordWithFlags(ev_a_, s, cudaEventRecordExternal)) != cudaSuccess)
+                return e;
+            if ((e = launch_cell<T>(CM_APPLY_PCG, pb_.nh, ca, s)) != cudaSuccess) return e;
+            if (j == 0 && ev_b_ && (e = cudaEventRecordWithFlags(ev_b_, s, cudaEventRecordExternal)) != cudaSuccess)
+                return e;
+            VecArgs<T> v = va_;
+            v.iter = j;
+            k_pcg_u1<T><<<gv, VEC_BLOCK, 0, s>>>(v);
+            k_pcg_u2<T><<<gv, VEC_BLOCK, 0, s>>>(v);
+            count_launch(2);
+        }
+        k_chunk_ctl<<<gi, 128, 0, s>>>(b_.ctl, ni, prm_.chunk, b_.counter);
+        count_launch();
+        return cudaGetLastError();
+    }
+
+    cudaError_t enqueue_tail(cudaStream_t s)
+    {
+        cudaError_t e;
+        const int gv = vec_grid(pb_.n_items);
+        const int ni = va_.n_inst, gi = (ni + 127) / 128;
+        if ((e = cudaMemsetAsync(b_.counter + 2, 0, sizeof(int), s)) != cudaSuccess) return e;
+        k_newton_update<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
+        k_tail_ctl<<<gi, 128, 0, s>>>(b_.ctl, ni, b_.counter);
+        count_launch(2);
+        return cudaGetLastError();
+    }
+
+    cudaError_t capture(cudaStream_t s, int which, cudaGraphExec_t *out, int64_t *n_kernels)
+    {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        t_capturing = true;
+        cudaError_t e2 = cudaSuccess;
+        if (which == 0) e2 = enqueue_head(s);
+        else if (which == 1) e2 = enqueue_chunk(s);
+        else {
+            e2 = enqueue_tail(s);
+            if (e2 == cudaSuccess) e2 = enqueue_head(s);
+        }
+        if (e2 == cudaSuccess)
+            e2 = cudaMemcpyAsync(h_counter_, b_.counter, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
+        t_capturing = false;
+        e = cudaStreamEndCapture(s, &g);
+        if (e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return e2;
+        }
+        if (e != cudaSuccess) return e;
+        *n_kernels = count_kernel_nodes(g);
+        e = cudaGraphInstantiate(out, g, 0);
+        cudaGraphDestroy(g);
+        return e;
+    }
+
+    // Returns FEM_OK or an error; per-instance outcomes stay in the Ctl blocks.
+    int run(cudaStream_t s, double timeout_s)
+    {
+        Graphs G;
+        struct EvPair {
+            cudaEvent_t a = nullptr, b = nullptr;
+            ~EvPair()
+            {
+                if (a) cudaEventDestroy(a);
+                if (b) cudaEventDestroy(b);
+            }
+        } ev;
+        if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) {
+            cudaGetLastError();
+            ev.a = ev.b = nullptr;
+        }
+        ev_a_ = ev.a;
+        ev_b_ = ev.b;
+        warm_occupancy(pb_.nh);
+        FEM_CUDA(capture(s, 0, &G.head, &G.n_head));
+        FEM_CUDA(capture(s, 1, &G.chunk, &G.n_chunk));
+        FEM_CUDA(capture(s, 2, &G.tail_head, &G.n_tail_head));
+        auto t0 = std::chrono::steady_clock::now();
+        auto expired = [&]() {
+            if (timeout_s <= 0) return false;
+            return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > timeout_s;
+        };
+        FEM_CUDA(cudaGraphLaunch(G.head, s));
+        count_launch(G.n_head);
+        FEM_CUDA(cudaStreamSynchronize(s));
+        int n_solving = h_counter_[0];
+        const int64_t max_rounds = (int64_t)(prm_.maxit + 2) * max_steps_ * 4 + 16;
+        const int64_t max_chunks = (int64_t)prm_.pcg_maxit / std::max(1, prm_.chunk) + 2;
+        for (int64_t round = 0;; ++round) {
+            if (n_solving > 0) {
+                for (int64_t ch = 0; ch < max_chunks; ++ch) {
+                    FEM_CUDA(cudaGraphLaunch(G.chunk, s));
+                    count_launch(G.n_chunk);
+                    FEM_CUDA(cudaStreamSynchronize(s));
+                    if (ev_a_) {
+                        float ms = 0;
+                        if (cudaEventElapsedTime(&ms, ev_a_, ev_b_) == cudaSuccess) {
+                            apply_ms_ += ms;
+                            apply_samples_++;
+                        } else {
+                            cudaGetLastError();
+                        }
+                    }
+                    if (h_counter_[1] == 0) break;
+                    if (expired()) return (set_error("solve watchdog expired"), FEM_ERR_TIMEOUT);
+                }
+            }
+            FEM_CUDA(cudaGraphLaunch(G.tail_head, s));
+            count_launch(G.n_tail_head);
+            FEM_CUDA(cudaStreamSynchronize(s));
+            n_solving = h_counter_[0];
+            if (h_counter_[2] == 0) break;
+            if (expired() || round >= max_rounds) return (set_error("solve watchdog expired"), FEM_ERR_TIMEOUT);
+        }
+        return FEM_OK;
+    }
+
+    const double *ustar64_ = nullptr;  // linear mode: the fixed state
+    int max_steps_ = 1;
+    double apply_ms_ = 0;   // sampled device time of CG applies
+    int apply_samples_ = 0;
+    cudaEvent_t ev_a_ = nullptr, ev_b_ = nullptr;
+
+  private:
+    const Problem &pb_;
+    Buffers<T> b_;
+    SolveMode mode_;
+    SolverParams prm_;
+    int *h_counter_;
+    VecArgs<T> va_;
+};
+
+// Pinned host counters shared by all solves of one thread.
+static int *host_counters()
+{
+    static thread_local int *h = nullptr;
+    if (!h) {
+        if (cudaHostAlloc((void **)&h, 4 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            h = nullptr;
+        }
+    }
+    return h;
+}
+
+static SolverParams params_from(const fem_options &o)
+{
+    SolverParams p;
+    p.rtol = o.newton_rtol;
+    p.atol = o.newton_atol;
+    p.maxit = o.newton_maxit;
+    p.eta = o.pcg_rtol;
+    p.pcg_maxit = o.pcg_maxit;
+    p.chunk = o.pcg_chunk > 0 ? o.pcg_chunk : 16;
+    return p;
+}
+
+static int check_options(const fem_options &o)
+{
+    if (o.precision != FEM_MIXED && o.precision != FEM_FP64)
+        return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
+    if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
+        !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1)
+        return (set_error("invalid solver options"), FEM_ERR_ARG);
+    return FEM_OK;
+}
+
+// Internal stream of the calling thread (graphs cannot be captured on the
+// legacy default stream a caller may pass).
+static cudaStream_t internal_stream()
+{
+    static thread_local cudaStream_t s = nullptr;
+    if (!s) cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    return s;
+}
+
+static cudaError_t join_streams(cudaStream_t from, cudaStream_t to)
+{
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev, from);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
+    cudaEventDestroy(ev);
+    return e;
+}
+
+// Workspace slots
+enum {
+    WS_CTL = 0, WS_CNT, WS_R64, WS_UT, WS_X, WS_R, WS_Z, WS_P, WS_Q, WS_DG, WS_LAM, WS_TAB, WS_CPT,
+    WS_U64CAT, WS_MASKCAT, WS_UBARCAT, WS_RHSCAT, WS_CP64CAT, WS_G64
+};
+
+template <typename T>
+static int alloc_buffers(Workspace &ws, const Problem &pb, Buffers<T> &b, bool need_uT, bool need_cpT)
+{
+    const int64_t D = pb.D, n = (int64_t)pb.desc.size();
+#define WSGET(dst, slot, type, cnt)                              \
+    do {                                                         \
+        dst = (type *)ws.get(slot, sizeof(type) * (size_t)(cnt)); \
+        if (!dst) return FEM_ERR_NOMEM;                          \
+    } while (0)
+    WSGET(b.ctl, WS_CTL, Ctl, n);
+    WSGET(b.counter, WS_CNT, int, 4);
+    WSGET(b.R64, WS_R64, double, D);
+    WSGET(b.x, WS_X, T, D);
+    WSGET(b.r, WS_R, T, D);
+    WSGET(b.z, WS_Z, T, D);
+    WSGET(b.p, WS_P, T, D);
+    WSGET(b.q, WS_Q, T, D);
+    WSGET(b.dg, WS_DG, T, D);
+    if (n > 1) WSGET(b.tab, WS_TAB, InstDesc, n);
+    else b.tab = nullptr;
+    if (need_uT) WSGET(b.uT, WS_UT, T, D);
+    if (need_cpT) WSGET(b.cpT, WS_CPT, T, pb.Ne);
+#undef WSGET
+    return FEM_OK;
+}
+
+static std::vector<Ctl> initial_ctl(const Problem &pb, int step_begin, bool linear)
+{
+    std::vector<Ctl> v(pb.desc.size());
+    for (size_t k = 0; k < v.size(); ++k) {
+        Ctl c{};
+        c.n_steps = linear ? 1 : pb.n_steps[k];
+        c.step = linear ? 1 : std::min(step_begin, c.n_steps);
+        c.need_bc = linear ? 0 : 1;
+        c.r_ref = -1.0;
+        v[k] = c;
+    }
+    return v;
+}
+
+struct ApplyTiming {
+    double ms = 0;
+    int samples = 0;
+};
+
+static void fill_stats(const Ctl &c, fem_stats *st, double ms, const ApplyTiming &at = ApplyTiming())
+{
+    if (!st) return;
+    st->apply_ms = at.ms;
+    st->apply_samples = at.samples;
+    st->apply_launches = c.pcg_total;
+    st->status = c.status == 1 ? FEM_OK : (c.status == 0 ? FEM_ERR_NOT_CONVERGED : c.status);
+    st->load_steps = c.steps_done;
+    st->newton_iters = c.newton_total;
+    st->pcg_iters = c.pcg_total;
+    st->ref_rnorm = c.r_ref;
+    st->final_rnorm = c.r_norm;
+    st->time_ms = ms;
+}
+
+// Solve one batch (shared by fem_solve and fem_solve_batched).
+template <typename T>
+static int solve_batch(Workspace &ws, Problem &pb, double *u64, const uint8_t *mask, const double *ubar,
+                       const double *rhs, const double *cp64, const fem_options &o, std::vector<Ctl> &ctl_out,
+                       ApplyTiming &at, cudaStream_t s)
+{
+    int *hc = host_counters();
+    if (!hc) return (set_error("pinned host allocation failed"), FEM_ERR_NOMEM);
+    const bool sepT = !std::is_same<T, double>::value;
+    Buffers<T> b{};
+    if (int rc = alloc_buffers<T>(ws, pb, b, sepT, sepT && cp64 != nullptr)) return rc;
+    b.u64 = u64;
+    b.mask = mask;
+    b.ubar = ubar;
+    b.rhs = rhs;
+    b.cp64 = cp64;
+    if (!sepT) {
+        b.uT = (T *)u64;
+        b.cpT = (T *)cp64;
+    } else if (!cp64) {
+        b.cpT = nullptr;
+    }
+    std::vector<Ctl> ctl = initial_ctl(pb, o.step_begin, false);
+    FEM_CUDA(cudaMemcpyAsync(b.ctl, ctl.data(), sizeof(Ctl) * ctl.size(), cudaMemcpyHostToDevice, s));
+    if (b.tab) FEM_CUDA(cudaMemcpyAsync(b.tab, pb.desc.data(), sizeof(InstDesc) * pb.desc.size(), cudaMemcpyHostToDevice, s));
+    if (sepT) {
+        k_convert<T><<<vec_grid(pb.n_items), 256, 0, s>>>(b.uT, u64, pb.D);
+        count_launch();
+        if (cp64) {
+            k_convert<T><<<vec_grid(pb.n_items), 256, 0, s>>>(b.cpT, cp64, pb.Ne);
+            count_launch();
+        }
+        FEM_CUDA(cudaGetLastError());
+    }
+    Core<T> core(pb, b, SM_NONLINEAR, params_from(o), hc);
+    core.max_steps_ = *std::max_element(pb.n_steps.begin(), pb.n_steps.end());
+    int rc = core.run(s, o.timeout_s);
+    at.ms = core.apply_ms_;
+    at.samples = core.apply_samples_;
+    ctl_out.resize(ctl.size());
+    cudaError_t e = cudaMemcpyAsync(ctl_out.data(), b.ctl, sizeof(Ctl) * ctl.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (rc) return rc;
+    FEM_CUDA(e);
+    return FEM_OK;
+}
+
+// Linear adjoint solve K(u*) lam = g with FP64 refinement, then the VJP.
+template <typename T>
+static int adjoint_batch(Workspace &ws, Problem &pb, const double *ustar, const uint8_t *mask, const double *g,
+                         const double *cp64, double *lam, const fem_options &o, Ctl &ctl_out, ApplyTiming &at,
+                         cudaStream_t s)
+{
+    int *hc = host_counters();
+    if (!hc) return (set_error("pinned host allocation failed"), FEM_ERR_NOMEM);
+    const bool sepT = !std::is_same<T, double>::value;
+    Buffers<T> b{};
+    if (int rc = alloc_buffers<T>(ws, pb, b, sepT, sepT && cp64 != nullptr)) return rc;
+    b.u64 = lam;
+    b.mask = mask;
+    b.ubar = nullptr;
+    b.rhs = g;
+    b.cp64 = cp64;
+    if (!sepT) {
+        b.uT = (T *)ustar;
+        b.cpT = (T *)cp64;
+    } else {
+        k_convert<T><<<vec_grid(pb.n_items), 256, 0, s>>>(b.uT, ustar, pb.D);
+        count_launch();
+        if (cp64) {
+            k_convert<T><<<vec_grid(pb.n_items), 256, 0, s>>>(b.cpT, cp64, pb.Ne);
+            count_launch();
+        } else {
+            b.cpT = nullptr;
+        }
+    }
+    FEM_CUDA(cudaMemsetAsync(lam, 0, sizeof(double) * pb.D, s));
+    std::vector<Ctl> ctl = initial_ctl(pb, 1, true);
+    FEM_CUDA(cudaMemcpyAsync(b.ctl, ctl.data(), sizeof(Ctl) * ctl.size(), cudaMemcpyHostToDevice, s));
+    SolverParams prm = params_from(o);
+    Core<T> core(pb, b, SM_LINEAR, prm, hc);
+    core.ustar64_ = ustar;
+    int rc = core.run(s, o.timeout_s);
+    at.ms = core.apply_ms_;
+    at.samples = core.apply_samples_;
+    cudaError_t e = cudaMemcpyAsync(&ctl_out, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (rc) return rc;
+    FEM_CUDA(e);
+    return FEM_OK;
+}
+
+}  // namespace femgb
+
+using namespace femgb;
+
+static int bc_check(fem_mesh_t m, const fem_bc *bc, bool need_ubar)
+{
+    if (!m || !bc || !bc->mask || (need_ubar && !bc->u_bar))
+        return (set_error("bc: mesh, mask and u_bar are required"), FEM_ERR_ARG);
+    return FEM_OK;
+}
+
+extern "C" int fem_solve(fem_mesh_t m, const fem_material *mat, const fem_bc *bc, const double *cell_param,
+                         int n_steps, const fem_options *opt, double *u_inout, fem_stats *stats, void *stream)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (int rc = bc_check(m, bc, true)) return rc;
+    if (int rc = check_material(mat)) return rc;
+    if (!u_inout || n_steps < 1) return (set_error("fem_solve: u_inout NULL or n_steps < 1"), FEM_ERR_ARG);
+    fem_options o;
+    fem_default_options(&o);
+    if (opt) o = *opt;
+    if (int rc = check_options(o)) return rc;
+    std::lock_guard<std::mutex> lk(m->mu);
+    Problem pb;
+    pb.desc.push_back(make_desc(m, mat));
+    pb.n_steps.push_back(n_steps);
+    pb.nh = mat->kind == FEM_NEOHOOKE;
+    pb.layout();
+    cudaStream_t s = internal_stream();
+    FEM_CUDA(join_streams((cudaStream_t)stream, s));
+    std::vector<Ctl> ctl;
+    ApplyTiming at;
+    int rc = o.precision == FEM_FP64
+                 ? solve_batch<double>(m->ws, pb, u_inout, bc->mask, bc->u_bar, bc->f_ext, cell_param, o, ctl, at, s)
+                 : solve_batch<float>(m->ws, pb, u_inout, bc->mask, bc->u_bar, bc->f_ext, cell_param, o, ctl, at, s);
+    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (!ctl.empty()) fill_stats(ctl[0], stats, ms, at);
+    if (rc) {
+        if (stats) stats->status = rc;
+        return rc;
+    }
+    return ctl[0].status == 1 ? FEM_OK : (ctl[0].status == 0 ? FEM_ERR_NOT_CONVERGED : ctl[0].status);
+}
+
+extern "C" int fem_adjoint(fem_mesh_t m, const fem_material *mat, const fem_bc *bc, const double *u_star,
+                           const double *cell_param, const double *dJdu, const double *dJdtheta_explicit,
+                           const fem_options *opt, double *dJdtheta_out, double *lambda_out, fem_stats *stats,
+                           void *stream)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (int rc = bc_check(m, bc, false)) return rc;
+    if (int rc = check_material(mat)) return rc;
+    if (!u_star || !dJdu || !dJdtheta_out) return (set_error("fem_adjoint: NULL argument"), FEM_ERR_ARG);
+    fem_options o;
+    fem_default_options(&o);
+    if (opt) o = *opt;
+    if (int rc = check_options(o)) return rc;
+    std::lock_guard<std::mutex> lk(m->mu);
+    Problem pb;
+    pb.desc.push_back(make_desc(m, mat));
+    pb.n_steps.push_back(1);
+    pb.nh = mat->kind == FEM_NEOHOOKE;
+    pb.layout();
+    cudaStream_t s = internal_stream();
+    FEM_CUDA(join_streams((cudaStream_t)stream, s));
+    double *lam = lambda_out;
+    if (!lam) {
+        lam = (double *)m->ws.get(WS_LAM, sizeof(double) * pb.D);
+        if (!lam) return FEM_ERR_NOMEM;
+    }
+    Ctl ctl{};
+    ApplyTiming at;
+    int rc = o.precision == FEM_FP64
+                 ? adjoint_batch<double>(m->ws, pb, u_star, bc->mask, dJdu, cell_param, lam, o, ctl, at, s)
+                 : adjoint_batch<float>(m->ws, pb, u_star, bc->mask, dJdu, cell_param, lam, o, ctl, at, s);
+    if (rc == FEM_OK && ctl.status == 1) {
+        // dJ/dtheta = -lambda^T dC/dtheta (FP64 VJP) + explicit part
+        CellArgs<double> ca{};
+        ca.d0 = pb.desc[0];
+        ca.n_tiles = pb.n_tiles;
+        ca.u = u_star;
+        ca.x = lam;
+        ca.cell_param = cell_param;
+        ca.mask = bc->mask;
+        ca.g = dJdtheta_out;
+        cudaError_t e = launch_cell<double>(CM_VJP, pb.nh, ca, s);
+        if (e == cudaSuccess && dJdtheta_explicit) {
+            k_add<<<vec_grid(pb.Ne / 1024 + 1), 256, 0, s>>>(dJdtheta_out, dJdtheta_explicit, pb.Ne);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "adjoint VJP", __FILE__, __LINE__);
+    }
+    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    fill_stats(ctl, stats, ms, at);
+    if (rc) {
+        if (stats) stats->status = rc;
+        return rc;
+    }
+    return ctl.status == 1 ? FEM_OK : (ctl.status == 0 ? FEM_ERR_NOT_CONVERGED : ctl.status);
+}
+
+namespace femgb {
+static std::mutex g_batch_mu;
+static Workspace g_batch_ws;
+}  // namespace femgb
+
+extern "C" int fem_solve_batched(int n_inst, const fem_instance *inst, const fem_options *opt, fem_stats *stats,
+                                 void *stream)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (n_inst < 1 || !inst) return (set_error("fem_solve_batched: no instances"), FEM_ERR_ARG);
+    fem_options o;
+    fem_default_options(&o);
+    if (opt) o = *opt;
+    if (int rc = check_options(o)) return rc;
+    Problem pb;
+    bool any_cp = false;
+    for (int k = 0; k < n_inst; ++k) {
+        const fem_instance &I = inst[k];
+        if (int rc = bc_check(I.mesh, &I.bc, true)) return rc;
+        if (int rc = check_material(&I.mat)) return rc;
+        if (!I.u_inout || I.n_steps < 1) return (set_error("fem_solve_batched: bad instance"), FEM_ERR_ARG);
+        if ((I.mat.kind == FEM_NEOHOOKE) != (inst[0].mat.kind == FEM_NEOHOOKE))
+            return (set_error("fem_solve_batched: all instances need the same law family"), FEM_ERR_ARG);
+        pb.desc.push_back(make_desc(I.mesh, &I.mat));
+        pb.n_steps.push_back(I.n_steps);
+        any_cp |= I.cell_param != nullptr;
+    }
+    pb.nh = inst[0].mat.kind == FEM_NEOHOOKE;
+    pb.layout();
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    Workspace &ws = g_batch_ws;
+    cudaStream_t s = internal_stream();
+    FEM_CUDA(join_streams((cudaStream_t)stream, s));
+    double *u64 = (double *)ws.get(WS_U64CAT, sizeof(double) * pb.D);
+    uint8_t *mask = (uint8_t *)ws.get(WS_MASKCAT, pb.D);
+    double *ubar = (double *)ws.get(WS_UBARCAT, sizeof(double) * pb.D);
+    double *rhs = (double *)ws.get(WS_RHSCAT, sizeof(double) * pb.D);
+    double *cp = any_cp ? (double *)ws.get(WS_CP64CAT, sizeof(double) * pb.Ne) : nullptr;
+    if (!u64 || !mask || !ubar || !rhs || (any_cp && !cp)) return FEM_ERR_NOMEM;
+    for (int k = 0; k < n_inst; ++k) {
+        const fem_instance &I = inst[k];
+        const InstDesc &d = pb.desc[k];
+        const int64_t Dk = d.n_dofs(), Nk = d.n_cells();
+        FEM_CUDA(cudaMemcpyAsync(u64 + d.dof_off, I.u_inout, sizeof(double) * Dk, cudaMemcpyDeviceToDevice, s));
+        FEM_CUDA(cudaMemcpyAsync(mask + d.dof_off, I.bc.mask, Dk, cudaMemcpyDeviceToDevice, s));
+        FEM_CUDA(cudaMemcpyAsync(ubar + d.dof_off, I.bc.u_bar, sizeof(double) * Dk, cudaMemcpyDeviceToDevice, s));
+        if (I.bc.f_ext)
+            FEM_CUDA(cudaMemcpyAsync(rhs + d.dof_off, I.bc.f_ext, sizeof(double) * Dk, cudaMemcpyDeviceToDevice, s));
+        else
+            FEM_CUDA(cudaMemsetAsync(rhs + d.dof_off, 0, sizeof(double) * Dk, s));
+        if (cp) {
+            if (I.cell_param)
+                FEM_CUDA(cudaMemcpyAsync(cp + d.cell_off, I.cell_param, sizeof(double) * Nk, cudaMemcpyDeviceToDevice, s));
+            else {
+                std::vector<double> ones(Nk, 1.0);
+                FEM_CUDA(cudaMemcpyAsync(cp + d.cell_off, ones.data(), sizeof(double) * Nk, cudaMemcpyHostToDevice, s));
+                FEM_CUDA(cudaStreamSynchronize(s));
+            }
+        }
+    }
+    std::vector<Ctl> ctl;
+    ApplyTiming at;
+    int rc = o.precision == FEM_FP64 ? solve_batch<double>(ws, pb, u64, mask, ubar, rhs, cp, o, ctl, at, s)
+                                     : solve_batch<float>(ws, pb, u64, mask, ubar, rhs, cp, o, ctl, at, s);
+    if (rc == FEM_OK) {
+        for (int k = 0; k < n_inst; ++k) {
+            const InstDesc &d = pb.desc[k];
+            FEM_CUDA(cudaMemcpyAsync(inst[k].u_inout, u64 + d.dof_off, sizeof(double) * d.n_dofs(),
+                                     cudaMemcpyDeviceToDevice, s));
+        }
+        FEM_CUDA(cudaStreamSynchronize(s));
+    }
+    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    int worst = FEM_OK;
+    for (int k = 0; k < (int)ctl.size(); ++k) {
+        fem_stats st{};
+        fill_stats(ctl[k], &st, ms, at);
+        if (stats) stats[k] = st;
+        if (st.status != FEM_OK && worst == FEM_OK) worst = st.status;
+    }
+    if (rc) return rc;
+    return worst;
+}

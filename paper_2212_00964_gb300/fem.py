@@ -1,0 +1,352 @@
+"""Thin Python binding of the C-ABI in include/fem.h (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Arrays are torch
+CUDA tensors (device memory and the current stream come from PyTorch); every
+computation runs in libfemgb.so.  If the library is missing the binding
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_lib", "libfemgb.so")
+
+FEM_OK = 0
+FEM_ERR_ARG, FEM_ERR_CUDA, FEM_ERR_NOT_CONVERGED, FEM_ERR_INVERTED = -1, -2, -3, -4
+FEM_ERR_BREAKDOWN, FEM_ERR_NONFINITE, FEM_ERR_TIMEOUT, FEM_ERR_NOMEM = -5, -6, -7, -8
+FEM_LINEAR, FEM_SIMP, FEM_NEOHOOKE = 0, 1, 2
+FEM_FP64, FEM_FP32, FEM_MIXED = 0, 1, 2
+FEM_MESH_CSR = 1
+FACES = {"x0": 0, "x1": 1, "y0": 2, "y1": 3, "z0": 4, "z1": 5}
+
+
+class FemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class fem_material(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("E", ctypes.c_double), ("nu", ctypes.c_double),
+                ("simp_p", ctypes.c_double), ("simp_emin", ctypes.c_double)]
+
+
+class fem_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("newton_rtol", ctypes.c_double),
+                ("newton_atol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
+                ("pcg_rtol", ctypes.c_double), ("pcg_maxit", ctypes.c_int),
+                ("pcg_chunk", ctypes.c_int), ("step_begin", ctypes.c_int),
+                ("cells_per_block", ctypes.c_int), ("deterministic", ctypes.c_int),
+                ("timeout_s", ctypes.c_double)]
+
+
+class fem_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("load_steps", ctypes.c_int), ("newton_iters", ctypes.c_int),
+                ("pcg_iters", ctypes.c_int), ("ref_rnorm", ctypes.c_double),
+                ("final_rnorm", ctypes.c_double), ("time_ms", ctypes.c_double),
+                ("apply_ms", ctypes.c_double), ("apply_samples", ctypes.c_int), ("apply_launches", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class fem_bc(ctypes.Structure):
+    _fields_ = [("mask", ctypes.c_void_p), ("u_bar", ctypes.c_void_p), ("f_ext", ctypes.c_void_p)]
+
+
+class fem_instance(ctypes.Structure):
+    _fields_ = [("mesh", ctypes.c_void_p), ("mat", fem_material), ("bc", fem_bc),
+                ("cell_param", ctypes.c_void_p), ("n_steps", ctypes.c_int), ("u_inout", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libfemgb.so (built by ``paper_2212_00964_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_SO):
+        raise RuntimeError(f"{_SO} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(_SO)
+    P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    MP = ctypes.POINTER(fem_material)
+    L.fem_mesh.argtypes = [I, I, I, D, D, D, I, P, ctypes.POINTER(P)]
+    L.fem_mesh_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    L.fem_mesh_export.argtypes = [P] * 8 + [P]
+    L.fem_mesh_destroy.argtypes = [P]
+    L.fem_load_traction.argtypes = [P, I, P, P, P]
+    L.fem_load_body.argtypes = [P, P, P, P]
+    L.fem_residual.argtypes = [P, MP, I, P, P, P, P, P, P]
+    L.fem_tangent_apply.argtypes = [P, MP, I, P, P, P, P, P, P]
+    L.fem_tangent_diag.argtypes = [P, MP, I, P, P, P, P, P]
+    L.fem_vjp.argtypes = [P, MP, I, P, P, P, P, P, P]
+    L.fem_assemble_csr.argtypes = [P, MP, I, P, P, P, P, P]
+    L.fem_default_options.argtypes = [ctypes.POINTER(fem_options)]
+    L.fem_default_options.restype = None
+    L.fem_solve.argtypes = [P, MP, ctypes.POINTER(fem_bc), P, I, ctypes.POINTER(fem_options), P,
+                            ctypes.POINTER(fem_stats), P]
+    L.fem_adjoint.argtypes = [P, MP, ctypes.POINTER(fem_bc), P, P, P, P, ctypes.POINTER(fem_options),
+                              P, P, ctypes.POINTER(fem_stats), P]
+    L.fem_solve_batched.argtypes = [I, ctypes.POINTER(fem_instance), ctypes.POINTER(fem_options),
+                                    ctypes.POINTER(fem_stats), P]
+    L.fem_status_string.argtypes = [I]
+    L.fem_status_string.restype = ctypes.c_char_p
+    L.fem_last_error.restype = ctypes.c_char_p
+    L.fem_kernel_launches.restype = I64
+    _lib = L
+    return L
+
+
+def _check(rc, what):
+    if rc != FEM_OK:
+        L = lib()
+        raise FemError(rc, f"{what}: {L.fem_status_string(rc).decode()}: {L.fem_last_error().decode()}")
+    return rc
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=None, n=None, name="array"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def kernel_launches() -> int:
+    return int(lib().fem_kernel_launches())
+
+
+def material(kind, E, nu, simp_p=3.0, simp_emin=1e-3) -> fem_material:
+    return fem_material(int(kind), float(E), float(nu), float(simp_p), float(simp_emin))
+
+
+def default_options(**kw) -> fem_options:
+    o = fem_options()
+    lib().fem_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Mesh:
+    """Owner of a fem_mesh_t handle."""
+
+    def __init__(self, handle, nx, ny, nz, lx, ly, lz, csr):
+        self.handle = handle
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.lx, self.ly, self.lz = lx, ly, lz
+        self.csr = csr
+        n = ctypes.c_int64()
+        e = ctypes.c_int64()
+        z = ctypes.c_int64()
+        _check(lib().fem_mesh_info(handle, ctypes.byref(n), ctypes.byref(e), ctypes.byref(z)), "fem_mesh_info")
+        self.n_nodes, self.n_cells, self.nnz = n.value, e.value, z.value
+
+    @property
+    def n_dofs(self):
+        return 3 * self.n_nodes
+
+    def close(self):
+        if self.handle:
+            lib().fem_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fem_mesh(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, csr=False, stream=None) -> Mesh:
+    h = ctypes.c_void_p()
+    _check(lib().fem_mesh(nx, ny, nz, lx, ly, lz, FEM_MESH_CSR if csr else 0, _stream(stream), ctypes.byref(h)),
+           "fem_mesh")
+    return Mesh(h, nx, ny, nz, lx, ly, lz, csr)
+
+
+def fem_mesh_export(m: Mesh, stream=None, csr=False):
+    dev = torch.device("cuda")
+    out = {
+        "conn": torch.empty((m.n_cells, 8), dtype=torch.int32, device=dev),
+        "X": torch.empty((m.n_nodes, 3), dtype=torch.float64, device=dev),
+        "colour_ptr": torch.empty(9, dtype=torch.int32, device=dev),
+        "cell_perm": torch.empty(m.n_cells, dtype=torch.int32, device=dev),
+    }
+    if csr:
+        out["row_ptr"] = torch.empty(m.n_dofs + 1, dtype=torch.int32, device=dev)
+        out["col"] = torch.empty(m.nnz, dtype=torch.int32, device=dev)
+        out["map"] = torch.empty((m.n_cells, 24, 24), dtype=torch.int32, device=dev)
+    g = lambda k: _ptr(out.get(k))
+    _check(lib().fem_mesh_export(m.handle, g("conn"), g("X"), g("colour_ptr"), g("cell_perm"), g("row_ptr"),
+                                 g("col"), g("map"), _stream(stream)), "fem_mesh_export")
+    return out
+
+
+def fem_load_traction(m: Mesh, face, t, f_ext: torch.Tensor, stream=None):
+    tt = (ctypes.c_double * 3)(*[float(v) for v in t])
+    fid = FACES[face] if isinstance(face, str) else int(face)
+    _check(lib().fem_load_traction(m.handle, fid, tt, _ptr(f_ext, torch.float64, m.n_dofs, "f_ext"),
+                                   _stream(stream)), "fem_load_traction")
+    return f_ext
+
+
+def fem_load_body(m: Mesh, b, f_ext: torch.Tensor, stream=None):
+    bb = (ctypes.c_double * 3)(*[float(v) for v in b])
+    _check(lib().fem_load_body(m.handle, bb, _ptr(f_ext, torch.float64, m.n_dofs, "f_ext"), _stream(stream)),
+           "fem_load_body")
+    return f_ext
+
+
+def _prec(dtype):
+    if dtype == torch.float64:
+        return FEM_FP64
+    if dtype == torch.float32:
+        return FEM_FP32
+    raise TypeError("cell operators take float64 or float32 tensors")
+
+
+def fem_residual(m: Mesh, mat: fem_material, u, cell_param=None, mask=None, f_ext=None, r=None, stream=None):
+    dt = u.dtype
+    r = torch.empty_like(u) if r is None else r
+    _check(lib().fem_residual(m.handle, ctypes.byref(mat), _prec(dt), _ptr(u, dt, m.n_dofs, "u"),
+                              _ptr(cell_param, dt, m.n_cells, "cell_param"),
+                              _ptr(mask, torch.uint8, m.n_dofs, "mask"), _ptr(f_ext, dt, m.n_dofs, "f_ext"),
+                              _ptr(r, dt, m.n_dofs, "r"), _stream(stream)), "fem_residual")
+    return r
+
+
+def fem_tangent_apply(m: Mesh, mat: fem_material, u, x, cell_param=None, mask=None, y=None, stream=None):
+    dt = u.dtype
+    y = torch.empty_like(x) if y is None else y
+    _check(lib().fem_tangent_apply(m.handle, ctypes.byref(mat), _prec(dt), _ptr(u, dt, m.n_dofs, "u"),
+                                   _ptr(cell_param, dt, m.n_cells, "cell_param"),
+                                   _ptr(mask, torch.uint8, m.n_dofs, "mask"), _ptr(x, dt, m.n_dofs, "x"),
+                                   _ptr(y, dt, m.n_dofs, "y"), _stream(stream)), "fem_tangent_apply")
+    return y
+
+
+def fem_tangent_diag(m: Mesh, mat: fem_material, u, cell_param=None, mask=None, d=None, stream=None):
+    dt = u.dtype
+    d = torch.empty_like(u) if d is None else d
+    _check(lib().fem_tangent_diag(m.handle, ctypes.byref(mat), _prec(dt), _ptr(u, dt, m.n_dofs, "u"),
+                                  _ptr(cell_param, dt, m.n_cells, "cell_param"),
+                                  _ptr(mask, torch.uint8, m.n_dofs, "mask"), _ptr(d, dt, m.n_dofs, "d"),
+                                  _stream(stream)), "fem_tangent_diag")
+    return d
+
+
+def fem_vjp(m: Mesh, mat: fem_material, u, lam, cell_param=None, mask=None, g=None, stream=None):
+    dt = u.dtype
+    g = torch.empty(m.n_cells, dtype=dt, device=u.device) if g is None else g
+    _check(lib().fem_vjp(m.handle, ctypes.byref(mat), _prec(dt), _ptr(u, dt, m.n_dofs, "u"),
+                         _ptr(lam, dt, m.n_dofs, "lambda"), _ptr(cell_param, dt, m.n_cells, "cell_param"),
+                         _ptr(mask, torch.uint8, m.n_dofs, "mask"), _ptr(g, dt, m.n_cells, "g"),
+                         _stream(stream)), "fem_vjp")
+    return g
+
+
+def fem_assemble_csr(m: Mesh, mat: fem_material, u, cell_param=None, mask=None, vals=None, stream=None):
+    dt = u.dtype
+    vals = torch.empty(m.nnz, dtype=dt, device=u.device) if vals is None else vals
+    _check(lib().fem_assemble_csr(m.handle, ctypes.byref(mat), _prec(dt), _ptr(u, dt, m.n_dofs, "u"),
+                                  _ptr(cell_param, dt, m.n_cells, "cell_param"),
+                                  _ptr(mask, torch.uint8, m.n_dofs, "mask"), _ptr(vals, dt, m.nnz, "vals"),
+                                  _stream(stream)), "fem_assemble_csr")
+    return vals
+
+
+def _bc(m: Mesh, mask, u_bar=None, f_ext=None) -> fem_bc:
+    return fem_bc(_ptr(mask, torch.uint8, m.n_dofs, "mask"), _ptr(u_bar, torch.float64, m.n_dofs, "u_bar"),
+                  _ptr(f_ext, torch.float64, m.n_dofs, "f_ext"))
+
+
+def fem_solve(m: Mesh, mat: fem_material, mask, u_bar, u, f_ext=None, cell_param=None, n_steps=1,
+              options: Optional[fem_options] = None, stream=None, check=True):
+    """Solve in place into u (float64 [D]); returns the fem_stats as a dict."""
+    bc = _bc(m, mask, u_bar, f_ext)
+    st = fem_stats()
+    rc = lib().fem_solve(m.handle, ctypes.byref(mat), ctypes.byref(bc),
+                         _ptr(cell_param, torch.float64, m.n_cells, "cell_param"), int(n_steps),
+                         ctypes.byref(options) if options is not None else None,
+                         _ptr(u, torch.float64, m.n_dofs, "u"), ctypes.byref(st), _stream(stream))
+    if check:
+        _check(rc, "fem_solve")
+    d = st.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def fem_adjoint(m: Mesh, mat: fem_material, mask, u_star, dJdu, cell_param=None, dJdtheta_explicit=None,
+                options: Optional[fem_options] = None, lam=None, stream=None, check=True):
+    """Returns (dJ/dtheta [Ne] float64, stats dict)."""
+    g = torch.empty(m.n_cells, dtype=torch.float64, device=u_star.device)
+    bc = _bc(m, mask)
+    st = fem_stats()
+    rc = lib().fem_adjoint(m.handle, ctypes.byref(mat), ctypes.byref(bc),
+                           _ptr(u_star, torch.float64, m.n_dofs, "u_star"),
+                           _ptr(cell_param, torch.float64, m.n_cells, "cell_param"),
+                           _ptr(dJdu, torch.float64, m.n_dofs, "dJdu"),
+                           _ptr(dJdtheta_explicit, torch.float64, m.n_cells, "dJdtheta_explicit"),
+                           ctypes.byref(options) if options is not None else None,
+                           _ptr(g, torch.float64, m.n_cells, "dJdtheta_out"),
+                           _ptr(lam, torch.float64, m.n_dofs, "lambda_out"), ctypes.byref(st), _stream(stream))
+    if check:
+        _check(rc, "fem_adjoint")
+    d = st.as_dict()
+    d["rc"] = rc
+    return g, d
+
+
+@dataclass
+class Instance:
+    mesh: Mesh
+    mat: fem_material
+    mask: torch.Tensor
+    u_bar: torch.Tensor
+    u: torch.Tensor
+    n_steps: int = 1
+    f_ext: Optional[torch.Tensor] = None
+    cell_param: Optional[torch.Tensor] = None
+
+
+def fem_solve_batched(instances: Sequence[Instance], options: Optional[fem_options] = None, stream=None,
+                      check=True):
+    n = len(instances)
+    arr = (fem_instance * n)()
+    for k, I in enumerate(instances):
+        m = I.mesh
+        arr[k].mesh = m.handle
+        arr[k].mat = I.mat
+        arr[k].bc = _bc(m, I.mask, I.u_bar, I.f_ext)
+        arr[k].cell_param = _ptr(I.cell_param, torch.float64, m.n_cells, "cell_param")
+        arr[k].n_steps = int(I.n_steps)
+        arr[k].u_inout = _ptr(I.u, torch.float64, m.n_dofs, "u")
+    stats = (fem_stats * n)()
+    rc = lib().fem_solve_batched(n, arr, ctypes.byref(options) if options is not None else None, stats,
+                                 _stream(stream))
+    if check:
+        _check(rc, "fem_solve_batched")
+    return rc, [s.as_dict() for s in stats]

@@ -1,0 +1,123 @@
+"""GPU parity of the solvers against the oracle's Newton / spsolve solutions:
+the linear-elastic c0 solve (FP64 and mixed), Neo-Hookean load-stepped
+Newton (FP64 and mixed with FP64 refinement), SIMP solve, and the 64^3
+Neo-Hookean benchmark solve checked by properties that hold at any size
+(mixed vs FP64 GPU solution, oracle FP64 residual at the GPU solution)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import solve as osolve
+from paper_2212_00964_gb300 import inputs
+from tests.gpu_common import TOL_FP64, TOL_REFINED, dev, fem, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_solve(w, precision, f_ext=None, **opt):
+    F = fem()
+    m = F.fem_mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)
+    if f_ext is None and w.traction is not None:
+        f = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
+        F.fem_load_traction(m, w.traction[0], w.traction[1], f)
+    elif f_ext is not None:
+        f = dev(f_ext)
+    elif w.point_load is not None:
+        f = dev(w.point_load)
+    else:
+        f = None
+    u = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
+    o = F.default_options(precision=precision, **opt)
+    cp = None if w.cell_param is None else dev(w.cell_param)
+    st = F.fem_solve(m, F.material(w.kind, w.E, w.nu, w.simp_p, w.simp_emin), dev(w.mask), dev(w.u_bar), u,
+                     f, cp, w.n_steps, o)
+    return host(u), st
+
+
+def oracle_solve(w):
+    om = oracle.mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)
+    mat = oracle.Material(w.kind, w.E, w.nu, w.simp_p, w.simp_emin)
+    f = None
+    if w.traction is not None:
+        f = oracle.traction(om, *w.traction)
+    elif w.point_load is not None:
+        f = w.point_load
+    if w.kind == oracle.NEOHOOKE:
+        return osolve.newton_solve(om, mat, w.mask, w.u_bar, f, w.cell_param, n_steps=w.n_steps)
+    return osolve.linear_solve(om, mat, w.mask, w.u_bar, f, w.cell_param)
+
+
+def test_c0_linear_elastic_fp64():
+    w = inputs.c0()
+    ref = oracle_solve(w)
+    u, st = gpu_solve(w, 0, newton_rtol=1e-13, pcg_rtol=1e-10)
+    assert st["status"] == 0
+    assert rel_l2(u, ref) <= TOL_FP64
+
+
+def test_c0_linear_elastic_mixed_refined():
+    w = inputs.c0()
+    ref = oracle_solve(w)
+    u, st = gpu_solve(w, 2, newton_rtol=1e-12)
+    assert st["status"] == 0 and st["newton_iters"] >= 2  # FP32 CG + FP64 refinement sweeps
+    assert rel_l2(u, ref) <= TOL_REFINED
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_neohooke_load_steps(n):
+    w = inputs.c1(n=n, n_steps=10)
+    ref = oracle_solve(w)
+    u64, st64 = gpu_solve(w, 0, newton_rtol=1e-13, pcg_rtol=1e-8)
+    assert st64["status"] == 0 and st64["load_steps"] == 10
+    assert rel_l2(u64, ref) <= TOL_FP64
+    u32, st32 = gpu_solve(w, 2, newton_rtol=1e-12)
+    assert st32["status"] == 0
+    assert rel_l2(u32, ref) <= TOL_REFINED
+
+
+def test_neohooke_noncubic_with_stiffness_field():
+    w = inputs.c1(n=4, n_steps=3)
+    w.nx, w.ny, w.nz = 6, 4, 3
+    w.lx, w.ly, w.lz = 1.5, 1.0, 0.75
+    w.mask, w.u_bar = inputs.clamp_and_compress(6, 4, 3, -0.1)
+    w.cell_param = np.random.default_rng(4).lognormal(0, 0.5, 6 * 4 * 3)
+    ref = oracle_solve(w)
+    u, st = gpu_solve(w, 2, newton_rtol=1e-12)
+    assert st["status"] == 0
+    assert rel_l2(u, ref) <= TOL_REFINED
+
+
+def test_simp_cantilever_small():
+    w = inputs.c2(nx=16, ny=8, nz=8)
+    ref = oracle_solve(w)
+    u, st = gpu_solve(w, 2, newton_rtol=1e-12)
+    assert st["status"] == 0
+    assert rel_l2(u, ref) <= TOL_REFINED
+    u64, st64 = gpu_solve(w, 0, newton_rtol=1e-13, pcg_rtol=1e-9)
+    assert rel_l2(u64, ref) <= TOL_FP64
+
+
+def test_deterministic_repeat():
+    """Same inputs, same launch configuration: solution equal to round-off
+    of the atomics order (and the FP64 residual drives both to 1e-12)."""
+    w = inputs.c1(n=6, n_steps=2)
+    a, _ = gpu_solve(w, 2, newton_rtol=1e-12)
+    b, _ = gpu_solve(w, 2, newton_rtol=1e-12)
+    assert rel_l2(a, b) <= 1e-9
+
+
+@pytest.mark.slow
+def test_c1_full_size_mixed_vs_fp64_and_oracle_residual():
+    """64^3 Neo-Hookean, 10 load steps: the mixed solution equals the all-FP64
+    GPU solution to 1e-8, and the oracle's FP64 residual at the mixed
+    solution is at the Newton tolerance (a property that holds at any size)."""
+    w = inputs.c1()
+    u32, st32 = gpu_solve(w, 2, newton_rtol=1e-10)
+    assert st32["status"] == 0 and st32["load_steps"] == 10
+    u64, st64 = gpu_solve(w, 0, newton_rtol=1e-10, pcg_rtol=1e-6)
+    assert st64["status"] == 0
+    assert rel_l2(u32, u64) <= TOL_REFINED
+    om = oracle.mesh(w.nx, w.ny, w.nz)
+    R = oracle.residual(om, oracle.Material(w.kind, w.E, w.nu), u32, None, None, w.mask)
+    assert np.linalg.norm(R) <= 1e-9 * st32["ref_rnorm"]
