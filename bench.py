@@ -158,6 +158,22 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def aggregate(total_s_local: float, units_per_rank: int, steps: int, dist=None):
+    """Replicas-only aggregation: every rank solved `steps` independent
+    instances of `units_per_rank` DOFs; the job time is the slowest rank's.
+    Returns (value in MDOF/s over all ranks, job time in s)."""
+    total_s = float(total_s_local)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    return units_per_rank * steps * world / total_s / 1e6, total_s
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -219,12 +235,7 @@ def run_gb300(args):
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     launches = F.kernel_launches() - launches0
-    total_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = D * args.steps * world / total_s / 1e6
+    value, total_s = aggregate(sum(step_ms) / 1e3, D, args.steps, dist)
     u_mixed = u.clone()
 
     apply_ms = sum(s["apply_ms"] for s in stats)

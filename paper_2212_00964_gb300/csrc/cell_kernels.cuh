@@ -19,7 +19,8 @@ enum CellMode {
     CM_VJP = 4,        // g_e = -s'(theta_e) lambda_e . R_e(u; unit scale)  (Eq. (23))
     CM_RESIDUAL_CTL = 5,  // CM_RESIDUAL gated by the solver control block
     CM_APPLY_CTL = 6,     // CM_APPLY (FP64 refinement residual) gated by the control block
-    CM_DIAG_CTL = 7       // CM_DIAG gated by the control block (instances that solve)
+    CM_DIAG_CTL = 7,      // CM_DIAG gated by the control block (instances that solve)
+    CM_APPLY_LIFT = 8     // y += K_e(u) x_e for instances starting a load step (lifting)
 };
 
 template <typename T>
@@ -71,6 +72,8 @@ __global__ void __launch_bounds__(CELL_BLOCK) cell_kernel(const CellArgs<T> a)
             if (a.ctl[k].status != 0) continue;
         } else if (MODE == CM_DIAG_CTL) {
             if (a.ctl[k].status != 0 || !a.ctl[k].solving) continue;
+        } else if (MODE == CM_APPLY_LIFT) {
+            if (a.ctl[k].status != 0 || !a.ctl[k].lift) continue;
         }
         const int64_t ne = a.cells ? a.n_list : d.n_cells();
         const int64_t local = (tile - d.tile_off) * (int64_t)blockDim.x + threadIdx.x;
@@ -101,7 +104,8 @@ __global__ void __launch_bounds__(CELL_BLOCK) cell_kernel(const CellArgs<T> a)
                 for (int n = 0; n < 8; ++n) v[n] = ub[3 * nid[n] + c];
                 grad_sf<T>(v, ihx, ihy, ihz, Gu[c]);
             }
-            constexpr bool IS_APPLY = (MODE == CM_APPLY || MODE == CM_APPLY_PCG || MODE == CM_APPLY_CTL);
+            constexpr bool IS_APPLY =
+                (MODE == CM_APPLY || MODE == CM_APPLY_PCG || MODE == CM_APPLY_CTL || MODE == CM_APPLY_LIFT);
             constexpr bool IS_RES = (MODE == CM_RESIDUAL || MODE == CM_RESIDUAL_CTL || MODE == CM_VJP);
             constexpr bool IS_DIAG = (MODE == CM_DIAG || MODE == CM_DIAG_CTL);
             T Gx[3][3][4];

@@ -67,6 +67,7 @@ static cudaError_t launch_mode(int mode, const CellArgs<T> &a, cudaStream_t s)
     case CM_RESIDUAL_CTL: return launch_one<T, NH, CM_RESIDUAL_CTL>(a, s);
     case CM_APPLY_CTL: return launch_one<T, NH, CM_APPLY_CTL>(a, s);
     case CM_DIAG_CTL: return launch_one<T, NH, CM_DIAG_CTL>(a, s);
+    case CM_APPLY_LIFT: return launch_one<T, NH, CM_APPLY_LIFT>(a, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -87,6 +88,7 @@ static void warm_one()
     resident_grid((const void *)cell_kernel<T, NH, CM_DIAG_CTL>, CELL_BLOCK, 0);
     resident_grid((const void *)cell_kernel<T, NH, CM_APPLY_PCG>, CELL_BLOCK, 0);
     resident_grid((const void *)cell_kernel<T, NH, CM_VJP>, CELL_BLOCK, 0);
+    resident_grid((const void *)cell_kernel<T, NH, CM_APPLY_LIFT>, CELL_BLOCK, 0);
 }
 
 void warm_occupancy(bool nh)

@@ -47,7 +47,7 @@ struct Ctl {
     int newton_total;
     int pcg_total;
     int steps_done;
-    int pad_;
+    int lift;       // this round's CG carries the Dirichlet increment of a new load step
     double r_ref;   // ||R_free|| at step 1, iteration 0
     double r_norm2; // accumulator of ||R_free||^2
     double r_norm;  // last ||R_free||

@@ -74,19 +74,34 @@ struct VecArgs {
 
 #define VEC_ITEMS_END }
 
+// Lifting of a new load step: z = Dirichlet increment (s/S) u_bar_c - u_c on
+// prescribed DOFs, 0 elsewhere.  Its image under the tangent moves to the
+// right-hand side, so the first linear system of the step is solved at the
+// previous equilibrium (where the tangent is positive definite).
 template <typename T>
-__global__ void __launch_bounds__(VEC_BLOCK) k_bc(const VecArgs<T> a)
+__global__ void __launch_bounds__(VEC_BLOCK) k_lift_vec(const VecArgs<T> a)
 {
     VEC_ITEMS_BEGIN
-    if (c.status != 0 || !c.need_bc) continue;
+    if (c.status != 0 || !c.lift) continue;
     const double f = (double)c.step / (double)c.n_steps;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const int64_t j = base + i;
-        if (a.mask[j]) {
-            const double v = f * a.ubar[j];
-            a.u64[j] = v;
-            if (a.write_uT) a.uT[j] = (T)v;
-        }
+        a.z[j] = a.mask[j] ? (T)(f * a.ubar[j] - a.u64[j]) : (T)0;
+    }
+    VEC_ITEMS_END
+}
+
+// r_f -= (K z)_f for lifted instances; q and z cleared for the CG.
+template <typename T>
+__global__ void __launch_bounds__(VEC_BLOCK) k_lift_rhs(const VecArgs<T> a)
+{
+    VEC_ITEMS_BEGIN
+    if (c.status != 0 || !c.lift) continue;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int64_t j = base + i;
+        if (!a.mask[j]) a.r[j] -= a.q[j];
+        a.q[j] = 0;
+        a.z[j] = 0;
     }
     VEC_ITEMS_END
 }
@@ -125,32 +140,41 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_res_finish(const VecArgs<T> a)
     VEC_ITEMS_END
 }
 
+// One thread per instance: read the FP64 residual norm, decide convergence,
+// advance load steps, start the next CG.
 __global__ void k_control(Ctl *ctl, int n_inst, SolverParams prm, int *counter)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_inst) return;
     Ctl &c = ctl[k];
+    const int first = c.need_bc;
     c.need_bc = 0;
     c.solving = 0;
+    c.lift = 0;
     if (c.status != 0) return;
     const double rn = sqrt(c.r_norm2);
     c.r_norm2 = 0;
     c.r_norm = rn;
     if (!isfinite(rn)) { c.status = FEM_ERR_NONFINITE; return; }
     if (c.jflag) { c.status = FEM_ERR_INVERTED; return; }
-    if (c.r_ref < 0) c.r_ref = rn > 0 ? rn : 1.0;
-    if (rn <= prm.rtol * c.r_ref || rn <= prm.atol) {
-        c.steps_done++;
-        if (c.step >= c.n_steps) {
-            c.status = 1;
-        } else {
+    bool lift = first != 0;
+    if (!lift) {
+        if (c.r_ref < 0) c.r_ref = rn > 0 ? rn : 1.0;
+        if (rn <= prm.rtol * c.r_ref || rn <= prm.atol) {
+            c.steps_done++;
+            if (c.step >= c.n_steps) {
+                c.status = 1;
+                return;
+            }
             c.step++;
-            c.need_bc = 1;
             c.newton_it = 0;
+            lift = true;
+        } else if (c.newton_it >= prm.maxit) {
+            c.status = FEM_ERR_NOT_CONVERGED;
+            return;
         }
-        return;
     }
-    if (c.newton_it >= prm.maxit) { c.status = FEM_ERR_NOT_CONVERGED; return; }
+    c.lift = lift ? 1 : 0;
     c.newton_it++;
     c.newton_total++;
     c.solving = 1;
@@ -239,11 +263,21 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_u2(const VecArgs<T> a)
         continue;
     }
     const double pAp = c.pAp[s], rr = c.rr[s];
-    if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(rr)) {
+    if (!isfinite(pAp) || !isfinite(rr)) {
         if (lead) {
-            c.status = isfinite(pAp) && isfinite(rr) ? FEM_ERR_BREAKDOWN : FEM_ERR_NONFINITE;
+            c.status = FEM_ERR_NONFINITE;
             c.pcg_done = 1;
             c.pcg_last = it + 1;
+        }
+        continue;
+    }
+    if (!(pAp > 0.0)) {
+        // negative curvature: keep the iterate of the previous iteration
+        // (truncated CG); with no iterate yet the tangent is unusable
+        if (lead) {
+            if (it == 0) c.status = FEM_ERR_BREAKDOWN;
+            c.pcg_done = 1;
+            c.pcg_last = it;
         }
         continue;
     }
@@ -275,9 +309,13 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_newton_update(const VecArgs<T> a)
 {
     VEC_ITEMS_BEGIN
     if (c.status != 0 || !c.solving) continue;
+    const double f = (double)c.step / (double)c.n_steps;
+    const bool lift = c.lift != 0;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const int64_t j = base + i;
-        const double v = a.u64[j] + (double)a.x[j];
+        double v;
+        if (lift && a.mask[j]) v = f * a.ubar[j];
+        else v = a.u64[j] + (double)a.x[j];
         a.u64[j] = v;
         if (a.write_uT) a.uT[j] = (T)v;
     }
@@ -292,6 +330,9 @@ __global__ void k_tail_ctl(Ctl *ctl, int n_inst, int *counter)
     if (c.solving) {
         c.pcg_total += c.pcg_last;
         c.solving = 0;
+        // reference norm of the first step: the lifted right-hand side, i.e.
+        // the linearised residual after the prescribed values are applied
+        if (c.lift && c.r_ref < 0) c.r_ref = c.rr0 > 0 ? sqrt(c.rr0) : 1.0;
     }
     if (c.status == 0) atomicAdd(&counter[2], 1);
 }
@@ -407,10 +448,6 @@ class Core {
         const int gv = vec_grid(pb_.n_items);
         const int ni = va_.n_inst, gi = (ni + 127) / 128;
         if ((e = cudaMemsetAsync(b_.counter, 0, sizeof(int), s)) != cudaSuccess) return e;
-        if (mode_ == SM_NONLINEAR) {
-            k_bc<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
-            count_launch();
-        }
         k_res_init<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
         count_launch();
         {
@@ -435,6 +472,23 @@ class Core {
         k_res_finish<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
         k_control<<<gi, 128, 0, s>>>(b_.ctl, ni, prm_, b_.counter);
         count_launch(2);
+        if (mode_ == SM_NONLINEAR) {
+            k_lift_vec<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
+            count_launch();
+            CellArgs<T> ca{};
+            ca.d0 = pb_.desc[0];
+            ca.tab = va_.tab;
+            ca.n_inst = ni;
+            ca.n_tiles = pb_.n_tiles;
+            ca.ctl = b_.ctl;
+            ca.cell_param = b_.cpT;
+            ca.u = b_.uT;
+            ca.x = b_.z;
+            ca.y = b_.q;
+            if ((e = launch_cell<T>(CM_APPLY_LIFT, pb_.nh, ca, s)) != cudaSuccess) return e;
+            k_lift_rhs<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
+            count_launch();
+        }
         {
             CellArgs<T> ca{};
             ca.d0 = pb_.desc[0];

@@ -49,8 +49,8 @@ def test_simp_compliance_adjoint_vs_oracle_and_fd():
         tm = theta.copy()
         tp[e] += h
         tm[e] -= h
-        cp_ = float(f @ gpu_forward(F, m, w, tp, 0, newton_rtol=1e-14, pcg_rtol=1e-10))
-        cm_ = float(f @ gpu_forward(F, m, w, tm, 0, newton_rtol=1e-14, pcg_rtol=1e-10))
+        cp_ = float(f @ gpu_forward(F, m, w, tp, 0, newton_rtol=1e-12, pcg_rtol=1e-10))
+        cm_ = float(f @ gpu_forward(F, m, w, tm, 0, newton_rtol=1e-12, pcg_rtol=1e-10))
         fd = (cp_ - cm_) / (2 * h)
         assert abs(float(g[e]) - fd) <= TOL_ADJ_FD * np.abs(g_ref).max()
 
@@ -89,8 +89,8 @@ def test_neohooke_face_objective_adjoint_vs_oracle_and_fd():
         sm_ = s.copy()
         sp_[e] += h
         sm_[e] -= h
-        jp = float(J(gpu_forward(F, m, w, sp_, 0, newton_rtol=1e-14, pcg_rtol=1e-10)))
-        jm = float(J(gpu_forward(F, m, w, sm_, 0, newton_rtol=1e-14, pcg_rtol=1e-10)))
+        jp = float(J(gpu_forward(F, m, w, sp_, 0, newton_rtol=1e-12, pcg_rtol=1e-10)))
+        jm = float(J(gpu_forward(F, m, w, sm_, 0, newton_rtol=1e-12, pcg_rtol=1e-10)))
         assert abs(float(g[e]) - (jp - jm) / (2 * h)) <= TOL_ADJ_FD * np.abs(g_ref).max()
 
 
@@ -139,6 +139,6 @@ def test_c2_full_size_compliance_closed_form():
         tm = w.cell_param.copy()
         tp[e] += h
         tm[e] -= h
-        cp_ = float(f @ gpu_forward(F, m, w, tp, 2, newton_rtol=1e-13))
-        cm_ = float(f @ gpu_forward(F, m, w, tm, 2, newton_rtol=1e-13))
+        cp_ = float(f @ gpu_forward(F, m, w, tp, 2, newton_rtol=1e-12))
+        cm_ = float(f @ gpu_forward(F, m, w, tm, 2, newton_rtol=1e-12))
         assert abs(float(g[e]) - (cp_ - cm_) / (2 * h)) <= TOL_ADJ_FD * np.abs(closed).max()
