@@ -223,6 +223,41 @@ typedef struct {
 int fem_solve_batched(int n_inst, const fem_instance *inst, const fem_options *opt,
                       fem_stats *stats, void *stream);
 
+/* Allocation-free variant of fem_solve for one nx*ny*nz box on
+ * [0,lx]x[0,ly]x[0,lz].  The paper has no counterpart.
+ *
+ * Some callers cannot allocate device memory when they solve:
+ *  - a process whose GPU memory belongs to another framework's caching
+ *    allocator;
+ *  - a real-time loop that forbids allocation after start-up;
+ *  - code running while a global-mode stream capture makes cudaMalloc
+ *    illegal.
+ * This call takes no mesh handle and calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its scratch (CG vectors, FP64 residual, control
+ * block) lives in one file-scope device array of FEM_STATIC_SCRATCH_BYTES
+ * (8 MiB), which every GPU that loads the library holds until the process
+ * exits.
+ *
+ * Size limit: a box whose scratch exceeds the array is rejected with
+ * FEM_ERR_ARG and a message naming the needed size.  FEM_MIXED needs about
+ * 36 bytes per DOF (+4 per cell with cell_param); FEM_FP64 about 56 bytes
+ * per DOF (+8 per cell).  So 40^3 cells fit in mixed precision and 34^3 in
+ * FP64.
+ *
+ * Shared state: the first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress).  Make that first call before any stream
+ * capture.  Every call shares the one array and overwrites what it needs, so
+ * calls that overlap on the GPU (other streams, other host threads) race.
+ *
+ * Execution: kernels launch directly on `stream`, with no CUDA graph, event
+ * or pinned host buffer; the call synchronises `stream` to read its
+ * counters.  Arguments, results and stats otherwise match fem_solve;
+ * apply_ms and apply_samples stay 0. */
+#define FEM_STATIC_SCRATCH_BYTES (8u << 20)
+int fem_solve_static(int nx, int ny, int nz, double lx, double ly, double lz, const fem_material *mat,
+                     const fem_bc *bc, const double *cell_param, int n_steps, const fem_options *opt,
+                     double *u_inout, fem_stats *stats, void *stream);
+
 /* ------------------------------------------------------------- utilities -- */
 const char *fem_status_string(int status);
 const char *fem_last_error(void);

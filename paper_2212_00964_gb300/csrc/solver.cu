@@ -552,6 +552,46 @@ class Core {
         return cudaGetLastError();
     }
 
+    // Same rounds as run(), launched straight onto `s` without graphs,
+    // events or pinned host memory (the counters are read into `hc`, a host
+    // array of 3 ints, with a pageable copy and a stream synchronisation).
+    int run_direct(cudaStream_t s, double timeout_s, int *hc)
+    {
+        warm_occupancy(pb_.nh);
+        auto t0 = std::chrono::steady_clock::now();
+        auto expired = [&]() {
+            if (timeout_s <= 0) return false;
+            return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > timeout_s;
+        };
+        auto read = [&]() -> cudaError_t {
+            cudaError_t e = cudaMemcpyAsync(hc, b_.counter, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            return e;
+        };
+        FEM_CUDA(enqueue_head(s));
+        FEM_CUDA(read());
+        int n_solving = hc[0];
+        const int64_t max_rounds = (int64_t)(prm_.maxit + 2) * max_steps_ * 4 + 16;
+        const int64_t max_chunks = (int64_t)prm_.pcg_maxit / std::max(1, prm_.chunk) + 2;
+        for (int64_t round = 0;; ++round) {
+            if (n_solving > 0) {
+                for (int64_t ch = 0; ch < max_chunks; ++ch) {
+                    FEM_CUDA(enqueue_chunk(s));
+                    FEM_CUDA(read());
+                    if (hc[1] == 0) break;
+                    if (expired()) return (set_error("solve watchdog expired"), FEM_ERR_TIMEOUT);
+                }
+            }
+            FEM_CUDA(enqueue_tail(s));
+            FEM_CUDA(enqueue_head(s));
+            FEM_CUDA(read());
+            n_solving = hc[0];
+            if (hc[2] == 0) break;
+            if (expired() || round >= max_rounds) return (set_error("solve watchdog expired"), FEM_ERR_TIMEOUT);
+        }
+        return FEM_OK;
+    }
+
     cudaError_t capture(cudaStream_t s, int which, cudaGraphExec_t *out, int64_t *n_kernels)
     {
         cudaGraph_t g = nullptr;
@@ -869,6 +909,115 @@ static int adjoint_batch(Workspace &ws, Problem &pb, const double *ustar, const 
     FEM_CUDA(e);
     return FEM_OK;
 }
+
+// ------------------------------------------------ solve in a fixed region --
+// One box mesh solved with every scratch buffer carved, 256-byte aligned, out
+// of a caller-provided device region.  Nothing is allocated: no device or
+// pinned memory, no stream, event or graph.
+static size_t carve(size_t &off, size_t bytes)
+{
+    size_t at = (off + 255) & ~(size_t)255;
+    off = at + bytes;
+    return at;
+}
+
+template <typename T>
+static size_t region_layout(const InstDesc &d, bool has_cp, Buffers<T> *b, char *base)
+{
+    const int64_t D = d.n_dofs(), Ne = d.n_cells();
+    const bool sepT = !std::is_same<T, double>::value;
+    size_t off = 0;
+    size_t o_ctl = carve(off, sizeof(Ctl));
+    size_t o_cnt = carve(off, 4 * sizeof(int));
+    size_t o_r64 = carve(off, sizeof(double) * D);
+    size_t o_vec[6];
+    for (int i = 0; i < 6; ++i) o_vec[i] = carve(off, sizeof(T) * D);
+    size_t o_ut = sepT ? carve(off, sizeof(T) * D) : 0;
+    size_t o_cp = (sepT && has_cp) ? carve(off, sizeof(T) * Ne) : 0;
+    if (b && base) {
+        b->ctl = (Ctl *)(base + o_ctl);
+        b->counter = (int *)(base + o_cnt);
+        b->tab = nullptr;
+        b->R64 = (double *)(base + o_r64);
+        T **v[6] = {&b->x, &b->r, &b->z, &b->p, &b->q, &b->dg};
+        for (int i = 0; i < 6; ++i) *v[i] = (T *)(base + o_vec[i]);
+        if (sepT) b->uT = (T *)(base + o_ut);
+        if (sepT && has_cp) b->cpT = (T *)(base + o_cp);
+    }
+    return off;
+}
+
+size_t region_bytes(const InstDesc &d, int precision, bool has_cp)
+{
+    return precision == FEM_FP64 ? region_layout<double>(d, has_cp, nullptr, nullptr)
+                                 : region_layout<float>(d, has_cp, nullptr, nullptr);
+}
+
+template <typename T>
+static int solve_region_t(const InstDesc &d, int n_steps, const fem_bc &bc, const double *cp64,
+                          const fem_options &o, double *u64, void *region, Ctl &ctl_out, cudaStream_t s)
+{
+    Problem pb;
+    pb.desc.push_back(d);
+    pb.n_steps.push_back(n_steps);
+    pb.nh = d.kind == FEM_NEOHOOKE;
+    pb.layout();
+    const bool sepT = !std::is_same<T, double>::value;
+    Buffers<T> b{};
+    region_layout<T>(pb.desc[0], cp64 != nullptr, &b, (char *)region);
+    b.u64 = u64;
+    b.mask = bc.mask;
+    b.ubar = bc.u_bar;
+    b.rhs = bc.f_ext;
+    b.cp64 = cp64;
+    if (!sepT) {
+        b.uT = (T *)u64;
+        b.cpT = (T *)cp64;
+    } else {
+        k_convert<T><<<vec_grid(pb.n_items), 256, 0, s>>>(b.uT, u64, pb.D);
+        count_launch();
+        if (cp64) {
+            k_convert<T><<<vec_grid(pb.n_items), 256, 0, s>>>(b.cpT, cp64, pb.Ne);
+            count_launch();
+        } else {
+            b.cpT = nullptr;
+        }
+        FEM_CUDA(cudaGetLastError());
+    }
+    Ctl c0{};
+    c0.n_steps = n_steps;
+    c0.step = std::min(o.step_begin, n_steps);
+    c0.need_bc = 1;
+    c0.r_ref = -1.0;
+    FEM_CUDA(cudaMemcpyAsync(b.ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    int hc[4] = {0, 0, 0, 0};
+    Core<T> core(pb, b, SM_NONLINEAR, params_from(o), hc);
+    core.max_steps_ = n_steps;
+    int rc = core.run_direct(s, o.timeout_s, hc);
+    cudaError_t e = cudaMemcpyAsync(&ctl_out, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (rc) return rc;
+    FEM_CUDA(e);
+    return FEM_OK;
+}
+
+int solve_in_region(const InstDesc &d, int n_steps, const fem_bc &bc, const double *cp64,
+                    const fem_options &o, double *u64, void *region, fem_stats *stats, cudaStream_t s)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    Ctl ctl{};
+    int rc = o.precision == FEM_FP64 ? solve_region_t<double>(d, n_steps, bc, cp64, o, u64, region, ctl, s)
+                                     : solve_region_t<float>(d, n_steps, bc, cp64, o, u64, region, ctl, s);
+    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    fill_stats(ctl, stats, ms);
+    if (rc) {
+        if (stats) stats->status = rc;
+        return rc;
+    }
+    return ctl.status == 1 ? FEM_OK : (ctl.status == 0 ? FEM_ERR_NOT_CONVERGED : ctl.status);
+}
+
+int check_solver_options(const fem_options &o) { return check_options(o); }
 
 }  // namespace femgb
 

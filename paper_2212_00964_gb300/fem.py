@@ -98,6 +98,8 @@ def lib():
                               P, P, ctypes.POINTER(fem_stats), P]
     L.fem_solve_batched.argtypes = [I, ctypes.POINTER(fem_instance), ctypes.POINTER(fem_options),
                                     ctypes.POINTER(fem_stats), P]
+    L.fem_solve_static.argtypes = [I, I, I, D, D, D, MP, ctypes.POINTER(fem_bc), P, I,
+                                   ctypes.POINTER(fem_options), P, ctypes.POINTER(fem_stats), P]
     L.fem_status_string.argtypes = [I]
     L.fem_status_string.restype = ctypes.c_char_p
     L.fem_last_error.restype = ctypes.c_char_p
@@ -318,6 +320,26 @@ def fem_adjoint(m: Mesh, mat: fem_material, mask, u_star, dJdu, cell_param=None,
     d = st.as_dict()
     d["rc"] = rc
     return g, d
+
+
+def fem_solve_static(nx, ny, nz, lx, ly, lz, mat: fem_material, mask, u_bar, u, f_ext=None, cell_param=None,
+                     n_steps=1, options: Optional[fem_options] = None, stream=None, check=True):
+    """fem_solve for one box without a mesh handle or any device allocation:
+    scratch comes from the library's fixed static device array (see
+    include/fem.h for the size limit and the sharing rules)."""
+    D = 3 * (nx + 1) * (ny + 1) * (nz + 1)
+    bc = fem_bc(_ptr(mask, torch.uint8, D, "mask"), _ptr(u_bar, torch.float64, D, "u_bar"),
+                _ptr(f_ext, torch.float64, D, "f_ext"))
+    st = fem_stats()
+    rc = lib().fem_solve_static(int(nx), int(ny), int(nz), float(lx), float(ly), float(lz), ctypes.byref(mat),
+                                ctypes.byref(bc), _ptr(cell_param, torch.float64, nx * ny * nz, "cell_param"),
+                                int(n_steps), ctypes.byref(options) if options is not None else None,
+                                _ptr(u, torch.float64, D, "u"), ctypes.byref(st), _stream(stream))
+    if check:
+        _check(rc, "fem_solve_static")
+    d = st.as_dict()
+    d["rc"] = rc
+    return d
 
 
 @dataclass
