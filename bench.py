@@ -304,7 +304,9 @@ def run_gb300(args):
         "e2e": {"value": D / e2e_t / 1e6, "unit": "MDOF/s", "h2d_bytes_per_step": int(D * (1 + 8 + 8)),
                 "d2h_bytes_per_step": int(D * 8)},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "alu", "kernel": "cell_kernel<float,NH,CM_APPLY_PCG>",
+        "roofline": {"bound": "alu",
+                     "kernel": ("apply_brick<float,NH>" if st0.get("apply_kernel") == 2
+                                else "cell_kernel<float,NH,CM_APPLY_PCG>"),
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",

@@ -158,7 +158,9 @@ typedef struct {
     int pcg_chunk;       /* CG iterations per CUDA-graph launch (0 = default) */
     int step_begin;      /* first load step to run (1 = from the start; k+1 resumes a
                             checkpoint taken after step k) */
-    int cells_per_block; /* cell-kernel CTA size (0 = autotuned) */
+    int apply_kernel;    /* CG tangent-apply kernel: 0 = autotuned (timed once per problem shape and
+                            cached), 1 = one thread per cell with a scatter per cell,
+                            2 = 8x4x4-cell bricks staged in shared memory */
     int deterministic;   /* 1: colour-ordered scatter (bit-reproducible), 0: atomics */
     double timeout_s;    /* host watchdog for one solve (0 = none) */
 } fem_options;
@@ -174,6 +176,7 @@ typedef struct {
     double apply_ms;     /* summed device time of the sampled CG tangent-apply launches */
     int apply_samples;   /* number of sampled launches (the first apply of each CG graph) */
     int apply_launches;  /* CG tangent-apply launches that did work */
+    int apply_kernel;    /* CG apply kernel that ran (1 per-cell, 2 bricks) */
 } fem_stats;
 
 typedef struct {
@@ -240,8 +243,8 @@ int fem_solve_batched(int n_inst, const fem_instance *inst, const fem_options *o
  *
  * Size limit: a box whose scratch exceeds the array is rejected with
  * FEM_ERR_ARG and a message naming the needed size.  FEM_MIXED needs about
- * 36 bytes per DOF (+4 per cell with cell_param); FEM_FP64 about 56 bytes
- * per DOF (+8 per cell).  So 40^3 cells fit in mixed precision and 34^3 in
+ * 40 bytes per DOF (+4 per cell with cell_param); FEM_FP64 about 64 bytes
+ * per DOF (+8 per cell).  So 39^3 cells fit in mixed precision and 33^3 in
  * FP64.
  *
  * Shared state: the first call on a device looks up the array's device

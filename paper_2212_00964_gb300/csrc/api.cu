@@ -54,7 +54,7 @@ extern "C" void fem_default_options(fem_options *o)
     o->pcg_maxit = 5000;
     o->pcg_chunk = 16;
     o->step_begin = 1;
-    o->cells_per_block = 0;
+    o->apply_kernel = 0;
     o->deterministic = 0;
     o->timeout_s = 0.0;
 }

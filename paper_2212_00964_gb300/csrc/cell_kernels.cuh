@@ -36,6 +36,7 @@ struct CellArgs {
     const uint8_t *mask;    // [D] (masked modes) or nullptr
     Ctl *ctl;               // control blocks (gated modes)
     int iter;               // CG iteration inside the current graph chunk
+    int pcg_maxit;          // CG iteration cap (CG apply)
     T *g;                   // VJP output [Ne]
     int *jflag;             // det F <= 0 flag (ungated residual)
     const int32_t *cells;   // explicit cell list (colour-ordered launch) or nullptr
@@ -65,9 +66,21 @@ __global__ void __launch_bounds__(CELL_BLOCK) cell_kernel(const CellArgs<T> a)
         }
         int slot = 0;
         if (MODE == CM_APPLY_PCG) {
-            const Ctl &c = a.ctl[k];
+            Ctl &c = a.ctl[k];
             if (c.status != 0 || !c.solving || c.pcg_done) continue;  // uniform per block
-            slot = (c.pcg_base + a.iter) % 3;
+            const int it = c.pcg_base + a.iter;
+            if (cg_converged(c, it, a.pcg_maxit)) {
+                if (tile == d.tile_off && threadIdx.x == 0) {
+                    c.pcg_done = 1;
+                    c.pcg_last = it;
+                }
+                continue;
+            }
+            slot = it & 3;
+            if (tile == d.tile_off && threadIdx.x == 0) {
+                c.gamma[(it + 1) & 3] = 0;
+                c.rr[(it + 1) & 3] = 0;
+            }
         } else if (MODE == CM_RESIDUAL_CTL || MODE == CM_APPLY_CTL) {
             if (a.ctl[k].status != 0) continue;
         } else if (MODE == CM_DIAG_CTL) {
@@ -75,20 +88,23 @@ __global__ void __launch_bounds__(CELL_BLOCK) cell_kernel(const CellArgs<T> a)
         } else if (MODE == CM_APPLY_LIFT) {
             if (a.ctl[k].status != 0 || !a.ctl[k].lift) continue;
         }
-        const int64_t ne = a.cells ? a.n_list : d.n_cells();
-        const int64_t local = (tile - d.tile_off) * (int64_t)blockDim.x + threadIdx.x;
+        // Per-instance cell and node counts stay below 2^31 (checked when the
+        // mesh is built), so the index arithmetic runs in 32 bits.
+        const int ne = (int)(a.cells ? a.n_list : d.n_cells());
+        const int local = (int)(tile - d.tile_off) * (int)blockDim.x + (int)threadIdx.x;
         const bool active = local < ne;
         T part = 0;
         if (active) {
-            const int64_t cell = a.cells ? (int64_t)a.cells[local] : local;
-            const int nx = d.nx, ny = d.ny;
-            const int ci = (int)(cell % nx);
-            const int cj = (int)((cell / nx) % ny);
-            const int ck = (int)(cell / ((int64_t)nx * ny));
-            const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
-            const int64_t n0 = ci + sy * (cj + (int64_t)(ny + 1) * ck);
-            int64_t nid[8] = {n0, n0 + 1, n0 + sy, n0 + sy + 1, n0 + sz, n0 + sz + 1, n0 + sz + sy,
-                              n0 + sz + sy + 1};
+            const int cell = a.cells ? a.cells[local] : local;
+            const unsigned nx = (unsigned)d.nx, ny = (unsigned)d.ny;
+            const unsigned rowc = (unsigned)cell / nx;
+            const int ci = (int)((unsigned)cell - rowc * nx);
+            const int ck = (int)(rowc / ny);
+            const int cj = (int)(rowc - (unsigned)ck * ny);
+            const int sy = (int)nx + 1, sz = ((int)nx + 1) * ((int)ny + 1);
+            const int n0 = ci + sy * cj + sz * ck;
+            const int nid[8] = {n0, n0 + 1, n0 + sy, n0 + sy + 1, n0 + sz, n0 + sz + 1, n0 + sz + sy,
+                                n0 + sz + sy + 1};
             const T *ub = a.u + d.dof_off;
             const T ihx = (T)(1.0 / d.hx), ihy = (T)(1.0 / d.hy), ihz = (T)(1.0 / d.hz);
             const T wdet = (T)(d.hx * d.hy * d.hz * 0.125);
@@ -232,7 +248,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) cell_kernel(const CellArgs<T> a)
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
                     for (int n = 0; n < 8; ++n) {
-                        int64_t dof = 3 * nid[n] + c;
+                        const int dof = 3 * nid[n] + c;
                         if (!(mb && mb[dof])) s += lb[dof] * ye[c][n];
                     }
                 double th = cp ? (double)cp[cell] : 1.0;
@@ -257,8 +273,171 @@ __global__ void __launch_bounds__(CELL_BLOCK) cell_kernel(const CellArgs<T> a)
         }
         if (MODE == CM_APPLY_PCG) {
             double s = block_sum<double, CELL_BLOCK>((double)part, sh);
-            if (threadIdx.x == 0) atomicAdd(&a.ctl[k].pAp[slot], s);
+            if (threadIdx.x == 0) atomicAdd(&a.ctl[k].delta[slot], s);
         }
+    }
+}
+
+
+// ------------------------------------------------------------------------
+// Brick-tiled CG tangent apply (the hot kernel).  One CTA of 128 threads
+// owns a brick of 8x4x4 cells; the brick's 9x5x5 nodal values of u and p are
+// staged in shared memory with row-contiguous loads (a brick row is 27
+// consecutive scalars of the interleaved DOF vector), each thread computes
+// its cell exactly as cell_kernel does, nodal results are summed in shared
+// memory, and the brick is flushed with one global reduction per node
+// component.  Compared with a scatter per cell this moves 4.5x fewer
+// reductions to L2 and reads each nodal value once per brick.
+template <typename T, int NH>
+__global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z) apply_brick(const CellArgs<T> a)
+{
+    constexpr int NX = BRICK_X + 1, NY = BRICK_Y + 1, NZ = BRICK_Z + 1, NN = NX * NY * NZ;
+    constexpr int NT = BRICK_X * BRICK_Y * BRICK_Z;
+    constexpr int ROW = 3 * NX;            // scalars per brick row
+    constexpr int NROW = NY * NZ;          // rows per brick
+    __shared__ T su[3][NN], sp[3][NN], sy[3][NN];
+    __shared__ double sh[NT / 32];
+    const int tid = threadIdx.x;
+    for (int64_t brick = blockIdx.x; brick < a.n_tiles; brick += gridDim.x) {
+        int k = 0;
+        InstDesc d;
+        if (a.tab) {
+            k = find_inst_by(a.tab, a.n_inst, brick, 2);
+            d = a.tab[k];
+        } else {
+            d = a.d0;
+        }
+        Ctl &cc = a.ctl[k];
+        if (cc.status != 0 || !cc.solving || cc.pcg_done) continue;  // uniform per CTA
+        const int it = cc.pcg_base + a.iter;
+        if (cg_converged(cc, it, a.pcg_maxit)) {
+            if (brick == d.brick_off && tid == 0) {
+                cc.pcg_done = 1;
+                cc.pcg_last = it;
+            }
+            continue;
+        }
+        const int slot = it & 3;
+        if (brick == d.brick_off && tid == 0) {
+            cc.gamma[(it + 1) & 3] = 0;
+            cc.rr[(it + 1) & 3] = 0;
+        }
+        const int nx = d.nx, ny = d.ny, nz = d.nz;
+        const int tnx = (nx + BRICK_X - 1) / BRICK_X, tny = (ny + BRICK_Y - 1) / BRICK_Y;
+        const int lb = (int)(brick - d.brick_off);
+        const int bt = lb / tnx;
+        const int i0 = (lb - bt * tnx) * BRICK_X;
+        const int bk = bt / tny;
+        const int j0 = (bt - bk * tny) * BRICK_Y;
+        const int k0 = bk * BRICK_Z;
+        const int sy_ = nx + 1, sz_ = (nx + 1) * (ny + 1);
+        const T *ub = a.u + d.dof_off;
+        const T *pb = a.x + d.dof_off;
+        // stage u and p; clear the accumulator
+        for (int t = tid; t < NROW * ROW; t += NT) {
+            const int row = t / ROW, f = t - row * ROW;
+            const int jj = row % NY, kk = row / NY;
+            const int ii = f / 3, c = f - 3 * ii;
+            const int I = i0 + ii, J = j0 + jj, K = k0 + kk;
+            const int ln = ii + NX * row;
+            T vu = 0, vp = 0;
+            if (I <= nx && J <= ny && K <= nz) {
+                const int g = 3 * (I + sy_ * J + sz_ * K) + c;
+                vu = ub[g];
+                vp = pb[g];
+            }
+            su[c][ln] = vu;
+            sp[c][ln] = vp;
+            sy[c][ln] = 0;
+        }
+        __syncthreads();
+        const int ci = tid % BRICK_X, cj = (tid / BRICK_X) % BRICK_Y, ck = tid / (BRICK_X * BRICK_Y);
+        const bool active = (i0 + ci < nx) && (j0 + cj < ny) && (k0 + ck < nz);
+        T part = 0;
+        if (active) {
+            const int l0 = ci + NX * (cj + NY * ck);
+            const int lid[8] = {l0, l0 + 1, l0 + NX, l0 + NX + 1, l0 + NX * NY, l0 + NX * NY + 1,
+                                l0 + NX * NY + NX, l0 + NX * NY + NX + 1};
+            const T ihx = (T)(1.0 / d.hx), ihy = (T)(1.0 / d.hy), ihz = (T)(1.0 / d.hz);
+            const T wdet = (T)(d.hx * d.hy * d.hz * 0.125);
+            const int cell = (i0 + ci) + nx * ((j0 + cj) + ny * (k0 + ck));
+            const T *cp = a.cell_param ? a.cell_param + d.cell_off : nullptr;
+            const Mat<T> m = cell_mat<T>(d, cp, cell);
+            T Gu[3][3][4], Gx[3][3][4], xe[3][8];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                T v[8];
+#pragma unroll
+                for (int n = 0; n < 8; ++n) {
+                    v[n] = su[c][lid[n]];
+                    xe[c][n] = sp[c][lid[n]];
+                }
+                grad_sf<T>(v, ihx, ihy, ihz, Gu[c]);
+                grad_sf<T>(xe[c], ihx, ihy, ihz, Gx[c]);
+            }
+            T S[3][3][4];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int dd = 0; dd < 3; ++dd)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) S[c][dd][q] = 0;
+#pragma unroll
+            for (int gp = 0; gp < 8; ++gp) {
+                const int al = gp & 1, be = (gp >> 1) & 1, ga = gp >> 2;
+                T H[9], dH[9], P[9];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    H[3 * c + 0] = Gu[c][0][be + 2 * ga];
+                    H[3 * c + 1] = Gu[c][1][al + 2 * ga];
+                    H[3 * c + 2] = Gu[c][2][al + 2 * be];
+                    dH[3 * c + 0] = Gx[c][0][be + 2 * ga];
+                    dH[3 * c + 1] = Gx[c][1][al + 2 * ga];
+                    dH[3 * c + 2] = Gx[c][2][al + 2 * be];
+                }
+                if (NH) {
+                    NHPoint<T> q;
+                    nh_point<T>(H, m, q);
+                    nh_dstress<T>(q, m, dH, P);
+                } else {
+                    le_stress<T>(dH, m, P);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    S[c][0][be + 2 * ga] += P[3 * c + 0];
+                    S[c][1][al + 2 * ga] += P[3 * c + 1];
+                    S[c][2][al + 2 * be] += P[3 * c + 2];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                T ye[8];
+#pragma unroll
+                for (int n = 0; n < 8; ++n) ye[n] = 0;
+                grad_sf_t<T>(S[c], ihx * wdet, ihy * wdet, ihz * wdet, ye);
+#pragma unroll
+                for (int n = 0; n < 8; ++n) {
+                    atomicAdd(&sy[c][lid[n]], ye[n]);
+                    part += xe[c][n] * ye[n];
+                }
+            }
+        }
+        __syncthreads();
+        // flush the brick: one global reduction per in-mesh node component
+        T *yb = a.y + d.dof_off;
+        for (int t = tid; t < NROW * ROW; t += NT) {
+            const int row = t / ROW, f = t - row * ROW;
+            const int jj = row % NY, kk = row / NY;
+            const int ii = f / 3, c = f - 3 * ii;
+            const int I = i0 + ii, J = j0 + jj, K = k0 + kk;
+            if (I <= nx && J <= ny && K <= nz) {
+                const T v = sy[c][ii + NX * row];
+                if (v != (T)0) atomicAdd(&yb[3 * (I + sy_ * J + sz_ * K) + c], v);
+            }
+        }
+        const double s = block_sum<double, NT>((double)part, sh);
+        if (tid == 0) atomicAdd(&a.ctl[k].delta[slot], s);
+        __syncthreads();  // shared arrays are reused by the next brick
     }
 }
 

@@ -89,6 +89,7 @@ static void warm_one()
     resident_grid((const void *)cell_kernel<T, NH, CM_APPLY_PCG>, CELL_BLOCK, 0);
     resident_grid((const void *)cell_kernel<T, NH, CM_VJP>, CELL_BLOCK, 0);
     resident_grid((const void *)cell_kernel<T, NH, CM_APPLY_LIFT>, CELL_BLOCK, 0);
+    resident_grid((const void *)apply_brick<T, NH>, BRICK_X * BRICK_Y * BRICK_Z, 0);
 }
 
 void warm_occupancy(bool nh)
@@ -102,6 +103,27 @@ void warm_occupancy(bool nh)
         warm_one<double, 0>();
     }
 }
+template <typename T>
+cudaError_t launch_apply_brick(bool nh, const CellArgs<T> &a, cudaStream_t s)
+{
+    const int nt = BRICK_X * BRICK_Y * BRICK_Z;
+    if (nh) {
+        auto f = apply_brick<T, 1>;
+        int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, nt, 0));
+        if (g < 1) return cudaSuccess;
+        f<<<(int)g, nt, 0, s>>>(a);
+    } else {
+        auto f = apply_brick<T, 0>;
+        int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, nt, 0));
+        if (g < 1) return cudaSuccess;
+        f<<<(int)g, nt, 0, s>>>(a);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+template cudaError_t launch_apply_brick<float>(bool, const CellArgs<float> &, cudaStream_t);
+template cudaError_t launch_apply_brick<double>(bool, const CellArgs<double> &, cudaStream_t);
+
 template cudaError_t launch_cell<float>(int, bool, const CellArgs<float> &, cudaStream_t);
 template cudaError_t launch_cell<double>(int, bool, const CellArgs<double> &, cudaStream_t);
 

@@ -26,13 +26,15 @@ struct InstDesc {
     int64_t cell_off;      // first cell (cell_param / per-cell outputs)
     int64_t tile_off;      // first cell tile (cell kernels)
     int64_t vec_off;       // first vector chunk (vector kernels)
+    int64_t brick_off;     // first 8x4x4-cell brick (brick-tiled kernels)
     __host__ __device__ int64_t n_dofs() const { return 3LL * (nx + 1) * (ny + 1) * (nz + 1); }
     __host__ __device__ int64_t n_cells() const { return (int64_t)nx * ny * nz; }
 };
 
-// Per-instance solver state, device resident.  The PCG scalars live in a
-// ring of three slots indexed by the CG iteration, so a slot can be cleared
-// one iteration ahead without a separate reset launch.
+// Per-instance solver state, device resident.  The CG scalars live in a
+// ring of four slots indexed by the CG iteration, so a slot can be cleared
+// by the kernel that runs between its last read and its next accumulation,
+// without a separate reset launch.
 struct Ctl {
     int n_steps;
     int step;       // current load step, 1-based
@@ -53,8 +55,18 @@ struct Ctl {
     double r_norm;  // last ||R_free||
     double eta;     // CG relative tolerance
     double rr0;     // ||r_0||^2 of the current CG
-    double pAp[3], rz[3], rr[3];
+    // CG in the single-reduction (Chronopoulos-Gear) form, iteration i:
+    // gamma_i = (r_i, z_i), delta_i = (A z_i, z_i), rr_i = (r_i, r_i), alpha_i
+    double gamma[4], delta[4], rr[4], alpha[4];
 };
+
+// CG iteration `it` of an instance is not run when the relative residual
+// reached eta, the iteration cap is hit or the right-hand side is zero.
+__device__ __forceinline__ bool cg_converged(const Ctl &c, int it, int pcg_maxit)
+{
+    const double rr = c.rr[it & 3];
+    return c.rr0 == 0.0 || rr <= c.eta * c.eta * c.rr0 || it >= pcg_maxit;
+}
 
 // ----------------------------------------------------------- launch count --
 // Kernels launched by this library (graph replays count their kernel nodes).
@@ -79,17 +91,28 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 constexpr int CELL_BLOCK = 128;  // default cells per CTA (one thread per cell)
 constexpr int VEC_BLOCK = 256;   // threads per CTA of the vector kernels
 constexpr int VEC_CHUNK = 2048;  // DOFs per vector work item
+constexpr int BRICK_X = 8, BRICK_Y = 4, BRICK_Z = 4;  // cells per brick (one CTA)
+__host__ __device__ inline int64_t brick_count(int nx, int ny, int nz)
+{
+    return (int64_t)((nx + BRICK_X - 1) / BRICK_X) * ((ny + BRICK_Y - 1) / BRICK_Y) * ((nz + BRICK_Z - 1) / BRICK_Z);
+}
 
-__device__ __forceinline__ int find_inst(const InstDesc *tab, int n, int64_t item, bool tiles)
+// which: 0 vector chunks, 1 cell tiles, 2 bricks
+__device__ __forceinline__ int find_inst_by(const InstDesc *tab, int n, int64_t item, int which)
 {
     // last instance whose offset <= item (offsets ascending)
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        int64_t off = tiles ? tab[mid].tile_off : tab[mid].vec_off;
+        int64_t off = which == 1 ? tab[mid].tile_off : (which == 2 ? tab[mid].brick_off : tab[mid].vec_off);
         if (off <= item) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+__device__ __forceinline__ int find_inst(const InstDesc *tab, int n, int64_t item, bool tiles)
+{
+    return find_inst_by(tab, n, item, tiles ? 1 : 0);
 }
 
 template <typename T>

@@ -17,7 +17,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -50,7 +52,7 @@ struct VecArgs {
     const uint8_t *mask;
     T *uT;              // state copy in T used by the T cell kernels
     int write_uT;       // refresh uT from u64 after updates
-    T *x, *r, *z, *p, *q, *dg;
+    T *x, *r, *z, *p, *q, *dg, *s;
     int iter;
     SolverParams prm;
     int *counter;       // [0] solving, [1] iterating, [2] active
@@ -183,17 +185,19 @@ __global__ void k_control(Ctl *ctl, int n_inst, SolverParams prm, int *counter)
     c.pcg_last = 0;
     c.rr0 = 0;
     c.eta = prm.eta;
-    for (int s = 0; s < 3; ++s) c.pAp[s] = c.rz[s] = c.rr[s] = 0;
+    for (int s = 0; s < 4; ++s) c.gamma[s] = c.delta[s] = c.rr[s] = c.alpha[s] = 0;
     atomicAdd(&counter[0], 1);
 }
 
+// CG start: z_0 = M r_0 (M = inverse Jacobi diagonal, 0 on prescribed DOFs),
+// gamma_0 = (r_0, z_0), rr_0 = (r_0, r_0).
 template <typename T>
 __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_init(const VecArgs<T> a)
 {
     __shared__ double sh[VEC_BLOCK / 32];
     VEC_ITEMS_BEGIN
     if (c.status != 0 || !c.solving) continue;
-    T arz = 0, arr = 0;
+    T ag = 0, arr = 0;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const int64_t j = base + i;
         const T dv = a.dg[j];
@@ -202,78 +206,53 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_init(const VecArgs<T> a)
         const T rv = a.r[j];
         const T zv = inv * rv;
         a.z[j] = zv;
-        a.p[j] = zv;
-        arz += rv * zv;
+        ag += rv * zv;
         arr += rv * rv;
     }
-    double s1 = block_sum<double, VEC_BLOCK>((double)arz, sh);
-    if (threadIdx.x == 0) atomicAdd(&c.rz[2], s1);
-    double s2 = block_sum<double, VEC_BLOCK>((double)arr, sh);
-    if (threadIdx.x == 0) atomicAdd(&c.rr0, s2);
+    const double s1 = block_sum<double, VEC_BLOCK>((double)ag, sh);
+    if (threadIdx.x == 0) atomicAdd(&c.gamma[0], s1);
+    const double s2 = block_sum<double, VEC_BLOCK>((double)arr, sh);
+    if (threadIdx.x == 0) {
+        atomicAdd(&c.rr[0], s2);
+        atomicAdd(&c.rr0, s2);
+    }
     VEC_ITEMS_END
 }
 
+// CG iteration `it` after the tangent apply w = K z_it (w lives in q and
+// delta_it = (w, z_it) was reduced by the apply):
+//   beta = gamma_it / gamma_{it-1}, alpha = gamma_it / (delta_it - beta gamma_it / alpha_{it-1})
+//   p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, z = M r,
+//   gamma_{it+1} = (r, z), rr_{it+1} = (r, r)   (one reduction phase per iteration)
+// Every block derives alpha and beta from the same reduced scalars; the
+// first block of the instance records alpha and clears the next delta slot.
 template <typename T>
-__global__ void __launch_bounds__(VEC_BLOCK) k_pcg_u1(const VecArgs<T> a)
+__global__ void __launch_bounds__(VEC_BLOCK) k_pcg_update(const VecArgs<T> a)
 {
     __shared__ double sh[VEC_BLOCK / 32];
     VEC_ITEMS_BEGIN
     if (c.status != 0 || !c.solving || c.pcg_done) continue;
     const int it = c.pcg_base + a.iter;
-    const int s = it % 3, sp = (it + 2) % 3, sn = (it + 1) % 3;
-    const double pAp = c.pAp[s];
-    if (!(pAp > 0.0) || !isfinite(pAp)) continue;  // breakdown: decided in k_pcg_u2
-    const T alpha = (T)(c.rz[sp] / pAp);
-    T arz = 0, arr = 0;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        const int64_t j = base + i;
-        const T pv = a.p[j], qv = a.q[j], inv = a.dg[j];
-        a.x[j] += alpha * pv;
-        T rv = a.r[j];
-        if (inv != (T)0) rv -= alpha * qv;
-        a.r[j] = rv;
-        const T zv = inv * rv;
-        a.z[j] = zv;
-        a.q[j] = 0;
-        arz += rv * zv;
-        arr += rv * rv;
-    }
-    double s1 = block_sum<double, VEC_BLOCK>((double)arz, sh);
-    if (threadIdx.x == 0) atomicAdd(&c.rz[s], s1);
-    double s2 = block_sum<double, VEC_BLOCK>((double)arr, sh);
-    if (threadIdx.x == 0) atomicAdd(&c.rr[s], s2);
-    if (item == d.vec_off && threadIdx.x == 0) {
-        c.pAp[sn] = 0;
-        c.rz[sn] = 0;
-        c.rr[sn] = 0;
-    }
-    VEC_ITEMS_END
-}
-
-template <typename T>
-__global__ void __launch_bounds__(VEC_BLOCK) k_pcg_u2(const VecArgs<T> a)
-{
-    VEC_ITEMS_BEGIN
-    if (c.status != 0 || !c.solving || c.pcg_done) continue;
-    const int it = c.pcg_base + a.iter;
-    const int s = it % 3, sp = (it + 2) % 3;
+    if (cg_converged(c, it, a.prm.pcg_maxit)) continue;  // the next apply records it
     const bool lead = (item == d.vec_off) && threadIdx.x == 0;
-    if (c.rr0 == 0.0) {
-        if (lead) { c.pcg_done = 1; c.pcg_last = it; }
-        continue;
+    const int s0 = it & 3, sm = (it + 3) & 3, sn = (it + 1) & 3;
+    const double g = c.gamma[s0];
+    double beta = 0.0, den = c.delta[s0];
+    if (it > 0) {
+        beta = g / c.gamma[sm];
+        den = den - beta * g / c.alpha[sm];
     }
-    const double pAp = c.pAp[s], rr = c.rr[s];
-    if (!isfinite(pAp) || !isfinite(rr)) {
+    if (!isfinite(den) || !isfinite(g)) {
         if (lead) {
             c.status = FEM_ERR_NONFINITE;
             c.pcg_done = 1;
-            c.pcg_last = it + 1;
+            c.pcg_last = it;
         }
         continue;
     }
-    if (!(pAp > 0.0)) {
-        // negative curvature: keep the iterate of the previous iteration
-        // (truncated CG); with no iterate yet the tangent is unusable
+    if (!(den > 0.0)) {
+        // p^T K p <= 0: negative curvature.  Keep the iterate so far
+        // (truncated CG); with no iterate yet the tangent is unusable.
         if (lead) {
             if (it == 0) c.status = FEM_ERR_BREAKDOWN;
             c.pcg_done = 1;
@@ -281,26 +260,75 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_u2(const VecArgs<T> a)
         }
         continue;
     }
-    if (rr <= c.eta * c.eta * c.rr0 || it + 1 >= a.prm.pcg_maxit) {
-        if (lead) { c.pcg_done = 1; c.pcg_last = it + 1; }
-        continue;
+    const double alpha = g / den;
+    if (lead) {
+        c.alpha[s0] = alpha;
+        c.delta[sn] = 0;
     }
-    const T beta = (T)(c.rz[s] / c.rz[sp]);
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        const int64_t j = base + i;
-        a.p[j] = a.z[j] + beta * a.p[j];
+    const T al = (T)alpha, be = (T)beta;
+    const bool first = it == 0;
+    T ag = 0, arr = 0;
+    const int64_t bd = blockDim.x;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += 4 * bd) {
+        // four independent elements per thread: all loads are issued first
+        T zv[4], wv[4], iv[4], xv[4], rv[4], pv[4], sv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t ii = i + u * bd;
+            if (ii < i1) {
+                const int64_t j = base + ii;
+                zv[u] = a.z[j];
+                wv[u] = a.q[j];
+                iv[u] = a.dg[j];
+                xv[u] = a.x[j];
+                rv[u] = a.r[j];
+                pv[u] = first ? (T)0 : a.p[j];
+                sv[u] = first ? (T)0 : a.s[j];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t ii = i + u * bd;
+            if (ii < i1) {
+                const int64_t j = base + ii;
+                const T pn = zv[u] + be * pv[u];
+                const T sn_ = iv[u] != (T)0 ? wv[u] + be * sv[u] : (T)0;
+                const T rn = rv[u] - al * sn_;
+                const T zn = iv[u] * rn;
+                a.p[j] = pn;
+                a.s[j] = sn_;
+                a.x[j] = xv[u] + al * pn;
+                a.r[j] = rn;
+                a.z[j] = zn;
+                a.q[j] = 0;
+                ag += rn * zn;
+                arr += rn * rn;
+            }
+        }
     }
+    const double s1 = block_sum<double, VEC_BLOCK>((double)ag, sh);
+    if (threadIdx.x == 0) atomicAdd(&c.gamma[sn], s1);
+    const double s2 = block_sum<double, VEC_BLOCK>((double)arr, sh);
+    if (threadIdx.x == 0) atomicAdd(&c.rr[sn], s2);
     VEC_ITEMS_END
 }
 
-__global__ void k_chunk_ctl(Ctl *ctl, int n_inst, int chunk, int *counter)
+// End of a graph chunk: instances whose next iteration would not run are
+// marked done here, the others advance their iteration base.
+__global__ void k_chunk_ctl(Ctl *ctl, int n_inst, int chunk, int pcg_maxit, int *counter)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_inst) return;
     Ctl &c = ctl[k];
     if (c.status == 0 && c.solving && !c.pcg_done) {
-        c.pcg_base += chunk;
-        atomicAdd(&counter[1], 1);
+        const int nxt = c.pcg_base + chunk;
+        if (cg_converged(c, nxt, pcg_maxit)) {
+            c.pcg_done = 1;
+            c.pcg_last = nxt;
+        } else {
+            c.pcg_base = nxt;
+            atomicAdd(&counter[1], 1);
+        }
     }
 }
 
@@ -359,17 +387,19 @@ static int vec_grid(int64_t n_items)
 struct Problem {
     std::vector<InstDesc> desc;  // offsets filled by layout()
     std::vector<int> n_steps;
-    int64_t D = 0, Ne = 0, n_tiles = 0, n_items = 0;
+    int64_t D = 0, Ne = 0, n_tiles = 0, n_items = 0, n_bricks = 0;
     bool nh = false;
 
     void layout()
     {
-        D = Ne = n_tiles = n_items = 0;
+        D = Ne = n_tiles = n_items = n_bricks = 0;
         for (auto &d : desc) {
             d.dof_off = D;
             d.cell_off = Ne;
             d.tile_off = n_tiles;
             d.vec_off = n_items;
+            d.brick_off = n_bricks;
+            n_bricks += brick_count(d.nx, d.ny, d.nz);
             D += d.n_dofs();
             Ne += d.n_cells();
             n_tiles += (d.n_cells() + CELL_BLOCK - 1) / CELL_BLOCK;
@@ -390,7 +420,8 @@ struct Buffers {
     const double *cp64;  // per-cell parameter (double), may be null
     T *cpT;              // the same in T (== cp64 when T = double)
     T *uT;
-    T *x, *r, *z, *p, *q, *dg;
+    T *x, *r, *z, *p, *q, *dg, *s;
+    Ctl *tune;           // scratch control blocks for the apply autotuner (may be null)
 };
 
 struct Graphs {
@@ -437,7 +468,7 @@ class Core {
         va_.mask = b.mask;
         va_.uT = b.uT;
         va_.write_uT = (mode == SM_NONLINEAR && (void *)b.uT != (void *)b.u64) ? 1 : 0;
-        va_.x = b.x; va_.r = b.r; va_.z = b.z; va_.p = b.p; va_.q = b.q; va_.dg = b.dg;
+        va_.x = b.x; va_.r = b.r; va_.z = b.z; va_.p = b.p; va_.q = b.q; va_.dg = b.dg; va_.s = b.s;
         va_.prm = prm;
         va_.counter = b.counter;
     }
@@ -520,22 +551,22 @@ class Core {
         ca.ctl = b_.ctl;
         ca.cell_param = b_.cpT;
         ca.u = b_.uT;
-        ca.x = b_.p;
+        ca.x = b_.z;
         ca.y = b_.q;
+        ca.pcg_maxit = prm_.pcg_maxit;
         for (int j = 0; j < prm_.chunk; ++j) {
             ca.iter = j;
             if (j == 0 && ev_a_ && (e = cudaEventRecordWithFlags(ev_a_, s, cudaEventRecordExternal)) != cudaSuccess)
                 return e;
-            if ((e = launch_cell<T>(CM_APPLY_PCG, pb_.nh, ca, s)) != cudaSuccess) return e;
+            if ((e = launch_apply(ca, s)) != cudaSuccess) return e;
             if (j == 0 && ev_b_ && (e = cudaEventRecordWithFlags(ev_b_, s, cudaEventRecordExternal)) != cudaSuccess)
                 return e;
             VecArgs<T> v = va_;
             v.iter = j;
-            k_pcg_u1<T><<<gv, VEC_BLOCK, 0, s>>>(v);
-            k_pcg_u2<T><<<gv, VEC_BLOCK, 0, s>>>(v);
-            count_launch(2);
+            k_pcg_update<T><<<gv, VEC_BLOCK, 0, s>>>(v);
+            count_launch();
         }
-        k_chunk_ctl<<<gi, 128, 0, s>>>(b_.ctl, ni, prm_.chunk, b_.counter);
+        k_chunk_ctl<<<gi, 128, 0, s>>>(b_.ctl, ni, prm_.chunk, prm_.pcg_maxit, b_.counter);
         count_launch();
         return cudaGetLastError();
     }
@@ -552,12 +583,86 @@ class Core {
         return cudaGetLastError();
     }
 
+    // The CG apply in the selected variant (1 per-cell scatter, 2 bricks).
+    cudaError_t launch_apply(CellArgs<T> ca, cudaStream_t s)
+    {
+        if (variant_ == 2) {
+            ca.n_tiles = pb_.n_bricks;
+            return launch_apply_brick<T>(pb_.nh, ca, s);
+        }
+        ca.n_tiles = pb_.n_tiles;
+        return launch_cell<T>(CM_APPLY_PCG, pb_.nh, ca, s);
+    }
+
+    // Autotuner: time both apply variants on this problem (scratch control
+    // blocks that keep every instance iterating) and keep the faster one.
+    // The choice is cached per (law, precision, DOFs, instances).
+    int autotune(cudaStream_t s)
+    {
+        static std::mutex mu;
+        static std::map<std::tuple<int, int, int64_t, int>, int> cache;
+        const auto key = std::make_tuple((int)pb_.nh, (int)sizeof(T), pb_.D, (int)pb_.desc.size());
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            auto it = cache.find(key);
+            if (it != cache.end()) return it->second;
+        }
+        if (!b_.tune) return 2;
+        std::vector<Ctl> tc(pb_.desc.size());
+        for (auto &c : tc) {
+            c = Ctl{};
+            c.solving = 1;
+            c.eta = 0.5;
+            c.rr0 = 1.0;
+            for (int q = 0; q < 4; ++q) c.rr[q] = 1.0;
+        }
+        if (cudaMemcpyAsync(b_.tune, tc.data(), sizeof(Ctl) * tc.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return (cudaGetLastError(), 2);
+        CellArgs<T> ca{};
+        ca.d0 = pb_.desc[0];
+        ca.tab = va_.tab;
+        ca.n_inst = va_.n_inst;
+        ca.ctl = b_.tune;
+        ca.cell_param = b_.cpT;
+        ca.u = b_.uT;
+        ca.x = b_.uT;
+        ca.y = b_.q;
+        ca.pcg_maxit = 1 << 30;
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess) return (cudaGetLastError(), 2);
+        if (cudaEventCreate(&e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            return (cudaGetLastError(), 2);
+        }
+        float best = 1e30f;
+        int choice = 2;
+        for (int v = 1; v <= 2; ++v) {
+            variant_ = v;
+            bool ok = launch_apply(ca, s) == cudaSuccess;
+            ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+            for (int r = 0; r < 3 && ok; ++r) ok = launch_apply(ca, s) == cudaSuccess;
+            ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+            float ms = 0;
+            if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+                best = ms;
+                choice = v;
+            }
+            cudaGetLastError();
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = choice;
+        return choice;
+    }
+
     // Same rounds as run(), launched straight onto `s` without graphs,
     // events or pinned host memory (the counters are read into `hc`, a host
     // array of 3 ints, with a pageable copy and a stream synchronisation).
     int run_direct(cudaStream_t s, double timeout_s, int *hc)
     {
         warm_occupancy(pb_.nh);
+        if (variant_ == 0) variant_ = 2;
         auto t0 = std::chrono::steady_clock::now();
         auto expired = [&]() {
             if (timeout_s <= 0) return false;
@@ -639,6 +744,7 @@ class Core {
         ev_a_ = ev.a;
         ev_b_ = ev.b;
         warm_occupancy(pb_.nh);
+        if (variant_ == 0) variant_ = autotune(s);
         FEM_CUDA(capture(s, 0, &G.head, &G.n_head));
         FEM_CUDA(capture(s, 1, &G.chunk, &G.n_chunk));
         FEM_CUDA(capture(s, 2, &G.tail_head, &G.n_tail_head));
@@ -684,6 +790,7 @@ class Core {
 
     const double *ustar64_ = nullptr;  // linear mode: the fixed state
     int max_steps_ = 1;
+    int variant_ = 0;       // CG apply kernel: 0 autotune, 1 per-cell, 2 bricks
     double apply_ms_ = 0;   // sampled device time of CG applies
     int apply_samples_ = 0;
     cudaEvent_t ev_a_ = nullptr, ev_b_ = nullptr;
@@ -727,7 +834,8 @@ static int check_options(const fem_options &o)
     if (o.precision != FEM_MIXED && o.precision != FEM_FP64)
         return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
     if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
-        !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1)
+        !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
+        o.apply_kernel < 0 || o.apply_kernel > 2)
         return (set_error("invalid solver options"), FEM_ERR_ARG);
     return FEM_OK;
 }
@@ -755,7 +863,7 @@ static cudaError_t join_streams(cudaStream_t from, cudaStream_t to)
 // Workspace slots
 enum {
     WS_CTL = 0, WS_CNT, WS_R64, WS_UT, WS_X, WS_R, WS_Z, WS_P, WS_Q, WS_DG, WS_LAM, WS_TAB, WS_CPT,
-    WS_U64CAT, WS_MASKCAT, WS_UBARCAT, WS_RHSCAT, WS_CP64CAT, WS_G64
+    WS_U64CAT, WS_MASKCAT, WS_UBARCAT, WS_RHSCAT, WS_CP64CAT, WS_G64, WS_S, WS_TUNE
 };
 
 template <typename T>
@@ -776,6 +884,8 @@ static int alloc_buffers(Workspace &ws, const Problem &pb, Buffers<T> &b, bool n
     WSGET(b.p, WS_P, T, D);
     WSGET(b.q, WS_Q, T, D);
     WSGET(b.dg, WS_DG, T, D);
+    WSGET(b.s, WS_S, T, D);
+    WSGET(b.tune, WS_TUNE, Ctl, n);
     if (n > 1) WSGET(b.tab, WS_TAB, InstDesc, n);
     else b.tab = nullptr;
     if (need_uT) WSGET(b.uT, WS_UT, T, D);
@@ -801,6 +911,7 @@ static std::vector<Ctl> initial_ctl(const Problem &pb, int step_begin, bool line
 struct ApplyTiming {
     double ms = 0;
     int samples = 0;
+    int variant = 0;
 };
 
 static void fill_stats(const Ctl &c, fem_stats *st, double ms, const ApplyTiming &at = ApplyTiming())
@@ -809,6 +920,7 @@ static void fill_stats(const Ctl &c, fem_stats *st, double ms, const ApplyTiming
     st->apply_ms = at.ms;
     st->apply_samples = at.samples;
     st->apply_launches = c.pcg_total;
+    st->apply_kernel = at.variant;
     st->status = c.status == 1 ? FEM_OK : (c.status == 0 ? FEM_ERR_NOT_CONVERGED : c.status);
     st->load_steps = c.steps_done;
     st->newton_iters = c.newton_total;
@@ -854,9 +966,11 @@ static int solve_batch(Workspace &ws, Problem &pb, double *u64, const uint8_t *m
     }
     Core<T> core(pb, b, SM_NONLINEAR, params_from(o), hc);
     core.max_steps_ = *std::max_element(pb.n_steps.begin(), pb.n_steps.end());
+    core.variant_ = o.apply_kernel;
     int rc = core.run(s, o.timeout_s);
     at.ms = core.apply_ms_;
     at.samples = core.apply_samples_;
+    at.variant = core.variant_;
     ctl_out.resize(ctl.size());
     cudaError_t e = cudaMemcpyAsync(ctl_out.data(), b.ctl, sizeof(Ctl) * ctl.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -900,9 +1014,11 @@ static int adjoint_batch(Workspace &ws, Problem &pb, const double *ustar, const 
     SolverParams prm = params_from(o);
     Core<T> core(pb, b, SM_LINEAR, prm, hc);
     core.ustar64_ = ustar;
+    core.variant_ = o.apply_kernel;
     int rc = core.run(s, o.timeout_s);
     at.ms = core.apply_ms_;
     at.samples = core.apply_samples_;
+    at.variant = core.variant_;
     cudaError_t e = cudaMemcpyAsync(&ctl_out, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (rc) return rc;
@@ -930,8 +1046,8 @@ static size_t region_layout(const InstDesc &d, bool has_cp, Buffers<T> *b, char 
     size_t o_ctl = carve(off, sizeof(Ctl));
     size_t o_cnt = carve(off, 4 * sizeof(int));
     size_t o_r64 = carve(off, sizeof(double) * D);
-    size_t o_vec[6];
-    for (int i = 0; i < 6; ++i) o_vec[i] = carve(off, sizeof(T) * D);
+    size_t o_vec[7];
+    for (int i = 0; i < 7; ++i) o_vec[i] = carve(off, sizeof(T) * D);
     size_t o_ut = sepT ? carve(off, sizeof(T) * D) : 0;
     size_t o_cp = (sepT && has_cp) ? carve(off, sizeof(T) * Ne) : 0;
     if (b && base) {
@@ -939,8 +1055,8 @@ static size_t region_layout(const InstDesc &d, bool has_cp, Buffers<T> *b, char 
         b->counter = (int *)(base + o_cnt);
         b->tab = nullptr;
         b->R64 = (double *)(base + o_r64);
-        T **v[6] = {&b->x, &b->r, &b->z, &b->p, &b->q, &b->dg};
-        for (int i = 0; i < 6; ++i) *v[i] = (T *)(base + o_vec[i]);
+        T **v[7] = {&b->x, &b->r, &b->z, &b->p, &b->q, &b->dg, &b->s};
+        for (int i = 0; i < 7; ++i) *v[i] = (T *)(base + o_vec[i]);
         if (sepT) b->uT = (T *)(base + o_ut);
         if (sepT && has_cp) b->cpT = (T *)(base + o_cp);
     }
@@ -993,6 +1109,7 @@ static int solve_region_t(const InstDesc &d, int n_steps, const fem_bc &bc, cons
     int hc[4] = {0, 0, 0, 0};
     Core<T> core(pb, b, SM_NONLINEAR, params_from(o), hc);
     core.max_steps_ = n_steps;
+    core.variant_ = o.apply_kernel;
     int rc = core.run_direct(s, o.timeout_s, hc);
     cudaError_t e = cudaMemcpyAsync(&ctl_out, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

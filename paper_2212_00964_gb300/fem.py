@@ -42,7 +42,7 @@ class fem_options(ctypes.Structure):
                 ("newton_atol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
                 ("pcg_rtol", ctypes.c_double), ("pcg_maxit", ctypes.c_int),
                 ("pcg_chunk", ctypes.c_int), ("step_begin", ctypes.c_int),
-                ("cells_per_block", ctypes.c_int), ("deterministic", ctypes.c_int),
+                ("apply_kernel", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("timeout_s", ctypes.c_double)]
 
 
@@ -50,7 +50,8 @@ class fem_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("load_steps", ctypes.c_int), ("newton_iters", ctypes.c_int),
                 ("pcg_iters", ctypes.c_int), ("ref_rnorm", ctypes.c_double),
                 ("final_rnorm", ctypes.c_double), ("time_ms", ctypes.c_double),
-                ("apply_ms", ctypes.c_double), ("apply_samples", ctypes.c_int), ("apply_launches", ctypes.c_int)]
+                ("apply_ms", ctypes.c_double), ("apply_samples", ctypes.c_int), ("apply_launches", ctypes.c_int),
+                ("apply_kernel", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
