@@ -106,8 +106,8 @@ __global__ void __launch_bounds__(CELL_BLOCK) cell_kernel(const CellArgs<T> a)
             const int nid[8] = {n0, n0 + 1, n0 + sy, n0 + sy + 1, n0 + sz, n0 + sz + 1, n0 + sz + sy,
                                 n0 + sz + sy + 1};
             const T *ub = a.u + d.dof_off;
-            const T ihx = (T)(1.0 / d.hx), ihy = (T)(1.0 / d.hy), ihz = (T)(1.0 / d.hz);
-            const T wdet = (T)(d.hx * d.hy * d.hz * 0.125);
+            const T ihx = d.ihx<T>(), ihy = d.ihy<T>(), ihz = d.ihz<T>();
+            const T wdet = d.wdet<T>();
             const T *cp = a.cell_param ? a.cell_param + d.cell_off : nullptr;
             // VJP uses the unit-scale residual: dR_e/dtheta_e = s'(theta_e) R_e(u; s = 1)
             const Mat<T> m = cell_mat<T>(d, (MODE == CM_VJP) ? nullptr : cp, cell);
@@ -358,8 +358,8 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z) apply_brick(const
             const int l0 = ci + NX * (cj + NY * ck);
             const int lid[8] = {l0, l0 + 1, l0 + NX, l0 + NX + 1, l0 + NX * NY, l0 + NX * NY + 1,
                                 l0 + NX * NY + NX, l0 + NX * NY + NX + 1};
-            const T ihx = (T)(1.0 / d.hx), ihy = (T)(1.0 / d.hy), ihz = (T)(1.0 / d.hz);
-            const T wdet = (T)(d.hx * d.hy * d.hz * 0.125);
+            const T ihx = d.ihx<T>(), ihy = d.ihy<T>(), ihz = d.ihz<T>();
+            const T wdet = d.wdet<T>();
             const int cell = (i0 + ci) + nx * ((j0 + cj) + ny * (k0 + ck));
             const T *cp = a.cell_param ? a.cell_param + d.cell_off : nullptr;
             const Mat<T> m = cell_mat<T>(d, cp, cell);
@@ -477,8 +477,8 @@ __global__ void __launch_bounds__(CELL_BLOCK) assemble_kernel(const AsmArgs<T> a
                           n0 + sz + sy + 1};
         const int64_t col_dof = 3 * nid[cn] + cc;
         if (a.mask && a.mask[col_dof]) continue;
-        const T ihx = (T)(1.0 / d.hx), ihy = (T)(1.0 / d.hy), ihz = (T)(1.0 / d.hz);
-        const T wdet = (T)(d.hx * d.hy * d.hz * 0.125);
+        const T ihx = d.ihx<T>(), ihy = d.ihy<T>(), ihz = d.ihz<T>();
+        const T wdet = d.wdet<T>();
         const Mat<T> m = cell_mat<T>(d, a.cell_param, cell);
         T Gu[3][3][4];
 #pragma unroll

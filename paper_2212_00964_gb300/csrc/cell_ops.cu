@@ -145,7 +145,8 @@ InstDesc make_desc(const fem_mesh_s *m, const fem_material *mat)
     d.kind = mat->kind;
     d.E = mat->E; d.nu = mat->nu; d.p = mat->simp_p; d.emin = mat->simp_emin;
     d.hx = m->lx / m->nx; d.hy = m->ly / m->ny; d.hz = m->lz / m->nz;
-    d.dof_off = 0; d.cell_off = 0; d.tile_off = 0; d.vec_off = 0;
+    d.dof_off = 0; d.cell_off = 0; d.tile_off = 0; d.vec_off = 0; d.brick_off = 0;
+    d.derive();
     return d;
 }
 

@@ -27,9 +27,57 @@ struct InstDesc {
     int64_t tile_off;      // first cell tile (cell kernels)
     int64_t vec_off;       // first vector chunk (vector kernels)
     int64_t brick_off;     // first 8x4x4-cell brick (brick-tiled kernels)
+    // Constants of the instance, precomputed on the host in both precisions
+    // so that no kernel evaluates a double expression per cell (GB300 runs
+    // FP64 at a small fraction of the FP32 rate):
+    //   c1u, c2u: material constants at unit stiffness scale
+    //             (LE/SIMP: lam, mu; NH: G, kappa);
+    //   ih: 1/h per direction; wdet: Gauss weight x det J = hx hy hz / 8.
+    double c1u_d, c2u_d, ihx_d, ihy_d, ihz_d, wdet_d;
+    float c1u_f, c2u_f, ihx_f, ihy_f, ihz_f, wdet_f;
+    float emin_f, p_f;
+    template <typename T> __host__ __device__ T c1u() const;
+    template <typename T> __host__ __device__ T c2u() const;
+    template <typename T> __host__ __device__ T ihx() const;
+    template <typename T> __host__ __device__ T ihy() const;
+    template <typename T> __host__ __device__ T ihz() const;
+    template <typename T> __host__ __device__ T wdet() const;
+    // fill the derived constants from nx.., kind, E, nu, p, emin, hx..
+    void derive()
+    {
+        if (kind == FEM_NEOHOOKE) {
+            c1u_d = E / (2.0 * (1.0 + nu));
+            c2u_d = E / (3.0 * (1.0 - 2.0 * nu));
+        } else {
+            c1u_d = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+            c2u_d = E / (2.0 * (1.0 + nu));
+        }
+        ihx_d = 1.0 / hx;
+        ihy_d = 1.0 / hy;
+        ihz_d = 1.0 / hz;
+        wdet_d = hx * hy * hz * 0.125;
+        c1u_f = (float)c1u_d; c2u_f = (float)c2u_d;
+        ihx_f = (float)ihx_d; ihy_f = (float)ihy_d; ihz_f = (float)ihz_d;
+        wdet_f = (float)wdet_d;
+        emin_f = (float)emin;
+        p_f = (float)p;
+    }
     __host__ __device__ int64_t n_dofs() const { return 3LL * (nx + 1) * (ny + 1) * (nz + 1); }
     __host__ __device__ int64_t n_cells() const { return (int64_t)nx * ny * nz; }
 };
+
+template <> __host__ __device__ inline double InstDesc::c1u<double>() const { return c1u_d; }
+template <> __host__ __device__ inline float InstDesc::c1u<float>() const { return c1u_f; }
+template <> __host__ __device__ inline double InstDesc::c2u<double>() const { return c2u_d; }
+template <> __host__ __device__ inline float InstDesc::c2u<float>() const { return c2u_f; }
+template <> __host__ __device__ inline double InstDesc::ihx<double>() const { return ihx_d; }
+template <> __host__ __device__ inline float InstDesc::ihx<float>() const { return ihx_f; }
+template <> __host__ __device__ inline double InstDesc::ihy<double>() const { return ihy_d; }
+template <> __host__ __device__ inline float InstDesc::ihy<float>() const { return ihy_f; }
+template <> __host__ __device__ inline double InstDesc::ihz<double>() const { return ihz_d; }
+template <> __host__ __device__ inline float InstDesc::ihz<float>() const { return ihz_f; }
+template <> __host__ __device__ inline double InstDesc::wdet<double>() const { return wdet_d; }
+template <> __host__ __device__ inline float InstDesc::wdet<float>() const { return wdet_f; }
 
 // Per-instance solver state, device resident.  The CG scalars live in a
 // ring of four slots indexed by the CG iteration, so a slot can be cleared
@@ -311,30 +359,23 @@ __device__ __forceinline__ void le_stress(const T *H, const Mat<T> &m, T *P)
             P[3 * i + j] = m.c2 * (H[3 * i + j] + H[3 * j + i]) + (i == j ? tr : (T)0);
 }
 
-// Cell material constants from the instance and the cell parameter.
+// Cell material constants from the instance and the cell parameter, in T
+// only (the unit-scale constants were derived on the host).
 template <typename T>
 __device__ __forceinline__ Mat<T> cell_mat(const InstDesc &d, const T *cell_param, int64_t cell)
 {
-    double s = 1.0;
-    Mat<T> m;
+    T sc = (T)1;
     if (d.kind == FEM_SIMP) {
-        T th = cell_param ? cell_param[cell] : (T)1;
-        T sp = (d.p == 3.0) ? th * th * th : (T)pow((double)th, d.p);
-        T sc = (T)d.emin + sp * (T)(1.0 - d.emin);
-        T E = (T)d.E * sc;
-        m.c1 = E * (T)(d.nu / ((1.0 + d.nu) * (1.0 - 2.0 * d.nu)));
-        m.c2 = E * (T)(1.0 / (2.0 * (1.0 + d.nu)));
-        return m;
+        const T th = cell_param ? cell_param[cell] : (T)1;
+        const T sp = (d.p_f == 3.0f) ? th * th * th : (T)pow((double)th, d.p);
+        const T emin = sizeof(T) == 4 ? (T)d.emin_f : (T)d.emin;
+        sc = emin + sp * ((T)1 - emin);
+    } else if (cell_param) {
+        sc = cell_param[cell];
     }
-    T sc = cell_param ? cell_param[cell] : (T)s;
-    T E = (T)d.E * sc;
-    if (d.kind == FEM_NEOHOOKE) {
-        m.c1 = E * (T)(1.0 / (2.0 * (1.0 + d.nu)));
-        m.c2 = E * (T)(1.0 / (3.0 * (1.0 - 2.0 * d.nu)));
-    } else {
-        m.c1 = E * (T)(d.nu / ((1.0 + d.nu) * (1.0 - 2.0 * d.nu)));
-        m.c2 = E * (T)(1.0 / (2.0 * (1.0 + d.nu)));
-    }
+    Mat<T> m;
+    m.c1 = d.c1u<T>() * sc;
+    m.c2 = d.c2u<T>() * sc;
     return m;
 }
 

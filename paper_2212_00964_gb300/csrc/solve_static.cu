@@ -70,6 +70,7 @@ extern "C" int fem_solve_static(int nx, int ny, int nz, double lx, double ly, do
     d.kind = mat->kind;
     d.E = mat->E; d.nu = mat->nu; d.p = mat->simp_p; d.emin = mat->simp_emin;
     d.hx = lx / nx; d.hy = ly / ny; d.hz = lz / nz;
+    d.derive();
     if (d.n_dofs() >= (int64_t)INT32_MAX)
         return (set_error("fem_solve_static: mesh too large"), FEM_ERR_ARG);
     const size_t need = region_bytes(d, o.precision, cell_param != nullptr);

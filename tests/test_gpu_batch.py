@@ -25,11 +25,12 @@ def make_instances(F, works):
     return insts
 
 
-def test_small_batch_vs_oracle_and_single():
+@pytest.mark.parametrize("apply_kernel", [1, 2])
+def test_small_batch_vs_oracle_and_single(apply_kernel):
     F = fem()
-    works = inputs.c3(n_inst=7, seed=3, lo=2, hi=5, n_steps=3)
+    works = inputs.c3(n_inst=7, seed=3, lo=2, hi=9, n_steps=3)
     insts = make_instances(F, works)
-    rc, stats = F.fem_solve_batched(insts, F.default_options(newton_rtol=1e-12))
+    rc, stats = F.fem_solve_batched(insts, F.default_options(newton_rtol=1e-12, apply_kernel=apply_kernel))
     assert rc == 0 and all(s["status"] == 0 for s in stats)
     for w, I, st in zip(works, insts, stats):
         om = oracle.mesh(w.nx, w.ny, w.nz)

@@ -3,6 +3,8 @@ the linear-elastic c0 solve (FP64 and mixed), Neo-Hookean load-stepped
 Newton (FP64 and mixed with FP64 refinement), SIMP solve, and the 64^3
 Neo-Hookean benchmark solve checked by properties that hold at any size
 (mixed vs FP64 GPU solution, oracle FP64 residual at the GPU solution)."""
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -48,6 +50,11 @@ def oracle_solve(w):
     return osolve.linear_solve(om, mat, w.mask, w.u_bar, f, w.cell_param)
 
 
+@functools.lru_cache(None)
+def oracle_c1(n):
+    return oracle_solve(inputs.c1(n=n, n_steps=10))
+
+
 def test_c0_linear_elastic_fp64():
     w = inputs.c0()
     ref = oracle_solve(w)
@@ -64,15 +71,18 @@ def test_c0_linear_elastic_mixed_refined():
     assert rel_l2(u, ref) <= TOL_REFINED
 
 
-@pytest.mark.parametrize("n", [4, 8])
-def test_neohooke_load_steps(n):
+@pytest.mark.parametrize("apply_kernel", [1, 2])
+@pytest.mark.parametrize("n", [4, 8, 9])
+def test_neohooke_load_steps(n, apply_kernel):
+    """Both CG apply kernels (per-cell scatter, 8x4x4 bricks); 9^3 leaves
+    ragged bricks in every direction."""
     w = inputs.c1(n=n, n_steps=10)
-    ref = oracle_solve(w)
-    u64, st64 = gpu_solve(w, 0, newton_rtol=1e-13, pcg_rtol=1e-8)
-    assert st64["status"] == 0 and st64["load_steps"] == 10
+    ref = oracle_c1(n)
+    u64, st64 = gpu_solve(w, 0, newton_rtol=1e-13, pcg_rtol=1e-8, apply_kernel=apply_kernel)
+    assert st64["status"] == 0 and st64["load_steps"] == 10 and st64["apply_kernel"] == apply_kernel
     assert rel_l2(u64, ref) <= TOL_FP64
-    u32, st32 = gpu_solve(w, 2, newton_rtol=1e-12)
-    assert st32["status"] == 0
+    u32, st32 = gpu_solve(w, 2, newton_rtol=1e-12, apply_kernel=apply_kernel)
+    assert st32["status"] == 0 and st32["apply_kernel"] == apply_kernel
     assert rel_l2(u32, ref) <= TOL_REFINED
 
 
@@ -88,13 +98,14 @@ def test_neohooke_noncubic_with_stiffness_field():
     assert rel_l2(u, ref) <= TOL_REFINED
 
 
-def test_simp_cantilever_small():
+@pytest.mark.parametrize("apply_kernel", [1, 2])
+def test_simp_cantilever_small(apply_kernel):
     w = inputs.c2(nx=16, ny=8, nz=8)
     ref = oracle_solve(w)
-    u, st = gpu_solve(w, 2, newton_rtol=1e-12)
+    u, st = gpu_solve(w, 2, newton_rtol=1e-12, apply_kernel=apply_kernel)
     assert st["status"] == 0
     assert rel_l2(u, ref) <= TOL_REFINED
-    u64, st64 = gpu_solve(w, 0, newton_rtol=1e-13, pcg_rtol=1e-9)
+    u64, st64 = gpu_solve(w, 0, newton_rtol=1e-13, pcg_rtol=1e-9, apply_kernel=apply_kernel)
     assert rel_l2(u64, ref) <= TOL_FP64
 
 
