@@ -52,7 +52,7 @@ __device__ __forceinline__ void scatter_add(T *p, T v, int plain)
 }
 
 template <typename T, int NH, int MODE>
-__global__ void __launch_bounds__(CELL_BLOCK) cell_kernel(const CellArgs<T> a)
+__global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? 3 : 1)) cell_kernel(const CellArgs<T> a)
 {
     __shared__ double sh[CELL_BLOCK / 32];
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
@@ -189,6 +189,11 @@ __global__ void __launch_bounds__(CELL_BLOCK) cell_kernel(const CellArgs<T> a)
                     } else {
                         le_stress<T>(dH, m, P);
                     }
+                    if (MODE == CM_APPLY_PCG) {
+                        // x_e . K_e x_e = sum_gp w detJ dP : dH
+#pragma unroll
+                        for (int t = 0; t < 9; ++t) part += wdet * P[t] * dH[t];
+                    }
                 }
                 if (IS_RES || IS_APPLY) {
 #pragma unroll
@@ -259,12 +264,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) cell_kernel(const CellArgs<T> a)
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
                     for (int n = 0; n < 8; ++n) scatter_add<T>(&yb[3 * nid[n] + c], ye[c][n], a.plain_store);
-                if (MODE == CM_APPLY_PCG) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-#pragma unroll
-                        for (int n = 0; n < 8; ++n) part += xe[c][n] * ye[c][n];
-                }
+
             }
             if (IS_RES && NH && inverted) {
                 if (MODE == CM_RESIDUAL_CTL) atomicExch(&a.ctl[k].jflag, 1);
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) cell_kernel(const CellArgs<T> a)
 // component.  Compared with a scatter per cell this moves 4.5x fewer
 // reductions to L2 and reads each nodal value once per brick.
 template <typename T, int NH>
-__global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z) apply_brick(const CellArgs<T> a)
+__global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ? 4 : 1)) apply_brick(const CellArgs<T> a)
 {
     constexpr int NX = BRICK_X + 1, NY = BRICK_Y + 1, NZ = BRICK_Z + 1, NN = NX * NY * NZ;
     constexpr int NT = BRICK_X * BRICK_Y * BRICK_Z;
@@ -363,17 +363,17 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z) apply_brick(const
             const int cell = (i0 + ci) + nx * ((j0 + cj) + ny * (k0 + ck));
             const T *cp = a.cell_param ? a.cell_param + d.cell_off : nullptr;
             const Mat<T> m = cell_mat<T>(d, cp, cell);
-            T Gu[3][3][4], Gx[3][3][4], xe[3][8];
+            T Gu[3][3][4], Gx[3][3][4];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                T v[8];
+                T v[8], w[8];
 #pragma unroll
                 for (int n = 0; n < 8; ++n) {
                     v[n] = su[c][lid[n]];
-                    xe[c][n] = sp[c][lid[n]];
+                    w[n] = sp[c][lid[n]];
                 }
                 grad_sf<T>(v, ihx, ihy, ihz, Gu[c]);
-                grad_sf<T>(xe[c], ihx, ihy, ihz, Gx[c]);
+                grad_sf<T>(w, ihx, ihy, ihz, Gx[c]);
             }
             T S[3][3][4];
 #pragma unroll
@@ -403,6 +403,8 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z) apply_brick(const
                     le_stress<T>(dH, m, P);
                 }
 #pragma unroll
+                for (int t = 0; t < 9; ++t) part += wdet * P[t] * dH[t];
+#pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     S[c][0][be + 2 * ga] += P[3 * c + 0];
                     S[c][1][al + 2 * ga] += P[3 * c + 1];
@@ -416,10 +418,7 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z) apply_brick(const
                 for (int n = 0; n < 8; ++n) ye[n] = 0;
                 grad_sf_t<T>(S[c], ihx * wdet, ihy * wdet, ihz * wdet, ye);
 #pragma unroll
-                for (int n = 0; n < 8; ++n) {
-                    atomicAdd(&sy[c][lid[n]], ye[n]);
-                    part += xe[c][n] * ye[n];
-                }
+                for (int n = 0; n < 8; ++n) atomicAdd(&sy[c][lid[n]], ye[n]);
             }
         }
         __syncthreads();

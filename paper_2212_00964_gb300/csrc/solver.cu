@@ -16,6 +16,8 @@
 // so CG is used.
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -634,7 +636,7 @@ class Core {
             cudaEventDestroy(e0);
             return (cudaGetLastError(), 2);
         }
-        float best = 1e30f;
+        float best = 1e30f, times[2] = {-1.f, -1.f};
         int choice = 2;
         for (int v = 1; v <= 2; ++v) {
             variant_ = v;
@@ -643,14 +645,22 @@ class Core {
             for (int r = 0; r < 3 && ok; ++r) ok = launch_apply(ca, s) == cudaSuccess;
             ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
             float ms = 0;
-            if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
-                best = ms;
-                choice = v;
+            if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+                times[v - 1] = ms;
+                if (ms < best) {
+                    best = ms;
+                    choice = v;
+                }
             }
             cudaGetLastError();
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        if (const char *env = getenv("FEMGB_TUNE_LOG")) {
+            if (env[0] == '1')
+                fprintf(stderr, "femgb autotune: D=%lld instances=%d per-cell %.3f ms, bricks %.3f ms -> %d\n",
+                        (long long)pb_.D, (int)pb_.desc.size(), times[0] / 3, times[1] / 3, choice);
+        }
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = choice;
         return choice;
