@@ -66,21 +66,30 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? 3 : 1)) cell_ker
         }
         int slot = 0;
         if (MODE == CM_APPLY_PCG) {
+            // thread 0 takes the CG decision (FP64 scalars) for the block
+            __shared__ int s_go;
             Ctl &c = a.ctl[k];
-            if (c.status != 0 || !c.solving || c.pcg_done) continue;  // uniform per block
             const int it = c.pcg_base + a.iter;
-            if (cg_converged(c, it, a.pcg_maxit)) {
-                if (tile == d.tile_off && threadIdx.x == 0) {
-                    c.pcg_done = 1;
-                    c.pcg_last = it;
+            if (threadIdx.x == 0) {
+                int go = c.status == 0 && c.solving && !c.pcg_done;
+                if (go && cg_converged(c, it, a.pcg_maxit)) {
+                    go = 0;
+                    if (tile == d.tile_off) {
+                        c.pcg_done = 1;
+                        c.pcg_last = it;
+                    }
                 }
-                continue;
+                if (go && tile == d.tile_off) {
+                    c.gamma[(it + 1) & 3] = 0;
+                    c.rr[(it + 1) & 3] = 0;
+                }
+                s_go = go;
             }
+            __syncthreads();
+            const int go = s_go;
+            __syncthreads();  // s_go is rewritten for the next tile
+            if (!go) continue;
             slot = it & 3;
-            if (tile == d.tile_off && threadIdx.x == 0) {
-                c.gamma[(it + 1) & 3] = 0;
-                c.rr[(it + 1) & 3] = 0;
-            }
         } else if (MODE == CM_RESIDUAL_CTL || MODE == CM_APPLY_CTL) {
             if (a.ctl[k].status != 0) continue;
         } else if (MODE == CM_DIAG_CTL) {
@@ -272,7 +281,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? 3 : 1)) cell_ker
             }
         }
         if (MODE == CM_APPLY_PCG) {
-            double s = block_sum<double, CELL_BLOCK>((double)part, sh);
+            const double s = block_sum_t<T, CELL_BLOCK>(part, sh);
             if (threadIdx.x == 0) atomicAdd(&a.ctl[k].delta[slot], s);
         }
     }
@@ -308,20 +317,28 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
             d = a.d0;
         }
         Ctl &cc = a.ctl[k];
-        if (cc.status != 0 || !cc.solving || cc.pcg_done) continue;  // uniform per CTA
         const int it = cc.pcg_base + a.iter;
-        if (cg_converged(cc, it, a.pcg_maxit)) {
-            if (brick == d.brick_off && tid == 0) {
-                cc.pcg_done = 1;
-                cc.pcg_last = it;
+        __shared__ int s_go;
+        if (tid == 0) {
+            int go = cc.status == 0 && cc.solving && !cc.pcg_done;
+            if (go && cg_converged(cc, it, a.pcg_maxit)) {
+                go = 0;
+                if (brick == d.brick_off) {
+                    cc.pcg_done = 1;
+                    cc.pcg_last = it;
+                }
             }
-            continue;
+            if (go && brick == d.brick_off) {
+                cc.gamma[(it + 1) & 3] = 0;
+                cc.rr[(it + 1) & 3] = 0;
+            }
+            s_go = go;
         }
+        __syncthreads();
+        const int go = s_go;
+        __syncthreads();
+        if (!go) continue;
         const int slot = it & 3;
-        if (brick == d.brick_off && tid == 0) {
-            cc.gamma[(it + 1) & 3] = 0;
-            cc.rr[(it + 1) & 3] = 0;
-        }
         const int nx = d.nx, ny = d.ny, nz = d.nz;
         const int tnx = (nx + BRICK_X - 1) / BRICK_X, tny = (ny + BRICK_Y - 1) / BRICK_Y;
         const int lb = (int)(brick - d.brick_off);
@@ -434,7 +451,7 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
                 if (v != (T)0) atomicAdd(&yb[3 * (I + sy_ * J + sz_ * K) + c], v);
             }
         }
-        const double s = block_sum<double, NT>((double)part, sh);
+        const double s = block_sum_t<T, NT>(part, sh);
         if (tid == 0) atomicAdd(&a.ctl[k].delta[slot], s);
         __syncthreads();  // shared arrays are reused by the next brick
     }

@@ -188,6 +188,32 @@ __device__ __forceinline__ T block_sum(T v, T *sh)
     return s;
 }
 
+// Block-wide sum of FP32 partials with the cross-warp sum in FP64: the warp
+// stage runs on the FP32 pipes (GB300's FP64 rate is a small fraction of
+// FP32), one FP64 add per warp.  The result is valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum_f(float v, double *sh)
+{
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = (double)v;
+    __syncthreads();
+    double s = 0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NT / 32; ++i) s += sh[i];
+    }
+    return s;
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ double block_sum_t(T v, double *sh)
+{
+    if (sizeof(T) == 4) return block_sum_f<NT>((float)v, sh);
+    return block_sum<double, NT>((double)v, sh);
+}
+
 // ------------------------------------------------ HEX8 on a uniform box ----
 // Reference cell [-1,1]^3, trilinear shape functions written as tensor
 // products phi_p(xi) phi_q(eta) phi_r(zeta), phi_0(s) = (1-s)/2,
@@ -291,7 +317,8 @@ __device__ __forceinline__ void nh_point(const T *H, const Mat<T> &m, NHPoint<T>
     T c20 = F[1] * F[5] - F[2] * F[4], c21 = F[2] * F[3] - F[0] * F[5], c22 = F[0] * F[4] - F[1] * F[3];
     q.Jm1 = det_ipH_m1(H);
     q.J = (T)1 + q.Jm1;
-    T iJ = (T)1 / q.J;
+    const T r = rcbrt_t(q.J);  // J^{-1/3}: J^{-2/3} = r^2 and 1/J = r^3 without a division
+    const T iJ = r * r * r;
     q.A[0] = c00 * iJ; q.A[1] = c01 * iJ; q.A[2] = c02 * iJ;
     q.A[3] = c10 * iJ; q.A[4] = c11 * iJ; q.A[5] = c12 * iJ;
     q.A[6] = c20 * iJ; q.A[7] = c21 * iJ; q.A[8] = c22 * iJ;
@@ -299,7 +326,6 @@ __device__ __forceinline__ void nh_point(const T *H, const Mat<T> &m, NHPoint<T>
 #pragma unroll
     for (int t = 0; t < 9; ++t) I1 += F[t] * F[t];
     q.I1 = I1;
-    T r = rcbrt_t(q.J);
     q.k1 = m.c1 * r * r;  // G J^{-2/3}
 }
 

@@ -211,9 +211,9 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_init(const VecArgs<T> a)
         ag += rv * zv;
         arr += rv * rv;
     }
-    const double s1 = block_sum<double, VEC_BLOCK>((double)ag, sh);
+    const double s1 = block_sum_t<T, VEC_BLOCK>(ag, sh);
     if (threadIdx.x == 0) atomicAdd(&c.gamma[0], s1);
-    const double s2 = block_sum<double, VEC_BLOCK>((double)arr, sh);
+    const double s2 = block_sum_t<T, VEC_BLOCK>(arr, sh);
     if (threadIdx.x == 0) {
         atomicAdd(&c.rr[0], s2);
         atomicAdd(&c.rr0, s2);
@@ -232,42 +232,54 @@ template <typename T>
 __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_update(const VecArgs<T> a)
 {
     __shared__ double sh[VEC_BLOCK / 32];
+    __shared__ double s_ab[2];
+    __shared__ int s_go;
     VEC_ITEMS_BEGIN
-    if (c.status != 0 || !c.solving || c.pcg_done) continue;
     const int it = c.pcg_base + a.iter;
-    if (cg_converged(c, it, a.prm.pcg_maxit)) continue;  // the next apply records it
-    const bool lead = (item == d.vec_off) && threadIdx.x == 0;
-    const int s0 = it & 3, sm = (it + 3) & 3, sn = (it + 1) & 3;
-    const double g = c.gamma[s0];
-    double beta = 0.0, den = c.delta[s0];
-    if (it > 0) {
-        beta = g / c.gamma[sm];
-        den = den - beta * g / c.alpha[sm];
-    }
-    if (!isfinite(den) || !isfinite(g)) {
-        if (lead) {
-            c.status = FEM_ERR_NONFINITE;
-            c.pcg_done = 1;
-            c.pcg_last = it;
+    // thread 0 takes the scalar decisions in FP64 and broadcasts them
+    if (threadIdx.x == 0) {
+        int go = c.status == 0 && c.solving && !c.pcg_done && !cg_converged(c, it, a.prm.pcg_maxit);
+        if (go) {
+            const bool lead = item == d.vec_off;
+            const int s0 = it & 3, sm = (it + 3) & 3, sn = (it + 1) & 3;
+            const double g = c.gamma[s0];
+            double beta = 0.0, den = c.delta[s0];
+            if (it > 0) {
+                beta = g / c.gamma[sm];
+                den = den - beta * g / c.alpha[sm];
+            }
+            if (!isfinite(den) || !isfinite(g)) {
+                if (lead) {
+                    c.status = FEM_ERR_NONFINITE;
+                    c.pcg_done = 1;
+                    c.pcg_last = it;
+                }
+                go = 0;
+            } else if (!(den > 0.0)) {
+                // p^T K p <= 0: negative curvature.  Keep the iterate so far
+                // (truncated CG); with no iterate yet the tangent is unusable.
+                if (lead) {
+                    if (it == 0) c.status = FEM_ERR_BREAKDOWN;
+                    c.pcg_done = 1;
+                    c.pcg_last = it;
+                }
+                go = 0;
+            } else {
+                s_ab[0] = g / den;
+                s_ab[1] = beta;
+                if (lead) {
+                    c.alpha[s0] = g / den;
+                    c.delta[sn] = 0;
+                }
+            }
         }
-        continue;
+        s_go = go;
     }
-    if (!(den > 0.0)) {
-        // p^T K p <= 0: negative curvature.  Keep the iterate so far
-        // (truncated CG); with no iterate yet the tangent is unusable.
-        if (lead) {
-            if (it == 0) c.status = FEM_ERR_BREAKDOWN;
-            c.pcg_done = 1;
-            c.pcg_last = it;
-        }
-        continue;
-    }
-    const double alpha = g / den;
-    if (lead) {
-        c.alpha[s0] = alpha;
-        c.delta[sn] = 0;
-    }
-    const T al = (T)alpha, be = (T)beta;
+    __syncthreads();
+    const int go = s_go;
+    const T al = (T)s_ab[0], be = (T)s_ab[1];
+    __syncthreads();
+    if (!go) continue;
     const bool first = it == 0;
     T ag = 0, arr = 0;
     const int64_t bd = blockDim.x;
@@ -308,10 +320,10 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_update(const VecArgs<T> a)
             }
         }
     }
-    const double s1 = block_sum<double, VEC_BLOCK>((double)ag, sh);
-    if (threadIdx.x == 0) atomicAdd(&c.gamma[sn], s1);
-    const double s2 = block_sum<double, VEC_BLOCK>((double)arr, sh);
-    if (threadIdx.x == 0) atomicAdd(&c.rr[sn], s2);
+    const double s1 = block_sum_t<T, VEC_BLOCK>(ag, sh);
+    if (threadIdx.x == 0) atomicAdd(&c.gamma[(it + 1) & 3], s1);
+    const double s2 = block_sum_t<T, VEC_BLOCK>(arr, sh);
+    if (threadIdx.x == 0) atomicAdd(&c.rr[(it + 1) & 3], s2);
     VEC_ITEMS_END
 }
 
