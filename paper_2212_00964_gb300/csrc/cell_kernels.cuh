@@ -55,6 +55,11 @@ template <typename T, int NH, int MODE>
 __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? 3 : 1)) cell_kernel(const CellArgs<T> a)
 {
     __shared__ double sh[CELL_BLOCK / 32];
+    // CG apply: p.Kp partials accumulate in registers over the tiles of one
+    // instance and are reduced once per block (or when the instance changes),
+    // so the tile loop itself has no block barrier.
+    T part = 0;
+    int acc_k = -1, acc_slot = 0;
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
         int k = 0;
         InstDesc d;
@@ -66,30 +71,33 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? 3 : 1)) cell_ker
         }
         int slot = 0;
         if (MODE == CM_APPLY_PCG) {
-            // thread 0 takes the CG decision (FP64 scalars) for the block
-            __shared__ int s_go;
+            if (acc_k >= 0 && k != acc_k) {  // uniform per block
+                const double s = block_sum_t<T, CELL_BLOCK>(part, sh);
+                if (threadIdx.x == 0) atomicAdd(&a.ctl[acc_k].delta[acc_slot], s);
+                part = 0;
+                acc_k = -1;
+            }
+            // every warp takes the same CG decision (lane 0, FP64 scalars)
             Ctl &c = a.ctl[k];
             const int it = c.pcg_base + a.iter;
-            if (threadIdx.x == 0) {
-                int go = c.status == 0 && c.solving && !c.pcg_done;
-                if (go && cg_converged(c, it, a.pcg_maxit)) {
-                    go = 0;
-                    if (tile == d.tile_off) {
+            int go = 0;
+            if ((threadIdx.x & 31) == 0) {
+                go = c.status == 0 && c.solving && !c.pcg_done && !cg_converged(c, it, a.pcg_maxit);
+                if (threadIdx.x == 0 && tile == d.tile_off) {
+                    if (go) {
+                        c.gamma[(it + 1) & 3] = 0;
+                        c.rr[(it + 1) & 3] = 0;
+                    } else if (c.status == 0 && c.solving && !c.pcg_done) {
                         c.pcg_done = 1;
                         c.pcg_last = it;
                     }
                 }
-                if (go && tile == d.tile_off) {
-                    c.gamma[(it + 1) & 3] = 0;
-                    c.rr[(it + 1) & 3] = 0;
-                }
-                s_go = go;
             }
-            __syncthreads();
-            const int go = s_go;
-            __syncthreads();  // s_go is rewritten for the next tile
+            go = __shfl_sync(0xffffffffu, go, 0);
             if (!go) continue;
             slot = it & 3;
+            acc_k = k;
+            acc_slot = slot;
         } else if (MODE == CM_RESIDUAL_CTL || MODE == CM_APPLY_CTL) {
             if (a.ctl[k].status != 0) continue;
         } else if (MODE == CM_DIAG_CTL) {
@@ -102,7 +110,6 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? 3 : 1)) cell_ker
         const int ne = (int)(a.cells ? a.n_list : d.n_cells());
         const int local = (int)(tile - d.tile_off) * (int)blockDim.x + (int)threadIdx.x;
         const bool active = local < ne;
-        T part = 0;
         if (active) {
             const int cell = a.cells ? a.cells[local] : local;
             const unsigned nx = (unsigned)d.nx, ny = (unsigned)d.ny;
@@ -280,10 +287,10 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? 3 : 1)) cell_ker
                 else if (a.jflag) atomicExch(a.jflag, 1);
             }
         }
-        if (MODE == CM_APPLY_PCG) {
-            const double s = block_sum_t<T, CELL_BLOCK>(part, sh);
-            if (threadIdx.x == 0) atomicAdd(&a.ctl[k].delta[slot], s);
-        }
+    }
+    if (MODE == CM_APPLY_PCG && acc_k >= 0) {  // uniform per block
+        const double s = block_sum_t<T, CELL_BLOCK>(part, sh);
+        if (threadIdx.x == 0) atomicAdd(&a.ctl[acc_k].delta[acc_slot], s);
     }
 }
 
