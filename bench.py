@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--n", type=int, default=64, help="mesh edge (64 = the benchmark workload)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--pcg-rtol", type=float, default=1e-4, help="inner CG relative tolerance")
+    ap.add_argument("--apply-kernel", type=int, default=0, help="0 autotuned, 1 per-cell, 2 bricks")
+    ap.add_argument("--no-suite", action="store_true",
+                    help="skip the secondary measurements (batch c3, adjoint c2, 128^3 c4)")
     return ap.parse_args()
 
 
@@ -174,6 +178,94 @@ def aggregate(total_s_local: float, units_per_rank: int, steps: int, dist=None):
     return units_per_rank * steps * world / total_s / 1e6, total_s
 
 
+def suite(F, inputs, torch):
+    """Secondary measurements of the hot path (each timed once after one
+    untimed run): the 256-instance batched Neo-Hookean solve, the SIMP
+    compliance adjoint on 128x64x64 and the 128^3 Neo-Hookean solve with the
+    adjoint of the face-displacement objective."""
+    out = {}
+    opt = F.default_options(newton_rtol=1e-10)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, r
+
+    # c3: 256 instances of uneven size in one batched launch sequence
+    works = inputs.c3()
+    meshes = {}
+    insts = []
+    for w in works:
+        key = (w.nx, w.ny, w.nz)
+        if key not in meshes:
+            meshes[key] = F.fem_mesh(*key)
+        insts.append(F.Instance(meshes[key], F.material(w.kind, w.E, w.nu), torch.tensor(w.mask, device="cuda"),
+                                torch.tensor(w.u_bar, device="cuda"),
+                                torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda"), w.n_steps))
+
+    def run_batch():
+        for I in insts:
+            I.u.zero_()
+        return F.fem_solve_batched(insts, opt)
+
+    t, (rc, st) = timed(run_batch)
+    dofs = sum(w.n_dofs for w in works)
+    out["batch_c3"] = {"instances": len(works), "dofs": dofs, "time_s": t, "instances_per_s": len(works) / t,
+                       "mdof_per_s": dofs / t / 1e6, "status": rc,
+                       "cg_iters_max": max(x["pcg_iters"] for x in st), "apply_kernel": st[0]["apply_kernel"]}
+    del insts, meshes
+
+    # c2: SIMP compliance, forward + adjoint (self-adjoint: lambda = u)
+    w = inputs.c2()
+    m = F.fem_mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)
+    mat = F.material(w.kind, w.E, w.nu, w.simp_p, w.simp_emin)
+    mask, ubar = torch.tensor(w.mask, device="cuda"), torch.tensor(w.u_bar, device="cuda")
+    f = torch.tensor(w.point_load, device="cuda")
+    th = torch.tensor(w.cell_param, device="cuda")
+    u = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
+
+    def fwd():
+        u.zero_()
+        return F.fem_solve(m, mat, mask, ubar, u, f, th, 1, opt)
+
+    tf, stf = timed(fwd)
+    ta, (g, sta) = timed(lambda: F.fem_adjoint(m, mat, mask, u, f, th, options=opt))
+    out["adjoint_c2"] = {"dofs": w.n_dofs, "cells": w.n_cells, "forward_s": tf, "adjoint_s": ta,
+                         "compliance": float(f @ u), "grad_norm": float(torch.linalg.norm(g)),
+                         "forward_cg_iters": stf["pcg_iters"], "adjoint_cg_iters": sta["pcg_iters"],
+                         "status": [stf["status"], sta["status"]]}
+    del m, u, g
+
+    # c4: 128^3 Neo-Hookean, 5 load steps, face-displacement objective
+    w = inputs.c4()
+    m = F.fem_mesh(w.nx, w.ny, w.nz)
+    mat = F.material(w.kind, w.E, w.nu)
+    mask, ubar = torch.tensor(w.mask, device="cuda"), torch.tensor(w.u_bar, device="cuda")
+    sc = torch.tensor(w.cell_param, device="cuda")
+    u = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
+    nodes = torch.tensor(w.extra["face_nodes"], device="cuda")
+    target = torch.tensor(w.extra["target"], device="cuda")
+
+    def fwd4():
+        u.zero_()
+        return F.fem_solve(m, mat, mask, ubar, u, None, sc, w.n_steps, opt)
+
+    tf, stf = timed(fwd4)
+    dJ = torch.zeros_like(u).view(-1, 3)
+    dJ[nodes] = 2 * (u.view(-1, 3)[nodes] - target) / len(nodes)
+    dJ = dJ.view(-1).contiguous()
+    ta, (g, sta) = timed(lambda: F.fem_adjoint(m, mat, mask, u, dJ, sc, options=opt))
+    out["nh_c4"] = {"dofs": w.n_dofs, "cells": w.n_cells, "forward_s": tf, "adjoint_s": ta,
+                    "newton_iters": stf["newton_iters"], "cg_iters": stf["pcg_iters"],
+                    "adjoint_cg_iters": sta["pcg_iters"],
+                    "tangent_apply_gdofs": w.n_dofs / (stf["apply_ms"] / max(stf["apply_samples"], 1) / 1e3) / 1e9,
+                    "status": [stf["status"], sta["status"]]}
+    return out
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -200,7 +292,8 @@ def run_gb300(args):
     mask = torch.tensor(w.mask, device="cuda")
     ubar = torch.tensor(w.u_bar, device="cuda")
     u = torch.zeros(D, dtype=torch.float64, device="cuda")
-    opt = F.default_options(precision=F.FEM_MIXED, newton_rtol=1e-10)
+    opt = F.default_options(precision=F.FEM_MIXED, newton_rtol=1e-10, pcg_rtol=args.pcg_rtol,
+                            apply_kernel=args.apply_kernel)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -242,6 +335,7 @@ def run_gb300(args):
     apply_n = sum(s["apply_samples"] for s in stats)
     apply_launches = sum(s["apply_launches"] for s in stats) / len(stats)
     t_apply = apply_ms / max(apply_n, 1) / 1e3
+    t_update = sum(s["update_ms"] for s in stats) / max(sum(s["update_samples"] for s in stats), 1) / 1e3
     flops = NH_APPLY_FLOPS_PER_CELL * w.n_cells
     achieved = flops / t_apply / 1e12
     share = apply_launches * t_apply / (statistics.mean(step_ms) / 1e3)
@@ -249,7 +343,7 @@ def run_gb300(args):
     # all-FP64 GPU path on the same mesh, for the mixed-vs-FP64 comparison
     fp64 = None
     if not args.no_fp64:
-        o64 = F.default_options(precision=F.FEM_FP64, newton_rtol=1e-10)
+        o64 = F.default_options(precision=F.FEM_FP64, newton_rtol=1e-10, pcg_rtol=args.pcg_rtol)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st64 = solve_once(o64)
@@ -280,6 +374,9 @@ def run_gb300(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_t = statistics.median(e2e_ms) / 1e3
 
+    extra = None
+    if not args.no_suite:
+        extra = suite(F, inputs, torch)
     if rank != 0:
         return 0
     cpu = None
@@ -305,14 +402,17 @@ def run_gb300(args):
                 "d2h_bytes_per_step": int(D * 8)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu",
-                     "kernel": ("apply_brick<float,NH>" if st0.get("apply_kernel") == 2
-                                else "cell_kernel<float,NH,CM_APPLY_PCG>"),
+                     "kernel": {1: "cell_kernel<float,NH,CM_APPLY_PCG,3>", 2: "apply_brick<float,NH>",
+                                3: "cell_kernel<float,NH,CM_APPLY_PCG,4>"}.get(st0.get("apply_kernel"), "?"),
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
                      "launch_us": t_apply * 1e6, "launches_per_step": apply_launches,
-                     "time_share": share, "hbm_gbs_algorithmic": 12 * D / t_apply / 1e9},
+                     "time_share": share, "hbm_gbs_algorithmic": 12 * D / t_apply / 1e9,
+                     "cg_update_us": t_update * 1e6,
+                     "apply_share_of_cg_kernels": t_apply / (t_apply + t_update)},
         "cpu_baseline": cpu,
+        "suite": extra,
         "wall_s_timed": t_wall,
     }
     print(json.dumps(line), flush=True)

@@ -160,7 +160,8 @@ typedef struct {
                             checkpoint taken after step k) */
     int apply_kernel;    /* CG tangent-apply kernel: 0 = autotuned (timed once per problem shape and
                             cached), 1 = one thread per cell with a scatter per cell,
-                            2 = 8x4x4-cell bricks staged in shared memory */
+                            2 = 8x4x4-cell bricks staged in shared memory,
+                            3 = as 1 with a register budget for 4 CTAs per SM */
     int deterministic;   /* 1: colour-ordered scatter (bit-reproducible), 0: atomics */
     double timeout_s;    /* host watchdog for one solve (0 = none) */
 } fem_options;
@@ -176,7 +177,9 @@ typedef struct {
     double apply_ms;     /* summed device time of the sampled CG tangent-apply launches */
     int apply_samples;   /* number of sampled launches (the first apply of each CG graph) */
     int apply_launches;  /* CG tangent-apply launches that did work */
-    int apply_kernel;    /* CG apply kernel that ran (1 per-cell, 2 bricks) */
+    int apply_kernel;    /* CG apply kernel that ran (1 per-cell, 2 bricks, 3 per-cell 4 CTA/SM) */
+    double update_ms;    /* summed device time of the sampled CG vector-update launches */
+    int update_samples;  /* number of sampled update launches */
 } fem_stats;
 
 typedef struct {

@@ -51,8 +51,10 @@ __device__ __forceinline__ void scatter_add(T *p, T v, int plain)
     else atomicAdd(p, v);
 }
 
-template <typename T, int NH, int MODE>
-__global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? 3 : 1)) cell_kernel(const CellArgs<T> a)
+// MINB: CTAs per SM the FP32 instantiation is register-budgeted for (the
+// CG apply is also built for 4, autotuned against 3).
+template <typename T, int NH, int MODE, int MINB = 3>
+__global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1)) cell_kernel(const CellArgs<T> a)
 {
     __shared__ double sh[CELL_BLOCK / 32];
     // CG apply: p.Kp partials accumulate in registers over the tiles of one

@@ -56,6 +56,17 @@ static cudaError_t launch_one(const CellArgs<T> &a, cudaStream_t s)
 }
 
 template <typename T, int NH>
+static cudaError_t launch_one4(const CellArgs<T> &a, cudaStream_t s)
+{
+    auto f = cell_kernel<T, NH, CM_APPLY_PCG, 4>;
+    int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, 0));
+    if (g < 1) return cudaSuccess;
+    f<<<(int)g, CELL_BLOCK, 0, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, int NH>
 static cudaError_t launch_mode(int mode, const CellArgs<T> &a, cudaStream_t s)
 {
     switch (mode) {
@@ -90,6 +101,7 @@ static void warm_one()
     resident_grid((const void *)cell_kernel<T, NH, CM_VJP>, CELL_BLOCK, 0);
     resident_grid((const void *)cell_kernel<T, NH, CM_APPLY_LIFT>, CELL_BLOCK, 0);
     resident_grid((const void *)apply_brick<T, NH>, BRICK_X * BRICK_Y * BRICK_Z, 0);
+    resident_grid((const void *)cell_kernel<T, NH, CM_APPLY_PCG, 4>, CELL_BLOCK, 0);
 }
 
 void warm_occupancy(bool nh)
@@ -122,6 +134,16 @@ cudaError_t launch_apply_brick(bool nh, const CellArgs<T> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 template cudaError_t launch_apply_brick<float>(bool, const CellArgs<float> &, cudaStream_t);
+
+// CG apply, per-cell variant budgeted for 4 CTAs per SM.
+template <typename T>
+cudaError_t launch_apply_cell4(bool nh, const CellArgs<T> &a, cudaStream_t s)
+{
+    cudaError_t e = nh ? launch_one4<T, 1>(a, s) : launch_one4<T, 0>(a, s);
+    return e;
+}
+template cudaError_t launch_apply_cell4<float>(bool, const CellArgs<float> &, cudaStream_t);
+template cudaError_t launch_apply_cell4<double>(bool, const CellArgs<double> &, cudaStream_t);
 template cudaError_t launch_apply_brick<double>(bool, const CellArgs<double> &, cudaStream_t);
 
 template cudaError_t launch_cell<float>(int, bool, const CellArgs<float> &, cudaStream_t);

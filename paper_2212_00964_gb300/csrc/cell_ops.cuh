@@ -13,6 +13,9 @@ cudaError_t launch_cell(int mode, bool nh, const CellArgs<T> &a, cudaStream_t s)
 template <typename T>
 cudaError_t launch_apply_brick(bool nh, const CellArgs<T> &a, cudaStream_t s);
 
+template <typename T>
+cudaError_t launch_apply_cell4(bool nh, const CellArgs<T> &a, cudaStream_t s);
+
 int device_sms();
 void warm_occupancy(bool nh);
 int resident_grid(const void *func, int block, size_t smem);

@@ -296,7 +296,17 @@ __device__ __forceinline__ T det_ipH_m1(const T *H)
     return tr + (T)0.5 * (tr * tr - tr2) + dH;
 }
 
-__device__ __forceinline__ float rcbrt_t(float x) { return rcbrtf(x); }
+// J^{-1/3}.  FP32: 2^(-log2(J)/3) with the PTX approximate base-2 log and
+// exponential (relative error a few 1e-7 for J near 1, ample for the FP32
+// tangent and residual).  FP64: the library rcbrt.
+__device__ __forceinline__ float rcbrt_t(float x)
+{
+    float l, r;
+    asm("lg2.approx.f32 %0, %1;" : "=f"(l) : "f"(x));
+    l *= -(1.0f / 3.0f);
+    asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(l));
+    return r;
+}
 __device__ __forceinline__ double rcbrt_t(double x) { return rcbrt(x); }
 
 // Neo-Hookean kinematics at one Gauss point: A = F^{-T}, J, J-1, I1, G J^{-2/3}.

@@ -577,8 +577,12 @@ class Core {
                 return e;
             VecArgs<T> v = va_;
             v.iter = j;
+            if (j == 0 && ev_c_ && (e = cudaEventRecordWithFlags(ev_c_, s, cudaEventRecordExternal)) != cudaSuccess)
+                return e;
             k_pcg_update<T><<<gv, VEC_BLOCK, 0, s>>>(v);
             count_launch();
+            if (j == 0 && ev_d_ && (e = cudaEventRecordWithFlags(ev_d_, s, cudaEventRecordExternal)) != cudaSuccess)
+                return e;
         }
         k_chunk_ctl<<<gi, 128, 0, s>>>(b_.ctl, ni, prm_.chunk, prm_.pcg_maxit, b_.counter);
         count_launch();
@@ -605,6 +609,7 @@ class Core {
             return launch_apply_brick<T>(pb_.nh, ca, s);
         }
         ca.n_tiles = pb_.n_tiles;
+        if (variant_ == 3) return launch_apply_cell4<T>(pb_.nh, ca, s);
         return launch_cell<T>(CM_APPLY_PCG, pb_.nh, ca, s);
     }
 
@@ -648,9 +653,9 @@ class Core {
             cudaEventDestroy(e0);
             return (cudaGetLastError(), 2);
         }
-        float best = 1e30f, times[2] = {-1.f, -1.f};
+        float best = 1e30f, times[3] = {-1.f, -1.f, -1.f};
         int choice = 2;
-        for (int v = 1; v <= 2; ++v) {
+        for (int v = 1; v <= 3; ++v) {
             variant_ = v;
             bool ok = launch_apply(ca, s) == cudaSuccess;
             ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
@@ -670,8 +675,10 @@ class Core {
         cudaEventDestroy(e1);
         if (const char *env = getenv("FEMGB_TUNE_LOG")) {
             if (env[0] == '1')
-                fprintf(stderr, "femgb autotune: D=%lld instances=%d per-cell %.3f ms, bricks %.3f ms -> %d\n",
-                        (long long)pb_.D, (int)pb_.desc.size(), times[0] / 3, times[1] / 3, choice);
+                fprintf(stderr,
+                        "femgb autotune: D=%lld instances=%d per-cell %.3f ms, bricks %.3f ms, "
+                        "per-cell(4 CTA/SM) %.3f ms -> %d\n",
+                        (long long)pb_.D, (int)pb_.desc.size(), times[0] / 3, times[1] / 3, times[2] / 3, choice);
         }
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = choice;
@@ -751,20 +758,26 @@ class Core {
     int run(cudaStream_t s, double timeout_s)
     {
         Graphs G;
-        struct EvPair {
-            cudaEvent_t a = nullptr, b = nullptr;
-            ~EvPair()
+        struct EvSet {
+            cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+            ~EvSet()
             {
-                if (a) cudaEventDestroy(a);
-                if (b) cudaEventDestroy(b);
+                for (auto x : e)
+                    if (x) cudaEventDestroy(x);
             }
         } ev;
-        if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) {
-            cudaGetLastError();
-            ev.a = ev.b = nullptr;
+        for (auto &x : ev.e) {
+            if (cudaEventCreate(&x) != cudaSuccess) {
+                cudaGetLastError();
+                x = nullptr;
+            }
         }
-        ev_a_ = ev.a;
-        ev_b_ = ev.b;
+        if (ev.e[0] && ev.e[1] && ev.e[2] && ev.e[3]) {
+            ev_a_ = ev.e[0];
+            ev_b_ = ev.e[1];
+            ev_c_ = ev.e[2];
+            ev_d_ = ev.e[3];
+        }
         warm_occupancy(pb_.nh);
         if (variant_ == 0) variant_ = autotune(s);
         FEM_CUDA(capture(s, 0, &G.head, &G.n_head));
@@ -788,10 +801,13 @@ class Core {
                     count_launch(G.n_chunk);
                     FEM_CUDA(cudaStreamSynchronize(s));
                     if (ev_a_) {
-                        float ms = 0;
-                        if (cudaEventElapsedTime(&ms, ev_a_, ev_b_) == cudaSuccess) {
+                        float ms = 0, ms2 = 0;
+                        if (cudaEventElapsedTime(&ms, ev_a_, ev_b_) == cudaSuccess &&
+                            cudaEventElapsedTime(&ms2, ev_c_, ev_d_) == cudaSuccess) {
                             apply_ms_ += ms;
                             apply_samples_++;
+                            update_ms_ += ms2;
+                            update_samples_++;
                         } else {
                             cudaGetLastError();
                         }
@@ -812,10 +828,12 @@ class Core {
 
     const double *ustar64_ = nullptr;  // linear mode: the fixed state
     int max_steps_ = 1;
-    int variant_ = 0;       // CG apply kernel: 0 autotune, 1 per-cell, 2 bricks
+    int variant_ = 0;       // CG apply kernel: 0 autotune, 1 per-cell, 2 bricks, 3 per-cell at 4 CTA/SM
     double apply_ms_ = 0;   // sampled device time of CG applies
     int apply_samples_ = 0;
-    cudaEvent_t ev_a_ = nullptr, ev_b_ = nullptr;
+    double update_ms_ = 0;  // sampled device time of CG vector updates
+    int update_samples_ = 0;
+    cudaEvent_t ev_a_ = nullptr, ev_b_ = nullptr, ev_c_ = nullptr, ev_d_ = nullptr;
 
   private:
     const Problem &pb_;
@@ -857,7 +875,7 @@ static int check_options(const fem_options &o)
         return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
     if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
         !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
-        o.apply_kernel < 0 || o.apply_kernel > 2)
+        o.apply_kernel < 0 || o.apply_kernel > 3)
         return (set_error("invalid solver options"), FEM_ERR_ARG);
     return FEM_OK;
 }
@@ -934,6 +952,8 @@ struct ApplyTiming {
     double ms = 0;
     int samples = 0;
     int variant = 0;
+    double upd_ms = 0;
+    int upd_samples = 0;
 };
 
 static void fill_stats(const Ctl &c, fem_stats *st, double ms, const ApplyTiming &at = ApplyTiming())
@@ -943,6 +963,8 @@ static void fill_stats(const Ctl &c, fem_stats *st, double ms, const ApplyTiming
     st->apply_samples = at.samples;
     st->apply_launches = c.pcg_total;
     st->apply_kernel = at.variant;
+    st->update_ms = at.upd_ms;
+    st->update_samples = at.upd_samples;
     st->status = c.status == 1 ? FEM_OK : (c.status == 0 ? FEM_ERR_NOT_CONVERGED : c.status);
     st->load_steps = c.steps_done;
     st->newton_iters = c.newton_total;
@@ -993,6 +1015,8 @@ static int solve_batch(Workspace &ws, Problem &pb, double *u64, const uint8_t *m
     at.ms = core.apply_ms_;
     at.samples = core.apply_samples_;
     at.variant = core.variant_;
+    at.upd_ms = core.update_ms_;
+    at.upd_samples = core.update_samples_;
     ctl_out.resize(ctl.size());
     cudaError_t e = cudaMemcpyAsync(ctl_out.data(), b.ctl, sizeof(Ctl) * ctl.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -51,7 +51,7 @@ class fem_stats(ctypes.Structure):
                 ("pcg_iters", ctypes.c_int), ("ref_rnorm", ctypes.c_double),
                 ("final_rnorm", ctypes.c_double), ("time_ms", ctypes.c_double),
                 ("apply_ms", ctypes.c_double), ("apply_samples", ctypes.c_int), ("apply_launches", ctypes.c_int),
-                ("apply_kernel", ctypes.c_int)]
+                ("apply_kernel", ctypes.c_int), ("update_ms", ctypes.c_double), ("update_samples", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
