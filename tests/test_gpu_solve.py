@@ -71,7 +71,7 @@ def test_c0_linear_elastic_mixed_refined():
     assert rel_l2(u, ref) <= TOL_REFINED
 
 
-@pytest.mark.parametrize("apply_kernel", [1, 2])
+@pytest.mark.parametrize("apply_kernel", [1, 2, 3])
 @pytest.mark.parametrize("n", [4, 8, 9])
 def test_neohooke_load_steps(n, apply_kernel):
     """Both CG apply kernels (per-cell scatter, 8x4x4 bricks); 9^3 leaves
@@ -98,7 +98,7 @@ def test_neohooke_noncubic_with_stiffness_field():
     assert rel_l2(u, ref) <= TOL_REFINED
 
 
-@pytest.mark.parametrize("apply_kernel", [1, 2])
+@pytest.mark.parametrize("apply_kernel", [1, 2, 3])
 def test_simp_cantilever_small(apply_kernel):
     w = inputs.c2(nx=16, ny=8, nz=8)
     ref = oracle_solve(w)
