@@ -37,6 +37,7 @@ struct CellArgs {
     Ctl *ctl;               // control blocks (gated modes)
     int iter;               // CG iteration inside the current graph chunk
     int pcg_maxit;          // CG iteration cap (CG apply)
+    int *arrive;            // arrival counter of the CG apply (last-block epilogue)
     T *g;                   // VJP output [Ne]
     int *jflag;             // det F <= 0 flag (ungated residual)
     const int32_t *cells;   // explicit cell list (colour-ordered launch) or nullptr
@@ -79,25 +80,15 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1)) cell_
                 part = 0;
                 acc_k = -1;
             }
-            // every warp takes the same CG decision (lane 0, FP64 scalars)
-            Ctl &c = a.ctl[k];
-            const int it = c.pcg_base + a.iter;
-            int go = 0;
+            // the previous kernel decided whether this CG iteration runs
+            int go = 0, base = 0;
             if ((threadIdx.x & 31) == 0) {
-                go = c.status == 0 && c.solving && !c.pcg_done && !cg_converged(c, it, a.pcg_maxit);
-                if (threadIdx.x == 0 && tile == d.tile_off) {
-                    if (go) {
-                        c.gamma[(it + 1) & 3] = 0;
-                        c.rr[(it + 1) & 3] = 0;
-                    } else if (c.status == 0 && c.solving && !c.pcg_done) {
-                        c.pcg_done = 1;
-                        c.pcg_last = it;
-                    }
-                }
+                go = a.ctl[k].go;
+                base = a.ctl[k].pcg_base;
             }
             go = __shfl_sync(0xffffffffu, go, 0);
-            if (!go) continue;
-            slot = it & 3;
+            if (!go) continue;  // uniform per block
+            slot = (__shfl_sync(0xffffffffu, base, 0) + a.iter) & 3;
             acc_k = k;
             acc_slot = slot;
         } else if (MODE == CM_RESIDUAL_CTL || MODE == CM_APPLY_CTL) {
@@ -290,9 +281,12 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1)) cell_
             }
         }
     }
-    if (MODE == CM_APPLY_PCG && acc_k >= 0) {  // uniform per block
-        const double s = block_sum_t<T, CELL_BLOCK>(part, sh);
-        if (threadIdx.x == 0) atomicAdd(&a.ctl[acc_k].delta[acc_slot], s);
+    if (MODE == CM_APPLY_PCG) {
+        if (acc_k >= 0) {  // uniform per block
+            const double s = block_sum_t<T, CELL_BLOCK>(part, sh);
+            if (threadIdx.x == 0) atomicAdd(&a.ctl[acc_k].delta[acc_slot], s);
+        }
+        if (last_block(a.arrive)) cg_after_apply(a.ctl, a.tab ? a.n_inst : 1, a.iter);
     }
 }
 
@@ -325,29 +319,9 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
         } else {
             d = a.d0;
         }
-        Ctl &cc = a.ctl[k];
-        const int it = cc.pcg_base + a.iter;
-        __shared__ int s_go;
-        if (tid == 0) {
-            int go = cc.status == 0 && cc.solving && !cc.pcg_done;
-            if (go && cg_converged(cc, it, a.pcg_maxit)) {
-                go = 0;
-                if (brick == d.brick_off) {
-                    cc.pcg_done = 1;
-                    cc.pcg_last = it;
-                }
-            }
-            if (go && brick == d.brick_off) {
-                cc.gamma[(it + 1) & 3] = 0;
-                cc.rr[(it + 1) & 3] = 0;
-            }
-            s_go = go;
-        }
-        __syncthreads();
-        const int go = s_go;
-        __syncthreads();
-        if (!go) continue;
-        const int slot = it & 3;
+        const Ctl &cc = a.ctl[k];
+        if (!cc.go) continue;  // decided by the previous kernel; uniform per CTA
+        const int slot = (cc.pcg_base + a.iter) & 3;
         const int nx = d.nx, ny = d.ny, nz = d.nz;
         const int tnx = (nx + BRICK_X - 1) / BRICK_X, tny = (ny + BRICK_Y - 1) / BRICK_Y;
         const int lb = (int)(brick - d.brick_off);
@@ -464,6 +438,7 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
         if (tid == 0) atomicAdd(&a.ctl[k].delta[slot], s);
         __syncthreads();  // shared arrays are reused by the next brick
     }
+    if (last_block(a.arrive)) cg_after_apply(a.ctl, a.tab ? a.n_inst : 1, a.iter);
 }
 
 // CSR assembly (Algorithm 1): one thread per (cell, column).  The column

@@ -106,14 +106,101 @@ struct Ctl {
     // CG in the single-reduction (Chronopoulos-Gear) form, iteration i:
     // gamma_i = (r_i, z_i), delta_i = (A z_i, z_i), rr_i = (r_i, r_i), alpha_i
     double gamma[4], delta[4], rr[4], alpha[4];
+    // Decisions handed from one CG kernel to the next (written by the last
+    // block of the previous kernel, so no kernel repeats FP64 scalar work):
+    int go;              // the next CG iteration runs
+    int pad2_;
+    double a_d, b_d;     // alpha_i, beta_i for the vector update
+    float a_f, b_f;
 };
 
-// CG iteration `it` of an instance is not run when the relative residual
-// reached eta, the iteration cap is hit or the right-hand side is zero.
-__device__ __forceinline__ bool cg_converged(const Ctl &c, int it, int pcg_maxit)
+// Last-block arrival: every block of the grid calls this once, after its
+// global reductions; it returns true in all threads of the block that
+// arrives last, which then sees every other block's writes.  The counter is
+// reset by that block for the next kernel.
+__device__ __forceinline__ bool last_block(int *arrive)
 {
-    const double rr = c.rr[it & 3];
-    return c.rr0 == 0.0 || rr <= c.eta * c.eta * c.rr0 || it >= pcg_maxit;
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int t = atomicAdd(arrive, 1);
+        s_last = (t == (int)gridDim.x - 1);
+        if (s_last) {
+            __threadfence();
+            *arrive = 0;
+        }
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+
+// After the CG apply of iteration `iter` (relative to each instance's chunk
+// base): alpha_i, beta_i from the reduced scalars, or the breakdown status.
+// Run by the last block; one thread per instance; L2-coherent loads.
+static __device__ __noinline__ void cg_after_apply(Ctl *ctl, int n_inst, int iter)
+{
+    for (int k = threadIdx.x; k < n_inst; k += blockDim.x) {
+        Ctl &c = ctl[k];
+        if (!__ldcg(&c.go)) continue;
+        const int it = __ldcg(&c.pcg_base) + iter;
+        const int s0 = it & 3, sm = (it + 3) & 3;
+        const double g = __ldcg(&c.gamma[s0]);
+        double beta = 0.0, den = __ldcg(&c.delta[s0]);
+        if (it > 0) {
+            beta = g / __ldcg(&c.gamma[sm]);
+            den -= beta * g / __ldcg(&c.alpha[sm]);
+        }
+        if (!isfinite(den) || !isfinite(g)) {
+            c.status = FEM_ERR_NONFINITE;
+            c.pcg_done = 1;
+            c.pcg_last = it;
+            c.go = 0;
+            continue;
+        }
+        if (!(den > 0.0)) {
+            // p^T K p <= 0: negative curvature.  Keep the iterate so far
+            // (truncated CG); with no iterate yet the tangent is unusable.
+            if (it == 0) c.status = FEM_ERR_BREAKDOWN;
+            c.pcg_done = 1;
+            c.pcg_last = it;
+            c.go = 0;
+            continue;
+        }
+        const double alpha = g / den;
+        c.alpha[s0] = alpha;
+        c.a_d = alpha;
+        c.b_d = beta;
+        c.a_f = (float)alpha;
+        c.b_f = (float)beta;
+        c.delta[(it + 1) & 3] = 0;
+    }
+}
+
+// After the CG update of iteration `iter`: does iteration it+1 run?  It does
+// not when the relative residual reached eta or the iteration cap is hit.
+static __device__ __noinline__ void cg_after_update(Ctl *ctl, int n_inst, int iter, int pcg_maxit)
+{
+    for (int k = threadIdx.x; k < n_inst; k += blockDim.x) {
+        Ctl &c = ctl[k];
+        if (!__ldcg(&c.go)) continue;
+        const int nxt = __ldcg(&c.pcg_base) + iter + 1;
+        const double rr = __ldcg(&c.rr[nxt & 3]);
+        const double eta = __ldcg(&c.eta), rr0 = __ldcg(&c.rr0);
+        if (!isfinite(rr)) {
+            c.status = FEM_ERR_NONFINITE;
+            c.pcg_done = 1;
+            c.pcg_last = nxt;
+            c.go = 0;
+        } else if (rr <= eta * eta * rr0 || nxt >= pcg_maxit) {
+            c.pcg_done = 1;
+            c.pcg_last = nxt;
+            c.go = 0;
+        } else {
+            c.gamma[(nxt + 1) & 3] = 0;
+            c.rr[(nxt + 1) & 3] = 0;
+        }
+    }
 }
 
 // ----------------------------------------------------------- launch count --
@@ -205,6 +292,30 @@ __device__ __forceinline__ double block_sum_f(float v, double *sh)
         for (int i = 0; i < NT / 32; ++i) s += sh[i];
     }
     return s;
+}
+
+// Two block-wide sums with one pair of barriers (FP32 warp stage, FP64 across
+// warps); results valid in thread 0.
+template <int NT>
+__device__ __forceinline__ void block_sum2_f(float a, float b, double *sh, double &ra, double &rb)
+{
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) {
+        sh[2 * w] = (double)a;
+        sh[2 * w + 1] = (double)b;
+    }
+    __syncthreads();
+    ra = rb = 0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NT / 32; ++i) {
+            ra += sh[2 * i];
+            rb += sh[2 * i + 1];
+        }
+    }
 }
 
 template <typename T, int NT>

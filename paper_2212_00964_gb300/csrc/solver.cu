@@ -58,6 +58,7 @@ struct VecArgs {
     int iter;
     SolverParams prm;
     int *counter;       // [0] solving, [1] iterating, [2] active
+    int *arrive;        // last-block arrival counter of the CG kernels
 };
 
 #define VEC_ITEMS_BEGIN                                                       \
@@ -187,6 +188,7 @@ __global__ void k_control(Ctl *ctl, int n_inst, SolverParams prm, int *counter)
     c.pcg_last = 0;
     c.rr0 = 0;
     c.eta = prm.eta;
+    c.go = 0;
     for (int s = 0; s < 4; ++s) c.gamma[s] = c.delta[s] = c.rr[s] = c.alpha[s] = 0;
     atomicAdd(&counter[0], 1);
 }
@@ -219,6 +221,20 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_init(const VecArgs<T> a)
         atomicAdd(&c.rr0, s2);
     }
     VEC_ITEMS_END
+    // last block: CG iteration 0 runs unless the right-hand side is zero
+    if (last_block(a.arrive)) {
+        for (int k = threadIdx.x; k < a.n_inst; k += blockDim.x) {
+            Ctl &c = a.ctl[k];
+            if (__ldcg(&c.status) != 0 || !__ldcg(&c.solving)) continue;
+            if (__ldcg(&c.rr0) > 0.0 && a.prm.pcg_maxit > 0) {
+                c.go = 1;
+            } else {
+                c.go = 0;
+                c.pcg_done = 1;
+                c.pcg_last = 0;
+            }
+        }
+    }
 }
 
 // CG iteration `it` after the tangent apply w = K z_it (w lives in q and
@@ -231,55 +247,12 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_init(const VecArgs<T> a)
 template <typename T>
 __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_update(const VecArgs<T> a)
 {
-    __shared__ double sh[VEC_BLOCK / 32];
-    __shared__ double s_ab[2];
-    __shared__ int s_go;
+    __shared__ double sh[2 * (VEC_BLOCK / 32)];
     VEC_ITEMS_BEGIN
+    if (!c.go) continue;  // alpha, beta and go come from the apply's last block
     const int it = c.pcg_base + a.iter;
-    // thread 0 takes the scalar decisions in FP64 and broadcasts them
-    if (threadIdx.x == 0) {
-        int go = c.status == 0 && c.solving && !c.pcg_done && !cg_converged(c, it, a.prm.pcg_maxit);
-        if (go) {
-            const bool lead = item == d.vec_off;
-            const int s0 = it & 3, sm = (it + 3) & 3, sn = (it + 1) & 3;
-            const double g = c.gamma[s0];
-            double beta = 0.0, den = c.delta[s0];
-            if (it > 0) {
-                beta = g / c.gamma[sm];
-                den = den - beta * g / c.alpha[sm];
-            }
-            if (!isfinite(den) || !isfinite(g)) {
-                if (lead) {
-                    c.status = FEM_ERR_NONFINITE;
-                    c.pcg_done = 1;
-                    c.pcg_last = it;
-                }
-                go = 0;
-            } else if (!(den > 0.0)) {
-                // p^T K p <= 0: negative curvature.  Keep the iterate so far
-                // (truncated CG); with no iterate yet the tangent is unusable.
-                if (lead) {
-                    if (it == 0) c.status = FEM_ERR_BREAKDOWN;
-                    c.pcg_done = 1;
-                    c.pcg_last = it;
-                }
-                go = 0;
-            } else {
-                s_ab[0] = g / den;
-                s_ab[1] = beta;
-                if (lead) {
-                    c.alpha[s0] = g / den;
-                    c.delta[sn] = 0;
-                }
-            }
-        }
-        s_go = go;
-    }
-    __syncthreads();
-    const int go = s_go;
-    const T al = (T)s_ab[0], be = (T)s_ab[1];
-    __syncthreads();
-    if (!go) continue;
+    const T al = sizeof(T) == 4 ? (T)c.a_f : (T)c.a_d;
+    const T be = sizeof(T) == 4 ? (T)c.b_f : (T)c.b_d;
     const bool first = it == 0;
     T ag = 0, arr = 0;
     const int64_t bd = blockDim.x;
@@ -320,11 +293,19 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_update(const VecArgs<T> a)
             }
         }
     }
-    const double s1 = block_sum_t<T, VEC_BLOCK>(ag, sh);
-    if (threadIdx.x == 0) atomicAdd(&c.gamma[(it + 1) & 3], s1);
-    const double s2 = block_sum_t<T, VEC_BLOCK>(arr, sh);
-    if (threadIdx.x == 0) atomicAdd(&c.rr[(it + 1) & 3], s2);
+    double s1, s2;
+    if (sizeof(T) == 4) {
+        block_sum2_f<VEC_BLOCK>((float)ag, (float)arr, sh, s1, s2);
+    } else {
+        s1 = block_sum<double, VEC_BLOCK>((double)ag, sh);
+        s2 = block_sum<double, VEC_BLOCK>((double)arr, sh);
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&c.gamma[(it + 1) & 3], s1);
+        atomicAdd(&c.rr[(it + 1) & 3], s2);
+    }
     VEC_ITEMS_END
+    if (last_block(a.arrive)) cg_after_update(a.ctl, a.n_inst, a.iter, a.prm.pcg_maxit);
 }
 
 // End of a graph chunk: instances whose next iteration would not run are
@@ -335,15 +316,10 @@ __global__ void k_chunk_ctl(Ctl *ctl, int n_inst, int chunk, int pcg_maxit, int 
     if (k >= n_inst) return;
     Ctl &c = ctl[k];
     if (c.status == 0 && c.solving && !c.pcg_done) {
-        const int nxt = c.pcg_base + chunk;
-        if (cg_converged(c, nxt, pcg_maxit)) {
-            c.pcg_done = 1;
-            c.pcg_last = nxt;
-        } else {
-            c.pcg_base = nxt;
-            atomicAdd(&counter[1], 1);
-        }
+        c.pcg_base += chunk;  // `go` already refers to the next iteration
+        atomicAdd(&counter[1], 1);
     }
+    (void)pcg_maxit;
 }
 
 template <typename T>
@@ -485,6 +461,7 @@ class Core {
         va_.x = b.x; va_.r = b.r; va_.z = b.z; va_.p = b.p; va_.q = b.q; va_.dg = b.dg; va_.s = b.s;
         va_.prm = prm;
         va_.counter = b.counter;
+        va_.arrive = b.counter + 3;
     }
 
     cudaError_t enqueue_head(cudaStream_t s)
@@ -568,6 +545,7 @@ class Core {
         ca.x = b_.z;
         ca.y = b_.q;
         ca.pcg_maxit = prm_.pcg_maxit;
+        ca.arrive = b_.counter + 3;
         for (int j = 0; j < prm_.chunk; ++j) {
             ca.iter = j;
             if (j == 0 && ev_a_ && (e = cudaEventRecordWithFlags(ev_a_, s, cudaEventRecordExternal)) != cudaSuccess)
@@ -631,11 +609,13 @@ class Core {
         for (auto &c : tc) {
             c = Ctl{};
             c.solving = 1;
+            c.go = 1;
             c.eta = 0.5;
             c.rr0 = 1.0;
             for (int q = 0; q < 4; ++q) c.rr[q] = 1.0;
         }
-        if (cudaMemcpyAsync(b_.tune, tc.data(), sizeof(Ctl) * tc.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        if (cudaMemcpyAsync(b_.tune, tc.data(), sizeof(Ctl) * tc.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(b_.counter + 3, 0, sizeof(int), s) != cudaSuccess)
             return (cudaGetLastError(), 2);
         CellArgs<T> ca{};
         ca.d0 = pb_.desc[0];
@@ -647,6 +627,7 @@ class Core {
         ca.x = b_.uT;
         ca.y = b_.q;
         ca.pcg_maxit = 1 << 30;
+        ca.arrive = b_.counter + 3;
         cudaEvent_t e0, e1;
         if (cudaEventCreate(&e0) != cudaSuccess) return (cudaGetLastError(), 2);
         if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -998,6 +979,7 @@ static int solve_batch(Workspace &ws, Problem &pb, double *u64, const uint8_t *m
     }
     std::vector<Ctl> ctl = initial_ctl(pb, o.step_begin, false);
     FEM_CUDA(cudaMemcpyAsync(b.ctl, ctl.data(), sizeof(Ctl) * ctl.size(), cudaMemcpyHostToDevice, s));
+    FEM_CUDA(cudaMemsetAsync(b.counter, 0, 4 * sizeof(int), s));
     if (b.tab) FEM_CUDA(cudaMemcpyAsync(b.tab, pb.desc.data(), sizeof(InstDesc) * pb.desc.size(), cudaMemcpyHostToDevice, s));
     if (sepT) {
         k_convert<T><<<vec_grid(pb.n_items), 256, 0, s>>>(b.uT, u64, pb.D);
@@ -1057,6 +1039,7 @@ static int adjoint_batch(Workspace &ws, Problem &pb, const double *ustar, const 
     FEM_CUDA(cudaMemsetAsync(lam, 0, sizeof(double) * pb.D, s));
     std::vector<Ctl> ctl = initial_ctl(pb, 1, true);
     FEM_CUDA(cudaMemcpyAsync(b.ctl, ctl.data(), sizeof(Ctl) * ctl.size(), cudaMemcpyHostToDevice, s));
+    FEM_CUDA(cudaMemsetAsync(b.counter, 0, 4 * sizeof(int), s));
     SolverParams prm = params_from(o);
     Core<T> core(pb, b, SM_LINEAR, prm, hc);
     core.ustar64_ = ustar;
@@ -1152,6 +1135,7 @@ static int solve_region_t(const InstDesc &d, int n_steps, const fem_bc &bc, cons
     c0.need_bc = 1;
     c0.r_ref = -1.0;
     FEM_CUDA(cudaMemcpyAsync(b.ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    FEM_CUDA(cudaMemsetAsync(b.counter, 0, 4 * sizeof(int), s));
     int hc[4] = {0, 0, 0, 0};
     Core<T> core(pb, b, SM_NONLINEAR, params_from(o), hc);
     core.max_steps_ = n_steps;
