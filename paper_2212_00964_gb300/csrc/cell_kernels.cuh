@@ -54,8 +54,11 @@ __device__ __forceinline__ void scatter_add(T *p, T v, int plain)
 
 // MINB: CTAs per SM the FP32 instantiation is register-budgeted for (the
 // CG apply is also built for 4, autotuned against 3).
-template <typename T, int NH, int MODE, int MINB = 3>
-__global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1)) cell_kernel(const CellArgs<T> a)
+// BATCHED = false: one instance whose descriptor is read in place from the
+// kernel parameter (no register copy held across the tile loop).
+template <typename T, int NH, int MODE, int MINB = 3, bool BATCHED = true>
+__global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
+    cell_kernel(const __grid_constant__ CellArgs<T> a)
 {
     __shared__ double sh[CELL_BLOCK / 32];
     // CG apply: p.Kp partials accumulate in registers over the tiles of one
@@ -65,13 +68,14 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1)) cell_
     int acc_k = -1, acc_slot = 0;
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
         int k = 0;
-        InstDesc d;
-        if (a.tab) {
+        InstDesc dcopy;
+        const InstDesc *dp = &a.d0;
+        if (BATCHED && a.tab) {
             k = find_inst(a.tab, a.n_inst, tile, true);
-            d = a.tab[k];
-        } else {
-            d = a.d0;
+            dcopy = a.tab[k];
+            dp = &dcopy;
         }
+        const InstDesc &d = *dp;
         int slot = 0;
         if (MODE == CM_APPLY_PCG) {
             if (acc_k >= 0 && k != acc_k) {  // uniform per block

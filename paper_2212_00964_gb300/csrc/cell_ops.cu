@@ -47,7 +47,7 @@ int resident_grid(const void *func, int block, size_t smem)
 template <typename T, int NH, int MODE>
 static cudaError_t launch_one(const CellArgs<T> &a, cudaStream_t s)
 {
-    auto f = cell_kernel<T, NH, MODE>;
+    auto f = a.tab ? cell_kernel<T, NH, MODE, 3, true> : cell_kernel<T, NH, MODE, 3, false>;
     int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, 0));
     if (g < 1) return cudaSuccess;
     f<<<(int)g, CELL_BLOCK, 0, s>>>(a);
@@ -58,7 +58,7 @@ static cudaError_t launch_one(const CellArgs<T> &a, cudaStream_t s)
 template <typename T, int NH>
 static cudaError_t launch_one4(const CellArgs<T> &a, cudaStream_t s)
 {
-    auto f = cell_kernel<T, NH, CM_APPLY_PCG, 4>;
+    auto f = a.tab ? cell_kernel<T, NH, CM_APPLY_PCG, 4, true> : cell_kernel<T, NH, CM_APPLY_PCG, 4, false>;
     int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, 0));
     if (g < 1) return cudaSuccess;
     f<<<(int)g, CELL_BLOCK, 0, s>>>(a);
@@ -94,14 +94,23 @@ cudaError_t launch_cell(int mode, bool nh, const CellArgs<T> &a, cudaStream_t s)
 template <typename T, int NH>
 static void warm_one()
 {
-    resident_grid((const void *)cell_kernel<T, NH, CM_RESIDUAL_CTL>, CELL_BLOCK, 0);
-    resident_grid((const void *)cell_kernel<T, NH, CM_APPLY_CTL>, CELL_BLOCK, 0);
-    resident_grid((const void *)cell_kernel<T, NH, CM_DIAG_CTL>, CELL_BLOCK, 0);
-    resident_grid((const void *)cell_kernel<T, NH, CM_APPLY_PCG>, CELL_BLOCK, 0);
-    resident_grid((const void *)cell_kernel<T, NH, CM_VJP>, CELL_BLOCK, 0);
-    resident_grid((const void *)cell_kernel<T, NH, CM_APPLY_LIFT>, CELL_BLOCK, 0);
+    for (int b = 0; b < 2; ++b) {
+        resident_grid((const void *)(b ? cell_kernel<T, NH, CM_RESIDUAL_CTL, 3, true>
+                                       : cell_kernel<T, NH, CM_RESIDUAL_CTL, 3, false>), CELL_BLOCK, 0);
+        resident_grid((const void *)(b ? cell_kernel<T, NH, CM_APPLY_CTL, 3, true>
+                                       : cell_kernel<T, NH, CM_APPLY_CTL, 3, false>), CELL_BLOCK, 0);
+        resident_grid((const void *)(b ? cell_kernel<T, NH, CM_DIAG_CTL, 3, true>
+                                       : cell_kernel<T, NH, CM_DIAG_CTL, 3, false>), CELL_BLOCK, 0);
+        resident_grid((const void *)(b ? cell_kernel<T, NH, CM_APPLY_PCG, 3, true>
+                                       : cell_kernel<T, NH, CM_APPLY_PCG, 3, false>), CELL_BLOCK, 0);
+        resident_grid((const void *)(b ? cell_kernel<T, NH, CM_VJP, 3, true>
+                                       : cell_kernel<T, NH, CM_VJP, 3, false>), CELL_BLOCK, 0);
+        resident_grid((const void *)(b ? cell_kernel<T, NH, CM_APPLY_LIFT, 3, true>
+                                       : cell_kernel<T, NH, CM_APPLY_LIFT, 3, false>), CELL_BLOCK, 0);
+        resident_grid((const void *)(b ? cell_kernel<T, NH, CM_APPLY_PCG, 4, true>
+                                       : cell_kernel<T, NH, CM_APPLY_PCG, 4, false>), CELL_BLOCK, 0);
+    }
     resident_grid((const void *)apply_brick<T, NH>, BRICK_X * BRICK_Y * BRICK_Z, 0);
-    resident_grid((const void *)cell_kernel<T, NH, CM_APPLY_PCG, 4>, CELL_BLOCK, 0);
 }
 
 void warm_occupancy(bool nh)

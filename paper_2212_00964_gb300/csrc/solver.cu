@@ -362,6 +362,13 @@ __global__ void k_convert(T *dst, const double *src, int64_t n)
         dst[i] = (T)src[i];
 }
 
+template <typename T>
+__global__ void k_fill(T *y, T v, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = v;
+}
+
 __global__ void k_add(double *y, const double *x, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -617,6 +624,9 @@ class Core {
         if (cudaMemcpyAsync(b_.tune, tc.data(), sizeof(Ctl) * tc.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(b_.counter + 3, 0, sizeof(int), s) != cudaSuccess)
             return (cudaGetLastError(), 2);
+        // a nonzero probe direction (p^T K p > 0 keeps every probe launch iterating)
+        k_fill<T><<<vec_grid(pb_.n_items), 256, 0, s>>>(b_.p, (T)1, pb_.D);
+        count_launch();
         CellArgs<T> ca{};
         ca.d0 = pb_.desc[0];
         ca.tab = va_.tab;
@@ -624,7 +634,7 @@ class Core {
         ca.ctl = b_.tune;
         ca.cell_param = b_.cpT;
         ca.u = b_.uT;
-        ca.x = b_.uT;
+        ca.x = b_.p;
         ca.y = b_.q;
         ca.pcg_maxit = 1 << 30;
         ca.arrive = b_.counter + 3;
