@@ -362,11 +362,18 @@ __global__ void k_convert(T *dst, const double *src, int64_t n)
         dst[i] = (T)src[i];
 }
 
+// Deterministic pseudo-random values in [-0.5, 0.5) (a probe direction
+// that is not a rigid-body mode, so p^T K p > 0).
 template <typename T>
-__global__ void k_fill(T *y, T v, int64_t n)
+__global__ void k_fill_hash(T *y, int64_t n)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = v;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t h = (uint32_t)i * 2654435761u;
+        h ^= h >> 15;
+        h *= 2246822519u;
+        h ^= h >> 13;
+        y[i] = (T)((double)(h >> 8) * (1.0 / 16777216.0) - 0.5);
+    }
 }
 
 __global__ void k_add(double *y, const double *x, int64_t n)
@@ -624,8 +631,9 @@ class Core {
         if (cudaMemcpyAsync(b_.tune, tc.data(), sizeof(Ctl) * tc.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(b_.counter + 3, 0, sizeof(int), s) != cudaSuccess)
             return (cudaGetLastError(), 2);
-        // a nonzero probe direction (p^T K p > 0 keeps every probe launch iterating)
-        k_fill<T><<<vec_grid(pb_.n_items), 256, 0, s>>>(b_.p, (T)1, pb_.D);
+        // a probe direction that is not a rigid-body mode, so p^T K p > 0 and
+        // every probe launch keeps iterating
+        k_fill_hash<T><<<vec_grid(pb_.n_items), 256, 0, s>>>(b_.p, pb_.D);
         count_launch();
         CellArgs<T> ca{};
         ca.d0 = pb_.desc[0];
@@ -645,14 +653,20 @@ class Core {
             return (cudaGetLastError(), 2);
         }
         float best = 1e30f, times[3] = {-1.f, -1.f, -1.f};
-        int choice = 2;
+        int choice = 1;
         for (int v = 1; v <= 3; ++v) {
             variant_ = v;
-            bool ok = launch_apply(ca, s) == cudaSuccess;
+            // fresh control blocks for each variant (the apply's epilogue updates them)
+            bool ok = cudaMemcpyAsync(b_.tune, tc.data(), sizeof(Ctl) * tc.size(), cudaMemcpyHostToDevice, s) ==
+                      cudaSuccess;
+            ok = ok && launch_apply(ca, s) == cudaSuccess;
             ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
             for (int r = 0; r < 3 && ok; ++r) ok = launch_apply(ca, s) == cudaSuccess;
             ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
             float ms = 0;
+            Ctl probe{};
+            ok = ok && cudaMemcpy(&probe, b_.tune, sizeof(Ctl), cudaMemcpyDeviceToHost) == cudaSuccess &&
+                 probe.status == 0 && probe.go == 1;  // the probe kept iterating
             if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
                 times[v - 1] = ms;
                 if (ms < best) {
