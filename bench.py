@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--n", type=int, default=64, help="mesh edge (64 = the benchmark workload)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--pcg-rtol", type=float, default=1e-4, help="inner CG relative tolerance")
+    ap.add_argument("--pcg-rtol", type=float, default=3e-3, help="inner CG relative tolerance")
     ap.add_argument("--apply-kernel", type=int, default=0, help="0 autotuned, 1 per-cell, 2 bricks")
     ap.add_argument("--no-suite", action="store_true",
                     help="skip the secondary measurements (batch c3, adjoint c2, 128^3 c4)")

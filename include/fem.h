@@ -153,7 +153,7 @@ typedef struct {
     double newton_rtol;  /* stop when ||R_free|| <= newton_rtol * ||R_free|| of step 1, it 0 */
     double newton_atol;  /* ... or ||R_free|| <= newton_atol */
     int newton_maxit;    /* Newton iterations per load step before FEM_ERR_NOT_CONVERGED */
-    double pcg_rtol;     /* inner CG: ||r|| <= pcg_rtol ||r_0|| */
+    double pcg_rtol;     /* inner CG: ||r|| <= pcg_rtol ||r_0|| (default 3e-3) */
     int pcg_maxit;       /* inner CG iteration cap (the iterate is still used) */
     int pcg_chunk;       /* CG iterations per CUDA-graph launch (0 = default) */
     int step_begin;      /* first load step to run (1 = from the start; k+1 resumes a
@@ -174,12 +174,13 @@ typedef struct {
     double ref_rnorm;    /* ||R_free|| at step 1, iteration 0 */
     double final_rnorm;  /* last ||R_free|| (double precision) */
     double time_ms;      /* wall time of the call */
-    double apply_ms;     /* summed device time of the sampled CG tangent-apply launches */
-    int apply_samples;   /* number of sampled launches (the first apply of each CG graph) */
+    double apply_ms;     /* summed device time of the CG tangent-apply launches that did work
+                            (first block start to last block end, %globaltimer) */
+    int apply_samples;   /* number of such launches */
     int apply_launches;  /* CG tangent-apply launches that did work */
     int apply_kernel;    /* CG apply kernel that ran (1 per-cell, 2 bricks, 3 per-cell 4 CTA/SM) */
-    double update_ms;    /* summed device time of the sampled CG vector-update launches */
-    int update_samples;  /* number of sampled update launches */
+    double update_ms;    /* the same for the CG vector-update launches */
+    int update_samples;
 } fem_stats;
 
 typedef struct {

@@ -38,6 +38,7 @@ struct CellArgs {
     int iter;               // CG iteration inside the current graph chunk
     int pcg_maxit;          // CG iteration cap (CG apply)
     int *arrive;            // arrival counter of the CG apply (last-block epilogue)
+    KernelClock *kclock;    // live span statistics of the CG apply (may be null)
     T *g;                   // VJP output [Ne]
     int *jflag;             // det F <= 0 flag (ungated residual)
     const int32_t *cells;   // explicit cell list (colour-ordered launch) or nullptr
@@ -66,6 +67,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
     // so the tile loop itself has no block barrier.
     T part = 0;
     int acc_k = -1, acc_slot = 0;
+    if (MODE == CM_APPLY_PCG && threadIdx.x == 0) kclock_start(a.kclock, 0);
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
         int k = 0;
         InstDesc dcopy;
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
             const double s = block_sum_t<T, CELL_BLOCK>(part, sh);
             if (threadIdx.x == 0) atomicAdd(&a.ctl[acc_k].delta[acc_slot], s);
         }
-        if (last_block(a.arrive)) cg_after_apply(a.ctl, a.tab ? a.n_inst : 1, a.iter);
+        if (last_block(a.arrive)) cg_apply_epilogue(a.ctl, a.tab ? a.n_inst : 1, a.iter, a.kclock);
     }
 }
 
@@ -314,6 +316,7 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
     __shared__ T su[3][NN], sp[3][NN], sy[3][NN];
     __shared__ double sh[NT / 32];
     const int tid = threadIdx.x;
+    if (tid == 0) kclock_start(a.kclock, 0);
     for (int64_t brick = blockIdx.x; brick < a.n_tiles; brick += gridDim.x) {
         int k = 0;
         InstDesc d;
@@ -442,7 +445,7 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
         if (tid == 0) atomicAdd(&a.ctl[k].delta[slot], s);
         __syncthreads();  // shared arrays are reused by the next brick
     }
-    if (last_block(a.arrive)) cg_after_apply(a.ctl, a.tab ? a.n_inst : 1, a.iter);
+    if (last_block(a.arrive)) cg_apply_epilogue(a.ctl, a.tab ? a.n_inst : 1, a.iter, a.kclock);
 }
 
 // CSR assembly (Algorithm 1): one thread per (cell, column).  The column

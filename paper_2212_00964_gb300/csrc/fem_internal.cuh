@@ -114,6 +114,40 @@ struct Ctl {
     float a_f, b_f;
 };
 
+// Live kernel-span statistics of the two CG kernels, in device memory: the
+// first block to start and the last block to finish bound each launch
+// (%globaltimer, nanoseconds).
+struct KernelClock {
+    unsigned long long t0[2];   // earliest block start of the running launch (0 apply, 1 update)
+    unsigned long long sum[2];  // summed spans of finished launches
+    unsigned long long n[2];    // launches that did work
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// call from thread 0 of every block at kernel start
+__device__ __forceinline__ void kclock_start(KernelClock *kc, int which)
+{
+    if (kc) atomicMin(&kc->t0[which], global_ns());
+}
+
+// call from the last block; `worked` says whether the launch did CG work
+__device__ __forceinline__ void kclock_end(KernelClock *kc, int which, bool worked)
+{
+    if (!kc) return;
+    const unsigned long long t = global_ns(), t0 = __ldcg(&kc->t0[which]);
+    if (worked && t > t0) {
+        kc->sum[which] += t - t0;
+        kc->n[which] += 1;
+    }
+    kc->t0[which] = ~0ull;
+}
+
 // Last-block arrival: every block of the grid calls this once, after its
 // global reductions; it returns true in all threads of the block that
 // arrives last, which then sees every other block's writes.  The counter is
@@ -533,4 +567,29 @@ __device__ __forceinline__ double cell_dscale(const InstDesc &d, double th)
     return d.p * pow(th, d.p - 1.0) * (1.0 - d.emin);
 }
 
+}  // namespace femgb
+
+
+namespace femgb {
+// Whether any instance ran this CG iteration (all threads of the last block).
+__device__ __forceinline__ bool any_go(const Ctl *ctl, int n_inst)
+{
+    int w = 0;
+    for (int k = threadIdx.x; k < n_inst; k += blockDim.x) w |= __ldcg(&ctl[k].go);
+    return __syncthreads_or(w) != 0;
+}
+
+__device__ __forceinline__ void cg_apply_epilogue(Ctl *ctl, int n_inst, int iter, KernelClock *kc)
+{
+    const bool worked = any_go(ctl, n_inst);
+    if (threadIdx.x == 0) kclock_end(kc, 0, worked);
+    cg_after_apply(ctl, n_inst, iter);
+}
+
+__device__ __forceinline__ void cg_update_epilogue(Ctl *ctl, int n_inst, int iter, int pcg_maxit, KernelClock *kc)
+{
+    const bool worked = any_go(ctl, n_inst);
+    if (threadIdx.x == 0) kclock_end(kc, 1, worked);
+    cg_after_update(ctl, n_inst, iter, pcg_maxit);
+}
 }  // namespace femgb

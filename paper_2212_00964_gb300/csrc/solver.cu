@@ -59,6 +59,7 @@ struct VecArgs {
     SolverParams prm;
     int *counter;       // [0] solving, [1] iterating, [2] active
     int *arrive;        // last-block arrival counter of the CG kernels
+    KernelClock *kclock;
 };
 
 #define VEC_ITEMS_BEGIN                                                       \
@@ -245,9 +246,10 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_init(const VecArgs<T> a)
 // Every block derives alpha and beta from the same reduced scalars; the
 // first block of the instance records alpha and clears the next delta slot.
 template <typename T>
-__global__ void __launch_bounds__(VEC_BLOCK) k_pcg_update(const VecArgs<T> a)
+__global__ void __launch_bounds__(VEC_BLOCK, (sizeof(T) == 4 ? 4 : 2)) k_pcg_update(const VecArgs<T> a)
 {
     __shared__ double sh[2 * (VEC_BLOCK / 32)];
+    if (threadIdx.x == 0) kclock_start(a.kclock, 1);
     VEC_ITEMS_BEGIN
     if (!c.go) continue;  // alpha, beta and go come from the apply's last block
     const int it = c.pcg_base + a.iter;
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_update(const VecArgs<T> a)
         atomicAdd(&c.rr[(it + 1) & 3], s2);
     }
     VEC_ITEMS_END
-    if (last_block(a.arrive)) cg_after_update(a.ctl, a.n_inst, a.iter, a.prm.pcg_maxit);
+    if (last_block(a.arrive)) cg_update_epilogue(a.ctl, a.n_inst, a.iter, a.prm.pcg_maxit, a.kclock);
 }
 
 // End of a graph chunk: instances whose next iteration would not run are
@@ -426,6 +428,7 @@ struct Buffers {
     T *uT;
     T *x, *r, *z, *p, *q, *dg, *s;
     Ctl *tune;           // scratch control blocks for the apply autotuner (may be null)
+    KernelClock *kclock; // live span statistics of the CG kernels (may be null)
 };
 
 struct Graphs {
@@ -476,6 +479,7 @@ class Core {
         va_.prm = prm;
         va_.counter = b.counter;
         va_.arrive = b.counter + 3;
+        va_.kclock = b.kclock;
     }
 
     cudaError_t enqueue_head(cudaStream_t s)
@@ -560,21 +564,14 @@ class Core {
         ca.y = b_.q;
         ca.pcg_maxit = prm_.pcg_maxit;
         ca.arrive = b_.counter + 3;
+        ca.kclock = b_.kclock;
         for (int j = 0; j < prm_.chunk; ++j) {
             ca.iter = j;
-            if (j == 0 && ev_a_ && (e = cudaEventRecordWithFlags(ev_a_, s, cudaEventRecordExternal)) != cudaSuccess)
-                return e;
             if ((e = launch_apply(ca, s)) != cudaSuccess) return e;
-            if (j == 0 && ev_b_ && (e = cudaEventRecordWithFlags(ev_b_, s, cudaEventRecordExternal)) != cudaSuccess)
-                return e;
             VecArgs<T> v = va_;
             v.iter = j;
-            if (j == 0 && ev_c_ && (e = cudaEventRecordWithFlags(ev_c_, s, cudaEventRecordExternal)) != cudaSuccess)
-                return e;
             k_pcg_update<T><<<gv, VEC_BLOCK, 0, s>>>(v);
             count_launch();
-            if (j == 0 && ev_d_ && (e = cudaEventRecordWithFlags(ev_d_, s, cudaEventRecordExternal)) != cudaSuccess)
-                return e;
         }
         k_chunk_ctl<<<gi, 128, 0, s>>>(b_.ctl, ni, prm_.chunk, prm_.pcg_maxit, b_.counter);
         count_launch();
@@ -646,6 +643,7 @@ class Core {
         ca.y = b_.q;
         ca.pcg_maxit = 1 << 30;
         ca.arrive = b_.counter + 3;
+        ca.kclock = nullptr;
         cudaEvent_t e0, e1;
         if (cudaEventCreate(&e0) != cudaSuccess) return (cudaGetLastError(), 2);
         if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -688,6 +686,21 @@ class Core {
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = choice;
         return choice;
+    }
+
+    // Live kernel spans recorded by the CG kernels during the solve.
+    cudaError_t read_clock(cudaStream_t s)
+    {
+        if (!b_.kclock) return cudaSuccess;
+        KernelClock kc{};
+        cudaError_t e = cudaMemcpyAsync(&kc, b_.kclock, sizeof(kc), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        apply_ms_ = kc.sum[0] * 1e-6;
+        apply_samples_ = (int)kc.n[0];
+        update_ms_ = kc.sum[1] * 1e-6;
+        update_samples_ = (int)kc.n[1];
+        return cudaSuccess;
     }
 
     // Same rounds as run(), launched straight onto `s` without graphs,
@@ -763,26 +776,6 @@ class Core {
     int run(cudaStream_t s, double timeout_s)
     {
         Graphs G;
-        struct EvSet {
-            cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
-            ~EvSet()
-            {
-                for (auto x : e)
-                    if (x) cudaEventDestroy(x);
-            }
-        } ev;
-        for (auto &x : ev.e) {
-            if (cudaEventCreate(&x) != cudaSuccess) {
-                cudaGetLastError();
-                x = nullptr;
-            }
-        }
-        if (ev.e[0] && ev.e[1] && ev.e[2] && ev.e[3]) {
-            ev_a_ = ev.e[0];
-            ev_b_ = ev.e[1];
-            ev_c_ = ev.e[2];
-            ev_d_ = ev.e[3];
-        }
         warm_occupancy(pb_.nh);
         if (variant_ == 0) variant_ = autotune(s);
         FEM_CUDA(capture(s, 0, &G.head, &G.n_head));
@@ -805,18 +798,7 @@ class Core {
                     FEM_CUDA(cudaGraphLaunch(G.chunk, s));
                     count_launch(G.n_chunk);
                     FEM_CUDA(cudaStreamSynchronize(s));
-                    if (ev_a_) {
-                        float ms = 0, ms2 = 0;
-                        if (cudaEventElapsedTime(&ms, ev_a_, ev_b_) == cudaSuccess &&
-                            cudaEventElapsedTime(&ms2, ev_c_, ev_d_) == cudaSuccess) {
-                            apply_ms_ += ms;
-                            apply_samples_++;
-                            update_ms_ += ms2;
-                            update_samples_++;
-                        } else {
-                            cudaGetLastError();
-                        }
-                    }
+
                     if (h_counter_[1] == 0) break;
                     if (expired()) return (set_error("solve watchdog expired"), FEM_ERR_TIMEOUT);
                 }
@@ -838,7 +820,7 @@ class Core {
     int apply_samples_ = 0;
     double update_ms_ = 0;  // sampled device time of CG vector updates
     int update_samples_ = 0;
-    cudaEvent_t ev_a_ = nullptr, ev_b_ = nullptr, ev_c_ = nullptr, ev_d_ = nullptr;
+
 
   private:
     const Problem &pb_;
@@ -908,7 +890,7 @@ static cudaError_t join_streams(cudaStream_t from, cudaStream_t to)
 // Workspace slots
 enum {
     WS_CTL = 0, WS_CNT, WS_R64, WS_UT, WS_X, WS_R, WS_Z, WS_P, WS_Q, WS_DG, WS_LAM, WS_TAB, WS_CPT,
-    WS_U64CAT, WS_MASKCAT, WS_UBARCAT, WS_RHSCAT, WS_CP64CAT, WS_G64, WS_S, WS_TUNE
+    WS_U64CAT, WS_MASKCAT, WS_UBARCAT, WS_RHSCAT, WS_CP64CAT, WS_G64, WS_S, WS_TUNE, WS_KCLOCK
 };
 
 template <typename T>
@@ -931,6 +913,7 @@ static int alloc_buffers(Workspace &ws, const Problem &pb, Buffers<T> &b, bool n
     WSGET(b.dg, WS_DG, T, D);
     WSGET(b.s, WS_S, T, D);
     WSGET(b.tune, WS_TUNE, Ctl, n);
+    WSGET(b.kclock, WS_KCLOCK, KernelClock, 1);
     if (n > 1) WSGET(b.tab, WS_TAB, InstDesc, n);
     else b.tab = nullptr;
     if (need_uT) WSGET(b.uT, WS_UT, T, D);
@@ -1004,6 +987,10 @@ static int solve_batch(Workspace &ws, Problem &pb, double *u64, const uint8_t *m
     std::vector<Ctl> ctl = initial_ctl(pb, o.step_begin, false);
     FEM_CUDA(cudaMemcpyAsync(b.ctl, ctl.data(), sizeof(Ctl) * ctl.size(), cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemsetAsync(b.counter, 0, 4 * sizeof(int), s));
+    {
+        static const KernelClock kc0 = {{~0ull, ~0ull}, {0, 0}, {0, 0}};
+        FEM_CUDA(cudaMemcpyAsync(b.kclock, &kc0, sizeof(kc0), cudaMemcpyHostToDevice, s));
+    }
     if (b.tab) FEM_CUDA(cudaMemcpyAsync(b.tab, pb.desc.data(), sizeof(InstDesc) * pb.desc.size(), cudaMemcpyHostToDevice, s));
     if (sepT) {
         k_convert<T><<<vec_grid(pb.n_items), 256, 0, s>>>(b.uT, u64, pb.D);
@@ -1018,6 +1005,7 @@ static int solve_batch(Workspace &ws, Problem &pb, double *u64, const uint8_t *m
     core.max_steps_ = *std::max_element(pb.n_steps.begin(), pb.n_steps.end());
     core.variant_ = o.apply_kernel;
     int rc = core.run(s, o.timeout_s);
+    if (rc == FEM_OK) FEM_CUDA(core.read_clock(s));
     at.ms = core.apply_ms_;
     at.samples = core.apply_samples_;
     at.variant = core.variant_;
@@ -1064,11 +1052,16 @@ static int adjoint_batch(Workspace &ws, Problem &pb, const double *ustar, const 
     std::vector<Ctl> ctl = initial_ctl(pb, 1, true);
     FEM_CUDA(cudaMemcpyAsync(b.ctl, ctl.data(), sizeof(Ctl) * ctl.size(), cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemsetAsync(b.counter, 0, 4 * sizeof(int), s));
+    {
+        static const KernelClock kc0 = {{~0ull, ~0ull}, {0, 0}, {0, 0}};
+        FEM_CUDA(cudaMemcpyAsync(b.kclock, &kc0, sizeof(kc0), cudaMemcpyHostToDevice, s));
+    }
     SolverParams prm = params_from(o);
     Core<T> core(pb, b, SM_LINEAR, prm, hc);
     core.ustar64_ = ustar;
     core.variant_ = o.apply_kernel;
     int rc = core.run(s, o.timeout_s);
+    if (rc == FEM_OK) FEM_CUDA(core.read_clock(s));
     at.ms = core.apply_ms_;
     at.samples = core.apply_samples_;
     at.variant = core.variant_;
