@@ -178,7 +178,7 @@ typedef struct {
                             (first block start to last block end, %globaltimer) */
     int apply_samples;   /* number of such launches */
     int apply_launches;  /* CG tangent-apply launches that did work */
-    int apply_kernel;    /* CG apply kernel that ran (1 per-cell, 2 bricks, 3 per-cell 4 CTA/SM) */
+    int apply_kernel;    /* CG apply kernel that ran (see fem_options.apply_kernel) */
     double update_ms;    /* the same for the CG vector-update launches */
     int update_samples;
 } fem_stats;

@@ -50,7 +50,7 @@ template <typename T>
 __device__ __forceinline__ void scatter_add(T *p, T v, int plain)
 {
     if (plain) *p += v;
-    else atomicAdd(p, v);
+    else red_add(p, v);
 }
 
 // MINB: CTAs per SM the FP32 instantiation is register-budgeted for (the
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
             const int I = i0 + ii, J = j0 + jj, K = k0 + kk;
             if (I <= nx && J <= ny && K <= nz) {
                 const T v = sy[c][ii + NX * row];
-                if (v != (T)0) atomicAdd(&yb[3 * (I + sy_ * J + sz_ * K) + c], v);
+                if (v != (T)0) red_add(&yb[3 * (I + sy_ * J + sz_ * K) + c], v);
             }
         }
         const double s = block_sum_t<T, NT>(part, sh);
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) assemble_kernel(const AsmArgs<T> a
             for (int c = 0; c < 3; ++c) {
                 const int64_t row = 3 * nid[n] + c;
                 if (a.mask && a.mask[row]) continue;
-                atomicAdd(&a.vals[a.row_ptr[row] + 3 * pos + cc], ye[c][n]);
+                red_add(&a.vals[a.row_ptr[row] + 3 * pos + cc], ye[c][n]);
             }
         }
         (void)nz;

@@ -152,6 +152,18 @@ __device__ __forceinline__ void kclock_end(KernelClock *kc, int which, bool work
 // global reductions; it returns true in all threads of the block that
 // arrives last, which then sees every other block's writes.  The counter is
 // reset by that block for the next kernel.
+// Fire-and-forget global add (PTX `red`): the compiler cannot prove that a
+// pointer taken from kernel arguments is global, and a generic atomicAdd
+// becomes an ATOM whose (unused) result the warp still waits for.
+__device__ __forceinline__ void red_add(float *p, float v)
+{
+    asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(double *p, double v)
+{
+    asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v) : "memory");
+}
+
 __device__ __forceinline__ bool last_block(int *arrive)
 {
     __shared__ int s_last;

@@ -135,9 +135,9 @@ __global__ void k_traction(int nx, int ny, int nz, int face, double tx, double t
                 idx[d1] = a + da;
                 idx[d2] = b + db;
                 int64_t node = idx[0] + (int64_t)(nx + 1) * (idx[1] + (int64_t)(ny + 1) * idx[2]);
-                atomicAdd(&f[3 * node + 0], tx * area * 0.25);
-                atomicAdd(&f[3 * node + 1], ty * area * 0.25);
-                atomicAdd(&f[3 * node + 2], tz * area * 0.25);
+                red_add(&f[3 * node + 0], tx * area * 0.25);
+                red_add(&f[3 * node + 1], ty * area * 0.25);
+                red_add(&f[3 * node + 2], tz * area * 0.25);
             }
     }
 }
@@ -151,9 +151,9 @@ __global__ void k_body(int nx, int ny, int nz, double bx, double by, double bz, 
         for (int a = 0; a < 8; ++a) {
             int64_t node = (i + c_vtk_off[a][0]) +
                            (int64_t)(nx + 1) * ((j + c_vtk_off[a][1]) + (int64_t)(ny + 1) * (k + c_vtk_off[a][2]));
-            atomicAdd(&f[3 * node + 0], bx * vol * 0.125);
-            atomicAdd(&f[3 * node + 1], by * vol * 0.125);
-            atomicAdd(&f[3 * node + 2], bz * vol * 0.125);
+            red_add(&f[3 * node + 0], bx * vol * 0.125);
+            red_add(&f[3 * node + 1], by * vol * 0.125);
+            red_add(&f[3 * node + 2], bz * vol * 0.125);
         }
     }
 }

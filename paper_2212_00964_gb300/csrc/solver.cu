@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_init(const VecArgs<T> a)
 // Every block derives alpha and beta from the same reduced scalars; the
 // first block of the instance records alpha and clears the next delta slot.
 template <typename T>
-__global__ void __launch_bounds__(VEC_BLOCK, (sizeof(T) == 4 ? 4 : 2)) k_pcg_update(const VecArgs<T> a)
+__global__ void __launch_bounds__(VEC_BLOCK, (sizeof(T) == 4 ? 3 : 2)) k_pcg_update(const VecArgs<T> a)
 {
     __shared__ double sh[2 * (VEC_BLOCK / 32)];
     if (threadIdx.x == 0) kclock_start(a.kclock, 1);
@@ -258,6 +258,57 @@ __global__ void __launch_bounds__(VEC_BLOCK, (sizeof(T) == 4 ? 4 : 2)) k_pcg_upd
     const bool first = it == 0;
     T ag = 0, arr = 0;
     const int64_t bd = blockDim.x;
+    if (sizeof(T) == 4 && ((base + i0) & 3) == 0) {
+        // FP32: four consecutive DOFs per 16-byte access
+        const int64_t n4 = (i1 - i0) >> 2;
+        const float alf = (float)al, bef = (float)be;
+        for (int64_t g = threadIdx.x; g < n4; g += bd) {
+            const int64_t j = base + i0 + 4 * g;
+            const float4 zv = *(const float4 *)(a.z + j);
+            const float4 wv = *(const float4 *)(a.q + j);
+            const float4 iv = *(const float4 *)(a.dg + j);
+            const float4 xv = *(const float4 *)(a.x + j);
+            const float4 rv = *(const float4 *)(a.r + j);
+            const float4 pv = first ? make_float4(0, 0, 0, 0) : *(const float4 *)(a.p + j);
+            const float4 sv = first ? make_float4(0, 0, 0, 0) : *(const float4 *)(a.s + j);
+            float4 pn, sn, xn, rn, zn;
+#define FEMGB_UPD(c)                                            \
+    pn.c = zv.c + bef * pv.c;                                   \
+    sn.c = iv.c != 0.f ? wv.c + bef * sv.c : 0.f;               \
+    rn.c = rv.c - alf * sn.c;                                   \
+    zn.c = iv.c * rn.c;                                         \
+    xn.c = xv.c + alf * pn.c;                                   \
+    ag += (T)(rn.c * zn.c);                                     \
+    arr += (T)(rn.c * rn.c);
+            FEMGB_UPD(x)
+            FEMGB_UPD(y)
+            FEMGB_UPD(z)
+            FEMGB_UPD(w)
+#undef FEMGB_UPD
+            *(float4 *)(a.p + j) = pn;
+            *(float4 *)(a.s + j) = sn;
+            *(float4 *)(a.x + j) = xn;
+            *(float4 *)(a.r + j) = rn;
+            *(float4 *)(a.z + j) = zn;
+            *(float4 *)(a.q + j) = make_float4(0, 0, 0, 0);
+        }
+        // scalar tail of the chunk
+        for (int64_t i = i0 + 4 * n4 + threadIdx.x; i < i1; i += bd) {
+            const int64_t j = base + i;
+            const T pn = a.z[j] + be * (first ? (T)0 : a.p[j]);
+            const T sn_ = a.dg[j] != (T)0 ? a.q[j] + be * (first ? (T)0 : a.s[j]) : (T)0;
+            const T rn = a.r[j] - al * sn_;
+            const T zn = a.dg[j] * rn;
+            a.p[j] = pn;
+            a.s[j] = sn_;
+            a.x[j] += al * pn;
+            a.r[j] = rn;
+            a.z[j] = zn;
+            a.q[j] = 0;
+            ag += rn * zn;
+            arr += rn * rn;
+        }
+    } else
     for (int64_t i = i0 + threadIdx.x; i < i1; i += 4 * bd) {
         // four independent elements per thread: all loads are issued first
         T zv[4], wv[4], iv[4], xv[4], rv[4], pv[4], sv[4];
@@ -400,6 +451,7 @@ struct Problem {
     {
         D = Ne = n_tiles = n_items = n_bricks = 0;
         for (auto &d : desc) {
+            D = (D + 3) & ~(int64_t)3;  // 16-byte aligned FP32 rows for vector loads
             d.dof_off = D;
             d.cell_off = Ne;
             d.tile_off = n_tiles;
