@@ -67,6 +67,9 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
     // so the tile loop itself has no block barrier.
     T part = 0;
     int acc_k = -1, acc_slot = 0;
+    // (go, slot) of the instance looked up last: fixed for one launch, so it
+    // is read once per instance rather than once per tile
+    int ctl_k = -1, ctl_go = 0, ctl_slot = 0;
     if (MODE == CM_APPLY_PCG && threadIdx.x == 0) kclock_start(a.kclock, 0);
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
         int k = 0;
@@ -87,14 +90,18 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                 acc_k = -1;
             }
             // the previous kernel decided whether this CG iteration runs
-            int go = 0, base = 0;
-            if ((threadIdx.x & 31) == 0) {
-                go = a.ctl[k].go;
-                base = a.ctl[k].pcg_base;
+            if (k != ctl_k) {  // uniform per block
+                int go = 0, base = 0;
+                if ((threadIdx.x & 31) == 0) {
+                    go = a.ctl[k].go;
+                    base = a.ctl[k].pcg_base;
+                }
+                ctl_go = __shfl_sync(0xffffffffu, go, 0);
+                ctl_slot = (__shfl_sync(0xffffffffu, base, 0) + a.iter) & 3;
+                ctl_k = k;
             }
-            go = __shfl_sync(0xffffffffu, go, 0);
-            if (!go) continue;  // uniform per block
-            slot = (__shfl_sync(0xffffffffu, base, 0) + a.iter) & 3;
+            if (!ctl_go) continue;  // uniform per block
+            slot = ctl_slot;
             acc_k = k;
             acc_slot = slot;
         } else if (MODE == CM_RESIDUAL_CTL || MODE == CM_APPLY_CTL) {
@@ -127,33 +134,39 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
             // VJP uses the unit-scale residual: dR_e/dtheta_e = s'(theta_e) R_e(u; s = 1)
             const Mat<T> m = cell_mat<T>(d, (MODE == CM_VJP) ? nullptr : cp, cell);
 
-            T Gu[3][3][4];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                T v[8];
-#pragma unroll
-                for (int n = 0; n < 8; ++n) v[n] = ub[3 * nid[n] + c];
-                grad_sf<T>(v, ihx, ihy, ihz, Gu[c]);
-            }
             constexpr bool IS_APPLY =
                 (MODE == CM_APPLY || MODE == CM_APPLY_PCG || MODE == CM_APPLY_CTL || MODE == CM_APPLY_LIFT);
             constexpr bool IS_RES = (MODE == CM_RESIDUAL || MODE == CM_RESIDUAL_CTL || MODE == CM_VJP);
             constexpr bool IS_DIAG = (MODE == CM_DIAG || MODE == CM_DIAG_CTL);
-            T Gx[3][3][4];
-            T xe[3][8];
+            // all node values are loaded before any arithmetic, so the gather
+            // latency is exposed once per cell
+            T ue[3][8], xe[3][8];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int n = 0; n < 8; ++n) ue[c][n] = ub[3 * nid[n] + c];
             if (IS_APPLY) {
                 const T *xb = a.x + d.dof_off;
-                const uint8_t *mb = a.mask ? a.mask + d.dof_off : nullptr;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
+                for (int c = 0; c < 3; ++c)
 #pragma unroll
-                    for (int n = 0; n < 8; ++n) {
-                        T v = xb[3 * nid[n] + c];
-                        if (mb && mb[3 * nid[n] + c]) v = 0;
-                        xe[c][n] = v;
-                    }
-                    grad_sf<T>(xe[c], ihx, ihy, ihz, Gx[c]);
+                    for (int n = 0; n < 8; ++n) xe[c][n] = xb[3 * nid[n] + c];
+                // CG directions vanish on prescribed DOFs already (no mask)
+                const uint8_t *mb = (MODE == CM_APPLY_PCG || !a.mask) ? nullptr : a.mask + d.dof_off;
+                if (mb) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int n = 0; n < 8; ++n)
+                            if (mb[3 * nid[n] + c]) xe[c][n] = 0;
                 }
+            }
+            T Gu[3][3][4], Gx[3][3][4];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) grad_sf<T>(ue[c], ihx, ihy, ihz, Gu[c]);
+            if (IS_APPLY) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) grad_sf<T>(xe[c], ihx, ihy, ihz, Gx[c]);
             }
             T S[3][3][4];
 #pragma unroll
