@@ -115,9 +115,14 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
         // mesh is built), so the index arithmetic runs in 32 bits.
         const int ne = (int)(a.cells ? a.n_list : d.n_cells());
         const int local = (int)(tile - d.tile_off) * (int)blockDim.x + (int)threadIdx.x;
-        const bool active = local < ne;
+        const bool live = local < ne;
+        // CG apply: the scatter merges +x neighbours across lanes, so every
+        // lane of a tile takes part (a lane past the end computes the last
+        // cell with zero weight and scatters nothing)
+        constexpr bool MERGE = (MODE == CM_APPLY_PCG);
+        const bool active = MERGE || live;
         if (active) {
-            const int cell = a.cells ? a.cells[local] : local;
+            const int cell = a.cells ? a.cells[local] : (live ? local : ne - 1);
             const unsigned nx = (unsigned)d.nx, ny = (unsigned)d.ny;
             const unsigned rowc = (unsigned)cell / nx;
             const int ci = (int)((unsigned)cell - rowc * nx);
@@ -130,6 +135,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
             const T *ub = a.u + d.dof_off;
             const T ihx = d.ihx<T>(), ihy = d.ihy<T>(), ihz = d.ihz<T>();
             const T wdet = d.wdet<T>();
+            const T wl = live ? wdet : (T)0;
             const T *cp = a.cell_param ? a.cell_param + d.cell_off : nullptr;
             // VJP uses the unit-scale residual: dR_e/dtheta_e = s'(theta_e) R_e(u; s = 1)
             const Mat<T> m = cell_mat<T>(d, (MODE == CM_VJP) ? nullptr : cp, cell);
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                     if (MODE == CM_APPLY_PCG) {
                         // x_e . K_e x_e = sum_gp w detJ dP : dH
 #pragma unroll
-                        for (int t = 0; t < 9; ++t) part += wdet * P[t] * dH[t];
+                        for (int t = 0; t < 9; ++t) part += wl * P[t] * dH[t];
                     }
                 }
                 if (IS_RES || IS_APPLY) {
@@ -286,13 +292,35 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                     }
                 double th = cp ? (double)cp[cell] : 1.0;
                 a.g[d.cell_off + cell] = (T)(-cell_dscale(d, th) * (double)s);
+            } else if (MERGE) {
+                // Cell `cell + 1` sits in the next lane.  Its -x nodes are this
+                // cell's +x nodes (n = 1, 3, 5, 7 -> 0, 2, 4, 6), so the +x
+                // contributions move one lane up and each shared node gets one
+                // global add per pair of cells instead of two.
+                const int lane = threadIdx.x & 31;
+                const bool from_left = live && ci > 0 && lane > 0;
+                const bool to_right = live && ci + 1 < (int)d.nx && lane < 31 && local + 1 < ne;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const T v = __shfl_up_sync(0xffffffffu, ye[c][2 * m + 1], 1);
+                        if (from_left) ye[c][2 * m] += v;
+                    }
+                if (live) {
+                    T *yb = a.y + d.dof_off;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int n = 0; n < 8; ++n)
+                            if (!((n & 1) && to_right)) red_add(&yb[3 * nid[n] + c], ye[c][n]);
+                }
             } else {
                 T *yb = a.y + d.dof_off;
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
                     for (int n = 0; n < 8; ++n) scatter_add<T>(&yb[3 * nid[n] + c], ye[c][n], a.plain_store);
-
             }
             if (IS_RES && NH && inverted) {
                 if (MODE == CM_RESIDUAL_CTL) atomicExch(&a.ctl[k].jflag, 1);
