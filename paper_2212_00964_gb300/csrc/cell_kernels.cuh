@@ -70,7 +70,10 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
     // (go, slot) of the instance looked up last: fixed for one launch, so it
     // is read once per instance rather than once per tile
     int ctl_k = -1, ctl_go = 0, ctl_slot = 0;
-    if (MODE == CM_APPLY_PCG && threadIdx.x == 0) kclock_start(a.kclock, 0);
+    if (MODE == CM_APPLY_PCG) {
+        pdl_wait();
+        if (threadIdx.x == 0) kclock_start(a.kclock, 0);
+    }
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
         int k = 0;
         InstDesc dcopy;
@@ -357,6 +360,7 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
     __shared__ T su[3][NN], sp[3][NN], sy[3][NN];
     __shared__ double sh[NT / 32];
     const int tid = threadIdx.x;
+    pdl_wait();
     if (tid == 0) kclock_start(a.kclock, 0);
     for (int64_t brick = blockIdx.x; brick < a.n_tiles; brick += gridDim.x) {
         int k = 0;

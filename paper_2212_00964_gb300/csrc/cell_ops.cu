@@ -50,8 +50,9 @@ static cudaError_t launch_one(const CellArgs<T> &a, cudaStream_t s)
     auto f = a.tab ? cell_kernel<T, NH, MODE, 3, true> : cell_kernel<T, NH, MODE, 3, false>;
     int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, 0));
     if (g < 1) return cudaSuccess;
-    f<<<(int)g, CELL_BLOCK, 0, s>>>(a);
     count_launch();
+    if (MODE == CM_APPLY_PCG) return launch_pdl(f, (int)g, CELL_BLOCK, 0, s, a);  // begins with pdl_wait()
+    f<<<(int)g, CELL_BLOCK, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -61,9 +62,8 @@ static cudaError_t launch_one4(const CellArgs<T> &a, cudaStream_t s)
     auto f = a.tab ? cell_kernel<T, NH, CM_APPLY_PCG, 4, true> : cell_kernel<T, NH, CM_APPLY_PCG, 4, false>;
     int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, 0));
     if (g < 1) return cudaSuccess;
-    f<<<(int)g, CELL_BLOCK, 0, s>>>(a);
     count_launch();
-    return cudaGetLastError();
+    return launch_pdl(f, (int)g, CELL_BLOCK, 0, s, a);
 }
 
 template <typename T, int NH>
@@ -128,19 +128,11 @@ template <typename T>
 cudaError_t launch_apply_brick(bool nh, const CellArgs<T> &a, cudaStream_t s)
 {
     const int nt = BRICK_X * BRICK_Y * BRICK_Z;
-    if (nh) {
-        auto f = apply_brick<T, 1>;
-        int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, nt, 0));
-        if (g < 1) return cudaSuccess;
-        f<<<(int)g, nt, 0, s>>>(a);
-    } else {
-        auto f = apply_brick<T, 0>;
-        int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, nt, 0));
-        if (g < 1) return cudaSuccess;
-        f<<<(int)g, nt, 0, s>>>(a);
-    }
+    auto f = nh ? apply_brick<T, 1> : apply_brick<T, 0>;
+    int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, nt, 0));
+    if (g < 1) return cudaSuccess;
     count_launch();
-    return cudaGetLastError();
+    return launch_pdl(f, (int)g, nt, 0, s, a);  // begins with pdl_wait()
 }
 template cudaError_t launch_apply_brick<float>(bool, const CellArgs<float> &, cudaStream_t);
 

@@ -1,6 +1,8 @@
 // cell_ops.cuh -- launcher interface shared by the cell operators and the solvers.
 #pragma once
 
+#include <utility>
+
 #include "cell_kernels.cuh"
 
 struct fem_mesh_s;
@@ -15,6 +17,24 @@ cudaError_t launch_apply_brick(bool nh, const CellArgs<T> &a, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_apply_cell4(bool nh, const CellArgs<T> &a, cudaStream_t s);
+
+// Launch with programmatic stream serialisation (the kernel must begin with
+// pdl_wait() before it reads anything its predecessor wrote).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 int device_sms();
 void warm_occupancy(bool nh);

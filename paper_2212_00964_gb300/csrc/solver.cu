@@ -249,6 +249,7 @@ template <typename T>
 __global__ void __launch_bounds__(VEC_BLOCK, (sizeof(T) == 4 ? 3 : 2)) k_pcg_update(const VecArgs<T> a)
 {
     __shared__ double sh[2 * (VEC_BLOCK / 32)];
+    pdl_wait();
     if (threadIdx.x == 0) kclock_start(a.kclock, 1);
     VEC_ITEMS_BEGIN
     if (!c.go) continue;  // alpha, beta and go come from the apply's last block
@@ -622,7 +623,7 @@ class Core {
             if ((e = launch_apply(ca, s)) != cudaSuccess) return e;
             VecArgs<T> v = va_;
             v.iter = j;
-            k_pcg_update<T><<<gv, VEC_BLOCK, 0, s>>>(v);
+            if ((e = launch_pdl(k_pcg_update<T>, gv, VEC_BLOCK, 0, s, v)) != cudaSuccess) return e;
             count_launch();
         }
         k_chunk_ctl<<<gi, 128, 0, s>>>(b_.ctl, ni, prm_.chunk, prm_.pcg_maxit, b_.counter);
