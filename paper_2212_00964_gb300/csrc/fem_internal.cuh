@@ -394,14 +394,34 @@ __device__ __forceinline__ double block_sum_t(T v, double *sh)
 
 // W[a + 2b] = sum_{i,j} B[a][i] B[b][j] d[i + 2j]; B is symmetric, so the
 // same operator is its own transpose.
+// Two-stage interpolation of four values d[j][k] (k along the first, j
+// along the second remaining direction) to the four Gauss combinations,
+// scaled by sc: W[a + 2b] = sc sum_jk B[b][j] B[a][k] d[j][k].  The scale
+// rides on the second-stage constants, so it costs no extra multiply.
 template <typename T>
-__device__ __forceinline__ void interp2(T d00, T d10, T d01, T d11, T *W)
+__device__ __forceinline__ void interp2(T d00, T d10, T d01, T d11, T sc, T *W)
 {
     const T ca = (T)FEM_CA, cb = (T)FEM_CB;
+    const T cas = ca * sc, cbs = cb * sc;
     T s00 = ca * d00 + cb * d10;  // a=0, j=0
     T s10 = cb * d00 + ca * d10;  // a=1, j=0
     T s01 = ca * d01 + cb * d11;  // a=0, j=1
     T s11 = cb * d01 + ca * d11;  // a=1, j=1
+    W[0] = cas * s00 + cbs * s01;
+    W[1] = cas * s10 + cbs * s11;
+    W[2] = cbs * s00 + cas * s01;
+    W[3] = cbs * s10 + cas * s11;
+}
+
+// interp2 with sc = 1.
+template <typename T>
+__device__ __forceinline__ void interp2u(T d00, T d10, T d01, T d11, T *W)
+{
+    const T ca = (T)FEM_CA, cb = (T)FEM_CB;
+    T s00 = ca * d00 + cb * d10;
+    T s10 = cb * d00 + ca * d10;
+    T s01 = ca * d01 + cb * d11;
+    T s11 = cb * d01 + ca * d11;
     W[0] = ca * s00 + cb * s01;
     W[1] = ca * s10 + cb * s11;
     W[2] = cb * s00 + ca * s01;
@@ -411,12 +431,24 @@ __device__ __forceinline__ void interp2(T d00, T d10, T d01, T d11, T *W)
 // Gradient values of one scalar nodal field v[8] (node n = p+2q+4r):
 // G[0][b+2g] = dv/dx at (.,b,g), G[1][a+2g] = dv/dy at (a,.,g),
 // G[2][a+2b] = dv/dz at (a,b,.).  ih = 1/h per direction.
+// FP64 (FP64-pipe bound) folds 1/h into the interpolation; FP32 (latency
+// bound) scales the differences, which measured faster in the CG apply.
 template <typename T>
 __device__ __forceinline__ void grad_sf(const T *v, T ihx, T ihy, T ihz, T G[3][4])
 {
-    interp2<T>((v[1] - v[0]) * ihx, (v[3] - v[2]) * ihx, (v[5] - v[4]) * ihx, (v[7] - v[6]) * ihx, G[0]);
-    interp2<T>((v[2] - v[0]) * ihy, (v[3] - v[1]) * ihy, (v[6] - v[4]) * ihy, (v[7] - v[5]) * ihy, G[1]);
-    interp2<T>((v[4] - v[0]) * ihz, (v[5] - v[1]) * ihz, (v[6] - v[2]) * ihz, (v[7] - v[3]) * ihz, G[2]);
+    constexpr bool FOLD = sizeof(T) == 8;
+    const T one = (T)1;
+    const T sx = FOLD ? ihx : one, sy = FOLD ? ihy : one, sz = FOLD ? ihz : one;
+    const T px = FOLD ? one : ihx, py = FOLD ? one : ihy, pz = FOLD ? one : ihz;
+    if (FOLD) {
+        interp2<T>(v[1] - v[0], v[3] - v[2], v[5] - v[4], v[7] - v[6], sx, G[0]);
+        interp2<T>(v[2] - v[0], v[3] - v[1], v[6] - v[4], v[7] - v[5], sy, G[1]);
+        interp2<T>(v[4] - v[0], v[5] - v[1], v[6] - v[2], v[7] - v[3], sz, G[2]);
+    } else {
+        interp2u<T>((v[1] - v[0]) * px, (v[3] - v[2]) * px, (v[5] - v[4]) * px, (v[7] - v[6]) * px, G[0]);
+        interp2u<T>((v[2] - v[0]) * py, (v[3] - v[1]) * py, (v[6] - v[4]) * py, (v[7] - v[5]) * py, G[1]);
+        interp2u<T>((v[4] - v[0]) * pz, (v[5] - v[1]) * pz, (v[6] - v[2]) * pz, (v[7] - v[3]) * pz, G[2]);
+    }
 }
 
 // Transpose of grad_sf: given S[d][.] = sum over the remaining Gauss index of
@@ -425,22 +457,28 @@ __device__ __forceinline__ void grad_sf(const T *v, T ihx, T ihy, T ihz, T G[3][
 template <typename T>
 __device__ __forceinline__ void grad_sf_t(T S[3][4], T ihx, T ihy, T ihz, T *y)
 {
+    constexpr bool FOLD = sizeof(T) == 8;  // as in grad_sf
     T W[4];
-    interp2<T>(S[0][0], S[0][1], S[0][2], S[0][3], W);  // W[q + 2r]
-    y[1] += W[0] * ihx; y[0] -= W[0] * ihx;
-    y[3] += W[1] * ihx; y[2] -= W[1] * ihx;
-    y[5] += W[2] * ihx; y[4] -= W[2] * ihx;
-    y[7] += W[3] * ihx; y[6] -= W[3] * ihx;
-    interp2<T>(S[1][0], S[1][1], S[1][2], S[1][3], W);  // W[p + 2r]
-    y[2] += W[0] * ihy; y[0] -= W[0] * ihy;
-    y[3] += W[1] * ihy; y[1] -= W[1] * ihy;
-    y[6] += W[2] * ihy; y[4] -= W[2] * ihy;
-    y[7] += W[3] * ihy; y[5] -= W[3] * ihy;
-    interp2<T>(S[2][0], S[2][1], S[2][2], S[2][3], W);  // W[p + 2q]
-    y[4] += W[0] * ihz; y[0] -= W[0] * ihz;
-    y[5] += W[1] * ihz; y[1] -= W[1] * ihz;
-    y[6] += W[2] * ihz; y[2] -= W[2] * ihz;
-    y[7] += W[3] * ihz; y[3] -= W[3] * ihz;
+    const T one = (T)1;
+    if (FOLD) interp2<T>(S[0][0], S[0][1], S[0][2], S[0][3], ihx, W);  // W[q + 2r]
+    else interp2u<T>(S[0][0], S[0][1], S[0][2], S[0][3], W);
+    const T fx = FOLD ? one : ihx, fy = FOLD ? one : ihy, fz = FOLD ? one : ihz;
+    y[1] += W[0] * fx; y[0] -= W[0] * fx;
+    y[3] += W[1] * fx; y[2] -= W[1] * fx;
+    y[5] += W[2] * fx; y[4] -= W[2] * fx;
+    y[7] += W[3] * fx; y[6] -= W[3] * fx;
+    if (FOLD) interp2<T>(S[1][0], S[1][1], S[1][2], S[1][3], ihy, W);  // W[p + 2r]
+    else interp2u<T>(S[1][0], S[1][1], S[1][2], S[1][3], W);
+    y[2] += W[0] * fy; y[0] -= W[0] * fy;
+    y[3] += W[1] * fy; y[1] -= W[1] * fy;
+    y[6] += W[2] * fy; y[4] -= W[2] * fy;
+    y[7] += W[3] * fy; y[5] -= W[3] * fy;
+    if (FOLD) interp2<T>(S[2][0], S[2][1], S[2][2], S[2][3], ihz, W);  // W[p + 2q]
+    else interp2u<T>(S[2][0], S[2][1], S[2][2], S[2][3], W);
+    y[4] += W[0] * fz; y[0] -= W[0] * fz;
+    y[5] += W[1] * fz; y[1] -= W[1] * fz;
+    y[6] += W[2] * fz; y[2] -= W[2] * fz;
+    y[7] += W[3] * fz; y[3] -= W[3] * fz;
 }
 
 // -------------------------------------------------- constitutive laws ----
@@ -463,7 +501,7 @@ __device__ __forceinline__ T det_ipH_m1(const T *H)
 
 // J^{-1/3}.  FP32: 2^(-log2(J)/3) with the PTX approximate base-2 log and
 // exponential (relative error a few 1e-7 for J near 1, ample for the FP32
-// tangent and residual).  FP64: the library rcbrt.
+// tangent and residual).
 __device__ __forceinline__ float rcbrt_t(float x)
 {
     float l, r;
@@ -472,7 +510,23 @@ __device__ __forceinline__ float rcbrt_t(float x)
     asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(l));
     return r;
 }
-__device__ __forceinline__ double rcbrt_t(double x) { return rcbrt(x); }
+// FP64: Newton's iteration for the reciprocal cube root,
+// r <- r + r (1 - x r^3) / 3, started from the FP32 value above (relative
+// error e0 below 1e-6).  The error squares each step (e1 ~ 2 e0^2 < 1e-11,
+// e2 below FP64 rounding), so two steps give a full-precision J^{-1/3} with
+// ten FP64 operations.  Negative x (an inverted cell, flagged by the caller)
+// gets the real cube root's sign.
+__device__ __forceinline__ double rcbrt_t(double x)
+{
+    const double ax = fabs(x);
+    double r = (double)rcbrt_t((float)ax);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double r3 = r * r * r;
+        r = fma(r * (1.0 / 3.0), fma(-ax, r3, 1.0), r);
+    }
+    return x < 0 ? -r : r;
+}
 
 // Neo-Hookean kinematics at one Gauss point: A = F^{-T}, J, J-1, I1, G J^{-2/3}.
 template <typename T>
