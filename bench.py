@@ -403,7 +403,8 @@ def run_gb300(args):
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu",
                      "kernel": {1: "cell_kernel<float,NH,CM_APPLY_PCG,3>", 2: "apply_brick<float,NH>",
-                                3: "cell_kernel<float,NH,CM_APPLY_PCG,4>"}.get(st0.get("apply_kernel"), "?"),
+                                3: "cell_kernel<float,NH,CM_APPLY_PCG,4>",
+                                4: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN>"}.get(st0.get("apply_kernel"), "?"),
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",

@@ -161,7 +161,10 @@ typedef struct {
     int apply_kernel;    /* CG tangent-apply kernel: 0 = autotuned (timed once per problem shape and
                             cached), 1 = one thread per cell with a scatter per cell,
                             2 = 8x4x4-cell bricks staged in shared memory,
-                            3 = as 1 with a register budget for 4 CTAs per SM */
+                            3 = as 1 with a register budget for 4 CTAs per SM,
+                            4 = as 1 on Neo-Hookean tangent data stored once per
+                                Newton iteration (Neo-Hookean only; not in
+                                fem_solve_static) */
     int deterministic;   /* 1: colour-ordered scatter (bit-reproducible), 0: atomics */
     double timeout_s;    /* host watchdog for one solve (0 = none) */
 } fem_options;

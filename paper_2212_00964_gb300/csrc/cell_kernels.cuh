@@ -44,6 +44,7 @@ struct CellArgs {
     const int32_t *cells;   // explicit cell list (colour-ordered launch) or nullptr
     int64_t n_list;         // length of the cell list
     int plain_store;        // 1: cells in one launch share no node -> plain RMW
+    T *kin;                 // stored NH tangent data (written by the diagonal, read by the KIN apply) or nullptr
 };
 
 template <typename T>
@@ -57,7 +58,7 @@ __device__ __forceinline__ void scatter_add(T *p, T v, int plain)
 // CG apply is also built for 4, autotuned against 3).
 // BATCHED = false: one instance whose descriptor is read in place from the
 // kernel parameter (no register copy held across the tile loop).
-template <typename T, int NH, int MODE, int MINB = 3, bool BATCHED = true>
+template <typename T, int NH, int MODE, int MINB = 3, bool BATCHED = true, bool KIN = false>
 __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
     cell_kernel(const __grid_constant__ CellArgs<T> a)
 {
@@ -219,7 +220,18 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                         dH[3 * c + 1] = Gx[c][1][al + 2 * ga];
                         dH[3 * c + 2] = Gx[c][2][al + 2 * be];
                     }
-                    if (NH) {
+                    if (NH && KIN) {
+                        // tangent data stored by the diagonal kernel of this Newton iteration
+                        const T *kb = a.kin + kin_slot(d.tile_off, cell, gp * KIN_VALUES);
+                        NHKin<T> kq;
+#pragma unroll
+                        for (int t = 0; t < 9; ++t) kq.A[t] = kb[t * CELL_BLOCK];
+                        kq.k1 = kb[9 * CELL_BLOCK];
+                        kq.a1 = kb[10 * CELL_BLOCK];
+                        kq.a3 = kb[11 * CELL_BLOCK];
+                        kq.kdA = kb[12 * CELL_BLOCK];
+                        nh_dstress_kin<T>(kq, H, dH, P);
+                    } else if (NH) {
                         NHPoint<T> q;
                         nh_point<T>(H, m, q);
                         nh_dstress<T>(q, m, dH, P);
@@ -243,7 +255,20 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                 if (IS_DIAG) {
                     // rows i of the tangent blocks C[i j][i l] by unit directions
                     NHPoint<T> q;
-                    if (NH) nh_point<T>(H, m, q);
+                    if (NH) {
+                        nh_point<T>(H, m, q);
+                        if (a.kin) {  // store the tangent data for the CG applies
+                            NHKin<T> kq;
+                            nh_kin<T>(q, m, kq);
+                            T *kb = a.kin + kin_slot(d.tile_off, cell, gp * KIN_VALUES);
+#pragma unroll
+                            for (int t = 0; t < 9; ++t) kb[t * CELL_BLOCK] = kq.A[t];
+                            kb[9 * CELL_BLOCK] = kq.k1;
+                            kb[10 * CELL_BLOCK] = kq.a1;
+                            kb[11 * CELL_BLOCK] = kq.a3;
+                            kb[12 * CELL_BLOCK] = kq.kdA;
+                        }
+                    }
                     T Crow[3][3][3];  // [i][l][j]
 #pragma unroll
                     for (int i = 0; i < 3; ++i)

@@ -109,6 +109,9 @@ static void warm_one()
                                        : cell_kernel<T, NH, CM_APPLY_LIFT, 3, false>), CELL_BLOCK, 0);
         resident_grid((const void *)(b ? cell_kernel<T, NH, CM_APPLY_PCG, 4, true>
                                        : cell_kernel<T, NH, CM_APPLY_PCG, 4, false>), CELL_BLOCK, 0);
+        if (NH)
+            resident_grid((const void *)(b ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, true>
+                                           : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, true>), CELL_BLOCK, 0);
     }
     resident_grid((const void *)apply_brick<T, NH>, BRICK_X * BRICK_Y * BRICK_Z, 0);
 }
@@ -144,6 +147,20 @@ cudaError_t launch_apply_cell4(bool nh, const CellArgs<T> &a, cudaStream_t s)
     return e;
 }
 template cudaError_t launch_apply_cell4<float>(bool, const CellArgs<float> &, cudaStream_t);
+
+// CG apply on stored Neo-Hookean tangent data (a.kin filled by the diagonal).
+template <typename T>
+cudaError_t launch_apply_kin(bool nh, const CellArgs<T> &a, cudaStream_t s)
+{
+    if (!nh || !a.kin) return cudaErrorInvalidValue;
+    auto f = a.tab ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, true> : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, true>;
+    int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, 0));
+    if (g < 1) return cudaSuccess;
+    count_launch();
+    return launch_pdl(f, (int)g, CELL_BLOCK, 0, s, a);  // begins with pdl_wait()
+}
+template cudaError_t launch_apply_kin<float>(bool, const CellArgs<float> &, cudaStream_t);
+template cudaError_t launch_apply_kin<double>(bool, const CellArgs<double> &, cudaStream_t);
 template cudaError_t launch_apply_cell4<double>(bool, const CellArgs<double> &, cudaStream_t);
 template cudaError_t launch_apply_brick<double>(bool, const CellArgs<double> &, cudaStream_t);
 

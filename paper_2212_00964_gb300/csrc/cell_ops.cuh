@@ -18,6 +18,9 @@ cudaError_t launch_apply_brick(bool nh, const CellArgs<T> &a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_apply_cell4(bool nh, const CellArgs<T> &a, cudaStream_t s);
 
+template <typename T>
+cudaError_t launch_apply_kin(bool nh, const CellArgs<T> &a, cudaStream_t s);
+
 // Launch with programmatic stream serialisation (the kernel must begin with
 // pdl_wait() before it reads anything its predecessor wrote).
 template <typename... KArgs, typename... Args>

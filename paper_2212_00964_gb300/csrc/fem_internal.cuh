@@ -602,6 +602,67 @@ __device__ __forceinline__ void nh_dstress(const NHPoint<T> &q, const Mat<T> &m,
         }
 }
 
+// Neo-Hookean tangent data at one Gauss point of a fixed state, stored once
+// per Newton iteration so the CG apply skips nh_point: A = F^{-T} and four
+// scalars that fold the coefficients of nh_dstress,
+//   kA = a1 c + a3 (F:dF),  kF = a3 c,  a1 = (2/3) k1 I1/3 + kappa (2J-1) J,
+//   a3 = -(2/3) k1,  kdA = k1 I1/3 - kappa J (J-1),  c = A:dF.
+constexpr int KIN_VALUES = 13;  // A (9), k1, a1, a3, kdA
+template <typename T>
+struct NHKin {
+    T A[9];
+    T k1, a1, a3, kdA;
+};
+
+template <typename T>
+__device__ __forceinline__ void nh_kin(const NHPoint<T> &q, const Mat<T> &m, NHKin<T> &k)
+{
+#pragma unroll
+    for (int t = 0; t < 9; ++t) k.A[t] = q.A[t];
+    const T kI = q.k1 * q.I1 * (T)(1.0 / 3.0);
+    k.k1 = q.k1;
+    k.a1 = (T)(2.0 / 3.0) * kI + m.c2 * ((T)1 + (T)2 * q.Jm1) * q.J;
+    k.a3 = (T)(-2.0 / 3.0) * q.k1;
+    k.kdA = kI - m.c2 * q.J * q.Jm1;
+}
+
+// nh_dstress from stored tangent data and F = I + H.
+template <typename T>
+__device__ __forceinline__ void nh_dstress_kin(const NHKin<T> &k, const T *H, const T *dF, T *dP)
+{
+    const T *A = k.A;
+    T c = 0, fd = 0;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        c += A[t] * dF[t];
+        fd += (H[t] + ((t % 4) == 0 ? (T)1 : (T)0)) * dF[t];
+    }
+    const T kA = k.a1 * c + k.a3 * fd;
+    const T kF = k.a3 * c;
+    T M[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            M[3 * i + j] = A[3 * i] * dF[3 * j] + A[3 * i + 1] * dF[3 * j + 1] + A[3 * i + 2] * dF[3 * j + 2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const T MA = M[3 * i] * A[j] + M[3 * i + 1] * A[3 + j] + M[3 * i + 2] * A[6 + j];
+            const T Fij = H[3 * i + j] + (i == j ? (T)1 : (T)0);
+            dP[3 * i + j] = k.k1 * dF[3 * i + j] + kA * A[3 * i + j] + kF * Fij + k.kdA * MA;
+        }
+}
+
+// Slot of value v (0..8*KIN_VALUES-1) of instance-local cell `cell` in the
+// stored tangent data: [tile][v][CELL_BLOCK] over the global tiles, so a
+// warp's accesses to one value are 128 contiguous bytes.
+__device__ __forceinline__ int64_t kin_slot(int64_t tile_off, int cell, int v)
+{
+    return ((tile_off + cell / CELL_BLOCK) * (8 * KIN_VALUES) + v) * CELL_BLOCK + cell % CELL_BLOCK;
+}
+
 // Linear elasticity (also the SIMP-scaled law): P = lam tr(H) I + mu (H + H^T).
 template <typename T>
 __device__ __forceinline__ void le_stress(const T *H, const Mat<T> &m, T *P)

@@ -482,6 +482,7 @@ struct Buffers {
     T *x, *r, *z, *p, *q, *dg, *s;
     Ctl *tune;           // scratch control blocks for the apply autotuner (may be null)
     KernelClock *kclock; // live span statistics of the CG kernels (may be null)
+    T *kin;              // stored NH tangent data for apply kernel 4 (may be null)
 };
 
 struct Graphs {
@@ -592,6 +593,7 @@ class Core {
             ca.cell_param = b_.cpT;
             ca.u = b_.uT;
             ca.y = b_.dg;
+            ca.kin = variant_ == 4 ? b_.kin : nullptr;  // apply kernel 4 reads the stored tangent data
             if ((e = launch_cell<T>(CM_DIAG_CTL, pb_.nh, ca, s)) != cudaSuccess) return e;
         }
         k_pcg_init<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
@@ -652,6 +654,10 @@ class Core {
         }
         ca.n_tiles = pb_.n_tiles;
         if (variant_ == 3) return launch_apply_cell4<T>(pb_.nh, ca, s);
+        if (variant_ == 4) {
+            ca.kin = b_.kin;
+            return launch_apply_kin<T>(pb_.nh, ca, s);
+        }
         return launch_cell<T>(CM_APPLY_PCG, pb_.nh, ca, s);
     }
 
@@ -703,13 +709,21 @@ class Core {
             cudaEventDestroy(e0);
             return (cudaGetLastError(), 2);
         }
-        float best = 1e30f, times[3] = {-1.f, -1.f, -1.f};
+        float best = 1e30f, times[4] = {-1.f, -1.f, -1.f, -1.f};
         int choice = 1;
-        for (int v = 1; v <= 3; ++v) {
+        const int n_var = (pb_.nh && b_.kin) ? 4 : 3;
+        for (int v = 1; v <= n_var; ++v) {
             variant_ = v;
             // fresh control blocks for each variant (the apply's epilogue updates them)
             bool ok = cudaMemcpyAsync(b_.tune, tc.data(), sizeof(Ctl) * tc.size(), cudaMemcpyHostToDevice, s) ==
                       cudaSuccess;
+            if (ok && v == 4) {  // tangent data of the probe state (dg is rebuilt by every head graph)
+                CellArgs<T> cd = ca;
+                cd.n_tiles = pb_.n_tiles;
+                cd.y = b_.dg;
+                cd.kin = b_.kin;
+                ok = launch_cell<T>(CM_DIAG_CTL, pb_.nh, cd, s) == cudaSuccess;
+            }
             ok = ok && launch_apply(ca, s) == cudaSuccess;
             ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
             for (int r = 0; r < 3 && ok; ++r) ok = launch_apply(ca, s) == cudaSuccess;
@@ -733,8 +747,9 @@ class Core {
             if (env[0] == '1')
                 fprintf(stderr,
                         "femgb autotune: D=%lld instances=%d per-cell %.3f ms, bricks %.3f ms, "
-                        "per-cell(4 CTA/SM) %.3f ms -> %d\n",
-                        (long long)pb_.D, (int)pb_.desc.size(), times[0] / 3, times[1] / 3, times[2] / 3, choice);
+                        "per-cell(4 CTA/SM) %.3f ms, stored tangent %.3f ms -> %d\n",
+                        (long long)pb_.D, (int)pb_.desc.size(), times[0] / 3, times[1] / 3, times[2] / 3,
+                        times[3] / 3, choice);
         }
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = choice;
@@ -761,6 +776,7 @@ class Core {
     // array of 3 ints, with a pageable copy and a stream synchronisation).
     int run_direct(cudaStream_t s, double timeout_s, int *hc)
     {
+        if (int rc = check_variant()) return rc;
         warm_occupancy(pb_.nh);
         if (variant_ == 0) variant_ = 2;
         auto t0 = std::chrono::steady_clock::now();
@@ -826,8 +842,19 @@ class Core {
     }
 
     // Returns FEM_OK or an error; per-instance outcomes stay in the Ctl blocks.
+    // Apply kernel 4 needs a Neo-Hookean law and its tangent-data buffer.
+    int check_variant() const
+    {
+        if (variant_ == 4 && !(pb_.nh && b_.kin))
+            return (set_error("apply_kernel 4 (stored tangent data) needs a Neo-Hookean problem and its buffer "
+                              "(not available in fem_solve_static)"),
+                    FEM_ERR_ARG);
+        return FEM_OK;
+    }
+
     int run(cudaStream_t s, double timeout_s)
     {
+        if (int rc = check_variant()) return rc;
         Graphs G;
         warm_occupancy(pb_.nh);
         if (variant_ == 0) variant_ = autotune(s);
@@ -868,7 +895,8 @@ class Core {
 
     const double *ustar64_ = nullptr;  // linear mode: the fixed state
     int max_steps_ = 1;
-    int variant_ = 0;       // CG apply kernel: 0 autotune, 1 per-cell, 2 bricks, 3 per-cell at 4 CTA/SM
+    int variant_ = 0;       // CG apply kernel: 0 autotune, 1 per-cell, 2 bricks, 3 per-cell at 4 CTA/SM,
+                            // 4 per-cell on stored NH tangent data
     double apply_ms_ = 0;   // sampled device time of CG applies
     int apply_samples_ = 0;
     double update_ms_ = 0;  // sampled device time of CG vector updates
@@ -915,7 +943,7 @@ static int check_options(const fem_options &o)
         return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
     if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
         !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
-        o.apply_kernel < 0 || o.apply_kernel > 3)
+        o.apply_kernel < 0 || o.apply_kernel > 4)
         return (set_error("invalid solver options"), FEM_ERR_ARG);
     return FEM_OK;
 }
@@ -943,7 +971,7 @@ static cudaError_t join_streams(cudaStream_t from, cudaStream_t to)
 // Workspace slots
 enum {
     WS_CTL = 0, WS_CNT, WS_R64, WS_UT, WS_X, WS_R, WS_Z, WS_P, WS_Q, WS_DG, WS_LAM, WS_TAB, WS_CPT,
-    WS_U64CAT, WS_MASKCAT, WS_UBARCAT, WS_RHSCAT, WS_CP64CAT, WS_G64, WS_S, WS_TUNE, WS_KCLOCK
+    WS_U64CAT, WS_MASKCAT, WS_UBARCAT, WS_RHSCAT, WS_CP64CAT, WS_G64, WS_S, WS_TUNE, WS_KCLOCK, WS_KIN
 };
 
 template <typename T>
@@ -967,6 +995,9 @@ static int alloc_buffers(Workspace &ws, const Problem &pb, Buffers<T> &b, bool n
     WSGET(b.s, WS_S, T, D);
     WSGET(b.tune, WS_TUNE, Ctl, n);
     WSGET(b.kclock, WS_KCLOCK, KernelClock, 1);
+    // stored tangent data (8 Gauss points x KIN_VALUES per cell slot); optional:
+    // without it apply kernel 4 is not offered
+    b.kin = pb.nh ? (T *)ws.get(WS_KIN, sizeof(T) * (size_t)pb.n_tiles * 8 * KIN_VALUES * CELL_BLOCK) : nullptr;
     if (n > 1) WSGET(b.tab, WS_TAB, InstDesc, n);
     else b.tab = nullptr;
     if (need_uT) WSGET(b.uT, WS_UT, T, D);

@@ -71,11 +71,12 @@ def test_c0_linear_elastic_mixed_refined():
     assert rel_l2(u, ref) <= TOL_REFINED
 
 
-@pytest.mark.parametrize("apply_kernel", [1, 2, 3])
+@pytest.mark.parametrize("apply_kernel", [1, 2, 3, 4])
 @pytest.mark.parametrize("n", [4, 8, 9])
 def test_neohooke_load_steps(n, apply_kernel):
-    """Both CG apply kernels (per-cell scatter, 8x4x4 bricks); 9^3 leaves
-    ragged bricks in every direction."""
+    """Every CG apply kernel (per-cell scatter at 3 and 4 CTAs/SM, 8x4x4
+    bricks, per-cell on stored tangent data); 9^3 leaves ragged bricks in
+    every direction and a ragged last cell tile."""
     w = inputs.c1(n=n, n_steps=10)
     ref = oracle_c1(n)
     u64, st64 = gpu_solve(w, 0, newton_rtol=1e-13, pcg_rtol=1e-8, apply_kernel=apply_kernel)
@@ -107,6 +108,16 @@ def test_simp_cantilever_small(apply_kernel):
     assert rel_l2(u, ref) <= TOL_REFINED
     u64, st64 = gpu_solve(w, 0, newton_rtol=1e-13, pcg_rtol=1e-9, apply_kernel=apply_kernel)
     assert rel_l2(u64, ref) <= TOL_FP64
+
+
+def test_stored_tangent_kernel_needs_neohooke():
+    """Apply kernel 4 is refused (argument error, nothing launched) for a
+    linear-elastic problem."""
+    w = inputs.c0()
+    F = fem()
+    with pytest.raises(F.FemError) as ei:
+        gpu_solve(w, 2, apply_kernel=4)
+    assert ei.value.status == -1  # FEM_ERR_ARG
 
 
 def test_deterministic_repeat():
