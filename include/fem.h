@@ -80,6 +80,10 @@ typedef struct {
 
 /* ------------------------------------------------------------------ mesh -- */
 #define FEM_MESH_CSR 1 /* also build the CSR pattern and scatter map (Algorithm 1) */
+#define FEM_MESH_DETERMINISTIC 2 /* fem_residual, fem_tangent_apply and fem_tangent_diag
+                                    on this mesh scatter colour by colour with plain
+                                    stores (cells of one colour share no node), so their
+                                    results are bit-reproducible; default: atomics */
 
 /* Build a structured box mesh on the device (the paper's linear hexahedra,
  * Sec. 3.1): connectivity, coordinates, the 8-colour cell colouring and,
@@ -165,7 +169,7 @@ typedef struct {
                             4 = as 1 on Neo-Hookean tangent data stored once per
                                 Newton iteration (Neo-Hookean only; not in
                                 fem_solve_static) */
-    int deterministic;   /* 1: colour-ordered scatter (bit-reproducible), 0: atomics */
+    int reserved;        /* must be 0 (bit-reproducible cell operators: FEM_MESH_DETERMINISTIC) */
     double timeout_s;    /* host watchdog for one solve (0 = none) */
 } fem_options;
 

@@ -218,6 +218,26 @@ __global__ void k_csr_diag_ones(const uint8_t *mask, const int32_t *row_ptr, con
 
 static int vgrid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
 
+// A cell operator over the whole mesh: one launch with atomic scatter, or,
+// on a FEM_MESH_DETERMINISTIC mesh, eight launches over the colour classes
+// (a2) with plain read-modify-write scatter, which fixes the order of the
+// additions into every node.
+template <typename T>
+static cudaError_t launch_mesh_op(int mode, bool nh, fem_mesh_t m, CellArgs<T> a, cudaStream_t s)
+{
+    if (!m->det) return launch_cell<T>(mode, nh, a, s);
+    for (int c = 0; c < 8; ++c) {
+        const int64_t n = m->colour_ptr_h[c + 1] - m->colour_ptr_h[c];
+        if (n == 0) continue;
+        a.cells = m->cell_perm + m->colour_ptr_h[c];
+        a.n_list = n;
+        a.n_tiles = (n + CELL_BLOCK - 1) / CELL_BLOCK;
+        a.plain_store = 1;
+        if (cudaError_t e = launch_cell<T>(mode, nh, a, s)) return e;
+    }
+    return cudaSuccess;
+}
+
 template <typename T>
 static int residual_t(fem_mesh_t m, const fem_material *mat, const T *u, const T *cp, const uint8_t *mask,
                       const T *f, T *r, cudaStream_t s)
@@ -229,7 +249,7 @@ static int residual_t(fem_mesh_t m, const fem_material *mat, const T *u, const T
     a.d0 = make_desc(m, mat);
     a.n_tiles = (m->n_cells + CELL_BLOCK - 1) / CELL_BLOCK;
     a.u = u; a.y = r; a.cell_param = cp; a.jflag = nullptr;
-    FEM_CUDA(launch_cell<T>(CM_RESIDUAL, mat->kind == FEM_NEOHOOKE, a, s));
+    FEM_CUDA(launch_mesh_op<T>(CM_RESIDUAL, mat->kind == FEM_NEOHOOKE, m, a, s));
     if (mask) {
         k_fix_mask<T><<<vgrid(D), 256, 0, s>>>(r, nullptr, mask, D, 0);
         count_launch();
@@ -248,7 +268,7 @@ static int apply_t(fem_mesh_t m, const fem_material *mat, const T *u, const T *c
     a.d0 = make_desc(m, mat);
     a.n_tiles = (m->n_cells + CELL_BLOCK - 1) / CELL_BLOCK;
     a.u = u; a.x = x; a.y = y; a.cell_param = cp; a.mask = mask;
-    FEM_CUDA(launch_cell<T>(CM_APPLY, mat->kind == FEM_NEOHOOKE, a, s));
+    FEM_CUDA(launch_mesh_op<T>(CM_APPLY, mat->kind == FEM_NEOHOOKE, m, a, s));
     if (mask) {
         k_fix_mask<T><<<vgrid(D), 256, 0, s>>>(y, x, mask, D, 1);
         count_launch();
@@ -267,7 +287,7 @@ static int diag_t(fem_mesh_t m, const fem_material *mat, const T *u, const T *cp
     a.d0 = make_desc(m, mat);
     a.n_tiles = (m->n_cells + CELL_BLOCK - 1) / CELL_BLOCK;
     a.u = u; a.y = dg; a.cell_param = cp;
-    FEM_CUDA(launch_cell<T>(CM_DIAG, mat->kind == FEM_NEOHOOKE, a, s));
+    FEM_CUDA(launch_mesh_op<T>(CM_DIAG, mat->kind == FEM_NEOHOOKE, m, a, s));
     if (mask) {
         k_fix_mask<T><<<vgrid(D), 256, 0, s>>>(dg, nullptr, mask, D, 2);
         count_launch();

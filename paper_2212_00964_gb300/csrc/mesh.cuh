@@ -53,6 +53,7 @@ struct fem_mesh_s {
     int32_t *cell_perm = nullptr;
     int32_t *row_ptr = nullptr;
     int32_t *col = nullptr;
+    bool det = false;  // FEM_MESH_DETERMINISTIC: colour-ordered cell operators
     femgb::Workspace ws;
     std::mutex mu;  // one solve per handle at a time
 

@@ -943,7 +943,7 @@ static int check_options(const fem_options &o)
         return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
     if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
         !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
-        o.apply_kernel < 0 || o.apply_kernel > 4)
+        o.apply_kernel < 0 || o.apply_kernel > 4 || o.reserved != 0)
         return (set_error("invalid solver options"), FEM_ERR_ARG);
     return FEM_OK;
 }

@@ -23,6 +23,7 @@ FEM_ERR_BREAKDOWN, FEM_ERR_NONFINITE, FEM_ERR_TIMEOUT, FEM_ERR_NOMEM = -5, -6, -
 FEM_LINEAR, FEM_SIMP, FEM_NEOHOOKE = 0, 1, 2
 FEM_FP64, FEM_FP32, FEM_MIXED = 0, 1, 2
 FEM_MESH_CSR = 1
+FEM_MESH_DETERMINISTIC = 2
 FACES = {"x0": 0, "x1": 1, "y0": 2, "y1": 3, "z0": 4, "z1": 5}
 
 
@@ -42,7 +43,7 @@ class fem_options(ctypes.Structure):
                 ("newton_atol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
                 ("pcg_rtol", ctypes.c_double), ("pcg_maxit", ctypes.c_int),
                 ("pcg_chunk", ctypes.c_int), ("step_begin", ctypes.c_int),
-                ("apply_kernel", ctypes.c_int), ("deterministic", ctypes.c_int),
+                ("apply_kernel", ctypes.c_int), ("reserved", ctypes.c_int),
                 ("timeout_s", ctypes.c_double)]
 
 
@@ -183,10 +184,10 @@ class Mesh:
             pass
 
 
-def fem_mesh(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, csr=False, stream=None) -> Mesh:
+def fem_mesh(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, csr=False, stream=None, deterministic=False) -> Mesh:
     h = ctypes.c_void_p()
-    _check(lib().fem_mesh(nx, ny, nz, lx, ly, lz, FEM_MESH_CSR if csr else 0, _stream(stream), ctypes.byref(h)),
-           "fem_mesh")
+    flags = (FEM_MESH_CSR if csr else 0) | (FEM_MESH_DETERMINISTIC if deterministic else 0)
+    _check(lib().fem_mesh(nx, ny, nz, lx, ly, lz, flags, _stream(stream), ctypes.byref(h)), "fem_mesh")
     return Mesh(h, nx, ny, nz, lx, ly, lz, csr)
 
 
