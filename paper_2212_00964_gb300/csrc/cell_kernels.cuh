@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
 #pragma unroll
                 for (int n = 0; n < 8; ++n) ye[c][n] = 0;
             bool inverted = false;
+            T pdh = 0;  // sum over Gauss points of dP : dH (CG apply), weighted once per cell
 
 #pragma unroll
             for (int gp = 0; gp < 8; ++gp) {
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                     if (MODE == CM_APPLY_PCG) {
                         // x_e . K_e x_e = sum_gp w detJ dP : dH
 #pragma unroll
-                        for (int t = 0; t < 9; ++t) part += wl * P[t] * dH[t];
+                        for (int t = 0; t < 9; ++t) pdh += P[t] * dH[t];
                     }
                 }
                 if (IS_RES || IS_APPLY) {
@@ -303,6 +304,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                     }
                 }
             }
+            if (MODE == CM_APPLY_PCG) part += wl * pdh;
             if (IS_RES || IS_APPLY) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) grad_sf_t<T>(S[c], ihx * wdet, ihy * wdet, ihz * wdet, ye[c]);
@@ -459,6 +461,7 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
                 for (int dd = 0; dd < 3; ++dd)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) S[c][dd][q] = 0;
+            T pdh = 0;
 #pragma unroll
             for (int gp = 0; gp < 8; ++gp) {
                 const int al = gp & 1, be = (gp >> 1) & 1, ga = gp >> 2;
@@ -480,7 +483,7 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
                     le_stress<T>(dH, m, P);
                 }
 #pragma unroll
-                for (int t = 0; t < 9; ++t) part += wdet * P[t] * dH[t];
+                for (int t = 0; t < 9; ++t) pdh += P[t] * dH[t];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     S[c][0][be + 2 * ga] += P[3 * c + 0];
@@ -488,6 +491,7 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
                     S[c][2][al + 2 * be] += P[3 * c + 2];
                 }
             }
+            part += wdet * pdh;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 T ye[8];

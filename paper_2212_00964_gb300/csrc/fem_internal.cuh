@@ -528,11 +528,13 @@ __device__ __forceinline__ double rcbrt_t(double x)
     return x < 0 ? -r : r;
 }
 
-// Neo-Hookean kinematics at one Gauss point: A = F^{-T}, J, J-1, I1, G J^{-2/3}.
+// Neo-Hookean kinematics at one Gauss point: the cofactor matrix cof(F)
+// (A = F^{-T} = cof / J is never formed: every use folds 1/J into a scalar
+// coefficient), J, J-1, 1/J, I1 and G J^{-2/3}.
 template <typename T>
 struct NHPoint {
-    T F[9], A[9];
-    T J, Jm1, I1, k1;
+    T F[9], C[9];  // C = cof(F) = J F^{-T}
+    T J, Jm1, iJ, I1, k1;
 };
 
 template <typename T>
@@ -541,21 +543,20 @@ __device__ __forceinline__ void nh_point(const T *H, const Mat<T> &m, NHPoint<T>
 #pragma unroll
     for (int t = 0; t < 9; ++t) q.F[t] = H[t] + ((t % 4) == 0 ? (T)1 : (T)0);
     const T *F = q.F;
-    T c00 = F[4] * F[8] - F[5] * F[7], c01 = F[5] * F[6] - F[3] * F[8], c02 = F[3] * F[7] - F[4] * F[6];
-    T c10 = F[2] * F[7] - F[1] * F[8], c11 = F[0] * F[8] - F[2] * F[6], c12 = F[1] * F[6] - F[0] * F[7];
-    T c20 = F[1] * F[5] - F[2] * F[4], c21 = F[2] * F[3] - F[0] * F[5], c22 = F[0] * F[4] - F[1] * F[3];
+    T *C = q.C;
+    C[0] = F[4] * F[8] - F[5] * F[7]; C[1] = F[5] * F[6] - F[3] * F[8]; C[2] = F[3] * F[7] - F[4] * F[6];
+    C[3] = F[2] * F[7] - F[1] * F[8]; C[4] = F[0] * F[8] - F[2] * F[6]; C[5] = F[1] * F[6] - F[0] * F[7];
+    C[6] = F[1] * F[5] - F[2] * F[4]; C[7] = F[2] * F[3] - F[0] * F[5]; C[8] = F[0] * F[4] - F[1] * F[3];
     q.Jm1 = det_ipH_m1(H);
     q.J = (T)1 + q.Jm1;
     const T r = rcbrt_t(q.J);  // J^{-1/3}: J^{-2/3} = r^2 and 1/J = r^3 without a division
-    const T iJ = r * r * r;
-    q.A[0] = c00 * iJ; q.A[1] = c01 * iJ; q.A[2] = c02 * iJ;
-    q.A[3] = c10 * iJ; q.A[4] = c11 * iJ; q.A[5] = c12 * iJ;
-    q.A[6] = c20 * iJ; q.A[7] = c21 * iJ; q.A[8] = c22 * iJ;
+    const T r2 = r * r;
+    q.iJ = r2 * r;
     T I1 = 0;
 #pragma unroll
     for (int t = 0; t < 9; ++t) I1 += F[t] * F[t];
     q.I1 = I1;
-    q.k1 = m.c1 * r * r;  // G J^{-2/3}
+    q.k1 = m.c1 * r2;  // G J^{-2/3}
 }
 
 // First Piola-Kirchhoff stress P = G J^{-2/3} (F - I1/3 A) + kappa J (J-1) A.
@@ -564,41 +565,45 @@ __device__ __forceinline__ void nh_stress(const NHPoint<T> &q, const Mat<T> &m, 
 {
     T a = q.k1 * q.I1 * (T)(1.0 / 3.0);
     T b = m.c2 * q.J * q.Jm1;
+    const T bc = (b - a) * q.iJ;  // coefficient of cof(F)
 #pragma unroll
-    for (int t = 0; t < 9; ++t) P[t] = q.k1 * q.F[t] + (b - a) * q.A[t];
+    for (int t = 0; t < 9; ++t) P[t] = q.k1 * q.F[t] + bc * q.C[t];
 }
 
 // dP = k1 dF + kA A + kF F + kdA dA with dA = -A dF^T A, c = A:dF, dI1 = 2F:dF,
 // kA = k1 (-dI1/3 + 2/9 c I1) + kappa (2J-1) J c, kF = -2/3 k1 c,
 // kdA = kappa J (J-1) - k1 I1/3  (directional derivative of nh_stress).
+// With A = cof/J: c = (cof:dF)/J, kA A = (kA/J) cof, dA = -(cof dF^T cof)/J^2.
 template <typename T>
 __device__ __forceinline__ void nh_dstress(const NHPoint<T> &q, const Mat<T> &m, const T *dF, T *dP)
 {
-    T c = 0, dI1 = 0;
+    const T *C = q.C;
+    T cc = 0, dI1 = 0;
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
-        c += q.A[t] * dF[t];
+        cc += C[t] * dF[t];
         dI1 += q.F[t] * dF[t];
     }
+    const T c = cc * q.iJ;
     dI1 *= (T)2;
-    const T *A = q.A;
-    // M = A dF^T  (M_ij = sum_k A_ik dF_jk)
+    // M = cof dF^T  (M_ij = sum_k C_ik dF_jk)
     T M[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
-            M[3 * i + j] = A[3 * i] * dF[3 * j] + A[3 * i + 1] * dF[3 * j + 1] + A[3 * i + 2] * dF[3 * j + 2];
-    T kA = q.k1 * ((T)(2.0 / 9.0) * c * q.I1 - dI1 * (T)(1.0 / 3.0)) + m.c2 * ((T)1 + (T)2 * q.Jm1) * q.J * c;
-    T kF = (T)(-2.0 / 3.0) * q.k1 * c;
-    T kdA = q.k1 * q.I1 * (T)(1.0 / 3.0) - m.c2 * q.J * q.Jm1;  // = -(coefficient of dA)
+            M[3 * i + j] = C[3 * i] * dF[3 * j] + C[3 * i + 1] * dF[3 * j + 1] + C[3 * i + 2] * dF[3 * j + 2];
+    const T kA = q.k1 * ((T)(2.0 / 9.0) * c * q.I1 - dI1 * (T)(1.0 / 3.0)) + m.c2 * ((T)1 + (T)2 * q.Jm1) * q.J * c;
+    const T kF = (T)(-2.0 / 3.0) * q.k1 * c;
+    const T kdA = q.k1 * q.I1 * (T)(1.0 / 3.0) - m.c2 * q.J * q.Jm1;  // = -(coefficient of dA)
+    const T kC = kA * q.iJ;                                              // coefficient of cof
+    const T kM = kdA * q.iJ * q.iJ;                                      // coefficient of cof dF^T cof
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            // (M A)_ij, dA = -(M A); dP += coef(dA) * dA = kdA * (M A)
-            T MA = M[3 * i] * A[j] + M[3 * i + 1] * A[3 + j] + M[3 * i + 2] * A[6 + j];
-            dP[3 * i + j] = q.k1 * dF[3 * i + j] + kA * A[3 * i + j] + kF * q.F[3 * i + j] + kdA * MA;
+            const T MC = M[3 * i] * C[j] + M[3 * i + 1] * C[3 + j] + M[3 * i + 2] * C[6 + j];
+            dP[3 * i + j] = q.k1 * dF[3 * i + j] + kC * C[3 * i + j] + kF * q.F[3 * i + j] + kM * MC;
         }
 }
 
@@ -618,7 +623,7 @@ template <typename T>
 __device__ __forceinline__ void nh_kin(const NHPoint<T> &q, const Mat<T> &m, NHKin<T> &k)
 {
 #pragma unroll
-    for (int t = 0; t < 9; ++t) k.A[t] = q.A[t];
+    for (int t = 0; t < 9; ++t) k.A[t] = q.C[t] * q.iJ;
     const T kI = q.k1 * q.I1 * (T)(1.0 / 3.0);
     k.k1 = q.k1;
     k.a1 = (T)(2.0 / 3.0) * kI + m.c2 * ((T)1 + (T)2 * q.Jm1) * q.J;
