@@ -36,11 +36,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "tangent-apply GDOF/s and Newton solve time, 64^3 Neo-Hookean, mixed vs FP64"
-# Algorithmic FP32 flops per cell of one Neo-Hookean CG tangent apply
-# (sum-factorised gradients of u and x: 576; 8 Gauss points x (kinematics 94 +
-# directional stress derivative 206 + flux accumulation 9) = 2472; transpose
-# 360 + 3; p.Kp 48; assembly adds 24).  FMA = 2 flops.
-NH_APPLY_FLOPS_PER_CELL = 3483
+# Algorithmic FP32 flops per cell of one Neo-Hookean CG tangent apply, FMA = 2:
+#   sum-factorised gradients of u and x            6 x 96 =   576
+#   per Gauss point: kinematics (F, cof F, J - 1, J^-1/3, I1, k1) 87,
+#     tangent coefficients 10, dP = dk1 F + k1 dF + dbeta cof + beta dcof 164,
+#     p.Kp partial 18, flux accumulation 9          8 x 288 = 2,304
+#   transposed gradients 3 x 120 + 3                           363
+#   p.Kp weight 2, assembly adds 24                              26
+NH_APPLY_FLOPS_PER_CELL = 3269
 # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Bytes a launch must move (u, x read; y written; FP32): 12 * D.

@@ -226,11 +226,11 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                         const T *kb = a.kin + kin_slot(d.tile_off, cell, gp * KIN_VALUES);
                         NHKin<T> kq;
 #pragma unroll
-                        for (int t = 0; t < 9; ++t) kq.A[t] = kb[t * CELL_BLOCK];
+                        for (int t = 0; t < 9; ++t) kq.C[t] = kb[t * CELL_BLOCK];
                         kq.k1 = kb[9 * CELL_BLOCK];
-                        kq.a1 = kb[10 * CELL_BLOCK];
-                        kq.a3 = kb[11 * CELL_BLOCK];
-                        kq.kdA = kb[12 * CELL_BLOCK];
+                        kq.beta = kb[10 * CELL_BLOCK];
+                        kq.e1 = kb[11 * CELL_BLOCK];
+                        kq.e2 = kb[12 * CELL_BLOCK];
                         nh_dstress_kin<T>(kq, H, dH, P);
                     } else if (NH) {
                         NHPoint<T> q;
@@ -263,11 +263,11 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                             nh_kin<T>(q, m, kq);
                             T *kb = a.kin + kin_slot(d.tile_off, cell, gp * KIN_VALUES);
 #pragma unroll
-                            for (int t = 0; t < 9; ++t) kb[t * CELL_BLOCK] = kq.A[t];
+                            for (int t = 0; t < 9; ++t) kb[t * CELL_BLOCK] = kq.C[t];
                             kb[9 * CELL_BLOCK] = kq.k1;
-                            kb[10 * CELL_BLOCK] = kq.a1;
-                            kb[11 * CELL_BLOCK] = kq.a3;
-                            kb[12 * CELL_BLOCK] = kq.kdA;
+                            kb[10 * CELL_BLOCK] = kq.beta;
+                            kb[11 * CELL_BLOCK] = kq.e1;
+                            kb[12 * CELL_BLOCK] = kq.e2;
                         }
                     }
                     T Crow[3][3][3];  // [i][l][j]

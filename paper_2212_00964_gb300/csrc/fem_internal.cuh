@@ -559,105 +559,103 @@ __device__ __forceinline__ void nh_point(const T *H, const Mat<T> &m, NHPoint<T>
     q.k1 = m.c1 * r2;  // G J^{-2/3}
 }
 
-// First Piola-Kirchhoff stress P = G J^{-2/3} (F - I1/3 A) + kappa J (J-1) A.
+// First Piola-Kirchhoff stress P = G J^{-2/3} (F - I1/3 A) + kappa J (J-1) A
+// with A = F^{-T} = cof(F)/J, written as P = k1 F + beta cof(F),
+// beta = kappa (J-1) - k1 I1 / (3J).
+template <typename T>
+__device__ __forceinline__ T nh_beta(const NHPoint<T> &q, const Mat<T> &m)
+{
+    return m.c2 * q.Jm1 - (T)(1.0 / 3.0) * (q.k1 * q.iJ) * q.I1;
+}
+
 template <typename T>
 __device__ __forceinline__ void nh_stress(const NHPoint<T> &q, const Mat<T> &m, T *P)
 {
-    T a = q.k1 * q.I1 * (T)(1.0 / 3.0);
-    T b = m.c2 * q.J * q.Jm1;
-    const T bc = (b - a) * q.iJ;  // coefficient of cof(F)
+    const T beta = nh_beta(q, m);
 #pragma unroll
-    for (int t = 0; t < 9; ++t) P[t] = q.k1 * q.F[t] + bc * q.C[t];
+    for (int t = 0; t < 9; ++t) P[t] = q.k1 * q.F[t] + beta * q.C[t];
 }
 
-// dP = k1 dF + kA A + kF F + kdA dA with dA = -A dF^T A, c = A:dF, dI1 = 2F:dF,
-// kA = k1 (-dI1/3 + 2/9 c I1) + kappa (2J-1) J c, kF = -2/3 k1 c,
-// kdA = kappa J (J-1) - k1 I1/3  (directional derivative of nh_stress).
-// With A = cof/J: c = (cof:dF)/J, kA A = (kA/J) cof, dA = -(cof dF^T cof)/J^2.
+// Directional derivative of cof(F) along dF: each entry of cof(F) is a 2x2
+// minor f_a f_b - f_c f_e of F, so its derivative is bilinear in (F, dF).
+template <typename T>
+__device__ __forceinline__ void dcof(const T *F, const T *dF, T *dC)
+{
+#define FEMGB_DM(a, b, c, e) (F[a] * dF[b] + dF[a] * F[b] - F[c] * dF[e] - dF[c] * F[e])
+    dC[0] = FEMGB_DM(4, 8, 5, 7); dC[1] = FEMGB_DM(5, 6, 3, 8); dC[2] = FEMGB_DM(3, 7, 4, 6);
+    dC[3] = FEMGB_DM(2, 7, 1, 8); dC[4] = FEMGB_DM(0, 8, 2, 6); dC[5] = FEMGB_DM(1, 6, 0, 7);
+    dC[6] = FEMGB_DM(1, 5, 2, 4); dC[7] = FEMGB_DM(2, 3, 0, 5); dC[8] = FEMGB_DM(0, 4, 1, 3);
+#undef FEMGB_DM
+}
+
+// Consistent tangent of nh_stress along dF (the Gateaux derivative of
+// Eq. (5) at one Gauss point), from P = k1 F + beta cof(F):
+//   dP = dk1 F + k1 dF + dbeta cof(F) + beta dcof(F)[dF],
+//   dJ = cof(F):dF,  dk1 = -(2/3) (k1/J) dJ,
+//   dbeta = (kappa + (5/9) k1 I1 / J^2) dJ - (2/3) (k1/J) F:dF.
+// The oracle's closed form (A dF^T A route) is the same derivative.
+template <typename T>
+__device__ __forceinline__ void nh_dstress_c(const T *F, const T *C, T k1, T beta, T e1, T e2, const T *dF, T *dP)
+{
+    T dJ = 0, fd = 0;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        dJ += C[t] * dF[t];
+        fd += F[t] * dF[t];
+    }
+    const T dk1 = e2 * dJ;
+    const T dbeta = e1 * dJ + e2 * fd;
+    T dC[9];
+    dcof(F, dF, dC);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) dP[t] = dk1 * F[t] + k1 * dF[t] + dbeta * C[t] + beta * dC[t];
+}
+
+// Scalar coefficients of nh_dstress_c at one Gauss point.
+template <typename T>
+__device__ __forceinline__ void nh_dcoef(const NHPoint<T> &q, const Mat<T> &m, T &beta, T &e1, T &e2)
+{
+    const T k1iJ = q.k1 * q.iJ;
+    beta = m.c2 * q.Jm1 - (T)(1.0 / 3.0) * k1iJ * q.I1;
+    e1 = m.c2 + (T)(5.0 / 9.0) * (k1iJ * q.iJ) * q.I1;
+    e2 = (T)(-2.0 / 3.0) * k1iJ;
+}
+
 template <typename T>
 __device__ __forceinline__ void nh_dstress(const NHPoint<T> &q, const Mat<T> &m, const T *dF, T *dP)
 {
-    const T *C = q.C;
-    T cc = 0, dI1 = 0;
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        cc += C[t] * dF[t];
-        dI1 += q.F[t] * dF[t];
-    }
-    const T c = cc * q.iJ;
-    dI1 *= (T)2;
-    // M = cof dF^T  (M_ij = sum_k C_ik dF_jk)
-    T M[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            M[3 * i + j] = C[3 * i] * dF[3 * j] + C[3 * i + 1] * dF[3 * j + 1] + C[3 * i + 2] * dF[3 * j + 2];
-    const T kA = q.k1 * ((T)(2.0 / 9.0) * c * q.I1 - dI1 * (T)(1.0 / 3.0)) + m.c2 * ((T)1 + (T)2 * q.Jm1) * q.J * c;
-    const T kF = (T)(-2.0 / 3.0) * q.k1 * c;
-    const T kdA = q.k1 * q.I1 * (T)(1.0 / 3.0) - m.c2 * q.J * q.Jm1;  // = -(coefficient of dA)
-    const T kC = kA * q.iJ;                                              // coefficient of cof
-    const T kM = kdA * q.iJ * q.iJ;                                      // coefficient of cof dF^T cof
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const T MC = M[3 * i] * C[j] + M[3 * i + 1] * C[3 + j] + M[3 * i + 2] * C[6 + j];
-            dP[3 * i + j] = q.k1 * dF[3 * i + j] + kC * C[3 * i + j] + kF * q.F[3 * i + j] + kM * MC;
-        }
+    T beta, e1, e2;
+    nh_dcoef(q, m, beta, e1, e2);
+    nh_dstress_c(q.F, q.C, q.k1, beta, e1, e2, dF, dP);
 }
 
 // Neo-Hookean tangent data at one Gauss point of a fixed state, stored once
-// per Newton iteration so the CG apply skips nh_point: A = F^{-T} and four
-// scalars that fold the coefficients of nh_dstress,
-//   kA = a1 c + a3 (F:dF),  kF = a3 c,  a1 = (2/3) k1 I1/3 + kappa (2J-1) J,
-//   a3 = -(2/3) k1,  kdA = k1 I1/3 - kappa J (J-1),  c = A:dF.
-constexpr int KIN_VALUES = 13;  // A (9), k1, a1, a3, kdA
+// per Newton iteration so the CG apply skips nh_point: cof(F) and the four
+// scalars of nh_dstress_c (F itself is rebuilt from the gathered state).
+constexpr int KIN_VALUES = 13;  // cof(F) (9), k1, beta, e1, e2
 template <typename T>
 struct NHKin {
-    T A[9];
-    T k1, a1, a3, kdA;
+    T C[9];
+    T k1, beta, e1, e2;
 };
 
 template <typename T>
 __device__ __forceinline__ void nh_kin(const NHPoint<T> &q, const Mat<T> &m, NHKin<T> &k)
 {
 #pragma unroll
-    for (int t = 0; t < 9; ++t) k.A[t] = q.C[t] * q.iJ;
-    const T kI = q.k1 * q.I1 * (T)(1.0 / 3.0);
+    for (int t = 0; t < 9; ++t) k.C[t] = q.C[t];
     k.k1 = q.k1;
-    k.a1 = (T)(2.0 / 3.0) * kI + m.c2 * ((T)1 + (T)2 * q.Jm1) * q.J;
-    k.a3 = (T)(-2.0 / 3.0) * q.k1;
-    k.kdA = kI - m.c2 * q.J * q.Jm1;
+    nh_dcoef(q, m, k.beta, k.e1, k.e2);
 }
 
 // nh_dstress from stored tangent data and F = I + H.
 template <typename T>
 __device__ __forceinline__ void nh_dstress_kin(const NHKin<T> &k, const T *H, const T *dF, T *dP)
 {
-    const T *A = k.A;
-    T c = 0, fd = 0;
+    T F[9];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        c += A[t] * dF[t];
-        fd += (H[t] + ((t % 4) == 0 ? (T)1 : (T)0)) * dF[t];
-    }
-    const T kA = k.a1 * c + k.a3 * fd;
-    const T kF = k.a3 * c;
-    T M[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            M[3 * i + j] = A[3 * i] * dF[3 * j] + A[3 * i + 1] * dF[3 * j + 1] + A[3 * i + 2] * dF[3 * j + 2];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const T MA = M[3 * i] * A[j] + M[3 * i + 1] * A[3 + j] + M[3 * i + 2] * A[6 + j];
-            const T Fij = H[3 * i + j] + (i == j ? (T)1 : (T)0);
-            dP[3 * i + j] = k.k1 * dF[3 * i + j] + kA * A[3 * i + j] + kF * Fij + k.kdA * MA;
-        }
+    for (int t = 0; t < 9; ++t) F[t] = H[t] + ((t % 4) == 0 ? (T)1 : (T)0);
+    nh_dstress_c(F, k.C, k.k1, k.beta, k.e1, k.e2, dF, dP);
 }
 
 // Slot of value v (0..8*KIN_VALUES-1) of instance-local cell `cell` in the
