@@ -24,6 +24,7 @@ collective on the data path.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -44,10 +45,29 @@ METRIC = "tangent-apply GDOF/s and Newton solve time, 64^3 Neo-Hookean, mixed vs
 #   transposed gradients 3 x 120 + 3                           363
 #   p.Kp weight 2, assembly adds 24                              26
 NH_APPLY_FLOPS_PER_CELL = 3269
+# DRAM bytes (read + write) of one launch of the per-cell CG apply
+# (apply kernel 1) from the ncu capture summarised in
+# profiles/cg_apply_nh64_cell_kernel.md.  Valid only for the kernel sources it
+# was taken on: reported as null once their hash changes.
+APPLY_TRAFFIC_BYTES = 9.950208e6
+APPLY_TRAFFIC_SOURCES = ("paper_2212_00964_gb300/csrc/cell_kernels.cuh", "paper_2212_00964_gb300/csrc/fem_internal.cuh")
+APPLY_TRAFFIC_SHA256 = "7a7223ccedac2012838ae61a6f08aaf055d8542321f9dd4cb66b3957311555bf"
 # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Bytes a launch must move (u, x read; y written; FP32): 12 * D.
 SAMPLE_N = 8
+
+
+def apply_traffic(kernel_id):
+    """ncu DRAM bytes per launch of the timed apply kernel, or None when the
+    capture does not describe the kernel that ran."""
+    if kernel_id != 1:
+        return None
+    h = hashlib.sha256()
+    for f in APPLY_TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return APPLY_TRAFFIC_BYTES if h.hexdigest() == APPLY_TRAFFIC_SHA256 else None
 
 
 def parse():
@@ -409,7 +429,7 @@ def run_gb300(args):
                                 3: "cell_kernel<float,NH,CM_APPLY_PCG,4>",
                                 4: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN>"}.get(st0.get("apply_kernel"), "?"),
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": apply_traffic(st0.get("apply_kernel")),
                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
                      "launch_us": t_apply * 1e6, "launches_per_step": apply_launches,
                      "time_share": share, "hbm_gbs_algorithmic": 12 * D / t_apply / 1e9,
