@@ -37,7 +37,6 @@ struct CellArgs {
     Ctl *ctl;               // control blocks (gated modes)
     int iter;               // CG iteration inside the current graph chunk
     int pcg_maxit;          // CG iteration cap (CG apply)
-    int *arrive;            // arrival counter of the CG apply (last-block epilogue)
     KernelClock *kclock;    // live span statistics of the CG apply (may be null)
     T *g;                   // VJP output [Ne]
     int *jflag;             // det F <= 0 flag (ungated residual)
@@ -71,9 +70,19 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
     // (go, slot) of the instance looked up last: fixed for one launch, so it
     // is read once per instance rather than once per tile
     int ctl_k = -1, ctl_go = 0, ctl_slot = 0;
+    bool worked = false;
     if (MODE == CM_APPLY_PCG) {
         pdl_wait();
         if (threadIdx.x == 0) kclock_start(a.kclock, 0);
+        if (blockIdx.x == 0) {
+            // decide, for every instance, whether this CG iteration runs (from
+            // the dots the previous update reduced) and book it; book the
+            // previous update's span
+            const int ni = a.tab ? a.n_inst : 1;
+            for (int kk = threadIdx.x; kk < ni; kk += blockDim.x)
+                cg_go_book(a.ctl[kk], __ldcg(&a.ctl[kk].pcg_base) + a.iter, a.pcg_maxit);
+            if (threadIdx.x == 0) kclock_account(a.kclock, 1);
+        }
     }
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
         int k = 0;
@@ -93,12 +102,14 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                 part = 0;
                 acc_k = -1;
             }
-            // the previous kernel decided whether this CG iteration runs
+            // whether this CG iteration runs, derived in every block from the
+            // dots of the previous update (the same decision block 0 books)
             if (k != ctl_k) {  // uniform per block
                 int go = 0, base = 0;
                 if ((threadIdx.x & 31) == 0) {
-                    go = a.ctl[k].go;
-                    base = a.ctl[k].pcg_base;
+                    base = __ldcg(&a.ctl[k].pcg_base);
+                    int nf = 0;
+                    go = cg_go_at(a.ctl[k], base + a.iter, a.pcg_maxit, &nf);
                 }
                 ctl_go = __shfl_sync(0xffffffffu, go, 0);
                 ctl_slot = (__shfl_sync(0xffffffffu, base, 0) + a.iter) & 3;
@@ -108,6 +119,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
             slot = ctl_slot;
             acc_k = k;
             acc_slot = slot;
+            worked = true;
         } else if (MODE == CM_RESIDUAL_CTL || MODE == CM_APPLY_CTL) {
             if (a.ctl[k].status != 0) continue;
         } else if (MODE == CM_DIAG_CTL) {
@@ -363,7 +375,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
             const double s = block_sum_t<T, CELL_BLOCK>(part, sh);
             if (threadIdx.x == 0) atomicAdd(&a.ctl[acc_k].delta[acc_slot], s);
         }
-        if (last_block(a.arrive)) cg_apply_epilogue(a.ctl, a.tab ? a.n_inst : 1, a.iter, a.kclock);
+        if (threadIdx.x == 0 && worked) kclock_stop(a.kclock, 0);
     }
 }
 
@@ -389,6 +401,14 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
     const int tid = threadIdx.x;
     pdl_wait();
     if (tid == 0) kclock_start(a.kclock, 0);
+    if (blockIdx.x == 0) {  // as in cell_kernel<CM_APPLY_PCG>
+        const int ni = a.tab ? a.n_inst : 1;
+        for (int kk = tid; kk < ni; kk += NT) cg_go_book(a.ctl[kk], __ldcg(&a.ctl[kk].pcg_base) + a.iter, a.pcg_maxit);
+        if (tid == 0) kclock_account(a.kclock, 1);
+    }
+    __shared__ int s_go, s_slot;
+    int ctl_k = -1;
+    bool worked = false;
     for (int64_t brick = blockIdx.x; brick < a.n_tiles; brick += gridDim.x) {
         int k = 0;
         InstDesc d;
@@ -398,9 +418,20 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
         } else {
             d = a.d0;
         }
-        const Ctl &cc = a.ctl[k];
-        if (!cc.go) continue;  // decided by the previous kernel; uniform per CTA
-        const int slot = (cc.pcg_base + a.iter) & 3;
+        if (k != ctl_k) {  // uniform per CTA
+            __syncthreads();
+            if (tid == 0) {
+                const int base = __ldcg(&a.ctl[k].pcg_base);
+                int nf = 0;
+                s_go = cg_go_at(a.ctl[k], base + a.iter, a.pcg_maxit, &nf);
+                s_slot = (base + a.iter) & 3;
+            }
+            __syncthreads();
+            ctl_k = k;
+        }
+        if (!s_go) continue;  // uniform per CTA
+        worked = true;
+        const int slot = s_slot;
         const int nx = d.nx, ny = d.ny, nz = d.nz;
         const int tnx = (nx + BRICK_X - 1) / BRICK_X, tny = (ny + BRICK_Y - 1) / BRICK_Y;
         const int lb = (int)(brick - d.brick_off);
@@ -519,7 +550,7 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
         if (tid == 0) atomicAdd(&a.ctl[k].delta[slot], s);
         __syncthreads();  // shared arrays are reused by the next brick
     }
-    if (last_block(a.arrive)) cg_apply_epilogue(a.ctl, a.tab ? a.n_inst : 1, a.iter, a.kclock);
+    if (tid == 0 && worked) kclock_stop(a.kclock, 0);
 }
 
 // CSR assembly (Algorithm 1): one thread per (cell, column).  The column

@@ -106,19 +106,16 @@ struct Ctl {
     // CG in the single-reduction (Chronopoulos-Gear) form, iteration i:
     // gamma_i = (r_i, z_i), delta_i = (A z_i, z_i), rr_i = (r_i, r_i), alpha_i
     double gamma[4], delta[4], rr[4], alpha[4];
-    // Decisions handed from one CG kernel to the next (written by the last
-    // block of the previous kernel, so no kernel repeats FP64 scalar work):
-    int go;              // the next CG iteration runs
+    int go;  // CG runs: set by the CG start, cleared by block 0 of the kernel that stops it
     int pad2_;
-    double a_d, b_d;     // alpha_i, beta_i for the vector update
-    float a_f, b_f;
 };
 
 // Live kernel-span statistics of the two CG kernels, in device memory: the
-// first block to start and the last block to finish bound each launch
-// (%globaltimer, nanoseconds).
+// first block to start and the last working block to finish bound each
+// launch (%globaltimer, nanoseconds); block 0 of the next CG kernel books it.
 struct KernelClock {
-    unsigned long long t0[2];   // earliest block start of the running launch (0 apply, 1 update)
+    unsigned long long t0[2];   // earliest block start of the latest launch (0 apply, 1 update)
+    unsigned long long t1[2];   // latest end of a block that did CG work in that launch
     unsigned long long sum[2];  // summed spans of finished launches
     unsigned long long n[2];    // launches that did work
 };
@@ -136,16 +133,24 @@ __device__ __forceinline__ void kclock_start(KernelClock *kc, int which)
     if (kc) atomicMin(&kc->t0[which], global_ns());
 }
 
-// call from the last block; `worked` says whether the launch did CG work
-__device__ __forceinline__ void kclock_end(KernelClock *kc, int which, bool worked)
+// call from thread 0 of every block that did CG work, at its end
+__device__ __forceinline__ void kclock_stop(KernelClock *kc, int which)
+{
+    if (kc) atomicMax(&kc->t1[which], global_ns());
+}
+
+// Books the span of the previous launch of kind `which` (it has completed:
+// called by thread 0 of block 0 of the kernel that follows it) and resets it.
+__device__ __forceinline__ void kclock_account(KernelClock *kc, int which)
 {
     if (!kc) return;
-    const unsigned long long t = global_ns(), t0 = __ldcg(&kc->t0[which]);
-    if (worked && t > t0) {
-        kc->sum[which] += t - t0;
+    const unsigned long long t0 = __ldcg(&kc->t0[which]), t1 = __ldcg(&kc->t1[which]);
+    if (t1 > t0 && t0 != ~0ull) {
+        kc->sum[which] += t1 - t0;
         kc->n[which] += 1;
     }
     kc->t0[which] = ~0ull;
+    kc->t1[which] = 0;
 }
 
 // Last-block arrival: every block of the grid calls this once, after its
@@ -189,71 +194,87 @@ __device__ __forceinline__ bool last_block(int *arrive)
     return s_last != 0;
 }
 
-// After the CG apply of iteration `iter` (relative to each instance's chunk
-// base): alpha_i, beta_i from the reduced scalars, or the breakdown status.
-// Run by the last block; one thread per instance; L2-coherent loads.
-static __device__ __noinline__ void cg_after_apply(Ctl *ctl, int n_inst, int iter)
+// CG scalar scheduling.  The scalars of iteration `it` are decided by the
+// kernel that consumes them, in every block (each block derives the same
+// values from the same reduced dot products), so no block has to finish
+// alone at the tail of a kernel; block 0 of the consumer also writes the
+// bookkeeping (ring slots, flags) for every instance.  L2-coherent loads.
+
+// Does CG iteration `it` run?  Iteration 0 was decided by the CG start; later
+// ones stop when (r, r) reached eta^2 (r0, r0), at the iteration cap, or on a
+// non-finite residual (*nonfinite = 1).
+__device__ __forceinline__ int cg_go_at(const Ctl &c, int it, int pcg_maxit, int *nonfinite)
 {
-    for (int k = threadIdx.x; k < n_inst; k += blockDim.x) {
-        Ctl &c = ctl[k];
-        if (!__ldcg(&c.go)) continue;
-        const int it = __ldcg(&c.pcg_base) + iter;
-        const int s0 = it & 3, sm = (it + 3) & 3;
-        const double g = __ldcg(&c.gamma[s0]);
-        double beta = 0.0, den = __ldcg(&c.delta[s0]);
-        if (it > 0) {
-            beta = g / __ldcg(&c.gamma[sm]);
-            den -= beta * g / __ldcg(&c.alpha[sm]);
-        }
-        if (!isfinite(den) || !isfinite(g)) {
-            c.status = FEM_ERR_NONFINITE;
-            c.pcg_done = 1;
-            c.pcg_last = it;
-            c.go = 0;
-            continue;
-        }
-        if (!(den > 0.0)) {
-            // p^T K p <= 0: negative curvature.  Keep the iterate so far
-            // (truncated CG); with no iterate yet the tangent is unusable.
-            if (it == 0) c.status = FEM_ERR_BREAKDOWN;
-            c.pcg_done = 1;
-            c.pcg_last = it;
-            c.go = 0;
-            continue;
-        }
-        const double alpha = g / den;
-        c.alpha[s0] = alpha;
-        c.a_d = alpha;
-        c.b_d = beta;
-        c.a_f = (float)alpha;
-        c.b_f = (float)beta;
-        c.delta[(it + 1) & 3] = 0;
+    if (!__ldcg(&c.go)) return 0;
+    if (it == 0) return 1;
+    const double rr = __ldcg(&c.rr[it & 3]);
+    const double eta = __ldcg(&c.eta), rr0 = __ldcg(&c.rr0);
+    if (!isfinite(rr)) {
+        *nonfinite = 1;
+        return 0;
+    }
+    return (rr <= eta * eta * rr0 || it >= pcg_maxit) ? 0 : 1;
+}
+
+// Bookkeeping of cg_go_at for every instance (block 0 of the CG apply, and
+// the end-of-chunk kernel): stop flags, or clear the reduction slots that
+// the update of `it` accumulates into.
+__device__ __forceinline__ void cg_go_book(Ctl &c, int it, int pcg_maxit)
+{
+    if (!__ldcg(&c.go)) return;
+    int nf = 0;
+    if (cg_go_at(c, it, pcg_maxit, &nf)) {
+        c.gamma[(it + 1) & 3] = 0;
+        c.rr[(it + 1) & 3] = 0;
+    } else {
+        if (nf) c.status = FEM_ERR_NONFINITE;
+        c.pcg_done = 1;
+        c.pcg_last = it;
+        c.go = 0;
     }
 }
 
-// After the CG update of iteration `iter`: does iteration it+1 run?  It does
-// not when the relative residual reached eta or the iteration cap is hit.
-static __device__ __noinline__ void cg_after_update(Ctl *ctl, int n_inst, int iter, int pcg_maxit)
+// alpha_it and beta_it of single-reduction CG from gamma_it = (r, z),
+// delta_it = (z, K z), gamma_{it-1} and alpha_{it-1}:
+//   beta = gamma_it / gamma_{it-1},  alpha = gamma_it / (delta_it - beta gamma_it / alpha_{it-1}).
+// Returns 0 when iteration `it` does not update: negative curvature (truncated
+// CG keeps the iterate; FEM_ERR_BREAKDOWN in iteration 0) or non-finite dots.
+__device__ __forceinline__ int cg_step(const Ctl &c, int it, double &alpha, double &beta, int &status)
 {
-    for (int k = threadIdx.x; k < n_inst; k += blockDim.x) {
-        Ctl &c = ctl[k];
-        if (!__ldcg(&c.go)) continue;
-        const int nxt = __ldcg(&c.pcg_base) + iter + 1;
-        const double rr = __ldcg(&c.rr[nxt & 3]);
-        const double eta = __ldcg(&c.eta), rr0 = __ldcg(&c.rr0);
-        if (!isfinite(rr)) {
-            c.status = FEM_ERR_NONFINITE;
-            c.pcg_done = 1;
-            c.pcg_last = nxt;
-            c.go = 0;
-        } else if (rr <= eta * eta * rr0 || nxt >= pcg_maxit) {
-            c.pcg_done = 1;
-            c.pcg_last = nxt;
-            c.go = 0;
-        } else {
-            c.gamma[(nxt + 1) & 3] = 0;
-            c.rr[(nxt + 1) & 3] = 0;
-        }
+    const double g = __ldcg(&c.gamma[it & 3]);
+    double den = __ldcg(&c.delta[it & 3]);
+    beta = 0.0;
+    if (it > 0) {
+        beta = g / __ldcg(&c.gamma[(it + 3) & 3]);
+        den -= beta * g / __ldcg(&c.alpha[(it + 3) & 3]);
+    }
+    status = 0;
+    if (!isfinite(den) || !isfinite(g)) {
+        status = FEM_ERR_NONFINITE;
+        return 0;
+    }
+    if (!(den > 0.0)) {
+        if (it == 0) status = FEM_ERR_BREAKDOWN;
+        return 0;
+    }
+    alpha = g / den;
+    return 1;
+}
+
+// Bookkeeping of cg_step for every instance (block 0 of the CG update).
+__device__ __forceinline__ void cg_step_book(Ctl &c, int it)
+{
+    if (!__ldcg(&c.go)) return;
+    double alpha, beta;
+    int status;
+    if (cg_step(c, it, alpha, beta, status)) {
+        c.alpha[it & 3] = alpha;
+        c.delta[(it + 1) & 3] = 0;
+    } else {
+        if (status) c.status = status;
+        c.pcg_done = 1;
+        c.pcg_last = it;
+        c.go = 0;
     }
 }
 
@@ -708,26 +729,4 @@ __device__ __forceinline__ double cell_dscale(const InstDesc &d, double th)
 }  // namespace femgb
 
 
-namespace femgb {
-// Whether any instance ran this CG iteration (all threads of the last block).
-__device__ __forceinline__ bool any_go(const Ctl *ctl, int n_inst)
-{
-    int w = 0;
-    for (int k = threadIdx.x; k < n_inst; k += blockDim.x) w |= __ldcg(&ctl[k].go);
-    return __syncthreads_or(w) != 0;
-}
 
-__device__ __forceinline__ void cg_apply_epilogue(Ctl *ctl, int n_inst, int iter, KernelClock *kc)
-{
-    const bool worked = any_go(ctl, n_inst);
-    if (threadIdx.x == 0) kclock_end(kc, 0, worked);
-    cg_after_apply(ctl, n_inst, iter);
-}
-
-__device__ __forceinline__ void cg_update_epilogue(Ctl *ctl, int n_inst, int iter, int pcg_maxit, KernelClock *kc)
-{
-    const bool worked = any_go(ctl, n_inst);
-    if (threadIdx.x == 0) kclock_end(kc, 1, worked);
-    cg_after_update(ctl, n_inst, iter, pcg_maxit);
-}
-}  // namespace femgb

@@ -58,7 +58,7 @@ struct VecArgs {
     int iter;
     SolverParams prm;
     int *counter;       // [0] solving, [1] iterating, [2] active
-    int *arrive;        // last-block arrival counter of the CG kernels
+    int *arrive;        // last-block arrival counter of the CG start
     KernelClock *kclock;
 };
 
@@ -249,13 +249,38 @@ template <typename T>
 __global__ void __launch_bounds__(VEC_BLOCK, (sizeof(T) == 4 ? 3 : 2)) k_pcg_update(const VecArgs<T> a)
 {
     __shared__ double sh[2 * (VEC_BLOCK / 32)];
+    __shared__ int s_go;
+    __shared__ double s_al, s_be;
     pdl_wait();
     if (threadIdx.x == 0) kclock_start(a.kclock, 1);
+    if (blockIdx.x == 0) {
+        // alpha, beta (or the stop) of this iteration for every instance, from
+        // the dots the apply reduced; book the apply's span
+        for (int kk = threadIdx.x; kk < a.n_inst; kk += blockDim.x)
+            cg_step_book(a.ctl[kk], __ldcg(&a.ctl[kk].pcg_base) + a.iter);
+        if (threadIdx.x == 0) kclock_account(a.kclock, 0);
+    }
+    int sk = -1;
+    bool worked = false;
     VEC_ITEMS_BEGIN
-    if (!c.go) continue;  // alpha, beta and go come from the apply's last block
+    if (k != sk) {  // uniform per block: every block derives the same scalars
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int go = __ldcg(&c.go), st = 0;
+            double al = 0.0, be = 0.0;
+            if (go) go = cg_step(c, __ldcg(&c.pcg_base) + a.iter, al, be, st);
+            s_go = go;
+            s_al = al;
+            s_be = be;
+        }
+        __syncthreads();
+        sk = k;
+    }
+    if (!s_go) continue;
+    worked = true;
     const int it = c.pcg_base + a.iter;
-    const T al = sizeof(T) == 4 ? (T)c.a_f : (T)c.a_d;
-    const T be = sizeof(T) == 4 ? (T)c.b_f : (T)c.b_d;
+    const T al = (T)s_al;
+    const T be = (T)s_be;
     const bool first = it == 0;
     T ag = 0, arr = 0;
     const int64_t bd = blockDim.x;
@@ -359,7 +384,7 @@ __global__ void __launch_bounds__(VEC_BLOCK, (sizeof(T) == 4 ? 3 : 2)) k_pcg_upd
         atomicAdd(&c.rr[(it + 1) & 3], s2);
     }
     VEC_ITEMS_END
-    if (last_block(a.arrive)) cg_update_epilogue(a.ctl, a.n_inst, a.iter, a.prm.pcg_maxit, a.kclock);
+    if (threadIdx.x == 0 && worked) kclock_stop(a.kclock, 1);
 }
 
 // End of a graph chunk: instances whose next iteration would not run are
@@ -370,10 +395,14 @@ __global__ void k_chunk_ctl(Ctl *ctl, int n_inst, int chunk, int pcg_maxit, int 
     if (k >= n_inst) return;
     Ctl &c = ctl[k];
     if (c.status == 0 && c.solving && !c.pcg_done) {
-        c.pcg_base += chunk;  // `go` already refers to the next iteration
-        atomicAdd(&counter[1], 1);
+        // decide iteration base + chunk now, so that finished instances end
+        // the chunk loop (the next apply derives the same decision)
+        cg_go_book(c, c.pcg_base + chunk, pcg_maxit);
+        if (!c.pcg_done) {
+            c.pcg_base += chunk;
+            atomicAdd(&counter[1], 1);
+        }
     }
-    (void)pcg_maxit;
 }
 
 template <typename T>
@@ -618,7 +647,6 @@ class Core {
         ca.x = b_.z;
         ca.y = b_.q;
         ca.pcg_maxit = prm_.pcg_maxit;
-        ca.arrive = b_.counter + 3;
         ca.kclock = b_.kclock;
         for (int j = 0; j < prm_.chunk; ++j) {
             ca.iter = j;
@@ -701,7 +729,6 @@ class Core {
         ca.x = b_.p;
         ca.y = b_.q;
         ca.pcg_maxit = 1 << 30;
-        ca.arrive = b_.counter + 3;
         ca.kclock = nullptr;
         cudaEvent_t e0, e1;
         if (cudaEventCreate(&e0) != cudaSuccess) return (cudaGetLastError(), 2);
@@ -764,6 +791,11 @@ class Core {
         cudaError_t e = cudaMemcpyAsync(&kc, b_.kclock, sizeof(kc), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
+        for (int w = 0; w < 2; ++w)  // the last launch of each kind is booked by no successor
+            if (kc.t1[w] > kc.t0[w] && kc.t0[w] != ~0ull) {
+                kc.sum[w] += kc.t1[w] - kc.t0[w];
+                kc.n[w] += 1;
+            }
         apply_ms_ = kc.sum[0] * 1e-6;
         apply_samples_ = (int)kc.n[0];
         update_ms_ = kc.sum[1] * 1e-6;
@@ -1072,7 +1104,7 @@ static int solve_batch(Workspace &ws, Problem &pb, double *u64, const uint8_t *m
     FEM_CUDA(cudaMemcpyAsync(b.ctl, ctl.data(), sizeof(Ctl) * ctl.size(), cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemsetAsync(b.counter, 0, 4 * sizeof(int), s));
     {
-        static const KernelClock kc0 = {{~0ull, ~0ull}, {0, 0}, {0, 0}};
+        static const KernelClock kc0 = {{~0ull, ~0ull}, {0, 0}, {0, 0}, {0, 0}};
         FEM_CUDA(cudaMemcpyAsync(b.kclock, &kc0, sizeof(kc0), cudaMemcpyHostToDevice, s));
     }
     if (b.tab) FEM_CUDA(cudaMemcpyAsync(b.tab, pb.desc.data(), sizeof(InstDesc) * pb.desc.size(), cudaMemcpyHostToDevice, s));
@@ -1137,7 +1169,7 @@ static int adjoint_batch(Workspace &ws, Problem &pb, const double *ustar, const 
     FEM_CUDA(cudaMemcpyAsync(b.ctl, ctl.data(), sizeof(Ctl) * ctl.size(), cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemsetAsync(b.counter, 0, 4 * sizeof(int), s));
     {
-        static const KernelClock kc0 = {{~0ull, ~0ull}, {0, 0}, {0, 0}};
+        static const KernelClock kc0 = {{~0ull, ~0ull}, {0, 0}, {0, 0}, {0, 0}};
         FEM_CUDA(cudaMemcpyAsync(b.kclock, &kc0, sizeof(kc0), cudaMemcpyHostToDevice, s));
     }
     SolverParams prm = params_from(o);
