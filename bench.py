@@ -45,6 +45,13 @@ METRIC = "tangent-apply GDOF/s and Newton solve time, 64^3 Neo-Hookean, mixed vs
 #   transposed gradients 3 x 120 + 3                           363
 #   p.Kp weight 2, assembly adds 24                              26
 NH_APPLY_FLOPS_PER_CELL = 3269
+# Apply kernels that read tangent data stored once per Newton iteration skip
+# part of the per-Gauss-point kinematics, so their own algorithmic count is
+# lower: kernel 4 (cof F and the scalars stored) keeps F = I + H 3 of the 87
+# kinematics flops -> 8 x 194 + 965 = 2,517; kernel 5 (scalars stored) keeps
+# F 3 and cof F 27 -> 8 x 221 + 965 = 2,733.
+APPLY_FLOPS_PER_CELL = {1: NH_APPLY_FLOPS_PER_CELL, 2: NH_APPLY_FLOPS_PER_CELL, 3: NH_APPLY_FLOPS_PER_CELL,
+                        4: 2517, 5: 2733}
 # DRAM bytes (read + write) of one launch of the per-cell CG apply
 # (apply kernel 1) from the ncu capture summarised in
 # profiles/cg_apply_nh64_cell_kernel.md.  Valid only for the kernel sources it
@@ -359,7 +366,7 @@ def run_gb300(args):
     apply_launches = sum(s["apply_launches"] for s in stats) / len(stats)
     t_apply = apply_ms / max(apply_n, 1) / 1e3
     t_update = sum(s["update_ms"] for s in stats) / max(sum(s["update_samples"] for s in stats), 1) / 1e3
-    flops = NH_APPLY_FLOPS_PER_CELL * w.n_cells
+    flops = APPLY_FLOPS_PER_CELL.get(stats[-1]["apply_kernel"], NH_APPLY_FLOPS_PER_CELL) * w.n_cells
     achieved = flops / t_apply / 1e12
     share = apply_launches * t_apply / (statistics.mean(step_ms) / 1e3)
 
@@ -427,10 +434,12 @@ def run_gb300(args):
         "roofline": {"bound": "alu",
                      "kernel": {1: "cell_kernel<float,NH,CM_APPLY_PCG,3>", 2: "apply_brick<float,NH>",
                                 3: "cell_kernel<float,NH,CM_APPLY_PCG,4>",
-                                4: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN>"}.get(st0.get("apply_kernel"), "?"),
+                                4: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN=1>",
+                                5: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN=2>"}.get(st0.get("apply_kernel"), "?"),
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": apply_traffic(st0.get("apply_kernel")),
                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "flop_per_cell": APPLY_FLOPS_PER_CELL.get(st0.get("apply_kernel"), NH_APPLY_FLOPS_PER_CELL),
                      "launch_us": t_apply * 1e6, "launches_per_step": apply_launches,
                      "time_share": share, "hbm_gbs_algorithmic": 12 * D / t_apply / 1e9,
                      "cg_update_us": t_update * 1e6,

@@ -168,7 +168,9 @@ typedef struct {
                             3 = as 1 with a register budget for 4 CTAs per SM,
                             4 = as 1 on Neo-Hookean tangent data stored once per
                                 Newton iteration (Neo-Hookean only; not in
-                                fem_solve_static) */
+                                fem_solve_static),
+                            5 = as 4 storing only the four tangent scalars per
+                                Gauss point (cof(F) rebuilt from the state) */
     int reserved;        /* must be 0 (bit-reproducible cell operators: FEM_MESH_DETERMINISTIC) */
     double timeout_s;    /* host watchdog for one solve (0 = none) */
 } fem_options;

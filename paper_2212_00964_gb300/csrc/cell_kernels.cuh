@@ -44,6 +44,7 @@ struct CellArgs {
     int64_t n_list;         // length of the cell list
     int plain_store;        // 1: cells in one launch share no node -> plain RMW
     T *kin;                 // stored NH tangent data (written by the diagonal, read by the KIN apply) or nullptr
+    int kin_mode;           // what the diagonal stores in kin: 1 cof(F) + scalars, 2 scalars only
 };
 
 template <typename T>
@@ -57,7 +58,7 @@ __device__ __forceinline__ void scatter_add(T *p, T v, int plain)
 // CG apply is also built for 4, autotuned against 3).
 // BATCHED = false: one instance whose descriptor is read in place from the
 // kernel parameter (no register copy held across the tile loop).
-template <typename T, int NH, int MODE, int MINB = 3, bool BATCHED = true, bool KIN = false>
+template <typename T, int NH, int MODE, int MINB = 3, bool BATCHED = true, int KIN = 0>
 __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
     cell_kernel(const __grid_constant__ CellArgs<T> a)
 {
@@ -233,7 +234,16 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                         dH[3 * c + 1] = Gx[c][1][al + 2 * ga];
                         dH[3 * c + 2] = Gx[c][2][al + 2 * be];
                     }
-                    if (NH && KIN) {
+                    if (NH && KIN == 2) {
+                        // scalars stored by the diagonal kernel of this Newton iteration
+                        const T *kb = a.kin + kin_slot(d.tile_off, cell, gp * KIN2_VALUES, KIN2_VALUES);
+                        const T k1 = kb[0], beta = kb[CELL_BLOCK], e1 = kb[2 * CELL_BLOCK], e2 = kb[3 * CELL_BLOCK];
+                        T F[9], C[9];
+#pragma unroll
+                        for (int t = 0; t < 9; ++t) F[t] = H[t] + ((t % 4) == 0 ? (T)1 : (T)0);
+                        cof3(F, C);
+                        nh_dstress_c(F, C, k1, beta, e1, e2, dH, P);
+                    } else if (NH && KIN == 1) {
                         // tangent data stored by the diagonal kernel of this Newton iteration
                         const T *kb = a.kin + kin_slot(d.tile_off, cell, gp * KIN_VALUES);
                         NHKin<T> kq;
@@ -270,7 +280,15 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                     NHPoint<T> q;
                     if (NH) {
                         nh_point<T>(H, m, q);
-                        if (a.kin) {  // store the tangent data for the CG applies
+                        if (a.kin && a.kin_mode == 2) {  // store the tangent scalars for the CG applies
+                            NHKin<T> kq;
+                            nh_kin<T>(q, m, kq);
+                            T *kb = a.kin + kin_slot(d.tile_off, cell, gp * KIN2_VALUES, KIN2_VALUES);
+                            kb[0] = kq.k1;
+                            kb[CELL_BLOCK] = kq.beta;
+                            kb[2 * CELL_BLOCK] = kq.e1;
+                            kb[3 * CELL_BLOCK] = kq.e2;
+                        } else if (a.kin) {  // store the tangent data for the CG applies
                             NHKin<T> kq;
                             nh_kin<T>(q, m, kq);
                             T *kb = a.kin + kin_slot(d.tile_off, cell, gp * KIN_VALUES);

@@ -109,9 +109,12 @@ static void warm_one()
                                        : cell_kernel<T, NH, CM_APPLY_LIFT, 3, false>), CELL_BLOCK, 0);
         resident_grid((const void *)(b ? cell_kernel<T, NH, CM_APPLY_PCG, 4, true>
                                        : cell_kernel<T, NH, CM_APPLY_PCG, 4, false>), CELL_BLOCK, 0);
-        if (NH)
-            resident_grid((const void *)(b ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, true>
-                                           : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, true>), CELL_BLOCK, 0);
+        if (NH) {
+            resident_grid((const void *)(b ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, 1>
+                                           : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 1>), CELL_BLOCK, 0);
+            resident_grid((const void *)(b ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, 2>
+                                           : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 2>), CELL_BLOCK, 0);
+        }
     }
     resident_grid((const void *)apply_brick<T, NH>, BRICK_X * BRICK_Y * BRICK_Z, 0);
 }
@@ -148,12 +151,15 @@ cudaError_t launch_apply_cell4(bool nh, const CellArgs<T> &a, cudaStream_t s)
 }
 template cudaError_t launch_apply_cell4<float>(bool, const CellArgs<float> &, cudaStream_t);
 
-// CG apply on stored Neo-Hookean tangent data (a.kin filled by the diagonal).
+// CG apply on stored Neo-Hookean tangent data (a.kin filled by the diagonal
+// in mode a.kin_mode: 1 cof(F) + scalars, 2 scalars only).
 template <typename T>
 cudaError_t launch_apply_kin(bool nh, const CellArgs<T> &a, cudaStream_t s)
 {
-    if (!nh || !a.kin) return cudaErrorInvalidValue;
-    auto f = a.tab ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, true> : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, true>;
+    if (!nh || !a.kin || (a.kin_mode != 1 && a.kin_mode != 2)) return cudaErrorInvalidValue;
+    auto f = a.kin_mode == 1
+                 ? (a.tab ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, 1> : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 1>)
+                 : (a.tab ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, 2> : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 2>);
     int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, 0));
     if (g < 1) return cudaSuccess;
     count_launch();

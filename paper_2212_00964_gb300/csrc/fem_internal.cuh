@@ -549,6 +549,15 @@ __device__ __forceinline__ double rcbrt_t(double x)
     return x < 0 ? -r : r;
 }
 
+// Cofactor matrix cof(F) = J F^{-T} of a 3x3 matrix (row-major): 2x2 minors.
+template <typename T>
+__device__ __forceinline__ void cof3(const T *F, T *C)
+{
+    C[0] = F[4] * F[8] - F[5] * F[7]; C[1] = F[5] * F[6] - F[3] * F[8]; C[2] = F[3] * F[7] - F[4] * F[6];
+    C[3] = F[2] * F[7] - F[1] * F[8]; C[4] = F[0] * F[8] - F[2] * F[6]; C[5] = F[1] * F[6] - F[0] * F[7];
+    C[6] = F[1] * F[5] - F[2] * F[4]; C[7] = F[2] * F[3] - F[0] * F[5]; C[8] = F[0] * F[4] - F[1] * F[3];
+}
+
 // Neo-Hookean kinematics at one Gauss point: the cofactor matrix cof(F)
 // (A = F^{-T} = cof / J is never formed: every use folds 1/J into a scalar
 // coefficient), J, J-1, 1/J, I1 and G J^{-2/3}.
@@ -564,10 +573,7 @@ __device__ __forceinline__ void nh_point(const T *H, const Mat<T> &m, NHPoint<T>
 #pragma unroll
     for (int t = 0; t < 9; ++t) q.F[t] = H[t] + ((t % 4) == 0 ? (T)1 : (T)0);
     const T *F = q.F;
-    T *C = q.C;
-    C[0] = F[4] * F[8] - F[5] * F[7]; C[1] = F[5] * F[6] - F[3] * F[8]; C[2] = F[3] * F[7] - F[4] * F[6];
-    C[3] = F[2] * F[7] - F[1] * F[8]; C[4] = F[0] * F[8] - F[2] * F[6]; C[5] = F[1] * F[6] - F[0] * F[7];
-    C[6] = F[1] * F[5] - F[2] * F[4]; C[7] = F[2] * F[3] - F[0] * F[5]; C[8] = F[0] * F[4] - F[1] * F[3];
+    cof3(F, q.C);
     q.Jm1 = det_ipH_m1(H);
     q.J = (T)1 + q.Jm1;
     const T r = rcbrt_t(q.J);  // J^{-1/3}: J^{-2/3} = r^2 and 1/J = r^3 without a division
@@ -679,12 +685,16 @@ __device__ __forceinline__ void nh_dstress_kin(const NHKin<T> &k, const T *H, co
     nh_dstress_c(F, k.C, k.k1, k.beta, k.e1, k.e2, dF, dP);
 }
 
-// Slot of value v (0..8*KIN_VALUES-1) of instance-local cell `cell` in the
+// The scalar part alone (k1, beta, e1, e2): cof(F) is then rebuilt from the
+// gathered state, and 32 values per cell fit the L2 beside the CG vectors.
+constexpr int KIN2_VALUES = 4;
+
+// Slot of value v (0..8*per_gp-1) of instance-local cell `cell` in the
 // stored tangent data: [tile][v][CELL_BLOCK] over the global tiles, so a
 // warp's accesses to one value are 128 contiguous bytes.
-__device__ __forceinline__ int64_t kin_slot(int64_t tile_off, int cell, int v)
+__device__ __forceinline__ int64_t kin_slot(int64_t tile_off, int cell, int v, int per_gp = KIN_VALUES)
 {
-    return ((tile_off + cell / CELL_BLOCK) * (8 * KIN_VALUES) + v) * CELL_BLOCK + cell % CELL_BLOCK;
+    return ((tile_off + cell / CELL_BLOCK) * (8 * per_gp) + v) * CELL_BLOCK + cell % CELL_BLOCK;
 }
 
 // Linear elasticity (also the SIMP-scaled law): P = lam tr(H) I + mu (H + H^T).

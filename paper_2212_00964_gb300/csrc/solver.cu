@@ -622,7 +622,9 @@ class Core {
             ca.cell_param = b_.cpT;
             ca.u = b_.uT;
             ca.y = b_.dg;
-            ca.kin = variant_ == 4 ? b_.kin : nullptr;  // apply kernel 4 reads the stored tangent data
+            // apply kernels 4 and 5 read the tangent data stored here
+            ca.kin = (variant_ == 4 || variant_ == 5) ? b_.kin : nullptr;
+            ca.kin_mode = variant_ == 4 ? 1 : 2;
             if ((e = launch_cell<T>(CM_DIAG_CTL, pb_.nh, ca, s)) != cudaSuccess) return e;
         }
         k_pcg_init<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
@@ -682,8 +684,9 @@ class Core {
         }
         ca.n_tiles = pb_.n_tiles;
         if (variant_ == 3) return launch_apply_cell4<T>(pb_.nh, ca, s);
-        if (variant_ == 4) {
+        if (variant_ == 4 || variant_ == 5) {
             ca.kin = b_.kin;
+            ca.kin_mode = variant_ == 4 ? 1 : 2;
             return launch_apply_kin<T>(pb_.nh, ca, s);
         }
         return launch_cell<T>(CM_APPLY_PCG, pb_.nh, ca, s);
@@ -736,19 +739,20 @@ class Core {
             cudaEventDestroy(e0);
             return (cudaGetLastError(), 2);
         }
-        float best = 1e30f, times[4] = {-1.f, -1.f, -1.f, -1.f};
+        float best = 1e30f, times[5] = {-1.f, -1.f, -1.f, -1.f, -1.f};
         int choice = 1;
-        const int n_var = (pb_.nh && b_.kin) ? 4 : 3;
+        const int n_var = (pb_.nh && b_.kin) ? 5 : 3;
         for (int v = 1; v <= n_var; ++v) {
             variant_ = v;
             // fresh control blocks for each variant (the apply's epilogue updates them)
             bool ok = cudaMemcpyAsync(b_.tune, tc.data(), sizeof(Ctl) * tc.size(), cudaMemcpyHostToDevice, s) ==
                       cudaSuccess;
-            if (ok && v == 4) {  // tangent data of the probe state (dg is rebuilt by every head graph)
+            if (ok && v >= 4) {  // tangent data of the probe state (dg is rebuilt by every head graph)
                 CellArgs<T> cd = ca;
                 cd.n_tiles = pb_.n_tiles;
                 cd.y = b_.dg;
                 cd.kin = b_.kin;
+                cd.kin_mode = v == 4 ? 1 : 2;
                 ok = launch_cell<T>(CM_DIAG_CTL, pb_.nh, cd, s) == cudaSuccess;
             }
             ok = ok && launch_apply(ca, s) == cudaSuccess;
@@ -774,9 +778,9 @@ class Core {
             if (env[0] == '1')
                 fprintf(stderr,
                         "femgb autotune: D=%lld instances=%d per-cell %.3f ms, bricks %.3f ms, "
-                        "per-cell(4 CTA/SM) %.3f ms, stored tangent %.3f ms -> %d\n",
+                        "per-cell(4 CTA/SM) %.3f ms, stored tangent %.3f ms, stored scalars %.3f ms -> %d\n",
                         (long long)pb_.D, (int)pb_.desc.size(), times[0] / 3, times[1] / 3, times[2] / 3,
-                        times[3] / 3, choice);
+                        times[3] / 3, times[4] / 3, choice);
         }
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = choice;
@@ -877,8 +881,8 @@ class Core {
     // Apply kernel 4 needs a Neo-Hookean law and its tangent-data buffer.
     int check_variant() const
     {
-        if (variant_ == 4 && !(pb_.nh && b_.kin))
-            return (set_error("apply_kernel 4 (stored tangent data) needs a Neo-Hookean problem and its buffer "
+        if ((variant_ == 4 || variant_ == 5) && !(pb_.nh && b_.kin))
+            return (set_error("apply_kernel 4/5 (stored tangent data) needs a Neo-Hookean problem and its buffer "
                               "(not available in fem_solve_static)"),
                     FEM_ERR_ARG);
         return FEM_OK;
@@ -928,7 +932,7 @@ class Core {
     const double *ustar64_ = nullptr;  // linear mode: the fixed state
     int max_steps_ = 1;
     int variant_ = 0;       // CG apply kernel: 0 autotune, 1 per-cell, 2 bricks, 3 per-cell at 4 CTA/SM,
-                            // 4 per-cell on stored NH tangent data
+                            // 4 per-cell on stored NH tangent data, 5 on stored NH tangent scalars
     double apply_ms_ = 0;   // sampled device time of CG applies
     int apply_samples_ = 0;
     double update_ms_ = 0;  // sampled device time of CG vector updates
@@ -975,7 +979,7 @@ static int check_options(const fem_options &o)
         return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
     if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
         !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
-        o.apply_kernel < 0 || o.apply_kernel > 4 || o.reserved != 0)
+        o.apply_kernel < 0 || o.apply_kernel > 5 || o.reserved != 0)
         return (set_error("invalid solver options"), FEM_ERR_ARG);
     return FEM_OK;
 }
