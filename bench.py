@@ -52,13 +52,13 @@ NH_APPLY_FLOPS_PER_CELL = 3269
 # F 3 and cof F 27 -> 8 x 221 + 965 = 2,733.
 APPLY_FLOPS_PER_CELL = {1: NH_APPLY_FLOPS_PER_CELL, 2: NH_APPLY_FLOPS_PER_CELL, 3: NH_APPLY_FLOPS_PER_CELL,
                         4: 2517, 5: 2733}
-# DRAM bytes (read + write) of one launch of the per-cell CG apply
-# (apply kernel 1) from the ncu capture summarised in
-# profiles/cg_apply_nh64_cell_kernel.md.  Valid only for the kernel sources it
-# was taken on: reported as null once their hash changes.
-APPLY_TRAFFIC_BYTES = 9.950208e6
+# DRAM bytes (read + write) of one launch of a CG apply kernel, by apply
+# kernel id, from the ncu capture summarised in profiles/ (kernel 5:
+# cg_apply_nh64_kernel5.md; cold caches under ncu).  Valid only for the kernel
+# sources the capture was taken on: reported as null once their hash changes.
+APPLY_TRAFFIC_BYTES = {5: 43.48288e6 + 47.36e3}
 APPLY_TRAFFIC_SOURCES = ("paper_2212_00964_gb300/csrc/cell_kernels.cuh", "paper_2212_00964_gb300/csrc/fem_internal.cuh")
-APPLY_TRAFFIC_SHA256 = "7a7223ccedac2012838ae61a6f08aaf055d8542321f9dd4cb66b3957311555bf"
+APPLY_TRAFFIC_SHA256 = "f925ad427927cca2ccfa740adae0760c2fa145e6b5642af9680773af9e70b0f4"
 # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Bytes a launch must move (u, x read; y written; FP32): 12 * D.
@@ -68,13 +68,13 @@ SAMPLE_N = 8
 def apply_traffic(kernel_id):
     """ncu DRAM bytes per launch of the timed apply kernel, or None when the
     capture does not describe the kernel that ran."""
-    if kernel_id != 1:
+    if kernel_id not in APPLY_TRAFFIC_BYTES:
         return None
     h = hashlib.sha256()
     for f in APPLY_TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return APPLY_TRAFFIC_BYTES if h.hexdigest() == APPLY_TRAFFIC_SHA256 else None
+    return APPLY_TRAFFIC_BYTES[kernel_id] if h.hexdigest() == APPLY_TRAFFIC_SHA256 else None
 
 
 def parse():
