@@ -65,17 +65,15 @@ struct VecArgs {
 #define VEC_ITEMS_BEGIN                                                       \
     for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {    \
         int k = 0;                                                            \
-        InstDesc d;                                                           \
+        const InstDesc *dp_ = &a.d0;                                          \
         if (a.tab) {                                                          \
             k = find_inst(a.tab, a.n_inst, item, false);                      \
-            d = a.tab[k];                                                     \
-        } else {                                                              \
-            d = a.d0;                                                         \
+            dp_ = &a.tab[k];                                                  \
         }                                                                     \
         Ctl &c = a.ctl[k];                                                    \
-        const int64_t i0 = (item - d.vec_off) * VEC_CHUNK;                    \
-        const int64_t i1 = min(i0 + (int64_t)VEC_CHUNK, d.n_dofs());          \
-        const int64_t base = d.dof_off;                                       \
+        const int64_t i0 = (item - dp_->vec_off) * VEC_CHUNK;                 \
+        const int64_t i1 = min(i0 + (int64_t)VEC_CHUNK, dp_->n_dofs());       \
+        const int64_t base = dp_->dof_off;                                    \
         (void)base;
 
 #define VEC_ITEMS_END }
