@@ -812,7 +812,7 @@ class Core {
     {
         if (int rc = check_variant()) return rc;
         warm_occupancy(pb_.nh);
-        if (variant_ == 0) variant_ = 2;
+        if (variant_ == 0) variant_ = 1;  // no probe timing without events: the per-cell kernel
         auto t0 = std::chrono::steady_clock::now();
         auto expired = [&]() {
             if (timeout_s <= 0) return false;
