@@ -87,7 +87,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--pcg-rtol", type=float, default=3e-3, help="inner CG relative tolerance")
-    ap.add_argument("--apply-kernel", type=int, default=0, help="0 autotuned, 1 per-cell, 2 bricks")
+    ap.add_argument("--apply-kernel", type=int, default=0,
+                    help="0 autotuned, 1 per-cell, 2 bricks, 3 per-cell 4 CTA/SM, 4/5 stored tangent data/scalars")
+    ap.add_argument("--cg-fused", type=int, default=0,
+                    help="1: one fused CG kernel per iteration (update + apply) instead of two")
     ap.add_argument("--no-suite", action="store_true",
                     help="skip the secondary measurements (batch c3, adjoint c2, 128^3 c4)")
     return ap.parse_args()
@@ -323,7 +326,7 @@ def run_gb300(args):
     ubar = torch.tensor(w.u_bar, device="cuda")
     u = torch.zeros(D, dtype=torch.float64, device="cuda")
     opt = F.default_options(precision=F.FEM_MIXED, newton_rtol=1e-10, pcg_rtol=args.pcg_rtol,
-                            apply_kernel=args.apply_kernel)
+                            apply_kernel=args.apply_kernel, cg_fused=args.cg_fused)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -365,7 +368,8 @@ def run_gb300(args):
     apply_n = sum(s["apply_samples"] for s in stats)
     apply_launches = sum(s["apply_launches"] for s in stats) / len(stats)
     t_apply = apply_ms / max(apply_n, 1) / 1e3
-    t_update = sum(s["update_ms"] for s in stats) / max(sum(s["update_samples"] for s in stats), 1) / 1e3
+    upd_n = sum(s["update_samples"] for s in stats)
+    t_update = sum(s["update_ms"] for s in stats) / upd_n / 1e3 if upd_n else None  # none: fused CG kernel
     flops = APPLY_FLOPS_PER_CELL.get(stats[-1]["apply_kernel"], NH_APPLY_FLOPS_PER_CELL) * w.n_cells
     achieved = flops / t_apply / 1e12
     share = apply_launches * t_apply / (statistics.mean(step_ms) / 1e3)
@@ -442,8 +446,9 @@ def run_gb300(args):
                      "flop_per_cell": APPLY_FLOPS_PER_CELL.get(st0.get("apply_kernel"), NH_APPLY_FLOPS_PER_CELL),
                      "launch_us": t_apply * 1e6, "launches_per_step": apply_launches,
                      "time_share": share, "hbm_gbs_algorithmic": 12 * D / t_apply / 1e9,
-                     "cg_update_us": t_update * 1e6,
-                     "apply_share_of_cg_kernels": t_apply / (t_apply + t_update)},
+                     "cg_update_us": t_update * 1e6 if t_update is not None else None,
+                     "cg_fused": t_update is None,
+                     "apply_share_of_cg_kernels": t_apply / (t_apply + t_update) if t_update is not None else 1.0},
         "cpu_baseline": cpu,
         "suite": extra,
         "wall_s_timed": t_wall,

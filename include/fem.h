@@ -171,7 +171,10 @@ typedef struct {
                                 fem_solve_static),
                             5 = as 4 storing only the four tangent scalars per
                                 Gauss point (cof(F) rebuilt from the state) */
-    int reserved;        /* must be 0 (bit-reproducible cell operators: FEM_MESH_DETERMINISTIC) */
+    int cg_fused;        /* 0: separate CG apply and update kernels; 1: one fused kernel per CG
+                            iteration (the vector update of the previous iteration recomputed
+                            per node inside the tangent apply) with apply kernels 1 and 5
+                            (measured slower on GB300: an option, not the default) */
     double timeout_s;    /* host watchdog for one solve (0 = none) */
 } fem_options;
 

@@ -55,6 +55,6 @@ extern "C" void fem_default_options(fem_options *o)
     o->pcg_chunk = 16;
     o->step_begin = 1;
     o->apply_kernel = 0;
-    o->reserved = 0;
+    o->cg_fused = 0;
     o->timeout_s = 0.0;
 }

@@ -113,11 +113,15 @@ struct Ctl {
 // Live kernel-span statistics of the two CG kernels, in device memory: the
 // first block to start and the last working block to finish bound each
 // launch (%globaltimer, nanoseconds); block 0 of the next CG kernel books it.
+// Slots: 0 CG apply, 1 CG update, 2 and 3 the fused CG kernel of even and
+// odd iterations (consecutive launches of one kind must not share a slot:
+// block 0 of a launch books its predecessor's span while its own blocks
+// start).
 struct KernelClock {
-    unsigned long long t0[2];   // earliest block start of the latest launch (0 apply, 1 update)
-    unsigned long long t1[2];   // latest end of a block that did CG work in that launch
-    unsigned long long sum[2];  // summed spans of finished launches
-    unsigned long long n[2];    // launches that did work
+    unsigned long long t0[4];   // earliest block start of the latest launch
+    unsigned long long t1[4];   // latest end of a block that did CG work in that launch
+    unsigned long long sum[4];  // summed spans of finished launches
+    unsigned long long n[4];    // launches that did work
 };
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -259,6 +263,50 @@ __device__ __forceinline__ int cg_step(const Ctl &c, int it, double &alpha, doub
     }
     alpha = g / den;
     return 1;
+}
+
+// Fused CG (one kernel per iteration: the update of iteration k-1 and the
+// apply of iteration k).  Iteration k-1 is completed, and iteration k
+// applied, unless CG stopped at k-1: (r_{k-1}, r_{k-1}) reached eta^2
+// (r0, r0), the cap of k-1 updates was reached, the dots are not finite, or
+// iteration k-1 has negative curvature (truncated CG; breakdown if k-1 = 0).
+// *last = number of CG updates done when it stops.
+__device__ __forceinline__ int cgf_decide(const Ctl &c, int k, int pcg_maxit, double &alpha, double &beta,
+                                          int &status, int &last)
+{
+    alpha = beta = 0.0;
+    status = 0;
+    last = k > 0 ? k - 1 : 0;
+    if (!__ldcg(&c.go)) return 0;
+    if (k == 0) return 1;
+    const double rr = __ldcg(&c.rr[(k - 1) & 3]);
+    const double eta = __ldcg(&c.eta), rr0 = __ldcg(&c.rr0);
+    if (!isfinite(rr)) {
+        status = FEM_ERR_NONFINITE;
+        return 0;
+    }
+    if (rr <= eta * eta * rr0 || k - 1 >= pcg_maxit) return 0;
+    return cg_step(c, k - 1, alpha, beta, status);
+}
+
+// Bookkeeping of cgf_decide for one instance (block 0 of the fused kernel,
+// and the end-of-chunk kernel for the next iteration).
+__device__ __forceinline__ void cgf_book(Ctl &c, int k, int pcg_maxit)
+{
+    if (!__ldcg(&c.go)) return;
+    double alpha, beta;
+    int status, last;
+    if (cgf_decide(c, k, pcg_maxit, alpha, beta, status, last)) {
+        if (k > 0) c.alpha[(k - 1) & 3] = alpha;
+        c.delta[(k + 1) & 3] = 0;
+        c.gamma[(k + 1) & 3] = 0;
+        c.rr[(k + 1) & 3] = 0;
+    } else {
+        if (status) c.status = status;
+        c.pcg_done = 1;
+        c.pcg_last = last;
+        c.go = 0;
+    }
 }
 
 // Bookkeeping of cg_step for every instance (block 0 of the CG update).

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "cell_ops.cuh"
+#include "cg_fused.cuh"
 #include "mesh.cuh"
 
 namespace femgb {
@@ -387,15 +388,16 @@ __global__ void __launch_bounds__(VEC_BLOCK, (sizeof(T) == 4 ? 3 : 2)) k_pcg_upd
 
 // End of a graph chunk: instances whose next iteration would not run are
 // marked done here, the others advance their iteration base.
-__global__ void k_chunk_ctl(Ctl *ctl, int n_inst, int chunk, int pcg_maxit, int *counter)
+__global__ void k_chunk_ctl(Ctl *ctl, int n_inst, int chunk, int pcg_maxit, int *counter, int fused)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_inst) return;
     Ctl &c = ctl[k];
     if (c.status == 0 && c.solving && !c.pcg_done) {
         // decide iteration base + chunk now, so that finished instances end
-        // the chunk loop (the next apply derives the same decision)
-        cg_go_book(c, c.pcg_base + chunk, pcg_maxit);
+        // the chunk loop (the next CG kernel derives the same decision)
+        if (fused) cgf_book(c, c.pcg_base + chunk, pcg_maxit);
+        else cg_go_book(c, c.pcg_base + chunk, pcg_maxit);
         if (!c.pcg_done) {
             c.pcg_base += chunk;
             atomicAdd(&counter[1], 1);
@@ -509,7 +511,8 @@ struct Buffers {
     T *x, *r, *z, *p, *q, *dg, *s;
     Ctl *tune;           // scratch control blocks for the apply autotuner (may be null)
     KernelClock *kclock; // live span statistics of the CG kernels (may be null)
-    T *kin;              // stored NH tangent data for apply kernel 4 (may be null)
+    T *kin;              // stored NH tangent data for apply kernels 4, 5 (may be null)
+    T *r2, *s2, *q2, *q3; // second r and s, second and third w of the fused CG kernel (may be null)
 };
 
 struct Graphs {
@@ -636,6 +639,37 @@ class Core {
         const int gv = vec_grid(pb_.n_items);
         const int ni = va_.n_inst, gi = (ni + 127) / 128;
         if ((e = cudaMemsetAsync(b_.counter + 1, 0, sizeof(int), s)) != cudaSuccess) return e;
+        if (fused_) {
+            FusedArgs<T> fa{};
+            fa.d0 = pb_.desc[0];
+            fa.tab = va_.tab;
+            fa.n_inst = ni;
+            fa.n_tiles = pb_.n_tiles;
+            fa.u = b_.uT;
+            fa.cell_param = b_.cpT;
+            fa.kin = variant_ == 5 ? b_.kin : nullptr;
+            fa.ctl = b_.ctl;
+            fa.chunk = prm_.chunk;
+            fa.pcg_maxit = prm_.pcg_maxit;
+            fa.kclock = b_.kclock;
+            fa.rb[0] = b_.r;
+            fa.rb[1] = b_.r2;
+            fa.sb[0] = b_.s;
+            fa.sb[1] = b_.s2;
+            fa.qb[0] = b_.q;
+            fa.qb[1] = b_.q2;
+            fa.qb[2] = b_.q3;
+            fa.p = b_.p;
+            fa.x = b_.x;
+            fa.dg = b_.dg;
+            for (int j = 0; j < prm_.chunk; ++j) {
+                fa.iter = j;
+                if ((e = launch_cg_fused<T>(pb_.nh, variant_ == 5 ? 2 : 0, fa, s)) != cudaSuccess) return e;
+            }
+            k_chunk_ctl<<<gi, 128, 0, s>>>(b_.ctl, ni, prm_.chunk, prm_.pcg_maxit, b_.counter, 1);
+            count_launch();
+            return cudaGetLastError();
+        }
         CellArgs<T> ca{};
         ca.d0 = pb_.desc[0];
         ca.tab = va_.tab;
@@ -656,7 +690,7 @@ class Core {
             if ((e = launch_pdl(k_pcg_update<T>, gv, VEC_BLOCK, 0, s, v)) != cudaSuccess) return e;
             count_launch();
         }
-        k_chunk_ctl<<<gi, 128, 0, s>>>(b_.ctl, ni, prm_.chunk, prm_.pcg_maxit, b_.counter);
+        k_chunk_ctl<<<gi, 128, 0, s>>>(b_.ctl, ni, prm_.chunk, prm_.pcg_maxit, b_.counter, 0);
         count_launch();
         return cudaGetLastError();
     }
@@ -793,13 +827,14 @@ class Core {
         cudaError_t e = cudaMemcpyAsync(&kc, b_.kclock, sizeof(kc), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
-        for (int w = 0; w < 2; ++w)  // the last launch of each kind is booked by no successor
+        for (int w = 0; w < 4; ++w)  // the last launch of each kind is booked by no successor
             if (kc.t1[w] > kc.t0[w] && kc.t0[w] != ~0ull) {
                 kc.sum[w] += kc.t1[w] - kc.t0[w];
                 kc.n[w] += 1;
             }
-        apply_ms_ = kc.sum[0] * 1e-6;
-        apply_samples_ = (int)kc.n[0];
+        // the fused kernel (slots 2, 3) counts as the CG apply
+        apply_ms_ = (kc.sum[0] + kc.sum[2] + kc.sum[3]) * 1e-6;
+        apply_samples_ = (int)(kc.n[0] + kc.n[2] + kc.n[3]);
         update_ms_ = kc.sum[1] * 1e-6;
         update_samples_ = (int)kc.n[1];
         return cudaSuccess;
@@ -877,6 +912,13 @@ class Core {
 
     // Returns FEM_OK or an error; per-instance outcomes stay in the Ctl blocks.
     // Apply kernel 4 needs a Neo-Hookean law and its tangent-data buffer.
+    // The fused CG kernel (on request) serves the per-cell apply kernels 1
+    // and 5 when its extra vectors exist (not in fem_solve_static).
+    bool choose_fused() const
+    {
+        return cg_fused_opt_ == 1 && (variant_ == 1 || variant_ == 5) && b_.r2 && b_.s2 && b_.q2 && b_.q3;
+    }
+
     int check_variant() const
     {
         if ((variant_ == 4 || variant_ == 5) && !(pb_.nh && b_.kin))
@@ -891,7 +933,9 @@ class Core {
         if (int rc = check_variant()) return rc;
         Graphs G;
         warm_occupancy(pb_.nh);
+        warm_cg_fused(pb_.nh);
         if (variant_ == 0) variant_ = autotune(s);
+        fused_ = choose_fused();
         FEM_CUDA(capture(s, 0, &G.head, &G.n_head));
         FEM_CUDA(capture(s, 1, &G.chunk, &G.n_chunk));
         FEM_CUDA(capture(s, 2, &G.tail_head, &G.n_tail_head));
@@ -929,6 +973,8 @@ class Core {
 
     const double *ustar64_ = nullptr;  // linear mode: the fixed state
     int max_steps_ = 1;
+    int cg_fused_opt_ = 0;  // 1: fused CG kernel where the apply kernel allows it
+    bool fused_ = false;    // CG iterations run as the fused update + apply kernel
     int variant_ = 0;       // CG apply kernel: 0 autotune, 1 per-cell, 2 bricks, 3 per-cell at 4 CTA/SM,
                             // 4 per-cell on stored NH tangent data, 5 on stored NH tangent scalars
     double apply_ms_ = 0;   // sampled device time of CG applies
@@ -977,7 +1023,7 @@ static int check_options(const fem_options &o)
         return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
     if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
         !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
-        o.apply_kernel < 0 || o.apply_kernel > 5 || o.reserved != 0)
+        o.apply_kernel < 0 || o.apply_kernel > 5 || o.cg_fused < 0 || o.cg_fused > 1)
         return (set_error("invalid solver options"), FEM_ERR_ARG);
     return FEM_OK;
 }
@@ -1005,7 +1051,8 @@ static cudaError_t join_streams(cudaStream_t from, cudaStream_t to)
 // Workspace slots
 enum {
     WS_CTL = 0, WS_CNT, WS_R64, WS_UT, WS_X, WS_R, WS_Z, WS_P, WS_Q, WS_DG, WS_LAM, WS_TAB, WS_CPT,
-    WS_U64CAT, WS_MASKCAT, WS_UBARCAT, WS_RHSCAT, WS_CP64CAT, WS_G64, WS_S, WS_TUNE, WS_KCLOCK, WS_KIN
+    WS_U64CAT, WS_MASKCAT, WS_UBARCAT, WS_RHSCAT, WS_CP64CAT, WS_G64, WS_S, WS_TUNE, WS_KCLOCK, WS_KIN,
+    WS_R2, WS_S2, WS_Q2, WS_Q3
 };
 
 template <typename T>
@@ -1032,6 +1079,11 @@ static int alloc_buffers(Workspace &ws, const Problem &pb, Buffers<T> &b, bool n
     // stored tangent data (8 Gauss points x KIN_VALUES per cell slot); optional:
     // without it apply kernel 4 is not offered
     b.kin = pb.nh ? (T *)ws.get(WS_KIN, sizeof(T) * (size_t)pb.n_tiles * 8 * KIN_VALUES * CELL_BLOCK) : nullptr;
+    // vectors of the fused CG kernel; optional: without them CG runs as two kernels
+    b.r2 = (T *)ws.get(WS_R2, sizeof(T) * (size_t)D);
+    b.s2 = (T *)ws.get(WS_S2, sizeof(T) * (size_t)D);
+    b.q2 = (T *)ws.get(WS_Q2, sizeof(T) * (size_t)D);
+    b.q3 = (T *)ws.get(WS_Q3, sizeof(T) * (size_t)D);
     if (n > 1) WSGET(b.tab, WS_TAB, InstDesc, n);
     else b.tab = nullptr;
     if (need_uT) WSGET(b.uT, WS_UT, T, D);
@@ -1106,7 +1158,7 @@ static int solve_batch(Workspace &ws, Problem &pb, double *u64, const uint8_t *m
     FEM_CUDA(cudaMemcpyAsync(b.ctl, ctl.data(), sizeof(Ctl) * ctl.size(), cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemsetAsync(b.counter, 0, 4 * sizeof(int), s));
     {
-        static const KernelClock kc0 = {{~0ull, ~0ull}, {0, 0}, {0, 0}, {0, 0}};
+        static const KernelClock kc0 = {{~0ull, ~0ull, ~0ull, ~0ull}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
         FEM_CUDA(cudaMemcpyAsync(b.kclock, &kc0, sizeof(kc0), cudaMemcpyHostToDevice, s));
     }
     if (b.tab) FEM_CUDA(cudaMemcpyAsync(b.tab, pb.desc.data(), sizeof(InstDesc) * pb.desc.size(), cudaMemcpyHostToDevice, s));
@@ -1122,6 +1174,7 @@ static int solve_batch(Workspace &ws, Problem &pb, double *u64, const uint8_t *m
     Core<T> core(pb, b, SM_NONLINEAR, params_from(o), hc);
     core.max_steps_ = *std::max_element(pb.n_steps.begin(), pb.n_steps.end());
     core.variant_ = o.apply_kernel;
+    core.cg_fused_opt_ = o.cg_fused;
     int rc = core.run(s, o.timeout_s);
     if (rc == FEM_OK) FEM_CUDA(core.read_clock(s));
     at.ms = core.apply_ms_;
@@ -1171,13 +1224,14 @@ static int adjoint_batch(Workspace &ws, Problem &pb, const double *ustar, const 
     FEM_CUDA(cudaMemcpyAsync(b.ctl, ctl.data(), sizeof(Ctl) * ctl.size(), cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemsetAsync(b.counter, 0, 4 * sizeof(int), s));
     {
-        static const KernelClock kc0 = {{~0ull, ~0ull}, {0, 0}, {0, 0}, {0, 0}};
+        static const KernelClock kc0 = {{~0ull, ~0ull, ~0ull, ~0ull}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
         FEM_CUDA(cudaMemcpyAsync(b.kclock, &kc0, sizeof(kc0), cudaMemcpyHostToDevice, s));
     }
     SolverParams prm = params_from(o);
     Core<T> core(pb, b, SM_LINEAR, prm, hc);
     core.ustar64_ = ustar;
     core.variant_ = o.apply_kernel;
+    core.cg_fused_opt_ = o.cg_fused;
     int rc = core.run(s, o.timeout_s);
     if (rc == FEM_OK) FEM_CUDA(core.read_clock(s));
     at.ms = core.apply_ms_;

@@ -43,7 +43,7 @@ class fem_options(ctypes.Structure):
                 ("newton_atol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
                 ("pcg_rtol", ctypes.c_double), ("pcg_maxit", ctypes.c_int),
                 ("pcg_chunk", ctypes.c_int), ("step_begin", ctypes.c_int),
-                ("apply_kernel", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("apply_kernel", ctypes.c_int), ("cg_fused", ctypes.c_int),
                 ("timeout_s", ctypes.c_double)]
 
 

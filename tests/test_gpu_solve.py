@@ -110,6 +110,19 @@ def test_simp_cantilever_small(apply_kernel):
     assert rel_l2(u64, ref) <= TOL_FP64
 
 
+@pytest.mark.parametrize("n", [8, 9])
+@pytest.mark.parametrize("apply_kernel", [1, 5])
+def test_fused_cg_kernel(apply_kernel, n):
+    """cg_fused = 1: one kernel per CG iteration (the update of iteration
+    k-1 recomputed per node inside the apply of iteration k, owners writing
+    the vectors); same parity bar as the two-kernel CG."""
+    w = inputs.c1(n=n, n_steps=10)
+    ref = oracle_c1(n)
+    u32, st32 = gpu_solve(w, 2, newton_rtol=1e-12, apply_kernel=apply_kernel, cg_fused=1)
+    assert st32["status"] == 0 and st32["apply_kernel"] == apply_kernel
+    assert rel_l2(u32, ref) <= TOL_REFINED
+
+
 def test_stored_tangent_kernel_needs_neohooke():
     """Apply kernel 4 is refused (argument error, nothing launched) for a
     linear-elastic problem."""
