@@ -43,3 +43,34 @@ def test_host_only_calls():
     assert "NULL" in L.fem_last_error().decode() or "out" in L.fem_last_error().decode()
     mat = fem.material(7, 1.0, 0.3)
     assert L.fem_residual(None, ctypes.byref(mat), 0, None, None, None, None, None, None) == fem.FEM_ERR_ARG
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that a C compiler gives the same struct from include/fem.h."""
+    import shutil
+    import subprocess
+    from paper_2212_00964_gb300 import fem
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    structs = [fem.fem_material, fem.fem_options, fem.fem_stats, fem.fem_bc, fem.fem_instance]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "fem.h"', "int main(void) {"]
+    for S in structs:
+        n = S.__name__
+        lines.append(f'printf("{n} size %zu\\n", sizeof({n}));')
+        for f in S._fields_:
+            lines.append(f'printf("{n} {f[0]} %zu\\n", offsetof({n}, {f[0]}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for S in structs:
+        n = S.__name__
+        assert got[(n, "size")] == ctypes.sizeof(S), n
+        for f in S._fields_:
+            assert got[(n, f[0])] == getattr(S, f[0]).offset, (n, f[0])
