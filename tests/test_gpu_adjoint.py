@@ -142,3 +142,39 @@ def test_c2_full_size_compliance_closed_form():
         cp_ = float(f @ gpu_forward(F, m, w, tp, 2, newton_rtol=1e-12))
         cm_ = float(f @ gpu_forward(F, m, w, tm, 2, newton_rtol=1e-12))
         assert abs(float(g[e]) - (cp_ - cm_) / (2 * h)) <= TOL_ADJ_FD * np.abs(closed).max()
+
+
+@pytest.mark.slow
+def test_c4_full_size_forward_and_adjoint_properties():
+    """128^3 Neo-Hookean with a log-normal stiffness field, 5 load steps, at
+    full size (6.4M DOF, beyond the oracle's direct solver), by properties
+    that hold at any size: the oracle's FP64 residual at the mixed-precision
+    GPU solution is at the Newton tolerance; the GPU adjoint variable solves
+    the oracle's tangent system K(u) lambda = dJ/du on the free DOFs; and the
+    GPU gradient equals the oracle's vector-Jacobian product at that lambda."""
+    F = fem()
+    w = inputs.c4()
+    m = F.fem_mesh(w.nx, w.ny, w.nz)
+    mat = F.material(w.kind, w.E, w.nu)
+    J = face_objective(w)
+    o = F.default_options(newton_rtol=1e-10)
+    u = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
+    st = F.fem_solve(m, mat, dev(w.mask), dev(w.u_bar), u, None, dev(w.cell_param), w.n_steps, o)
+    assert st["status"] == 0 and st["load_steps"] == w.n_steps
+    om = oracle.mesh(w.nx, w.ny, w.nz)
+    omat = oracle.Material(w.kind, w.E, w.nu)
+    uh = host(u)
+    R = oracle.residual(om, omat, uh, w.cell_param, None, w.mask)
+    assert np.linalg.norm(R) <= 1e-9 * st["ref_rnorm"]
+    uu = u.clone().requires_grad_(True)
+    dJdu = torch.autograd.grad(J(uu), uu)[0].contiguous()
+    lam = torch.zeros_like(u)
+    g, sta = F.fem_adjoint(m, mat, dev(w.mask), u, dJdu, dev(w.cell_param), options=o, lam=lam)
+    assert sta["status"] == 0
+    lh, b = host(lam), host(dJdu)
+    free = w.mask == 0
+    assert np.all(lh[~free] == 0)
+    Kl = oracle.tangent_apply(om, omat, uh, lh, w.cell_param, w.mask)
+    assert np.linalg.norm((Kl - b)[free]) <= 1e-8 * np.linalg.norm(b[free])
+    g_ref = oracle.vjp(om, omat, uh, lh, w.cell_param, w.mask)
+    assert rel_l2(host(g), g_ref) <= TOL_ADJ_ORACLE
