@@ -214,8 +214,9 @@ def aggregate(total_s_local: float, units_per_rank: int, steps: int, dist=None):
 def suite(F, inputs, torch):
     """Secondary measurements of the hot path (each timed once after one
     untimed run): the 256-instance batched Neo-Hookean solve, the SIMP
-    compliance adjoint on 128x64x64 and the 128^3 Neo-Hookean solve with the
-    adjoint of the face-displacement objective."""
+    compliance adjoint on 128x64x64, the 128^3 Neo-Hookean solve with the
+    adjoint of the face-displacement objective, the standalone tangent apply
+    in FP32 and FP64 at 64^3 and 128^3, and the 8^3 linear-elastic solve."""
     out = {}
     opt = F.default_options(newton_rtol=1e-10)
 
@@ -296,6 +297,59 @@ def suite(F, inputs, torch):
                     "adjoint_cg_iters": sta["pcg_iters"],
                     "tangent_apply_gdofs": w.n_dofs / (stf["apply_ms"] / max(stf["apply_samples"], 1) / 1e3) / 1e9,
                     "status": [stf["status"], sta["status"]]}
+    del m, u, g
+
+    # standalone tangent apply through the ABI cell operator (fem_tangent_apply:
+    # zeroing y, the apply, the masked rows) at 64^3 and 128^3 in FP32 and FP64,
+    # state u = 0.02 h N(0,1) (seed 11), direction x = N(0,1) (seed 12); L2
+    # flushed before each timed call; median of 10
+    import numpy as np
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out["apply_standalone"] = {}
+    for n in (64, 128):
+        w = inputs.c4(n=n) if n == 128 else inputs.c1(n=n)
+        m = F.fem_mesh(w.nx, w.ny, w.nz)
+        mat = F.material(w.kind, w.E, w.nu)
+        mask = torch.tensor(w.mask, device="cuda")
+        u0 = 0.02 / n * np.random.default_rng(11).standard_normal(w.n_dofs)
+        x0 = np.random.default_rng(12).standard_normal(w.n_dofs)
+        for name, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+            uu = torch.tensor(u0, dtype=dt, device="cuda")
+            xx = torch.tensor(x0, dtype=dt, device="cuda")
+            yy = torch.empty_like(xx)
+            cp = torch.tensor(w.cell_param, dtype=dt, device="cuda") if w.cell_param is not None else None
+            F.fem_tangent_apply(m, mat, uu, xx, cp, mask, yy)
+            times = []
+            for _ in range(10):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                F.fem_tangent_apply(m, mat, uu, xx, cp, mask, yy)
+                e1.record()
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+            t = float(np.median(times))
+            out["apply_standalone"][f"{n}^3_{name}"] = {"dofs": w.n_dofs, "time_us": t * 1e6,
+                                                         "gdofs": w.n_dofs / t / 1e9}
+        del m, uu, xx, yy
+    del flush
+
+    # c0: linear elasticity 8^3, one FP64 linear solve to 1e-10
+    w = inputs.c0()
+    m = F.fem_mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)
+    mat = F.material(w.kind, w.E, w.nu)
+    f = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
+    F.fem_load_traction(m, w.traction[0], w.traction[1], f)
+    u = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
+    mask, ubar = torch.tensor(w.mask, device="cuda"), torch.tensor(w.u_bar, device="cuda")
+    o64 = F.default_options(precision=F.FEM_FP64, newton_rtol=1e-10, pcg_rtol=1e-10)
+
+    def fwd0():
+        u.zero_()
+        return F.fem_solve(m, mat, mask, ubar, u, f, None, 1, o64)
+
+    t0s, st0 = timed(fwd0)
+    out["le_c0"] = {"dofs": w.n_dofs, "solve_s": t0s, "cg_iters": st0["pcg_iters"], "status": st0["status"]}
     return out
 
 
