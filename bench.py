@@ -49,9 +49,11 @@ NH_APPLY_FLOPS_PER_CELL = 3269
 # part of the per-Gauss-point kinematics, so their own algorithmic count is
 # lower: kernel 4 (cof F and the scalars stored) keeps F = I + H 3 of the 87
 # kinematics flops -> 8 x 194 + 965 = 2,517; kernel 5 (scalars stored) keeps
-# F 3 and cof F 27 -> 8 x 221 + 965 = 2,733.
+# F 3 and cof F 27 -> 8 x 221 + 965 = 2,733; kernel 6 (scalars and the
+# displacement gradient stored) also skips the 3 x 96 flops of the gradient of
+# u -> 2,445.
 APPLY_FLOPS_PER_CELL = {1: NH_APPLY_FLOPS_PER_CELL, 2: NH_APPLY_FLOPS_PER_CELL, 3: NH_APPLY_FLOPS_PER_CELL,
-                        4: 2517, 5: 2733}
+                        4: 2517, 5: 2733, 6: 2445}
 # DRAM bytes (read + write) of one launch of a CG apply kernel, by apply
 # kernel id, from the ncu capture summarised in profiles/ (kernel 5:
 # cg_apply_nh64_kernel5.md; cold caches under ncu).  Valid only for the kernel
@@ -88,7 +90,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--pcg-rtol", type=float, default=3e-3, help="inner CG relative tolerance")
     ap.add_argument("--apply-kernel", type=int, default=0,
-                    help="0 autotuned, 1 per-cell, 2 bricks, 3 per-cell 4 CTA/SM, 4/5 stored tangent data/scalars")
+                    help="0 autotuned, 1 per-cell, 2 bricks, 3 per-cell 4 CTA/SM, 4/5/6 stored tangent data")
     ap.add_argument("--cg-fused", type=int, default=0,
                     help="1: one fused CG kernel per iteration (update + apply) instead of two")
     ap.add_argument("--no-suite", action="store_true",
@@ -493,7 +495,8 @@ def run_gb300(args):
                      "kernel": {1: "cell_kernel<float,NH,CM_APPLY_PCG,3>", 2: "apply_brick<float,NH>",
                                 3: "cell_kernel<float,NH,CM_APPLY_PCG,4>",
                                 4: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN=1>",
-                                5: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN=2>"}.get(st0.get("apply_kernel"), "?"),
+                                5: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN=2>",
+                                6: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN=3>"}.get(st0.get("apply_kernel"), "?"),
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": apply_traffic(st0.get("apply_kernel")),
                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",

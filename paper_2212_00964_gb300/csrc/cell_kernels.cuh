@@ -164,10 +164,12 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
             // all node values are loaded before any arithmetic, so the gather
             // latency is exposed once per cell
             T ue[3][8], xe[3][8];
+            if (!(IS_APPLY && KIN == 3)) {  // kernel 6 reads the stored displacement gradient instead
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
+                for (int c = 0; c < 3; ++c)
 #pragma unroll
-                for (int n = 0; n < 8; ++n) ue[c][n] = ub[3 * nid[n] + c];
+                    for (int n = 0; n < 8; ++n) ue[c][n] = ub[3 * nid[n] + c];
+            }
             if (IS_APPLY) {
                 const T *xb = a.x + d.dof_off;
 #pragma unroll
@@ -185,8 +187,27 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                 }
             }
             T Gu[3][3][4], Gx[3][3][4];
+            if (IS_APPLY && KIN == 3) {
+                const T *kb = a.kin + kin3_slot(d.tile_off, cell, 8 * KIN2_VALUES);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) grad_sf<T>(ue[c], ihx, ihy, ihz, Gu[c]);
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int dd = 0; dd < 3; ++dd)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) Gu[c][dd][q] = kb[((c * 3 + dd) * 4 + q) * CELL_BLOCK];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) grad_sf<T>(ue[c], ihx, ihy, ihz, Gu[c]);
+            }
+            if (IS_DIAG && NH && a.kin && a.kin_mode == 3) {  // store the gradient for kernel 6
+                T *kb = a.kin + kin3_slot(d.tile_off, cell, 8 * KIN2_VALUES);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int dd = 0; dd < 3; ++dd)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) kb[((c * 3 + dd) * 4 + q) * CELL_BLOCK] = Gu[c][dd][q];
+            }
             if (IS_APPLY) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) grad_sf<T>(xe[c], ihx, ihy, ihz, Gx[c]);
@@ -234,9 +255,10 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                         dH[3 * c + 1] = Gx[c][1][al + 2 * ga];
                         dH[3 * c + 2] = Gx[c][2][al + 2 * be];
                     }
-                    if (NH && KIN == 2) {
+                    if (NH && (KIN == 2 || KIN == 3)) {
                         // scalars stored by the diagonal kernel of this Newton iteration
-                        const T *kb = a.kin + kin_slot(d.tile_off, cell, gp * KIN2_VALUES, KIN2_VALUES);
+                        const T *kb = a.kin + (KIN == 3 ? kin3_slot(d.tile_off, cell, gp * KIN2_VALUES)
+                                                        : kin_slot(d.tile_off, cell, gp * KIN2_VALUES, KIN2_VALUES));
                         const T k1 = kb[0], beta = kb[CELL_BLOCK], e1 = kb[2 * CELL_BLOCK], e2 = kb[3 * CELL_BLOCK];
                         T F[9], C[9];
 #pragma unroll
@@ -280,10 +302,11 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
                     NHPoint<T> q;
                     if (NH) {
                         nh_point<T>(H, m, q);
-                        if (a.kin && a.kin_mode == 2) {  // store the tangent scalars for the CG applies
+                        if (a.kin && (a.kin_mode == 2 || a.kin_mode == 3)) {  // tangent scalars for the CG applies
                             NHKin<T> kq;
                             nh_kin<T>(q, m, kq);
-                            T *kb = a.kin + kin_slot(d.tile_off, cell, gp * KIN2_VALUES, KIN2_VALUES);
+                            T *kb = a.kin + (a.kin_mode == 3 ? kin3_slot(d.tile_off, cell, gp * KIN2_VALUES)
+                                                             : kin_slot(d.tile_off, cell, gp * KIN2_VALUES, KIN2_VALUES));
                             kb[0] = kq.k1;
                             kb[CELL_BLOCK] = kq.beta;
                             kb[2 * CELL_BLOCK] = kq.e1;

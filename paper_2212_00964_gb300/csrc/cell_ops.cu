@@ -114,6 +114,8 @@ static void warm_one()
                                            : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 1>), CELL_BLOCK, 0);
             resident_grid((const void *)(b ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, 2>
                                            : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 2>), CELL_BLOCK, 0);
+            resident_grid((const void *)(b ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, 3>
+                                           : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 3>), CELL_BLOCK, 0);
         }
     }
     resident_grid((const void *)apply_brick<T, NH>, BRICK_X * BRICK_Y * BRICK_Z, 0);
@@ -156,10 +158,12 @@ template cudaError_t launch_apply_cell4<float>(bool, const CellArgs<float> &, cu
 template <typename T>
 cudaError_t launch_apply_kin(bool nh, const CellArgs<T> &a, cudaStream_t s)
 {
-    if (!nh || !a.kin || (a.kin_mode != 1 && a.kin_mode != 2)) return cudaErrorInvalidValue;
+    if (!nh || !a.kin || a.kin_mode < 1 || a.kin_mode > 3) return cudaErrorInvalidValue;
     auto f = a.kin_mode == 1
                  ? (a.tab ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, 1> : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 1>)
-                 : (a.tab ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, 2> : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 2>);
+             : a.kin_mode == 2
+                 ? (a.tab ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, 2> : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 2>)
+                 : (a.tab ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, 3> : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 3>);
     int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, 0));
     if (g < 1) return cudaSuccess;
     count_launch();

@@ -736,6 +736,13 @@ __device__ __forceinline__ void nh_dstress_kin(const NHKin<T> &k, const T *H, co
 // The scalar part alone (k1, beta, e1, e2): cof(F) is then rebuilt from the
 // gathered state, and 32 values per cell fit the L2 beside the CG vectors.
 constexpr int KIN2_VALUES = 4;
+// Mode 3: the scalars of mode 2 plus the 36 sum-factorised displacement
+// gradient values of the cell (the CG apply then gathers no displacement).
+constexpr int KIN3_CELL = 8 * KIN2_VALUES + 36;  // values per cell
+__device__ __forceinline__ int64_t kin3_slot(int64_t tile_off, int cell, int v)
+{
+    return ((tile_off + cell / CELL_BLOCK) * KIN3_CELL + v) * CELL_BLOCK + cell % CELL_BLOCK;
+}
 
 // Slot of value v (0..8*per_gp-1) of instance-local cell `cell` in the
 // stored tangent data: [tile][v][CELL_BLOCK] over the global tiles, so a

@@ -624,8 +624,8 @@ class Core {
             ca.u = b_.uT;
             ca.y = b_.dg;
             // apply kernels 4 and 5 read the tangent data stored here
-            ca.kin = (variant_ == 4 || variant_ == 5) ? b_.kin : nullptr;
-            ca.kin_mode = variant_ == 4 ? 1 : 2;
+            ca.kin = variant_ >= 4 ? b_.kin : nullptr;
+            ca.kin_mode = variant_ - 3;
             if ((e = launch_cell<T>(CM_DIAG_CTL, pb_.nh, ca, s)) != cudaSuccess) return e;
         }
         k_pcg_init<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
@@ -716,9 +716,9 @@ class Core {
         }
         ca.n_tiles = pb_.n_tiles;
         if (variant_ == 3) return launch_apply_cell4<T>(pb_.nh, ca, s);
-        if (variant_ == 4 || variant_ == 5) {
+        if (variant_ >= 4) {
             ca.kin = b_.kin;
-            ca.kin_mode = variant_ == 4 ? 1 : 2;
+            ca.kin_mode = variant_ - 3;
             return launch_apply_kin<T>(pb_.nh, ca, s);
         }
         return launch_cell<T>(CM_APPLY_PCG, pb_.nh, ca, s);
@@ -771,9 +771,9 @@ class Core {
             cudaEventDestroy(e0);
             return (cudaGetLastError(), 2);
         }
-        float best = 1e30f, times[5] = {-1.f, -1.f, -1.f, -1.f, -1.f};
+        float best = 1e30f, times[6] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
         int choice = 1;
-        const int n_var = (pb_.nh && b_.kin) ? 5 : 3;
+        const int n_var = (pb_.nh && b_.kin) ? 6 : 3;
         for (int v = 1; v <= n_var; ++v) {
             variant_ = v;
             // fresh control blocks for each variant (the apply's epilogue updates them)
@@ -784,7 +784,7 @@ class Core {
                 cd.n_tiles = pb_.n_tiles;
                 cd.y = b_.dg;
                 cd.kin = b_.kin;
-                cd.kin_mode = v == 4 ? 1 : 2;
+                cd.kin_mode = v - 3;
                 ok = launch_cell<T>(CM_DIAG_CTL, pb_.nh, cd, s) == cudaSuccess;
             }
             ok = ok && launch_apply(ca, s) == cudaSuccess;
@@ -810,9 +810,10 @@ class Core {
             if (env[0] == '1')
                 fprintf(stderr,
                         "femgb autotune: D=%lld instances=%d per-cell %.3f ms, bricks %.3f ms, "
-                        "per-cell(4 CTA/SM) %.3f ms, stored tangent %.3f ms, stored scalars %.3f ms -> %d\n",
+                        "per-cell(4 CTA/SM) %.3f ms, stored tangent %.3f ms, stored scalars %.3f ms, "
+                        "stored scalars + gradient %.3f ms -> %d\n",
                         (long long)pb_.D, (int)pb_.desc.size(), times[0] / 3, times[1] / 3, times[2] / 3,
-                        times[3] / 3, times[4] / 3, choice);
+                        times[3] / 3, times[4] / 3, times[5] / 3, choice);
         }
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = choice;
@@ -921,8 +922,8 @@ class Core {
 
     int check_variant() const
     {
-        if ((variant_ == 4 || variant_ == 5) && !(pb_.nh && b_.kin))
-            return (set_error("apply_kernel 4/5 (stored tangent data) needs a Neo-Hookean problem and its buffer "
+        if (variant_ >= 4 && !(pb_.nh && b_.kin))
+            return (set_error("apply_kernel 4-6 (stored tangent data) needs a Neo-Hookean problem and its buffer "
                               "(not available in fem_solve_static)"),
                     FEM_ERR_ARG);
         return FEM_OK;
@@ -1023,7 +1024,7 @@ static int check_options(const fem_options &o)
         return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
     if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
         !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
-        o.apply_kernel < 0 || o.apply_kernel > 5 || o.cg_fused < 0 || o.cg_fused > 1)
+        o.apply_kernel < 0 || o.apply_kernel > 6 || o.cg_fused < 0 || o.cg_fused > 1)
         return (set_error("invalid solver options"), FEM_ERR_ARG);
     return FEM_OK;
 }
