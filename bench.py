@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--pcg-rtol", type=float, default=3e-3, help="inner CG relative tolerance")
     ap.add_argument("--apply-kernel", type=int, default=0,
                     help="0 autotuned, 1 per-cell, 2 bricks, 3 per-cell 4 CTA/SM, 4/5/6 stored tangent data")
+    ap.add_argument("--newton-res32", type=int, default=1,
+                    help="0: FP64 Newton residual in every iteration")
     ap.add_argument("--cg-fused", type=int, default=0,
                     help="1: one fused CG kernel per iteration (update + apply) instead of two")
     ap.add_argument("--no-suite", action="store_true",
@@ -382,7 +384,8 @@ def run_gb300(args):
     ubar = torch.tensor(w.u_bar, device="cuda")
     u = torch.zeros(D, dtype=torch.float64, device="cuda")
     opt = F.default_options(precision=F.FEM_MIXED, newton_rtol=1e-10, pcg_rtol=args.pcg_rtol,
-                            apply_kernel=args.apply_kernel, cg_fused=args.cg_fused)
+                            apply_kernel=args.apply_kernel, cg_fused=args.cg_fused,
+                            newton_res32=args.newton_res32)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def barrier():

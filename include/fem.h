@@ -178,6 +178,10 @@ typedef struct {
                             per node inside the tangent apply) with apply kernels 1 and 5
                             (measured slower on GB300: an option, not the default) */
     double timeout_s;    /* host watchdog for one solve (0 = none) */
+    int newton_res32;    /* FEM_MIXED: 1 (default) evaluates the Newton residual in FP32 after a
+                            load step's first correction and while ||R_free|| > 1e-2 ||R_ref||
+                            (far above FP32 rounding; such a residual never decides
+                            convergence), FP64 otherwise; 0: always FP64 */
 } fem_options;
 
 typedef struct {

@@ -57,4 +57,5 @@ extern "C" void fem_default_options(fem_options *o)
     o->apply_kernel = 0;
     o->cg_fused = 0;
     o->timeout_s = 0.0;
+    o->newton_res32 = 1;
 }

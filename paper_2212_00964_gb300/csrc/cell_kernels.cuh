@@ -121,7 +121,11 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
             acc_k = k;
             acc_slot = slot;
             worked = true;
-        } else if (MODE == CM_RESIDUAL_CTL || MODE == CM_APPLY_CTL) {
+        } else if (MODE == CM_RESIDUAL_CTL) {
+            // the round's residual runs in one precision: FP32 while far from
+            // convergence (Ctl::res32), FP64 otherwise
+            if (a.ctl[k].status != 0 || (sizeof(T) == 4) != (a.ctl[k].res32 != 0)) continue;
+        } else if (MODE == CM_APPLY_CTL) {
             if (a.ctl[k].status != 0) continue;
         } else if (MODE == CM_DIAG_CTL) {
             if (a.ctl[k].status != 0 || !a.ctl[k].solving) continue;

@@ -106,8 +106,8 @@ struct Ctl {
     // CG in the single-reduction (Chronopoulos-Gear) form, iteration i:
     // gamma_i = (r_i, z_i), delta_i = (A z_i, z_i), rr_i = (r_i, r_i), alpha_i
     double gamma[4], delta[4], rr[4], alpha[4];
-    int go;  // CG runs: set by the CG start, cleared by block 0 of the kernel that stops it
-    int pad2_;
+    int go;     // CG runs: set by the CG start, cleared by block 0 of the kernel that stops it
+    int res32;  // this round's Newton residual is evaluated in FP32 (far from convergence)
 };
 
 // Live kernel-span statistics of the two CG kernels, in device memory: the

@@ -37,6 +37,7 @@ struct SolverParams {
     double eta;
     int pcg_maxit;
     int chunk;
+    double res32_tau;  // FP32 Newton residual while ||R|| > res32_tau ||R_ref|| (0: always FP64)
 };
 
 enum SolveMode { SM_NONLINEAR = 0, SM_LINEAR = 1 };
@@ -116,9 +117,11 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_res_init(const VecArgs<T> a)
 {
     VEC_ITEMS_BEGIN
     if (c.status != 0) continue;
+    const bool r32 = c.res32 != 0;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const int64_t j = base + i;
         a.R64[j] = a.rhs ? -a.rhs[j] : 0.0;
+        if (r32) a.s[j] = 0;  // accumulator of the FP32 residual
     }
     VEC_ITEMS_END
 }
@@ -130,9 +133,10 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_res_finish(const VecArgs<T> a)
     VEC_ITEMS_BEGIN
     if (c.status != 0) continue;
     double acc = 0;
+    const bool r32 = c.res32 != 0;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const int64_t j = base + i;
-        const double R = a.mask[j] ? 0.0 : a.R64[j];
+        const double R = a.mask[j] ? 0.0 : a.R64[j] + (r32 ? (double)a.s[j] : 0.0);
         a.R64[j] = R;
         acc += R * R;
         a.r[j] = (T)(-R);
@@ -158,6 +162,7 @@ __global__ void k_control(Ctl *ctl, int n_inst, SolverParams prm, int *counter)
     c.lift = 0;
     if (c.status != 0) return;
     const double rn = sqrt(c.r_norm2);
+    const bool was32 = c.res32 != 0;  // an FP32 residual never decides convergence
     c.r_norm2 = 0;
     c.r_norm = rn;
     if (!isfinite(rn)) { c.status = FEM_ERR_NONFINITE; return; }
@@ -165,7 +170,7 @@ __global__ void k_control(Ctl *ctl, int n_inst, SolverParams prm, int *counter)
     bool lift = first != 0;
     if (!lift) {
         if (c.r_ref < 0) c.r_ref = rn > 0 ? rn : 1.0;
-        if (rn <= prm.rtol * c.r_ref || rn <= prm.atol) {
+        if (!was32 && (rn <= prm.rtol * c.r_ref || rn <= prm.atol)) {
             c.steps_done++;
             if (c.step >= c.n_steps) {
                 c.status = 1;
@@ -180,6 +185,11 @@ __global__ void k_control(Ctl *ctl, int n_inst, SolverParams prm, int *counter)
         }
     }
     c.lift = lift ? 1 : 0;
+    // precision of the next round's residual: FP32 after a lifting round and
+    // while ||R|| stays above res32_tau ||R_ref|| (its rounding error is then
+    // far below the inexactness of the CG correction); FP64 near convergence,
+    // where it is the refinement residual
+    c.res32 = (prm.res32_tau > 0 && (lift || rn > prm.res32_tau * c.r_ref)) ? 1 : 0;
     c.newton_it++;
     c.newton_total++;
     c.solving = 1;
@@ -546,6 +556,10 @@ class Core {
     Core(const Problem &pb, const Buffers<T> &b, SolveMode mode, const SolverParams &prm, int *h_counter)
         : pb_(pb), b_(b), mode_(mode), prm_(prm), h_counter_(h_counter)
     {
+        // the FP32 residual serves the nonlinear solve only (the linear and
+        // adjoint solves compute their residual by an FP64 apply), and only
+        // when the cell kernels run in FP32
+        if (mode_ != SM_NONLINEAR || std::is_same<T, double>::value) prm_.res32_tau = 0;
         va_ = VecArgs<T>{};
         va_.d0 = pb.desc[0];
         va_.tab = pb.desc.size() > 1 ? b.tab : nullptr;
@@ -586,6 +600,19 @@ class Core {
             if (mode_ == SM_NONLINEAR) {
                 ca.u = b_.u64;
                 if ((e = launch_cell<double>(CM_RESIDUAL_CTL, pb_.nh, ca, s)) != cudaSuccess) return e;
+                if (!std::is_same<T, double>::value && prm_.res32_tau > 0) {
+                    // instances whose residual runs in FP32 this round, into s
+                    CellArgs<T> c32{};
+                    c32.d0 = pb_.desc[0];
+                    c32.tab = va_.tab;
+                    c32.n_inst = ni;
+                    c32.n_tiles = pb_.n_tiles;
+                    c32.ctl = b_.ctl;
+                    c32.cell_param = b_.cpT;
+                    c32.u = b_.uT;
+                    c32.y = b_.s;
+                    if ((e = launch_cell<T>(CM_RESIDUAL_CTL, pb_.nh, c32, s)) != cudaSuccess) return e;
+                }
             } else {
                 ca.u = ustar64_;
                 ca.x = b_.u64;
@@ -1015,6 +1042,7 @@ static SolverParams params_from(const fem_options &o)
     p.eta = o.pcg_rtol;
     p.pcg_maxit = o.pcg_maxit;
     p.chunk = o.pcg_chunk > 0 ? o.pcg_chunk : 16;
+    p.res32_tau = (o.precision == FEM_MIXED && o.newton_res32) ? 1e-2 : 0.0;
     return p;
 }
 
@@ -1024,7 +1052,8 @@ static int check_options(const fem_options &o)
         return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
     if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
         !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
-        o.apply_kernel < 0 || o.apply_kernel > 6 || o.cg_fused < 0 || o.cg_fused > 1)
+        o.apply_kernel < 0 || o.apply_kernel > 6 || o.cg_fused < 0 || o.cg_fused > 1 || o.newton_res32 < 0 ||
+        o.newton_res32 > 1)
         return (set_error("invalid solver options"), FEM_ERR_ARG);
     return FEM_OK;
 }
