@@ -58,9 +58,9 @@ APPLY_FLOPS_PER_CELL = {1: NH_APPLY_FLOPS_PER_CELL, 2: NH_APPLY_FLOPS_PER_CELL, 
 # kernel id, from the ncu capture summarised in profiles/ (kernel 6:
 # cg_apply_nh64_kernel6.md; cold caches under ncu).  Valid only for the kernel
 # sources the capture was taken on: reported as null once their hash changes.
-APPLY_TRAFFIC_BYTES = {6: 77.93408e6 + 1.357824e6}
+APPLY_TRAFFIC_BYTES = {6: 77.93536e6 + 1.577472e6}
 APPLY_TRAFFIC_SOURCES = ("paper_2212_00964_gb300/csrc/cell_kernels.cuh", "paper_2212_00964_gb300/csrc/fem_internal.cuh")
-APPLY_TRAFFIC_SHA256 = "85b59149ad27e386a9e7265396700df861dc1db9bd25fc6fb897ccdc1b9e6098"
+APPLY_TRAFFIC_SHA256 = "075c317aa4c533f1b6d4b864e693bdf6a94698b9a13a59964bdb02b9c0c8f71b"
 # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Bytes a launch must move (u, x read; y written; FP32): 12 * D.
