@@ -53,7 +53,7 @@ NH_APPLY_FLOPS_PER_CELL = 3269
 # displacement gradient stored) also skips the 3 x 96 flops of the gradient of
 # u -> 2,445.
 APPLY_FLOPS_PER_CELL = {1: NH_APPLY_FLOPS_PER_CELL, 2: NH_APPLY_FLOPS_PER_CELL, 3: NH_APPLY_FLOPS_PER_CELL,
-                        4: 2517, 5: 2733, 6: 2445}
+                        4: 2517, 5: 2733, 6: 2445, 7: 2445}
 # DRAM bytes (read + write) of one launch of a CG apply kernel, by apply
 # kernel id, from the ncu capture summarised in profiles/ (kernel 6:
 # cg_apply_nh64_kernel6.md; cold caches under ncu).  Valid only for the kernel
@@ -506,7 +506,8 @@ def run_gb300(args):
                                 3: "cell_kernel<float,NH,CM_APPLY_PCG,4>",
                                 4: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN=1>",
                                 5: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN=2>",
-                                6: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN=3>"}.get(st0.get("apply_kernel"), "?"),
+                                6: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN=3>",
+                                7: "cell_kernel<float,NH,CM_APPLY_PCG,4,KIN=3>"}.get(st0.get("apply_kernel"), "?"),
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": apply_traffic(st0.get("apply_kernel")),
                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",

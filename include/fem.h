@@ -172,7 +172,8 @@ typedef struct {
                             5 = as 4 storing only the four tangent scalars per
                                 Gauss point (cof(F) rebuilt from the state),
                             6 = as 5 also storing the cell's displacement
-                                gradient (no displacement gather in the apply) */
+                                gradient (no displacement gather in the apply),
+                            7 = as 6 with a register budget for 4 CTAs per SM */
     int cg_fused;        /* 0: separate CG apply and update kernels; 1: one fused kernel per CG
                             iteration (the vector update of the previous iteration recomputed
                             per node inside the tangent apply) with apply kernels 1 and 5

@@ -116,6 +116,8 @@ static void warm_one()
                                            : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 2>), CELL_BLOCK, 0);
             resident_grid((const void *)(b ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, 3>
                                            : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 3>), CELL_BLOCK, 0);
+            resident_grid((const void *)(b ? cell_kernel<T, 1, CM_APPLY_PCG, 4, true, 3>
+                                           : cell_kernel<T, 1, CM_APPLY_PCG, 4, false, 3>), CELL_BLOCK, 0);
         }
     }
     resident_grid((const void *)apply_brick<T, NH>, BRICK_X * BRICK_Y * BRICK_Z, 0);
@@ -156,9 +158,16 @@ template cudaError_t launch_apply_cell4<float>(bool, const CellArgs<float> &, cu
 // CG apply on stored Neo-Hookean tangent data (a.kin filled by the diagonal
 // in mode a.kin_mode: 1 cof(F) + scalars, 2 scalars only).
 template <typename T>
-cudaError_t launch_apply_kin(bool nh, const CellArgs<T> &a, cudaStream_t s)
+cudaError_t launch_apply_kin(bool nh, const CellArgs<T> &a, cudaStream_t s, bool four_ctas)
 {
     if (!nh || !a.kin || a.kin_mode < 1 || a.kin_mode > 3) return cudaErrorInvalidValue;
+    if (four_ctas && a.kin_mode == 3) {  // kernel 6 fits 128 registers without spills
+        auto f4 = a.tab ? cell_kernel<T, 1, CM_APPLY_PCG, 4, true, 3> : cell_kernel<T, 1, CM_APPLY_PCG, 4, false, 3>;
+        int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f4, CELL_BLOCK, 0));
+        if (g < 1) return cudaSuccess;
+        count_launch();
+        return launch_pdl(f4, (int)g, CELL_BLOCK, 0, s, a);
+    }
     auto f = a.kin_mode == 1
                  ? (a.tab ? cell_kernel<T, 1, CM_APPLY_PCG, 3, true, 1> : cell_kernel<T, 1, CM_APPLY_PCG, 3, false, 1>)
              : a.kin_mode == 2
@@ -169,8 +178,8 @@ cudaError_t launch_apply_kin(bool nh, const CellArgs<T> &a, cudaStream_t s)
     count_launch();
     return launch_pdl(f, (int)g, CELL_BLOCK, 0, s, a);  // begins with pdl_wait()
 }
-template cudaError_t launch_apply_kin<float>(bool, const CellArgs<float> &, cudaStream_t);
-template cudaError_t launch_apply_kin<double>(bool, const CellArgs<double> &, cudaStream_t);
+template cudaError_t launch_apply_kin<float>(bool, const CellArgs<float> &, cudaStream_t, bool);
+template cudaError_t launch_apply_kin<double>(bool, const CellArgs<double> &, cudaStream_t, bool);
 template cudaError_t launch_apply_cell4<double>(bool, const CellArgs<double> &, cudaStream_t);
 template cudaError_t launch_apply_brick<double>(bool, const CellArgs<double> &, cudaStream_t);
 

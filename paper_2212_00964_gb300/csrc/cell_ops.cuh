@@ -19,7 +19,7 @@ template <typename T>
 cudaError_t launch_apply_cell4(bool nh, const CellArgs<T> &a, cudaStream_t s);
 
 template <typename T>
-cudaError_t launch_apply_kin(bool nh, const CellArgs<T> &a, cudaStream_t s);
+cudaError_t launch_apply_kin(bool nh, const CellArgs<T> &a, cudaStream_t s, bool four_ctas = false);
 
 // Launch with programmatic stream serialisation (the kernel must begin with
 // pdl_wait() before it reads anything its predecessor wrote).

@@ -652,7 +652,7 @@ class Core {
             ca.y = b_.dg;
             // apply kernels 4 and 5 read the tangent data stored here
             ca.kin = variant_ >= 4 ? b_.kin : nullptr;
-            ca.kin_mode = variant_ - 3;
+            ca.kin_mode = variant_ == 7 ? 3 : variant_ - 3;
             if ((e = launch_cell<T>(CM_DIAG_CTL, pb_.nh, ca, s)) != cudaSuccess) return e;
         }
         k_pcg_init<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
@@ -745,8 +745,8 @@ class Core {
         if (variant_ == 3) return launch_apply_cell4<T>(pb_.nh, ca, s);
         if (variant_ >= 4) {
             ca.kin = b_.kin;
-            ca.kin_mode = variant_ - 3;
-            return launch_apply_kin<T>(pb_.nh, ca, s);
+            ca.kin_mode = variant_ == 7 ? 3 : variant_ - 3;
+            return launch_apply_kin<T>(pb_.nh, ca, s, variant_ == 7);
         }
         return launch_cell<T>(CM_APPLY_PCG, pb_.nh, ca, s);
     }
@@ -798,9 +798,9 @@ class Core {
             cudaEventDestroy(e0);
             return (cudaGetLastError(), 2);
         }
-        float best = 1e30f, times[6] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
+        float best = 1e30f, times[7] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
         int choice = 1;
-        const int n_var = (pb_.nh && b_.kin) ? 6 : 3;
+        const int n_var = (pb_.nh && b_.kin) ? 7 : 3;
         for (int v = 1; v <= n_var; ++v) {
             variant_ = v;
             // fresh control blocks for each variant (the apply's epilogue updates them)
@@ -811,7 +811,7 @@ class Core {
                 cd.n_tiles = pb_.n_tiles;
                 cd.y = b_.dg;
                 cd.kin = b_.kin;
-                cd.kin_mode = v - 3;
+                cd.kin_mode = v == 7 ? 3 : v - 3;
                 ok = launch_cell<T>(CM_DIAG_CTL, pb_.nh, cd, s) == cudaSuccess;
             }
             ok = ok && launch_apply(ca, s) == cudaSuccess;
@@ -838,9 +838,9 @@ class Core {
                 fprintf(stderr,
                         "femgb autotune: D=%lld instances=%d per-cell %.3f ms, bricks %.3f ms, "
                         "per-cell(4 CTA/SM) %.3f ms, stored tangent %.3f ms, stored scalars %.3f ms, "
-                        "stored scalars + gradient %.3f ms -> %d\n",
+                        "stored scalars + gradient %.3f ms (4 CTA/SM %.3f ms) -> %d\n",
                         (long long)pb_.D, (int)pb_.desc.size(), times[0] / 3, times[1] / 3, times[2] / 3,
-                        times[3] / 3, times[4] / 3, times[5] / 3, choice);
+                        times[3] / 3, times[4] / 3, times[5] / 3, times[6] / 3, choice);
         }
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = choice;
@@ -950,7 +950,7 @@ class Core {
     int check_variant() const
     {
         if (variant_ >= 4 && !(pb_.nh && b_.kin))
-            return (set_error("apply_kernel 4-6 (stored tangent data) needs a Neo-Hookean problem and its buffer "
+            return (set_error("apply_kernel 4-7 (stored tangent data) needs a Neo-Hookean problem and its buffer "
                               "(not available in fem_solve_static)"),
                     FEM_ERR_ARG);
         return FEM_OK;
@@ -1004,7 +1004,8 @@ class Core {
     int cg_fused_opt_ = 0;  // 1: fused CG kernel where the apply kernel allows it
     bool fused_ = false;    // CG iterations run as the fused update + apply kernel
     int variant_ = 0;       // CG apply kernel: 0 autotune, 1 per-cell, 2 bricks, 3 per-cell at 4 CTA/SM,
-                            // 4 per-cell on stored NH tangent data, 5 on stored NH tangent scalars
+                            // 4 per-cell on stored NH tangent data, 5 on stored NH tangent scalars,
+                            // 6 on stored scalars and displacement gradient, 7 as 6 at 4 CTA/SM
     double apply_ms_ = 0;   // sampled device time of CG applies
     int apply_samples_ = 0;
     double update_ms_ = 0;  // sampled device time of CG vector updates
@@ -1052,7 +1053,7 @@ static int check_options(const fem_options &o)
         return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
     if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
         !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
-        o.apply_kernel < 0 || o.apply_kernel > 6 || o.cg_fused < 0 || o.cg_fused > 1 || o.newton_res32 < 0 ||
+        o.apply_kernel < 0 || o.apply_kernel > 7 || o.cg_fused < 0 || o.cg_fused > 1 || o.newton_res32 < 0 ||
         o.newton_res32 > 1)
         return (set_error("invalid solver options"), FEM_ERR_ARG);
     return FEM_OK;
