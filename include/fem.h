@@ -194,11 +194,12 @@ typedef struct {
     double final_rnorm;  /* last ||R_free|| (double precision) */
     double time_ms;      /* wall time of the call */
     double apply_ms;     /* summed device time of the CG tangent-apply launches that did work
-                            (first block start to last block end, %globaltimer) */
+                            (first block start to last working block end, %globaltimer; with
+                            fem_options.cg_fused the fused update + apply launches) */
     int apply_samples;   /* number of such launches */
     int apply_launches;  /* CG tangent-apply launches that did work */
     int apply_kernel;    /* CG apply kernel that ran (see fem_options.apply_kernel) */
-    double update_ms;    /* the same for the CG vector-update launches */
+    double update_ms;    /* the same for the CG vector-update launches (0 with cg_fused) */
     int update_samples;
 } fem_stats;
 

@@ -1,0 +1,37 @@
+"""Host-side logic of bench.py (no GPU): the workload name shared by both
+arms, and the guard that reports the ncu DRAM traffic only for the apply
+kernel and the kernel sources the capture was taken on."""
+import importlib.util
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def load_bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+def test_workload_name_counts_dofs():
+    b = load_bench()
+    assert "(823875 DOF)" in b.workload_name(64)
+    assert b.workload_name(8).startswith("Neo-Hookean 8^3")
+
+
+def test_traffic_only_for_the_captured_kernel_and_sources():
+    b = load_bench()
+    for k in range(1, 8):
+        t = b.apply_traffic(k)
+        assert (t is None) == (k not in b.APPLY_TRAFFIC_BYTES)
+    k = next(iter(b.APPLY_TRAFFIC_BYTES))
+    assert b.apply_traffic(k) == b.APPLY_TRAFFIC_BYTES[k]
+    b.APPLY_TRAFFIC_SHA256 = "0" * 64  # sources changed since the capture
+    assert b.apply_traffic(k) is None
+
+
+def test_every_apply_kernel_has_a_flop_count_and_name():
+    b = load_bench()
+    assert set(b.APPLY_FLOPS_PER_CELL) == set(range(1, 8))
+    assert all(0 < v <= b.NH_APPLY_FLOPS_PER_CELL for v in b.APPLY_FLOPS_PER_CELL.values())
