@@ -151,6 +151,20 @@ int fem_vjp(fem_mesh_t m, const fem_material *mat, int precision, const void *u,
 int fem_assemble_csr(fem_mesh_t m, const fem_material *mat, int precision, const void *u,
                      const void *cell_param, const uint8_t *mask, void *vals, void *stream);
 
+/* The paper's linear solver (Sec. 5 item 2) on an assembled matrix:
+ * Jacobi-preconditioned BiCGSTAB for A x = b, A given by vals[nnz] in the
+ * mesh's CSR pattern (FEM_MESH_CSR; e.g. from fem_assemble_csr, whose
+ * prescribed rows are identity rows, so b holds the prescribed values
+ * there).  precision FEM_FP64 (vals, b, x double) or FEM_FP32 (float); dot
+ * products in double.  x: start value in, solution out (device).  Stops when
+ * ||b - A x|| <= rtol ||b||; FEM_ERR_NOT_CONVERGED after maxit iterations
+ * (x holds the last iterate), FEM_ERR_BREAKDOWN / FEM_ERR_NONFINITE on a
+ * vanishing or non-finite BiCGSTAB scalar.  *iters and *rel_res (may be
+ * NULL) receive the iterations and ||r|| / ||b||.  Synchronises the stream
+ * once per dot product; serialised per mesh handle. */
+int fem_bicgstab_csr(fem_mesh_t m, int precision, const void *vals, const void *b, void *x, double rtol,
+                     int maxit, int *iters, double *rel_res, void *stream);
+
 /* ---------------------------------------------------------------- solvers -- */
 typedef struct {
     int precision;       /* FEM_MIXED (default) or FEM_FP64 */

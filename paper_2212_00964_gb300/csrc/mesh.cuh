@@ -8,8 +8,11 @@
 namespace femgb {
 
 // Named device buffers that grow on demand and are never shrunk.
+// Slots 0..31 belong to the solvers; WS_BICG0.. to the assembled-matrix solver.
+enum { WS_BICG0 = 32 };
+
 struct Workspace {
-    enum { N_SLOTS = 32 };
+    enum { N_SLOTS = 48 };
     void *ptr[N_SLOTS] = {};
     size_t cap[N_SLOTS] = {};
 

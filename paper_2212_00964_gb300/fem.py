@@ -92,6 +92,7 @@ def lib():
     L.fem_tangent_diag.argtypes = [P, MP, I, P, P, P, P, P]
     L.fem_vjp.argtypes = [P, MP, I, P, P, P, P, P, P]
     L.fem_assemble_csr.argtypes = [P, MP, I, P, P, P, P, P]
+    L.fem_bicgstab_csr.argtypes = [P, I, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     L.fem_default_options.argtypes = [ctypes.POINTER(fem_options)]
     L.fem_default_options.restype = None
     L.fem_solve.argtypes = [P, MP, ctypes.POINTER(fem_bc), P, I, ctypes.POINTER(fem_options), P,
@@ -280,6 +281,20 @@ def fem_assemble_csr(m: Mesh, mat: fem_material, u, cell_param=None, mask=None, 
                                   _ptr(mask, torch.uint8, m.n_dofs, "mask"), _ptr(vals, dt, m.nnz, "vals"),
                                   _stream(stream)), "fem_assemble_csr")
     return vals
+
+
+def fem_bicgstab_csr(m: Mesh, vals, b, x=None, rtol=1e-10, maxit=10000, stream=None, check=True):
+    """Jacobi-BiCGSTAB on an assembled matrix; returns (x, iterations, ||r||/||b||)."""
+    dt = vals.dtype
+    x = torch.zeros_like(b) if x is None else x
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    rc = lib().fem_bicgstab_csr(m.handle, _prec(dt), _ptr(vals, dt, m.nnz, "vals"), _ptr(b, dt, m.n_dofs, "b"),
+                                _ptr(x, dt, m.n_dofs, "x"), ctypes.c_double(rtol), int(maxit), ctypes.byref(it),
+                                ctypes.byref(res), _stream(stream))
+    if check:
+        _check(rc, "fem_bicgstab_csr")
+    return x, it.value, res.value
 
 
 def _bc(m: Mesh, mask, u_bar=None, f_ext=None) -> fem_bc:
