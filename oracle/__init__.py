@@ -6,9 +6,11 @@ CPU-baseline leg of ``bench.py`` may import this package; the product path
 library.
 
 ``fem_oracle.c`` holds the plain element-level definitions (shape functions,
-Gauss rule, constitutive laws, element residual / JVP, assembly); this module
-loads it with ctypes and exposes numpy-level functions.  ``oracle.solve``
-holds the Newton / adjoint drivers (library ``spsolve`` as the linear step).
+Gauss rule, constitutive laws, element residual / JVP, assembly, the scalar
+Poisson element of Sec. 3.1); this module loads it with ctypes and exposes
+numpy-level functions.  ``oracle.solve`` holds the Newton / adjoint drivers
+(library ``spsolve`` as the linear step); ``oracle.poisson`` the forward
+solve, objective and adjoint gradient of the full-field inference problem.
 """
 from __future__ import annotations
 
@@ -69,6 +71,9 @@ def lib():
         L.oracle_vjp.argtypes = [I64, I64, P, P] + mat + [P, P, P, P, P]
         L.oracle_body_force.argtypes = [I64, P, P, P, P, P]
         L.oracle_traction.argtypes = [I, I, I, P, P, I, P, P]
+        L.oracle_poisson_element.argtypes = [P, P, I64, D, P, P]
+        L.oracle_poisson_apply.argtypes = [I64, I64, P, P, D, P, P, P]
+        L.oracle_poisson_load.argtypes = [I64, I64, P, P, P, P, P]
         _lib = L
     return _lib
 

@@ -686,3 +686,84 @@ void oracle_traction(int nx, int ny, int nz, const int32_t *conn, const double *
                     }
             }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Scalar Poisson problem of Sec. 3.1 (full-field inference): strong form    */
+/* Eq. (24), -alpha Lap u = b in Omega with u = 0 on the whole boundary, and */
+/* its weak form Eq. (25).  One DOF per node (DOF id = node id).  Reading:   */
+/* the controlled source is discretised by its nodal values theta,           */
+/* b^h = sum_a N_a theta_a, so the right-hand side of Eq. (26) is            */
+/* F(theta) = M theta with the mass matrix M.                                */
+/* ------------------------------------------------------------------------ */
+
+/* Element matrices of cell e, 2x2x2 Gauss:
+ *   Ke[8a+b] = alpha int_{Omega_e} grad N_a . grad N_b   (left side of Eq. (25))
+ *   Me[8a+b] =       int_{Omega_e} N_a N_b               (right side, b = b^h)
+ * Either output may be NULL. */
+void oracle_poisson_element(const int32_t *conn, const double *X, int64_t e, double alpha, double *Ke,
+                            double *Me)
+{
+    double gp[24], w[8], N[8], gradN[24];
+    oracle_gauss(gp, w);
+    for (int t = 0; t < 64; ++t) {
+        if (Ke) Ke[t] = 0.0;
+        if (Me) Me[t] = 0.0;
+    }
+    for (int q = 0; q < 8; ++q) {
+        double detJ = cell_geometry(conn, X, e, gp + 3 * q, N, gradN);
+        for (int a = 0; a < 8; ++a)
+            for (int b = 0; b < 8; ++b) {
+                if (Ke) {
+                    double g = 0.0;
+                    for (int j = 0; j < 3; ++j) g += gradN[3 * a + j] * gradN[3 * b + j];
+                    Ke[8 * a + b] += w[q] * detJ * alpha * g;
+                }
+                if (Me) Me[8 * a + b] += w[q] * detJ * N[a] * N[b];
+            }
+    }
+}
+
+/* y = A x matrix-free (left side of Eq. (25) discretised).  With a mask
+ * (mask[n] != 0: u_n prescribed to 0) the constrained entries of x are
+ * removed from the product and y_c = x_c, as for the vector operators. */
+void oracle_poisson_apply(int64_t n_nodes, int64_t n_cells, const int32_t *conn, const double *X,
+                          double alpha, const double *x, const uint8_t *mask, double *y)
+{
+    double Ke[64], xe[8];
+    for (int64_t n = 0; n < n_nodes; ++n) y[n] = 0.0;
+    for (int64_t e = 0; e < n_cells; ++e) {
+        oracle_poisson_element(conn, X, e, alpha, Ke, NULL);
+        for (int a = 0; a < 8; ++a) {
+            int64_t n = conn[8 * e + a];
+            xe[a] = (mask && mask[n]) ? 0.0 : x[n];
+        }
+        for (int a = 0; a < 8; ++a) {
+            double s = 0.0;
+            for (int b = 0; b < 8; ++b) s += Ke[8 * a + b] * xe[b];
+            y[conn[8 * e + a]] += s;
+        }
+    }
+    if (mask)
+        for (int64_t n = 0; n < n_nodes; ++n)
+            if (mask[n]) y[n] = x[n];
+}
+
+/* F = M theta (right side of Eq. (25) with b = b^h); F_c = 0 where masked,
+ * the prescribed value. */
+void oracle_poisson_load(int64_t n_nodes, int64_t n_cells, const int32_t *conn, const double *X,
+                         const double *theta, const uint8_t *mask, double *F)
+{
+    double Me[64];
+    for (int64_t n = 0; n < n_nodes; ++n) F[n] = 0.0;
+    for (int64_t e = 0; e < n_cells; ++e) {
+        oracle_poisson_element(conn, X, e, 1.0, NULL, Me);
+        for (int a = 0; a < 8; ++a) {
+            double s = 0.0;
+            for (int b = 0; b < 8; ++b) s += Me[8 * a + b] * theta[conn[8 * e + b]];
+            F[conn[8 * e + a]] += s;
+        }
+    }
+    if (mask)
+        for (int64_t n = 0; n < n_nodes; ++n)
+            if (mask[n]) F[n] = 0.0;
+}

@@ -171,3 +171,63 @@ def c4(n=128, seed=4, target_seed=5001, n_steps=5) -> Workload:
 def fd_cells(n_cells, k=64, seed=7):
     """Cells picked for finite-difference checks."""
     return np.sort(np.random.default_rng(seed).choice(n_cells, size=min(k, n_cells), replace=False))
+
+
+@dataclass
+class PoissonInference:
+    """Full-field inference from sparse observations (the scalar Poisson
+    example): box, coefficient alpha, the boundary nodes (u = 0 there), the
+    nodal source values theta_true of the bimodal source and the observed
+    node ids.  One DOF per node."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    lx: float
+    ly: float
+    lz: float
+    alpha: float
+    mask: np.ndarray        # uint8 [N], 1 = boundary node (u = 0)
+    theta_true: np.ndarray  # float64 [N], nodal values of the source b
+    obs: np.ndarray         # int64 [n_obs], sorted interior node ids
+
+    @property
+    def n_nodes(self):
+        return (self.nx + 1) * (self.ny + 1) * (self.nz + 1)
+
+    @property
+    def n_cells(self):
+        return self.nx * self.ny * self.nz
+
+
+def boundary_nodes(nx, ny, nz):
+    """uint8 [N]: 1 on every node of the six faces of the box."""
+    mask = np.zeros((nx + 1) * (ny + 1) * (nz + 1), np.uint8)
+    for f in ("x0", "x1", "y0", "y1", "z0", "z1"):
+        mask[face_nodes(nx, ny, nz, f)] = 1
+    return mask
+
+
+def poisson_inference(nx=50, ny=50, nz=10, lx=1.0, ly=1.0, lz=0.2, n_obs=250, seed=11,
+                      alpha=1.0) -> PoissonInference:
+    """The paper's 50x50x10 hexahedra on a 1 x 1 x 0.2 box with 250 observed
+    points.  Source b(x) = 10 exp(-10 |x - c1|^2) + 10 exp(-10 |x - c2|^2),
+    evaluated at the nodes, with the centres c1 = (0.25 lx, 0.25 ly, 0.5 lz)
+    and c2 = (0.75 lx, 0.75 ly, 0.5 lz) (the printed centres lie outside the
+    box; these are their positions scaled into it).  Observed nodes: n_obs
+    distinct interior nodes drawn uniformly (default_rng(seed))."""
+    I, J, K = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
+    ids = node_index(nx, ny, nz, I, J, K).reshape(-1)
+    pos = np.zeros((ids.size, 3))
+    pos[ids, 0] = (lx * I / nx).reshape(-1)
+    pos[ids, 1] = (ly * J / ny).reshape(-1)
+    pos[ids, 2] = (lz * K / nz).reshape(-1)
+    theta = np.zeros(ids.size)
+    for c in ((0.25 * lx, 0.25 * ly, 0.5 * lz), (0.75 * lx, 0.75 * ly, 0.5 * lz)):
+        theta += 10.0 * np.exp(-10.0 * ((pos - np.asarray(c)) ** 2).sum(axis=1))
+    mask = boundary_nodes(nx, ny, nz)
+    interior = np.flatnonzero(mask == 0)
+    obs = np.sort(np.random.default_rng(seed).choice(interior, size=min(n_obs, interior.size),
+                                                      replace=False)).astype(np.int64)
+    return PoissonInference(f"poisson_{nx}x{ny}x{nz}_obs{obs.size}", nx, ny, nz, lx, ly, lz, alpha,
+                            mask, theta, obs)

@@ -8,7 +8,8 @@ operand in the oracle shows up as a mismatch:
     sigma : grad phi with JVPs);
   * ``nh_energy``: the Neo-Hookean strain energy W(F) typed from Sec. 2.3,
     Eq. (13) of the paper (the oracle only has P = dW/dF and dP);
-  * rigid-body modes, face-load weights and the uniaxial closed form.
+  * rigid-body modes, face-load weights and the uniaxial closed form;
+  * ``hex_volume``: cell volume by a 3-point Gauss rule of det J.
 """
 from __future__ import annotations
 
@@ -106,6 +107,25 @@ def fd_grad(fun, x, h=1e-6):
         xm[idx] -= h
         g[idx] = (fun(xp) - fun(xm)) / (2 * h)
     return g
+
+
+def hex_volume(Xe):
+    """Volume of a trilinear hexahedron with corners Xe [8, 3] (VTK order):
+    the integral of det(dX/dxi) over [-1, 1]^3 by a 3-point Gauss-Legendre
+    rule per axis (det J is at most quadratic in each reference coordinate,
+    so the rule is exact)."""
+    pts, wts = np.polynomial.legendre.leggauss(3)
+    s = CORNERS
+    vol = 0.0
+    for a, wa in zip(pts, wts):
+        for b, wb in zip(pts, wts):
+            for c, wc in zip(pts, wts):
+                p = np.array([a, b, c])
+                f = 1 + s * p[None, :]
+                dN = np.stack([s[:, 0] * f[:, 1] * f[:, 2], f[:, 0] * s[:, 1] * f[:, 2],
+                               f[:, 0] * f[:, 1] * s[:, 2]], axis=1) / 8
+                vol += wa * wb * wc * np.linalg.det(Xe.T @ dN)
+    return vol
 
 
 def random_rotation(rng):
