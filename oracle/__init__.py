@@ -7,10 +7,12 @@ library.
 
 ``fem_oracle.c`` holds the plain element-level definitions (shape functions,
 Gauss rule, constitutive laws, element residual / JVP, assembly, the scalar
-Poisson element of Sec. 3.1); this module loads it with ctypes and exposes
-numpy-level functions.  ``oracle.solve`` holds the Newton / adjoint drivers
-(library ``spsolve`` as the linear step); ``oracle.poisson`` the forward
-solve, objective and adjoint gradient of the full-field inference problem.
+Poisson element of Sec. 3.1, the J2 return map of Sec. 2.3); this module
+loads it with ctypes and exposes numpy-level functions.  ``oracle.solve``
+holds the Newton / adjoint drivers (library ``spsolve`` as the linear step);
+``oracle.poisson`` the forward solve, objective and adjoint gradient of the
+full-field inference problem; ``oracle.plasticity`` the load-stepped J2
+plasticity solve with its Gauss-point history.
 """
 from __future__ import annotations
 
@@ -74,6 +76,14 @@ def lib():
         L.oracle_poisson_element.argtypes = [P, P, I64, D, P, P]
         L.oracle_poisson_apply.argtypes = [I64, I64, P, P, D, P, P, P]
         L.oracle_poisson_load.argtypes = [I64, I64, P, P, P, P, P]
+        L.oracle_j2_stress.argtypes = [D, D, D, P, P, P, P, P]
+        L.oracle_j2_stress.restype = D
+        L.oracle_j2_dstress.argtypes = [D, D, D, P, P, P, P, P]
+        L.oracle_gp_jxw.argtypes = [I64, P, P, P]
+        L.oracle_j2_residual.argtypes = [I64, I64, P, P, D, D, D, P, P, P, P, P, P, P, P]
+        L.oracle_j2_residual.restype = I64
+        L.oracle_j2_tangent_apply.argtypes = [I64, I64, P, P, D, D, D, P, P, P, P, P, P]
+        L.oracle_j2_element_tangent.argtypes = [P, P, D, D, D, P, P, P, I64, P]
         _lib = L
     return _lib
 

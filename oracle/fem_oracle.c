@@ -767,3 +767,210 @@ void oracle_poisson_load(int64_t n_nodes, int64_t n_cells, const int32_t *conn, 
         for (int64_t n = 0; n < n_nodes; ++n)
             if (mask[n]) F[n] = 0.0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Perfect J2 plasticity of Sec. 2.3, Eqs. (14)-(15), small strain.  The     */
+/* history of every Gauss point is the total strain eps^{k-1} and the stress */
+/* sigma^{k-1} of the previous load step, stored as full 3x3 matrices:       */
+/* hist_eps[(8e+q)*9 + 3i+j], hist_sig likewise.  Lame parameters as r3.     */
+/*   sigma_trial = sigma^{k-1} + lam tr(d eps) I + 2 mu d eps,                */
+/*   d eps = sym(grad u^k) - eps^{k-1},  s = dev(sigma_trial),               */
+/*   q = sqrt(3/2 s:s),  f = q - sigma_y,                                     */
+/*   sigma^k = sigma_trial - (s/q) <f>_+ .                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Trial state of one Gauss point: eps^k (sym H), sigma_trial, its deviator
+ * s and q.  Returns f_yield. */
+static double j2_trial(double E, double nu, double sy, const double *eps_old, const double *sig_old,
+                       const double *H, double *eps, double *sig_tr, double *s, double *q)
+{
+    double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    double mu = E / (2.0 * (1.0 + nu));
+    double de[9], tr = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            eps[3 * i + j] = 0.5 * (H[3 * i + j] + H[3 * j + i]);
+            de[3 * i + j] = eps[3 * i + j] - eps_old[3 * i + j];
+        }
+    tr = de[0] + de[4] + de[8];
+    for (int t = 0; t < 9; ++t) sig_tr[t] = sig_old[t] + 2.0 * mu * de[t] + ((t % 4) == 0 ? lam * tr : 0.0);
+    double p = (sig_tr[0] + sig_tr[4] + sig_tr[8]) / 3.0, ss = 0.0;
+    for (int t = 0; t < 9; ++t) {
+        s[t] = sig_tr[t] - ((t % 4) == 0 ? p : 0.0);
+        ss += s[t] * s[t];
+    }
+    *q = sqrt(1.5 * ss);
+    return *q - sy;
+}
+
+/* sigma^k of Eq. (15) (and eps^k if eps_out).  Returns f_yield of the trial
+ * state (> 0: the point yields in this step). */
+double oracle_j2_stress(double E, double nu, double sy, const double *eps_old, const double *sig_old,
+                        const double *H, double *sig, double *eps_out)
+{
+    double eps[9], sig_tr[9], s[9], q;
+    double f = j2_trial(E, nu, sy, eps_old, sig_old, H, eps, sig_tr, s, &q);
+    double ramp = 0.5 * (f + fabs(f));
+    for (int t = 0; t < 9; ++t) sig[t] = sig_tr[t] - (ramp > 0.0 ? s[t] / q * ramp : 0.0);
+    if (eps_out)
+        for (int t = 0; t < 9; ++t) eps_out[t] = eps[t];
+    return f;
+}
+
+/* d sigma^k for the direction dH (the derivative of Eq. (15) in eps^k,
+ * d eps = sym dH).  Elastic (f <= 0; reading: the ramp's derivative at
+ * f = 0 is taken as 0): lam tr(d eps) I + 2 mu d eps.  Plastic (f > 0),
+ * from sigma^k = p I + (sigma_y / q) s:
+ *   dp = K tr(d eps), K = lam + 2 mu / 3,  ds = 2 mu dev(d eps),
+ *   dq = (3/2) s:ds / q = 3 mu s:d eps / q,
+ *   d sigma = dp I + sigma_y (ds / q - s dq / q^2).                           */
+void oracle_j2_dstress(double E, double nu, double sy, const double *eps_old, const double *sig_old,
+                       const double *H, const double *dH, double *dsig)
+{
+    double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    double mu = E / (2.0 * (1.0 + nu));
+    double eps[9], sig_tr[9], s[9], q, de[9];
+    double f = j2_trial(E, nu, sy, eps_old, sig_old, H, eps, sig_tr, s, &q);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) de[3 * i + j] = 0.5 * (dH[3 * i + j] + dH[3 * j + i]);
+    double tr = de[0] + de[4] + de[8];
+    if (f <= 0.0) {
+        for (int t = 0; t < 9; ++t) dsig[t] = 2.0 * mu * de[t] + ((t % 4) == 0 ? lam * tr : 0.0);
+        return;
+    }
+    double K = lam + 2.0 * mu / 3.0, sde = 0.0;
+    for (int t = 0; t < 9; ++t) sde += s[t] * de[t];
+    double dq = 3.0 * mu * sde / q;
+    for (int t = 0; t < 9; ++t) {
+        double ds = 2.0 * mu * (de[t] - ((t % 4) == 0 ? tr / 3.0 : 0.0));
+        dsig[t] = ((t % 4) == 0 ? K * tr : 0.0) + sy * (ds / q - s[t] * dq / (q * q));
+    }
+}
+
+/* Gauss-point weights w_q det J of every cell: jxw[8e + q]. */
+void oracle_gp_jxw(int64_t n_cells, const int32_t *conn, const double *X, double *jxw)
+{
+    double gp[24], w[8], N[8], gradN[24];
+    oracle_gauss(gp, w);
+    for (int64_t e = 0; e < n_cells; ++e)
+        for (int q = 0; q < 8; ++q) jxw[8 * e + q] = w[q] * cell_geometry(conn, X, e, gp + 3 * q, N, gradN);
+}
+
+/* Gradient H = grad u of cell e at Gauss point q (from the 24 nodal values). */
+static double j2_grad(const int32_t *conn, const double *X, int64_t e, int q, const double *ue, double *H,
+                      double *gradN)
+{
+    double gp[24], w[8], N[8];
+    oracle_gauss(gp, w);
+    double detJ = cell_geometry(conn, X, e, gp + 3 * q, N, gradN);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int a = 0; a < 8; ++a) s += ue[3 * a + i] * gradN[3 * a + j];
+            H[3 * i + j] = s;
+        }
+    return w[q] * detJ;
+}
+
+/* R = sum_e int sigma^k(grad u) : grad phi - f_ext, R_c = 0 (Eq. (14) in the
+ * weak form of Eq. (2)).  Also writes eps^k, sigma^k of every Gauss point
+ * (if eps_new / sig_new are given: the history once u has converged).
+ * Returns the number of Gauss points whose trial state yields. */
+int64_t oracle_j2_residual(int64_t n_nodes, int64_t n_cells, const int32_t *conn, const double *X, double E,
+                           double nu, double sy, const double *hist_eps, const double *hist_sig,
+                           const double *u, const double *f_ext, const uint8_t *mask, double *R,
+                           double *eps_new, double *sig_new)
+{
+    double ue[24], H[9], gradN[24], sig[9], eps[9];
+    int64_t n_yield = 0;
+    for (int64_t d = 0; d < 3 * n_nodes; ++d) R[d] = f_ext ? -f_ext[d] : 0.0;
+    for (int64_t e = 0; e < n_cells; ++e) {
+        gather(conn, e, u, ue);
+        for (int q = 0; q < 8; ++q) {
+            double jw = j2_grad(conn, X, e, q, ue, H, gradN);
+            int64_t g = 8 * e + q;
+            double f = oracle_j2_stress(E, nu, sy, hist_eps + 9 * g, hist_sig + 9 * g, H, sig, eps);
+            if (f > 0.0) ++n_yield;
+            if (eps_new)
+                for (int t = 0; t < 9; ++t) eps_new[9 * g + t] = eps[t];
+            if (sig_new)
+                for (int t = 0; t < 9; ++t) sig_new[9 * g + t] = sig[t];
+            for (int a = 0; a < 8; ++a)
+                for (int i = 0; i < 3; ++i) {
+                    double s = 0.0;
+                    for (int j = 0; j < 3; ++j) s += sig[3 * i + j] * gradN[3 * a + j];
+                    R[3 * (int64_t)conn[8 * e + a] + i] += jw * s;
+                }
+        }
+    }
+    if (mask)
+        for (int64_t d = 0; d < 3 * n_nodes; ++d)
+            if (mask[d]) R[d] = 0.0;
+    return n_yield;
+}
+
+/* Element tangent of cell e applied to xe (the JVP of the element residual). */
+static void j2_element_jvp(const int32_t *conn, const double *X, double E, double nu, double sy,
+                           const double *hist_eps, const double *hist_sig, int64_t e, const double *ue,
+                           const double *xe, double *ye)
+{
+    double H[9], dH[9], gradN[24], dsig[9];
+    for (int t = 0; t < 24; ++t) ye[t] = 0.0;
+    for (int q = 0; q < 8; ++q) {
+        double jw = j2_grad(conn, X, e, q, ue, H, gradN);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double s = 0.0;
+                for (int a = 0; a < 8; ++a) s += xe[3 * a + i] * gradN[3 * a + j];
+                dH[3 * i + j] = s;
+            }
+        int64_t g = 8 * e + q;
+        oracle_j2_dstress(E, nu, sy, hist_eps + 9 * g, hist_sig + 9 * g, H, dH, dsig);
+        for (int a = 0; a < 8; ++a)
+            for (int i = 0; i < 3; ++i) {
+                double s = 0.0;
+                for (int j = 0; j < 3; ++j) s += dsig[3 * i + j] * gradN[3 * a + j];
+                ye[3 * a + i] += jw * s;
+            }
+    }
+}
+
+/* y = K(u) x with K the tangent of the J2 residual; masked x_c removed and
+ * y_c = x_c (the same elimination as the other laws). */
+void oracle_j2_tangent_apply(int64_t n_nodes, int64_t n_cells, const int32_t *conn, const double *X,
+                             double E, double nu, double sy, const double *hist_eps,
+                             const double *hist_sig, const double *u, const double *x,
+                             const uint8_t *mask, double *y)
+{
+    double ue[24], xe[24], ye[24];
+    for (int64_t d = 0; d < 3 * n_nodes; ++d) y[d] = 0.0;
+    for (int64_t e = 0; e < n_cells; ++e) {
+        gather(conn, e, u, ue);
+        for (int a = 0; a < 8; ++a)
+            for (int i = 0; i < 3; ++i) {
+                int64_t d = 3 * (int64_t)conn[8 * e + a] + i;
+                xe[3 * a + i] = (mask && mask[d]) ? 0.0 : x[d];
+            }
+        j2_element_jvp(conn, X, E, nu, sy, hist_eps, hist_sig, e, ue, xe, ye);
+        for (int a = 0; a < 8; ++a)
+            for (int i = 0; i < 3; ++i) y[3 * (int64_t)conn[8 * e + a] + i] += ye[3 * a + i];
+    }
+    if (mask)
+        for (int64_t d = 0; d < 3 * n_nodes; ++d)
+            if (mask[d]) y[d] = x[d];
+}
+
+/* Dense element tangent of cell e (24x24 row-major), column c = JVP with
+ * the unit vector e_c; no mask (the driver eliminates prescribed DOFs). */
+void oracle_j2_element_tangent(const int32_t *conn, const double *X, double E, double nu, double sy,
+                               const double *hist_eps, const double *hist_sig, const double *u,
+                               int64_t e, double *Ke)
+{
+    double ue[24], xe[24], ye[24];
+    gather(conn, e, u, ue);
+    for (int c = 0; c < 24; ++c) {
+        for (int t = 0; t < 24; ++t) xe[t] = (t == c) ? 1.0 : 0.0;
+        j2_element_jvp(conn, X, E, nu, sy, hist_eps, hist_sig, e, ue, xe, ye);
+        for (int r = 0; r < 24; ++r) Ke[24 * r + c] = ye[r];
+    }
+}

@@ -231,3 +231,20 @@ def poisson_inference(nx=50, ny=50, nz=10, lx=1.0, ly=1.0, lz=0.2, n_obs=250, se
                                                       replace=False)).astype(np.int64)
     return PoissonInference(f"poisson_{nx}x{ny}x{nz}_obs{obs.size}", nx, ny, nz, lx, ly, lz, alpha,
                             mask, theta, obs)
+
+
+def j2_uniaxial(n=2, L=1.0, E=70e3, nu=0.3, sigma_y=250.0, strain_max=2.5 * 250.0 / 70e3, n_load=10,
+                n_unload=10):
+    """Load/unload path of the J2 plasticity example on an n^3 box of edge L:
+    symmetry rollers (u_x = 0 on x=0, u_y = 0 on y=0, u_z = 0 on z=0) and
+    u_z = L * strain on z=L, the strain rising from 0 to strain_max in n_load
+    steps and back to 0 in n_unload steps.  Returns (mask u8[D], list of
+    u_bar f64[D] per step, list of the step strains, material tuple)."""
+    strains = list(np.linspace(0.0, strain_max, n_load + 1)[1:]) + \
+        list(np.linspace(strain_max, 0.0, n_unload + 1)[1:])
+    mask = None
+    ubars = []
+    for s in strains:
+        mask, ub = dirichlet(n, n, n, [("x0", 0, 0.0), ("y0", 1, 0.0), ("z0", 2, 0.0), ("z1", 2, L * s)])
+        ubars.append(ub)
+    return mask, ubars, strains, (E, nu, sigma_y)
