@@ -248,3 +248,15 @@ def j2_uniaxial(n=2, L=1.0, E=70e3, nu=0.3, sigma_y=250.0, strain_max=2.5 * 250.
         mask, ub = dirichlet(n, n, n, [("x0", 0, 0.0), ("y0", 1, 0.0), ("z0", 2, 0.0), ("z1", 2, L * s)])
         ubars.append(ub)
     return mask, ubars, strains, (E, nu, sigma_y)
+
+
+def topopt_cantilever(nx=16, ny=8, nz=4, lx=2.0, ly=1.0, lz=0.5, volfrac=0.5, rmin=1.5):
+    """Box cantilever of the topology-optimisation loop (the paper's plate and
+    bracket geometries are not available): the SIMP law of c2, x=0 clamped,
+    total force (0, 0, -1) over the 4x4 node patch at the bottom of the far
+    face (c2's load), volume fraction 0.5, filter radius 1.5 cells, uniform
+    initial design.  Returns a Workload with extra = {volfrac, rmin}."""
+    mask, ubar = dirichlet(nx, ny, nz, [("x0", 0, 0.0), ("x0", 1, 0.0), ("x0", 2, 0.0)])
+    return Workload(f"topopt_cantilever_{nx}x{ny}x{nz}", nx, ny, nz, lx, ly, lz, SIMP, 1.0, 0.3, 3.0, 1e-3,
+                    n_steps=1, mask=mask, u_bar=ubar, point_load=simp_patch_load(nx, ny, nz),
+                    cell_param=np.full(nx * ny * nz, volfrac), extra={"volfrac": volfrac, "rmin": rmin})
