@@ -165,6 +165,49 @@ int fem_assemble_csr(fem_mesh_t m, const fem_material *mat, int precision, const
 int fem_bicgstab_csr(fem_mesh_t m, int precision, const void *vals, const void *b, void *x, double rtol,
                      int maxit, int *iters, double *rel_res, void *stream);
 
+/* ------------------------------------------------ scalar Poisson problem -- */
+/* The linear Poisson problem of the full-field inference example (Sec. 3.1):
+ * -alpha Lap u = b with u = 0 where prescribed, weak form Eq. (25), on the
+ * mesh's box with one value per NODE (node id as above, arrays of length
+ * n_nodes; no CSR needed).  mask: uint8 [n_nodes], 1 = u prescribed, or
+ * NULL.  The source is given by its nodal values theta, b^h = sum N_a theta_a,
+ * so the load is F(theta) = M theta with the mass matrix M.  precision
+ * FEM_FP64 (value arrays double) or FEM_FP32 (float; dot products double).
+ * Asynchronous on `stream` unless stated; serialised per mesh handle. */
+#define FEM_POISSON_STIFFNESS 0 /* A_ab = alpha int grad N_a . grad N_b */
+#define FEM_POISSON_MASS 1      /* M_ab = int N_a N_b */
+
+/* y = A x (op FEM_POISSON_STIFFNESS) with the prescribed columns removed and
+ * y_c = x_c; or y = M x (op FEM_POISSON_MASS) with all of x and y_c = 0.
+ * mask NULL: the plain product.  x, y: [n_nodes], distinct. */
+int fem_poisson_apply(fem_mesh_t m, int precision, double alpha, int op, const uint8_t *mask,
+                      const void *x, void *y, void *stream);
+
+/* Jacobi-preconditioned CG for A u = b with A the stiffness with prescribed
+ * rows and columns eliminated (row c reads u_c = b_c; a nonzero prescribed
+ * value needs the caller's lifting b_f - A_fc u_c).  u: start in, solution
+ * out.  Stops when ||b - A u|| <= rtol ||b||, checked every 8 iterations
+ * (so up to 7 more iterations run); FEM_ERR_NOT_CONVERGED after maxit
+ * (<= 1e6), FEM_ERR_BREAKDOWN if p^T A p <= 0, FEM_ERR_NONFINITE.  *iters,
+ * *rel_res (host, may be NULL): iterations run and ||r|| / ||b||.
+ * Synchronises the stream. */
+int fem_poisson_solve(fem_mesh_t m, int precision, double alpha, const uint8_t *mask, const void *b,
+                      void *u, double rtol, int maxit, int *iters, double *rel_res, void *stream);
+
+/* Objective of Eq. (26) and its gradient by the adjoint method (Sec. 3,
+ * Eqs. (17)-(23)): u solves A u = M theta (free rows, u = 0 on masked nodes);
+ * J = sum_i (u[obs[i]] - u_obs[i])^2 (host double *J); lambda solves
+ * A lambda = dJ/du = 2 (u - u_obs) on the observed free nodes; grad =
+ * dJ/dtheta = M lambda.  theta, u, lambda, grad: [n_nodes]; obs: int64
+ * [n_obs] node ids (device; an id outside [0, n_nodes) gives FEM_ERR_ARG;
+ * repeated ids count repeatedly); u_obs: [n_obs].  Both solves as
+ * fem_poisson_solve with (rtol, maxit); iters (host int[2], may be NULL):
+ * forward and adjoint CG iterations.  Synchronises the stream. */
+int fem_poisson_gradient(fem_mesh_t m, int precision, double alpha, const uint8_t *mask,
+                         const void *theta, const int64_t *obs, const void *u_obs, int64_t n_obs,
+                         double rtol, int maxit, void *u, void *lambda, void *grad, double *J,
+                         int *iters, void *stream);
+
 /* ---------------------------------------------------------------- solvers -- */
 typedef struct {
     int precision;       /* FEM_MIXED (default) or FEM_FP64 */

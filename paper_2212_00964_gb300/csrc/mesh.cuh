@@ -8,11 +8,12 @@
 namespace femgb {
 
 // Named device buffers that grow on demand and are never shrunk.
-// Slots 0..31 belong to the solvers; WS_BICG0.. to the assembled-matrix solver.
+// Slots 0..31 belong to the solvers, WS_BICG0.. to the assembled-matrix
+// solver, 48..63 to the scalar Poisson path.
 enum { WS_BICG0 = 32 };
 
 struct Workspace {
-    enum { N_SLOTS = 48 };
+    enum { N_SLOTS = 64 };
     void *ptr[N_SLOTS] = {};
     size_t cap[N_SLOTS] = {};
 

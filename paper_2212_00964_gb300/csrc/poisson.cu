@@ -1,0 +1,400 @@
+// poisson.cu -- the scalar Poisson path of the full-field inference example
+// (Sec. 3.1): the stiffness and mass operators of Eq. (25) as 27-point
+// stencils (poisson_core.cuh), Jacobi-preconditioned CG, and the objective
+// of Eq. (26) with its adjoint gradient.
+//
+// Layout: one value per node, node id = i + (nx+1)(j + (ny+1)k); the mask is
+// per node (1 = u prescribed).  The stencil tables (27 node classes x 27
+// offsets, per operator) are built by one thread on the device and staged
+// in shared memory by every block of the operator kernel.
+//
+// CG keeps its scalars on the device: iteration k reads rz_k = (r_k, z_k)
+// and pq_k = (p_k, A p_k) from an array indexed by k, so no launch waits on
+// the host; the host reads the residual norms once every CG_CHECK
+// iterations.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "mesh.cuh"
+#include "poisson_core.cuh"
+
+namespace femgb {
+
+namespace {
+
+constexpr int PB = 256;        // threads per block
+constexpr int CG_CHECK = 8;    // iterations between host checks
+constexpr int MAX_ITERS = 1000000;
+
+// workspace slots of this path
+enum { WS_PTAB = 48, WS_PR, WS_PZ, WS_PP, WS_PQ, WS_PDINV, WS_PSC, WS_PRHS, WS_PSMALL };
+
+int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + PB - 1) / PB, 152 * 8)); }
+
+// Both stencil tables in the value type T: tab[0, TAB) stiffness, [TAB, 2 TAB) mass.
+// Built in double by one thread (a few thousand adds), converted by the block.
+template <typename T>
+__global__ void k_pois_tables(double hx, double hy, double hz, double alpha, T *tab)
+{
+    __shared__ double t[2 * poisson::TAB];
+    __shared__ double scratch[128];
+    if (threadIdx.x == 0) poisson::stencil_tables(hx, hy, hz, alpha, t, scratch);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * poisson::TAB; i += blockDim.x) tab[i] = (T)t[i];
+}
+
+// y = op x for every node (mode: poisson::OUT_*); with dot != nullptr also
+// adds sum_n x_n y_n to *dot (one atomic per block).
+template <typename T>
+__global__ void __launch_bounds__(PB) k_pois_op(const T *__restrict__ tab, const T *__restrict__ x,
+                                               const uint8_t *__restrict__ mask, int mode, T *__restrict__ y,
+                                               int nx, int ny, int nz, int64_t N, double *dot)
+{
+    __shared__ T st[poisson::TAB];
+    __shared__ double sh[PB / 32];
+    for (int t = threadIdx.x; t < poisson::TAB; t += PB) st[t] = tab[t];
+    __syncthreads();
+    double acc = 0.0;
+    for (int64_t n = blockIdx.x * (int64_t)PB + threadIdx.x; n < N; n += (int64_t)gridDim.x * PB) {
+        const T v = poisson::operator_row<T, T>(st, x, mask, mode, n, nx, ny, nz);
+        y[n] = v;
+        acc += (double)x[n] * (double)v;
+    }
+    if (dot) {
+        const double s = block_sum<double, PB>(acc, sh);
+        if (threadIdx.x == 0) atomicAdd(dot, s);
+    }
+}
+
+template <typename T>
+__global__ void k_pois_dinv(const T *__restrict__ tab, const uint8_t *__restrict__ mask, T *__restrict__ dinv, int nx,
+                            int ny, int nz, int64_t N)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        const double d = poisson::diag_row<T>(tab, mask, n, nx, ny, nz);
+        dinv[n] = d != 0.0 ? (T)(1.0 / d) : (T)0;
+    }
+}
+
+// r = b - q (q = A u), z = D r, p = z; sc0[0] += (r, z), sc0[2] += (r, r), *bb += (b, b)
+template <typename T>
+__global__ void __launch_bounds__(PB) k_pois_cg_init(const T *__restrict__ b, const T *__restrict__ q,
+                                                    const T *__restrict__ dinv, T *__restrict__ r, T *__restrict__ z,
+                                                    T *__restrict__ p, int64_t N, double *sc0, double *bb)
+{
+    __shared__ double sh[PB / 32];
+    double rz = 0, rr = 0, b2 = 0;
+    for (int64_t n = blockIdx.x * (int64_t)PB + threadIdx.x; n < N; n += (int64_t)gridDim.x * PB) {
+        const T rn = b[n] - q[n];
+        const T zn = dinv[n] * rn;
+        r[n] = rn;
+        z[n] = zn;
+        p[n] = zn;
+        rz += (double)rn * (double)zn;
+        rr += (double)rn * (double)rn;
+        b2 += (double)b[n] * (double)b[n];
+    }
+    rz = block_sum<double, PB>(rz, sh);
+    if (threadIdx.x == 0) atomicAdd(&sc0[0], rz);
+    rr = block_sum<double, PB>(rr, sh);
+    if (threadIdx.x == 0) atomicAdd(&sc0[2], rr);
+    b2 = block_sum<double, PB>(b2, sh);
+    if (threadIdx.x == 0) atomicAdd(bb, b2);
+}
+
+// alpha_k = rz_k / pq_k (0 when pq_k <= 0: the host reports the breakdown);
+// u += alpha p, r -= alpha q, z = D r; sck1[0] += (r, z), sck1[2] += (r, r).
+template <typename T>
+__global__ void __launch_bounds__(PB) k_pois_cg_update(T *__restrict__ u, T *__restrict__ r, T *__restrict__ z,
+                                                      const T *__restrict__ p, const T *__restrict__ q,
+                                                      const T *__restrict__ dinv, int64_t N, const double *sck,
+                                                      double *sck1)
+{
+    __shared__ double sh[PB / 32];
+    const double pq = sck[1];
+    const T alpha = pq > 0.0 ? (T)(sck[0] / pq) : (T)0;
+    double rz = 0, rr = 0;
+    for (int64_t n = blockIdx.x * (int64_t)PB + threadIdx.x; n < N; n += (int64_t)gridDim.x * PB) {
+        u[n] += alpha * p[n];
+        const T rn = r[n] - alpha * q[n];
+        const T zn = dinv[n] * rn;
+        r[n] = rn;
+        z[n] = zn;
+        rz += (double)rn * (double)zn;
+        rr += (double)rn * (double)rn;
+    }
+    rz = block_sum<double, PB>(rz, sh);
+    if (threadIdx.x == 0) atomicAdd(&sck1[0], rz);
+    rr = block_sum<double, PB>(rr, sh);
+    if (threadIdx.x == 0) atomicAdd(&sck1[2], rr);
+}
+
+// beta = rz_{k+1} / rz_k; p = z + beta p
+template <typename T>
+__global__ void k_pois_cg_dir(T *__restrict__ p, const T *__restrict__ z, int64_t N, const double *sck,
+                              const double *sck1)
+{
+    const double rz = sck[0];
+    const T beta = rz > 0.0 ? (T)(sck1[0] / rz) : (T)0;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+        p[n] = z[n] + beta * p[n];
+}
+
+// Objective of Eq. (26) and the adjoint right-hand side:
+// J += (u[o] - u_obs[i])^2, rhs[o] += 2 (u[o] - u_obs[i]) on free nodes.
+// An observation index outside [0, N) sets *bad and is skipped.
+template <typename T>
+__global__ void __launch_bounds__(PB) k_pois_obs(const T *__restrict__ u, const int64_t *__restrict__ obs,
+                                                const T *__restrict__ u_obs, int64_t n_obs,
+                                                const uint8_t *__restrict__ mask, int64_t N, T *rhs, double *J,
+                                                int *bad)
+{
+    __shared__ double sh[PB / 32];
+    double acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)PB + threadIdx.x; i < n_obs; i += (int64_t)gridDim.x * PB) {
+        const int64_t o = obs[i];
+        if (o < 0 || o >= N) {
+            atomicOr(bad, 1);
+            continue;
+        }
+        const double d = (double)u[o] - (double)u_obs[i];
+        acc += d * d;
+        if (!(mask && mask[o])) atomicAdd(&rhs[o], (T)(2.0 * d));
+    }
+    acc = block_sum<double, PB>(acc, sh);
+    if (threadIdx.x == 0) atomicAdd(J, acc);
+}
+
+struct Ctx {
+    fem_mesh_t m;
+    int64_t N;
+    cudaStream_t s;
+};
+
+// Stencil tables for (alpha, the mesh's cell size) in the workspace.
+template <typename T>
+const T *make_tables(const Ctx &c, double alpha)
+{
+    T *tab = (T *)c.m->ws.get(WS_PTAB, sizeof(T) * 2 * poisson::TAB);
+    if (!tab) return nullptr;
+    k_pois_tables<T><<<1, 128, 0, c.s>>>(c.m->lx / c.m->nx, c.m->ly / c.m->ny, c.m->lz / c.m->nz, alpha, tab);
+    count_launch();
+    return tab;
+}
+
+template <typename T>
+void launch_op(const Ctx &c, const T *tab, const T *x, const uint8_t *mask, int mode, T *y, double *dot)
+{
+    k_pois_op<T><<<grid_for(c.N), PB, 0, c.s>>>(tab, x, mask, mode, y, c.m->nx, c.m->ny, c.m->nz, c.N, dot);
+    count_launch();
+}
+
+// Jacobi-PCG for the eliminated stiffness: A u = b, u in/out.
+template <typename T>
+int cg_solve(const Ctx &c, const T *tabA, const uint8_t *mask, const T *b, T *u, double rtol, int maxit, int *iters,
+             double *rel_res)
+{
+    const int64_t N = c.N;
+    T *r = (T *)c.m->ws.get(WS_PR, sizeof(T) * N);
+    T *z = (T *)c.m->ws.get(WS_PZ, sizeof(T) * N);
+    T *p = (T *)c.m->ws.get(WS_PP, sizeof(T) * N);
+    T *q = (T *)c.m->ws.get(WS_PQ, sizeof(T) * N);
+    T *dinv = (T *)c.m->ws.get(WS_PDINV, sizeof(T) * N);
+    double *sc = (double *)c.m->ws.get(WS_PSC, sizeof(double) * 3 * ((size_t)maxit + 2));
+    double *small = (double *)c.m->ws.get(WS_PSMALL, sizeof(double) * 4);
+    if (!r || !z || !p || !q || !dinv || !sc || !small) return FEM_ERR_NOMEM;
+    const int g = grid_for(N);
+    FEM_CUDA(cudaMemsetAsync(sc, 0, sizeof(double) * 3 * ((size_t)maxit + 2), c.s));
+    FEM_CUDA(cudaMemsetAsync(small, 0, sizeof(double) * 4, c.s));
+    k_pois_dinv<T><<<g, PB, 0, c.s>>>(tabA, mask, dinv, c.m->nx, c.m->ny, c.m->nz, N);
+    count_launch();
+    launch_op<T>(c, tabA, u, mask, poisson::OUT_ELIM, q, nullptr);
+    k_pois_cg_init<T><<<g, PB, 0, c.s>>>(b, q, dinv, r, z, p, N, sc, &small[0]);
+    count_launch();
+    FEM_CUDA(cudaGetLastError());
+    double h0[3], bb;
+    FEM_CUDA(cudaMemcpyAsync(h0, sc, sizeof(h0), cudaMemcpyDeviceToHost, c.s));
+    FEM_CUDA(cudaMemcpyAsync(&bb, &small[0], sizeof(double), cudaMemcpyDeviceToHost, c.s));
+    FEM_CUDA(cudaStreamSynchronize(c.s));
+    const double bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
+    double rr = h0[2];
+    if (!std::isfinite(rr) || !std::isfinite(h0[0])) return (set_error("poisson CG: non-finite residual"), FEM_ERR_NONFINITE);
+    int k = 0;
+    int rc = std::sqrt(rr) <= rtol * bn ? FEM_OK : FEM_ERR_NOT_CONVERGED;
+    std::vector<double> hs;
+    while (rc == FEM_ERR_NOT_CONVERGED && k < maxit) {
+        const int k0 = k;
+        const int k1 = std::min(maxit, k + CG_CHECK);
+        for (; k < k1; ++k) {
+            double *sck = sc + 3 * (size_t)k, *sck1 = sc + 3 * ((size_t)k + 1);
+            launch_op<T>(c, tabA, p, mask, poisson::OUT_ELIM, q, &sck[1]);
+            k_pois_cg_update<T><<<g, PB, 0, c.s>>>(u, r, z, p, q, dinv, N, sck, sck1);
+            k_pois_cg_dir<T><<<g, PB, 0, c.s>>>(p, z, N, sck, sck1);
+            count_launch(2);
+        }
+        FEM_CUDA(cudaGetLastError());
+        hs.resize(3 * (size_t)(k - k0 + 1));
+        FEM_CUDA(cudaMemcpyAsync(hs.data(), sc + 3 * (size_t)k0, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, c.s));
+        FEM_CUDA(cudaStreamSynchronize(c.s));
+        for (int j = 0; j < k - k0; ++j) {
+            const double rz = hs[3 * j], pq = hs[3 * j + 1], rr1 = hs[3 * (j + 1) + 2];
+            if (!std::isfinite(rz) || !std::isfinite(pq) || !std::isfinite(rr1)) {
+                set_error("poisson CG: non-finite scalar");
+                rc = FEM_ERR_NONFINITE;
+                break;
+            }
+            if (pq <= 0.0 && rz > 0.0) {
+                set_error("poisson CG: p^T A p <= 0 (operator not positive definite)");
+                rc = FEM_ERR_BREAKDOWN;
+                break;
+            }
+            rr = rr1;
+            if (std::sqrt(rr) <= rtol * bn) {
+                rc = FEM_OK;
+                // the later iterations of this batch ran as well; report the final residual
+                rr = hs[3 * (size_t)(k - k0) + 2];
+                break;
+            }
+        }
+    }
+    if (iters) *iters = k;
+    if (rel_res) *rel_res = std::sqrt(rr) / bn;
+    if (rc == FEM_ERR_NOT_CONVERGED) set_error("poisson CG: iteration limit reached");
+    return rc;
+}
+
+int check_mesh(fem_mesh_t m, const char *what)
+{
+    if (!m) return (set_error(std::string(what) + ": NULL mesh"), FEM_ERR_ARG);
+    return FEM_OK;
+}
+
+template <typename T>
+int apply_t(fem_mesh_t m, double alpha, int op, const uint8_t *mask, const T *x, T *y, cudaStream_t s)
+{
+    Ctx c{m, m->n_nodes, s};
+    const T *tab = make_tables<T>(c, alpha);
+    if (!tab) return FEM_ERR_NOMEM;
+    const int mode = op == 0 ? (mask ? poisson::OUT_ELIM : poisson::OUT_PLAIN)
+                             : (mask ? poisson::OUT_ZERO : poisson::OUT_PLAIN);
+    launch_op<T>(c, tab + op * poisson::TAB, x, mask, mode, y, nullptr);
+    FEM_CUDA(cudaGetLastError());
+    return FEM_OK;
+}
+
+template <typename T>
+int solve_t(fem_mesh_t m, double alpha, const uint8_t *mask, const T *b, T *u, double rtol, int maxit, int *iters,
+            double *rel_res, cudaStream_t s)
+{
+    Ctx c{m, m->n_nodes, s};
+    const T *tab = make_tables<T>(c, alpha);
+    if (!tab) return FEM_ERR_NOMEM;
+    return cg_solve<T>(c, tab, mask, b, u, rtol, maxit, iters, rel_res);
+}
+
+template <typename T>
+int gradient_t(fem_mesh_t m, double alpha, const uint8_t *mask, const T *theta, const int64_t *obs, const T *u_obs,
+               int64_t n_obs, double rtol, int maxit, T *u, T *lam, T *grad, double *J, int *iters, cudaStream_t s)
+{
+    Ctx c{m, m->n_nodes, s};
+    const int64_t N = c.N;
+    const T *tab = make_tables<T>(c, alpha);
+    T *rhs = (T *)m->ws.get(WS_PRHS, sizeof(T) * N);
+    if (!tab || !rhs) return FEM_ERR_NOMEM;
+    // forward: A u = M theta (free rows), u = 0 on masked nodes
+    launch_op<T>(c, tab + poisson::TAB, theta, mask, mask ? poisson::OUT_ZERO : poisson::OUT_PLAIN, rhs, nullptr);
+    FEM_CUDA(cudaMemsetAsync(u, 0, sizeof(T) * N, s));
+    int it_f = 0, it_a = 0;
+    int rc = cg_solve<T>(c, tab, mask, rhs, u, rtol, maxit, &it_f, nullptr);
+    if (rc != FEM_OK) return rc;
+    // objective and adjoint right-hand side 2 (u - u_obs) on the observed free nodes
+    double *small = (double *)m->ws.get(WS_PSMALL, sizeof(double) * 4);
+    if (!small) return FEM_ERR_NOMEM;
+    FEM_CUDA(cudaMemsetAsync(small, 0, sizeof(double) * 4, s));
+    FEM_CUDA(cudaMemsetAsync(rhs, 0, sizeof(T) * N, s));
+    if (n_obs > 0) {
+        k_pois_obs<T><<<grid_for(n_obs), PB, 0, s>>>(u, obs, u_obs, n_obs, mask, N, rhs, &small[1], (int *)&small[2]);
+        count_launch();
+    }
+    double hJ[2];
+    FEM_CUDA(cudaMemcpyAsync(hJ, &small[1], sizeof(hJ), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    int bad;
+    memcpy(&bad, &hJ[1], sizeof(int));
+    if (bad) return (set_error("fem_poisson_gradient: observation index outside [0, n_nodes)"), FEM_ERR_ARG);
+    // adjoint: A lambda = dJ/du (A symmetric), lambda = 0 on masked nodes
+    FEM_CUDA(cudaMemsetAsync(lam, 0, sizeof(T) * N, s));
+    rc = cg_solve<T>(c, tab, mask, rhs, lam, rtol, maxit, &it_a, nullptr);
+    if (rc != FEM_OK) return rc;
+    // dJ/dtheta = M^T lambda (M symmetric; lambda vanishes on masked nodes)
+    launch_op<T>(c, tab + poisson::TAB, lam, nullptr, poisson::OUT_PLAIN, grad, nullptr);
+    FEM_CUDA(cudaGetLastError());
+    FEM_CUDA(cudaStreamSynchronize(s));
+    if (J) *J = hJ[0];
+    if (iters) {
+        iters[0] = it_f;
+        iters[1] = it_a;
+    }
+    return FEM_OK;
+}
+
+}  // namespace
+
+}  // namespace femgb
+
+using namespace femgb;
+
+extern "C" int fem_poisson_apply(fem_mesh_t m, int precision, double alpha, int op, const uint8_t *mask,
+                                 const void *x, void *y, void *stream)
+{
+    if (int rc = check_mesh(m, "fem_poisson_apply")) return rc;
+    if (!x || !y || x == y) return (set_error("fem_poisson_apply: x, y must be distinct non-NULL arrays"), FEM_ERR_ARG);
+    if (op != FEM_POISSON_STIFFNESS && op != FEM_POISSON_MASS)
+        return (set_error("fem_poisson_apply: op must be FEM_POISSON_STIFFNESS or FEM_POISSON_MASS"), FEM_ERR_ARG);
+    if (!std::isfinite(alpha)) return (set_error("fem_poisson_apply: alpha must be finite"), FEM_ERR_ARG);
+    std::lock_guard<std::mutex> lk(m->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == FEM_FP64) return apply_t<double>(m, alpha, op, mask, (const double *)x, (double *)y, s);
+    if (precision == FEM_FP32) return apply_t<float>(m, alpha, op, mask, (const float *)x, (float *)y, s);
+    return (set_error("fem_poisson_apply: precision must be FEM_FP64 or FEM_FP32"), FEM_ERR_ARG);
+}
+
+extern "C" int fem_poisson_solve(fem_mesh_t m, int precision, double alpha, const uint8_t *mask, const void *b,
+                                 void *u, double rtol, int maxit, int *iters, double *rel_res, void *stream)
+{
+    if (int rc = check_mesh(m, "fem_poisson_solve")) return rc;
+    if (!b || !u) return (set_error("fem_poisson_solve: NULL argument"), FEM_ERR_ARG);
+    if (!(alpha > 0) || !(rtol > 0) || maxit < 0 || maxit > MAX_ITERS)
+        return (set_error("fem_poisson_solve: alpha > 0, rtol > 0 and 0 <= maxit <= 1e6 required"), FEM_ERR_ARG);
+    std::lock_guard<std::mutex> lk(m->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == FEM_FP64)
+        return solve_t<double>(m, alpha, mask, (const double *)b, (double *)u, rtol, maxit, iters, rel_res, s);
+    if (precision == FEM_FP32)
+        return solve_t<float>(m, alpha, mask, (const float *)b, (float *)u, rtol, maxit, iters, rel_res, s);
+    return (set_error("fem_poisson_solve: precision must be FEM_FP64 or FEM_FP32"), FEM_ERR_ARG);
+}
+
+extern "C" int fem_poisson_gradient(fem_mesh_t m, int precision, double alpha, const uint8_t *mask,
+                                    const void *theta, const int64_t *obs, const void *u_obs, int64_t n_obs,
+                                    double rtol, int maxit, void *u, void *lambda, void *grad, double *J, int *iters,
+                                    void *stream)
+{
+    if (int rc = check_mesh(m, "fem_poisson_gradient")) return rc;
+    if (!theta || !u || !lambda || !grad || n_obs < 0 || (n_obs > 0 && (!obs || !u_obs)))
+        return (set_error("fem_poisson_gradient: NULL argument or n_obs < 0"), FEM_ERR_ARG);
+    if (!(alpha > 0) || !(rtol > 0) || maxit < 0 || maxit > MAX_ITERS)
+        return (set_error("fem_poisson_gradient: alpha > 0, rtol > 0 and 0 <= maxit <= 1e6 required"), FEM_ERR_ARG);
+    std::lock_guard<std::mutex> lk(m->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == FEM_FP64)
+        return gradient_t<double>(m, alpha, mask, (const double *)theta, obs, (const double *)u_obs, n_obs, rtol,
+                                  maxit, (double *)u, (double *)lambda, (double *)grad, J, iters, s);
+    if (precision == FEM_FP32)
+        return gradient_t<float>(m, alpha, mask, (const float *)theta, obs, (const float *)u_obs, n_obs, rtol, maxit,
+                                 (float *)u, (float *)lambda, (float *)grad, J, iters, s);
+    return (set_error("fem_poisson_gradient: precision must be FEM_FP64 or FEM_FP32"), FEM_ERR_ARG);
+}

@@ -24,6 +24,7 @@ FEM_LINEAR, FEM_SIMP, FEM_NEOHOOKE = 0, 1, 2
 FEM_FP64, FEM_FP32, FEM_MIXED = 0, 1, 2
 FEM_MESH_CSR = 1
 FEM_MESH_DETERMINISTIC = 2
+FEM_POISSON_STIFFNESS, FEM_POISSON_MASS = 0, 1
 FACES = {"x0": 0, "x1": 1, "y0": 2, "y1": 3, "z0": 4, "z1": 5}
 
 
@@ -93,6 +94,10 @@ def lib():
     L.fem_vjp.argtypes = [P, MP, I, P, P, P, P, P, P]
     L.fem_assemble_csr.argtypes = [P, MP, I, P, P, P, P, P]
     L.fem_bicgstab_csr.argtypes = [P, I, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
+    L.fem_poisson_apply.argtypes = [P, I, D, I, P, P, P, P]
+    L.fem_poisson_solve.argtypes = [P, I, D, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
+    L.fem_poisson_gradient.argtypes = [P, I, D, P, P, P, P, I64, D, I, P, P, P, ctypes.POINTER(D),
+                                       ctypes.POINTER(I), P]
     L.fem_default_options.argtypes = [ctypes.POINTER(fem_options)]
     L.fem_default_options.restype = None
     L.fem_solve.argtypes = [P, MP, ctypes.POINTER(fem_bc), P, I, ctypes.POINTER(fem_options), P,
@@ -295,6 +300,54 @@ def fem_bicgstab_csr(m: Mesh, vals, b, x=None, rtol=1e-10, maxit=10000, stream=N
     if check:
         _check(rc, "fem_bicgstab_csr")
     return x, it.value, res.value
+
+
+def fem_poisson_apply(m: Mesh, x, alpha=1.0, op=FEM_POISSON_STIFFNESS, mask=None, y=None, stream=None):
+    """y = A x (stiffness, prescribed columns removed, y_c = x_c) or y = M x
+    (mass, y_c = 0) of the scalar Poisson problem; per-node arrays."""
+    dt = x.dtype
+    y = torch.empty_like(x) if y is None else y
+    _check(lib().fem_poisson_apply(m.handle, _prec(dt), ctypes.c_double(alpha), int(op),
+                                   _ptr(mask, torch.uint8, m.n_nodes, "mask"), _ptr(x, dt, m.n_nodes, "x"),
+                                   _ptr(y, dt, m.n_nodes, "y"), _stream(stream)), "fem_poisson_apply")
+    return y
+
+
+def fem_poisson_solve(m: Mesh, b, alpha=1.0, mask=None, u=None, rtol=1e-10, maxit=10000, stream=None,
+                      check=True):
+    """Jacobi-PCG for the eliminated Poisson stiffness: returns (u, iterations, ||r||/||b||)."""
+    dt = b.dtype
+    u = torch.zeros_like(b) if u is None else u
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    rc = lib().fem_poisson_solve(m.handle, _prec(dt), ctypes.c_double(alpha),
+                                 _ptr(mask, torch.uint8, m.n_nodes, "mask"), _ptr(b, dt, m.n_nodes, "b"),
+                                 _ptr(u, dt, m.n_nodes, "u"), ctypes.c_double(rtol), int(maxit), ctypes.byref(it),
+                                 ctypes.byref(res), _stream(stream))
+    if check:
+        _check(rc, "fem_poisson_solve")
+    return u, it.value, res.value
+
+
+def fem_poisson_gradient(m: Mesh, theta, obs, u_obs, alpha=1.0, mask=None, rtol=1e-10, maxit=10000,
+                         stream=None):
+    """Objective of the full-field inference problem and its adjoint
+    gradient: returns dict(J, grad, u, lam, iters)."""
+    dt = theta.dtype
+    u = torch.empty_like(theta)
+    lam = torch.empty_like(theta)
+    grad = torch.empty_like(theta)
+    J = ctypes.c_double(0.0)
+    its = (ctypes.c_int * 2)()
+    n_obs = obs.numel()
+    _check(lib().fem_poisson_gradient(m.handle, _prec(dt), ctypes.c_double(alpha),
+                                      _ptr(mask, torch.uint8, m.n_nodes, "mask"),
+                                      _ptr(theta, dt, m.n_nodes, "theta"), _ptr(obs, torch.int64, n_obs, "obs"),
+                                      _ptr(u_obs, dt, n_obs, "u_obs"), int(n_obs), ctypes.c_double(rtol),
+                                      int(maxit), _ptr(u, dt, m.n_nodes, "u"), _ptr(lam, dt, m.n_nodes, "lam"),
+                                      _ptr(grad, dt, m.n_nodes, "grad"), ctypes.byref(J), its,
+                                      _stream(stream)), "fem_poisson_gradient")
+    return {"J": J.value, "grad": grad, "u": u, "lam": lam, "iters": (its[0], its[1])}
 
 
 def _bc(m: Mesh, mask, u_bar=None, f_ext=None) -> fem_bc:

@@ -43,6 +43,12 @@ def test_host_only_calls():
     assert "NULL" in L.fem_last_error().decode() or "out" in L.fem_last_error().decode()
     mat = fem.material(7, 1.0, 0.3)
     assert L.fem_residual(None, ctypes.byref(mat), 0, None, None, None, None, None, None) == fem.FEM_ERR_ARG
+    # the scalar Poisson entry points validate on the host too
+    assert L.fem_poisson_apply(None, 0, 1.0, 0, None, None, None, None) == fem.FEM_ERR_ARG
+    assert L.fem_poisson_solve(None, 0, 1.0, None, None, None, 1e-8, 10, None, None, None) == fem.FEM_ERR_ARG
+    assert L.fem_poisson_gradient(None, 0, 1.0, None, None, None, None, 0, 1e-8, 10, None, None, None, None,
+                                  None, None) == fem.FEM_ERR_ARG
+    assert "NULL mesh" in L.fem_last_error().decode()
 
 
 def test_binding_struct_layouts_match_the_header(tmp_path):
