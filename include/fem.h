@@ -208,6 +208,50 @@ int fem_poisson_gradient(fem_mesh_t m, int precision, double alpha, const uint8_
                          double rtol, int maxit, void *u, void *lambda, void *grad, double *J,
                          int *iters, void *stream);
 
+/* ------------------------------------------------ perfect J2 plasticity -- */
+/* Small-strain perfect J2 plasticity (Sec. 2.3, Eqs. (14)-(15)): the stress
+ * of load step k is the radial return of the elastic trial stress
+ * sigma^{k-1} + lam tr(d eps) I + 2 mu d eps, d eps = sym(grad u^k) - eps^{k-1},
+ * onto the von Mises surface of radius sigma_y.  Lame parameters from
+ * (E, nu) as for FEM_LINEAR.  FP64 only.  DOF layout and mask as above
+ * (mask[d] != 0: u_d prescribed; rows and columns eliminated).
+ * History: double hist[12 * 8 * n_cells], structure of arrays
+ * hist[(comp * 8 + q) * n_cells + e]: comp 0..5 the total strain eps, 6..11
+ * the stress sigma, each as (xx, yy, zz, yz, xz, xy) tensor components;
+ * q = gx + 2 gy + 4 gz the Gauss point at reference coordinates
+ * (2 g - 1)/sqrt(3).  All zeros is the virgin state. */
+typedef struct {
+    double E, nu, sigma_y;
+} fem_j2_material;
+
+/* r = sum_e int sigma^k(grad u) : grad phi, r_c = 0 on masked DOFs (mask may
+ * be NULL); hist_new (may be NULL): the returned (eps^k, sigma^k) of every
+ * Gauss point at u; *n_yield (host, may be NULL; synchronises): Gauss points
+ * whose trial state yields.  u, r: [D]. */
+int fem_j2_residual(fem_mesh_t m, const fem_j2_material *mat, const uint8_t *mask, const double *u,
+                    const double *hist, double *r, double *hist_new, int64_t *n_yield, void *stream);
+
+/* y = K(u) x with K the consistent tangent of the return map (its
+ * derivative in eps^k: the elastic law where the trial state does not yield;
+ * K tr(d eps) I + (sigma_y/q)(2 mu dev d eps - 3 mu s (s : d eps)/q^2) where it
+ * does, s the trial deviator, q = sqrt(3/2 s:s)); masked columns removed and
+ * y_c = x_c.  x, y: [D], distinct. */
+int fem_j2_tangent_apply(fem_mesh_t m, const fem_j2_material *mat, const uint8_t *mask, const double *u,
+                         const double *hist, const double *x, double *y, void *stream);
+
+/* One load step: u_c = u_bar_c on masked DOFs, then Newton on the free DOFs
+ * with Jacobi-PCG on the consistent tangent (tolerance cg_rtol, at most
+ * cg_maxit <= 1e6 iterations per Newton step) until ||r|| <= newton_rtol *
+ * max(||r|| of the first iteration, E h^2 1e-12), h the smallest cell edge;
+ * the free DOFs of u start from their values on entry.  On success hist
+ * becomes (eps^k, sigma^k) at the converged u.  newton_iters, cg_iters,
+ * n_yield (host, may be NULL): Newton iterations, total CG iterations,
+ * yielding Gauss points.  FEM_ERR_NOT_CONVERGED after newton_maxit (hist
+ * unchanged).  Synchronises the stream. */
+int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, const uint8_t *mask, const double *u_bar, double *u,
+                double *hist, double newton_rtol, int newton_maxit, double cg_rtol, int cg_maxit,
+                int *newton_iters, int *cg_iters, int64_t *n_yield, void *stream);
+
 /* ---------------------------------------------------------------- solvers -- */
 typedef struct {
     int precision;       /* FEM_MIXED (default) or FEM_FP64 */

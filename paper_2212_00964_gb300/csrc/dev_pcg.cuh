@@ -1,0 +1,167 @@
+// dev_pcg.cuh -- Jacobi-preconditioned CG with its scalars on the device,
+// for the operators of the scalar Poisson path and of J2 plasticity (both
+// symmetric positive (semi-)definite after the elimination of prescribed
+// values).
+//
+// Iteration k reads rz_k = (r_k, z_k) and pq_k = (p_k, A p_k) from
+// sc[3k + 0] and sc[3k + 1] and writes rz_{k+1}, rr_{k+1} = (r_{k+1}, r_{k+1})
+// to sc[3(k+1) + 0] and sc[3(k+1) + 2]; the operator adds pq_k itself.  No
+// launch waits for the host; the host reads the scalars once every
+// DPCG_CHECK iterations to test ||r|| <= rtol ||b||, non-finite values and
+// p^T A p <= 0 (breakdown), so up to DPCG_CHECK - 1 extra iterations run
+// after convergence.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "fem_internal.cuh"
+
+namespace femgb {
+namespace dpcg {
+
+constexpr int NT = 256;
+constexpr int CHECK = 8;
+
+inline int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + NT - 1) / NT, 152 * 8)); }
+
+// r = b - q (q = A u), z = D r, p = z; sc0[0] += (r, z), sc0[2] += (r, r), *bb += (b, b)
+template <typename T>
+__global__ void __launch_bounds__(NT) k_init(const T *__restrict__ b, const T *__restrict__ q,
+                                            const T *__restrict__ dinv, T *__restrict__ r, T *__restrict__ z,
+                                            T *__restrict__ p, int64_t N, double *sc0, double *bb)
+{
+    __shared__ double sh[NT / 32];
+    double rz = 0, rr = 0, b2 = 0;
+    for (int64_t n = blockIdx.x * (int64_t)NT + threadIdx.x; n < N; n += (int64_t)gridDim.x * NT) {
+        const T rn = b[n] - q[n];
+        const T zn = dinv[n] * rn;
+        r[n] = rn;
+        z[n] = zn;
+        p[n] = zn;
+        rz += (double)rn * (double)zn;
+        rr += (double)rn * (double)rn;
+        b2 += (double)b[n] * (double)b[n];
+    }
+    rz = block_sum<double, NT>(rz, sh);
+    if (threadIdx.x == 0) atomicAdd(&sc0[0], rz);
+    rr = block_sum<double, NT>(rr, sh);
+    if (threadIdx.x == 0) atomicAdd(&sc0[2], rr);
+    b2 = block_sum<double, NT>(b2, sh);
+    if (threadIdx.x == 0) atomicAdd(bb, b2);
+}
+
+// alpha_k = rz_k / pq_k (0 when pq_k <= 0: the host reports the breakdown);
+// u += alpha p, r -= alpha q, z = D r; sck1[0] += (r, z), sck1[2] += (r, r).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_update(T *__restrict__ u, T *__restrict__ r, T *__restrict__ z,
+                                              const T *__restrict__ p, const T *__restrict__ q,
+                                              const T *__restrict__ dinv, int64_t N, const double *sck, double *sck1)
+{
+    __shared__ double sh[NT / 32];
+    const double pq = sck[1];
+    const T alpha = pq > 0.0 ? (T)(sck[0] / pq) : (T)0;
+    double rz = 0, rr = 0;
+    for (int64_t n = blockIdx.x * (int64_t)NT + threadIdx.x; n < N; n += (int64_t)gridDim.x * NT) {
+        u[n] += alpha * p[n];
+        const T rn = r[n] - alpha * q[n];
+        const T zn = dinv[n] * rn;
+        r[n] = rn;
+        z[n] = zn;
+        rz += (double)rn * (double)zn;
+        rr += (double)rn * (double)rn;
+    }
+    rz = block_sum<double, NT>(rz, sh);
+    if (threadIdx.x == 0) atomicAdd(&sck1[0], rz);
+    rr = block_sum<double, NT>(rr, sh);
+    if (threadIdx.x == 0) atomicAdd(&sck1[2], rr);
+}
+
+// beta = rz_{k+1} / rz_k; p = z + beta p
+template <typename T>
+__global__ void __launch_bounds__(NT) k_dir(T *__restrict__ p, const T *__restrict__ z, int64_t N, const double *sck,
+                                           const double *sck1)
+{
+    const double rz = sck[0];
+    const T beta = rz > 0.0 ? (T)(sck1[0] / rz) : (T)0;
+    for (int64_t n = blockIdx.x * (int64_t)NT + threadIdx.x; n < N; n += (int64_t)gridDim.x * NT)
+        p[n] = z[n] + beta * p[n];
+}
+
+template <typename T>
+struct Buffers {
+    T *r, *z, *p, *q;
+    double *sc;     // 3 * (maxit + 2) doubles
+    double *small;  // 1 double
+};
+
+inline size_t scalar_count(int maxit) { return 3 * ((size_t)maxit + 2); }
+
+// Solve A u = b; u holds the start value.  apply(x, y, dot) must launch
+// y = A x on the stream and, when dot is not null, add (x, A x) to *dot.
+template <typename T, typename Apply>
+int solve(cudaStream_t s, int64_t N, Apply apply, const T *dinv, const T *b, T *u, const Buffers<T> &w, double rtol,
+          int maxit, int *iters, double *rel_res, const char *who)
+{
+    const int g = grid_for(N);
+    FEM_CUDA(cudaMemsetAsync(w.sc, 0, sizeof(double) * scalar_count(maxit), s));
+    FEM_CUDA(cudaMemsetAsync(w.small, 0, sizeof(double), s));
+    if (int rc = apply(u, w.q, nullptr)) return rc;
+    k_init<T><<<g, NT, 0, s>>>(b, w.q, dinv, w.r, w.z, w.p, N, w.sc, w.small);
+    count_launch();
+    FEM_CUDA(cudaGetLastError());
+    double h0[3], bb;
+    FEM_CUDA(cudaMemcpyAsync(h0, w.sc, sizeof(h0), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaMemcpyAsync(&bb, w.small, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    const double bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
+    double rr = h0[2];
+    if (!std::isfinite(rr) || !std::isfinite(h0[0]))
+        return (set_error(std::string(who) + ": non-finite residual"), FEM_ERR_NONFINITE);
+    int k = 0;
+    int rc = std::sqrt(rr) <= rtol * bn ? FEM_OK : FEM_ERR_NOT_CONVERGED;
+    std::vector<double> hs;
+    while (rc == FEM_ERR_NOT_CONVERGED && k < maxit) {
+        const int k0 = k;
+        const int k1 = std::min(maxit, k + CHECK);
+        for (; k < k1; ++k) {
+            double *sck = w.sc + 3 * (size_t)k, *sck1 = w.sc + 3 * ((size_t)k + 1);
+            if (int e = apply(w.p, w.q, &sck[1])) return e;
+            k_update<T><<<g, NT, 0, s>>>(u, w.r, w.z, w.p, w.q, dinv, N, sck, sck1);
+            k_dir<T><<<g, NT, 0, s>>>(w.p, w.z, N, sck, sck1);
+            count_launch(2);
+        }
+        FEM_CUDA(cudaGetLastError());
+        hs.resize(3 * (size_t)(k - k0 + 1));
+        FEM_CUDA(cudaMemcpyAsync(hs.data(), w.sc + 3 * (size_t)k0, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost,
+                                 s));
+        FEM_CUDA(cudaStreamSynchronize(s));
+        for (int j = 0; j < k - k0; ++j) {
+            const double rz = hs[3 * j], pq = hs[3 * j + 1], rr1 = hs[3 * (j + 1) + 2];
+            if (!std::isfinite(rz) || !std::isfinite(pq) || !std::isfinite(rr1)) {
+                set_error(std::string(who) + ": non-finite CG scalar");
+                rc = FEM_ERR_NONFINITE;
+                break;
+            }
+            if (pq <= 0.0 && rz > 0.0) {
+                set_error(std::string(who) + ": p^T A p <= 0 (operator not positive definite)");
+                rc = FEM_ERR_BREAKDOWN;
+                break;
+            }
+            rr = rr1;
+            if (std::sqrt(rr) <= rtol * bn) {
+                rc = FEM_OK;
+                rr = hs[3 * (size_t)(k - k0) + 2];  // the batch's later iterations ran as well
+                break;
+            }
+        }
+    }
+    if (iters) *iters = k;
+    if (rel_res) *rel_res = std::sqrt(rr) / bn;
+    if (rc == FEM_ERR_NOT_CONVERGED) set_error(std::string(who) + ": CG iteration limit reached");
+    return rc;
+}
+
+}  // namespace dpcg
+}  // namespace femgb

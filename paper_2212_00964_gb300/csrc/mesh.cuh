@@ -9,11 +9,11 @@ namespace femgb {
 
 // Named device buffers that grow on demand and are never shrunk.
 // Slots 0..31 belong to the solvers, WS_BICG0.. to the assembled-matrix
-// solver, 48..63 to the scalar Poisson path.
+// solver, 48..63 to the scalar Poisson path, 64..79 to J2 plasticity.
 enum { WS_BICG0 = 32 };
 
 struct Workspace {
-    enum { N_SLOTS = 64 };
+    enum { N_SLOTS = 80 };
     void *ptr[N_SLOTS] = {};
     size_t cap[N_SLOTS] = {};
 

@@ -8,16 +8,15 @@
 // offsets, per operator) are built by one thread on the device and staged
 // in shared memory by every block of the operator kernel.
 //
-// CG keeps its scalars on the device: iteration k reads rz_k = (r_k, z_k)
-// and pq_k = (p_k, A p_k) from an array indexed by k, so no launch waits on
-// the host; the host reads the residual norms once every CG_CHECK
-// iterations.
+// CG (dev_pcg.cuh) keeps its scalars on the device: no launch waits on the
+// host, which reads the residual norms once every 8 iterations.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
 
+#include "dev_pcg.cuh"
 #include "mesh.cuh"
 #include "poisson_core.cuh"
 
@@ -25,8 +24,7 @@ namespace femgb {
 
 namespace {
 
-constexpr int PB = 256;        // threads per block
-constexpr int CG_CHECK = 8;    // iterations between host checks
+constexpr int PB = 256;  // threads per block
 constexpr int MAX_ITERS = 1000000;
 
 // workspace slots of this path
@@ -77,70 +75,6 @@ __global__ void k_pois_dinv(const T *__restrict__ tab, const uint8_t *__restrict
         const double d = poisson::diag_row<T>(tab, mask, n, nx, ny, nz);
         dinv[n] = d != 0.0 ? (T)(1.0 / d) : (T)0;
     }
-}
-
-// r = b - q (q = A u), z = D r, p = z; sc0[0] += (r, z), sc0[2] += (r, r), *bb += (b, b)
-template <typename T>
-__global__ void __launch_bounds__(PB) k_pois_cg_init(const T *__restrict__ b, const T *__restrict__ q,
-                                                    const T *__restrict__ dinv, T *__restrict__ r, T *__restrict__ z,
-                                                    T *__restrict__ p, int64_t N, double *sc0, double *bb)
-{
-    __shared__ double sh[PB / 32];
-    double rz = 0, rr = 0, b2 = 0;
-    for (int64_t n = blockIdx.x * (int64_t)PB + threadIdx.x; n < N; n += (int64_t)gridDim.x * PB) {
-        const T rn = b[n] - q[n];
-        const T zn = dinv[n] * rn;
-        r[n] = rn;
-        z[n] = zn;
-        p[n] = zn;
-        rz += (double)rn * (double)zn;
-        rr += (double)rn * (double)rn;
-        b2 += (double)b[n] * (double)b[n];
-    }
-    rz = block_sum<double, PB>(rz, sh);
-    if (threadIdx.x == 0) atomicAdd(&sc0[0], rz);
-    rr = block_sum<double, PB>(rr, sh);
-    if (threadIdx.x == 0) atomicAdd(&sc0[2], rr);
-    b2 = block_sum<double, PB>(b2, sh);
-    if (threadIdx.x == 0) atomicAdd(bb, b2);
-}
-
-// alpha_k = rz_k / pq_k (0 when pq_k <= 0: the host reports the breakdown);
-// u += alpha p, r -= alpha q, z = D r; sck1[0] += (r, z), sck1[2] += (r, r).
-template <typename T>
-__global__ void __launch_bounds__(PB) k_pois_cg_update(T *__restrict__ u, T *__restrict__ r, T *__restrict__ z,
-                                                      const T *__restrict__ p, const T *__restrict__ q,
-                                                      const T *__restrict__ dinv, int64_t N, const double *sck,
-                                                      double *sck1)
-{
-    __shared__ double sh[PB / 32];
-    const double pq = sck[1];
-    const T alpha = pq > 0.0 ? (T)(sck[0] / pq) : (T)0;
-    double rz = 0, rr = 0;
-    for (int64_t n = blockIdx.x * (int64_t)PB + threadIdx.x; n < N; n += (int64_t)gridDim.x * PB) {
-        u[n] += alpha * p[n];
-        const T rn = r[n] - alpha * q[n];
-        const T zn = dinv[n] * rn;
-        r[n] = rn;
-        z[n] = zn;
-        rz += (double)rn * (double)zn;
-        rr += (double)rn * (double)rn;
-    }
-    rz = block_sum<double, PB>(rz, sh);
-    if (threadIdx.x == 0) atomicAdd(&sck1[0], rz);
-    rr = block_sum<double, PB>(rr, sh);
-    if (threadIdx.x == 0) atomicAdd(&sck1[2], rr);
-}
-
-// beta = rz_{k+1} / rz_k; p = z + beta p
-template <typename T>
-__global__ void k_pois_cg_dir(T *__restrict__ p, const T *__restrict__ z, int64_t N, const double *sck,
-                              const double *sck1)
-{
-    const double rz = sck[0];
-    const T beta = rz > 0.0 ? (T)(sck1[0] / rz) : (T)0;
-    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
-        p[n] = z[n] + beta * p[n];
 }
 
 // Objective of Eq. (26) and the adjoint right-hand side:
@@ -198,72 +132,22 @@ int cg_solve(const Ctx &c, const T *tabA, const uint8_t *mask, const T *b, T *u,
              double *rel_res)
 {
     const int64_t N = c.N;
-    T *r = (T *)c.m->ws.get(WS_PR, sizeof(T) * N);
-    T *z = (T *)c.m->ws.get(WS_PZ, sizeof(T) * N);
-    T *p = (T *)c.m->ws.get(WS_PP, sizeof(T) * N);
-    T *q = (T *)c.m->ws.get(WS_PQ, sizeof(T) * N);
+    dpcg::Buffers<T> w;
+    w.r = (T *)c.m->ws.get(WS_PR, sizeof(T) * N);
+    w.z = (T *)c.m->ws.get(WS_PZ, sizeof(T) * N);
+    w.p = (T *)c.m->ws.get(WS_PP, sizeof(T) * N);
+    w.q = (T *)c.m->ws.get(WS_PQ, sizeof(T) * N);
+    w.sc = (double *)c.m->ws.get(WS_PSC, sizeof(double) * dpcg::scalar_count(maxit));
+    w.small = (double *)c.m->ws.get(WS_PSMALL, sizeof(double) * 4);
     T *dinv = (T *)c.m->ws.get(WS_PDINV, sizeof(T) * N);
-    double *sc = (double *)c.m->ws.get(WS_PSC, sizeof(double) * 3 * ((size_t)maxit + 2));
-    double *small = (double *)c.m->ws.get(WS_PSMALL, sizeof(double) * 4);
-    if (!r || !z || !p || !q || !dinv || !sc || !small) return FEM_ERR_NOMEM;
-    const int g = grid_for(N);
-    FEM_CUDA(cudaMemsetAsync(sc, 0, sizeof(double) * 3 * ((size_t)maxit + 2), c.s));
-    FEM_CUDA(cudaMemsetAsync(small, 0, sizeof(double) * 4, c.s));
-    k_pois_dinv<T><<<g, PB, 0, c.s>>>(tabA, mask, dinv, c.m->nx, c.m->ny, c.m->nz, N);
+    if (!w.r || !w.z || !w.p || !w.q || !w.sc || !w.small || !dinv) return FEM_ERR_NOMEM;
+    k_pois_dinv<T><<<grid_for(N), PB, 0, c.s>>>(tabA, mask, dinv, c.m->nx, c.m->ny, c.m->nz, N);
     count_launch();
-    launch_op<T>(c, tabA, u, mask, poisson::OUT_ELIM, q, nullptr);
-    k_pois_cg_init<T><<<g, PB, 0, c.s>>>(b, q, dinv, r, z, p, N, sc, &small[0]);
-    count_launch();
-    FEM_CUDA(cudaGetLastError());
-    double h0[3], bb;
-    FEM_CUDA(cudaMemcpyAsync(h0, sc, sizeof(h0), cudaMemcpyDeviceToHost, c.s));
-    FEM_CUDA(cudaMemcpyAsync(&bb, &small[0], sizeof(double), cudaMemcpyDeviceToHost, c.s));
-    FEM_CUDA(cudaStreamSynchronize(c.s));
-    const double bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
-    double rr = h0[2];
-    if (!std::isfinite(rr) || !std::isfinite(h0[0])) return (set_error("poisson CG: non-finite residual"), FEM_ERR_NONFINITE);
-    int k = 0;
-    int rc = std::sqrt(rr) <= rtol * bn ? FEM_OK : FEM_ERR_NOT_CONVERGED;
-    std::vector<double> hs;
-    while (rc == FEM_ERR_NOT_CONVERGED && k < maxit) {
-        const int k0 = k;
-        const int k1 = std::min(maxit, k + CG_CHECK);
-        for (; k < k1; ++k) {
-            double *sck = sc + 3 * (size_t)k, *sck1 = sc + 3 * ((size_t)k + 1);
-            launch_op<T>(c, tabA, p, mask, poisson::OUT_ELIM, q, &sck[1]);
-            k_pois_cg_update<T><<<g, PB, 0, c.s>>>(u, r, z, p, q, dinv, N, sck, sck1);
-            k_pois_cg_dir<T><<<g, PB, 0, c.s>>>(p, z, N, sck, sck1);
-            count_launch(2);
-        }
-        FEM_CUDA(cudaGetLastError());
-        hs.resize(3 * (size_t)(k - k0 + 1));
-        FEM_CUDA(cudaMemcpyAsync(hs.data(), sc + 3 * (size_t)k0, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, c.s));
-        FEM_CUDA(cudaStreamSynchronize(c.s));
-        for (int j = 0; j < k - k0; ++j) {
-            const double rz = hs[3 * j], pq = hs[3 * j + 1], rr1 = hs[3 * (j + 1) + 2];
-            if (!std::isfinite(rz) || !std::isfinite(pq) || !std::isfinite(rr1)) {
-                set_error("poisson CG: non-finite scalar");
-                rc = FEM_ERR_NONFINITE;
-                break;
-            }
-            if (pq <= 0.0 && rz > 0.0) {
-                set_error("poisson CG: p^T A p <= 0 (operator not positive definite)");
-                rc = FEM_ERR_BREAKDOWN;
-                break;
-            }
-            rr = rr1;
-            if (std::sqrt(rr) <= rtol * bn) {
-                rc = FEM_OK;
-                // the later iterations of this batch ran as well; report the final residual
-                rr = hs[3 * (size_t)(k - k0) + 2];
-                break;
-            }
-        }
-    }
-    if (iters) *iters = k;
-    if (rel_res) *rel_res = std::sqrt(rr) / bn;
-    if (rc == FEM_ERR_NOT_CONVERGED) set_error("poisson CG: iteration limit reached");
-    return rc;
+    auto apply = [&](const T *x, T *y, double *dot) -> int {
+        launch_op<T>(c, tabA, x, mask, poisson::OUT_ELIM, y, dot);
+        return FEM_OK;
+    };
+    return dpcg::solve<T>(c.s, N, apply, dinv, b, u, w, rtol, maxit, iters, rel_res, "poisson CG");
 }
 
 int check_mesh(fem_mesh_t m, const char *what)

@@ -39,6 +39,10 @@ class fem_material(ctypes.Structure):
                 ("simp_p", ctypes.c_double), ("simp_emin", ctypes.c_double)]
 
 
+class fem_j2_material(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("sigma_y", ctypes.c_double)]
+
+
 class fem_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("newton_rtol", ctypes.c_double),
                 ("newton_atol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
@@ -94,6 +98,11 @@ def lib():
     L.fem_vjp.argtypes = [P, MP, I, P, P, P, P, P, P]
     L.fem_assemble_csr.argtypes = [P, MP, I, P, P, P, P, P]
     L.fem_bicgstab_csr.argtypes = [P, I, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
+    JP = ctypes.POINTER(fem_j2_material)
+    L.fem_j2_residual.argtypes = [P, JP, P, P, P, P, P, ctypes.POINTER(I64), P]
+    L.fem_j2_tangent_apply.argtypes = [P, JP, P, P, P, P, P, P]
+    L.fem_j2_step.argtypes = [P, JP, P, P, P, P, D, I, D, I, ctypes.POINTER(I), ctypes.POINTER(I),
+                              ctypes.POINTER(I64), P]
     L.fem_poisson_apply.argtypes = [P, I, D, I, P, P, P, P]
     L.fem_poisson_solve.argtypes = [P, I, D, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     L.fem_poisson_gradient.argtypes = [P, I, D, P, P, P, P, I64, D, I, P, P, P, ctypes.POINTER(D),
@@ -348,6 +357,52 @@ def fem_poisson_gradient(m: Mesh, theta, obs, u_obs, alpha=1.0, mask=None, rtol=
                                       _ptr(grad, dt, m.n_nodes, "grad"), ctypes.byref(J), its,
                                       _stream(stream)), "fem_poisson_gradient")
     return {"J": J.value, "grad": grad, "u": u, "lam": lam, "iters": (its[0], its[1])}
+
+
+def j2_material(E, nu, sigma_y) -> fem_j2_material:
+    return fem_j2_material(float(E), float(nu), float(sigma_y))
+
+
+def j2_history(m: Mesh):
+    """Virgin Gauss-point history (float64 [12 * 8 * n_cells], all zeros)."""
+    return torch.zeros(12 * 8 * m.n_cells, dtype=torch.float64, device="cuda")
+
+
+def fem_j2_residual(m: Mesh, mat: fem_j2_material, u, hist, mask=None, r=None, hist_new=None, stream=None):
+    """(r, n_yield) of perfect J2 plasticity; hist_new (if given) receives
+    the returned states."""
+    H = 12 * 8 * m.n_cells
+    r = torch.empty_like(u) if r is None else r
+    ny = ctypes.c_int64(0)
+    _check(lib().fem_j2_residual(m.handle, ctypes.byref(mat), _ptr(mask, torch.uint8, m.n_dofs, "mask"),
+                                 _ptr(u, torch.float64, m.n_dofs, "u"), _ptr(hist, torch.float64, H, "hist"),
+                                 _ptr(r, torch.float64, m.n_dofs, "r"),
+                                 _ptr(hist_new, torch.float64, H, "hist_new"), ctypes.byref(ny), _stream(stream)),
+           "fem_j2_residual")
+    return r, ny.value
+
+
+def fem_j2_tangent_apply(m: Mesh, mat: fem_j2_material, u, hist, x, mask=None, y=None, stream=None):
+    H = 12 * 8 * m.n_cells
+    y = torch.empty_like(x) if y is None else y
+    _check(lib().fem_j2_tangent_apply(m.handle, ctypes.byref(mat), _ptr(mask, torch.uint8, m.n_dofs, "mask"),
+                                      _ptr(u, torch.float64, m.n_dofs, "u"), _ptr(hist, torch.float64, H, "hist"),
+                                      _ptr(x, torch.float64, m.n_dofs, "x"), _ptr(y, torch.float64, m.n_dofs, "y"),
+                                      _stream(stream)), "fem_j2_tangent_apply")
+    return y
+
+
+def fem_j2_step(m: Mesh, mat: fem_j2_material, mask, u_bar, u, hist, newton_rtol=1e-10, newton_maxit=30,
+                cg_rtol=1e-10, cg_maxit=20000, stream=None):
+    """One load step in place (u, hist); returns dict(newton_iters, cg_iters, n_yield)."""
+    H = 12 * 8 * m.n_cells
+    ni, ci, ny = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int64(0)
+    _check(lib().fem_j2_step(m.handle, ctypes.byref(mat), _ptr(mask, torch.uint8, m.n_dofs, "mask"),
+                             _ptr(u_bar, torch.float64, m.n_dofs, "u_bar"), _ptr(u, torch.float64, m.n_dofs, "u"),
+                             _ptr(hist, torch.float64, H, "hist"), ctypes.c_double(newton_rtol), int(newton_maxit),
+                             ctypes.c_double(cg_rtol), int(cg_maxit), ctypes.byref(ni), ctypes.byref(ci),
+                             ctypes.byref(ny), _stream(stream)), "fem_j2_step")
+    return {"newton_iters": ni.value, "cg_iters": ci.value, "n_yield": ny.value}
 
 
 def _bc(m: Mesh, mask, u_bar=None, f_ext=None) -> fem_bc:

@@ -49,6 +49,10 @@ def test_host_only_calls():
     assert L.fem_poisson_gradient(None, 0, 1.0, None, None, None, None, 0, 1e-8, 10, None, None, None, None,
                                   None, None) == fem.FEM_ERR_ARG
     assert "NULL mesh" in L.fem_last_error().decode()
+    jm = fem.j2_material(70e3, 0.3, 250.0)
+    assert L.fem_j2_residual(None, ctypes.byref(jm), None, None, None, None, None, None, None) == fem.FEM_ERR_ARG
+    assert L.fem_j2_step(None, ctypes.byref(jm), None, None, None, None, 1e-10, 10, 1e-10, 10, None, None, None,
+                         None) == fem.FEM_ERR_ARG
 
 
 def test_binding_struct_layouts_match_the_header(tmp_path):
@@ -61,7 +65,7 @@ def test_binding_struct_layouts_match_the_header(tmp_path):
     if cc is None:
         import pytest
         pytest.skip("no C compiler")
-    structs = [fem.fem_material, fem.fem_options, fem.fem_stats, fem.fem_bc, fem.fem_instance]
+    structs = [fem.fem_material, fem.fem_options, fem.fem_stats, fem.fem_bc, fem.fem_instance, fem.fem_j2_material]
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "fem.h"', "int main(void) {"]
     for S in structs:
         n = S.__name__
