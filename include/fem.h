@@ -252,6 +252,33 @@ int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, const uint8_t *mask, c
                 double *hist, double newton_rtol, int newton_maxit, double cg_rtol, int cg_maxit,
                 int *newton_iters, int *cg_iters, int64_t *n_yield, void *stream);
 
+/* ------------------------------------------------ topology optimisation -- */
+/* The data-parallel steps of the compliance-minimisation loop (Sec. 3.2)
+ * besides the SIMP solve (fem_solve) and the compliance gradient
+ * (fem_adjoint with dJ/du = f).  Per-cell arrays [n_cells] of double. */
+
+/* Sensitivity filter: g_filtered_e = sum_f w_ef g_f / sum_f w_ef with the
+ * cone kernel w_ef = max(0, rmin - |c_e - c_f|) between cell centres,
+ * measured in cells (0 < rmin <= 64; rmin <= 1 is the identity). */
+int fem_density_filter(fem_mesh_t m, double rmin, const double *g, double *g_filtered, void *stream);
+
+/* One step of the method of moving asymptotes (Svanberg 1987) for
+ * min f0(x) s.t. f1(x) <= 0, x_min <= x <= x_max, over the n_cells
+ * variables x: df0, df1 the gradients at x, f1 the constraint value (host).
+ * Asymptotes start at 0.5 (x_max - x_min) from x for iter 0 and 1 and are
+ * then shrunk (0.7) or widened (1.2) per variable as its last two moves
+ * changed sign or not; move limits at 9/10 of the way to them; the convex
+ * subproblem is solved through its one-dimensional dual by bisection.
+ * State owned by the caller, [n_cells] each: x1, x2 (previous iterates;
+ * on return x2 <- x1, x1 <- x), low, upp (asymptotes, read when iter >= 2,
+ * written always).  iter: steps taken before this one.  y: the new x (must
+ * not alias x).  *lam_out (host, may be NULL): the multiplier.
+ * FEM_ERR_NOT_CONVERGED if no multiplier below 1e300 makes the subproblem
+ * feasible.  Synchronises the stream once per dual evaluation. */
+int fem_mma_step(fem_mesh_t m, const double *x, double f1, const double *df0, const double *df1, double x_min,
+                 double x_max, int iter, double *x1, double *x2, double *low, double *upp, double *y,
+                 double *lam_out, void *stream);
+
 /* ---------------------------------------------------------------- solvers -- */
 typedef struct {
     int precision;       /* FEM_MIXED (default) or FEM_FP64 */

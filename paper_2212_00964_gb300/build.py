@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 SO = os.path.join(OUT_DIR, "libfemgb.so")
 SOURCES = ["api.cu", "mesh.cu", "cell_ops.cu", "cg_fused.cu", "solver.cu", "solve_static.cu", "bicgstab.cu",
-           "poisson.cu", "plasticity.cu"]
+           "poisson.cu", "plasticity.cu", "topopt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,134 @@
+// topopt_core.cuh -- per-cell arithmetic of the topology-optimisation loop
+// (Sec. 3.2) as host/device functions: the sensitivity filter and the
+// element-wise part of one step of the method of moving asymptotes
+// (Svanberg 1987).  The kernels call them per cell; a host build checks
+// them against the oracle on the CPU.
+//
+// Filter: g~_e = sum_f w_ef g_f / sum_f w_ef with the cone kernel
+// w_ef = max(0, r_min - |c_e - c_f|) between cell centres (cell units).
+// MMA, one inequality constraint f1 <= 0, per variable j:
+//   asymptotes  iterations 0, 1: L = x - s0 (x_max - x_min), U = x + s0 (...);
+//               later: the distances x1 - L and U - x1 are scaled by s_dec
+//               (0.7) where (x - x1)(x1 - x2) < 0, s_inc (1.2) where > 0;
+//   move limits alpha = max(x_min, 0.9 L + 0.1 x), beta = min(x_max, 0.9 U + 0.1 x);
+//   p_i = (U - x)^2 max(df_i, 0), q_i = (x - L)^2 max(-df_i, 0)  (i = 0, 1);
+//   for a multiplier lam: y = (sqrt(P) L + sqrt(Q) U) / (sqrt(P) + sqrt(Q)),
+//   P = p_0 + lam p_1, Q = q_0 + lam q_1, clipped to [alpha, beta] (y = x
+//   when P = Q = 0); the constraint model is r_1 + sum_j p_1/(U - y) + q_1/(y - L).
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define TO_HD __host__ __device__ __forceinline__
+#else
+#define TO_HD inline
+#endif
+
+namespace femgb {
+namespace topopt {
+
+TO_HD double filter_cell(const double *g, int64_t e, int nx, int ny, int nz, double rmin)
+{
+    const int64_t nxy = (int64_t)nx * ny;
+    const int k = (int)(e / nxy);
+    const int64_t rem = e - (int64_t)k * nxy;
+    const int j = (int)(rem / nx);
+    const int i = (int)(rem - (int64_t)j * nx);
+    const int R = (int)ceil(rmin) - 1;
+    double num = 0.0, den = 0.0;
+    for (int kk = (k - R > 0 ? k - R : 0); kk <= (k + R < nz - 1 ? k + R : nz - 1); ++kk)
+        for (int jj = (j - R > 0 ? j - R : 0); jj <= (j + R < ny - 1 ? j + R : ny - 1); ++jj)
+            for (int ii = (i - R > 0 ? i - R : 0); ii <= (i + R < nx - 1 ? i + R : nx - 1); ++ii) {
+                const double di = ii - i, dj = jj - j, dk = kk - k;
+                const double w = rmin - sqrt(di * di + dj * dj + dk * dk);
+                if (w > 0.0) {
+                    num += w * g[ii + (int64_t)nx * (jj + (int64_t)ny * kk)];
+                    den += w;
+                }
+            }
+    return num / den;
+}
+
+struct MmaParams {
+    double x_min, x_max, s0, s_dec, s_inc;
+};
+
+// Per-variable state of one MMA step: asymptotes, move limits and the
+// coefficients of the two approximations.
+struct MmaVar {
+    double L, U, alpha, beta, p0, q0, p1, q1;
+};
+
+// iter: the number of steps taken before this one.  x1, x2: the two
+// previous iterates; Lp, Up: the previous asymptotes (read when iter >= 2).
+TO_HD MmaVar mma_setup(const MmaParams &P, int iter, double x, double x1, double x2, double Lp, double Up,
+                       double df0, double df1)
+{
+    MmaVar v;
+    const double span = P.x_max - P.x_min;
+    if (iter < 2) {
+        v.L = x - P.s0 * span;
+        v.U = x + P.s0 * span;
+    } else {
+        const double sg = (x - x1) * (x1 - x2);
+        const double fac = sg < 0.0 ? P.s_dec : (sg > 0.0 ? P.s_inc : 1.0);
+        v.L = x - fac * (x1 - Lp);
+        v.U = x + fac * (Up - x1);
+    }
+    v.alpha = fmax(P.x_min, 0.9 * v.L + 0.1 * x);
+    v.beta = fmin(P.x_max, 0.9 * v.U + 0.1 * x);
+    const double dU = v.U - x, dL = x - v.L;
+    v.p0 = dU * dU * fmax(df0, 0.0);
+    v.q0 = dL * dL * fmax(-df0, 0.0);
+    v.p1 = dU * dU * fmax(df1, 0.0);
+    v.q1 = dL * dL * fmax(-df1, 0.0);
+    return v;
+}
+
+// the constant part of the constraint model: p1/(U - x) + q1/(x - L)
+TO_HD double mma_model_at_x(const MmaVar &v, double x) { return v.p1 / (v.U - x) + v.q1 / (x - v.L); }
+
+TO_HD double mma_y(const MmaVar &v, double x, double lam)
+{
+    const double sP = sqrt(v.p0 + lam * v.p1), sQ = sqrt(v.q0 + lam * v.q1);
+    const double den = sP + sQ;
+    const double y = den > 0.0 ? (sP * v.L + sQ * v.U) / den : x;
+    return fmin(fmax(y, v.alpha), v.beta);
+}
+
+// this variable's term of the constraint model at y(lam)
+TO_HD double mma_g1_term(const MmaVar &v, double x, double lam)
+{
+    const double y = mma_y(v, x, lam);
+    return v.p1 / (v.U - y) + v.q1 / (y - v.L);
+}
+
+// Multiplier of the MMA subproblem's one-dimensional dual: g1(lam) (the
+// constraint model at y(lam), non-increasing in lam) is given as a callable.
+// lam = 0 when g1(0) <= 0; otherwise the bracket [0, 1] is doubled until
+// g1(hi) <= 0 and then bisected to the last representable midpoint (at most
+// 200 halvings).  Returns a negative value when no bracket is found below
+// 1e300.  Host code (the callable may launch kernels).
+template <typename G>
+double mma_dual(G g1)
+{
+    if (!(g1(0.0) > 0.0)) return 0.0;
+    double lo = 0.0, hi = 1.0;
+    while (g1(hi) > 0.0) {
+        lo = hi;
+        hi *= 2.0;
+        if (hi > 1e300) return -1.0;
+    }
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        if (g1(mid) > 0.0) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
+}  // namespace topopt
+}  // namespace femgb

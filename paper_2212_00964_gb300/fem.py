@@ -103,6 +103,8 @@ def lib():
     L.fem_j2_tangent_apply.argtypes = [P, JP, P, P, P, P, P, P]
     L.fem_j2_step.argtypes = [P, JP, P, P, P, P, D, I, D, I, ctypes.POINTER(I), ctypes.POINTER(I),
                               ctypes.POINTER(I64), P]
+    L.fem_density_filter.argtypes = [P, D, P, P, P]
+    L.fem_mma_step.argtypes = [P, P, D, P, P, D, D, I, P, P, P, P, P, ctypes.POINTER(D), P]
     L.fem_poisson_apply.argtypes = [P, I, D, I, P, P, P, P]
     L.fem_poisson_solve.argtypes = [P, I, D, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     L.fem_poisson_gradient.argtypes = [P, I, D, P, P, P, P, I64, D, I, P, P, P, ctypes.POINTER(D),
@@ -357,6 +359,41 @@ def fem_poisson_gradient(m: Mesh, theta, obs, u_obs, alpha=1.0, mask=None, rtol=
                                       _ptr(grad, dt, m.n_nodes, "grad"), ctypes.byref(J), its,
                                       _stream(stream)), "fem_poisson_gradient")
     return {"J": J.value, "grad": grad, "u": u, "lam": lam, "iters": (its[0], its[1])}
+
+
+def fem_density_filter(m: Mesh, g, rmin=1.5, out=None, stream=None):
+    """Cone-kernel sensitivity filter over the cells (float64 [n_cells])."""
+    out = torch.empty_like(g) if out is None else out
+    _check(lib().fem_density_filter(m.handle, ctypes.c_double(rmin), _ptr(g, torch.float64, m.n_cells, "g"),
+                                     _ptr(out, torch.float64, m.n_cells, "out"), _stream(stream)),
+           "fem_density_filter")
+    return out
+
+
+class MMAState:
+    """Caller-owned state of fem_mma_step (device arrays [n_cells])."""
+
+    def __init__(self, m: Mesh, x_min=0.0, x_max=1.0):
+        z = lambda: torch.zeros(m.n_cells, dtype=torch.float64, device="cuda")
+        self.m, self.x_min, self.x_max = m, float(x_min), float(x_max)
+        self.x1, self.x2, self.low, self.upp = z(), z(), z(), z()
+        self.iter = 0
+        self.lam = 0.0
+
+    def step(self, x, f1, df0, df1, stream=None):
+        n = self.m.n_cells
+        y = torch.empty_like(x)
+        lam = ctypes.c_double(0.0)
+        _check(lib().fem_mma_step(self.m.handle, _ptr(x, torch.float64, n, "x"), ctypes.c_double(f1),
+                                  _ptr(df0, torch.float64, n, "df0"), _ptr(df1, torch.float64, n, "df1"),
+                                  ctypes.c_double(self.x_min), ctypes.c_double(self.x_max), int(self.iter),
+                                  _ptr(self.x1, torch.float64, n), _ptr(self.x2, torch.float64, n),
+                                  _ptr(self.low, torch.float64, n), _ptr(self.upp, torch.float64, n),
+                                  _ptr(y, torch.float64, n, "y"), ctypes.byref(lam), _stream(stream)),
+               "fem_mma_step")
+        self.iter += 1
+        self.lam = lam.value
+        return y
 
 
 def j2_material(E, nu, sigma_y) -> fem_j2_material:

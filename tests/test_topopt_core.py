@@ -1,0 +1,104 @@
+"""CPU checks of the CUDA library's topology-optimisation arithmetic
+(csrc/topopt_core.cuh, compiled here with g++ through
+tests/topopt_core_host.cpp): the cone filter against the oracle's filter
+matrix, and MMA steps (the library's per-variable formulas and dual search)
+against the oracle's MMA, step by step, and in the closed-form problems."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import topopt as ot
+from paper_2212_00964_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(HERE, "topopt_core_host.cpp")
+HDR = os.path.join(ROOT, "paper_2212_00964_gb300", "csrc", "topopt_core.cuh")
+SO = os.path.join(ROOT, "paper_2212_00964_gb300", "_lib", "topopt_core_host.so")
+
+
+@pytest.fixture(scope="module")
+def core():
+    os.makedirs(os.path.dirname(SO), exist_ok=True)
+    if not os.path.exists(SO) or os.path.getmtime(SO) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)):
+        tmp = SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-Wall",
+                               SRC, "-o", tmp])
+        os.replace(tmp, SO)
+    L = ctypes.CDLL(SO)
+    P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    L.host_filter.argtypes = [P, P, I, I, I, D]
+    L.host_mma_step.argtypes = [I64, P, D, P, P, D, D, I, P, P, P, P, P]
+    L.host_mma_step.restype = D
+    return L
+
+
+def p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@pytest.mark.parametrize("rmin", [1.0, 1.5, 2.3, 3.0])
+def test_filter_matches_oracle(core, rmin):
+    nx, ny, nz = 7, 4, 3
+    g = np.random.default_rng(int(rmin * 10)).standard_normal(nx * ny * nz)
+    out = np.zeros_like(g)
+    core.host_filter(p(g), p(out), nx, ny, nz, rmin)
+    ref = ot.filter_sensitivities(ot.filter_matrix(nx, ny, nz, rmin), g)
+    assert np.abs(out - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+class HostMMA:
+    def __init__(self, core, n, x_min, x_max):
+        self.core, self.x_min, self.x_max = core, x_min, x_max
+        self.x1, self.x2, self.L, self.U = (np.zeros(n) for _ in range(4))
+        self.k = 0
+
+    def step(self, x, f0, df0, f1, df1):
+        y = np.zeros_like(x)
+        x = np.ascontiguousarray(x, np.float64)
+        df0 = np.ascontiguousarray(df0, np.float64)
+        df1 = np.ascontiguousarray(df1, np.float64)
+        lam = self.core.host_mma_step(x.size, p(x), f1, p(df0), p(df1), self.x_min, self.x_max, self.k,
+                                      p(self.x1), p(self.x2), p(self.L), p(self.U), p(y))
+        assert lam >= 0
+        self.k += 1
+        self.lam = lam
+        return y
+
+
+def test_mma_steps_match_oracle_on_the_cantilever_loop(core):
+    """Ten design iterations of the box cantilever: the oracle's loop with
+    its MMA replaced by the library's arithmetic stays with the oracle's own
+    loop to rounding."""
+    w = inputs.topopt_cantilever(nx=8, ny=4, nz=4, lx=2.0, ly=1.0, lz=1.0)
+    m = oracle.mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)
+    mat = oracle.Material(oracle.SIMP, w.E, w.nu, w.simp_p, w.simp_emin)
+    H = ot.filter_matrix(w.nx, w.ny, w.nz, 1.5)
+    ref_mma = ot.MMA(m.n_cells, 0.0, 1.0)
+    host_mma = HostMMA(core, m.n_cells, 0.0, 1.0)
+    theta = np.full(m.n_cells, 0.5)
+    for it in range(10):
+        c, g, _ = ot.compliance_and_gradient(m, mat, w.mask, w.point_load, theta)
+        gf = ot.filter_sensitivities(H, g)
+        args = (theta, c, gf, float(theta.mean() - 0.5), np.full(m.n_cells, 1.0 / m.n_cells))
+        t_ref = ref_mma.step(*args)
+        t_host = host_mma.step(*args)
+        assert np.abs(t_host - t_ref).max() <= 1e-12, it
+        assert abs(host_mma.lam - ref_mma.lam) <= 1e-12 * max(1.0, ref_mma.lam)
+        theta = t_ref
+
+
+def test_mma_closed_form_nonlinear_constraint(core):
+    b = np.array([61.0, 37.0, 19.0, 7.0, 1.0])
+    a = 0.0624
+    lam = ((a / 3) ** 0.75 * np.sum(b ** 0.25)) ** (4 / 3)
+    xs = (3 * lam * b / a) ** 0.25
+    mma = HostMMA(core, 5, 1.0, 10.0)
+    x = np.full(5, 5.0)
+    for _ in range(60):
+        x = mma.step(x, a * x.sum(), np.full(5, a), np.sum(b / x ** 3) - 1, -3 * b / x ** 4)
+    assert np.abs(x - xs).max() <= 1e-9 * xs.max()

@@ -1,0 +1,51 @@
+// Host build of the topology-optimisation arithmetic of the CUDA library
+// (paper_2212_00964_gb300/csrc/topopt_core.cuh): the filter row and one MMA
+// step driven by the same dual search the library uses, with the
+// reductions done by plain loops.  Test code only.
+#include <stdint.h>
+
+#include <vector>
+
+#include "../paper_2212_00964_gb300/csrc/topopt_core.cuh"
+
+using namespace femgb::topopt;
+
+extern "C" {
+
+void host_filter(const double *g, double *out, int nx, int ny, int nz, double rmin)
+{
+    const int64_t n = (int64_t)nx * ny * nz;
+    for (int64_t e = 0; e < n; ++e) out[e] = filter_cell(g, e, nx, ny, nz, rmin);
+}
+
+// Mirrors fem_mma_step: returns the multiplier (negative: no bracket).
+double host_mma_step(int64_t n, const double *x, double f1, const double *df0, const double *df1, double x_min,
+                     double x_max, int iter, double *x1, double *x2, double *low, double *upp, double *y)
+{
+    const MmaParams P{x_min, x_max, 0.5, 0.7, 1.2};
+    std::vector<MmaVar> v(n);
+    double base = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        const bool h = iter >= 2;
+        v[j] = mma_setup(P, iter, x[j], h ? x1[j] : 0.0, h ? x2[j] : 0.0, h ? low[j] : 0.0, h ? upp[j] : 0.0,
+                         df0[j], df1[j]);
+        base += mma_model_at_x(v[j], x[j]);
+    }
+    const double r1 = f1 - base;
+    auto g1 = [&](double lam) {
+        double s = 0.0;
+        for (int64_t j = 0; j < n; ++j) s += mma_g1_term(v[j], x[j], lam);
+        return r1 + s;
+    };
+    const double lam = mma_dual(g1);
+    if (lam < 0) return lam;
+    for (int64_t j = 0; j < n; ++j) {
+        y[j] = mma_y(v[j], x[j], lam);
+        x2[j] = x1[j];
+        x1[j] = x[j];
+        low[j] = v[j].L;
+        upp[j] = v[j].U;
+    }
+    return lam;
+}
+}
