@@ -8,7 +8,10 @@
  * with 2x2x2 Gauss quadrature -- residual, matrix-free consistent tangent
  * (Eq. (5)), Jacobi diagonal, adjoint vector-Jacobian product (Eq. (23)) --
  * and the solvers around it (Newton, Eq. (4), with Jacobi-preconditioned CG;
- * adjoint solve, Eq. (22)).
+ * adjoint solve, Eq. (22)).  Further sections: the paper's assembled-matrix
+ * BiCGSTAB, the scalar Poisson problem of the full-field inference example
+ * (Sec. 3.1), perfect J2 plasticity (Sec. 2.3) and the filter and optimiser
+ * steps of topology optimisation (Sec. 3.2).
  *
  * Conventions shared by every call
  *   Mesh      structured box of nx*ny*nz cells on [0,lx]x[0,ly]x[0,lz];
