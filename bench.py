@@ -97,6 +97,8 @@ def parse():
                     help="1: one fused CG kernel per iteration (update + apply) instead of two")
     ap.add_argument("--no-suite", action="store_true",
                     help="skip the secondary measurements (batch c3, adjoint c2, 128^3 c4)")
+    ap.add_argument("--next-suite", action="store_true",
+                    help="also time the Poisson inference, J2 plasticity and topology-optimisation paths")
     return ap.parse_args()
 
 
@@ -383,6 +385,112 @@ def suite(F, inputs, torch):
     return out
 
 
+def next_suite(F, inputs, torch):
+    """Timings of the scalar Poisson, J2 plasticity and topology-optimisation
+    paths (opt-in): one objective + adjoint gradient of the full-field
+    inference at the paper's 50x50x10 and at 256x256x64, with the stiffness
+    stencil timed alone by CUDA events; the J2 load / unload path on a 16^3
+    box; one topology-optimisation iteration (SIMP solve, adjoint, filter,
+    MMA step) on the 128x64x64 cantilever.  Each entry records its error
+    instead of stopping the benchmark."""
+    import numpy as np
+    out = {}
+
+    def guarded(name, fn):
+        try:
+            out[name] = fn()
+        except Exception as e:  # keep the other entries
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+
+    def poisson(nx, ny, nz):
+        w = inputs.poisson_inference(nx, ny, nz, 1.0, 1.0, 0.2)
+        m = F.fem_mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)
+        mask = torch.tensor(w.mask, device="cuda")
+        th = torch.tensor(w.theta_true, device="cuda")
+        obs = torch.tensor(w.obs, device="cuda")
+        uobs = torch.zeros(w.obs.size, dtype=torch.float64, device="cuda")
+        F.fem_poisson_gradient(m, th, obs, uobs, w.alpha, mask, rtol=1e-10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = F.fem_poisson_gradient(m, th, obs, uobs, w.alpha, mask, rtol=1e-10)
+        torch.cuda.synchronize()
+        tg = time.perf_counter() - t0
+        res = {"nodes": m.n_nodes, "gradient_s": tg, "cg_iters": list(r["iters"])}
+        for name, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+            x = torch.randn(m.n_nodes, dtype=dt, device="cuda")
+            F.fem_poisson_apply(m, x, 1.0, F.FEM_POISSON_STIFFNESS, mask)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                F.fem_poisson_apply(m, x, 1.0, F.FEM_POISSON_STIFFNESS, mask)
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / 20 / 1e3
+            nbytes = m.n_nodes * (2 * x.element_size() + 1)
+            res[f"apply_{name}"] = {"us": t * 1e6, "gbs_algorithmic": nbytes / t / 1e9,
+                                    "note": "includes the stencil-table build launch"}
+        return res
+
+    guarded("poisson_50x50x10", lambda: poisson(50, 50, 10))
+    guarded("poisson_256x256x64", lambda: poisson(256, 256, 64))
+
+    def j2_path():
+        n = 16
+        mask_h, ubars, strains, (E, nu, sy) = inputs.j2_uniaxial(n=n)
+        m = F.fem_mesh(n, n, n)
+        mat = F.j2_material(E, nu, sy)
+        mask = torch.tensor(mask_h, device="cuda")
+        ub = [torch.tensor(b, device="cuda") for b in ubars]
+        u = torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda")
+        hist = F.j2_history(m)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = [F.fem_j2_step(m, mat, mask, b, u, hist) for b in ub]
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        return {"dofs": m.n_dofs, "steps": len(ub), "path_s": t,
+                "newton_iters": sum(i["newton_iters"] for i in its), "cg_iters": sum(i["cg_iters"] for i in its)}
+
+    guarded("j2_16cube_path", j2_path)
+
+    def topopt_iter():
+        w = inputs.c2()
+        m = F.fem_mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)
+        mat = F.material(w.kind, w.E, w.nu, w.simp_p, w.simp_emin)
+        mask, f = torch.tensor(w.mask, device="cuda"), torch.tensor(w.point_load, device="cuda")
+        zero = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
+        theta = torch.full((w.n_cells,), 0.5, dtype=torch.float64, device="cuda")
+        st = F.MMAState(m, 0.0, 1.0)
+        dv = torch.full_like(theta, 1.0 / w.n_cells)
+        opt = F.default_options(newton_rtol=1e-10)
+        t = {}
+
+        def one():
+            nonlocal theta
+            u = torch.zeros_like(zero)
+            a = time.perf_counter()
+            F.fem_solve(m, mat, mask, zero, u, f, theta, 1, opt)
+            torch.cuda.synchronize()
+            b = time.perf_counter()
+            g, _ = F.fem_adjoint(m, mat, mask, u, f, theta, options=opt)
+            torch.cuda.synchronize()
+            c = time.perf_counter()
+            gf = F.fem_density_filter(m, g, 1.5)
+            torch.cuda.synchronize()
+            d = time.perf_counter()
+            theta = st.step(theta, float(theta.mean()) - 0.5, gf, dv)
+            torch.cuda.synchronize()
+            e = time.perf_counter()
+            t.update(solve_s=b - a, adjoint_s=c - b, filter_s=d - c, mma_s=e - d)
+
+        one()
+        one()
+        return {"cells": w.n_cells, "dofs": w.n_dofs, **t}
+
+    guarded("topopt_iter_c2", topopt_iter)
+    return out
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -496,6 +604,9 @@ def run_gb300(args):
     extra = None
     if not args.no_suite:
         extra = suite(F, inputs, torch)
+    if args.next_suite:
+        extra = dict(extra or {})
+        extra["next"] = next_suite(F, inputs, torch)
     if rank != 0:
         return 0
     cpu = None
