@@ -6,23 +6,22 @@
 // Iteration k reads rz_k = (r_k, z_k) and pq_k = (p_k, A p_k) from
 // sc[3k + 0] and sc[3k + 1] and writes rz_{k+1}, rr_{k+1} = (r_{k+1}, r_{k+1})
 // to sc[3(k+1) + 0] and sc[3(k+1) + 2]; the operator adds pq_k itself.  No
-// launch waits for the host; the host reads the scalars once every
-// DPCG_CHECK iterations to test ||r|| <= rtol ||b||, non-finite values and
-// p^T A p <= 0 (breakdown), so up to DPCG_CHECK - 1 extra iterations run
-// after convergence.
+// launch waits for the host; the host control (dpcg_control.h) reads the
+// scalars once every CHECK iterations to test ||r|| <= rtol ||b||,
+// non-finite values and p^T A p <= 0 (breakdown).
 #pragma once
 
 #include <algorithm>
 #include <cmath>
-#include <vector>
+#include <string>
 
+#include "dpcg_control.h"
 #include "fem_internal.cuh"
 
 namespace femgb {
 namespace dpcg {
 
 constexpr int NT = 256;
-constexpr int CHECK = 8;
 
 inline int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + NT - 1) / NT, 152 * 8)); }
 
@@ -98,34 +97,43 @@ struct Buffers {
 
 inline size_t scalar_count(int maxit) { return 3 * ((size_t)maxit + 2); }
 
-// Solve A u = b; u holds the start value.  apply(x, y, dot) must launch
-// y = A x on the stream and, when dot is not null, add (x, A x) to *dot.
+static_assert((int)ST_NOT_CONVERGED == (int)FEM_ERR_NOT_CONVERGED && (int)ST_BREAKDOWN == (int)FEM_ERR_BREAKDOWN &&
+                  (int)ST_NONFINITE == (int)FEM_ERR_NONFINITE,
+              "CG control status codes are the library's");
+
+// The device side of control(): kernels on the stream, scalars in w.sc.
 template <typename T, typename Apply>
-int solve(cudaStream_t s, int64_t N, Apply apply, const T *dinv, const T *b, T *u, const Buffers<T> &w, double rtol,
-          int maxit, int *iters, double *rel_res, const char *who)
-{
-    const int g = grid_for(N);
-    FEM_CUDA(cudaMemsetAsync(w.sc, 0, sizeof(double) * scalar_count(maxit), s));
-    FEM_CUDA(cudaMemsetAsync(w.small, 0, sizeof(double), s));
-    if (int rc = apply(u, w.q, nullptr)) return rc;
-    k_init<T><<<g, NT, 0, s>>>(b, w.q, dinv, w.r, w.z, w.p, N, w.sc, w.small);
-    count_launch();
-    FEM_CUDA(cudaGetLastError());
-    double h0[3], bb;
-    FEM_CUDA(cudaMemcpyAsync(h0, w.sc, sizeof(h0), cudaMemcpyDeviceToHost, s));
-    FEM_CUDA(cudaMemcpyAsync(&bb, w.small, sizeof(double), cudaMemcpyDeviceToHost, s));
-    FEM_CUDA(cudaStreamSynchronize(s));
-    const double bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
-    double rr = h0[2];
-    if (!std::isfinite(rr) || !std::isfinite(h0[0]))
-        return (set_error(std::string(who) + ": non-finite residual"), FEM_ERR_NONFINITE);
-    int k = 0;
-    int rc = std::sqrt(rr) <= rtol * bn ? FEM_OK : FEM_ERR_NOT_CONVERGED;
-    std::vector<double> hs;
-    while (rc == FEM_ERR_NOT_CONVERGED && k < maxit) {
-        const int k0 = k;
-        const int k1 = std::min(maxit, k + CHECK);
-        for (; k < k1; ++k) {
+struct DeviceOps {
+    cudaStream_t s;
+    int64_t N;
+    Apply &apply;
+    const T *dinv;
+    const T *b;
+    T *u;
+    const Buffers<T> &w;
+    int maxit;
+    const char *who;
+
+    int start(double *rz0, double *rr0, double *bb)
+    {
+        FEM_CUDA(cudaMemsetAsync(w.sc, 0, sizeof(double) * scalar_count(maxit), s));
+        FEM_CUDA(cudaMemsetAsync(w.small, 0, sizeof(double), s));
+        if (int rc = apply(u, w.q, nullptr)) return rc;
+        k_init<T><<<grid_for(N), NT, 0, s>>>(b, w.q, dinv, w.r, w.z, w.p, N, w.sc, w.small);
+        count_launch();
+        FEM_CUDA(cudaGetLastError());
+        double h0[3];
+        FEM_CUDA(cudaMemcpyAsync(h0, w.sc, sizeof(h0), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaMemcpyAsync(bb, w.small, sizeof(double), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaStreamSynchronize(s));
+        *rz0 = h0[0];
+        *rr0 = h0[2];
+        return FEM_OK;
+    }
+    int iterate(int k0, int k1)
+    {
+        const int g = grid_for(N);
+        for (int k = k0; k < k1; ++k) {
             double *sck = w.sc + 3 * (size_t)k, *sck1 = w.sc + 3 * ((size_t)k + 1);
             if (int e = apply(w.p, w.q, &sck[1])) return e;
             k_update<T><<<g, NT, 0, s>>>(u, w.r, w.z, w.p, w.q, dinv, N, sck, sck1);
@@ -133,34 +141,26 @@ int solve(cudaStream_t s, int64_t N, Apply apply, const T *dinv, const T *b, T *
             count_launch(2);
         }
         FEM_CUDA(cudaGetLastError());
-        hs.resize(3 * (size_t)(k - k0 + 1));
-        FEM_CUDA(cudaMemcpyAsync(hs.data(), w.sc + 3 * (size_t)k0, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost,
-                                 s));
-        FEM_CUDA(cudaStreamSynchronize(s));
-        for (int j = 0; j < k - k0; ++j) {
-            const double rz = hs[3 * j], pq = hs[3 * j + 1], rr1 = hs[3 * (j + 1) + 2];
-            if (!std::isfinite(rz) || !std::isfinite(pq) || !std::isfinite(rr1)) {
-                set_error(std::string(who) + ": non-finite CG scalar");
-                rc = FEM_ERR_NONFINITE;
-                break;
-            }
-            if (pq <= 0.0 && rz > 0.0) {
-                set_error(std::string(who) + ": p^T A p <= 0 (operator not positive definite)");
-                rc = FEM_ERR_BREAKDOWN;
-                break;
-            }
-            rr = rr1;
-            if (std::sqrt(rr) <= rtol * bn) {
-                rc = FEM_OK;
-                rr = hs[3 * (size_t)(k - k0) + 2];  // the batch's later iterations ran as well
-                break;
-            }
-        }
+        return FEM_OK;
     }
-    if (iters) *iters = k;
-    if (rel_res) *rel_res = std::sqrt(rr) / bn;
-    if (rc == FEM_ERR_NOT_CONVERGED) set_error(std::string(who) + ": CG iteration limit reached");
-    return rc;
+    int read(int k0, int k1, double *hs)
+    {
+        FEM_CUDA(cudaMemcpyAsync(hs, w.sc + 3 * (size_t)k0, sizeof(double) * 3 * (size_t)(k1 - k0 + 1),
+                                 cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaStreamSynchronize(s));
+        return FEM_OK;
+    }
+    void fail(const char *what) { set_error(std::string(who) + ": " + what); }
+};
+
+// Solve A u = b; u holds the start value.  apply(x, y, dot) must launch
+// y = A x on the stream and, when dot is not null, add (x, A x) to *dot.
+template <typename T, typename Apply>
+int solve(cudaStream_t s, int64_t N, Apply apply, const T *dinv, const T *b, T *u, const Buffers<T> &w, double rtol,
+          int maxit, int *iters, double *rel_res, const char *who)
+{
+    DeviceOps<T, Apply> ops{s, N, apply, dinv, b, u, w, maxit, who};
+    return control(ops, rtol, maxit, iters, rel_res);
 }
 
 }  // namespace dpcg

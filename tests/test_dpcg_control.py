@@ -1,0 +1,101 @@
+"""CPU checks of the host control of the device-scalar Jacobi-PCG
+(csrc/dpcg_control.h) that the Poisson and J2 paths share, driven through
+tests/dpcg_control_host.cpp by CPU stand-ins of its kernels: convergence to
+numpy's solution, the batching of iterations between host reads, and the
+exits (already converged, zero right-hand side, iteration limit, an
+indefinite operator, non-finite input)."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(HERE, "dpcg_control_host.cpp")
+HDR = os.path.join(ROOT, "paper_2212_00964_gb300", "csrc", "dpcg_control.h")
+SO = os.path.join(ROOT, "paper_2212_00964_gb300", "_lib", "dpcg_control_host.so")
+OK, NOT_CONVERGED, BREAKDOWN, NONFINITE = 0, -3, -5, -6
+CHECK = 8
+
+
+@pytest.fixture(scope="module")
+def L():
+    os.makedirs(os.path.dirname(SO), exist_ok=True)
+    if not os.path.exists(SO) or os.path.getmtime(SO) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)):
+        tmp = SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-Wall", SRC, "-o", tmp])
+        os.replace(tmp, SO)
+    lib = ctypes.CDLL(SO)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.host_pcg.argtypes = [I, P, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]
+    lib.host_pcg_error.restype = ctypes.c_char_p
+    return lib
+
+
+def p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def run(L, A, b, u0=None, rtol=1e-12, maxit=500):
+    A = np.ascontiguousarray(A, np.float64)
+    n = A.shape[0]
+    d = np.diag(A)
+    dinv = np.where(d != 0, 1.0 / np.where(d != 0, d, 1.0), 0.0)
+    u = np.zeros(n) if u0 is None else np.array(u0, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    it, res, calls = ctypes.c_int(-1), ctypes.c_double(-1), ctypes.c_int(-1)
+    rc = L.host_pcg(n, p(A), p(dinv), p(b), p(u), rtol, maxit, ctypes.byref(it), ctypes.byref(res),
+                    ctypes.byref(calls))
+    return rc, u, it.value, res.value, calls.value, L.host_pcg_error().decode()
+
+
+def spd(n, seed, cond=1e3):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return Q @ np.diag(np.geomspace(1.0, cond, n)) @ Q.T
+
+
+def test_converges_to_the_solution(L):
+    A = spd(60, 1)
+    b = np.random.default_rng(2).standard_normal(60)
+    rc, u, it, res, calls, _ = run(L, A, b)
+    assert rc == OK
+    assert np.linalg.norm(A @ u - b) <= 1e-11 * np.linalg.norm(b)
+    # the reported residual is CG's recursively updated one (the true one
+    # stagnates at the rounding level, which the line above bounds)
+    assert res <= 1e-12
+    assert it % CHECK == 0 and calls == it // CHECK
+
+
+def test_exact_start_and_zero_rhs(L):
+    A = spd(20, 3)
+    b = np.random.default_rng(4).standard_normal(20)
+    rc, u, it, res, _, _ = run(L, A, b, u0=np.linalg.solve(A, b), rtol=1e-8)
+    assert rc == OK and it == 0
+    rc, u, it, res, _, _ = run(L, A, np.zeros(20))
+    assert rc == OK and it == 0 and res == 0.0 and np.all(u == 0)
+
+
+def test_iteration_limit(L):
+    A = spd(80, 5, cond=1e8)
+    b = np.random.default_rng(6).standard_normal(80)
+    rc, u, it, res, calls, err = run(L, A, b, maxit=11)
+    assert rc == NOT_CONVERGED and it == 11 and calls == 2 and "limit" in err and res > 1e-12
+
+
+def test_indefinite_operator_is_a_breakdown(L):
+    rng = np.random.default_rng(7)
+    Q, _ = np.linalg.qr(rng.standard_normal((30, 30)))
+    A = Q @ np.diag(np.linspace(-1.0, 2.0, 30)) @ Q.T
+    rc, _, _, _, _, err = run(L, A, rng.standard_normal(30), maxit=200)
+    assert rc == BREAKDOWN and "positive definite" in err
+
+
+def test_non_finite_input(L):
+    A = spd(10, 8)
+    b = np.ones(10)
+    b[3] = np.nan
+    rc, _, it, _, _, err = run(L, A, b)
+    assert rc == NONFINITE and "non-finite" in err
