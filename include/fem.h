@@ -175,7 +175,10 @@ int fem_bicgstab_csr(fem_mesh_t m, int precision, const void *vals, const void *
  * n_nodes; no CSR needed).  mask: uint8 [n_nodes], 1 = u prescribed, or
  * NULL.  The source is given by its nodal values theta, b^h = sum N_a theta_a,
  * so the load is F(theta) = M theta with the mass matrix M.  precision
- * FEM_FP64 (value arrays double) or FEM_FP32 (float; dot products double).
+ * FEM_FP64 (value arrays double) or FEM_FP32 (float; dot products double);
+ * the solves also take FEM_MIXED (arrays double): FP64 residuals b - A u
+ * drive rounds of FP32 CG on the correction (relative tolerance 1e-4 each,
+ * at most 40 rounds), and maxit bounds the FP32 iterations of all rounds.
  * Asynchronous on `stream` unless stated; serialised per mesh handle. */
 #define FEM_POISSON_STIFFNESS 0 /* A_ab = alpha int grad N_a . grad N_b */
 #define FEM_POISSON_MASS 1      /* M_ab = int N_a N_b */

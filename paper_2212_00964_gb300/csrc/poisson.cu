@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "dev_pcg.cuh"
@@ -28,7 +29,12 @@ constexpr int PB = 256;  // threads per block
 constexpr int MAX_ITERS = 1000000;
 
 // workspace slots of this path
-enum { WS_PTAB = 48, WS_PR, WS_PZ, WS_PP, WS_PQ, WS_PDINV, WS_PSC, WS_PRHS, WS_PSMALL };
+enum {
+    WS_PTAB = 48, WS_PR, WS_PZ, WS_PP, WS_PQ, WS_PDINV, WS_PSC, WS_PRHS, WS_PSMALL,
+    WS_PTAB32, WS_PMSMALL, WS_PR32, WS_PC32, WS_PQ64
+};
+constexpr int MAX_REFINE = 40;  // FP64 refinement rounds of the mixed solve
+constexpr double INNER_RTOL = 1e-4;  // FP32 CG tolerance per refinement round
 
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + PB - 1) / PB, 152 * 8)); }
 
@@ -77,6 +83,32 @@ __global__ void k_pois_dinv(const T *__restrict__ tab, const uint8_t *__restrict
     }
 }
 
+// Mixed solve, FP64 side: r = b - q (q = A u in FP64), r32 = (float) r;
+// acc[0] += (r, r), acc[1] += (b, b).
+__global__ void __launch_bounds__(PB) k_pois_refine(const double *__restrict__ b, const double *__restrict__ q,
+                                                   float *__restrict__ r32, int64_t N, double *acc)
+{
+    __shared__ double sh[PB / 32];
+    double rr = 0, bb = 0;
+    for (int64_t n = blockIdx.x * (int64_t)PB + threadIdx.x; n < N; n += (int64_t)gridDim.x * PB) {
+        const double r = b[n] - q[n];
+        r32[n] = (float)r;
+        rr += r * r;
+        bb += b[n] * b[n];
+    }
+    rr = block_sum<double, PB>(rr, sh);
+    if (threadIdx.x == 0) atomicAdd(&acc[0], rr);
+    bb = block_sum<double, PB>(bb, sh);
+    if (threadIdx.x == 0) atomicAdd(&acc[1], bb);
+}
+
+// u += (double) c
+__global__ void k_pois_correct(double *__restrict__ u, const float *__restrict__ c, int64_t N)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+        u[n] += (double)c[n];
+}
+
 // Objective of Eq. (26) and the adjoint right-hand side:
 // J += (u[o] - u_obs[i])^2, rhs[o] += 2 (u[o] - u_obs[i]) on free nodes.
 // An observation index outside [0, N) sets *bad and is skipped.
@@ -110,9 +142,9 @@ struct Ctx {
 
 // Stencil tables for (alpha, the mesh's cell size) in the workspace.
 template <typename T>
-const T *make_tables(const Ctx &c, double alpha)
+const T *make_tables(const Ctx &c, double alpha, int slot = WS_PTAB)
 {
-    T *tab = (T *)c.m->ws.get(WS_PTAB, sizeof(T) * 2 * poisson::TAB);
+    T *tab = (T *)c.m->ws.get(slot, sizeof(T) * 2 * poisson::TAB);
     if (!tab) return nullptr;
     k_pois_tables<T><<<1, 128, 0, c.s>>>(c.m->lx / c.m->nx, c.m->ly / c.m->ny, c.m->lz / c.m->nz, alpha, tab);
     count_launch();
@@ -150,6 +182,52 @@ int cg_solve(const Ctx &c, const T *tabA, const uint8_t *mask, const T *b, T *u,
     return dpcg::solve<T>(c.s, N, apply, dinv, b, u, w, rtol, maxit, iters, rel_res, "poisson CG");
 }
 
+// Mixed precision: FP64 residuals b - A u drive rounds of FP32 CG on the
+// correction (tolerance INNER_RTOL each), u += c, until ||b - A u|| <=
+// rtol ||b|| in FP64.  maxit bounds the FP32 CG iterations of all rounds.
+int solve_mixed(const Ctx &c, const double *tab64, const float *tab32, const uint8_t *mask, const double *b, double *u,
+                double rtol, int maxit, int *iters, double *rel_res)
+{
+    const int64_t N = c.N;
+    double *q64 = (double *)c.m->ws.get(WS_PQ64, sizeof(double) * N);
+    float *r32 = (float *)c.m->ws.get(WS_PR32, sizeof(float) * N);
+    float *c32 = (float *)c.m->ws.get(WS_PC32, sizeof(float) * N);
+    double *acc = (double *)c.m->ws.get(WS_PMSMALL, sizeof(double) * 2);
+    if (!q64 || !r32 || !c32 || !acc) return FEM_ERR_NOMEM;
+    int total = 0;
+    double rel = 0.0;
+    int rc = FEM_ERR_NOT_CONVERGED;
+    for (int round = 0; round <= MAX_REFINE; ++round) {
+        FEM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * 2, c.s));
+        launch_op<double>(c, tab64, u, mask, poisson::OUT_ELIM, q64, nullptr);
+        k_pois_refine<<<grid_for(N), PB, 0, c.s>>>(b, q64, r32, N, acc);
+        count_launch();
+        FEM_CUDA(cudaGetLastError());
+        double h[2];
+        FEM_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, c.s));
+        FEM_CUDA(cudaStreamSynchronize(c.s));
+        if (!std::isfinite(h[0])) return (set_error("poisson mixed solve: non-finite residual"), FEM_ERR_NONFINITE);
+        const double bn = std::sqrt(h[1]) > 0 ? std::sqrt(h[1]) : 1.0;
+        rel = std::sqrt(h[0]) / bn;
+        if (rel <= rtol) {
+            rc = FEM_OK;
+            break;
+        }
+        if (round == MAX_REFINE || total >= maxit) break;
+        FEM_CUDA(cudaMemsetAsync(c32, 0, sizeof(float) * N, c.s));
+        int it = 0;
+        const int inner = cg_solve<float>(c, tab32, mask, r32, c32, INNER_RTOL, maxit - total, &it, nullptr);
+        total += it;
+        if (inner != FEM_OK && inner != FEM_ERR_NOT_CONVERGED) return inner;
+        k_pois_correct<<<grid_for(N), PB, 0, c.s>>>(u, c32, N);
+        count_launch();
+    }
+    if (iters) *iters = total;
+    if (rel_res) *rel_res = rel;
+    if (rc != FEM_OK) set_error("poisson mixed solve: iteration limit reached");
+    return rc;
+}
+
 int check_mesh(fem_mesh_t m, const char *what)
 {
     if (!m) return (set_error(std::string(what) + ": NULL mesh"), FEM_ERR_ARG);
@@ -171,28 +249,44 @@ int apply_t(fem_mesh_t m, double alpha, int op, const uint8_t *mask, const T *x,
 
 template <typename T>
 int solve_t(fem_mesh_t m, double alpha, const uint8_t *mask, const T *b, T *u, double rtol, int maxit, int *iters,
-            double *rel_res, cudaStream_t s)
+            double *rel_res, cudaStream_t s, bool mixed = false)
 {
     Ctx c{m, m->n_nodes, s};
     const T *tab = make_tables<T>(c, alpha);
     if (!tab) return FEM_ERR_NOMEM;
+    if constexpr (std::is_same<T, double>::value) {
+        if (mixed) {
+            const float *tab32 = make_tables<float>(c, alpha, WS_PTAB32);
+            if (!tab32) return FEM_ERR_NOMEM;
+            return solve_mixed(c, tab, tab32, mask, b, u, rtol, maxit, iters, rel_res);
+        }
+    }
     return cg_solve<T>(c, tab, mask, b, u, rtol, maxit, iters, rel_res);
 }
 
 template <typename T>
 int gradient_t(fem_mesh_t m, double alpha, const uint8_t *mask, const T *theta, const int64_t *obs, const T *u_obs,
-               int64_t n_obs, double rtol, int maxit, T *u, T *lam, T *grad, double *J, int *iters, cudaStream_t s)
+               int64_t n_obs, double rtol, int maxit, T *u, T *lam, T *grad, double *J, int *iters, cudaStream_t s,
+               bool mixed = false)
 {
     Ctx c{m, m->n_nodes, s};
     const int64_t N = c.N;
     const T *tab = make_tables<T>(c, alpha);
     T *rhs = (T *)m->ws.get(WS_PRHS, sizeof(T) * N);
     if (!tab || !rhs) return FEM_ERR_NOMEM;
+    const float *tab32 = nullptr;
+    if (mixed && !(tab32 = make_tables<float>(c, alpha, WS_PTAB32))) return FEM_ERR_NOMEM;
+    auto cg_solve = [&](const uint8_t *mk, const T *bb, T *x, double rt, int mi, int *it, double *rr) -> int {
+        if constexpr (std::is_same<T, double>::value) {
+            if (mixed) return solve_mixed(c, tab, tab32, mk, bb, x, rt, mi, it, rr);
+        }
+        return ::femgb::cg_solve<T>(c, tab, mk, bb, x, rt, mi, it, rr);
+    };
     // forward: A u = M theta (free rows), u = 0 on masked nodes
     launch_op<T>(c, tab + poisson::TAB, theta, mask, mask ? poisson::OUT_ZERO : poisson::OUT_PLAIN, rhs, nullptr);
     FEM_CUDA(cudaMemsetAsync(u, 0, sizeof(T) * N, s));
     int it_f = 0, it_a = 0;
-    int rc = cg_solve<T>(c, tab, mask, rhs, u, rtol, maxit, &it_f, nullptr);
+    int rc = cg_solve(mask, rhs, u, rtol, maxit, &it_f, nullptr);
     if (rc != FEM_OK) return rc;
     // objective and adjoint right-hand side 2 (u - u_obs) on the observed free nodes
     double *small = (double *)m->ws.get(WS_PSMALL, sizeof(double) * 4);
@@ -211,7 +305,7 @@ int gradient_t(fem_mesh_t m, double alpha, const uint8_t *mask, const T *theta, 
     if (bad) return (set_error("fem_poisson_gradient: observation index outside [0, n_nodes)"), FEM_ERR_ARG);
     // adjoint: A lambda = dJ/du (A symmetric), lambda = 0 on masked nodes
     FEM_CUDA(cudaMemsetAsync(lam, 0, sizeof(T) * N, s));
-    rc = cg_solve<T>(c, tab, mask, rhs, lam, rtol, maxit, &it_a, nullptr);
+    rc = cg_solve(mask, rhs, lam, rtol, maxit, &it_a, nullptr);
     if (rc != FEM_OK) return rc;
     // dJ/dtheta = M^T lambda (M symmetric; lambda vanishes on masked nodes)
     launch_op<T>(c, tab + poisson::TAB, lam, nullptr, poisson::OUT_PLAIN, grad, nullptr);
@@ -255,11 +349,12 @@ extern "C" int fem_poisson_solve(fem_mesh_t m, int precision, double alpha, cons
         return (set_error("fem_poisson_solve: alpha > 0, rtol > 0 and 0 <= maxit <= 1e6 required"), FEM_ERR_ARG);
     std::lock_guard<std::mutex> lk(m->mu);
     cudaStream_t s = (cudaStream_t)stream;
-    if (precision == FEM_FP64)
-        return solve_t<double>(m, alpha, mask, (const double *)b, (double *)u, rtol, maxit, iters, rel_res, s);
+    if (precision == FEM_FP64 || precision == FEM_MIXED)
+        return solve_t<double>(m, alpha, mask, (const double *)b, (double *)u, rtol, maxit, iters, rel_res, s,
+                               precision == FEM_MIXED);
     if (precision == FEM_FP32)
         return solve_t<float>(m, alpha, mask, (const float *)b, (float *)u, rtol, maxit, iters, rel_res, s);
-    return (set_error("fem_poisson_solve: precision must be FEM_FP64 or FEM_FP32"), FEM_ERR_ARG);
+    return (set_error("fem_poisson_solve: precision must be FEM_FP64, FEM_FP32 or FEM_MIXED"), FEM_ERR_ARG);
 }
 
 extern "C" int fem_poisson_gradient(fem_mesh_t m, int precision, double alpha, const uint8_t *mask,
@@ -274,11 +369,12 @@ extern "C" int fem_poisson_gradient(fem_mesh_t m, int precision, double alpha, c
         return (set_error("fem_poisson_gradient: alpha > 0, rtol > 0 and 0 <= maxit <= 1e6 required"), FEM_ERR_ARG);
     std::lock_guard<std::mutex> lk(m->mu);
     cudaStream_t s = (cudaStream_t)stream;
-    if (precision == FEM_FP64)
+    if (precision == FEM_FP64 || precision == FEM_MIXED)
         return gradient_t<double>(m, alpha, mask, (const double *)theta, obs, (const double *)u_obs, n_obs, rtol,
-                                  maxit, (double *)u, (double *)lambda, (double *)grad, J, iters, s);
+                                  maxit, (double *)u, (double *)lambda, (double *)grad, J, iters, s,
+                                  precision == FEM_MIXED);
     if (precision == FEM_FP32)
         return gradient_t<float>(m, alpha, mask, (const float *)theta, obs, (const float *)u_obs, n_obs, rtol, maxit,
                                  (float *)u, (float *)lambda, (float *)grad, J, iters, s);
-    return (set_error("fem_poisson_gradient: precision must be FEM_FP64 or FEM_FP32"), FEM_ERR_ARG);
+    return (set_error("fem_poisson_gradient: precision must be FEM_FP64, FEM_FP32 or FEM_MIXED"), FEM_ERR_ARG);
 }

@@ -324,14 +324,23 @@ def fem_poisson_apply(m: Mesh, x, alpha=1.0, op=FEM_POISSON_STIFFNESS, mask=None
     return y
 
 
+def _poisson_prec(dt, mixed):
+    if mixed:
+        if dt != torch.float64:
+            raise TypeError("the mixed-precision Poisson calls take float64 tensors")
+        return FEM_MIXED
+    return _prec(dt)
+
+
 def fem_poisson_solve(m: Mesh, b, alpha=1.0, mask=None, u=None, rtol=1e-10, maxit=10000, stream=None,
-                      check=True):
-    """Jacobi-PCG for the eliminated Poisson stiffness: returns (u, iterations, ||r||/||b||)."""
+                      check=True, mixed=False):
+    """Jacobi-PCG for the eliminated Poisson stiffness (mixed=True: FP32 CG
+    under FP64 refinement): returns (u, iterations, ||r||/||b||)."""
     dt = b.dtype
     u = torch.zeros_like(b) if u is None else u
     it = ctypes.c_int(0)
     res = ctypes.c_double(0.0)
-    rc = lib().fem_poisson_solve(m.handle, _prec(dt), ctypes.c_double(alpha),
+    rc = lib().fem_poisson_solve(m.handle, _poisson_prec(dt, mixed), ctypes.c_double(alpha),
                                  _ptr(mask, torch.uint8, m.n_nodes, "mask"), _ptr(b, dt, m.n_nodes, "b"),
                                  _ptr(u, dt, m.n_nodes, "u"), ctypes.c_double(rtol), int(maxit), ctypes.byref(it),
                                  ctypes.byref(res), _stream(stream))
@@ -341,17 +350,18 @@ def fem_poisson_solve(m: Mesh, b, alpha=1.0, mask=None, u=None, rtol=1e-10, maxi
 
 
 def fem_poisson_gradient(m: Mesh, theta, obs, u_obs, alpha=1.0, mask=None, rtol=1e-10, maxit=10000,
-                         stream=None):
+                         stream=None, mixed=False):
     """Objective of the full-field inference problem and its adjoint
     gradient: returns dict(J, grad, u, lam, iters)."""
     dt = theta.dtype
+    prec = _poisson_prec(dt, mixed)
     u = torch.empty_like(theta)
     lam = torch.empty_like(theta)
     grad = torch.empty_like(theta)
     J = ctypes.c_double(0.0)
     its = (ctypes.c_int * 2)()
     n_obs = obs.numel()
-    _check(lib().fem_poisson_gradient(m.handle, _prec(dt), ctypes.c_double(alpha),
+    _check(lib().fem_poisson_gradient(m.handle, prec, ctypes.c_double(alpha),
                                       _ptr(mask, torch.uint8, m.n_nodes, "mask"),
                                       _ptr(theta, dt, m.n_nodes, "theta"), _ptr(obs, torch.int64, n_obs, "obs"),
                                       _ptr(u_obs, dt, n_obs, "u_obs"), int(n_obs), ctypes.c_double(rtol),

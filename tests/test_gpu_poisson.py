@@ -59,6 +59,26 @@ def test_solve_paper_size(prec):
     assert np.all(host(u)[w.mask == 1] == 0)
 
 
+def test_mixed_precision_solve_and_gradient():
+    """FP32 CG under FP64 refinement reaches the FP64 answer at the paper's size."""
+    w = inputs.poisson_inference()
+    F = fem()
+    m = F.fem_mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)
+    om, prob = op.from_workload(w)
+    b = F.fem_poisson_apply(m, dev(w.theta_true), w.alpha, F.FEM_POISSON_MASS, dev(w.mask))
+    u, it, res = F.fem_poisson_solve(m, b, w.alpha, dev(w.mask), rtol=1e-11, maxit=20000, mixed=True)
+    assert res <= 1e-11 and it > 0
+    assert rel_l2(host(u), prob.solve(w.theta_true)) <= 1e-8
+    rng = np.random.default_rng(8)
+    theta = rng.standard_normal(om.n_nodes)
+    u_obs = 0.01 * rng.standard_normal(w.obs.size)
+    J, g, _, _ = prob.gradient(theta, w.obs, u_obs)
+    out = F.fem_poisson_gradient(m, dev(theta), dev(w.obs), dev(u_obs), w.alpha, dev(w.mask), rtol=1e-11,
+                                 maxit=20000, mixed=True)
+    assert abs(out["J"] - J) <= 1e-8 * abs(J)
+    assert rel_l2(host(out["grad"]), g) <= 1e-7
+
+
 def test_gradient_parity_small_and_paper_size():
     for w in (inputs.poisson_inference(4, 4, 3, 1.0, 1.0, 0.2, n_obs=6, seed=3), inputs.poisson_inference()):
         F = fem()
