@@ -15,6 +15,7 @@
 
 #include "dev_pcg.cuh"
 #include "j2_core.cuh"
+#include "j2_newton.h"
 #include "mesh.cuh"
 
 namespace femgb {
@@ -285,51 +286,66 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, const uint8
     w.small = small + 3;
     if (!R || !b || !du || !dg || !dinv || !hn || !w.r || !w.z || !w.p || !w.q || !w.sc || !small)
         return FEM_ERR_NOMEM;
-    k_j2_prescribe<<<vec_grid(D), VB, 0, s>>>(u, u_bar, mask, D);
-    count_launch();
-    const double h = std::min(1.0 / g.ihx, std::min(1.0 / g.ihy, 1.0 / g.ihz));
-    double ref = -1.0;
-    int cg_total = 0;
-    for (int it = 0;; ++it) {
-        FEM_CUDA(cudaMemsetAsync(small, 0, sizeof(double) * 2, s));
-        unsigned long long *ny_dev = (unsigned long long *)&small[1];
-        if (int rc = residual_launch(g, mask, u, hist, R, hn, ny_dev, b, &small[0], s)) return rc;
-        double hv[2];
-        FEM_CUDA(cudaMemcpyAsync(hv, small, sizeof(hv), cudaMemcpyDeviceToHost, s));
-        FEM_CUDA(cudaStreamSynchronize(s));
-        const double nrm = std::sqrt(hv[0]);
-        if (!std::isfinite(nrm)) return (set_error("fem_j2_step: non-finite residual"), FEM_ERR_NONFINITE);
-        if (ref < 0) ref = std::max(nrm, mat->E * h * h * 1e-12);
-        if (nrm <= newton_rtol * ref) {
-            // converged: the returned states at this u become the history
-            FEM_CUDA(cudaMemcpyAsync(hist, hn, hb, cudaMemcpyDeviceToDevice, s));
+    struct Ops {
+        const Geo &g;
+        const uint8_t *mask;
+        const double *u_bar;
+        double *u, *hist, *R, *b, *du, *dg, *dinv, *hn, *small;
+        const dpcg::Buffers<double> &w;
+        double cg_rtol;
+        int cg_maxit;
+        size_t hb;
+        cudaStream_t s;
+
+        int prescribe()
+        {
+            k_j2_prescribe<<<vec_grid(g.dofs), VB, 0, s>>>(u, u_bar, mask, g.dofs);
+            count_launch();
+            FEM_CUDA(cudaGetLastError());
+            return FEM_OK;
+        }
+        int residual(double *nrm, int64_t *n_yield)
+        {
+            FEM_CUDA(cudaMemsetAsync(small, 0, sizeof(double) * 2, s));
+            unsigned long long *ny_dev = (unsigned long long *)&small[1];
+            if (int rc = residual_launch(g, mask, u, hist, R, hn, ny_dev, b, &small[0], s)) return rc;
+            double hv[2];
+            FEM_CUDA(cudaMemcpyAsync(hv, small, sizeof(hv), cudaMemcpyDeviceToHost, s));
             FEM_CUDA(cudaStreamSynchronize(s));
             unsigned long long nyv;
             memcpy(&nyv, &hv[1], sizeof(nyv));
-            if (newton_iters) *newton_iters = it;
-            if (cg_iters) *cg_iters = cg_total;
-            if (n_yield) *n_yield = (int64_t)nyv;
+            *nrm = std::sqrt(hv[0]);
+            *n_yield = (int64_t)nyv;
             return FEM_OK;
         }
-        if (it == newton_maxit) {
-            if (newton_iters) *newton_iters = it;
-            if (cg_iters) *cg_iters = cg_total;
-            return (set_error("fem_j2_step: Newton iteration limit reached"), FEM_ERR_NOT_CONVERGED);
+        int correction(int *cg_it)
+        {
+            // Jacobi diagonal of the tangent at u, then K du = -R by PCG, u += du
+            FEM_CUDA(cudaMemsetAsync(dg, 0, sizeof(double) * g.dofs, s));
+            k_j2_diag<<<cell_grid(g.ne), CB, 0, s>>>(g, u, hist, dg);
+            k_j2_dinv<<<vec_grid(g.dofs), VB, 0, s>>>(dg, mask, dinv, g.dofs);
+            count_launch(2);
+            FEM_CUDA(cudaMemsetAsync(du, 0, sizeof(double) * g.dofs, s));
+            auto apply = [&](const double *x, double *y, double *dot) -> int {
+                return apply_launch(g, mask, u, hist, x, y, dot, s);
+            };
+            const int rc = dpcg::solve<double>(s, g.dofs, apply, dinv, b, du, w, cg_rtol, cg_maxit, cg_it, nullptr,
+                                               "fem_j2_step");
+            if (rc != FEM_OK) return rc;
+            k_j2_axpy<<<vec_grid(g.dofs), VB, 0, s>>>(u, du, g.dofs);
+            count_launch();
+            FEM_CUDA(cudaGetLastError());
+            return FEM_OK;
         }
-        // Jacobi diagonal of the tangent at u, then K du = -R by PCG
-        FEM_CUDA(cudaMemsetAsync(dg, 0, sizeof(double) * D, s));
-        k_j2_diag<<<cell_grid(g.ne), CB, 0, s>>>(g, u, hist, dg);
-        k_j2_dinv<<<vec_grid(D), VB, 0, s>>>(dg, mask, dinv, D);
-        count_launch(2);
-        FEM_CUDA(cudaMemsetAsync(du, 0, sizeof(double) * D, s));
-        auto apply = [&](const double *x, double *y, double *dot) -> int {
-            return apply_launch(g, mask, u, hist, x, y, dot, s);
-        };
-        int cg_it = 0;
-        int rc = dpcg::solve<double>(s, D, apply, dinv, b, du, w, cg_rtol, cg_maxit, &cg_it, nullptr, "fem_j2_step");
-        cg_total += cg_it;
-        if (rc != FEM_OK) return rc;
-        k_j2_axpy<<<vec_grid(D), VB, 0, s>>>(u, du, D);
-        count_launch();
-    }
+        int accept()
+        {
+            FEM_CUDA(cudaMemcpyAsync(hist, hn, hb, cudaMemcpyDeviceToDevice, s));
+            FEM_CUDA(cudaStreamSynchronize(s));
+            return FEM_OK;
+        }
+        void fail(const char *what) { set_error(std::string("fem_j2_step: ") + what); }
+    };
+    Ops ops{g, mask, u_bar, u, hist, R, b, du, dg, dinv, hn, small, w, cg_rtol, cg_maxit, hb, s};
+    const double h = std::min(1.0 / g.ihx, std::min(1.0 / g.ihy, 1.0 / g.ihz));
+    return j2::newton_step(ops, mat->E, h, newton_rtol, newton_maxit, newton_iters, cg_iters, n_yield);
 }

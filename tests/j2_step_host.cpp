@@ -1,0 +1,210 @@
+// Host build of one J2 plasticity load step as the library runs it: the
+// Newton control (paper_2212_00964_gb300/csrc/j2_newton.h), the CG control
+// (dpcg_control.h) and the per-cell arithmetic (j2_core.cuh), with plain
+// loops standing in for the kernels (gather, per-cell work, scatter, the
+// element-tangent diagonal, the PCG vector updates with the library's
+// scalar layout).  Test code only.
+#include <stdint.h>
+
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "../paper_2212_00964_gb300/csrc/dpcg_control.h"
+#include "../paper_2212_00964_gb300/csrc/j2_core.cuh"
+#include "../paper_2212_00964_gb300/csrc/j2_newton.h"
+
+using namespace femgb;
+
+namespace {
+
+struct Box {
+    int nx, ny, nz;
+    double ihx, ihy, ihz, w;
+    int64_t ne, D;
+    j2::Consts c;
+};
+
+template <typename F>
+void for_cells(const Box &g, F f)
+{
+    for (int k = 0; k < g.nz; ++k)
+        for (int j = 0; j < g.ny; ++j)
+            for (int i = 0; i < g.nx; ++i) f(i, j, k, i + (int64_t)g.nx * (j + (int64_t)g.ny * k));
+}
+
+struct CpuPcg {
+    int64_t n;
+    std::function<void(const double *, double *, double *)> apply;
+    const double *dinv, *b;
+    double *u;
+    int maxit;
+    std::vector<double> r, z, p, q, sc;
+    std::string err;
+
+    int start(double *rz0, double *rr0, double *bb)
+    {
+        sc.assign(3 * ((size_t)maxit + 2), 0.0);
+        r.assign(n, 0.0), z.assign(n, 0.0), p.assign(n, 0.0), q.assign(n, 0.0);
+        apply(u, q.data(), nullptr);
+        double b2 = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            r[i] = b[i] - q[i];
+            z[i] = dinv[i] * r[i];
+            p[i] = z[i];
+            sc[0] += r[i] * z[i];
+            sc[2] += r[i] * r[i];
+            b2 += b[i] * b[i];
+        }
+        *rz0 = sc[0], *rr0 = sc[2], *bb = b2;
+        return 0;
+    }
+    int iterate(int k0, int k1)
+    {
+        for (int k = k0; k < k1; ++k) {
+            double *sck = &sc[3 * (size_t)k], *sck1 = &sc[3 * ((size_t)k + 1)];
+            apply(p.data(), q.data(), &sck[1]);
+            const double alpha = sck[1] > 0.0 ? sck[0] / sck[1] : 0.0;
+            for (int64_t i = 0; i < n; ++i) {
+                u[i] += alpha * p[i];
+                r[i] -= alpha * q[i];
+                z[i] = dinv[i] * r[i];
+                sck1[0] += r[i] * z[i];
+                sck1[2] += r[i] * r[i];
+            }
+            const double beta = sck[0] > 0.0 ? sck1[0] / sck[0] : 0.0;
+            for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        }
+        return 0;
+    }
+    int read(int k0, int k1, double *hs)
+    {
+        std::memcpy(hs, &sc[3 * (size_t)k0], sizeof(double) * 3 * (size_t)(k1 - k0 + 1));
+        return 0;
+    }
+    void fail(const char *what) { err = what; }
+};
+
+struct CpuStep {
+    Box g;
+    const uint8_t *mask;
+    const double *u_bar;
+    double *u, *hist;
+    double cg_rtol;
+    int cg_maxit;
+    std::vector<double> R, b, du, dg, dinv, hn;
+    std::string err;
+
+    int prescribe()
+    {
+        for (int64_t d = 0; d < g.D; ++d)
+            if (mask[d]) u[d] = u_bar[d];
+        return 0;
+    }
+    int residual(double *nrm, int64_t *n_yield)
+    {
+        R.assign(g.D, 0.0);
+        hn.assign(12 * 8 * (size_t)g.ne, 0.0);
+        int64_t ny = 0;
+        for_cells(g, [&](int i, int j, int k, int64_t e) {
+            double ue[24], Re[24];
+            for (int a = 0; a < 8; ++a)
+                for (int t = 0; t < 3; ++t) ue[3 * a + t] = u[3 * j2::cell_node(i, j, k, a, g.nx, g.ny) + t];
+            ny += j2::cell_residual<double>(g.c, g.ihx, g.ihy, g.ihz, g.w, ue, hist, hn.data(), g.ne, e, Re);
+            for (int a = 0; a < 8; ++a)
+                for (int t = 0; t < 3; ++t) R[3 * j2::cell_node(i, j, k, a, g.nx, g.ny) + t] += Re[3 * a + t];
+        });
+        b.assign(g.D, 0.0);
+        double s = 0;
+        for (int64_t d = 0; d < g.D; ++d) {
+            if (mask[d]) R[d] = 0.0;
+            b[d] = -R[d];
+            s += R[d] * R[d];
+        }
+        *nrm = std::sqrt(s);
+        *n_yield = ny;
+        return 0;
+    }
+    void apply(const double *x, double *y, double *dot)
+    {
+        for (int64_t d = 0; d < g.D; ++d) y[d] = 0.0;
+        for_cells(g, [&](int i, int j, int k, int64_t e) {
+            double ue[24], xe[24], ye[24];
+            for (int a = 0; a < 8; ++a)
+                for (int t = 0; t < 3; ++t) {
+                    const int64_t d = 3 * j2::cell_node(i, j, k, a, g.nx, g.ny) + t;
+                    ue[3 * a + t] = u[d];
+                    xe[3 * a + t] = mask[d] ? 0.0 : x[d];
+                }
+            j2::cell_jvp<double>(g.c, g.ihx, g.ihy, g.ihz, g.w, ue, xe, hist, g.ne, e, ye);
+            for (int a = 0; a < 8; ++a)
+                for (int t = 0; t < 3; ++t) y[3 * j2::cell_node(i, j, k, a, g.nx, g.ny) + t] += ye[3 * a + t];
+        });
+        double acc = 0;
+        for (int64_t d = 0; d < g.D; ++d) {
+            if (mask[d]) y[d] = x[d];
+            acc += x[d] * y[d];
+        }
+        if (dot) *dot += acc;
+    }
+    int correction(int *cg_it)
+    {
+        dg.assign(g.D, 0.0);
+        for_cells(g, [&](int i, int j, int k, int64_t e) {
+            double ue[24], xe[24], ye[24];
+            for (int a = 0; a < 8; ++a)
+                for (int t = 0; t < 3; ++t) ue[3 * a + t] = u[3 * j2::cell_node(i, j, k, a, g.nx, g.ny) + t];
+            for (int c = 0; c < 24; ++c) {
+                for (int t = 0; t < 24; ++t) xe[t] = t == c ? 1.0 : 0.0;
+                j2::cell_jvp<double>(g.c, g.ihx, g.ihy, g.ihz, g.w, ue, xe, hist, g.ne, e, ye);
+                dg[3 * j2::cell_node(i, j, k, c / 3, g.nx, g.ny) + c % 3] += ye[c];
+            }
+        });
+        dinv.assign(g.D, 0.0);
+        for (int64_t d = 0; d < g.D; ++d) dinv[d] = mask[d] ? 1.0 : (dg[d] != 0.0 ? 1.0 / dg[d] : 0.0);
+        du.assign(g.D, 0.0);
+        CpuPcg pcg{g.D, [&](const double *x, double *y, double *dot) { apply(x, y, dot); }, dinv.data(), b.data(),
+                   du.data(), cg_maxit};
+        const int rc = dpcg::control(pcg, cg_rtol, cg_maxit, cg_it, nullptr);
+        if (rc) {
+            err = pcg.err;
+            return rc;
+        }
+        for (int64_t d = 0; d < g.D; ++d) u[d] += du[d];
+        return 0;
+    }
+    int accept()
+    {
+        std::memcpy(hist, hn.data(), sizeof(double) * hn.size());
+        return 0;
+    }
+    void fail(const char *what) { err = what; }
+};
+
+thread_local std::string last_err;
+
+}  // namespace
+
+extern "C" {
+
+int host_j2_step(int nx, int ny, int nz, double lx, double ly, double lz, double E, double nu, double sy,
+                 const uint8_t *mask, const double *u_bar, double *u, double *hist, double newton_rtol,
+                 int newton_maxit, double cg_rtol, int cg_maxit, int *newton_iters, int *cg_iters, int64_t *n_yield)
+{
+    Box g;
+    g.nx = nx, g.ny = ny, g.nz = nz;
+    const double hx = lx / nx, hy = ly / ny, hz = lz / nz;
+    g.ihx = 1.0 / hx, g.ihy = 1.0 / hy, g.ihz = 1.0 / hz, g.w = hx * hy * hz / 8.0;
+    g.ne = (int64_t)nx * ny * nz;
+    g.D = 3 * (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+    g.c = j2::consts(E, nu, sy);
+    CpuStep ops{g, mask, u_bar, u, hist, cg_rtol, cg_maxit};
+    const double h = std::min(hx, std::min(hy, hz));
+    const int rc = j2::newton_step(ops, E, h, newton_rtol, newton_maxit, newton_iters, cg_iters, n_yield);
+    last_err = ops.err;
+    return rc;
+}
+
+const char *host_j2_step_error() { return last_err.c_str(); }
+}

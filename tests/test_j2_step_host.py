@@ -1,0 +1,119 @@
+"""CPU run of the library's J2 load step: the Newton control (j2_newton.h),
+the CG control (dpcg_control.h) and the per-cell arithmetic (j2_core.cuh)
+compiled for the host through tests/j2_step_host.cpp, with loops standing in
+for the kernels; against the oracle's load-stepped Newton with direct solves
+on the load / unload / reverse-yield path, and on a sheared box whose
+yielding is not uniform."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import plasticity as pl
+from paper_2212_00964_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(HERE, "j2_step_host.cpp")
+CSRC = os.path.join(ROOT, "paper_2212_00964_gb300", "csrc")
+HDRS = [os.path.join(CSRC, h) for h in ("j2_core.cuh", "j2_newton.h", "dpcg_control.h")]
+SO = os.path.join(ROOT, "paper_2212_00964_gb300", "_lib", "j2_step_host.so")
+
+
+@pytest.fixture(scope="module")
+def L():
+    os.makedirs(os.path.dirname(SO), exist_ok=True)
+    if not os.path.exists(SO) or os.path.getmtime(SO) < max(os.path.getmtime(f) for f in [SRC] + HDRS):
+        tmp = SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-Wall", SRC, "-o", tmp])
+        os.replace(tmp, SO)
+    lib = ctypes.CDLL(SO)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.host_j2_step.argtypes = [I, I, I, D, D, D, D, D, D, P, P, P, P, D, I, D, I, ctypes.POINTER(I),
+                                 ctypes.POINTER(I), ctypes.POINTER(ctypes.c_int64)]
+    lib.host_j2_step_error.restype = ctypes.c_char_p
+    return lib
+
+
+def p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def six(T):
+    return np.array([T[..., 0, 0], T[..., 1, 1], T[..., 2, 2], T[..., 1, 2], T[..., 0, 2], T[..., 0, 1]])
+
+
+def to_soa(hist):
+    eps, sig = hist
+    return np.ascontiguousarray(np.concatenate([six(eps).transpose(0, 2, 1), six(sig).transpose(0, 2, 1)]).reshape(-1))
+
+
+def run_path(L, dims, mat, mask, ubars, newton_maxit=30):
+    nx, ny, nz, lx, ly, lz = dims
+    D = 3 * (nx + 1) * (ny + 1) * (nz + 1)
+    u = np.zeros(D)
+    hist = np.zeros(12 * 8 * nx * ny * nz)
+    out = []
+    for ub in ubars:
+        ni, ci, nyd = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        rc = L.host_j2_step(nx, ny, nz, lx, ly, lz, mat.E, mat.nu, mat.sy, p(mask), p(np.ascontiguousarray(ub)),
+                            p(u), p(hist), 1e-12, newton_maxit, 1e-12, 20000, ctypes.byref(ni), ctypes.byref(ci),
+                            ctypes.byref(nyd))
+        out.append((rc, u.copy(), hist.copy(), ni.value, ci.value, nyd.value))
+        if rc:
+            break
+    return out
+
+
+def test_uniaxial_path_matches_oracle(L):
+    n = 3
+    mask, ubars, strains, (E, nu, sy) = inputs.j2_uniaxial(n=n)
+    mat = pl.Material(E, nu, sy)
+    om = oracle.mesh(n, n, n)
+    ref = pl.solve_path(om, mat, mask, ubars)
+    got = run_path(L, (n, n, n, 1.0, 1.0, 1.0), mat, mask, ubars)
+    for k, ((rc, u, h, ni, ci, nyd), (u_ref, hist_ref, ny_ref)) in enumerate(zip(got, ref)):
+        assert rc == 0, (k, L.host_j2_step_error())
+        assert np.abs(u - u_ref).max() <= 1e-10 * np.abs(u_ref).max()
+        assert np.abs(h - to_soa(hist_ref)).max() <= 1e-8 * sy
+        assert 1 <= ni <= 10
+
+
+def sheared_box():
+    """2x3x2 box: bottom clamped, top pushed down and sheared; yielding
+    spreads from the top corners (not uniform)."""
+    nx, ny, nz = 2, 3, 2
+    steps = [0.3e-2, 0.6e-2, 0.9e-2, 0.5e-2, 0.0]
+    ubars = []
+    mask = None
+    for s in steps:
+        mask, ub = inputs.dirichlet(nx, ny, nz, [("z0", 0, 0.0), ("z0", 1, 0.0), ("z0", 2, 0.0),
+                                                 ("z1", 0, s), ("z1", 2, -0.5 * s)])
+        ubars.append(ub)
+    return (nx, ny, nz, 1.0, 1.5, 1.0), mask, ubars
+
+
+def test_sheared_box_matches_oracle(L):
+    dims, mask, ubars = sheared_box()
+    mat = pl.Material(70e3, 0.3, 250.0)
+    om = oracle.mesh(*dims)
+    ref = pl.solve_path(om, mat, mask, ubars)
+    got = run_path(L, dims, mat, mask, ubars)
+    mixes = 0
+    for k, ((rc, u, h, ni, ci, nyd), (u_ref, hist_ref, ny_ref)) in enumerate(zip(got, ref)):
+        assert rc == 0, (k, L.host_j2_step_error())
+        assert np.abs(u - u_ref).max() <= 1e-9 * np.abs(u_ref).max()
+        assert np.abs(h - to_soa(hist_ref)).max() <= 1e-7 * 250.0
+        assert nyd == ny_ref
+        mixes += 0 < ny_ref < 8 * om.n_cells
+    assert mixes >= 1
+
+
+def test_newton_limit_leaves_the_history(L):
+    dims, mask, ubars = sheared_box()
+    got = run_path(L, dims, pl.Material(70e3, 0.3, 250.0), mask, ubars[2:3], newton_maxit=0)
+    rc, u, h, ni, ci, nyd = got[0]
+    assert rc == -3 and "limit" in L.host_j2_step_error().decode() and np.all(h == 0)
