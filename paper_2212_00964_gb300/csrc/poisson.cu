@@ -19,6 +19,7 @@
 
 #include "dev_pcg.cuh"
 #include "mesh.cuh"
+#include "poisson_control.h"
 #include "poisson_core.cuh"
 
 namespace femgb {
@@ -33,8 +34,6 @@ enum {
     WS_PTAB = 48, WS_PR, WS_PZ, WS_PP, WS_PQ, WS_PDINV, WS_PSC, WS_PRHS, WS_PSMALL,
     WS_PTAB32, WS_PMSMALL, WS_PR32, WS_PC32, WS_PQ64
 };
-constexpr int MAX_REFINE = 40;  // FP64 refinement rounds of the mixed solve
-constexpr double INNER_RTOL = 1e-4;  // FP32 CG tolerance per refinement round
 
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + PB - 1) / PB, 152 * 8)); }
 
@@ -182,50 +181,53 @@ int cg_solve(const Ctx &c, const T *tabA, const uint8_t *mask, const T *b, T *u,
     return dpcg::solve<T>(c.s, N, apply, dinv, b, u, w, rtol, maxit, iters, rel_res, "poisson CG");
 }
 
-// Mixed precision: FP64 residuals b - A u drive rounds of FP32 CG on the
-// correction (tolerance INNER_RTOL each), u += c, until ||b - A u|| <=
-// rtol ||b|| in FP64.  maxit bounds the FP32 CG iterations of all rounds.
+// Mixed precision (poisson::refine): FP64 residuals, FP32 CG on the correction.
 int solve_mixed(const Ctx &c, const double *tab64, const float *tab32, const uint8_t *mask, const double *b, double *u,
                 double rtol, int maxit, int *iters, double *rel_res)
 {
     const int64_t N = c.N;
-    double *q64 = (double *)c.m->ws.get(WS_PQ64, sizeof(double) * N);
-    float *r32 = (float *)c.m->ws.get(WS_PR32, sizeof(float) * N);
-    float *c32 = (float *)c.m->ws.get(WS_PC32, sizeof(float) * N);
-    double *acc = (double *)c.m->ws.get(WS_PMSMALL, sizeof(double) * 2);
-    if (!q64 || !r32 || !c32 || !acc) return FEM_ERR_NOMEM;
-    int total = 0;
-    double rel = 0.0;
-    int rc = FEM_ERR_NOT_CONVERGED;
-    for (int round = 0; round <= MAX_REFINE; ++round) {
-        FEM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * 2, c.s));
-        launch_op<double>(c, tab64, u, mask, poisson::OUT_ELIM, q64, nullptr);
-        k_pois_refine<<<grid_for(N), PB, 0, c.s>>>(b, q64, r32, N, acc);
-        count_launch();
-        FEM_CUDA(cudaGetLastError());
-        double h[2];
-        FEM_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, c.s));
-        FEM_CUDA(cudaStreamSynchronize(c.s));
-        if (!std::isfinite(h[0])) return (set_error("poisson mixed solve: non-finite residual"), FEM_ERR_NONFINITE);
-        const double bn = std::sqrt(h[1]) > 0 ? std::sqrt(h[1]) : 1.0;
-        rel = std::sqrt(h[0]) / bn;
-        if (rel <= rtol) {
-            rc = FEM_OK;
-            break;
+    struct Ops {
+        const Ctx &c;
+        const double *tab64;
+        const float *tab32;
+        const uint8_t *mask;
+        const double *b;
+        double *u, *q64, *acc;
+        float *r32, *c32;
+
+        int residual(double *rr, double *bb)
+        {
+            FEM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * 2, c.s));
+            launch_op<double>(c, tab64, u, mask, poisson::OUT_ELIM, q64, nullptr);
+            k_pois_refine<<<grid_for(c.N), PB, 0, c.s>>>(b, q64, r32, c.N, acc);
+            count_launch();
+            FEM_CUDA(cudaGetLastError());
+            double h[2];
+            FEM_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, c.s));
+            FEM_CUDA(cudaStreamSynchronize(c.s));
+            *rr = h[0];
+            *bb = h[1];
+            return FEM_OK;
         }
-        if (round == MAX_REFINE || total >= maxit) break;
-        FEM_CUDA(cudaMemsetAsync(c32, 0, sizeof(float) * N, c.s));
-        int it = 0;
-        const int inner = cg_solve<float>(c, tab32, mask, r32, c32, INNER_RTOL, maxit - total, &it, nullptr);
-        total += it;
-        if (inner != FEM_OK && inner != FEM_ERR_NOT_CONVERGED) return inner;
-        k_pois_correct<<<grid_for(N), PB, 0, c.s>>>(u, c32, N);
-        count_launch();
-    }
-    if (iters) *iters = total;
-    if (rel_res) *rel_res = rel;
-    if (rc != FEM_OK) set_error("poisson mixed solve: iteration limit reached");
-    return rc;
+        int inner(int maxit_left, int *it)
+        {
+            FEM_CUDA(cudaMemsetAsync(c32, 0, sizeof(float) * c.N, c.s));
+            return cg_solve<float>(c, tab32, mask, r32, c32, poisson::INNER_RTOL, maxit_left, it, nullptr);
+        }
+        int correct()
+        {
+            k_pois_correct<<<grid_for(c.N), PB, 0, c.s>>>(u, c32, c.N);
+            count_launch();
+            FEM_CUDA(cudaGetLastError());
+            return FEM_OK;
+        }
+        void fail(const char *what) { set_error(std::string("poisson mixed solve: ") + what); }
+    };
+    Ops ops{c, tab64, tab32, mask, b, u,
+            (double *)c.m->ws.get(WS_PQ64, sizeof(double) * N), (double *)c.m->ws.get(WS_PMSMALL, sizeof(double) * 2),
+            (float *)c.m->ws.get(WS_PR32, sizeof(float) * N), (float *)c.m->ws.get(WS_PC32, sizeof(float) * N)};
+    if (!ops.q64 || !ops.acc || !ops.r32 || !ops.c32) return FEM_ERR_NOMEM;
+    return poisson::refine(ops, rtol, maxit, iters, rel_res);
 }
 
 int check_mesh(fem_mesh_t m, const char *what)
@@ -282,41 +284,72 @@ int gradient_t(fem_mesh_t m, double alpha, const uint8_t *mask, const T *theta, 
         }
         return ::femgb::cg_solve<T>(c, tab, mk, bb, x, rt, mi, it, rr);
     };
-    // forward: A u = M theta (free rows), u = 0 on masked nodes
-    launch_op<T>(c, tab + poisson::TAB, theta, mask, mask ? poisson::OUT_ZERO : poisson::OUT_PLAIN, rhs, nullptr);
-    FEM_CUDA(cudaMemsetAsync(u, 0, sizeof(T) * N, s));
-    int it_f = 0, it_a = 0;
-    int rc = cg_solve(mask, rhs, u, rtol, maxit, &it_f, nullptr);
-    if (rc != FEM_OK) return rc;
-    // objective and adjoint right-hand side 2 (u - u_obs) on the observed free nodes
     double *small = (double *)m->ws.get(WS_PSMALL, sizeof(double) * 4);
     if (!small) return FEM_ERR_NOMEM;
-    FEM_CUDA(cudaMemsetAsync(small, 0, sizeof(double) * 4, s));
-    FEM_CUDA(cudaMemsetAsync(rhs, 0, sizeof(T) * N, s));
-    if (n_obs > 0) {
-        k_pois_obs<T><<<grid_for(n_obs), PB, 0, s>>>(u, obs, u_obs, n_obs, mask, N, rhs, &small[1], (int *)&small[2]);
-        count_launch();
-    }
-    double hJ[2];
-    FEM_CUDA(cudaMemcpyAsync(hJ, &small[1], sizeof(hJ), cudaMemcpyDeviceToHost, s));
-    FEM_CUDA(cudaStreamSynchronize(s));
-    int bad;
-    memcpy(&bad, &hJ[1], sizeof(int));
-    if (bad) return (set_error("fem_poisson_gradient: observation index outside [0, n_nodes)"), FEM_ERR_ARG);
-    // adjoint: A lambda = dJ/du (A symmetric), lambda = 0 on masked nodes
-    FEM_CUDA(cudaMemsetAsync(lam, 0, sizeof(T) * N, s));
-    rc = cg_solve(mask, rhs, lam, rtol, maxit, &it_a, nullptr);
-    if (rc != FEM_OK) return rc;
-    // dJ/dtheta = M^T lambda (M symmetric; lambda vanishes on masked nodes)
-    launch_op<T>(c, tab + poisson::TAB, lam, nullptr, poisson::OUT_PLAIN, grad, nullptr);
-    FEM_CUDA(cudaGetLastError());
-    FEM_CUDA(cudaStreamSynchronize(s));
-    if (J) *J = hJ[0];
-    if (iters) {
-        iters[0] = it_f;
-        iters[1] = it_a;
-    }
-    return FEM_OK;
+    struct Ops {
+        const Ctx &c;
+        decltype(cg_solve) &solve;
+        const T *tab, *theta, *u_obs;
+        const uint8_t *mask;
+        const int64_t *obs;
+        int64_t n_obs;
+        double rtol;
+        int maxit;
+        T *u, *lam, *grad, *rhs;
+        double *small;
+
+        int load()
+        {
+            // rhs = M theta (free rows), 0 on masked nodes
+            launch_op<T>(c, tab + poisson::TAB, theta, mask, mask ? poisson::OUT_ZERO : poisson::OUT_PLAIN, rhs,
+                         nullptr);
+            FEM_CUDA(cudaGetLastError());
+            return FEM_OK;
+        }
+        int solve_forward(int *it)
+        {
+            FEM_CUDA(cudaMemsetAsync(u, 0, sizeof(T) * c.N, c.s));
+            return solve(mask, rhs, u, rtol, maxit, it, nullptr);
+        }
+        int objective(double *J, bool *bad)
+        {
+            // J and the adjoint right-hand side 2 (u - u_obs) on the observed free nodes
+            FEM_CUDA(cudaMemsetAsync(small, 0, sizeof(double) * 4, c.s));
+            FEM_CUDA(cudaMemsetAsync(rhs, 0, sizeof(T) * c.N, c.s));
+            if (n_obs > 0) {
+                k_pois_obs<T><<<grid_for(n_obs), PB, 0, c.s>>>(u, obs, u_obs, n_obs, mask, c.N, rhs, &small[1],
+                                                               (int *)&small[2]);
+                count_launch();
+            }
+            double hJ[2];
+            FEM_CUDA(cudaMemcpyAsync(hJ, &small[1], sizeof(hJ), cudaMemcpyDeviceToHost, c.s));
+            FEM_CUDA(cudaStreamSynchronize(c.s));
+            int flag;
+            memcpy(&flag, &hJ[1], sizeof(int));
+            *J = hJ[0];
+            *bad = flag != 0;
+            return FEM_OK;
+        }
+        int solve_adjoint(int *it)
+        {
+            // A lambda = dJ/du (A symmetric), lambda = 0 on masked nodes
+            FEM_CUDA(cudaMemsetAsync(lam, 0, sizeof(T) * c.N, c.s));
+            return solve(mask, rhs, lam, rtol, maxit, it, nullptr);
+        }
+        int gradient()
+        {
+            // dJ/dtheta = M^T lambda (M symmetric; lambda vanishes on masked nodes)
+            launch_op<T>(c, tab + poisson::TAB, lam, nullptr, poisson::OUT_PLAIN, grad, nullptr);
+            FEM_CUDA(cudaGetLastError());
+            FEM_CUDA(cudaStreamSynchronize(c.s));
+            return FEM_OK;
+        }
+        void fail(const char *what) { set_error(std::string("fem_poisson_gradient: ") + what); }
+    };
+    Ops ops{c, cg_solve, tab, theta, u_obs, mask, obs, n_obs, rtol, maxit, u, lam, grad, rhs, small};
+    const int rc = poisson::objective_gradient(ops, J, iters);
+    static_assert((int)poisson::ST_ARG == (int)FEM_ERR_ARG, "argument status");
+    return rc;
 }
 
 }  // namespace

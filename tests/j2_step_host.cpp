@@ -14,6 +14,7 @@
 #include "../paper_2212_00964_gb300/csrc/dpcg_control.h"
 #include "../paper_2212_00964_gb300/csrc/j2_core.cuh"
 #include "../paper_2212_00964_gb300/csrc/j2_newton.h"
+#include "cpu_pcg.h"
 
 using namespace femgb;
 
@@ -33,58 +34,6 @@ void for_cells(const Box &g, F f)
         for (int j = 0; j < g.ny; ++j)
             for (int i = 0; i < g.nx; ++i) f(i, j, k, i + (int64_t)g.nx * (j + (int64_t)g.ny * k));
 }
-
-struct CpuPcg {
-    int64_t n;
-    std::function<void(const double *, double *, double *)> apply;
-    const double *dinv, *b;
-    double *u;
-    int maxit;
-    std::vector<double> r, z, p, q, sc;
-    std::string err;
-
-    int start(double *rz0, double *rr0, double *bb)
-    {
-        sc.assign(3 * ((size_t)maxit + 2), 0.0);
-        r.assign(n, 0.0), z.assign(n, 0.0), p.assign(n, 0.0), q.assign(n, 0.0);
-        apply(u, q.data(), nullptr);
-        double b2 = 0;
-        for (int64_t i = 0; i < n; ++i) {
-            r[i] = b[i] - q[i];
-            z[i] = dinv[i] * r[i];
-            p[i] = z[i];
-            sc[0] += r[i] * z[i];
-            sc[2] += r[i] * r[i];
-            b2 += b[i] * b[i];
-        }
-        *rz0 = sc[0], *rr0 = sc[2], *bb = b2;
-        return 0;
-    }
-    int iterate(int k0, int k1)
-    {
-        for (int k = k0; k < k1; ++k) {
-            double *sck = &sc[3 * (size_t)k], *sck1 = &sc[3 * ((size_t)k + 1)];
-            apply(p.data(), q.data(), &sck[1]);
-            const double alpha = sck[1] > 0.0 ? sck[0] / sck[1] : 0.0;
-            for (int64_t i = 0; i < n; ++i) {
-                u[i] += alpha * p[i];
-                r[i] -= alpha * q[i];
-                z[i] = dinv[i] * r[i];
-                sck1[0] += r[i] * z[i];
-                sck1[2] += r[i] * r[i];
-            }
-            const double beta = sck[0] > 0.0 ? sck1[0] / sck[0] : 0.0;
-            for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
-        }
-        return 0;
-    }
-    int read(int k0, int k1, double *hs)
-    {
-        std::memcpy(hs, &sc[3 * (size_t)k0], sizeof(double) * 3 * (size_t)(k1 - k0 + 1));
-        return 0;
-    }
-    void fail(const char *what) { err = what; }
-};
 
 struct CpuStep {
     Box g;
@@ -164,7 +113,7 @@ struct CpuStep {
         dinv.assign(g.D, 0.0);
         for (int64_t d = 0; d < g.D; ++d) dinv[d] = mask[d] ? 1.0 : (dg[d] != 0.0 ? 1.0 / dg[d] : 0.0);
         du.assign(g.D, 0.0);
-        CpuPcg pcg{g.D, [&](const double *x, double *y, double *dot) { apply(x, y, dot); }, dinv.data(), b.data(),
+        CpuPcg<double> pcg{g.D, [&](const double *x, double *y, double *dot) { apply(x, y, dot); }, dinv.data(), b.data(),
                    du.data(), cg_maxit};
         const int rc = dpcg::control(pcg, cg_rtol, cg_maxit, cg_it, nullptr);
         if (rc) {

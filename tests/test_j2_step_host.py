@@ -19,7 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "j2_step_host.cpp")
 CSRC = os.path.join(ROOT, "paper_2212_00964_gb300", "csrc")
-HDRS = [os.path.join(CSRC, h) for h in ("j2_core.cuh", "j2_newton.h", "dpcg_control.h")]
+HDRS = [os.path.join(CSRC, h) for h in ("j2_core.cuh", "j2_newton.h", "dpcg_control.h")] + \
+    [os.path.join(HERE, "cpu_pcg.h")]
 SO = os.path.join(ROOT, "paper_2212_00964_gb300", "_lib", "j2_step_host.so")
 
 
