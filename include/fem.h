@@ -214,6 +214,15 @@ int fem_poisson_gradient(fem_mesh_t m, int precision, double alpha, const uint8_
                          double rtol, int maxit, void *u, void *lambda, void *grad, double *J,
                          int *iters, void *stream);
 
+/* Vector-Jacobian product of the map theta -> u(theta) of fem_poisson_solve
+ * with b = M theta: lambda solves A lambda = dJdu on the free nodes (lambda =
+ * 0 on masked nodes, whatever dJdu holds there) and grad = M lambda, so
+ * grad = (du/dtheta)^T dJdu.  dJdu, lambda, grad: [n_nodes].  Solve as
+ * fem_poisson_solve; *iters (host, may be NULL): CG iterations.
+ * Synchronises the stream. */
+int fem_poisson_adjoint(fem_mesh_t m, int precision, double alpha, const uint8_t *mask, const void *dJdu,
+                        double rtol, int maxit, void *lambda, void *grad, int *iters, void *stream);
+
 /* ------------------------------------------------ perfect J2 plasticity -- */
 /* Small-strain perfect J2 plasticity (Sec. 2.3, Eqs. (14)-(15)): the stress
  * of load step k is the radial return of the elastic trial stress

@@ -1,4 +1,5 @@
-"""torch.autograd.Function around fem_solve / fem_adjoint.
+"""torch.autograd.Function around fem_solve / fem_adjoint, and around the
+scalar Poisson solve of the full-field inference example (Sec. 3.1).
 
 Forward: theta (per-cell parameter) -> u*(theta), the converged state of the
 load-stepped Newton solve.  Only u* is saved (the checkpoint); no Newton or CG
@@ -52,3 +53,41 @@ class FemSolve:
 
     def __call__(self, theta):
         return _SolveFn.apply(theta, self)
+
+
+class _PoissonFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, theta, solver):
+        ctx.solver = solver
+        return solver.forward_solve(theta.detach())
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        g = ctx.solver.adjoint(grad_u.contiguous().to(ctx.solver.dtype))
+        return g, None
+
+
+class PoissonSolve:
+    """Differentiable theta -> u(theta) of the Poisson problem: A u = M theta
+    on the free nodes, u = 0 on masked ones.  Backward: fem_poisson_adjoint
+    (A lambda = dJ/du, dJ/dtheta = M lambda), so any torch objective of u
+    gets its gradient by the adjoint method, as in the paper's PDE-CO loop."""
+
+    def __init__(self, mesh, alpha=1.0, mask=None, rtol=1e-10, maxit=10000, mixed=False, dtype=torch.float64):
+        self.mesh, self.alpha, self.mask = mesh, float(alpha), mask
+        self.rtol, self.maxit, self.mixed, self.dtype = rtol, maxit, mixed, dtype
+
+    def forward_solve(self, theta):
+        th = theta.to(self.dtype).contiguous()
+        b = F.fem_poisson_apply(self.mesh, th, self.alpha, F.FEM_POISSON_MASS, self.mask)
+        u, _, _ = F.fem_poisson_solve(self.mesh, b, self.alpha, self.mask, rtol=self.rtol, maxit=self.maxit,
+                                      mixed=self.mixed)
+        return u
+
+    def adjoint(self, dJdu):
+        g, _, _ = F.fem_poisson_adjoint(self.mesh, dJdu, self.alpha, self.mask, rtol=self.rtol, maxit=self.maxit,
+                                        mixed=self.mixed)
+        return g
+
+    def __call__(self, theta):
+        return _PoissonFn.apply(theta, self)

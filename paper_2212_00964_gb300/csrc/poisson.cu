@@ -108,6 +108,15 @@ __global__ void k_pois_correct(double *__restrict__ u, const float *__restrict__
         u[n] += (double)c[n];
 }
 
+// y = x on free nodes, 0 on masked ones
+template <typename T>
+__global__ void k_pois_free_copy(const T *__restrict__ x, const uint8_t *__restrict__ mask, T *__restrict__ y,
+                                 int64_t N)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+        y[n] = (mask && mask[n]) ? (T)0 : x[n];
+}
+
 // Objective of Eq. (26) and the adjoint right-hand side:
 // J += (u[o] - u_obs[i])^2, rhs[o] += 2 (u[o] - u_obs[i]) on free nodes.
 // An observation index outside [0, N) sets *bad and is skipped.
@@ -352,11 +361,62 @@ int gradient_t(fem_mesh_t m, double alpha, const uint8_t *mask, const T *theta, 
     return rc;
 }
 
+// Vector-Jacobian product of theta -> u(theta): A lambda = dJ/du on the free
+// nodes (lambda = 0 on masked ones), grad = M lambda.
+template <typename T>
+int adjoint_t(fem_mesh_t m, double alpha, const uint8_t *mask, const T *dJdu, double rtol, int maxit, T *lam, T *grad,
+              int *iters, cudaStream_t s, bool mixed)
+{
+    Ctx c{m, m->n_nodes, s};
+    const int64_t N = c.N;
+    const T *tab = make_tables<T>(c, alpha);
+    T *rhs = (T *)m->ws.get(WS_PRHS, sizeof(T) * N);
+    if (!tab || !rhs) return FEM_ERR_NOMEM;
+    k_pois_free_copy<T><<<grid_for(N), PB, 0, s>>>(dJdu, mask, rhs, N);
+    count_launch();
+    FEM_CUDA(cudaMemsetAsync(lam, 0, sizeof(T) * N, s));
+    int rc;
+    if constexpr (std::is_same<T, double>::value) {
+        if (mixed) {
+            const float *tab32 = make_tables<float>(c, alpha, WS_PTAB32);
+            if (!tab32) return FEM_ERR_NOMEM;
+            rc = solve_mixed(c, tab, tab32, mask, rhs, lam, rtol, maxit, iters, nullptr);
+        } else {
+            rc = cg_solve<T>(c, tab, mask, rhs, lam, rtol, maxit, iters, nullptr);
+        }
+    } else {
+        rc = cg_solve<T>(c, tab, mask, rhs, lam, rtol, maxit, iters, nullptr);
+    }
+    if (rc != FEM_OK) return rc;
+    launch_op<T>(c, tab + poisson::TAB, lam, nullptr, poisson::OUT_PLAIN, grad, nullptr);
+    FEM_CUDA(cudaGetLastError());
+    FEM_CUDA(cudaStreamSynchronize(s));
+    return FEM_OK;
+}
+
 }  // namespace
 
 }  // namespace femgb
 
 using namespace femgb;
+
+extern "C" int fem_poisson_adjoint(fem_mesh_t m, int precision, double alpha, const uint8_t *mask, const void *dJdu,
+                                   double rtol, int maxit, void *lambda, void *grad, int *iters, void *stream)
+{
+    if (int rc = check_mesh(m, "fem_poisson_adjoint")) return rc;
+    if (!dJdu || !lambda || !grad) return (set_error("fem_poisson_adjoint: NULL argument"), FEM_ERR_ARG);
+    if (!(alpha > 0) || !(rtol > 0) || maxit < 0 || maxit > MAX_ITERS)
+        return (set_error("fem_poisson_adjoint: alpha > 0, rtol > 0 and 0 <= maxit <= 1e6 required"), FEM_ERR_ARG);
+    std::lock_guard<std::mutex> lk(m->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == FEM_FP64 || precision == FEM_MIXED)
+        return adjoint_t<double>(m, alpha, mask, (const double *)dJdu, rtol, maxit, (double *)lambda, (double *)grad,
+                                 iters, s, precision == FEM_MIXED);
+    if (precision == FEM_FP32)
+        return adjoint_t<float>(m, alpha, mask, (const float *)dJdu, rtol, maxit, (float *)lambda, (float *)grad,
+                                iters, s, false);
+    return (set_error("fem_poisson_adjoint: precision must be FEM_FP64, FEM_FP32 or FEM_MIXED"), FEM_ERR_ARG);
+}
 
 extern "C" int fem_poisson_apply(fem_mesh_t m, int precision, double alpha, int op, const uint8_t *mask,
                                  const void *x, void *y, void *stream)

@@ -105,6 +105,7 @@ def lib():
                               ctypes.POINTER(I64), P]
     L.fem_density_filter.argtypes = [P, D, P, P, P]
     L.fem_mma_step.argtypes = [P, P, D, P, P, D, D, I, P, P, P, P, P, ctypes.POINTER(D), P]
+    L.fem_poisson_adjoint.argtypes = [P, I, D, P, P, D, I, P, P, ctypes.POINTER(I), P]
     L.fem_poisson_apply.argtypes = [P, I, D, I, P, P, P, P]
     L.fem_poisson_solve.argtypes = [P, I, D, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     L.fem_poisson_gradient.argtypes = [P, I, D, P, P, P, P, I64, D, I, P, P, P, ctypes.POINTER(D),
@@ -347,6 +348,20 @@ def fem_poisson_solve(m: Mesh, b, alpha=1.0, mask=None, u=None, rtol=1e-10, maxi
     if check:
         _check(rc, "fem_poisson_solve")
     return u, it.value, res.value
+
+
+def fem_poisson_adjoint(m: Mesh, dJdu, alpha=1.0, mask=None, rtol=1e-10, maxit=10000, stream=None, mixed=False):
+    """(du/dtheta)^T dJdu for theta -> u(theta) (A u = M theta): returns (grad, lambda, iterations)."""
+    dt = dJdu.dtype
+    lam = torch.empty_like(dJdu)
+    grad = torch.empty_like(dJdu)
+    it = ctypes.c_int(0)
+    _check(lib().fem_poisson_adjoint(m.handle, _poisson_prec(dt, mixed), ctypes.c_double(alpha),
+                                     _ptr(mask, torch.uint8, m.n_nodes, "mask"), _ptr(dJdu, dt, m.n_nodes, "dJdu"),
+                                     ctypes.c_double(rtol), int(maxit), _ptr(lam, dt, m.n_nodes, "lambda"),
+                                     _ptr(grad, dt, m.n_nodes, "grad"), ctypes.byref(it), _stream(stream)),
+           "fem_poisson_adjoint")
+    return grad, lam, it.value
 
 
 def fem_poisson_gradient(m: Mesh, theta, obs, u_obs, alpha=1.0, mask=None, rtol=1e-10, maxit=10000,

@@ -48,6 +48,7 @@ def test_host_only_calls():
     assert L.fem_poisson_solve(None, 0, 1.0, None, None, None, 1e-8, 10, None, None, None) == fem.FEM_ERR_ARG
     assert L.fem_poisson_gradient(None, 0, 1.0, None, None, None, None, 0, 1e-8, 10, None, None, None, None,
                                   None, None) == fem.FEM_ERR_ARG
+    assert L.fem_poisson_adjoint(None, 0, 1.0, None, None, 1e-8, 10, None, None, None, None) == fem.FEM_ERR_ARG
     assert "NULL mesh" in L.fem_last_error().decode()
     jm = fem.j2_material(70e3, 0.3, 250.0)
     assert L.fem_j2_residual(None, ctypes.byref(jm), None, None, None, None, None, None, None) == fem.FEM_ERR_ARG

@@ -149,6 +149,29 @@ def test_inference_loop_with_gpu_gradient():
     assert 0.06 <= err <= 0.24
 
 
+@pytest.mark.parametrize("mixed", [False, True])
+def test_autograd_solve_matches_the_adjoint_gradient(mixed):
+    """torch autograd through PoissonSolve (forward: mass + CG; backward:
+    fem_poisson_adjoint) gives the oracle's gradient of the objective of
+    Eq. (26) written as plain torch ops on u."""
+    from paper_2212_00964_gb300.autograd import PoissonSolve
+    w = inputs.poisson_inference(12, 10, 4, 1.0, 1.0, 0.2, n_obs=30, seed=6)
+    F = fem()
+    m = F.fem_mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)
+    om, prob = op.from_workload(w)
+    rng = np.random.default_rng(10)
+    theta = rng.standard_normal(om.n_nodes)
+    u_obs = 0.01 * rng.standard_normal(w.obs.size)
+    J_ref, g_ref, _, _ = prob.gradient(theta, w.obs, u_obs)
+    solve = PoissonSolve(m, w.alpha, dev(w.mask), rtol=1e-12, mixed=mixed)
+    th = dev(theta).requires_grad_(True)
+    u = solve(th)
+    J = ((u[dev(w.obs)] - dev(u_obs)) ** 2).sum()
+    J.backward()
+    assert abs(float(J) - J_ref) <= 1e-9 * J_ref
+    assert rel_l2(host(th.grad), g_ref) <= 1e-8
+
+
 def test_bad_observation_index_is_an_argument_error():
     w = inputs.poisson_inference(4, 4, 3, 1.0, 1.0, 0.2, n_obs=6, seed=3)
     F = fem()
