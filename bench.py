@@ -434,7 +434,7 @@ def next_suite(F, inputs, torch):
     guarded("poisson_50x50x10", lambda: poisson(50, 50, 10))
     guarded("poisson_256x256x64", lambda: poisson(256, 256, 64))
 
-    def j2_path():
+    def j2_path(mixed):
         n = 16
         mask_h, ubars, strains, (E, nu, sy) = inputs.j2_uniaxial(n=n)
         m = F.fem_mesh(n, n, n)
@@ -445,13 +445,14 @@ def next_suite(F, inputs, torch):
         hist = F.j2_history(m)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        its = [F.fem_j2_step(m, mat, mask, b, u, hist) for b in ub]
+        its = [F.fem_j2_step(m, mat, mask, b, u, hist, mixed=mixed) for b in ub]
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
         return {"dofs": m.n_dofs, "steps": len(ub), "path_s": t,
                 "newton_iters": sum(i["newton_iters"] for i in its), "cg_iters": sum(i["cg_iters"] for i in its)}
 
-    guarded("j2_16cube_path", j2_path)
+    guarded("j2_16cube_path_fp64", lambda: j2_path(False))
+    guarded("j2_16cube_path_mixed", lambda: j2_path(True))
 
     def topopt_iter():
         w = inputs.c2()

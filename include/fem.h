@@ -228,7 +228,7 @@ int fem_poisson_adjoint(fem_mesh_t m, int precision, double alpha, const uint8_t
  * of load step k is the radial return of the elastic trial stress
  * sigma^{k-1} + lam tr(d eps) I + 2 mu d eps, d eps = sym(grad u^k) - eps^{k-1},
  * onto the von Mises surface of radius sigma_y.  Lame parameters from
- * (E, nu) as for FEM_LINEAR.  FP64 only.  DOF layout and mask as above
+ * (E, nu) as for FEM_LINEAR.  FP64 arrays.  DOF layout and mask as above
  * (mask[d] != 0: u_d prescribed; rows and columns eliminated).
  * History: double hist[12 * 8 * n_cells], structure of arrays
  * hist[(comp * 8 + q) * n_cells + e]: comp 0..5 the total strain eps, 6..11
@@ -258,14 +258,17 @@ int fem_j2_tangent_apply(fem_mesh_t m, const fem_j2_material *mat, const uint8_t
  * with Jacobi-PCG on the consistent tangent (tolerance cg_rtol, at most
  * cg_maxit <= 1e6 iterations per Newton step) until ||r|| <= newton_rtol *
  * max(||r|| of the first iteration, E h^2 1e-12), h the smallest cell edge;
- * the free DOFs of u start from their values on entry.  On success hist
- * becomes (eps^k, sigma^k) at the converged u.  newton_iters, cg_iters,
+ * the free DOFs of u start from their values on entry.  precision FEM_FP64,
+ * or FEM_MIXED: the tangent apply, the CG vectors and the correction in FP32
+ * (the residual, history, diagonal and u stay FP64; an FP32 correction is
+ * an inexact Newton step, so cg_rtol of about 1e-4 suits it).  On success
+ * hist becomes (eps^k, sigma^k) at the converged u.  newton_iters, cg_iters,
  * n_yield (host, may be NULL): Newton iterations, total CG iterations,
  * yielding Gauss points.  FEM_ERR_NOT_CONVERGED after newton_maxit (hist
  * unchanged).  Synchronises the stream. */
-int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, const uint8_t *mask, const double *u_bar, double *u,
-                double *hist, double newton_rtol, int newton_maxit, double cg_rtol, int cg_maxit,
-                int *newton_iters, int *cg_iters, int64_t *n_yield, void *stream);
+int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precision, const uint8_t *mask,
+                const double *u_bar, double *u, double *hist, double newton_rtol, int newton_maxit,
+                double cg_rtol, int cg_maxit, int *newton_iters, int *cg_iters, int64_t *n_yield, void *stream);
 
 /* ------------------------------------------------ topology optimisation -- */
 /* The data-parallel steps of the compliance-minimisation loop (Sec. 3.2)

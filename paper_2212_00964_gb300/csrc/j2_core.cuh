@@ -149,13 +149,14 @@ J2_HD void flux(const T *S, int q, T ihx, T ihy, T ihz, T w, T *out)
 }
 
 // History of Gauss point q of cell e in the structure-of-arrays layout
-// hist[(comp * 8 + q) * n_cells + e], comp 0..5 eps, 6..11 sigma.
-template <typename T>
-J2_HD void load_hist(const T *hist, int64_t n_cells, int64_t e, int q, T *eps, T *sig)
+// hist[(comp * 8 + q) * n_cells + e], comp 0..5 eps, 6..11 sigma; stored in
+// S, computed in T.
+template <typename T, typename S>
+J2_HD void load_hist(const S *hist, int64_t n_cells, int64_t e, int q, T *eps, T *sig)
 {
     for (int t = 0; t < 6; ++t) {
-        eps[t] = hist[((int64_t)t * 8 + q) * n_cells + e];
-        sig[t] = hist[((int64_t)(t + 6) * 8 + q) * n_cells + e];
+        eps[t] = (T)hist[((int64_t)t * 8 + q) * n_cells + e];
+        sig[t] = (T)hist[((int64_t)(t + 6) * 8 + q) * n_cells + e];
     }
 }
 
@@ -188,9 +189,10 @@ J2_HD int cell_residual(const Consts &c, T ihx, T ihy, T ihz, T w, const T *ue, 
     return n_yield;
 }
 
-// Element tangent applied to xe[24] (the JVP of the element residual).
-template <typename T>
-J2_HD void cell_jvp(const Consts &c, T ihx, T ihy, T ihz, T w, const T *ue, const T *xe, const T *hist,
+// Element tangent applied to xe[24] (the JVP of the element residual),
+// computed in T from a history stored in S.
+template <typename T, typename S = T>
+J2_HD void cell_jvp(const Consts &c, T ihx, T ihy, T ihz, T w, const T *ue, const T *xe, const S *hist,
                     int64_t n_cells, int64_t e, T *ye)
 {
     for (int t = 0; t < 24; ++t) ye[t] = (T)0;

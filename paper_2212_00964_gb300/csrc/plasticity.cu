@@ -1,7 +1,8 @@
 // plasticity.cu -- perfect J2 plasticity (Sec. 2.3, Eqs. (14)-(15)) on the
 // GPU: the residual with its Gauss-point history, the consistent tangent
 // (matrix-free), its Jacobi diagonal, and one load step of Newton with
-// device-scalar PCG (dev_pcg.cuh).  FP64 throughout.
+// device-scalar PCG (dev_pcg.cuh).  Residual, history and diagonal in FP64;
+// the tangent and CG in FP64, or in FP32 in the mixed mode.
 //
 // One thread per cell: it gathers the 24 nodal values, runs the per-cell
 // arithmetic of j2_core.cuh (8 Gauss points, return map, flux) and scatters
@@ -27,6 +28,8 @@ constexpr int VB = 256;  // threads per block of the vector kernels
 constexpr int MAX_ITERS = 1000000;
 
 enum { WS_JR = 64, WS_JB, WS_JDU, WS_JD, WS_JDINV, WS_JHN, WS_JCR, WS_JCZ, WS_JCP, WS_JCQ, WS_JSC, WS_JSMALL };
+// FP32 buffers of the mixed-precision correction
+enum { WS_JB32 = 88, WS_JDU32, WS_JDINV32, WS_JCR32, WS_JCZ32, WS_JCP32, WS_JCQ32 };
 
 struct Geo {
     int nx, ny, nz;
@@ -89,24 +92,25 @@ __global__ void __launch_bounds__(CB) k_j2_residual(Geo g, const double *__restr
     if (threadIdx.x == 0 && n_yield) atomicAdd(n_yield, (unsigned long long)s);
 }
 
-// y += sum_e K_e(u) x_e with masked entries of x removed
+// y += sum_e K_e(u) x_e with masked entries of x removed, computed in T
+// (double, or float inside the mixed-precision CG) from the FP64 state
+template <typename T>
 __global__ void __launch_bounds__(CB) k_j2_apply(Geo g, const double *__restrict__ u, const double *__restrict__ hist,
-                                                const double *__restrict__ x, const uint8_t *__restrict__ mask,
-                                                double *y)
+                                                const T *__restrict__ x, const uint8_t *__restrict__ mask, T *y)
 {
     for (int64_t e = blockIdx.x * (int64_t)CB + threadIdx.x; e < g.ne; e += (int64_t)gridDim.x * CB) {
         int i, j, k;
         cell_ijk(g, e, i, j, k);
-        double ue[24], xe[24], ye[24];
+        T ue[24], xe[24], ye[24];
         for (int a = 0; a < 8; ++a) {
             const int64_t n = j2::cell_node(i, j, k, a, g.nx, g.ny);
             for (int t = 0; t < 3; ++t) {
                 const int64_t d = 3 * n + t;
-                ue[3 * a + t] = u[d];
-                xe[3 * a + t] = (mask && mask[d]) ? 0.0 : x[d];
+                ue[3 * a + t] = (T)u[d];
+                xe[3 * a + t] = (mask && mask[d]) ? (T)0 : x[d];
             }
         }
-        j2::cell_jvp<double>(g.c, g.ihx, g.ihy, g.ihz, g.w, ue, xe, hist, g.ne, e, ye);
+        j2::cell_jvp<T, double>(g.c, (T)g.ihx, (T)g.ihy, (T)g.ihz, (T)g.w, ue, xe, hist, g.ne, e, ye);
         for (int a = 0; a < 8; ++a) {
             const int64_t n = j2::cell_node(i, j, k, a, g.nx, g.ny);
             for (int t = 0; t < 3; ++t) atomicAdd(&y[3 * n + t], ye[3 * a + t]);
@@ -136,14 +140,15 @@ __global__ void __launch_bounds__(CB) k_j2_diag(Geo g, const double *__restrict_
 }
 
 // y_c = x_c on masked DOFs; *dot += (x, y) (dot may be null)
-__global__ void __launch_bounds__(VB) k_j2_fix_dot(const double *__restrict__ x, const uint8_t *__restrict__ mask,
-                                                  double *__restrict__ y, int64_t D, double *dot)
+template <typename T>
+__global__ void __launch_bounds__(VB) k_j2_fix_dot(const T *__restrict__ x, const uint8_t *__restrict__ mask,
+                                                  T *__restrict__ y, int64_t D, double *dot)
 {
     __shared__ double sh[VB / 32];
     double acc = 0;
     for (int64_t d = blockIdx.x * (int64_t)VB + threadIdx.x; d < D; d += (int64_t)gridDim.x * VB) {
         if (mask && mask[d]) y[d] = x[d];
-        acc += x[d] * y[d];
+        acc += (double)x[d] * (double)y[d];
     }
     if (dot) {
         acc = block_sum<double, VB>(acc, sh);
@@ -168,11 +173,19 @@ __global__ void __launch_bounds__(VB) k_j2_mask_norm(double *__restrict__ R, con
     if (threadIdx.x == 0) atomicAdd(nrm2, acc);
 }
 
-__global__ void k_j2_dinv(const double *__restrict__ d, const uint8_t *__restrict__ mask, double *__restrict__ dinv,
+template <typename T>
+__global__ void k_j2_dinv(const double *__restrict__ d, const uint8_t *__restrict__ mask, T *__restrict__ dinv,
                           int64_t D)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < D; i += (int64_t)gridDim.x * blockDim.x)
-        dinv[i] = (mask && mask[i]) ? 1.0 : (d[i] != 0.0 ? 1.0 / d[i] : 0.0);
+        dinv[i] = (T)((mask && mask[i]) ? 1.0 : (d[i] != 0.0 ? 1.0 / d[i] : 0.0));
+}
+
+// b32 = (float) b
+__global__ void k_j2_to_f32(const double *__restrict__ b, float *__restrict__ b32, int64_t D)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < D; i += (int64_t)gridDim.x * blockDim.x)
+        b32[i] = (float)b[i];
 }
 
 // u_c = u_bar_c on masked DOFs
@@ -183,10 +196,11 @@ __global__ void k_j2_prescribe(double *__restrict__ u, const double *__restrict_
         if (mask[i]) u[i] = ubar[i];
 }
 
-__global__ void k_j2_axpy(double *__restrict__ u, const double *__restrict__ du, int64_t D)
+template <typename T>
+__global__ void k_j2_axpy(double *__restrict__ u, const T *__restrict__ du, int64_t D)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < D; i += (int64_t)gridDim.x * blockDim.x)
-        u[i] += du[i];
+        u[i] += (double)du[i];
 }
 
 int residual_launch(const Geo &g, const uint8_t *mask, const double *u, const double *hist, double *R,
@@ -200,12 +214,13 @@ int residual_launch(const Geo &g, const uint8_t *mask, const double *u, const do
     return FEM_OK;
 }
 
-int apply_launch(const Geo &g, const uint8_t *mask, const double *u, const double *hist, const double *x, double *y,
-                 double *dot, cudaStream_t s)
+template <typename T>
+int apply_launch(const Geo &g, const uint8_t *mask, const double *u, const double *hist, const T *x, T *y, double *dot,
+                 cudaStream_t s)
 {
-    FEM_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * g.dofs, s));
-    k_j2_apply<<<cell_grid(g.ne), CB, 0, s>>>(g, u, hist, x, mask, y);
-    k_j2_fix_dot<<<vec_grid(g.dofs), VB, 0, s>>>(x, mask, y, g.dofs, dot);
+    FEM_CUDA(cudaMemsetAsync(y, 0, sizeof(T) * g.dofs, s));
+    k_j2_apply<T><<<cell_grid(g.ne), CB, 0, s>>>(g, u, hist, x, mask, y);
+    k_j2_fix_dot<T><<<vec_grid(g.dofs), VB, 0, s>>>(x, mask, y, g.dofs, dot);
     count_launch(2);
     FEM_CUDA(cudaGetLastError());
     return FEM_OK;
@@ -254,14 +269,18 @@ extern "C" int fem_j2_tangent_apply(fem_mesh_t m, const fem_j2_material *mat, co
     if (!u || !hist || !x || !y || x == y)
         return (set_error("fem_j2_tangent_apply: NULL argument or x aliases y"), FEM_ERR_ARG);
     std::lock_guard<std::mutex> lk(m->mu);
-    return apply_launch(geo(m, mat), mask, u, hist, x, y, nullptr, (cudaStream_t)stream);
+    return apply_launch<double>(geo(m, mat), mask, u, hist, x, y, nullptr, (cudaStream_t)stream);
 }
 
-extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, const uint8_t *mask, const double *u_bar,
-                           double *u, double *hist, double newton_rtol, int newton_maxit, double cg_rtol, int cg_maxit,
-                           int *newton_iters, int *cg_iters, int64_t *n_yield, void *stream)
+extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precision, const uint8_t *mask,
+                           const double *u_bar, double *u, double *hist, double newton_rtol, int newton_maxit,
+                           double cg_rtol, int cg_maxit, int *newton_iters, int *cg_iters, int64_t *n_yield,
+                           void *stream)
 {
     if (int rc = check_args(m, mat, "fem_j2_step")) return rc;
+    if (precision != FEM_FP64 && precision != FEM_MIXED)
+        return (set_error("fem_j2_step: precision must be FEM_FP64 or FEM_MIXED"), FEM_ERR_ARG);
+    const bool mixed = precision == FEM_MIXED;
     if (!mask || !u_bar || !u || !hist) return (set_error("fem_j2_step: NULL argument"), FEM_ERR_ARG);
     if (!(newton_rtol > 0) || newton_maxit < 0 || !(cg_rtol > 0) || cg_maxit < 0 || cg_maxit > MAX_ITERS)
         return (set_error("fem_j2_step: tolerances > 0, 0 <= maxit (CG <= 1e6) required"), FEM_ERR_ARG);
@@ -286,12 +305,29 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, const uint8
     w.small = small + 3;
     if (!R || !b || !du || !dg || !dinv || !hn || !w.r || !w.z || !w.p || !w.q || !w.sc || !small)
         return FEM_ERR_NOMEM;
+    dpcg::Buffers<float> w32{};
+    float *b32 = nullptr, *du32 = nullptr, *dinv32 = nullptr;
+    if (mixed) {
+        b32 = (float *)m->ws.get(WS_JB32, sizeof(float) * D);
+        du32 = (float *)m->ws.get(WS_JDU32, sizeof(float) * D);
+        dinv32 = (float *)m->ws.get(WS_JDINV32, sizeof(float) * D);
+        w32.r = (float *)m->ws.get(WS_JCR32, sizeof(float) * D);
+        w32.z = (float *)m->ws.get(WS_JCZ32, sizeof(float) * D);
+        w32.p = (float *)m->ws.get(WS_JCP32, sizeof(float) * D);
+        w32.q = (float *)m->ws.get(WS_JCQ32, sizeof(float) * D);
+        w32.sc = w.sc;
+        w32.small = w.small;
+        if (!b32 || !du32 || !dinv32 || !w32.r || !w32.z || !w32.p || !w32.q) return FEM_ERR_NOMEM;
+    }
     struct Ops {
         const Geo &g;
         const uint8_t *mask;
         const double *u_bar;
         double *u, *hist, *R, *b, *du, *dg, *dinv, *hn, *small;
         const dpcg::Buffers<double> &w;
+        const dpcg::Buffers<float> &w32;
+        float *b32, *du32, *dinv32;
+        bool mixed;
         double cg_rtol;
         int cg_maxit;
         size_t hb;
@@ -320,19 +356,36 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, const uint8
         }
         int correction(int *cg_it)
         {
-            // Jacobi diagonal of the tangent at u, then K du = -R by PCG, u += du
+            // Jacobi diagonal of the tangent at u, then K du = -R by PCG, u += du;
+            // mixed: tangent, CG vectors and du in FP32 (the residual stays FP64)
             FEM_CUDA(cudaMemsetAsync(dg, 0, sizeof(double) * g.dofs, s));
             k_j2_diag<<<cell_grid(g.ne), CB, 0, s>>>(g, u, hist, dg);
-            k_j2_dinv<<<vec_grid(g.dofs), VB, 0, s>>>(dg, mask, dinv, g.dofs);
-            count_launch(2);
-            FEM_CUDA(cudaMemsetAsync(du, 0, sizeof(double) * g.dofs, s));
-            auto apply = [&](const double *x, double *y, double *dot) -> int {
-                return apply_launch(g, mask, u, hist, x, y, dot, s);
-            };
-            const int rc = dpcg::solve<double>(s, g.dofs, apply, dinv, b, du, w, cg_rtol, cg_maxit, cg_it, nullptr,
-                                               "fem_j2_step");
-            if (rc != FEM_OK) return rc;
-            k_j2_axpy<<<vec_grid(g.dofs), VB, 0, s>>>(u, du, g.dofs);
+            count_launch();
+            int rc;
+            if (mixed) {
+                k_j2_dinv<float><<<vec_grid(g.dofs), VB, 0, s>>>(dg, mask, dinv32, g.dofs);
+                k_j2_to_f32<<<vec_grid(g.dofs), VB, 0, s>>>(b, b32, g.dofs);
+                count_launch(2);
+                FEM_CUDA(cudaMemsetAsync(du32, 0, sizeof(float) * g.dofs, s));
+                auto apply = [&](const float *x, float *y, double *dot) -> int {
+                    return apply_launch<float>(g, mask, u, hist, x, y, dot, s);
+                };
+                rc = dpcg::solve<float>(s, g.dofs, apply, dinv32, b32, du32, w32, cg_rtol, cg_maxit, cg_it, nullptr,
+                                        "fem_j2_step");
+                if (rc != FEM_OK) return rc;
+                k_j2_axpy<float><<<vec_grid(g.dofs), VB, 0, s>>>(u, du32, g.dofs);
+            } else {
+                k_j2_dinv<double><<<vec_grid(g.dofs), VB, 0, s>>>(dg, mask, dinv, g.dofs);
+                count_launch();
+                FEM_CUDA(cudaMemsetAsync(du, 0, sizeof(double) * g.dofs, s));
+                auto apply = [&](const double *x, double *y, double *dot) -> int {
+                    return apply_launch<double>(g, mask, u, hist, x, y, dot, s);
+                };
+                rc = dpcg::solve<double>(s, g.dofs, apply, dinv, b, du, w, cg_rtol, cg_maxit, cg_it, nullptr,
+                                         "fem_j2_step");
+                if (rc != FEM_OK) return rc;
+                k_j2_axpy<double><<<vec_grid(g.dofs), VB, 0, s>>>(u, du, g.dofs);
+            }
             count_launch();
             FEM_CUDA(cudaGetLastError());
             return FEM_OK;
@@ -345,7 +398,8 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, const uint8
         }
         void fail(const char *what) { set_error(std::string("fem_j2_step: ") + what); }
     };
-    Ops ops{g, mask, u_bar, u, hist, R, b, du, dg, dinv, hn, small, w, cg_rtol, cg_maxit, hb, s};
+    Ops ops{g, mask, u_bar, u, hist, R, b, du, dg, dinv, hn, small, w, w32, b32, du32, dinv32, mixed, cg_rtol, cg_maxit,
+            hb, s};
     const double h = std::min(1.0 / g.ihx, std::min(1.0 / g.ihy, 1.0 / g.ihz));
     return j2::newton_step(ops, mat->E, h, newton_rtol, newton_maxit, newton_iters, cg_iters, n_yield);
 }

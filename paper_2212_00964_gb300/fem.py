@@ -101,7 +101,7 @@ def lib():
     JP = ctypes.POINTER(fem_j2_material)
     L.fem_j2_residual.argtypes = [P, JP, P, P, P, P, P, ctypes.POINTER(I64), P]
     L.fem_j2_tangent_apply.argtypes = [P, JP, P, P, P, P, P, P]
-    L.fem_j2_step.argtypes = [P, JP, P, P, P, P, D, I, D, I, ctypes.POINTER(I), ctypes.POINTER(I),
+    L.fem_j2_step.argtypes = [P, JP, I, P, P, P, P, D, I, D, I, ctypes.POINTER(I), ctypes.POINTER(I),
                               ctypes.POINTER(I64), P]
     L.fem_density_filter.argtypes = [P, D, P, P, P]
     L.fem_mma_step.argtypes = [P, P, D, P, P, D, D, I, P, P, P, P, P, ctypes.POINTER(D), P]
@@ -455,11 +455,15 @@ def fem_j2_tangent_apply(m: Mesh, mat: fem_j2_material, u, hist, x, mask=None, y
 
 
 def fem_j2_step(m: Mesh, mat: fem_j2_material, mask, u_bar, u, hist, newton_rtol=1e-10, newton_maxit=30,
-                cg_rtol=1e-10, cg_maxit=20000, stream=None):
-    """One load step in place (u, hist); returns dict(newton_iters, cg_iters, n_yield)."""
+                cg_rtol=None, cg_maxit=20000, stream=None, mixed=False):
+    """One load step in place (u, hist); mixed=True: FP32 tangent and CG
+    inside the FP64 Newton.  Returns dict(newton_iters, cg_iters, n_yield)."""
     H = 12 * 8 * m.n_cells
+    if cg_rtol is None:
+        cg_rtol = 1e-4 if mixed else 1e-10
     ni, ci, ny = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int64(0)
-    _check(lib().fem_j2_step(m.handle, ctypes.byref(mat), _ptr(mask, torch.uint8, m.n_dofs, "mask"),
+    _check(lib().fem_j2_step(m.handle, ctypes.byref(mat), FEM_MIXED if mixed else FEM_FP64,
+                             _ptr(mask, torch.uint8, m.n_dofs, "mask"),
                              _ptr(u_bar, torch.float64, m.n_dofs, "u_bar"), _ptr(u, torch.float64, m.n_dofs, "u"),
                              _ptr(hist, torch.float64, H, "hist"), ctypes.c_double(newton_rtol), int(newton_maxit),
                              ctypes.c_double(cg_rtol), int(cg_maxit), ctypes.byref(ni), ctypes.byref(ci),

@@ -42,6 +42,7 @@ struct CpuStep {
     double *u, *hist;
     double cg_rtol;
     int cg_maxit;
+    bool mixed;
     std::vector<double> R, b, du, dg, dinv, hn;
     std::string err;
 
@@ -75,25 +76,27 @@ struct CpuStep {
         *n_yield = ny;
         return 0;
     }
-    void apply(const double *x, double *y, double *dot)
+    // the tangent computed in T from the FP64 state, as k_j2_apply<T> + k_j2_fix_dot<T>
+    template <typename T>
+    void apply(const T *x, T *y, double *dot)
     {
-        for (int64_t d = 0; d < g.D; ++d) y[d] = 0.0;
+        for (int64_t d = 0; d < g.D; ++d) y[d] = (T)0;
         for_cells(g, [&](int i, int j, int k, int64_t e) {
-            double ue[24], xe[24], ye[24];
+            T ue[24], xe[24], ye[24];
             for (int a = 0; a < 8; ++a)
                 for (int t = 0; t < 3; ++t) {
                     const int64_t d = 3 * j2::cell_node(i, j, k, a, g.nx, g.ny) + t;
-                    ue[3 * a + t] = u[d];
-                    xe[3 * a + t] = mask[d] ? 0.0 : x[d];
+                    ue[3 * a + t] = (T)u[d];
+                    xe[3 * a + t] = mask[d] ? (T)0 : x[d];
                 }
-            j2::cell_jvp<double>(g.c, g.ihx, g.ihy, g.ihz, g.w, ue, xe, hist, g.ne, e, ye);
+            j2::cell_jvp<T, double>(g.c, (T)g.ihx, (T)g.ihy, (T)g.ihz, (T)g.w, ue, xe, hist, g.ne, e, ye);
             for (int a = 0; a < 8; ++a)
                 for (int t = 0; t < 3; ++t) y[3 * j2::cell_node(i, j, k, a, g.nx, g.ny) + t] += ye[3 * a + t];
         });
         double acc = 0;
         for (int64_t d = 0; d < g.D; ++d) {
             if (mask[d]) y[d] = x[d];
-            acc += x[d] * y[d];
+            acc += (double)x[d] * (double)y[d];
         }
         if (dot) *dot += acc;
     }
@@ -112,9 +115,21 @@ struct CpuStep {
         });
         dinv.assign(g.D, 0.0);
         for (int64_t d = 0; d < g.D; ++d) dinv[d] = mask[d] ? 1.0 : (dg[d] != 0.0 ? 1.0 / dg[d] : 0.0);
+        if (mixed) {
+            std::vector<float> dinv32(dinv.begin(), dinv.end()), b32(b.begin(), b.end()), du32(g.D, 0.0f);
+            CpuPcg<float> pcg{g.D, [&](const float *x, float *y, double *dot) { apply<float>(x, y, dot); },
+                              dinv32.data(), b32.data(), du32.data(), cg_maxit};
+            const int rc = dpcg::control(pcg, cg_rtol, cg_maxit, cg_it, nullptr);
+            if (rc) {
+                err = pcg.err;
+                return rc;
+            }
+            for (int64_t d = 0; d < g.D; ++d) u[d] += (double)du32[d];
+            return 0;
+        }
         du.assign(g.D, 0.0);
-        CpuPcg<double> pcg{g.D, [&](const double *x, double *y, double *dot) { apply(x, y, dot); }, dinv.data(), b.data(),
-                   du.data(), cg_maxit};
+        CpuPcg<double> pcg{g.D, [&](const double *x, double *y, double *dot) { apply<double>(x, y, dot); },
+                           dinv.data(), b.data(), du.data(), cg_maxit};
         const int rc = dpcg::control(pcg, cg_rtol, cg_maxit, cg_it, nullptr);
         if (rc) {
             err = pcg.err;
@@ -139,7 +154,8 @@ extern "C" {
 
 int host_j2_step(int nx, int ny, int nz, double lx, double ly, double lz, double E, double nu, double sy,
                  const uint8_t *mask, const double *u_bar, double *u, double *hist, double newton_rtol,
-                 int newton_maxit, double cg_rtol, int cg_maxit, int *newton_iters, int *cg_iters, int64_t *n_yield)
+                 int newton_maxit, double cg_rtol, int cg_maxit, int mixed, int *newton_iters, int *cg_iters,
+                 int64_t *n_yield)
 {
     Box g;
     g.nx = nx, g.ny = ny, g.nz = nz;
@@ -148,7 +164,7 @@ int host_j2_step(int nx, int ny, int nz, double lx, double ly, double lz, double
     g.ne = (int64_t)nx * ny * nz;
     g.D = 3 * (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
     g.c = j2::consts(E, nu, sy);
-    CpuStep ops{g, mask, u_bar, u, hist, cg_rtol, cg_maxit};
+    CpuStep ops{g, mask, u_bar, u, hist, cg_rtol, cg_maxit, mixed != 0};
     const double h = std::min(hx, std::min(hy, hz));
     const int rc = j2::newton_step(ops, E, h, newton_rtol, newton_maxit, newton_iters, cg_iters, n_yield);
     last_err = ops.err;

@@ -51,7 +51,8 @@ def test_residual_and_tangent_parity():
     assert rel_l2(host(y), pl.tangent_apply(om, omat, hist, u, x, mask)) <= 1e-10
 
 
-def test_load_unload_path_vs_oracle_and_closed_form():
+@pytest.mark.parametrize("mixed", [False, True])
+def test_load_unload_path_vs_oracle_and_closed_form(mixed):
     n, L = 4, 1.0
     mask, ubars, strains, (E_, nu, sy) = inputs.j2_uniaxial(n=n, L=L)
     F = fem()
@@ -64,7 +65,8 @@ def test_load_unload_path_vs_oracle_and_closed_form():
     mask_d = dev(mask)
     sig_prev, e_prev = 0.0, 0.0
     for k, ub in enumerate(ubars):
-        st = F.fem_j2_step(m, mat, mask_d, dev(ub), u, hist, newton_rtol=1e-12, cg_rtol=1e-12)
+        st = F.fem_j2_step(m, mat, mask_d, dev(ub), u, hist, newton_rtol=1e-12, cg_rtol=1e-4 if mixed else 1e-12,
+                           mixed=mixed)
         u_ref, (eps_ref, sig_ref), ny_ref = ref_path[k]
         assert rel_l2(host(u), u_ref) <= 1e-8
         h = host(hist).reshape(12, 8, om.n_cells)

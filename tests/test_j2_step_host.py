@@ -33,7 +33,7 @@ def L():
         os.replace(tmp, SO)
     lib = ctypes.CDLL(SO)
     P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
-    lib.host_j2_step.argtypes = [I, I, I, D, D, D, D, D, D, P, P, P, P, D, I, D, I, ctypes.POINTER(I),
+    lib.host_j2_step.argtypes = [I, I, I, D, D, D, D, D, D, P, P, P, P, D, I, D, I, I, ctypes.POINTER(I),
                                  ctypes.POINTER(I), ctypes.POINTER(ctypes.c_int64)]
     lib.host_j2_step_error.restype = ctypes.c_char_p
     return lib
@@ -52,7 +52,7 @@ def to_soa(hist):
     return np.ascontiguousarray(np.concatenate([six(eps).transpose(0, 2, 1), six(sig).transpose(0, 2, 1)]).reshape(-1))
 
 
-def run_path(L, dims, mat, mask, ubars, newton_maxit=30):
+def run_path(L, dims, mat, mask, ubars, newton_maxit=30, mixed=False):
     nx, ny, nz, lx, ly, lz = dims
     D = 3 * (nx + 1) * (ny + 1) * (nz + 1)
     u = np.zeros(D)
@@ -61,26 +61,27 @@ def run_path(L, dims, mat, mask, ubars, newton_maxit=30):
     for ub in ubars:
         ni, ci, nyd = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
         rc = L.host_j2_step(nx, ny, nz, lx, ly, lz, mat.E, mat.nu, mat.sy, p(mask), p(np.ascontiguousarray(ub)),
-                            p(u), p(hist), 1e-12, newton_maxit, 1e-12, 20000, ctypes.byref(ni), ctypes.byref(ci),
-                            ctypes.byref(nyd))
+                            p(u), p(hist), 1e-12, newton_maxit, 1e-4 if mixed else 1e-12, 20000, int(mixed),
+                            ctypes.byref(ni), ctypes.byref(ci), ctypes.byref(nyd))
         out.append((rc, u.copy(), hist.copy(), ni.value, ci.value, nyd.value))
         if rc:
             break
     return out
 
 
-def test_uniaxial_path_matches_oracle(L):
+@pytest.mark.parametrize("mixed", [False, True])
+def test_uniaxial_path_matches_oracle(L, mixed):
     n = 3
     mask, ubars, strains, (E, nu, sy) = inputs.j2_uniaxial(n=n)
     mat = pl.Material(E, nu, sy)
     om = oracle.mesh(n, n, n)
     ref = pl.solve_path(om, mat, mask, ubars)
-    got = run_path(L, (n, n, n, 1.0, 1.0, 1.0), mat, mask, ubars)
+    got = run_path(L, (n, n, n, 1.0, 1.0, 1.0), mat, mask, ubars, mixed=mixed)
     for k, ((rc, u, h, ni, ci, nyd), (u_ref, hist_ref, ny_ref)) in enumerate(zip(got, ref)):
         assert rc == 0, (k, L.host_j2_step_error())
         assert np.abs(u - u_ref).max() <= 1e-10 * np.abs(u_ref).max()
         assert np.abs(h - to_soa(hist_ref)).max() <= 1e-8 * sy
-        assert 1 <= ni <= 10
+        assert 1 <= ni <= (15 if mixed else 10)
 
 
 def sheared_box():
@@ -97,12 +98,13 @@ def sheared_box():
     return (nx, ny, nz, 1.0, 1.5, 1.0), mask, ubars
 
 
-def test_sheared_box_matches_oracle(L):
+@pytest.mark.parametrize("mixed", [False, True])
+def test_sheared_box_matches_oracle(L, mixed):
     dims, mask, ubars = sheared_box()
     mat = pl.Material(70e3, 0.3, 250.0)
     om = oracle.mesh(*dims)
     ref = pl.solve_path(om, mat, mask, ubars)
-    got = run_path(L, dims, mat, mask, ubars)
+    got = run_path(L, dims, mat, mask, ubars, mixed=mixed)
     mixes = 0
     for k, ((rc, u, h, ni, ci, nyd), (u_ref, hist_ref, ny_ref)) in enumerate(zip(got, ref)):
         assert rc == 0, (k, L.host_j2_step_error())
