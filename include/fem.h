@@ -275,10 +275,24 @@ int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precision, const u
  * besides the SIMP solve (fem_solve) and the compliance gradient
  * (fem_adjoint with dJ/du = f).  Per-cell arrays [n_cells] of double. */
 
-/* Sensitivity filter: g_filtered_e = sum_f w_ef g_f / sum_f w_ef with the
- * cone kernel w_ef = max(0, rmin - |c_e - c_f|) between cell centres,
- * measured in cells (0 < rmin <= 64; rmin <= 1 is the identity). */
-int fem_density_filter(fem_mesh_t m, double rmin, const double *g, double *g_filtered, void *stream);
+/* Cone-kernel filter: transpose 0 gives g_filtered_e = sum_f w_ef g_f /
+ * Hs_e, Hs_e = sum_f w_ef, with w_ef = max(0, rmin - |c_e - c_f|) between
+ * cell centres measured in cells (0 < rmin <= 64; rmin <= 1 is the
+ * identity): the paper's blur of the sensitivities, or a density filter.
+ * transpose 1 gives its transpose, sum_f w_fe g_f / Hs_f: the chain rule
+ * that carries dJ/dtheta~ of a filtered density back to dJ/dtheta. */
+int fem_density_filter(fem_mesh_t m, double rmin, int transpose, const double *g, double *g_filtered,
+                       void *stream);
+
+/* Optimality-criteria update (the classic alternative to MMA for one volume
+ * constraint): y_e = clip(x_e sqrt(-min(g_e, 0) / (lam dv_e)),
+ * max(x_min, x_e - move), min(x_max, x_e + move)) with lam such that
+ * sum dv y = volfrac sum dv (bisection on log lam over [1e-40, 1e40]).
+ * x, g (dJ/dx), dv (the constraint's per-cell weights, e.g. cell volumes),
+ * y: [n_cells]; *lam_out (host, may be NULL).  Synchronises the stream once
+ * per bisection step. */
+int fem_oc_step(fem_mesh_t m, const double *x, const double *g, const double *dv, double volfrac, double move,
+                double x_min, double x_max, double *y, double *lam_out, void *stream);
 
 /* One step of the method of moving asymptotes (Svanberg 1987) for
  * min f0(x) s.t. f1(x) <= 0, x_min <= x <= x_max, over the n_cells

@@ -15,6 +15,9 @@ One design iteration, as Sec. 3 lays out the PDE-CO loop:
      units), normalised by the kernel's row sums;
   4. one step of the method of moving asymptotes (Svanberg 1987) for
      min c(theta) s.t. mean(theta) - v_f <= 0, theta in [theta_min, 1].
+An alternative optimiser step is the optimality-criteria update (``oc_step``);
+``filter_transpose`` is the chain rule of the filter when it is applied to
+the density instead of the sensitivities.
 The MMA step follows Svanberg's 1987 construction, restated:
   * asymptotes: in the first two iterations L = x - s0 (x_max - x_min),
     U = x + s0 (x_max - x_min) with s0 = 0.5; afterwards each variable's
@@ -66,6 +69,45 @@ def filter_matrix(nx, ny, nz, rmin):
 def filter_sensitivities(H, g):
     """g~_e = sum_f H_ef g_f / sum_f H_ef."""
     return (H @ g) / np.asarray(H.sum(axis=1)).reshape(-1)
+
+
+def filter_transpose(H, g):
+    """The transpose of the normalised filter: (diag(1/Hs) H)^T g =
+    H^T (g / Hs), Hs the row sums.  With the filter applied to the density
+    (theta~ = filter(theta) enters the physics) this carries dJ/dtheta~ back
+    to dJ/dtheta by the chain rule."""
+    hs = np.asarray(H.sum(axis=1)).reshape(-1)
+    return H.T @ (g / hs)
+
+
+def oc_step(x, g, dv, volfrac, move=0.2, x_min=0.0, x_max=1.0):
+    """One optimality-criteria update for min c(x) s.t. sum dv x <= volfrac
+    sum dv (the classic SIMP update; an alternative to MMA).  With
+    B_e(lam) = -g_e / (lam dv_e) (g <= 0 for compliance):
+        x_new = clip(x B^(1/2), max(x_min, x - move), min(x_max, x + move)),
+    lam found by bisection on the volume, which is non-increasing in lam
+    (on log(lam), until the bracket's relative width is 1e-13 or after 200
+    halvings).  Returns (x_new, lam)."""
+    x = np.asarray(x, np.float64)
+    g = np.minimum(np.asarray(g, np.float64), 0.0)
+    dv = np.asarray(dv, np.float64)
+    target = volfrac * dv.sum()
+    lo_b = np.maximum(x_min, x - move)
+    hi_b = np.minimum(x_max, x + move)
+
+    def x_of(lam):
+        return np.clip(x * np.sqrt(-g / (lam * dv)), lo_b, hi_b)
+
+    lo, hi = 1e-40, 1e40
+    for _ in range(200):
+        mid = np.sqrt(lo * hi)
+        if (dv @ x_of(mid)) > target:
+            lo = mid
+        else:
+            hi = mid
+        if hi - lo <= 1e-13 * hi:
+            break
+    return x_of(hi), hi
 
 
 class MMA:

@@ -1,8 +1,9 @@
 // topopt.cu -- the data-parallel parts of the topology-optimisation loop
-// (Sec. 3.2) on the GPU: the cone-kernel sensitivity filter and one step of
-// the method of moving asymptotes under one constraint (the per-variable
-// arithmetic of topopt_core.cuh; the dual multiplier by bisection, one
-// reduction per evaluation).  The forward SIMP solve and the compliance
+// (Sec. 3.2) on the GPU: the cone-kernel filter (and its transpose), one
+// step of the method of moving asymptotes under one constraint, and the
+// optimality-criteria update (the per-variable arithmetic of
+// topopt_core.cuh; each multiplier by bisection, one reduction per
+// evaluation).  The forward SIMP solve and the compliance
 // gradient are fem_solve and fem_adjoint.  FP64.
 #include <algorithm>
 #include <cmath>
@@ -21,11 +22,41 @@ enum { WS_TVARS = 80, WS_TACC };
 int tgrid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + TB - 1) / TB, 152 * 8)); }
 
 __global__ void __launch_bounds__(TB) k_filter(const double *__restrict__ g, double *__restrict__ out, int nx, int ny,
-                                              int nz, double rmin)
+                                              int nz, double rmin, int transpose)
 {
     const int64_t n = (int64_t)nx * ny * nz;
     for (int64_t e = blockIdx.x * (int64_t)TB + threadIdx.x; e < n; e += (int64_t)gridDim.x * TB)
-        out[e] = topopt::filter_cell(g, e, nx, ny, nz, rmin);
+        out[e] = transpose ? topopt::filter_cell_t(g, e, nx, ny, nz, rmin) : topopt::filter_cell(g, e, nx, ny, nz, rmin);
+}
+
+// *acc += sum_j w_j (w may be null: the count)
+__global__ void __launch_bounds__(TB) k_sum(const double *__restrict__ w, int64_t n, double *acc)
+{
+    __shared__ double sh[TB / 32];
+    double s = 0.0;
+    for (int64_t j = blockIdx.x * (int64_t)TB + threadIdx.x; j < n; j += (int64_t)gridDim.x * TB) s += w[j];
+    s = block_sum<double, TB>(s, sh);
+    if (threadIdx.x == 0) atomicAdd(acc, s);
+}
+
+// *acc += sum_j dv_j x_j(lam) of the optimality-criteria update
+__global__ void __launch_bounds__(TB) k_oc_volume(const double *__restrict__ x, const double *__restrict__ g,
+                                                 const double *__restrict__ dv, double lam, double move, double x_min,
+                                                 double x_max, int64_t n, double *acc)
+{
+    __shared__ double sh[TB / 32];
+    double s = 0.0;
+    for (int64_t j = blockIdx.x * (int64_t)TB + threadIdx.x; j < n; j += (int64_t)gridDim.x * TB)
+        s += dv[j] * topopt::oc_x(x[j], g[j], dv[j], lam, move, x_min, x_max);
+    s = block_sum<double, TB>(s, sh);
+    if (threadIdx.x == 0) atomicAdd(acc, s);
+}
+
+__global__ void k_oc_finish(const double *__restrict__ x, const double *__restrict__ g, const double *__restrict__ dv,
+                            double lam, double move, double x_min, double x_max, int64_t n, double *__restrict__ y)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        y[j] = topopt::oc_x(x[j], g[j], dv[j], lam, move, x_min, x_max);
 }
 
 // vars[j] = setup of variable j; *acc += the constraint model at x
@@ -81,13 +112,15 @@ __global__ void k_mma_finish(const topopt::MmaVar *__restrict__ vars, const doub
 
 using namespace femgb;
 
-extern "C" int fem_density_filter(fem_mesh_t m, double rmin, const double *g, double *g_filtered, void *stream)
+extern "C" int fem_density_filter(fem_mesh_t m, double rmin, int transpose, const double *g, double *g_filtered,
+                                  void *stream)
 {
     if (!m || !g || !g_filtered || g == g_filtered)
         return (set_error("fem_density_filter: NULL argument or in-place call"), FEM_ERR_ARG);
     if (!(rmin > 0) || rmin > 64) return (set_error("fem_density_filter: 0 < rmin <= 64 required"), FEM_ERR_ARG);
+    if (transpose != 0 && transpose != 1) return (set_error("fem_density_filter: transpose must be 0 or 1"), FEM_ERR_ARG);
     cudaStream_t s = (cudaStream_t)stream;
-    k_filter<<<tgrid(m->n_cells), TB, 0, s>>>(g, g_filtered, m->nx, m->ny, m->nz, rmin);
+    k_filter<<<tgrid(m->n_cells), TB, 0, s>>>(g, g_filtered, m->nx, m->ny, m->nz, rmin, transpose);
     count_launch();
     FEM_CUDA(cudaGetLastError());
     return FEM_OK;
@@ -130,6 +163,41 @@ extern "C" int fem_mma_step(fem_mesh_t m, const double *x, double f1, const doub
     FEM_CUDA(err);
     if (lam < 0) return (set_error("fem_mma_step: no multiplier makes the subproblem feasible"), FEM_ERR_NOT_CONVERGED);
     k_mma_finish<<<tgrid(n), TB, 0, s>>>(vars, x, lam, n, y, x1, x2, low, upp);
+    count_launch();
+    FEM_CUDA(cudaGetLastError());
+    if (lam_out) *lam_out = lam;
+    return FEM_OK;
+}
+
+extern "C" int fem_oc_step(fem_mesh_t m, const double *x, const double *g, const double *dv, double volfrac,
+                           double move, double x_min, double x_max, double *y, double *lam_out, void *stream)
+{
+    if (!m || !x || !g || !dv || !y || y == x) return (set_error("fem_oc_step: NULL argument or y aliases x"), FEM_ERR_ARG);
+    if (!(x_max > x_min) || !(move > 0) || !(volfrac > 0))
+        return (set_error("fem_oc_step: x_max > x_min, move > 0 and volfrac > 0 required"), FEM_ERR_ARG);
+    std::lock_guard<std::mutex> lk(m->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = m->n_cells;
+    double *acc = (double *)m->ws.get(WS_TACC, sizeof(double));
+    if (!acc) return FEM_ERR_NOMEM;
+    cudaError_t err = cudaSuccess;
+    auto reduce = [&](auto launch) -> double {
+        if (err != cudaSuccess) return 0.0;
+        double v = 0.0;
+        if ((err = cudaMemsetAsync(acc, 0, sizeof(double), s)) != cudaSuccess) return 0.0;
+        launch();
+        count_launch();
+        if ((err = cudaMemcpyAsync(&v, acc, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return 0.0;
+        if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return 0.0;
+        return v;
+    };
+    const double total = reduce([&] { k_sum<<<tgrid(n), TB, 0, s>>>(dv, n, acc); });
+    auto vol = [&](double lam) {
+        return reduce([&] { k_oc_volume<<<tgrid(n), TB, 0, s>>>(x, g, dv, lam, move, x_min, x_max, n, acc); });
+    };
+    const double lam = topopt::oc_bisect(vol, volfrac * total);
+    FEM_CUDA(err);
+    k_oc_finish<<<tgrid(n), TB, 0, s>>>(x, g, dv, lam, move, x_min, x_max, n, y);
     count_launch();
     FEM_CUDA(cudaGetLastError());
     if (lam_out) *lam_out = lam;

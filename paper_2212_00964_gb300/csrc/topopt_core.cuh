@@ -1,7 +1,8 @@
 // topopt_core.cuh -- per-cell arithmetic of the topology-optimisation loop
-// (Sec. 3.2) as host/device functions: the sensitivity filter and the
-// element-wise part of one step of the method of moving asymptotes
-// (Svanberg 1987).  The kernels call them per cell; a host build checks
+// (Sec. 3.2) as host/device functions: the sensitivity filter (and its
+// transpose, for a filter applied to the density), the element-wise part
+// of one step of the method of moving asymptotes (Svanberg 1987), and the
+// optimality-criteria update.  The kernels call them per cell; a host build checks
 // them against the oracle on the CPU.
 //
 // Filter: g~_e = sum_f w_ef g_f / sum_f w_ef with the cone kernel
@@ -49,6 +50,60 @@ TO_HD double filter_cell(const double *g, int64_t e, int nx, int ny, int nz, dou
                 }
             }
     return num / den;
+}
+
+// sum_f w_ef: the row sum of the cone weights around cell e
+TO_HD double filter_weight_sum(int64_t e, int nx, int ny, int nz, double rmin)
+{
+    const int64_t nxy = (int64_t)nx * ny;
+    const int k = (int)(e / nxy);
+    const int64_t rem = e - (int64_t)k * nxy;
+    const int j = (int)(rem / nx);
+    const int i = (int)(rem - (int64_t)j * nx);
+    const int R = (int)ceil(rmin) - 1;
+    double den = 0.0;
+    for (int kk = (k - R > 0 ? k - R : 0); kk <= (k + R < nz - 1 ? k + R : nz - 1); ++kk)
+        for (int jj = (j - R > 0 ? j - R : 0); jj <= (j + R < ny - 1 ? j + R : ny - 1); ++jj)
+            for (int ii = (i - R > 0 ? i - R : 0); ii <= (i + R < nx - 1 ? i + R : nx - 1); ++ii) {
+                const double di = ii - i, dj = jj - j, dk = kk - k;
+                const double w = rmin - sqrt(di * di + dj * dj + dk * dk);
+                if (w > 0.0) den += w;
+            }
+    return den;
+}
+
+// The transpose of the normalised filter at cell e: sum_f w_fe g_f / Hs_f
+// (the weights are symmetric), the chain rule of a filter applied to the
+// density.
+TO_HD double filter_cell_t(const double *g, int64_t e, int nx, int ny, int nz, double rmin)
+{
+    const int64_t nxy = (int64_t)nx * ny;
+    const int k = (int)(e / nxy);
+    const int64_t rem = e - (int64_t)k * nxy;
+    const int j = (int)(rem / nx);
+    const int i = (int)(rem - (int64_t)j * nx);
+    const int R = (int)ceil(rmin) - 1;
+    double acc = 0.0;
+    for (int kk = (k - R > 0 ? k - R : 0); kk <= (k + R < nz - 1 ? k + R : nz - 1); ++kk)
+        for (int jj = (j - R > 0 ? j - R : 0); jj <= (j + R < ny - 1 ? j + R : ny - 1); ++jj)
+            for (int ii = (i - R > 0 ? i - R : 0); ii <= (i + R < nx - 1 ? i + R : nx - 1); ++ii) {
+                const double di = ii - i, dj = jj - j, dk = kk - k;
+                const double w = rmin - sqrt(di * di + dj * dj + dk * dk);
+                if (w > 0.0) {
+                    const int64_t f = ii + (int64_t)nx * (jj + (int64_t)ny * kk);
+                    acc += w * g[f] / filter_weight_sum(f, nx, ny, nz, rmin);
+                }
+            }
+    return acc;
+}
+
+// Optimality-criteria update of one variable for the multiplier lam:
+// clip(x sqrt(-min(g, 0) / (lam dv)), max(x_min, x - move), min(x_max, x + move)).
+TO_HD double oc_x(double x, double g, double dv, double lam, double move, double x_min, double x_max)
+{
+    const double lo = fmax(x_min, x - move), hi = fmin(x_max, x + move);
+    const double y = x * sqrt(-fmin(g, 0.0) / (lam * dv));
+    return fmin(fmax(y, lo), hi);
 }
 
 struct MmaParams {
@@ -126,6 +181,23 @@ double mma_dual(G g1)
         if (mid == lo || mid == hi) break;
         if (g1(mid) > 0.0) lo = mid;
         else hi = mid;
+    }
+    return hi;
+}
+
+// Multiplier of the optimality-criteria update: the volume vol(lam) =
+// sum dv x(lam) is non-increasing in lam; bisection on log(lam) over
+// [1e-40, 1e40] until the bracket's relative width is 1e-13 (at most 200
+// halvings).  Returns the upper end.  Host code.
+template <typename V>
+double oc_bisect(V vol, double target)
+{
+    double lo = 1e-40, hi = 1e40;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = sqrt(lo * hi);
+        if (vol(mid) > target) lo = mid;
+        else hi = mid;
+        if (hi - lo <= 1e-13 * hi) break;
     }
     return hi;
 }

@@ -103,7 +103,8 @@ def lib():
     L.fem_j2_tangent_apply.argtypes = [P, JP, P, P, P, P, P, P]
     L.fem_j2_step.argtypes = [P, JP, I, P, P, P, P, D, I, D, I, ctypes.POINTER(I), ctypes.POINTER(I),
                               ctypes.POINTER(I64), P]
-    L.fem_density_filter.argtypes = [P, D, P, P, P]
+    L.fem_density_filter.argtypes = [P, D, I, P, P, P]
+    L.fem_oc_step.argtypes = [P, P, P, P, D, D, D, D, P, ctypes.POINTER(D), P]
     L.fem_mma_step.argtypes = [P, P, D, P, P, D, D, I, P, P, P, P, P, ctypes.POINTER(D), P]
     L.fem_poisson_adjoint.argtypes = [P, I, D, P, P, D, I, P, P, ctypes.POINTER(I), P]
     L.fem_poisson_apply.argtypes = [P, I, D, I, P, P, P, P]
@@ -386,13 +387,27 @@ def fem_poisson_gradient(m: Mesh, theta, obs, u_obs, alpha=1.0, mask=None, rtol=
     return {"J": J.value, "grad": grad, "u": u, "lam": lam, "iters": (its[0], its[1])}
 
 
-def fem_density_filter(m: Mesh, g, rmin=1.5, out=None, stream=None):
-    """Cone-kernel sensitivity filter over the cells (float64 [n_cells])."""
+def fem_density_filter(m: Mesh, g, rmin=1.5, out=None, stream=None, transpose=False):
+    """Cone-kernel filter over the cells (float64 [n_cells]); transpose=True
+    applies its transpose (the chain rule of a filtered density)."""
     out = torch.empty_like(g) if out is None else out
-    _check(lib().fem_density_filter(m.handle, ctypes.c_double(rmin), _ptr(g, torch.float64, m.n_cells, "g"),
+    _check(lib().fem_density_filter(m.handle, ctypes.c_double(rmin), int(bool(transpose)),
+                                     _ptr(g, torch.float64, m.n_cells, "g"),
                                      _ptr(out, torch.float64, m.n_cells, "out"), _stream(stream)),
            "fem_density_filter")
     return out
+
+
+def fem_oc_step(m: Mesh, x, g, dv, volfrac, move=0.2, x_min=0.0, x_max=1.0, stream=None):
+    """Optimality-criteria update; returns (y, lam)."""
+    n = m.n_cells
+    y = torch.empty_like(x)
+    lam = ctypes.c_double(0.0)
+    _check(lib().fem_oc_step(m.handle, _ptr(x, torch.float64, n, "x"), _ptr(g, torch.float64, n, "g"),
+                             _ptr(dv, torch.float64, n, "dv"), ctypes.c_double(volfrac), ctypes.c_double(move),
+                             ctypes.c_double(x_min), ctypes.c_double(x_max), _ptr(y, torch.float64, n, "y"),
+                             ctypes.byref(lam), _stream(stream)), "fem_oc_step")
+    return y, lam.value
 
 
 class MMAState:

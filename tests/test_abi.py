@@ -54,7 +54,8 @@ def test_host_only_calls():
     assert L.fem_j2_residual(None, ctypes.byref(jm), None, None, None, None, None, None, None) == fem.FEM_ERR_ARG
     assert L.fem_j2_step(None, ctypes.byref(jm), 0, None, None, None, None, 1e-10, 10, 1e-10, 10, None, None,
                          None, None) == fem.FEM_ERR_ARG
-    assert L.fem_density_filter(None, 1.5, None, None, None) == fem.FEM_ERR_ARG
+    assert L.fem_density_filter(None, 1.5, 0, None, None, None) == fem.FEM_ERR_ARG
+    assert L.fem_oc_step(None, None, None, None, 0.5, 0.2, 0.0, 1.0, None, None, None) == fem.FEM_ERR_ARG
     assert L.fem_mma_step(None, None, 0.0, None, None, 0.0, 1.0, 0, None, None, None, None, None, None,
                           None) == fem.FEM_ERR_ARG
 

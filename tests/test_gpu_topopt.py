@@ -25,6 +25,34 @@ def test_filter_parity(rmin):
     assert rel_l2(host(out), ref) <= 1e-14
 
 
+@pytest.mark.parametrize("rmin", [1.5, 2.3])
+def test_filter_transpose_parity(rmin):
+    nx, ny, nz = 21, 8, 5
+    F = fem()
+    m = F.fem_mesh(nx, ny, nz)
+    g = np.random.default_rng(6).standard_normal(nx * ny * nz)
+    out = F.fem_density_filter(m, dev(g), rmin, transpose=True)
+    ref = ot.filter_transpose(ot.filter_matrix(nx, ny, nz, rmin), g)
+    assert rel_l2(host(out), ref) <= 1e-14
+
+
+def test_oc_steps_parity():
+    F = fem()
+    m = F.fem_mesh(6, 5, 4)
+    n = m.n_cells
+    rng = np.random.default_rng(7)
+    c = rng.uniform(0.2, 1.0, n)
+    dv = rng.uniform(0.5, 1.5, n)
+    x = np.full(n, 0.4)
+    for it in range(8):
+        g = -c / x ** 2
+        ref, lam_ref = ot.oc_step(x, g, dv, 0.4, 0.15, 0.01, 1.0)
+        y, lam = F.fem_oc_step(m, dev(x), dev(g), dev(dv), 0.4, 0.15, 0.01, 1.0)
+        assert abs(lam - lam_ref) <= 1e-12 * lam_ref
+        assert np.abs(host(y) - ref).max() <= 1e-12, it
+        x = ref
+
+
 def test_mma_steps_parity():
     """Twelve steps on min sum c/x under a mean constraint, oracle and GPU
     fed the same iterates."""

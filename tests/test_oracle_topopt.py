@@ -145,3 +145,48 @@ def test_design_loop_on_box_cantilever():
     assert np.mean((th > 0.1) & (th < 0.9)) < 0.1
     cs = np.array([h[0] for h in hist])
     assert np.all(np.diff(cs[:12]) < 0)
+
+
+def test_filter_transpose_is_the_adjoint():
+    """<F a, b> = <a, F^T b> for the normalised filter F = diag(1/Hs) H, and
+    the chain rule through a density filter matches central differences."""
+    nx, ny, nz = 5, 4, 3
+    H = ot.filter_matrix(nx, ny, nz, 1.7)
+    rng = np.random.default_rng(21)
+    a, b = rng.standard_normal(60), rng.standard_normal(60)
+    assert abs(ot.filter_sensitivities(H, a) @ b - a @ ot.filter_transpose(H, b)) <= 1e-13 * np.abs(a).sum()
+    # J(theta) = sum c_e / filter(theta)_e
+    c = rng.uniform(0.5, 1.5, 60)
+    theta = rng.uniform(0.3, 0.9, 60)
+    J = lambda t: np.sum(c / ot.filter_sensitivities(H, t))
+    g_tilde = -c / ot.filter_sensitivities(H, theta) ** 2
+    g = ot.filter_transpose(H, g_tilde)
+    h = 1e-6
+    for e in (0, 17, 59):
+        d = np.zeros(60)
+        d[e] = h
+        assert abs((J(theta + d) - J(theta - d)) / (2 * h) - g[e]) <= 1e-6 * np.abs(g).max()
+
+
+def test_oc_reaches_the_closed_form_optimum():
+    """min sum c_j / x_j s.t. mean(x) <= V: the OC fixed point is the KKT
+    point x_j = V n sqrt(c_j) / sum sqrt(c) (all inside the bounds here), and
+    the volume constraint holds with equality at every step."""
+    rng = np.random.default_rng(22)
+    n, V = 30, 0.4
+    c = rng.uniform(0.2, 1.0, n)
+    xs = V * n * np.sqrt(c) / np.sqrt(c).sum()
+    x = np.full(n, V)
+    dv = np.ones(n)
+    for _ in range(60):
+        x, lam = ot.oc_step(x, -c / x ** 2, dv, V, move=0.2, x_min=0.01)
+        assert abs(x.mean() - V) <= 1e-10
+    assert np.abs(x - xs).max() <= 1e-9
+
+
+def test_oc_move_limit_and_bounds():
+    x = np.array([0.5, 0.5, 0.05, 0.95])
+    g = np.array([-100.0, -1e-6, -1.0, -1.0])
+    y, _ = ot.oc_step(x, g, np.ones(4), 0.5, move=0.1, x_min=0.0, x_max=1.0)
+    assert np.all(y >= np.maximum(0, x - 0.1) - 1e-15) and np.all(y <= np.minimum(1, x + 0.1) + 1e-15)
+    assert y[0] == 0.6 and y[1] == 0.4

@@ -34,6 +34,9 @@ def core():
     L.host_filter.argtypes = [P, P, I, I, I, D]
     L.host_mma_step.argtypes = [I64, P, D, P, P, D, D, I, P, P, P, P, P]
     L.host_mma_step.restype = D
+    L.host_filter_t.argtypes = [P, P, I, I, I, D]
+    L.host_oc_step.argtypes = [I64, P, P, P, D, D, D, D, P]
+    L.host_oc_step.restype = D
     return L
 
 
@@ -102,3 +105,29 @@ def test_mma_closed_form_nonlinear_constraint(core):
     for _ in range(60):
         x = mma.step(x, a * x.sum(), np.full(5, a), np.sum(b / x ** 3) - 1, -3 * b / x ** 4)
     assert np.abs(x - xs).max() <= 1e-9 * xs.max()
+
+
+@pytest.mark.parametrize("rmin", [1.0, 1.5, 2.3])
+def test_filter_transpose_matches_oracle(core, rmin):
+    nx, ny, nz = 6, 5, 3
+    g = np.random.default_rng(int(rmin * 7)).standard_normal(nx * ny * nz)
+    out = np.zeros_like(g)
+    core.host_filter_t(p(g), p(out), nx, ny, nz, rmin)
+    ref = ot.filter_transpose(ot.filter_matrix(nx, ny, nz, rmin), g)
+    assert np.abs(out - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+def test_oc_steps_match_oracle(core):
+    rng = np.random.default_rng(23)
+    n = 40
+    c = rng.uniform(0.2, 1.0, n)
+    dv = rng.uniform(0.5, 1.5, n)
+    x = np.full(n, 0.4)
+    for _ in range(8):
+        g = -c / x ** 2
+        ref, lam_ref = ot.oc_step(x, g, dv, 0.4, 0.15, 0.01, 1.0)
+        y = np.zeros(n)
+        lam = core.host_oc_step(n, p(x), p(np.ascontiguousarray(g)), p(dv), 0.4, 0.15, 0.01, 1.0, p(y))
+        assert abs(lam - lam_ref) <= 1e-12 * lam_ref
+        assert np.abs(y - ref).max() <= 1e-12
+        x = ref

@@ -18,6 +18,28 @@ void host_filter(const double *g, double *out, int nx, int ny, int nz, double rm
     for (int64_t e = 0; e < n; ++e) out[e] = filter_cell(g, e, nx, ny, nz, rmin);
 }
 
+void host_filter_t(const double *g, double *out, int nx, int ny, int nz, double rmin)
+{
+    const int64_t n = (int64_t)nx * ny * nz;
+    for (int64_t e = 0; e < n; ++e) out[e] = filter_cell_t(g, e, nx, ny, nz, rmin);
+}
+
+// Mirrors fem_oc_step: returns the multiplier.
+double host_oc_step(int64_t n, const double *x, const double *g, const double *dv, double volfrac, double move,
+                    double x_min, double x_max, double *y)
+{
+    double total = 0.0;
+    for (int64_t j = 0; j < n; ++j) total += dv[j];
+    auto vol = [&](double lam) {
+        double s = 0.0;
+        for (int64_t j = 0; j < n; ++j) s += dv[j] * oc_x(x[j], g[j], dv[j], lam, move, x_min, x_max);
+        return s;
+    };
+    const double lam = oc_bisect(vol, volfrac * total);
+    for (int64_t j = 0; j < n; ++j) y[j] = oc_x(x[j], g[j], dv[j], lam, move, x_min, x_max);
+    return lam;
+}
+
 // Mirrors fem_mma_step: returns the multiplier (negative: no bracket).
 double host_mma_step(int64_t n, const double *x, double f1, const double *df0, const double *df1, double x_min,
                      double x_max, int iter, double *x1, double *x2, double *low, double *upp, double *y)
