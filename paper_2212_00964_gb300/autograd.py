@@ -73,7 +73,7 @@ class PoissonSolve:
     (A lambda = dJ/du, dJ/dtheta = M lambda), so any torch objective of u
     gets its gradient by the adjoint method, as in the paper's PDE-CO loop."""
 
-    def __init__(self, mesh, alpha=1.0, mask=None, rtol=1e-10, maxit=10000, mixed=False, dtype=torch.float64):
+    def __init__(self, mesh, alpha=1.0, mask=None, rtol=None, maxit=10000, mixed=False, dtype=torch.float64):
         self.mesh, self.alpha, self.mask = mesh, float(alpha), mask
         self.rtol, self.maxit, self.mixed, self.dtype = rtol, maxit, mixed, dtype
 

@@ -334,11 +334,20 @@ def _poisson_prec(dt, mixed):
     return _prec(dt)
 
 
-def fem_poisson_solve(m: Mesh, b, alpha=1.0, mask=None, u=None, rtol=1e-10, maxit=10000, stream=None,
+def _poisson_rtol(rtol, dt, mixed):
+    # FP32 CG stalls near 1e-7 relative, so its default is looser
+    if rtol is not None:
+        return rtol
+    return 1e-6 if (dt == torch.float32 and not mixed) else 1e-10
+
+
+def fem_poisson_solve(m: Mesh, b, alpha=1.0, mask=None, u=None, rtol=None, maxit=10000, stream=None,
                       check=True, mixed=False):
     """Jacobi-PCG for the eliminated Poisson stiffness (mixed=True: FP32 CG
-    under FP64 refinement): returns (u, iterations, ||r||/||b||)."""
+    under FP64 refinement): returns (u, iterations, ||r||/||b||).  rtol
+    defaults to 1e-10 (FP64, mixed) or 1e-6 (FP32)."""
     dt = b.dtype
+    rtol = _poisson_rtol(rtol, dt, mixed)
     u = torch.zeros_like(b) if u is None else u
     it = ctypes.c_int(0)
     res = ctypes.c_double(0.0)
@@ -351,9 +360,10 @@ def fem_poisson_solve(m: Mesh, b, alpha=1.0, mask=None, u=None, rtol=1e-10, maxi
     return u, it.value, res.value
 
 
-def fem_poisson_adjoint(m: Mesh, dJdu, alpha=1.0, mask=None, rtol=1e-10, maxit=10000, stream=None, mixed=False):
+def fem_poisson_adjoint(m: Mesh, dJdu, alpha=1.0, mask=None, rtol=None, maxit=10000, stream=None, mixed=False):
     """(du/dtheta)^T dJdu for theta -> u(theta) (A u = M theta): returns (grad, lambda, iterations)."""
     dt = dJdu.dtype
+    rtol = _poisson_rtol(rtol, dt, mixed)
     lam = torch.empty_like(dJdu)
     grad = torch.empty_like(dJdu)
     it = ctypes.c_int(0)
@@ -365,11 +375,12 @@ def fem_poisson_adjoint(m: Mesh, dJdu, alpha=1.0, mask=None, rtol=1e-10, maxit=1
     return grad, lam, it.value
 
 
-def fem_poisson_gradient(m: Mesh, theta, obs, u_obs, alpha=1.0, mask=None, rtol=1e-10, maxit=10000,
+def fem_poisson_gradient(m: Mesh, theta, obs, u_obs, alpha=1.0, mask=None, rtol=None, maxit=10000,
                          stream=None, mixed=False):
     """Objective of the full-field inference problem and its adjoint
     gradient: returns dict(J, grad, u, lam, iters)."""
     dt = theta.dtype
+    rtol = _poisson_rtol(rtol, dt, mixed)
     prec = _poisson_prec(dt, mixed)
     u = torch.empty_like(theta)
     lam = torch.empty_like(theta)
