@@ -87,12 +87,12 @@ J2_HD T stress(const Consts &c, const T *eps_old, const T *sig_old, const T *H, 
     return f;
 }
 
-// d sigma for the direction dH at the state (eps_old, sig_old, H).
+// d sigma for the direction dH, given the trial deviator s, q and f of the
+// state (the linear map of the consistent tangent).
 template <typename T>
-J2_HD void dstress(const Consts &c, const T *eps_old, const T *sig_old, const T *H, const T *dH, T *dsig)
+J2_HD void dstress_at(const Consts &c, const T *s, T q, T f, const T *dH, T *dsig)
 {
-    T eps[6], s[6], sig_tr[6], q, de[6];
-    const T f = trial(c, eps_old, sig_old, H, eps, s, sig_tr, &q);
+    T de[6];
     sym6(dH, de);
     const T tr = de[0] + de[1] + de[2];
     if (!(f > (T)0)) {
@@ -106,6 +106,15 @@ J2_HD void dstress(const Consts &c, const T *eps_old, const T *sig_old, const T 
         const T dev = de[t] - (t < 3 ? tr / (T)3 : (T)0);
         dsig[t] = (t < 3 ? (T)c.K * tr : (T)0) + a * ((T)(2.0 * c.mu) * dev - b * s[t]);
     }
+}
+
+// d sigma for the direction dH at the state (eps_old, sig_old, H).
+template <typename T>
+J2_HD void dstress(const Consts &c, const T *eps_old, const T *sig_old, const T *H, const T *dH, T *dsig)
+{
+    T eps[6], s[6], sig_tr[6], q;
+    const T f = trial(c, eps_old, sig_old, H, eps, s, sig_tr, &q);
+    dstress_at(c, s, q, f, dH, dsig);
 }
 
 // Shape-function gradients of local node a at Gauss point q (box cell).
@@ -203,6 +212,37 @@ J2_HD void cell_jvp(const Consts &c, T ihx, T ihy, T ihz, T w, const T *ue, cons
         load_hist(hist, n_cells, e, q, eo, so);
         dstress(c, eo, so, H, dH, dsig);
         flux(dsig, q, ihx, ihy, ihz, w, ye);
+    }
+}
+
+// Diagonal of the element tangent, de[3a + i] = dR_{a,i} / du_{a,i}
+//   = sum_q w sum_{j,l} dN_a/dx_j (d sigma_ij / d H_il) dN_a/dx_l,
+// with the column d sigma / d H_il from the tangent along dH = e_i (x) e_l:
+// nine directions per Gauss point instead of 24 element JVPs.  Computed in
+// T from a history stored in S.
+template <typename T, typename S = T>
+J2_HD void cell_diag(const Consts &c, T ihx, T ihy, T ihz, T w, const T *ue, const S *hist, int64_t n_cells,
+                     int64_t e, T *de)
+{
+    for (int t = 0; t < 24; ++t) de[t] = (T)0;
+    for (int q = 0; q < 8; ++q) {
+        T H[9], eo[6], so[6], eps[6], s[6], sig_tr[6], qv;
+        grad_at(ue, q, ihx, ihy, ihz, H);
+        load_hist(hist, n_cells, e, q, eo, so);
+        const T f = trial(c, eo, so, H, eps, s, sig_tr, &qv);
+        T g[8][3];
+        for (int a = 0; a < 8; ++a) grad_n(a, q, ihx, ihy, ihz, g[a]);
+        for (int i = 0; i < 3; ++i)
+            for (int l = 0; l < 3; ++l) {
+                T dH[9] = {};
+                dH[3 * i + l] = (T)1;
+                T ds[6];
+                dstress_at(c, s, qv, f, dH, ds);
+                // row i of the symmetric d sigma: (d sigma_i0, d sigma_i1, d sigma_i2)
+                const T M[9] = {ds[0], ds[5], ds[4], ds[5], ds[1], ds[3], ds[4], ds[3], ds[2]};
+                for (int a = 0; a < 8; ++a)
+                    de[3 * a + i] += w * g[a][l] * (M[3 * i] * g[a][0] + M[3 * i + 1] * g[a][1] + M[3 * i + 2] * g[a][2]);
+            }
     }
 }
 

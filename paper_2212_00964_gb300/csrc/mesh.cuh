@@ -9,12 +9,12 @@ namespace femgb {
 
 // Named device buffers that grow on demand and are never shrunk.
 // Slots 0..31 belong to the solvers, WS_BICG0.. to the assembled-matrix
-// solver, 48..63 to the scalar Poisson path, 64..79 and 88..95 to J2
+// solver, 48..63 to the scalar Poisson path, 64..79 and 88..96 to J2
 // plasticity, 80..87 to the topology-optimisation step.
 enum { WS_BICG0 = 32 };
 
 struct Workspace {
-    enum { N_SLOTS = 96 };
+    enum { N_SLOTS = 97 };
     void *ptr[N_SLOTS] = {};
     size_t cap[N_SLOTS] = {};
 

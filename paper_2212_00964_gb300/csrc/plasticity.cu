@@ -1,8 +1,8 @@
 // plasticity.cu -- perfect J2 plasticity (Sec. 2.3, Eqs. (14)-(15)) on the
 // GPU: the residual with its Gauss-point history, the consistent tangent
 // (matrix-free), its Jacobi diagonal, and one load step of Newton with
-// device-scalar PCG (dev_pcg.cuh).  Residual, history and diagonal in FP64;
-// the tangent and CG in FP64, or in FP32 in the mixed mode.
+// device-scalar PCG (dev_pcg.cuh).  Residual and history in FP64; the
+// tangent, its diagonal and CG in FP64, or in FP32 in the mixed mode.
 //
 // One thread per cell: it gathers the 24 nodal values, runs the per-cell
 // arithmetic of j2_core.cuh (8 Gauss points, return map, flux) and scatters
@@ -29,7 +29,7 @@ constexpr int MAX_ITERS = 1000000;
 
 enum { WS_JR = 64, WS_JB, WS_JDU, WS_JD, WS_JDINV, WS_JHN, WS_JCR, WS_JCZ, WS_JCP, WS_JCQ, WS_JSC, WS_JSMALL };
 // FP32 buffers of the mixed-precision correction
-enum { WS_JB32 = 88, WS_JDU32, WS_JDINV32, WS_JCR32, WS_JCZ32, WS_JCP32, WS_JCQ32 };
+enum { WS_JB32 = 88, WS_JDU32, WS_JDINV32, WS_JCR32, WS_JCZ32, WS_JCP32, WS_JCQ32, WS_JD32 };
 
 struct Geo {
     int nx, ny, nz;
@@ -118,23 +118,24 @@ __global__ void __launch_bounds__(CB) k_j2_apply(Geo g, const double *__restrict
     }
 }
 
-// d += diagonal of the element tangents (one unit-vector JVP per local DOF)
+// d += diagonal of the element tangents (closed form, j2::cell_diag),
+// computed in T from the FP64 state
+template <typename T>
 __global__ void __launch_bounds__(CB) k_j2_diag(Geo g, const double *__restrict__ u, const double *__restrict__ hist,
-                                               double *d)
+                                               T *d)
 {
     for (int64_t e = blockIdx.x * (int64_t)CB + threadIdx.x; e < g.ne; e += (int64_t)gridDim.x * CB) {
         int i, j, k;
         cell_ijk(g, e, i, j, k);
-        double ue[24], xe[24], ye[24];
+        T ue[24], de[24];
         for (int a = 0; a < 8; ++a) {
             const int64_t n = j2::cell_node(i, j, k, a, g.nx, g.ny);
-            for (int t = 0; t < 3; ++t) ue[3 * a + t] = u[3 * n + t];
+            for (int t = 0; t < 3; ++t) ue[3 * a + t] = (T)u[3 * n + t];
         }
-        for (int c = 0; c < 24; ++c) {
-            for (int t = 0; t < 24; ++t) xe[t] = t == c ? 1.0 : 0.0;
-            j2::cell_jvp<double>(g.c, g.ihx, g.ihy, g.ihz, g.w, ue, xe, hist, g.ne, e, ye);
-            const int64_t n = j2::cell_node(i, j, k, c / 3, g.nx, g.ny);
-            atomicAdd(&d[3 * n + c % 3], ye[c]);
+        j2::cell_diag<T, double>(g.c, (T)g.ihx, (T)g.ihy, (T)g.ihz, (T)g.w, ue, hist, g.ne, e, de);
+        for (int a = 0; a < 8; ++a) {
+            const int64_t n = j2::cell_node(i, j, k, a, g.nx, g.ny);
+            for (int t = 0; t < 3; ++t) atomicAdd(&d[3 * n + t], de[3 * a + t]);
         }
     }
 }
@@ -174,11 +175,10 @@ __global__ void __launch_bounds__(VB) k_j2_mask_norm(double *__restrict__ R, con
 }
 
 template <typename T>
-__global__ void k_j2_dinv(const double *__restrict__ d, const uint8_t *__restrict__ mask, T *__restrict__ dinv,
-                          int64_t D)
+__global__ void k_j2_dinv(const T *__restrict__ d, const uint8_t *__restrict__ mask, T *__restrict__ dinv, int64_t D)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < D; i += (int64_t)gridDim.x * blockDim.x)
-        dinv[i] = (T)((mask && mask[i]) ? 1.0 : (d[i] != 0.0 ? 1.0 / d[i] : 0.0));
+        dinv[i] = (mask && mask[i]) ? (T)1 : (d[i] != (T)0 ? (T)1 / d[i] : (T)0);
 }
 
 // b32 = (float) b
@@ -306,8 +306,9 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
     if (!R || !b || !du || !dg || !dinv || !hn || !w.r || !w.z || !w.p || !w.q || !w.sc || !small)
         return FEM_ERR_NOMEM;
     dpcg::Buffers<float> w32{};
-    float *b32 = nullptr, *du32 = nullptr, *dinv32 = nullptr;
+    float *b32 = nullptr, *du32 = nullptr, *dinv32 = nullptr, *dg32 = nullptr;
     if (mixed) {
+        dg32 = (float *)m->ws.get(WS_JD32, sizeof(float) * D);
         b32 = (float *)m->ws.get(WS_JB32, sizeof(float) * D);
         du32 = (float *)m->ws.get(WS_JDU32, sizeof(float) * D);
         dinv32 = (float *)m->ws.get(WS_JDINV32, sizeof(float) * D);
@@ -317,7 +318,7 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
         w32.q = (float *)m->ws.get(WS_JCQ32, sizeof(float) * D);
         w32.sc = w.sc;
         w32.small = w.small;
-        if (!b32 || !du32 || !dinv32 || !w32.r || !w32.z || !w32.p || !w32.q) return FEM_ERR_NOMEM;
+        if (!b32 || !du32 || !dinv32 || !dg32 || !w32.r || !w32.z || !w32.p || !w32.q) return FEM_ERR_NOMEM;
     }
     struct Ops {
         const Geo &g;
@@ -326,7 +327,7 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
         double *u, *hist, *R, *b, *du, *dg, *dinv, *hn, *small;
         const dpcg::Buffers<double> &w;
         const dpcg::Buffers<float> &w32;
-        float *b32, *du32, *dinv32;
+        float *b32, *du32, *dinv32, *dg32;
         bool mixed;
         double cg_rtol;
         int cg_maxit;
@@ -358,14 +359,13 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
         {
             // Jacobi diagonal of the tangent at u, then K du = -R by PCG, u += du;
             // mixed: tangent, CG vectors and du in FP32 (the residual stays FP64)
-            FEM_CUDA(cudaMemsetAsync(dg, 0, sizeof(double) * g.dofs, s));
-            k_j2_diag<<<cell_grid(g.ne), CB, 0, s>>>(g, u, hist, dg);
-            count_launch();
             int rc;
             if (mixed) {
-                k_j2_dinv<float><<<vec_grid(g.dofs), VB, 0, s>>>(dg, mask, dinv32, g.dofs);
+                FEM_CUDA(cudaMemsetAsync(dg32, 0, sizeof(float) * g.dofs, s));
+                k_j2_diag<float><<<cell_grid(g.ne), CB, 0, s>>>(g, u, hist, dg32);
+                k_j2_dinv<float><<<vec_grid(g.dofs), VB, 0, s>>>(dg32, mask, dinv32, g.dofs);
                 k_j2_to_f32<<<vec_grid(g.dofs), VB, 0, s>>>(b, b32, g.dofs);
-                count_launch(2);
+                count_launch(3);
                 FEM_CUDA(cudaMemsetAsync(du32, 0, sizeof(float) * g.dofs, s));
                 auto apply = [&](const float *x, float *y, double *dot) -> int {
                     return apply_launch<float>(g, mask, u, hist, x, y, dot, s);
@@ -375,8 +375,10 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
                 if (rc != FEM_OK) return rc;
                 k_j2_axpy<float><<<vec_grid(g.dofs), VB, 0, s>>>(u, du32, g.dofs);
             } else {
+                FEM_CUDA(cudaMemsetAsync(dg, 0, sizeof(double) * g.dofs, s));
+                k_j2_diag<double><<<cell_grid(g.ne), CB, 0, s>>>(g, u, hist, dg);
                 k_j2_dinv<double><<<vec_grid(g.dofs), VB, 0, s>>>(dg, mask, dinv, g.dofs);
-                count_launch();
+                count_launch(2);
                 FEM_CUDA(cudaMemsetAsync(du, 0, sizeof(double) * g.dofs, s));
                 auto apply = [&](const double *x, double *y, double *dot) -> int {
                     return apply_launch<double>(g, mask, u, hist, x, y, dot, s);
@@ -398,8 +400,8 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
         }
         void fail(const char *what) { set_error(std::string("fem_j2_step: ") + what); }
     };
-    Ops ops{g, mask, u_bar, u, hist, R, b, du, dg, dinv, hn, small, w, w32, b32, du32, dinv32, mixed, cg_rtol, cg_maxit,
-            hb, s};
+    Ops ops{g,  mask, u_bar, u, hist, R, b, du, dg, dinv, hn, small, w, w32, b32, du32, dinv32, dg32, mixed, cg_rtol,
+            cg_maxit, hb, s};
     const double h = std::min(1.0 / g.ihx, std::min(1.0 / g.ihy, 1.0 / g.ihz));
     return j2::newton_step(ops, mat->E, h, newton_rtol, newton_maxit, newton_iters, cg_iters, n_yield);
 }

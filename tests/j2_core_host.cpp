@@ -77,4 +77,35 @@ void host_j2_apply(int nx, int ny, int nz, double lx, double ly, double lz, doub
         for (int64_t d = 0; d < 3 * nn; ++d)
             if (mask[d]) y[d] = x[d];
 }
+
+// d = diagonal of the assembled tangent (no mask), summed over cells.
+void host_j2_diag(int nx, int ny, int nz, double lx, double ly, double lz, double E, double nu, double sy,
+                  const double *u, const double *hist, double *d, int fp32)
+{
+    const Consts c = consts(E, nu, sy);
+    const double hx = lx / nx, hy = ly / ny, hz = lz / nz;
+    const int64_t ne = (int64_t)nx * ny * nz, nn = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+    for (int64_t t = 0; t < 3 * nn; ++t) d[t] = 0.0;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const int64_t e = i + (int64_t)nx * (j + (int64_t)ny * k);
+                double de[24];
+                if (fp32) {
+                    float ue[24], df[24];
+                    for (int a = 0; a < 8; ++a)
+                        for (int t = 0; t < 3; ++t) ue[3 * a + t] = (float)u[3 * cell_node(i, j, k, a, nx, ny) + t];
+                    cell_diag<float, double>(c, (float)(1.0 / hx), (float)(1.0 / hy), (float)(1.0 / hz),
+                                             (float)(hx * hy * hz / 8.0), ue, hist, ne, e, df);
+                    for (int t = 0; t < 24; ++t) de[t] = df[t];
+                } else {
+                    double ue[24];
+                    for (int a = 0; a < 8; ++a)
+                        for (int t = 0; t < 3; ++t) ue[3 * a + t] = u[3 * cell_node(i, j, k, a, nx, ny) + t];
+                    cell_diag<double, double>(c, 1.0 / hx, 1.0 / hy, 1.0 / hz, hx * hy * hz / 8.0, ue, hist, ne, e, de);
+                }
+                for (int a = 0; a < 8; ++a)
+                    for (int t = 0; t < 3; ++t) d[3 * cell_node(i, j, k, a, nx, ny) + t] += de[3 * a + t];
+            }
+}
 }

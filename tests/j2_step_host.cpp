@@ -102,21 +102,24 @@ struct CpuStep {
     }
     int correction(int *cg_it)
     {
-        dg.assign(g.D, 0.0);
-        for_cells(g, [&](int i, int j, int k, int64_t e) {
-            double ue[24], xe[24], ye[24];
-            for (int a = 0; a < 8; ++a)
-                for (int t = 0; t < 3; ++t) ue[3 * a + t] = u[3 * j2::cell_node(i, j, k, a, g.nx, g.ny) + t];
-            for (int c = 0; c < 24; ++c) {
-                for (int t = 0; t < 24; ++t) xe[t] = t == c ? 1.0 : 0.0;
-                j2::cell_jvp<double>(g.c, g.ihx, g.ihy, g.ihz, g.w, ue, xe, hist, g.ne, e, ye);
-                dg[3 * j2::cell_node(i, j, k, c / 3, g.nx, g.ny) + c % 3] += ye[c];
-            }
-        });
-        dinv.assign(g.D, 0.0);
-        for (int64_t d = 0; d < g.D; ++d) dinv[d] = mask[d] ? 1.0 : (dg[d] != 0.0 ? 1.0 / dg[d] : 0.0);
+        // the closed-form element diagonal in the CG's precision, as k_j2_diag<T> + k_j2_dinv<T>
+        auto diag_inv = [&](auto zero, auto &out) {
+            using T = decltype(zero);
+            std::vector<T> d(g.D, (T)0);
+            for_cells(g, [&](int i, int j, int k, int64_t e) {
+                T ue[24], de[24];
+                for (int a = 0; a < 8; ++a)
+                    for (int t = 0; t < 3; ++t) ue[3 * a + t] = (T)u[3 * j2::cell_node(i, j, k, a, g.nx, g.ny) + t];
+                j2::cell_diag<T, double>(g.c, (T)g.ihx, (T)g.ihy, (T)g.ihz, (T)g.w, ue, hist, g.ne, e, de);
+                for (int a = 0; a < 8; ++a)
+                    for (int t = 0; t < 3; ++t) d[3 * j2::cell_node(i, j, k, a, g.nx, g.ny) + t] += de[3 * a + t];
+            });
+            out.assign(g.D, (T)0);
+            for (int64_t q = 0; q < g.D; ++q) out[q] = mask[q] ? (T)1 : (d[q] != (T)0 ? (T)1 / d[q] : (T)0);
+        };
         if (mixed) {
-            std::vector<float> dinv32(dinv.begin(), dinv.end()), b32(b.begin(), b.end()), du32(g.D, 0.0f);
+            std::vector<float> dinv32, b32(b.begin(), b.end()), du32(g.D, 0.0f);
+            diag_inv(0.0f, dinv32);
             CpuPcg<float> pcg{g.D, [&](const float *x, float *y, double *dot) { apply<float>(x, y, dot); },
                               dinv32.data(), b32.data(), du32.data(), cg_maxit};
             const int rc = dpcg::control(pcg, cg_rtol, cg_maxit, cg_it, nullptr);
@@ -127,6 +130,7 @@ struct CpuStep {
             for (int64_t d = 0; d < g.D; ++d) u[d] += (double)du32[d];
             return 0;
         }
+        diag_inv(0.0, dinv);
         du.assign(g.D, 0.0);
         CpuPcg<double> pcg{g.D, [&](const double *x, double *y, double *dot) { apply<double>(x, y, dot); },
                            dinv.data(), b.data(), du.data(), cg_maxit};

@@ -39,6 +39,7 @@ def core():
     L.host_j2_residual.argtypes = [I, I, I, D, D, D, D, D, D, P, P, P, P, P]
     L.host_j2_residual.restype = I64
     L.host_j2_apply.argtypes = [I, I, I, D, D, D, D, D, D, P, P, P, P, P]
+    L.host_j2_diag.argtypes = [I, I, I, D, D, D, D, D, D, P, P, P, I]
     return L
 
 
@@ -136,3 +137,21 @@ def test_cell_residual_and_tangent_over_a_box(core, dims):
     core.host_j2_apply(nx, ny, nz, lx, ly, lz, MAT.E, MAT.nu, MAT.sy, p(u), p(h), p(x), p(mask), p(y))
     y_ref = pl.tangent_apply(m, MAT, hist, u, x, mask)
     assert np.abs(y - y_ref).max() <= 1e-10 * np.abs(y_ref).max()
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_cell_diagonal_equals_the_assembled_diagonal(core, fp32):
+    """The closed-form element diagonal (nine tangent directions per Gauss
+    point) summed over a box = the diagonal of the oracle's assembled
+    tangent, on a partly yielded state; in FP32 to float rounding."""
+    nx, ny, nz, lx, ly, lz = 3, 2, 2, 1.2, 0.8, 0.6
+    m = oracle.mesh(nx, ny, nz, lx, ly, lz)
+    rng = np.random.default_rng(31)
+    hist, u1 = random_history(m, rng, 6e-4)
+    u = u1 + 3e-4 * rng.standard_normal(m.n_dofs)
+    _, _, n_y = pl.residual(m, MAT, hist, u)
+    assert 0 < n_y < 8 * m.n_cells
+    d = np.zeros(m.n_dofs)
+    core.host_j2_diag(nx, ny, nz, lx, ly, lz, MAT.E, MAT.nu, MAT.sy, p(u), p(to_soa(hist)), p(d), fp32)
+    ref = pl.assemble(m, MAT, hist, u).diagonal()
+    assert np.abs(d - ref).max() <= (2e-6 if fp32 else 1e-12) * np.abs(ref).max()
