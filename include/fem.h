@@ -261,7 +261,8 @@ int fem_j2_tangent_apply(fem_mesh_t m, const fem_j2_material *mat, const uint8_t
  * the free DOFs of u start from their values on entry.  precision FEM_FP64,
  * or FEM_MIXED: the tangent apply, the CG vectors and the correction in FP32
  * (the residual, history, diagonal and u stay FP64; an FP32 correction is
- * an inexact Newton step, so cg_rtol of about 1e-4 suits it).  On success
+ * an inexact Newton step, so cg_rtol of about 1e-4 suits it).  An inner
+ * solve that stops at cg_maxit still supplies its correction.  On success
  * hist becomes (eps^k, sigma^k) at the converged u.  newton_iters, cg_iters,
  * n_yield (host, may be NULL): Newton iterations, total CG iterations,
  * yielding Gauss points.  FEM_ERR_NOT_CONVERGED after newton_maxit (hist

@@ -372,7 +372,8 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
                 };
                 rc = dpcg::solve<float>(s, g.dofs, apply, dinv32, b32, du32, w32, cg_rtol, cg_maxit, cg_it, nullptr,
                                         "fem_j2_step");
-                if (rc != FEM_OK) return rc;
+                // a truncated inner solve still gives a usable (inexact) Newton correction
+                if (rc != FEM_OK && rc != FEM_ERR_NOT_CONVERGED) return rc;
                 k_j2_axpy<float><<<vec_grid(g.dofs), VB, 0, s>>>(u, du32, g.dofs);
             } else {
                 FEM_CUDA(cudaMemsetAsync(dg, 0, sizeof(double) * g.dofs, s));
@@ -385,7 +386,7 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
                 };
                 rc = dpcg::solve<double>(s, g.dofs, apply, dinv, b, du, w, cg_rtol, cg_maxit, cg_it, nullptr,
                                          "fem_j2_step");
-                if (rc != FEM_OK) return rc;
+                if (rc != FEM_OK && rc != FEM_ERR_NOT_CONVERGED) return rc;
                 k_j2_axpy<double><<<vec_grid(g.dofs), VB, 0, s>>>(u, du, g.dofs);
             }
             count_launch();

@@ -123,7 +123,7 @@ struct CpuStep {
             CpuPcg<float> pcg{g.D, [&](const float *x, float *y, double *dot) { apply<float>(x, y, dot); },
                               dinv32.data(), b32.data(), du32.data(), cg_maxit};
             const int rc = dpcg::control(pcg, cg_rtol, cg_maxit, cg_it, nullptr);
-            if (rc) {
+            if (rc && rc != dpcg::ST_NOT_CONVERGED) {
                 err = pcg.err;
                 return rc;
             }
@@ -135,7 +135,7 @@ struct CpuStep {
         CpuPcg<double> pcg{g.D, [&](const double *x, double *y, double *dot) { apply<double>(x, y, dot); },
                            dinv.data(), b.data(), du.data(), cg_maxit};
         const int rc = dpcg::control(pcg, cg_rtol, cg_maxit, cg_it, nullptr);
-        if (rc) {
+        if (rc && rc != dpcg::ST_NOT_CONVERGED) {
             err = pcg.err;
             return rc;
         }

@@ -120,3 +120,20 @@ def test_newton_limit_leaves_the_history(L):
     got = run_path(L, dims, pl.Material(70e3, 0.3, 250.0), mask, ubars[2:3], newton_maxit=0)
     rc, u, h, ni, ci, nyd = got[0]
     assert rc == -3 and "limit" in L.host_j2_step_error().decode() and np.all(h == 0)
+
+
+def test_truncated_inner_solves_still_converge(L):
+    """With at most 3 CG iterations per correction the step still reaches
+    the oracle's solution: truncated inner solves are inexact Newton steps."""
+    dims, mask, ubars = sheared_box()
+    mat = pl.Material(70e3, 0.3, 250.0)
+    nx, ny, nz, lx, ly, lz = dims
+    D = 3 * (nx + 1) * (ny + 1) * (nz + 1)
+    u, hist = np.zeros(D), np.zeros(12 * 8 * nx * ny * nz)
+    ni, ci, nyd = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    rc = L.host_j2_step(nx, ny, nz, lx, ly, lz, mat.E, mat.nu, mat.sy, p(mask), p(np.ascontiguousarray(ubars[0])),
+                        p(u), p(hist), 1e-10, 200, 1e-12, 3, 0, ctypes.byref(ni), ctypes.byref(ci), ctypes.byref(nyd))
+    assert rc == 0, L.host_j2_step_error()
+    ref = pl.solve_path(oracle.mesh(*dims), mat, mask, ubars[:1])[0][0]
+    assert np.abs(u - ref).max() <= 1e-8 * np.abs(ref).max()
+    assert ni.value > 5
