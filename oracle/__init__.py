@@ -25,7 +25,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fem_oracle.c")
-_SO = os.path.join(_HERE, "liboracle.so")
+# FEMGB_HOST_SANITIZE=1: an AddressSanitizer + UBSan build in a separate file
+# (the process must run with the ASan runtime preloaded)
+_SANITIZE = os.environ.get("FEMGB_HOST_SANITIZE") == "1"
+_SO = os.path.join(_HERE, "liboracle_san.so" if _SANITIZE else "liboracle.so")
 
 LINEAR, SIMP, NEOHOOKE = 0, 1, 2
 
@@ -36,9 +39,10 @@ def build(force: bool = False) -> str:
     """Compile fem_oracle.c with gcc -O2 -ffp-contract=off into liboracle.so."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + ".tmp%d" % os.getpid()
+        san = ["-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+               "-fno-sanitize-recover=all"] if _SANITIZE else ["-O2"]
         subprocess.check_call(
-            ["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared",
-             _SRC, "-o", tmp, "-lm"])
+            ["gcc"] + san + ["-ffp-contract=off", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 

@@ -5,29 +5,19 @@ numpy's solution, the batching of iterations between host reads, and the
 exits (already converged, zero right-hand side, iteration limit, an
 indefinite operator, non-finite input)."""
 import ctypes
-import os
-import subprocess
 
 import numpy as np
 import pytest
 
-HERE = os.path.dirname(os.path.abspath(__file__))
-ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "dpcg_control_host.cpp")
-HDR = os.path.join(ROOT, "paper_2212_00964_gb300", "csrc", "dpcg_control.h")
-SO = os.path.join(ROOT, "paper_2212_00964_gb300", "_lib", "dpcg_control_host.so")
+from tests import host_build
+
 OK, NOT_CONVERGED, BREAKDOWN, NONFINITE = 0, -3, -5, -6
 CHECK = 8
 
 
 @pytest.fixture(scope="module")
 def L():
-    os.makedirs(os.path.dirname(SO), exist_ok=True)
-    if not os.path.exists(SO) or os.path.getmtime(SO) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)):
-        tmp = SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-Wall", SRC, "-o", tmp])
-        os.replace(tmp, SO)
-    lib = ctypes.CDLL(SO)
+    lib = host_build.build("dpcg_control_host", extra_flags=[])
     P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     lib.host_pcg.argtypes = [I, P, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]
     lib.host_pcg_error.restype = ctypes.c_char_p

@@ -5,8 +5,6 @@ and the per-cell residual and tangent assembled over a box, against the
 oracle (Sec. 2.3, Eqs. (14)-(15)), with the history in the kernels'
 structure-of-arrays layout."""
 import ctypes
-import os
-import subprocess
 
 import numpy as np
 import pytest
@@ -14,24 +12,14 @@ import pytest
 import oracle
 from oracle import plasticity as pl
 from paper_2212_00964_gb300 import inputs
+from tests import host_build
 
-HERE = os.path.dirname(os.path.abspath(__file__))
-ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "j2_core_host.cpp")
-HDR = os.path.join(ROOT, "paper_2212_00964_gb300", "csrc", "j2_core.cuh")
-SO = os.path.join(ROOT, "paper_2212_00964_gb300", "_lib", "j2_core_host.so")
 MAT = pl.Material(70e3, 0.3, 250.0)
 
 
 @pytest.fixture(scope="module")
 def core():
-    os.makedirs(os.path.dirname(SO), exist_ok=True)
-    if not os.path.exists(SO) or os.path.getmtime(SO) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)):
-        tmp = SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-Wall",
-                               SRC, "-o", tmp])
-        os.replace(tmp, SO)
-    L = ctypes.CDLL(SO)
+    L = host_build.build("j2_core_host", extra_flags=['-ffp-contract=off'])
     P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
     L.host_j2_stress.argtypes = [D, D, D, P, P, P, P, P]
     L.host_j2_stress.restype = D

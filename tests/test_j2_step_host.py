@@ -5,8 +5,6 @@ for the kernels; against the oracle's load-stepped Newton with direct solves
 on the load / unload / reverse-yield path, and on a sheared box whose
 yielding is not uniform."""
 import ctypes
-import os
-import subprocess
 
 import numpy as np
 import pytest
@@ -14,24 +12,12 @@ import pytest
 import oracle
 from oracle import plasticity as pl
 from paper_2212_00964_gb300 import inputs
-
-HERE = os.path.dirname(os.path.abspath(__file__))
-ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "j2_step_host.cpp")
-CSRC = os.path.join(ROOT, "paper_2212_00964_gb300", "csrc")
-HDRS = [os.path.join(CSRC, h) for h in ("j2_core.cuh", "j2_newton.h", "dpcg_control.h")] + \
-    [os.path.join(HERE, "cpu_pcg.h")]
-SO = os.path.join(ROOT, "paper_2212_00964_gb300", "_lib", "j2_step_host.so")
+from tests import host_build
 
 
 @pytest.fixture(scope="module")
 def L():
-    os.makedirs(os.path.dirname(SO), exist_ok=True)
-    if not os.path.exists(SO) or os.path.getmtime(SO) < max(os.path.getmtime(f) for f in [SRC] + HDRS):
-        tmp = SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-Wall", SRC, "-o", tmp])
-        os.replace(tmp, SO)
-    lib = ctypes.CDLL(SO)
+    lib = host_build.build("j2_step_host", extra_flags=[])
     P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     lib.host_j2_step.argtypes = [I, I, I, D, D, D, D, D, D, P, P, P, P, D, I, D, I, I, ctypes.POINTER(I),
                                  ctypes.POINTER(I), ctypes.POINTER(ctypes.c_int64)]

@@ -4,8 +4,6 @@ tests/poisson_core_host.cpp) against the oracle's assembled operators: the
 27-class stencil tables and the row formula, index arithmetic included, on
 anisotropic boxes, one-cell-thick boxes and arbitrary masks."""
 import ctypes
-import os
-import subprocess
 
 import numpy as np
 import pytest
@@ -13,25 +11,15 @@ import pytest
 import oracle
 from oracle import poisson as op
 from paper_2212_00964_gb300 import inputs
+from tests import host_build
 
-HERE = os.path.dirname(os.path.abspath(__file__))
-ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "poisson_core_host.cpp")
-HDR = os.path.join(ROOT, "paper_2212_00964_gb300", "csrc", "poisson_core.cuh")
-SO = os.path.join(ROOT, "paper_2212_00964_gb300", "_lib", "poisson_core_host.so")
 TAB = 27 * 27
 OUT_ELIM, OUT_ZERO, OUT_PLAIN = 0, 1, 2
 
 
 @pytest.fixture(scope="module")
 def core():
-    os.makedirs(os.path.dirname(SO), exist_ok=True)
-    if not os.path.exists(SO) or os.path.getmtime(SO) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)):
-        tmp = SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-Wall",
-                               SRC, "-o", tmp])
-        os.replace(tmp, SO)
-    L = ctypes.CDLL(SO)
+    L = host_build.build("poisson_core_host", extra_flags=['-ffp-contract=off'])
     P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     L.host_tables.argtypes = [D, D, D, D, P]
     L.host_apply.argtypes = [I, I, I, P, I, I, P, P, P]

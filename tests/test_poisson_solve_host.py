@@ -4,32 +4,18 @@ the mixed-precision refinement and the objective / adjoint control
 compiled for the host through tests/poisson_solve_host.cpp, against the
 oracle's LU solves and adjoint gradient (Sec. 3.1)."""
 import ctypes
-import os
-import subprocess
 
 import numpy as np
 import pytest
 
 from oracle import poisson as op
 from paper_2212_00964_gb300 import inputs
-
-HERE = os.path.dirname(os.path.abspath(__file__))
-ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "poisson_solve_host.cpp")
-CSRC = os.path.join(ROOT, "paper_2212_00964_gb300", "csrc")
-DEPS = [SRC, os.path.join(HERE, "cpu_pcg.h")] + \
-    [os.path.join(CSRC, h) for h in ("dpcg_control.h", "poisson_control.h", "poisson_core.cuh")]
-SO = os.path.join(ROOT, "paper_2212_00964_gb300", "_lib", "poisson_solve_host.so")
+from tests import host_build
 
 
 @pytest.fixture(scope="module")
 def L():
-    os.makedirs(os.path.dirname(SO), exist_ok=True)
-    if not os.path.exists(SO) or os.path.getmtime(SO) < max(os.path.getmtime(f) for f in DEPS):
-        tmp = SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-Wall", SRC, "-o", tmp])
-        os.replace(tmp, SO)
-    lib = ctypes.CDLL(SO)
+    lib = host_build.build("poisson_solve_host", extra_flags=[])
     P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
     lib.host_poisson_solve.argtypes = [I, I, I, D, D, D, D, P, P, P, D, I, I, ctypes.POINTER(I), ctypes.POINTER(D)]
     lib.host_poisson_gradient.argtypes = [I, I, I, D, D, D, D, P, P, P, P, I64, D, I, I, P, P, P,

@@ -4,8 +4,6 @@ tests/topopt_core_host.cpp): the cone filter against the oracle's filter
 matrix, and MMA steps (the library's per-variable formulas and dual search)
 against the oracle's MMA, step by step, and in the closed-form problems."""
 import ctypes
-import os
-import subprocess
 
 import numpy as np
 import pytest
@@ -13,23 +11,12 @@ import pytest
 import oracle
 from oracle import topopt as ot
 from paper_2212_00964_gb300 import inputs
-
-HERE = os.path.dirname(os.path.abspath(__file__))
-ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "topopt_core_host.cpp")
-HDR = os.path.join(ROOT, "paper_2212_00964_gb300", "csrc", "topopt_core.cuh")
-SO = os.path.join(ROOT, "paper_2212_00964_gb300", "_lib", "topopt_core_host.so")
+from tests import host_build
 
 
 @pytest.fixture(scope="module")
 def core():
-    os.makedirs(os.path.dirname(SO), exist_ok=True)
-    if not os.path.exists(SO) or os.path.getmtime(SO) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)):
-        tmp = SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-Wall",
-                               SRC, "-o", tmp])
-        os.replace(tmp, SO)
-    L = ctypes.CDLL(SO)
+    L = host_build.build("topopt_core_host", extra_flags=['-ffp-contract=off'])
     P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
     L.host_filter.argtypes = [P, P, I, I, I, D]
     L.host_mma_step.argtypes = [I64, P, D, P, P, D, D, I, P, P, P, P, P]
