@@ -190,6 +190,25 @@ def compliance_and_gradient(m: Mesh, mat: Material, mask, f, theta, pattern=None
     return float(f @ u), g, u
 
 
+def simp_scale(theta, p=3.0, emin=1e-3):
+    """(s, ds/dtheta) of the SIMP law s = emin + theta^p (1 - emin)."""
+    theta = np.asarray(theta, np.float64)
+    return emin + theta ** p * (1 - emin), p * theta ** (p - 1) * (1 - emin)
+
+
+def compliance_and_gradient_nh(m: Mesh, E, nu, mask, f, theta, p=3.0, emin=1e-3, n_steps=1, pattern=None,
+                               rtol=1e-12):
+    """(c, dc/dtheta, u) for SIMP applied to the Neo-Hookean law, the
+    paper's plate (Eqs. (29)-(30): theta^p P): the per-cell stiffness scale
+    is s(theta) (both moduli scale with E, so s P(F; E) = P(F; s E)); the
+    adjoint gives dc/ds, and dc/dtheta = dc/ds ds/dtheta."""
+    mat = Material(2, E, nu)
+    s, ds = simp_scale(theta, p, emin)
+    u = osolve.newton_solve(m, mat, mask, np.zeros(m.n_dofs), f, s, n_steps=n_steps, pattern=pattern, rtol=rtol)
+    g_s, _ = osolve.adjoint_gradient(m, mat, mask, u, f, s, pattern=pattern)
+    return float(f @ u), g_s * ds, u
+
+
 def optimise(m: Mesh, mat: Material, mask, f, volfrac=0.5, rmin=1.5, n_iter=30, theta_min=0.0,
              history=None):
     """The design loop (steps 1-4 above) from the uniform design theta =

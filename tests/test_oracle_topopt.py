@@ -190,3 +190,29 @@ def test_oc_move_limit_and_bounds():
     y, _ = ot.oc_step(x, g, np.ones(4), 0.5, move=0.1, x_min=0.0, x_max=1.0)
     assert np.all(y >= np.maximum(0, x - 0.1) - 1e-15) and np.all(y <= np.minimum(1, x + 0.1) + 1e-15)
     assert y[0] == 0.6 and y[1] == 0.4
+
+
+def test_hyperelastic_simp_gradient_central_differences():
+    """SIMP on the Neo-Hookean law (the paper's plate): the chain-ruled
+    adjoint gradient against central differences of the compliance, and the
+    small-load limit where it matches the linear-elastic SIMP gradient."""
+    w = inputs.topopt_cantilever(nx=4, ny=4, nz=4, lx=2.0, ly=1.0, lz=1.0)
+    m = oracle.mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)
+    rng = np.random.default_rng(41)
+    theta = rng.uniform(0.3, 1.0, m.n_cells)
+    f = w.point_load * 2e-3  # tip deflection of a few percent of the depth: mildly nonlinear
+    c, g, _ = ot.compliance_and_gradient_nh(m, 1.0, 0.3, w.mask, f, theta)
+    h = 1e-6
+    for e in (0, 21, 42, 63):
+        tp, tm = theta.copy(), theta.copy()
+        tp[e] += h
+        tm[e] -= h
+        fd = (ot.compliance_and_gradient_nh(m, 1.0, 0.3, w.mask, f, tp)[0] -
+              ot.compliance_and_gradient_nh(m, 1.0, 0.3, w.mask, f, tm)[0]) / (2 * h)
+        assert abs(fd - g[e]) <= 1e-5 * np.abs(g).max()
+    # tiny load: the hyperelastic compliance gradient approaches the linear one
+    mat = oracle.Material(oracle.SIMP, 1.0, 0.3, 3.0, 1e-3)
+    f_small = w.point_load * 1e-6
+    _, g_nh, _ = ot.compliance_and_gradient_nh(m, 1.0, 0.3, w.mask, f_small, theta, rtol=1e-8)
+    _, g_le, _ = ot.compliance_and_gradient(m, mat, w.mask, f_small, theta)
+    assert np.abs(g_nh - g_le).max() <= 1e-4 * np.abs(g_le).max()
