@@ -74,8 +74,8 @@ TO_HD double filter_weight_sum(int64_t e, int nx, int ny, int nz, double rmin)
 
 // The transpose of the normalised filter at cell e: sum_f w_fe g_f / Hs_f
 // (the weights are symmetric), the chain rule of a filter applied to the
-// density.
-TO_HD double filter_cell_t(const double *g, int64_t e, int nx, int ny, int nz, double rmin)
+// density; hs[f] = filter_weight_sum(f) precomputed.
+TO_HD double filter_cell_t(const double *g, const double *hs, int64_t e, int nx, int ny, int nz, double rmin)
 {
     const int64_t nxy = (int64_t)nx * ny;
     const int k = (int)(e / nxy);
@@ -91,7 +91,7 @@ TO_HD double filter_cell_t(const double *g, int64_t e, int nx, int ny, int nz, d
                 const double w = rmin - sqrt(di * di + dj * dj + dk * dk);
                 if (w > 0.0) {
                     const int64_t f = ii + (int64_t)nx * (jj + (int64_t)ny * kk);
-                    acc += w * g[f] / filter_weight_sum(f, nx, ny, nz, rmin);
+                    acc += w * g[f] / hs[f];
                 }
             }
     return acc;

@@ -18,10 +18,13 @@ void host_filter(const double *g, double *out, int nx, int ny, int nz, double rm
     for (int64_t e = 0; e < n; ++e) out[e] = filter_cell(g, e, nx, ny, nz, rmin);
 }
 
+// Mirrors fem_density_filter with transpose: the row sums first, then the rows.
 void host_filter_t(const double *g, double *out, int nx, int ny, int nz, double rmin)
 {
     const int64_t n = (int64_t)nx * ny * nz;
-    for (int64_t e = 0; e < n; ++e) out[e] = filter_cell_t(g, e, nx, ny, nz, rmin);
+    std::vector<double> hs(n);
+    for (int64_t e = 0; e < n; ++e) hs[e] = filter_weight_sum(e, nx, ny, nz, rmin);
+    for (int64_t e = 0; e < n; ++e) out[e] = filter_cell_t(g, hs.data(), e, nx, ny, nz, rmin);
 }
 
 // Mirrors fem_oc_step: returns the multiplier.
