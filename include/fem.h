@@ -257,7 +257,8 @@ int fem_j2_tangent_apply(fem_mesh_t m, const fem_j2_material *mat, const uint8_t
 /* One load step: u_c = u_bar_c on masked DOFs, then Newton on the free DOFs
  * with Jacobi-PCG on the consistent tangent (tolerance cg_rtol, at most
  * cg_maxit <= 1e6 iterations per Newton step) until ||r|| <= newton_rtol *
- * max(||r|| of the first iteration, E h^2 1e-12), h the smallest cell edge;
+ * max(||r|| of the first iteration, sigma_y h^2), h the smallest cell edge
+ * (the yield force of one cell face: a step with no load change ends);
  * the free DOFs of u start from their values on entry.  precision FEM_FP64,
  * or FEM_MIXED: the tangent apply, the CG vectors and the correction in FP32
  * (the residual, history, diagonal and u stay FP64; an FP32 correction is

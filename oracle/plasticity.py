@@ -9,9 +9,11 @@ R(u^k; history) = 0 with the consistent tangent of the return map; the
 linear step is ``scipy.sparse.linalg.spsolve`` on the free-free block of the
 assembled tangent.  Once converged, the history becomes (eps^k, sigma^k).
 Readings (the paper gives none of these): the Newton stop is
-||R_free|| <= rtol * max(||R_free|| at iteration 0 of the step, the scale
-E * h^2 * 1e-12 for a step with no load change); the first iterate of a step
-is the previous converged state with the new prescribed values.
+||R_free|| <= rtol * max(||R_free|| at iteration 0 of the step, sigma_y h^2),
+h the smallest cell edge: the yield force of one cell face is the floor, so
+a step with little or no load change, whose first residual is at the
+rounding level of the internal forces, still ends; the first iterate of a
+step is the previous converged state with the new prescribed values.
 """
 from __future__ import annotations
 
@@ -118,7 +120,7 @@ def newton_step(m: Mesh, mat: Material, hist, mask, u_bar, u0, rtol=1e-12, maxit
         R, new_hist, n_yield = residual(m, mat, hist, u, mask)
         nrm = float(np.linalg.norm(R))
         if ref is None:
-            ref = max(nrm, mat.E * h * h * 1e-12)
+            ref = max(nrm, mat.sy * h * h)
         if nrm <= rtol * ref:
             return u, new_hist, n_yield, it
         K = assemble(m, mat, hist, u)

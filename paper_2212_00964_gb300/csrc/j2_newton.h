@@ -22,12 +22,14 @@
 namespace femgb {
 namespace j2 {
 
-// Converged when ||r|| <= newton_rtol * max(||r|| of iteration 0, E h^2 1e-12)
-// (h the smallest cell edge); the states returned at the converged u become
-// the history.  ST_NOT_CONVERGED after newton_maxit corrections (history
+// Converged when ||r|| <= newton_rtol * max(||r|| of iteration 0, sigma_y h^2)
+// (h the smallest cell edge: the yield force of one cell face is the floor,
+// so a step whose first residual is already at the rounding level of the
+// internal forces ends); the states returned at the converged u become the
+// history.  ST_NOT_CONVERGED after newton_maxit corrections (history
 // unchanged).
 template <typename Ops>
-int newton_step(Ops &ops, double E, double h, double newton_rtol, int newton_maxit, int *newton_iters,
+int newton_step(Ops &ops, double sigma_y, double h, double newton_rtol, int newton_maxit, int *newton_iters,
                 int *cg_iters, int64_t *n_yield)
 {
     if (int rc = ops.prescribe()) return rc;
@@ -41,7 +43,7 @@ int newton_step(Ops &ops, double E, double h, double newton_rtol, int newton_max
             ops.fail("non-finite residual");
             return dpcg::ST_NONFINITE;
         }
-        if (ref < 0) ref = std::max(nrm, E * h * h * 1e-12);
+        if (ref < 0) ref = std::max(nrm, sigma_y * h * h);
         if (newton_iters) *newton_iters = it;
         if (cg_iters) *cg_iters = cg_total;
         if (nrm <= newton_rtol * ref) {

@@ -404,5 +404,5 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
     Ops ops{g,  mask, u_bar, u, hist, R, b, du, dg, dinv, hn, small, w, w32, b32, du32, dinv32, dg32, mixed, cg_rtol,
             cg_maxit, hb, s};
     const double h = std::min(1.0 / g.ihx, std::min(1.0 / g.ihy, 1.0 / g.ihz));
-    return j2::newton_step(ops, mat->E, h, newton_rtol, newton_maxit, newton_iters, cg_iters, n_yield);
+    return j2::newton_step(ops, mat->sigma_y, h, newton_rtol, newton_maxit, newton_iters, cg_iters, n_yield);
 }

@@ -170,7 +170,7 @@ int host_j2_step(int nx, int ny, int nz, double lx, double ly, double lz, double
     g.c = j2::consts(E, nu, sy);
     CpuStep ops{g, mask, u_bar, u, hist, cg_rtol, cg_maxit, mixed != 0};
     const double h = std::min(hx, std::min(hy, hz));
-    const int rc = j2::newton_step(ops, E, h, newton_rtol, newton_maxit, newton_iters, cg_iters, n_yield);
+    const int rc = j2::newton_step(ops, sy, h, newton_rtol, newton_maxit, newton_iters, cg_iters, n_yield);
     last_err = ops.err;
     return rc;
 }

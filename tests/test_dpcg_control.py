@@ -89,3 +89,11 @@ def test_non_finite_input(L):
     b[3] = np.nan
     rc, _, it, _, _, err = run(L, A, b)
     assert rc == NONFINITE and "non-finite" in err
+
+
+def test_zero_iteration_limit(L):
+    A = spd(10, 9)
+    rc, u, it, res, calls, err = run(L, A, np.ones(10), maxit=0)
+    assert rc == NOT_CONVERGED and it == 0 and calls == 0 and np.all(u == 0)
+    rc, u, it, res, calls, err = run(L, A, np.zeros(10), maxit=0)
+    assert rc == OK and it == 0

@@ -123,3 +123,27 @@ def test_truncated_inner_solves_still_converge(L):
     ref = pl.solve_path(oracle.mesh(*dims), mat, mask, ubars[:1])[0][0]
     assert np.abs(u - ref).max() <= 1e-8 * np.abs(ref).max()
     assert ni.value > 5
+
+
+def test_edge_cases(L):
+    """A one-cell box; a load step that changes nothing (converged at
+    iteration 0, history kept); a step back to the virgin state."""
+    mat = pl.Material(70e3, 0.3, 250.0)
+    mask, ubars, strains, _ = inputs.j2_uniaxial(n=1)
+    got = run_path(L, (1, 1, 1, 1.0, 1.0, 1.0), mat, mask, ubars[:4])
+    ref = pl.solve_path(oracle.mesh(1, 1, 1), mat, mask, ubars[:4])
+    for (rc, u, h, ni, ci, nyd), (u_ref, hist_ref, ny_ref) in zip(got, ref):
+        assert rc == 0 and np.abs(u - u_ref).max() <= 1e-10 * np.abs(u_ref).max()
+    # repeating the last prescribed state: nothing to do
+    rc, u, h, ni, ci, nyd = got[-1]
+    again = run_path(L, (1, 1, 1, 1.0, 1.0, 1.0), mat, mask, [ubars[3]] * 1)
+    assert again[0][0] == 0
+    D = 3 * 8
+    uu, hh = u.copy(), h.copy()
+    ni2, ci2, ny2 = ctypes.c_int(-1), ctypes.c_int(-1), ctypes.c_int64(-1)
+    rc = L.host_j2_step(1, 1, 1, 1.0, 1.0, 1.0, mat.E, mat.nu, mat.sy, p(mask), p(np.ascontiguousarray(ubars[3])),
+                        p(uu), p(hh), 1e-12, 30, 1e-12, 1000, 0, ctypes.byref(ni2), ctypes.byref(ci2),
+                        ctypes.byref(ny2))
+    assert rc == 0 and ni2.value == 0 and ci2.value == 0
+    assert np.array_equal(uu, u) and np.abs(hh - h).max() <= 1e-12 * np.abs(h).max()
+    assert uu.size == D

@@ -83,3 +83,31 @@ def test_bad_observation_and_iteration_limit(L):
     rc = L.host_poisson_solve(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, w.alpha, p(w.mask), p(b), p(np.zeros(m.n_nodes)),
                               1e-12, 5, 1, ctypes.byref(it), ctypes.byref(res))
     assert rc == -3 and it.value == 5 and "limit" in L.host_poisson_error().decode()
+
+
+def test_edge_cases(L):
+    """No observations (J = 0, zero gradient, zero adjoint iterations); a
+    one-cell box whose every node is prescribed (u = b, no CG iteration);
+    maxit = 0 on an unsolved system."""
+    w = workload()
+    m, _ = op.from_workload(w)
+    n = m.n_nodes
+    u, lam, g = np.zeros(n), np.ones(n), np.ones(n)
+    J, its = ctypes.c_double(-1.0), (ctypes.c_int * 2)()
+    empty = np.zeros(0, np.int64)
+    rc = L.host_poisson_gradient(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, w.alpha, p(w.mask), p(np.ones(n)), p(empty),
+                                 p(np.zeros(0)), 0, 1e-10, 1000, 0, p(u), p(lam), p(g), ctypes.byref(J), its)
+    assert rc == 0 and J.value == 0.0 and its[1] == 0 and np.all(lam == 0) and np.all(g == 0)
+    mask1 = np.ones(8, np.uint8)
+    b1 = np.arange(8, dtype=np.float64)
+    u1 = np.zeros(8)
+    it, res = ctypes.c_int(-1), ctypes.c_double(-1)
+    for mixed in (0, 1):
+        u1[:] = 0
+        rc = L.host_poisson_solve(1, 1, 1, 1.0, 1.0, 1.0, 1.0, p(mask1), p(b1), p(u1), 1e-12, 100, mixed,
+                                  ctypes.byref(it), ctypes.byref(res))
+        assert rc == 0 and np.array_equal(u1, b1) and res.value <= 1e-12
+    b = op.load(m, np.ones(n), w.mask)
+    rc = L.host_poisson_solve(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, w.alpha, p(w.mask), p(b), p(np.zeros(n)), 1e-10, 0,
+                              0, ctypes.byref(it), ctypes.byref(res))
+    assert rc == -3 and it.value == 0

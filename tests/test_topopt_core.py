@@ -118,3 +118,29 @@ def test_oc_steps_match_oracle(core):
         assert abs(lam - lam_ref) <= 1e-12 * lam_ref
         assert np.abs(y - ref).max() <= 1e-12
         x = ref
+
+
+def test_edge_cases(core):
+    """Filters on one-cell-thick boxes and a single cell; OC with zero and
+    positive gradient entries (those variables go to their lower limit);
+    MMA on a variable already at its bound with a gradient pushing outward
+    (it stays there)."""
+    for nx, ny, nz in ((1, 1, 1), (7, 1, 1), (1, 5, 1), (4, 3, 1)):
+        g = np.random.default_rng(nx * 10 + ny).standard_normal(nx * ny * nz)
+        H = ot.filter_matrix(nx, ny, nz, 2.0)
+        out = np.zeros_like(g)
+        core.host_filter(p(g), p(out), nx, ny, nz, 2.0)
+        assert np.abs(out - ot.filter_sensitivities(H, g)).max() <= 1e-14 * max(1.0, np.abs(g).max())
+        core.host_filter_t(p(g), p(out), nx, ny, nz, 2.0)
+        assert np.abs(out - ot.filter_transpose(H, g)).max() <= 1e-14 * max(1.0, np.abs(g).max())
+    x = np.array([0.5, 0.5, 0.5, 0.5])
+    g = np.array([-1.0, 0.0, 2.0, -3.0])
+    y = np.zeros(4)
+    core.host_oc_step(4, p(x), p(g), p(np.ones(4)), 0.3, 0.2, 0.0, 1.0, p(y))
+    ref, _ = ot.oc_step(x, g, np.ones(4), 0.3, 0.2, 0.0, 1.0)
+    assert np.abs(y - ref).max() <= 1e-12 and y[1] == 0.3 and y[2] == 0.3
+    mma = HostMMA(core, 2, 0.0, 1.0)
+    x = np.array([1.0, 0.0])
+    for _ in range(3):
+        x = mma.step(x, 0.0, np.array([-1.0, 1.0]), -1.0, np.zeros(2))
+    assert np.array_equal(x, [1.0, 0.0])
