@@ -141,3 +141,13 @@ def test_hyperelastic_simp_steps():
         y_ref = ref_mma.step(theta, c_ref, ot.filter_sensitivities(H, g_ref), float(theta.mean() - 0.5), dv)
         assert np.abs(host(y) - y_ref).max() <= 1e-6, it
         theta = y_ref
+
+
+def test_mma_infeasible_constraint_is_not_converged():
+    F = fem()
+    m = F.fem_mesh(2, 1, 1)
+    st = F.MMAState(m, 0.0, 1.0)
+    x = dev(np.array([0.5, 0.7]))
+    with pytest.raises(F.FemError) as e:
+        st.step(x, 2.0 - 0.6, dev(np.zeros(2)), dev(np.full(2, -0.5)))
+    assert e.value.status == F.FEM_ERR_NOT_CONVERGED

@@ -144,3 +144,14 @@ def test_edge_cases(core):
     for _ in range(3):
         x = mma.step(x, 0.0, np.array([-1.0, 1.0]), -1.0, np.zeros(2))
     assert np.array_equal(x, [1.0, 0.0])
+
+
+def test_mma_infeasible_constraint_reports_no_multiplier(core):
+    """x >= 2 with x <= 1 (f1 = 2 - x): no multiplier makes the subproblem
+    feasible, so the dual search returns a negative value (the library
+    reports FEM_ERR_NOT_CONVERGED) and leaves the state untouched."""
+    x = np.array([0.5, 0.7])
+    x1, x2, lo, up, y = (np.zeros(2) for _ in range(5))
+    lam = core.host_mma_step(2, p(x), float(2 - x.mean()), p(np.zeros(2)), p(np.full(2, -0.5)), 0.0, 1.0, 0,
+                             p(x1), p(x2), p(lo), p(up), p(y))
+    assert lam < 0 and np.all(x1 == 0) and np.all(y == 0)
