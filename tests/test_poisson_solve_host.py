@@ -111,3 +111,22 @@ def test_edge_cases(L):
     rc = L.host_poisson_solve(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, w.alpha, p(w.mask), p(b), p(np.zeros(n)), 1e-10, 0,
                               0, ctypes.byref(it), ctypes.byref(res))
     assert rc == -3 and it.value == 0
+
+
+def test_observation_on_a_prescribed_node(L):
+    """An observed boundary node counts in J (u = 0 there) but feeds no
+    adjoint load, as in the oracle (only free rows carry the adjoint)."""
+    w = workload()
+    m, prob = op.from_workload(w)
+    obs = np.concatenate([w.obs[:5], np.flatnonzero(w.mask)[:3]]).astype(np.int64)
+    rng = np.random.default_rng(12)
+    theta = rng.standard_normal(m.n_nodes)
+    u_obs = 0.01 * rng.standard_normal(obs.size)
+    J_ref, g_ref, _, _ = prob.gradient(theta, obs, u_obs)
+    u, lam, g = np.zeros(m.n_nodes), np.zeros(m.n_nodes), np.zeros(m.n_nodes)
+    J, its = ctypes.c_double(), (ctypes.c_int * 2)()
+    rc = L.host_poisson_gradient(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, w.alpha, p(w.mask), p(theta), p(obs),
+                                 p(u_obs), obs.size, 1e-12, 20000, 0, p(u), p(lam), p(g), ctypes.byref(J), its)
+    assert rc == 0
+    assert abs(J.value - J_ref) <= 1e-10 * J_ref
+    assert np.linalg.norm(g - g_ref) <= 1e-8 * np.linalg.norm(g_ref)
