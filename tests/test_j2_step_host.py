@@ -147,3 +147,20 @@ def test_edge_cases(L):
     assert rc == 0 and ni2.value == 0 and ci2.value == 0
     assert np.array_equal(uu, u) and np.abs(hh - h).max() <= 1e-12 * np.abs(h).max()
     assert uu.size == D
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_one_large_step_far_into_plastic_flow(L, mixed):
+    """A single step to a 10% shear and compression of the sheared box:
+    Newton with the consistent tangent reaches the oracle's solution in a
+    few iterations, in FP64 and with FP32 inner solves."""
+    nx, ny, nz = 2, 3, 2
+    s = 0.1
+    mask, ub = inputs.dirichlet(nx, ny, nz, [("z0", 0, 0.0), ("z0", 1, 0.0), ("z0", 2, 0.0), ("z1", 0, s),
+                                             ("z1", 2, -0.5 * s)])
+    dims = (nx, ny, nz, 1.0, 1.5, 1.0)
+    mat = pl.Material(70e3, 0.3, 250.0)
+    ref = pl.solve_path(oracle.mesh(*dims), mat, mask, [ub])[0][0]
+    rc, u, h, ni, ci, nyd = run_path(L, dims, mat, mask, [ub], newton_maxit=50, mixed=mixed)[0]
+    assert rc == 0 and ni <= 12
+    assert np.abs(u - ref).max() <= 1e-10 * np.abs(ref).max()
