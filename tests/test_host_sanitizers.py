@@ -14,7 +14,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 HARNESS_TESTS = ["test_poisson_core.py", "test_j2_core.py", "test_topopt_core.py", "test_dpcg_control.py",
-                 "test_j2_step_host.py", "test_poisson_solve_host.py"]
+                 "test_j2_step_host.py", "test_poisson_solve_host.py", "test_host_properties.py"]
 ORACLE_TESTS = ["test_oracle_element.py", "test_oracle_global.py", "test_oracle_mesh.py", "test_oracle_solve.py",
                 "test_oracle_poisson.py", "test_oracle_plasticity.py", "test_oracle_topopt.py", "test_golden.py"]
 
