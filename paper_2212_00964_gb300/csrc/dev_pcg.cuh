@@ -8,7 +8,10 @@
 // to sc[3(k+1) + 0] and sc[3(k+1) + 2]; the operator adds pq_k itself.  No
 // launch waits for the host; the host control (dpcg_control.h) reads the
 // scalars once every CHECK iterations to test ||r|| <= rtol ||b||,
-// non-finite values and p^T A p <= 0 (breakdown).
+// non-finite values and p^T A p <= 0 (breakdown).  Dot products: per-thread
+// partials in the vector type, block and grid sums in FP64 (GB300 runs FP64
+// at a small fraction of the FP32 rate, so FP32 vectors keep FP64 off the
+// per-element path).
 #pragma once
 
 #include <algorithm>
@@ -32,23 +35,23 @@ __global__ void __launch_bounds__(NT) k_init(const T *__restrict__ b, const T *_
                                             T *__restrict__ p, int64_t N, double *sc0, double *bb)
 {
     __shared__ double sh[NT / 32];
-    double rz = 0, rr = 0, b2 = 0;
+    T rz = 0, rr = 0, b2 = 0;  // per-thread partials in T, the block sum in FP64
     for (int64_t n = blockIdx.x * (int64_t)NT + threadIdx.x; n < N; n += (int64_t)gridDim.x * NT) {
         const T rn = b[n] - q[n];
         const T zn = dinv[n] * rn;
         r[n] = rn;
         z[n] = zn;
         p[n] = zn;
-        rz += (double)rn * (double)zn;
-        rr += (double)rn * (double)rn;
-        b2 += (double)b[n] * (double)b[n];
+        rz += rn * zn;
+        rr += rn * rn;
+        b2 += b[n] * b[n];
     }
-    rz = block_sum<double, NT>(rz, sh);
-    if (threadIdx.x == 0) atomicAdd(&sc0[0], rz);
-    rr = block_sum<double, NT>(rr, sh);
-    if (threadIdx.x == 0) atomicAdd(&sc0[2], rr);
-    b2 = block_sum<double, NT>(b2, sh);
-    if (threadIdx.x == 0) atomicAdd(bb, b2);
+    double v = block_sum_t<T, NT>(rz, sh);
+    if (threadIdx.x == 0) atomicAdd(&sc0[0], v);
+    v = block_sum_t<T, NT>(rr, sh);
+    if (threadIdx.x == 0) atomicAdd(&sc0[2], v);
+    v = block_sum_t<T, NT>(b2, sh);
+    if (threadIdx.x == 0) atomicAdd(bb, v);
 }
 
 // alpha_k = rz_k / pq_k (0 when pq_k <= 0: the host reports the breakdown);
@@ -61,20 +64,20 @@ __global__ void __launch_bounds__(NT) k_update(T *__restrict__ u, T *__restrict_
     __shared__ double sh[NT / 32];
     const double pq = sck[1];
     const T alpha = pq > 0.0 ? (T)(sck[0] / pq) : (T)0;
-    double rz = 0, rr = 0;
+    T rz = 0, rr = 0;
     for (int64_t n = blockIdx.x * (int64_t)NT + threadIdx.x; n < N; n += (int64_t)gridDim.x * NT) {
         u[n] += alpha * p[n];
         const T rn = r[n] - alpha * q[n];
         const T zn = dinv[n] * rn;
         r[n] = rn;
         z[n] = zn;
-        rz += (double)rn * (double)zn;
-        rr += (double)rn * (double)rn;
+        rz += rn * zn;
+        rr += rn * rn;
     }
-    rz = block_sum<double, NT>(rz, sh);
-    if (threadIdx.x == 0) atomicAdd(&sck1[0], rz);
-    rr = block_sum<double, NT>(rr, sh);
-    if (threadIdx.x == 0) atomicAdd(&sck1[2], rr);
+    double v = block_sum_t<T, NT>(rz, sh);
+    if (threadIdx.x == 0) atomicAdd(&sck1[0], v);
+    v = block_sum_t<T, NT>(rr, sh);
+    if (threadIdx.x == 0) atomicAdd(&sck1[2], v);
 }
 
 // beta = rz_{k+1} / rz_k; p = z + beta p

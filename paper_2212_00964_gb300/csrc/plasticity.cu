@@ -146,14 +146,14 @@ __global__ void __launch_bounds__(VB) k_j2_fix_dot(const T *__restrict__ x, cons
                                                   T *__restrict__ y, int64_t D, double *dot)
 {
     __shared__ double sh[VB / 32];
-    double acc = 0;
+    T acc = 0;
     for (int64_t d = blockIdx.x * (int64_t)VB + threadIdx.x; d < D; d += (int64_t)gridDim.x * VB) {
         if (mask && mask[d]) y[d] = x[d];
-        acc += (double)x[d] * (double)y[d];
+        if (dot) acc += x[d] * y[d];
     }
     if (dot) {
-        acc = block_sum<double, VB>(acc, sh);
-        if (threadIdx.x == 0) atomicAdd(dot, acc);
+        const double s = block_sum_t<T, VB>(acc, sh);
+        if (threadIdx.x == 0) atomicAdd(dot, s);
     }
 }
 

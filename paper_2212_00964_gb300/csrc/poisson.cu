@@ -60,14 +60,14 @@ __global__ void __launch_bounds__(PB) k_pois_op(const T *__restrict__ tab, const
     __shared__ double sh[PB / 32];
     for (int t = threadIdx.x; t < poisson::TAB; t += PB) st[t] = tab[t];
     __syncthreads();
-    double acc = 0.0;
+    T acc = 0;
     for (int64_t n = blockIdx.x * (int64_t)PB + threadIdx.x; n < N; n += (int64_t)gridDim.x * PB) {
         const T v = poisson::operator_row<T, T>(st, x, mask, mode, n, nx, ny, nz);
         y[n] = v;
-        acc += (double)x[n] * (double)v;
+        if (dot) acc += x[n] * v;
     }
     if (dot) {
-        const double s = block_sum<double, PB>(acc, sh);
+        const double s = block_sum_t<T, PB>(acc, sh);
         if (threadIdx.x == 0) atomicAdd(dot, s);
     }
 }

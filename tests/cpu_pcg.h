@@ -2,7 +2,9 @@
 // k_update, k_dir of dev_pcg.cuh) with the same scalar layout
 // sc[3k + {0, 1, 2}] = (rz_k, pq_k, rr_k), for host builds that run the
 // library's control code (dpcg_control.h and the controls built on it).
-// Vectors in T, dot products in double, as on the device.  Test code only.
+// Vectors in T; each product rounded to T and the sum taken in double, as
+// the device's per-thread partials (one element per thread at these sizes)
+// and FP64 block sums do.  Test code only.
 #pragma once
 
 #include <cstring>
@@ -31,9 +33,9 @@ struct CpuPcg {
             r[i] = b[i] - q[i];
             z[i] = dinv[i] * r[i];
             p[i] = z[i];
-            sc[0] += (double)r[i] * (double)z[i];
-            sc[2] += (double)r[i] * (double)r[i];
-            b2 += (double)b[i] * (double)b[i];
+            sc[0] += (double)(T)(r[i] * z[i]);
+            sc[2] += (double)(T)(r[i] * r[i]);
+            b2 += (double)(T)(b[i] * b[i]);
         }
         *rz0 = sc[0], *rr0 = sc[2], *bb = b2;
         return 0;
@@ -48,8 +50,8 @@ struct CpuPcg {
                 u[i] += alpha * p[i];
                 r[i] = r[i] - alpha * q[i];
                 z[i] = dinv[i] * r[i];
-                sck1[0] += (double)r[i] * (double)z[i];
-                sck1[2] += (double)r[i] * (double)r[i];
+                sck1[0] += (double)(T)(r[i] * z[i]);
+                sck1[2] += (double)(T)(r[i] * r[i]);
             }
             const T beta = sck[0] > 0.0 ? (T)(sck1[0] / sck[0]) : (T)0;
             for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];

@@ -96,7 +96,7 @@ struct CpuStep {
         double acc = 0;
         for (int64_t d = 0; d < g.D; ++d) {
             if (mask[d]) y[d] = x[d];
-            acc += (double)x[d] * (double)y[d];
+            acc += (double)(T)(x[d] * y[d]);
         }
         if (dot) *dot += acc;
     }

@@ -39,7 +39,7 @@ void op(const Grid &g, const C *tab, const T *x, const uint8_t *mask, int mode, 
     double acc = 0;
     for (int64_t n = 0; n < g.N; ++n) {
         y[n] = poisson::operator_row<T, C>(tab, x, mask, mode, n, g.nx, g.ny, g.nz);
-        acc += (double)x[n] * (double)y[n];
+        acc += (double)(T)(x[n] * y[n]);
     }
     if (dot) *dot += acc;
 }
