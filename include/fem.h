@@ -279,7 +279,7 @@ int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precision, const u
 
 /* Cone-kernel filter: transpose 0 gives g_filtered_e = sum_f w_ef g_f /
  * Hs_e, Hs_e = sum_f w_ef, with w_ef = max(0, rmin - |c_e - c_f|) between
- * cell centres measured in cells (0 < rmin <= 16; rmin <= 1 is the
+ * cell centres measured in cells (0 < rmin <= 12; rmin <= 1 is the
  * identity): the paper's blur of the sensitivities, or a density filter.
  * transpose 1 gives its transpose, sum_f w_fe g_f / Hs_f: the chain rule
  * that carries dJ/dtheta~ of a filtered density back to dJ/dtheta (one

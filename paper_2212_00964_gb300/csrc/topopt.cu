@@ -21,28 +21,54 @@ enum { WS_TVARS = 80, WS_TACC, WS_THS };
 
 int tgrid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + TB - 1) / TB, 152 * 8)); }
 
+// The cone weights of one call, built by each block into shared memory:
+// (2R + 1)^3 doubles, at most 23^3 = 97 KB for rmin <= 12 (above 48 KB,
+// from rmin > 9, the opt-in dynamic shared memory size is set at launch).
+
+__device__ __forceinline__ void stage_weights(double rmin, double *w)
+{
+    if (threadIdx.x == 0) topopt::filter_weights(rmin, w);
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(TB) k_filter(const double *__restrict__ g, double *__restrict__ out, int nx, int ny,
                                               int nz, double rmin)
 {
+    extern __shared__ double w[];
+    stage_weights(rmin, w);
+    const int R = topopt::filter_radius(rmin);
     const int64_t n = (int64_t)nx * ny * nz;
     for (int64_t e = blockIdx.x * (int64_t)TB + threadIdx.x; e < n; e += (int64_t)gridDim.x * TB)
-        out[e] = topopt::filter_cell(g, e, nx, ny, nz, rmin);
+        out[e] = topopt::filter_cell(g, e, nx, ny, nz, R, w);
 }
 
 // hs[e] = sum_f w_ef (the row sums the transpose divides by)
 __global__ void __launch_bounds__(TB) k_filter_rowsum(double *__restrict__ hs, int nx, int ny, int nz, double rmin)
 {
+    extern __shared__ double w[];
+    stage_weights(rmin, w);
+    const int R = topopt::filter_radius(rmin);
     const int64_t n = (int64_t)nx * ny * nz;
     for (int64_t e = blockIdx.x * (int64_t)TB + threadIdx.x; e < n; e += (int64_t)gridDim.x * TB)
-        hs[e] = topopt::filter_weight_sum(e, nx, ny, nz, rmin);
+        hs[e] = topopt::filter_weight_sum(e, nx, ny, nz, R, w);
 }
 
 __global__ void __launch_bounds__(TB) k_filter_t(const double *__restrict__ g, const double *__restrict__ hs,
                                                 double *__restrict__ out, int nx, int ny, int nz, double rmin)
 {
+    extern __shared__ double w[];
+    stage_weights(rmin, w);
+    const int R = topopt::filter_radius(rmin);
     const int64_t n = (int64_t)nx * ny * nz;
     for (int64_t e = blockIdx.x * (int64_t)TB + threadIdx.x; e < n; e += (int64_t)gridDim.x * TB)
-        out[e] = topopt::filter_cell_t(g, hs, e, nx, ny, nz, rmin);
+        out[e] = topopt::filter_cell_t(g, hs, e, nx, ny, nz, R, w);
+}
+
+// dynamic shared memory of the filter kernels for radius rmin
+size_t filter_smem(double rmin)
+{
+    const int W = 2 * topopt::filter_radius(rmin) + 1;
+    return sizeof(double) * (size_t)W * W * W;
 }
 
 // *acc += sum_j w_j (w may be null: the count)
@@ -133,11 +159,18 @@ extern "C" int fem_density_filter(fem_mesh_t m, double rmin, int transpose, cons
 {
     if (!m || !g || !g_filtered || g == g_filtered)
         return (set_error("fem_density_filter: NULL argument or in-place call"), FEM_ERR_ARG);
-    if (!(rmin > 0) || rmin > 16) return (set_error("fem_density_filter: 0 < rmin <= 16 required"), FEM_ERR_ARG);
+    if (!(rmin > 0) || rmin > 12) return (set_error("fem_density_filter: 0 < rmin <= 12 required"), FEM_ERR_ARG);
     if (transpose != 0 && transpose != 1) return (set_error("fem_density_filter: transpose must be 0 or 1"), FEM_ERR_ARG);
     cudaStream_t s = (cudaStream_t)stream;
+    const size_t smem = filter_smem(rmin);
+    if (smem > 48 * 1024) {
+        // beyond the default dynamic shared memory (rmin > 9 cells)
+        FEM_CUDA(cudaFuncSetAttribute(k_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FEM_CUDA(cudaFuncSetAttribute(k_filter_rowsum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FEM_CUDA(cudaFuncSetAttribute(k_filter_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
     if (!transpose) {
-        k_filter<<<tgrid(m->n_cells), TB, 0, s>>>(g, g_filtered, m->nx, m->ny, m->nz, rmin);
+        k_filter<<<tgrid(m->n_cells), TB, smem, s>>>(g, g_filtered, m->nx, m->ny, m->nz, rmin);
         count_launch();
         FEM_CUDA(cudaGetLastError());
         return FEM_OK;
@@ -145,8 +178,8 @@ extern "C" int fem_density_filter(fem_mesh_t m, double rmin, int transpose, cons
     std::lock_guard<std::mutex> lk(m->mu);
     double *hs = (double *)m->ws.get(WS_THS, sizeof(double) * m->n_cells);
     if (!hs) return FEM_ERR_NOMEM;
-    k_filter_rowsum<<<tgrid(m->n_cells), TB, 0, s>>>(hs, m->nx, m->ny, m->nz, rmin);
-    k_filter_t<<<tgrid(m->n_cells), TB, 0, s>>>(g, hs, g_filtered, m->nx, m->ny, m->nz, rmin);
+    k_filter_rowsum<<<tgrid(m->n_cells), TB, smem, s>>>(hs, m->nx, m->ny, m->nz, rmin);
+    k_filter_t<<<tgrid(m->n_cells), TB, smem, s>>>(g, hs, g_filtered, m->nx, m->ny, m->nz, rmin);
     count_launch(2);
     FEM_CUDA(cudaGetLastError());
     return FEM_OK;

@@ -30,71 +30,63 @@
 namespace femgb {
 namespace topopt {
 
-TO_HD double filter_cell(const double *g, int64_t e, int nx, int ny, int nz, double rmin)
+// Cone weights of the offsets (di, dj, dk) in [-R, R]^3, R = ceil(rmin) - 1:
+// w[(di + R) + W (dj + R) + W^2 (dk + R)], W = 2R + 1 (0 beyond rmin).
+TO_HD int filter_radius(double rmin) { return (int)ceil(rmin) - 1; }
+
+TO_HD void filter_weights(double rmin, double *w)
+{
+    const int R = filter_radius(rmin), W = 2 * R + 1;
+    for (int dk = -R; dk <= R; ++dk)
+        for (int dj = -R; dj <= R; ++dj)
+            for (int di = -R; di <= R; ++di) {
+                const double d = sqrt((double)(di * di + dj * dj + dk * dk));
+                const double v = rmin - d;
+                w[(di + R) + W * (dj + R) + W * W * (dk + R)] = v > 0.0 ? v : 0.0;
+            }
+}
+
+// sum over the in-box neighbours f of cell e of w_ef * val(f)
+template <typename F>
+TO_HD double filter_sum(int64_t e, int nx, int ny, int nz, int R, const double *w, F val)
 {
     const int64_t nxy = (int64_t)nx * ny;
     const int k = (int)(e / nxy);
     const int64_t rem = e - (int64_t)k * nxy;
     const int j = (int)(rem / nx);
     const int i = (int)(rem - (int64_t)j * nx);
-    const int R = (int)ceil(rmin) - 1;
-    double num = 0.0, den = 0.0;
+    const int W = 2 * R + 1;
+    double acc = 0.0;
     for (int kk = (k - R > 0 ? k - R : 0); kk <= (k + R < nz - 1 ? k + R : nz - 1); ++kk)
         for (int jj = (j - R > 0 ? j - R : 0); jj <= (j + R < ny - 1 ? j + R : ny - 1); ++jj)
             for (int ii = (i - R > 0 ? i - R : 0); ii <= (i + R < nx - 1 ? i + R : nx - 1); ++ii) {
-                const double di = ii - i, dj = jj - j, dk = kk - k;
-                const double w = rmin - sqrt(di * di + dj * dj + dk * dk);
-                if (w > 0.0) {
-                    num += w * g[ii + (int64_t)nx * (jj + (int64_t)ny * kk)];
-                    den += w;
-                }
+                const double wt = w[(ii - i + R) + W * (jj - j + R) + W * W * (kk - k + R)];
+                if (wt > 0.0) acc += wt * val(ii + (int64_t)nx * (jj + (int64_t)ny * kk));
             }
+    return acc;
+}
+
+// The filter at cell e: sum_f w_ef g_f / sum_f w_ef.
+TO_HD double filter_cell(const double *g, int64_t e, int nx, int ny, int nz, int R, const double *w)
+{
+    const double num = filter_sum(e, nx, ny, nz, R, w, [&](int64_t f) { return g[f]; });
+    const double den = filter_sum(e, nx, ny, nz, R, w, [](int64_t) { return 1.0; });
     return num / den;
 }
 
 // sum_f w_ef: the row sum of the cone weights around cell e
-TO_HD double filter_weight_sum(int64_t e, int nx, int ny, int nz, double rmin)
+TO_HD double filter_weight_sum(int64_t e, int nx, int ny, int nz, int R, const double *w)
 {
-    const int64_t nxy = (int64_t)nx * ny;
-    const int k = (int)(e / nxy);
-    const int64_t rem = e - (int64_t)k * nxy;
-    const int j = (int)(rem / nx);
-    const int i = (int)(rem - (int64_t)j * nx);
-    const int R = (int)ceil(rmin) - 1;
-    double den = 0.0;
-    for (int kk = (k - R > 0 ? k - R : 0); kk <= (k + R < nz - 1 ? k + R : nz - 1); ++kk)
-        for (int jj = (j - R > 0 ? j - R : 0); jj <= (j + R < ny - 1 ? j + R : ny - 1); ++jj)
-            for (int ii = (i - R > 0 ? i - R : 0); ii <= (i + R < nx - 1 ? i + R : nx - 1); ++ii) {
-                const double di = ii - i, dj = jj - j, dk = kk - k;
-                const double w = rmin - sqrt(di * di + dj * dj + dk * dk);
-                if (w > 0.0) den += w;
-            }
-    return den;
+    return filter_sum(e, nx, ny, nz, R, w, [](int64_t) { return 1.0; });
 }
 
 // The transpose of the normalised filter at cell e: sum_f w_fe g_f / Hs_f
 // (the weights are symmetric), the chain rule of a filter applied to the
 // density; hs[f] = filter_weight_sum(f) precomputed.
-TO_HD double filter_cell_t(const double *g, const double *hs, int64_t e, int nx, int ny, int nz, double rmin)
+TO_HD double filter_cell_t(const double *g, const double *hs, int64_t e, int nx, int ny, int nz, int R,
+                           const double *w)
 {
-    const int64_t nxy = (int64_t)nx * ny;
-    const int k = (int)(e / nxy);
-    const int64_t rem = e - (int64_t)k * nxy;
-    const int j = (int)(rem / nx);
-    const int i = (int)(rem - (int64_t)j * nx);
-    const int R = (int)ceil(rmin) - 1;
-    double acc = 0.0;
-    for (int kk = (k - R > 0 ? k - R : 0); kk <= (k + R < nz - 1 ? k + R : nz - 1); ++kk)
-        for (int jj = (j - R > 0 ? j - R : 0); jj <= (j + R < ny - 1 ? j + R : ny - 1); ++jj)
-            for (int ii = (i - R > 0 ? i - R : 0); ii <= (i + R < nx - 1 ? i + R : nx - 1); ++ii) {
-                const double di = ii - i, dj = jj - j, dk = kk - k;
-                const double w = rmin - sqrt(di * di + dj * dj + dk * dk);
-                if (w > 0.0) {
-                    const int64_t f = ii + (int64_t)nx * (jj + (int64_t)ny * kk);
-                    acc += w * g[f] / hs[f];
-                }
-            }
-    return acc;
+    return filter_sum(e, nx, ny, nz, R, w, [&](int64_t f) { return g[f] / hs[f]; });
 }
 
 // Optimality-criteria update of one variable for the multiplier lam:

@@ -12,19 +12,31 @@ using namespace femgb::topopt;
 
 extern "C" {
 
+// Mirrors the filter kernels: the weight table first, then the rows.
+static std::vector<double> weights(double rmin)
+{
+    const int W = 2 * filter_radius(rmin) + 1;
+    std::vector<double> w((size_t)W * W * W);
+    filter_weights(rmin, w.data());
+    return w;
+}
+
 void host_filter(const double *g, double *out, int nx, int ny, int nz, double rmin)
 {
     const int64_t n = (int64_t)nx * ny * nz;
-    for (int64_t e = 0; e < n; ++e) out[e] = filter_cell(g, e, nx, ny, nz, rmin);
+    const std::vector<double> w = weights(rmin);
+    for (int64_t e = 0; e < n; ++e) out[e] = filter_cell(g, e, nx, ny, nz, filter_radius(rmin), w.data());
 }
 
 // Mirrors fem_density_filter with transpose: the row sums first, then the rows.
 void host_filter_t(const double *g, double *out, int nx, int ny, int nz, double rmin)
 {
     const int64_t n = (int64_t)nx * ny * nz;
+    const std::vector<double> w = weights(rmin);
+    const int R = filter_radius(rmin);
     std::vector<double> hs(n);
-    for (int64_t e = 0; e < n; ++e) hs[e] = filter_weight_sum(e, nx, ny, nz, rmin);
-    for (int64_t e = 0; e < n; ++e) out[e] = filter_cell_t(g, hs.data(), e, nx, ny, nz, rmin);
+    for (int64_t e = 0; e < n; ++e) hs[e] = filter_weight_sum(e, nx, ny, nz, R, w.data());
+    for (int64_t e = 0; e < n; ++e) out[e] = filter_cell_t(g, hs.data(), e, nx, ny, nz, R, w.data());
 }
 
 // Mirrors fem_oc_step: returns the multiplier.
