@@ -46,7 +46,7 @@ def jcore():
     return _JC
 
 
-@settings(max_examples=25, deadline=None)
+@settings(max_examples=25, deadline=None, derandomize=True)
 @given(nx=st.integers(1, 5), ny=st.integers(1, 5), nz=st.integers(1, 4),
        lx=st.floats(0.1, 3.0), ly=st.floats(0.1, 3.0), lz=st.floats(0.1, 3.0),
        alpha=st.floats(0.01, 100.0), density=st.floats(0.0, 1.0), seed=st.integers(0, 2 ** 31 - 1))
@@ -75,7 +75,7 @@ def full(s):
     return np.array([[s[0], s[5], s[4]], [s[5], s[1], s[3]], [s[4], s[3], s[2]]])
 
 
-@settings(max_examples=60, deadline=None)
+@settings(max_examples=60, deadline=None, derandomize=True)
 @given(E=st.floats(1.0, 1e6), nu=st.floats(-0.5, 0.49), sy_frac=st.floats(1e-4, 1e-2),
        amp=st.floats(1e-6, 1e-1), seed=st.integers(0, 2 ** 31 - 1))
 def test_j2_return_map_and_tangent(E, nu, sy_frac, amp, seed):
