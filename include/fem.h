@@ -194,7 +194,8 @@ int fem_poisson_apply(fem_mesh_t m, int precision, double alpha, int op, const u
  * value needs the caller's lifting b_f - A_fc u_c).  u: start in, solution
  * out.  Stops when ||b - A u|| <= rtol ||b||, checked every 8 iterations
  * (so up to 7 more iterations run); FEM_ERR_NOT_CONVERGED after maxit
- * (<= 1e6), FEM_ERR_BREAKDOWN if p^T A p <= 0, FEM_ERR_NONFINITE.  *iters,
+ * (<= 1e6) or at a later direction with p^T A p <= 0 (u keeps the iterate
+ * before it), FEM_ERR_BREAKDOWN if the first one has it, FEM_ERR_NONFINITE.  *iters,
  * *rel_res (host, may be NULL): iterations run and ||r|| / ||b||.
  * Synchronises the stream. */
 int fem_poisson_solve(fem_mesh_t m, int precision, double alpha, const uint8_t *mask, const void *b,
@@ -263,7 +264,10 @@ int fem_j2_tangent_apply(fem_mesh_t m, const fem_j2_material *mat, const uint8_t
  * or FEM_MIXED: the tangent apply, the CG vectors and the correction in FP32
  * (the residual, history, diagonal and u stay FP64; an FP32 correction is
  * an inexact Newton step, so cg_rtol of about 1e-4 suits it).  An inner
- * solve that stops at cg_maxit still supplies its correction.  On success
+ * solve that stops at cg_maxit, or is truncated at a direction of
+ * non-positive curvature (the tangent of perfect plasticity is singular
+ * once a mechanism yields), still supplies its correction; a correction
+ * that raises ||r|| is halved up to 10 times.  On success
  * hist becomes (eps^k, sigma^k) at the converged u.  newton_iters, cg_iters,
  * n_yield (host, may be NULL): Newton iterations, total CG iterations,
  * yielding Gauss points.  FEM_ERR_NOT_CONVERGED after newton_maxit (hist

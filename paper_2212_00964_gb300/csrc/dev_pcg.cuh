@@ -54,16 +54,28 @@ __global__ void __launch_bounds__(NT) k_init(const T *__restrict__ b, const T *_
     if (threadIdx.x == 0) atomicAdd(bb, v);
 }
 
-// alpha_k = rz_k / pq_k (0 when pq_k <= 0: the host reports the breakdown);
-// u += alpha p, r -= alpha q, z = D r; sck1[0] += (r, z), sck1[2] += (r, r).
+// alpha_k = rz_k / pq_k; u += alpha p, r -= alpha q, z = D r;
+// sck1[0] += (r, z), sck1[2] += (r, r).  Truncation: once some pq_k <= 0
+// (curvature not positive, e.g. a singular tangent) the iterate stays as it
+// is: *halt is set and this and every later update only carry the scalars
+// forward, so the host finds the last iterate and its residual.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_update(T *__restrict__ u, T *__restrict__ r, T *__restrict__ z,
                                               const T *__restrict__ p, const T *__restrict__ q,
-                                              const T *__restrict__ dinv, int64_t N, const double *sck, double *sck1)
+                                              const T *__restrict__ dinv, int64_t N, const double *sck, double *sck1,
+                                              int *halt)
 {
     __shared__ double sh[NT / 32];
     const double pq = sck[1];
-    const T alpha = pq > 0.0 ? (T)(sck[0] / pq) : (T)0;
+    if (*halt || !(pq > 0.0)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            sck1[0] = sck[0];
+            sck1[2] = sck[2];
+            *halt = 1;
+        }
+        return;
+    }
+    const T alpha = (T)(sck[0] / pq);
     T rz = 0, rr = 0;
     for (int64_t n = blockIdx.x * (int64_t)NT + threadIdx.x; n < N; n += (int64_t)gridDim.x * NT) {
         u[n] += alpha * p[n];
@@ -80,11 +92,12 @@ __global__ void __launch_bounds__(NT) k_update(T *__restrict__ u, T *__restrict_
     if (threadIdx.x == 0) atomicAdd(&sck1[2], v);
 }
 
-// beta = rz_{k+1} / rz_k; p = z + beta p
+// beta = rz_{k+1} / rz_k; p = z + beta p (nothing once truncated)
 template <typename T>
 __global__ void __launch_bounds__(NT) k_dir(T *__restrict__ p, const T *__restrict__ z, int64_t N, const double *sck,
-                                           const double *sck1)
+                                           const double *sck1, const int *halt)
 {
+    if (*halt) return;
     const double rz = sck[0];
     const T beta = rz > 0.0 ? (T)(sck1[0] / rz) : (T)0;
     for (int64_t n = blockIdx.x * (int64_t)NT + threadIdx.x; n < N; n += (int64_t)gridDim.x * NT)
@@ -95,7 +108,7 @@ template <typename T>
 struct Buffers {
     T *r, *z, *p, *q;
     double *sc;     // 3 * (maxit + 2) doubles
-    double *small;  // 1 double
+    double *small;  // 2 doubles: (b, b) and the truncation flag
 };
 
 inline size_t scalar_count(int maxit) { return 3 * ((size_t)maxit + 2); }
@@ -120,7 +133,7 @@ struct DeviceOps {
     int start(double *rz0, double *rr0, double *bb)
     {
         FEM_CUDA(cudaMemsetAsync(w.sc, 0, sizeof(double) * scalar_count(maxit), s));
-        FEM_CUDA(cudaMemsetAsync(w.small, 0, sizeof(double), s));
+        FEM_CUDA(cudaMemsetAsync(w.small, 0, sizeof(double) * 2, s));
         if (int rc = apply(u, w.q, nullptr)) return rc;
         k_init<T><<<grid_for(N), NT, 0, s>>>(b, w.q, dinv, w.r, w.z, w.p, N, w.sc, w.small);
         count_launch();
@@ -139,8 +152,9 @@ struct DeviceOps {
         for (int k = k0; k < k1; ++k) {
             double *sck = w.sc + 3 * (size_t)k, *sck1 = w.sc + 3 * ((size_t)k + 1);
             if (int e = apply(w.p, w.q, &sck[1])) return e;
-            k_update<T><<<g, NT, 0, s>>>(u, w.r, w.z, w.p, w.q, dinv, N, sck, sck1);
-            k_dir<T><<<g, NT, 0, s>>>(w.p, w.z, N, sck, sck1);
+            int *halt = (int *)&w.small[1];
+            k_update<T><<<g, NT, 0, s>>>(u, w.r, w.z, w.p, w.q, dinv, N, sck, sck1, halt);
+            k_dir<T><<<g, NT, 0, s>>>(w.p, w.z, N, sck, sck1, halt);
             count_launch(2);
         }
         FEM_CUDA(cudaGetLastError());

@@ -28,7 +28,10 @@ constexpr int CHECK = 8;  // iterations between host reads
 
 // Stops when ||r_k|| <= rtol ||b|| (||b|| = 1 when b = 0), tested every
 // CHECK iterations, so up to CHECK - 1 more iterations run; *iters gets the
-// iterations run and *rel_res the last ||r|| / ||b||.
+// iterations run and *rel_res the last ||r|| / ||b||.  A direction with
+// p^T A p <= 0 truncates the solve (the device side keeps the iterate
+// reached before it): ST_BREAKDOWN if that happens in the first iteration,
+// else ST_NOT_CONVERGED with that iterate (a Newton caller may use it).
 template <typename Ops>
 int control(Ops &ops, double rtol, int maxit, int *iters, double *rel_res)
 {
@@ -42,7 +45,8 @@ int control(Ops &ops, double rtol, int maxit, int *iters, double *rel_res)
     int k = 0;
     int rc = std::sqrt(rr) <= rtol * bn ? ST_OK : ST_NOT_CONVERGED;
     std::vector<double> hs;
-    while (rc == ST_NOT_CONVERGED && k < maxit) {
+    bool truncated = false;
+    while (rc == ST_NOT_CONVERGED && k < maxit && !truncated) {
         const int k0 = k;
         const int k1 = std::min(maxit, k + CHECK);
         if (int e = ops.iterate(k0, k1)) return e;
@@ -56,9 +60,14 @@ int control(Ops &ops, double rtol, int maxit, int *iters, double *rel_res)
                 rc = ST_NONFINITE;
                 break;
             }
-            if (pq <= 0.0 && rz > 0.0) {
-                ops.fail("p^T A p <= 0 (operator not positive definite)");
-                rc = ST_BREAKDOWN;
+            if (pq <= 0.0 && rz != 0.0) {
+                if (k0 + j == 0) {
+                    ops.fail("p^T A p <= 0 (operator not positive definite)");
+                    rc = ST_BREAKDOWN;
+                } else {
+                    ops.fail("truncated at a direction with p^T A p <= 0");
+                    truncated = true;
+                }
                 break;
             }
             rr = rr1;
@@ -71,7 +80,7 @@ int control(Ops &ops, double rtol, int maxit, int *iters, double *rel_res)
     }
     if (iters) *iters = k;
     if (rel_res) *rel_res = std::sqrt(rr) / bn;
-    if (rc == ST_NOT_CONVERGED) ops.fail("CG iteration limit reached");
+    if (rc == ST_NOT_CONVERGED && !truncated) ops.fail("CG iteration limit reached");
     return rc;
 }
 

@@ -8,6 +8,7 @@
 //       r at u with the history, r_c = 0, b = -r, returned states to the
 //       new-history buffer; ||r||_2 and the yielding Gauss points
 //   int correction(int *cg_iters)         du from K(u) du = b (PCG), u += du
+//   int adjust(double c)                  u += c du (the last correction)
 //   int accept()                          history <- new-history buffer
 //   void fail(const char *what)
 // Status codes as in dpcg_control.h.
@@ -28,21 +29,36 @@ namespace j2 {
 // internal forces ends); the states returned at the converged u become the
 // history.  ST_NOT_CONVERGED after newton_maxit corrections (history
 // unchanged).
+// A correction that does not lower ||r|| is halved (u -= du/2, du/4, ...,
+// at most MAX_HALVINGS times) before the next tangent: backtracking on the
+// residual norm, which changes the iterates but not the discrete solution
+// they converge to.  It guards the steps where the tangent of perfect
+// plasticity is nearly singular and the CG correction is truncated.
+constexpr int MAX_HALVINGS = 10;
+
 template <typename Ops>
 int newton_step(Ops &ops, double sigma_y, double h, double newton_rtol, int newton_maxit, int *newton_iters,
                 int *cg_iters, int64_t *n_yield)
 {
     if (int rc = ops.prescribe()) return rc;
-    double ref = -1.0;
+    double ref = -1.0, prev = -1.0;
     int cg_total = 0;
     for (int it = 0;; ++it) {
         double nrm = 0.0;
         int64_t ny = 0;
         if (int rc = ops.residual(&nrm, &ny)) return rc;
+        // backtrack while the last correction made the residual worse
+        double step = 1.0;
+        for (int hv = 0; it > 0 && hv < MAX_HALVINGS && !(nrm < prev); ++hv) {
+            step *= 0.5;
+            if (int rc = ops.adjust(-step)) return rc;
+            if (int rc = ops.residual(&nrm, &ny)) return rc;
+        }
         if (!std::isfinite(nrm)) {
             ops.fail("non-finite residual");
             return dpcg::ST_NONFINITE;
         }
+        prev = nrm;
         if (ref < 0) ref = std::max(nrm, sigma_y * h * h);
         if (newton_iters) *newton_iters = it;
         if (cg_iters) *cg_iters = cg_total;

@@ -196,11 +196,12 @@ __global__ void k_j2_prescribe(double *__restrict__ u, const double *__restrict_
         if (mask[i]) u[i] = ubar[i];
 }
 
+// u += c du
 template <typename T>
-__global__ void k_j2_axpy(double *__restrict__ u, const T *__restrict__ du, int64_t D)
+__global__ void k_j2_axpy(double *__restrict__ u, const T *__restrict__ du, double c, int64_t D)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < D; i += (int64_t)gridDim.x * blockDim.x)
-        u[i] += (double)du[i];
+        u[i] += c * (double)du[i];
 }
 
 int residual_launch(const Geo &g, const uint8_t *mask, const double *u, const double *hist, double *R,
@@ -301,7 +302,7 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
     w.p = (double *)m->ws.get(WS_JCP, sizeof(double) * D);
     w.q = (double *)m->ws.get(WS_JCQ, sizeof(double) * D);
     w.sc = (double *)m->ws.get(WS_JSC, sizeof(double) * dpcg::scalar_count(cg_maxit));
-    double *small = (double *)m->ws.get(WS_JSMALL, sizeof(double) * 4);
+    double *small = (double *)m->ws.get(WS_JSMALL, sizeof(double) * 6);
     w.small = small + 3;
     if (!R || !b || !du || !dg || !dinv || !hn || !w.r || !w.z || !w.p || !w.q || !w.sc || !small)
         return FEM_ERR_NOMEM;
@@ -374,7 +375,7 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
                                         "fem_j2_step");
                 // a truncated inner solve still gives a usable (inexact) Newton correction
                 if (rc != FEM_OK && rc != FEM_ERR_NOT_CONVERGED) return rc;
-                k_j2_axpy<float><<<vec_grid(g.dofs), VB, 0, s>>>(u, du32, g.dofs);
+                k_j2_axpy<float><<<vec_grid(g.dofs), VB, 0, s>>>(u, du32, 1.0, g.dofs);
             } else {
                 FEM_CUDA(cudaMemsetAsync(dg, 0, sizeof(double) * g.dofs, s));
                 k_j2_diag<double><<<cell_grid(g.ne), CB, 0, s>>>(g, u, hist, dg);
@@ -387,8 +388,16 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
                 rc = dpcg::solve<double>(s, g.dofs, apply, dinv, b, du, w, cg_rtol, cg_maxit, cg_it, nullptr,
                                          "fem_j2_step");
                 if (rc != FEM_OK && rc != FEM_ERR_NOT_CONVERGED) return rc;
-                k_j2_axpy<double><<<vec_grid(g.dofs), VB, 0, s>>>(u, du, g.dofs);
+                k_j2_axpy<double><<<vec_grid(g.dofs), VB, 0, s>>>(u, du, 1.0, g.dofs);
             }
+            count_launch();
+            FEM_CUDA(cudaGetLastError());
+            return FEM_OK;
+        }
+        int adjust(double c)
+        {
+            if (mixed) k_j2_axpy<float><<<vec_grid(g.dofs), VB, 0, s>>>(u, du32, c, g.dofs);
+            else k_j2_axpy<double><<<vec_grid(g.dofs), VB, 0, s>>>(u, du, c, g.dofs);
             count_launch();
             FEM_CUDA(cudaGetLastError());
             return FEM_OK;

@@ -40,12 +40,20 @@ struct CpuPcg {
         *rz0 = sc[0], *rr0 = sc[2], *bb = b2;
         return 0;
     }
+    bool halt = false;
+
     int iterate(int k0, int k1)
     {
         for (int k = k0; k < k1; ++k) {
             double *sck = &sc[3 * (size_t)k], *sck1 = &sc[3 * ((size_t)k + 1)];
             apply(p.data(), q.data(), &sck[1]);
-            const T alpha = sck[1] > 0.0 ? (T)(sck[0] / sck[1]) : (T)0;
+            if (halt || !(sck[1] > 0.0)) {  // truncated: carry the scalars, keep the iterate
+                sck1[0] = sck[0];
+                sck1[2] = sck[2];
+                halt = true;
+                continue;
+            }
+            const T alpha = (T)(sck[0] / sck[1]);
             for (int64_t i = 0; i < n; ++i) {
                 u[i] += alpha * p[i];
                 r[i] = r[i] - alpha * q[i];

@@ -21,6 +21,7 @@ struct CpuOps {
     std::vector<double> r, z, p, q, sc;
     std::string err;
     int n_iterate_calls = 0;
+    bool halt = false;
 
     void apply(const double *x, double *y, double *dot)
     {
@@ -58,7 +59,13 @@ struct CpuOps {
         for (int k = k0; k < k1; ++k) {
             double *sck = &sc[3 * (size_t)k], *sck1 = &sc[3 * ((size_t)k + 1)];
             apply(p.data(), q.data(), &sck[1]);
-            const double alpha = sck[1] > 0.0 ? sck[0] / sck[1] : 0.0;
+            if (halt || !(sck[1] > 0.0)) {  // truncated: carry the scalars, keep the iterate
+                sck1[0] = sck[0];
+                sck1[2] = sck[2];
+                halt = true;
+                continue;
+            }
+            const double alpha = sck[0] / sck[1];
             for (int i = 0; i < n; ++i) {
                 u[i] += alpha * p[i];
                 r[i] -= alpha * q[i];

@@ -43,7 +43,7 @@ struct CpuStep {
     double cg_rtol;
     int cg_maxit;
     bool mixed;
-    std::vector<double> R, b, du, dg, dinv, hn;
+    std::vector<double> R, b, du, dg, dinv, hn, last;
     std::string err;
 
     int prescribe()
@@ -128,6 +128,7 @@ struct CpuStep {
                 return rc;
             }
             for (int64_t d = 0; d < g.D; ++d) u[d] += (double)du32[d];
+            last.assign(du32.begin(), du32.end());
             return 0;
         }
         diag_inv(0.0, dinv);
@@ -140,6 +141,13 @@ struct CpuStep {
             return rc;
         }
         for (int64_t d = 0; d < g.D; ++d) u[d] += du[d];
+        last = du;
+        return 0;
+    }
+    // u += c du of the last correction (as stored: FP32 in the mixed mode)
+    int adjust(double c)
+    {
+        for (int64_t d = 0; d < g.D; ++d) u[d] += c * last[d];
         return 0;
     }
     int accept()

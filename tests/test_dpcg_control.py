@@ -2,8 +2,9 @@
 (csrc/dpcg_control.h) that the Poisson and J2 paths share, driven through
 tests/dpcg_control_host.cpp by CPU stand-ins of its kernels: convergence to
 numpy's solution, the batching of iterations between host reads, and the
-exits (already converged, zero right-hand side, iteration limit, an
-indefinite operator, non-finite input)."""
+exits (already converged, zero right-hand side, iteration limit, negative
+curvature in the first iteration (breakdown) or later (truncation at the
+last iterate), non-finite input)."""
 import ctypes
 
 import numpy as np
@@ -75,12 +76,25 @@ def test_iteration_limit(L):
     assert rc == NOT_CONVERGED and it == 11 and calls == 2 and "limit" in err and res > 1e-12
 
 
-def test_indefinite_operator_is_a_breakdown(L):
+def test_negative_curvature_first_is_a_breakdown(L):
+    A = -spd(12, 10)
+    rc, _, it, _, _, err = run(L, A, np.ones(12))
+    assert rc == BREAKDOWN and "positive definite" in err
+
+
+def test_negative_curvature_later_truncates_at_the_last_iterate(L):
+    """An indefinite operator whose first directions have positive
+    curvature: the solve stops at the iterate reached before the first
+    p^T A p <= 0 (the later iterations of the batch change nothing), and the
+    reported residual is that iterate's."""
     rng = np.random.default_rng(7)
     Q, _ = np.linalg.qr(rng.standard_normal((30, 30)))
     A = Q @ np.diag(np.linspace(-1.0, 2.0, 30)) @ Q.T
-    rc, _, _, _, _, err = run(L, A, rng.standard_normal(30), maxit=200)
-    assert rc == BREAKDOWN and "positive definite" in err
+    b = rng.standard_normal(30)
+    rc, u, it, res, _, err = run(L, A, b, maxit=200)
+    assert rc == NOT_CONVERGED and "truncated" in err
+    assert np.all(np.isfinite(u)) and np.any(u != 0)
+    assert abs(np.linalg.norm(b - A @ u) / np.linalg.norm(b) - res) <= 1e-8
 
 
 def test_non_finite_input(L):

@@ -164,3 +164,43 @@ def test_one_large_step_far_into_plastic_flow(L, mixed):
     rc, u, h, ni, ci, nyd = run_path(L, dims, mat, mask, [ub], newton_maxit=50, mixed=mixed)[0]
     assert rc == 0 and ni <= 12
     assert np.abs(u - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def random_paths(seed, n):
+    """Random boxes clamped at z=0 with a random 4-step displacement path of
+    the z=1 face."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        nx, ny, nz = rng.integers(1, 4, 3)
+        dims = (int(nx), int(ny), int(nz), float(rng.uniform(0.5, 2)), float(rng.uniform(0.5, 2)),
+                float(rng.uniform(0.5, 2)))
+        path = np.cumsum(rng.standard_normal((4, 3)) * 4e-3, axis=0)
+        ubars = []
+        mask = None
+        for d in path:
+            mask, ub = inputs.dirichlet(dims[0], dims[1], dims[2], [("z0", 0, 0.0), ("z0", 1, 0.0), ("z0", 2, 0.0),
+                                                                ("z1", 0, d[0]), ("z1", 1, d[1]), ("z1", 2, d[2])])
+            ubars.append(ub)
+        out.append((dims, mask, ubars))
+    return out
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_random_load_paths_match_the_oracle(L, mixed):
+    """Random non-proportional paths (seed 5, the first six; the fifth once
+    diverged before truncated CG and backtracking): wherever the oracle's
+    exact Newton converges, the library reaches the same solution."""
+    mat = pl.Material(70e3, 0.3, 250.0)
+    compared = 0
+    for dims, mask, ubars in random_paths(5, 6):
+        try:
+            ref = pl.solve_path(oracle.mesh(*dims), mat, mask, ubars)
+        except (RuntimeError, pl.np.linalg.LinAlgError):
+            continue
+        got = run_path(L, dims, mat, mask, ubars, newton_maxit=50, mixed=mixed)
+        for (rc, u, h, ni, ci, nyd), (u_ref, _, _) in zip(got, ref):
+            assert rc == 0, L.host_j2_step_error()
+            assert np.abs(u - u_ref).max() <= 1e-8 * np.abs(u_ref).max()
+        compared += 1
+    assert compared >= 4
