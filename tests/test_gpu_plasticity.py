@@ -92,3 +92,16 @@ def test_not_converged_keeps_the_history():
         F.fem_j2_step(m, mat, dev(mask), dev(ubars[5]), u, hist, newton_maxit=0)
     assert e.value.status == F.FEM_ERR_NOT_CONVERGED
     assert float(hist.abs().max()) == 0.0
+
+
+def test_non_finite_prescribed_value_is_reported():
+    n = 2
+    mask, ubars, _, _ = inputs.j2_uniaxial(n=n)
+    F = fem()
+    m = F.fem_mesh(n, n, n)
+    ub = np.array(ubars[0])
+    ub[np.flatnonzero(mask)[-1]] = np.nan
+    u = torch.zeros(3 * (n + 1) ** 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(F.FemError) as e:
+        F.fem_j2_step(m, F.j2_material(E, NU, SY), dev(mask), dev(ub), u, F.j2_history(m))
+    assert e.value.status == F.FEM_ERR_NONFINITE

@@ -184,3 +184,15 @@ def test_bad_observation_index_is_an_argument_error():
     # the handle stays usable
     y = F.fem_poisson_apply(m, dev(np.ones(m.n_nodes)), 1.0)
     assert abs(float(y.sum())) <= 1e-12
+
+
+def test_non_finite_right_hand_side_is_reported():
+    w = inputs.poisson_inference(6, 5, 3, 1.0, 1.0, 0.2, n_obs=5, seed=2)
+    F = fem()
+    m = F.fem_mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)
+    b = np.zeros(m.n_nodes)
+    b[int(np.flatnonzero(w.mask == 0)[0])] = np.nan
+    for mixed in (False, True):
+        with pytest.raises(F.FemError) as e:
+            F.fem_poisson_solve(m, dev(b), w.alpha, dev(w.mask), mixed=mixed)
+        assert e.value.status == F.FEM_ERR_NONFINITE

@@ -204,3 +204,11 @@ def test_random_load_paths_match_the_oracle(L, mixed):
             assert np.abs(u - u_ref).max() <= 1e-8 * np.abs(u_ref).max()
         compared += 1
     assert compared >= 4
+
+
+def test_non_finite_prescribed_value_is_reported(L):
+    dims, mask, ubars = sheared_box()
+    ub = np.array(ubars[0])
+    ub[np.flatnonzero(mask)[-1]] = np.nan
+    got = run_path(L, dims, pl.Material(70e3, 0.3, 250.0), mask, [ub])
+    assert got[0][0] == -6 and "non-finite" in L.host_j2_step_error().decode()

@@ -130,3 +130,15 @@ def test_observation_on_a_prescribed_node(L):
     assert rc == 0
     assert abs(J.value - J_ref) <= 1e-10 * J_ref
     assert np.linalg.norm(g - g_ref) <= 1e-8 * np.linalg.norm(g_ref)
+
+
+def test_non_finite_input_is_reported(L):
+    w = workload()
+    m, _ = op.from_workload(w)
+    b = op.load(m, np.ones(m.n_nodes), w.mask)
+    b[int(np.flatnonzero(w.mask == 0)[3])] = np.nan
+    it, res = ctypes.c_int(), ctypes.c_double()
+    for mixed in (0, 1):
+        rc = L.host_poisson_solve(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, w.alpha, p(w.mask), p(b),
+                                  p(np.zeros(m.n_nodes)), 1e-10, 100, mixed, ctypes.byref(it), ctypes.byref(res))
+        assert rc == -6 and "non-finite" in L.host_poisson_error().decode()
