@@ -111,3 +111,15 @@ def test_zero_iteration_limit(L):
     assert rc == NOT_CONVERGED and it == 0 and calls == 0 and np.all(u == 0)
     rc, u, it, res, calls, err = run(L, A, np.zeros(10), maxit=0)
     assert rc == OK and it == 0
+
+
+def test_reported_residual_is_the_final_one(L):
+    """Away from the rounding floor CG's recursive residual equals the true
+    one, so the reported ||r|| / ||b|| must match ||b - A u|| / ||b|| of the
+    returned iterate (the last of its batch)."""
+    A = spd(40, 11, cond=1e2)
+    b = np.random.default_rng(12).standard_normal(40)
+    rc, u, it, res, calls, _ = run(L, A, b, rtol=1e-6)
+    true = np.linalg.norm(b - A @ u) / np.linalg.norm(b)
+    assert rc == OK and res <= 1e-6
+    assert abs(res - true) <= 1e-9

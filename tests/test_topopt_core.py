@@ -155,3 +155,12 @@ def test_mma_infeasible_constraint_reports_no_multiplier(core):
     lam = core.host_mma_step(2, p(x), float(2 - x.mean()), p(np.zeros(2)), p(np.full(2, -0.5)), 0.0, 1.0, 0,
                              p(x1), p(x2), p(lo), p(up), p(y))
     assert lam < 0 and np.all(x1 == 0) and np.all(y == 0)
+
+
+def test_mma_first_step_stops_at_the_move_limits(core):
+    """In the first step the asymptotes sit 0.5 of the range away and the
+    move limits 9/10 of the way to them: a linear objective with a slack
+    constraint moves every variable by 0.45 of the range, as in the oracle."""
+    mma = HostMMA(core, 3, 0.0, 2.0)
+    y = mma.step(np.full(3, 1.0), 0.0, np.array([1.0, -1.0, 2.0]), -5.0, np.zeros(3))
+    assert np.abs(y - [0.1, 1.9, 0.1]).max() <= 1e-15
