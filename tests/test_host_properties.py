@@ -1,7 +1,9 @@
 """Property-based parity of the host builds of the CUDA library's
 arithmetic against the oracle (hypothesis draws the cases): the Poisson
-stencil rows on random boxes, lengths and masks, and the J2 return map and
-its tangent on random histories and strain increments."""
+stencil rows on random boxes, lengths and masks, the J2 return map and its
+tangent on random histories and strain increments, and the cone filter, its
+transpose and the optimality-criteria step on random boxes, radii and
+designs."""
 import ctypes
 
 import numpy as np
@@ -102,3 +104,48 @@ def test_j2_return_map_and_tangent(E, nu, sy_frac, amp, seed):
                       p(ds))
     ref = pl.dstress(mat, eo, so, H, dH)
     assert np.abs(full(ds) - ref).max() <= 1e-9 * max(1e-300, np.abs(ref).max())
+
+
+_TC = None
+
+
+def tcore():
+    global _TC
+    if _TC is None:
+        _TC = host_build.build("topopt_core_host", extra_flags=["-ffp-contract=off"])
+        P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+        _TC.host_filter.argtypes = [P, P, I, I, I, D]
+        _TC.host_filter_t.argtypes = [P, P, I, I, I, D]
+        _TC.host_oc_step.argtypes = [I64, P, P, P, D, D, D, D, P]
+        _TC.host_oc_step.restype = D
+    return _TC
+
+
+@settings(max_examples=30, deadline=None, derandomize=True)
+@given(nx=st.integers(1, 7), ny=st.integers(1, 7), nz=st.integers(1, 4), rmin=st.floats(0.3, 4.0),
+       seed=st.integers(0, 2 ** 31 - 1))
+def test_filter_and_transpose(nx, ny, nz, rmin, seed):
+    from oracle import topopt as ot
+    L = tcore()
+    g = np.random.default_rng(seed).standard_normal(nx * ny * nz)
+    H = ot.filter_matrix(nx, ny, nz, rmin)
+    out = np.zeros_like(g)
+    L.host_filter(p(g), p(out), nx, ny, nz, rmin)
+    assert np.abs(out - ot.filter_sensitivities(H, g)).max() <= 1e-13 * np.abs(g).max()
+    L.host_filter_t(p(g), p(out), nx, ny, nz, rmin)
+    assert np.abs(out - ot.filter_transpose(H, g)).max() <= 1e-13 * np.abs(g).max()
+
+
+@settings(max_examples=30, deadline=None, derandomize=True)
+@given(n=st.integers(1, 40), vol=st.floats(0.05, 0.95), move=st.floats(0.01, 0.5), seed=st.integers(0, 2 ** 31 - 1))
+def test_oc_step(n, vol, move, seed):
+    from oracle import topopt as ot
+    L = tcore()
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0.01, 1.0, n)
+    g = -rng.uniform(0.0, 10.0, n) * (rng.uniform(size=n) < 0.9)
+    dv = rng.uniform(0.5, 2.0, n)
+    ref, lam_ref = ot.oc_step(x, g, dv, vol, move, 0.0, 1.0)
+    y = np.zeros(n)
+    lam = L.host_oc_step(n, p(x), p(np.ascontiguousarray(g)), p(dv), vol, move, 0.0, 1.0, p(y))
+    assert np.abs(y - ref).max() <= 1e-12
