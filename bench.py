@@ -395,6 +395,12 @@ def next_suite(F, inputs, torch):
     instead of stopping the benchmark."""
     import numpy as np
     out = {}
+    hbm_peak = None
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            hbm_peak = float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        pass
 
     def guarded(name, fn):
         try:
@@ -427,12 +433,40 @@ def next_suite(F, inputs, torch):
             e1.synchronize()
             t = e0.elapsed_time(e1) / 20 / 1e3
             nbytes = m.n_nodes * (2 * x.element_size() + 1)
-            res[f"apply_{name}"] = {"us": t * 1e6, "gbs_algorithmic": nbytes / t / 1e9,
+            gbs = nbytes / t / 1e9
+            res[f"apply_{name}"] = {"us": t * 1e6, "gbs_algorithmic": gbs,
+                                    "hbm_frac_of_measured": gbs / hbm_peak if hbm_peak else None,
+                                    "flops": 54 * m.n_nodes / t,
                                     "note": "includes the stencil-table build launch"}
         return res
 
     guarded("poisson_50x50x10", lambda: poisson(50, 50, 10))
     guarded("poisson_256x256x64", lambda: poisson(256, 256, 64))
+
+    def j2_apply():
+        """The FP64 tangent apply alone (fem_j2_tangent_apply) at 32^3 on the
+        yielded uniaxial state: about 4,400 FP64 operations per cell."""
+        n = 32
+        mask_h, ubars, _, (E, nu, sy) = inputs.j2_uniaxial(n=n)
+        m = F.fem_mesh(n, n, n)
+        mat = F.j2_material(E, nu, sy)
+        mask = torch.tensor(mask_h, device="cuda")
+        u = torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda")
+        hist = F.j2_history(m)
+        F.fem_j2_step(m, mat, mask, torch.tensor(ubars[4], device="cuda"), u, hist, mixed=True)
+        x = torch.randn(m.n_dofs, dtype=torch.float64, device="cuda")
+        F.fem_j2_tangent_apply(m, mat, u, hist, x, mask)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            F.fem_j2_tangent_apply(m, mat, u, hist, x, mask)
+        e1.record()
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 10 / 1e3
+        return {"cells": m.n_cells, "us": t * 1e6, "fp64_tflops": 4400 * m.n_cells / t / 1e12,
+                "note": "includes the y memset and the masked-row pass"}
+
+    guarded("j2_apply_32cube_fp64", j2_apply)
 
     def j2_path(mixed):
         n = 16
