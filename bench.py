@@ -444,8 +444,9 @@ def next_suite(F, inputs, torch):
     guarded("poisson_256x256x64", lambda: poisson(256, 256, 64))
 
     def j2_apply():
-        """The FP64 tangent apply alone (fem_j2_tangent_apply) at 32^3 on the
-        yielded uniaxial state: about 4,400 FP64 operations per cell."""
+        """The tangent apply alone (fem_j2_tangent_apply, FP64 and the FP32
+        apply of the mixed mode) at 32^3 on the yielded uniaxial state:
+        about 4,400 operations per cell."""
         n = 32
         mask_h, ubars, _, (E, nu, sy) = inputs.j2_uniaxial(n=n)
         m = F.fem_mesh(n, n, n)
@@ -454,19 +455,23 @@ def next_suite(F, inputs, torch):
         u = torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda")
         hist = F.j2_history(m)
         F.fem_j2_step(m, mat, mask, torch.tensor(ubars[4], device="cuda"), u, hist, mixed=True)
-        x = torch.randn(m.n_dofs, dtype=torch.float64, device="cuda")
-        F.fem_j2_tangent_apply(m, mat, u, hist, x, mask)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(10):
+        res = {"cells": m.n_cells, "note": "includes the y memset and the masked-row pass"}
+        for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+            x = torch.randn(m.n_dofs, dtype=dt, device="cuda")
             F.fem_j2_tangent_apply(m, mat, u, hist, x, mask)
-        e1.record()
-        e1.synchronize()
-        t = e0.elapsed_time(e1) / 10 / 1e3
-        return {"cells": m.n_cells, "us": t * 1e6, "fp64_tflops": 4400 * m.n_cells / t / 1e12,
-                "note": "includes the y memset and the masked-row pass"}
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                F.fem_j2_tangent_apply(m, mat, u, hist, x, mask)
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / 10 / 1e3
+            tf = 4400 * m.n_cells / t / 1e12
+            res[name] = {"us": t * 1e6, "tflops": tf,
+                         "frac_fp32_peak": tf / FP32_PEAK_TFLOPS if name == "fp32" else None}
+        return res
 
-    guarded("j2_apply_32cube_fp64", j2_apply)
+    guarded("j2_apply_32cube", j2_apply)
 
     def j2_path(mixed):
         n = 16

@@ -251,9 +251,11 @@ int fem_j2_residual(fem_mesh_t m, const fem_j2_material *mat, const uint8_t *mas
  * derivative in eps^k: the elastic law where the trial state does not yield;
  * K tr(d eps) I + (sigma_y/q)(2 mu dev d eps - 3 mu s (s : d eps)/q^2) where it
  * does, s the trial deviator, q = sqrt(3/2 s:s)); masked columns removed and
- * y_c = x_c.  x, y: [D], distinct. */
-int fem_j2_tangent_apply(fem_mesh_t m, const fem_j2_material *mat, const uint8_t *mask, const double *u,
-                         const double *hist, const double *x, double *y, void *stream);
+ * y_c = x_c.  precision FEM_FP64 (x, y double) or FEM_FP32 (x, y float,
+ * computed in FP32 from the FP64 u and history: the apply of the mixed
+ * mode).  x, y: [D], distinct. */
+int fem_j2_tangent_apply(fem_mesh_t m, const fem_j2_material *mat, int precision, const uint8_t *mask,
+                         const double *u, const double *hist, const void *x, void *y, void *stream);
 
 /* One load step: u_c = u_bar_c on masked DOFs, then Newton on the free DOFs
  * with Jacobi-PCG on the consistent tangent (tolerance cg_rtol, at most

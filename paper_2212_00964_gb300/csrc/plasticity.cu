@@ -263,14 +263,19 @@ extern "C" int fem_j2_residual(fem_mesh_t m, const fem_j2_material *mat, const u
     return FEM_OK;
 }
 
-extern "C" int fem_j2_tangent_apply(fem_mesh_t m, const fem_j2_material *mat, const uint8_t *mask, const double *u,
-                                    const double *hist, const double *x, double *y, void *stream)
+extern "C" int fem_j2_tangent_apply(fem_mesh_t m, const fem_j2_material *mat, int precision, const uint8_t *mask,
+                                    const double *u, const double *hist, const void *x, void *y, void *stream)
 {
     if (int rc = check_args(m, mat, "fem_j2_tangent_apply")) return rc;
     if (!u || !hist || !x || !y || x == y)
         return (set_error("fem_j2_tangent_apply: NULL argument or x aliases y"), FEM_ERR_ARG);
     std::lock_guard<std::mutex> lk(m->mu);
-    return apply_launch<double>(geo(m, mat), mask, u, hist, x, y, nullptr, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == FEM_FP64)
+        return apply_launch<double>(geo(m, mat), mask, u, hist, (const double *)x, (double *)y, nullptr, s);
+    if (precision == FEM_FP32)
+        return apply_launch<float>(geo(m, mat), mask, u, hist, (const float *)x, (float *)y, nullptr, s);
+    return (set_error("fem_j2_tangent_apply: precision must be FEM_FP64 or FEM_FP32"), FEM_ERR_ARG);
 }
 
 extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precision, const uint8_t *mask,

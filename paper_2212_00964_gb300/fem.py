@@ -100,7 +100,7 @@ def lib():
     L.fem_bicgstab_csr.argtypes = [P, I, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     JP = ctypes.POINTER(fem_j2_material)
     L.fem_j2_residual.argtypes = [P, JP, P, P, P, P, P, ctypes.POINTER(I64), P]
-    L.fem_j2_tangent_apply.argtypes = [P, JP, P, P, P, P, P, P]
+    L.fem_j2_tangent_apply.argtypes = [P, JP, I, P, P, P, P, P, P]
     L.fem_j2_step.argtypes = [P, JP, I, P, P, P, P, D, I, D, I, ctypes.POINTER(I), ctypes.POINTER(I),
                               ctypes.POINTER(I64), P]
     L.fem_density_filter.argtypes = [P, D, I, P, P, P]
@@ -471,11 +471,14 @@ def fem_j2_residual(m: Mesh, mat: fem_j2_material, u, hist, mask=None, r=None, h
 
 
 def fem_j2_tangent_apply(m: Mesh, mat: fem_j2_material, u, hist, x, mask=None, y=None, stream=None):
+    """y = K(u) x; x float64 (FP64) or float32 (FP32 from the FP64 state)."""
     H = 12 * 8 * m.n_cells
+    dt = x.dtype
     y = torch.empty_like(x) if y is None else y
-    _check(lib().fem_j2_tangent_apply(m.handle, ctypes.byref(mat), _ptr(mask, torch.uint8, m.n_dofs, "mask"),
+    _check(lib().fem_j2_tangent_apply(m.handle, ctypes.byref(mat), _prec(dt),
+                                      _ptr(mask, torch.uint8, m.n_dofs, "mask"),
                                       _ptr(u, torch.float64, m.n_dofs, "u"), _ptr(hist, torch.float64, H, "hist"),
-                                      _ptr(x, torch.float64, m.n_dofs, "x"), _ptr(y, torch.float64, m.n_dofs, "y"),
+                                      _ptr(x, dt, m.n_dofs, "x"), _ptr(y, dt, m.n_dofs, "y"),
                                       _stream(stream)), "fem_j2_tangent_apply")
     return y
 

@@ -52,6 +52,7 @@ def test_host_only_calls():
     assert "NULL mesh" in L.fem_last_error().decode()
     jm = fem.j2_material(70e3, 0.3, 250.0)
     assert L.fem_j2_residual(None, ctypes.byref(jm), None, None, None, None, None, None, None) == fem.FEM_ERR_ARG
+    assert L.fem_j2_tangent_apply(None, ctypes.byref(jm), 0, None, None, None, None, None, None) == fem.FEM_ERR_ARG
     assert L.fem_j2_step(None, ctypes.byref(jm), 0, None, None, None, None, 1e-10, 10, 1e-10, 10, None, None,
                          None, None) == fem.FEM_ERR_ARG
     assert L.fem_density_filter(None, 1.5, 0, None, None, None) == fem.FEM_ERR_ARG

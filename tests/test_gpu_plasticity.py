@@ -47,8 +47,11 @@ def test_residual_and_tangent_parity():
     assert rel_l2(host(r), R_ref) <= 1e-10
     assert rel_l2(host(h_new), to_soa(new_ref)) <= 1e-12
     x = rng.standard_normal(om.n_dofs)
+    ref = pl.tangent_apply(om, omat, hist, u, x, mask)
     y = F.fem_j2_tangent_apply(m, mat, dev(u), dev(to_soa(hist)), dev(x), dev(mask))
-    assert rel_l2(host(y), pl.tangent_apply(om, omat, hist, u, x, mask)) <= 1e-10
+    assert rel_l2(host(y), ref) <= 1e-10
+    y32 = F.fem_j2_tangent_apply(m, mat, dev(u), dev(to_soa(hist)), dev(x, torch.float32), dev(mask))
+    assert y32.dtype == torch.float32 and rel_l2(host(y32), ref) <= 1e-5
 
 
 @pytest.mark.parametrize("mixed", [False, True])
