@@ -52,8 +52,10 @@ NH_APPLY_FLOPS_PER_CELL = 3269
 # F 3 and cof F 27 -> 8 x 221 + 965 = 2,733; kernel 6 (scalars and the
 # displacement gradient stored) also skips the 3 x 96 flops of the gradient of
 # u -> 2,445.
+# Kernels 8 and 9 are kernels 1 and 6 evaluated two Gauss points per packed
+# FP32 instruction: the same algorithmic flops.
 APPLY_FLOPS_PER_CELL = {1: NH_APPLY_FLOPS_PER_CELL, 2: NH_APPLY_FLOPS_PER_CELL, 3: NH_APPLY_FLOPS_PER_CELL,
-                        4: 2517, 5: 2733, 6: 2445, 7: 2445}
+                        4: 2517, 5: 2733, 6: 2445, 7: 2445, 8: NH_APPLY_FLOPS_PER_CELL, 9: 2445}
 # DRAM bytes (read + write) of one launch of a CG apply kernel, by apply
 # kernel id, from the ncu capture summarised in profiles/ (kernel 6:
 # cg_apply_nh64_kernel6.md; cold caches under ncu).  Valid only for the kernel
@@ -63,6 +65,9 @@ APPLY_TRAFFIC_SOURCES = ("paper_2212_00964_gb300/csrc/cell_kernels.cuh", "paper_
 APPLY_TRAFFIC_SHA256 = "075c317aa4c533f1b6d4b864e693bdf6a94698b9a13a59964bdb02b9c0c8f71b"
 # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 peak: measured on a GB300 with a DFMA throughput loop (1.196 TFLOP/s;
+# 8 independent chains per thread, 8 blocks of 256 threads per SM).
+FP64_PEAK_TFLOPS = 1.196
 # Bytes a launch must move (u, x read; y written; FP32): 12 * D.
 SAMPLE_N = 8
 
@@ -90,7 +95,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--pcg-rtol", type=float, default=3e-3, help="inner CG relative tolerance")
     ap.add_argument("--apply-kernel", type=int, default=0,
-                    help="0 autotuned, 1 per-cell, 2 bricks, 3 per-cell 4 CTA/SM, 4/5/6 stored tangent data")
+                    help="0 autotuned, 1 per-cell, 2 bricks, 3 per-cell 4 CTA/SM, 4/5/6/7 stored tangent data, "
+                         "8/9 packed Gauss-point pairs (recomputed / stored data)")
     ap.add_argument("--newton-res32", type=int, default=1,
                     help="0: FP64 Newton residual in every iteration")
     ap.add_argument("--cg-fused", type=int, default=0,
@@ -302,6 +308,18 @@ def suite(F, inputs, torch):
         return F.fem_solve(m, mat, mask, ubar, u, None, sc, w.n_steps, opt)
 
     tf, stf = timed(fwd4)
+    # the all-FP64 GPU solve of the same problem: mixed vs FP64 relative L2
+    u_mixed = u.clone()
+    o64 = F.default_options(precision=F.FEM_FP64, newton_rtol=1e-10)
+    torch.cuda.synchronize()
+    t64_0 = time.perf_counter()
+    u.zero_()
+    st64 = F.fem_solve(m, mat, mask, ubar, u, None, sc, w.n_steps, o64)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t64_0
+    rel64 = float(torch.linalg.norm(u_mixed - u) / torch.linalg.norm(u))
+    u.copy_(u_mixed)
+    del u_mixed
     dJ = torch.zeros_like(u).view(-1, 3)
     dJ[nodes] = 2 * (u.view(-1, 3)[nodes] - target) / len(nodes)
     dJ = dJ.view(-1).contiguous()
@@ -310,7 +328,10 @@ def suite(F, inputs, torch):
                     "newton_iters": stf["newton_iters"], "cg_iters": stf["pcg_iters"],
                     "adjoint_cg_iters": sta["pcg_iters"],
                     "tangent_apply_gdofs": w.n_dofs / (stf["apply_ms"] / max(stf["apply_samples"], 1) / 1e3) / 1e9,
-                    "status": [stf["status"], sta["status"]]}
+                    "fp64_forward_s": t64, "fp64_newton_iters": st64["newton_iters"],
+                    "fp64_note": "one call, including the FP64 apply autotune probes",
+                    "mixed_vs_fp64_rel_l2": rel64,
+                    "status": [stf["status"], sta["status"], st64["status"]]}
     del m, u, g
 
     # standalone tangent apply through the ABI cell operator (fem_tangent_apply:
@@ -437,7 +458,7 @@ def next_suite(F, inputs, torch):
             res[f"apply_{name}"] = {"us": t * 1e6, "gbs_algorithmic": gbs,
                                     "hbm_frac_of_measured": gbs / hbm_peak if hbm_peak else None,
                                     "flops": 54 * m.n_nodes / t,
-                                    "note": "includes the stencil-table build launch"}
+                                    "note": "separable stencil, one launch per call"}
         return res
 
     guarded("poisson_50x50x10", lambda: poisson(50, 50, 10))
@@ -445,33 +466,40 @@ def next_suite(F, inputs, torch):
 
     def j2_apply():
         """The tangent apply alone (fem_j2_tangent_apply, FP64 and the FP32
-        apply of the mixed mode) at 32^3 on the yielded uniaxial state:
-        about 4,400 operations per cell."""
-        n = 32
-        mask_h, ubars, _, (E, nu, sy) = inputs.j2_uniaxial(n=n)
+        apply of the mixed mode) at 64^3 at a Newton iterate of the uniaxial
+        path: the accepted state of load step 5 scaled to the strain of step
+        6 (the path is homogeneous), with step 5's history, so that every
+        Gauss point has a definite branch; about 4,400 operations per cell."""
+        n = 64
+        mask_h, ubars, strains, (E, nu, sy) = inputs.j2_uniaxial(n=n)
         m = F.fem_mesh(n, n, n)
         mat = F.j2_material(E, nu, sy)
         mask = torch.tensor(mask_h, device="cuda")
         u = torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda")
         hist = F.j2_history(m)
-        F.fem_j2_step(m, mat, mask, torch.tensor(ubars[4], device="cuda"), u, hist, mixed=True)
-        res = {"cells": m.n_cells, "note": "includes the y memset and the masked-row pass"}
+        for b in ubars[:5]:
+            F.fem_j2_step(m, mat, mask, torch.tensor(b, device="cuda"), u, hist, mixed=True)
+        u_it = u * (strains[5] / strains[4])
+        _, n_yield = F.fem_j2_residual(m, mat, u_it, hist, mask)
+        res = {"cells": m.n_cells, "gauss_points_yielding": int(n_yield), "gauss_points": 8 * m.n_cells,
+               "note": "includes the y memset and the masked-row pass"}
         for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
             x = torch.randn(m.n_dofs, dtype=dt, device="cuda")
-            F.fem_j2_tangent_apply(m, mat, u, hist, x, mask)
+            F.fem_j2_tangent_apply(m, mat, u_it, hist, x, mask)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(10):
-                F.fem_j2_tangent_apply(m, mat, u, hist, x, mask)
+                F.fem_j2_tangent_apply(m, mat, u_it, hist, x, mask)
             e1.record()
             e1.synchronize()
             t = e0.elapsed_time(e1) / 10 / 1e3
             tf = 4400 * m.n_cells / t / 1e12
             res[name] = {"us": t * 1e6, "tflops": tf,
-                         "frac_fp32_peak": tf / FP32_PEAK_TFLOPS if name == "fp32" else None}
+                         "frac_fp32_peak": tf / FP32_PEAK_TFLOPS if name == "fp32" else None,
+                         "frac_fp64_peak": tf / FP64_PEAK_TFLOPS if name == "fp64" else None}
         return res
 
-    guarded("j2_apply_32cube", j2_apply)
+    guarded("j2_apply_64cube", j2_apply)
 
     def j2_path(mixed):
         n = 16
@@ -611,13 +639,18 @@ def run_gb300(args):
     fp64 = None
     if not args.no_fp64:
         o64 = F.default_options(precision=F.FEM_FP64, newton_rtol=1e-10, pcg_rtol=args.pcg_rtol)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st64 = solve_once(o64)
-        torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
+        solve_once(o64)  # warm-up: autotune probes and graph capture of the FP64 solver
+        t64s = []
+        for _ in range(3):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st64 = solve_once(o64)
+            torch.cuda.synchronize()
+            t64s.append(time.perf_counter() - t0)
+        t64 = statistics.median(t64s)
         rel = float(torch.linalg.norm(u - u_mixed) / torch.linalg.norm(u))
-        fp64 = {"newton_solve_s": t64, "value": D / t64 / 1e6, "unit": "MDOF/s",
+        fp64 = {"newton_solve_s": t64, "repeats_s": t64s, "value": D / t64 / 1e6, "unit": "MDOF/s",
                 "tangent_apply_gdofs": D / (st64["apply_ms"] / max(st64["apply_samples"], 1) / 1e3) / 1e9,
                 "newton_iters": st64["newton_iters"], "pcg_iters": st64["pcg_iters"],
                 "mixed_vs_fp64_rel_l2": rel, "speedup_mixed_vs_fp64": t64 / (statistics.mean(step_ms) / 1e3)}
@@ -676,7 +709,9 @@ def run_gb300(args):
                                 4: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN=1>",
                                 5: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN=2>",
                                 6: "cell_kernel<float,NH,CM_APPLY_PCG,3,KIN=3>",
-                                7: "cell_kernel<float,NH,CM_APPLY_PCG,4,KIN=3>"}.get(st0.get("apply_kernel"), "?"),
+                                7: "cell_kernel<float,NH,CM_APPLY_PCG,4,KIN=3>",
+                                8: "cell_apply_x2<NH,CM_APPLY_PCG,KIN=0>",
+                                9: "cell_apply_x2<NH,CM_APPLY_PCG,KIN=3>"}.get(st0.get("apply_kernel"), "?"),
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": apply_traffic(st0.get("apply_kernel")),
                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",

@@ -342,7 +342,11 @@ typedef struct {
                                 Gauss point (cof(F) rebuilt from the state),
                             6 = as 5 also storing the cell's displacement
                                 gradient (no displacement gather in the apply),
-                            7 = as 6 with a register budget for 4 CTAs per SM */
+                            7 = as 6 with a register budget for 4 CTAs per SM,
+                            8 = as 1 with two Gauss points per instruction (packed
+                                FP32 pairs; FEM_MIXED only, FEM_FP64 runs 1),
+                            9 = as 6 with two Gauss points per instruction
+                                (FEM_MIXED only, FEM_FP64 runs 6) */
     int cg_fused;        /* 0: separate CG apply and update kernels; 1: one fused kernel per CG
                             iteration (the vector update of the previous iteration recomputed
                             per node inside the tangent apply) with apply kernels 1 and 5

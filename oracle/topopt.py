@@ -5,8 +5,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 One design iteration, as Sec. 3 lays out the PDE-CO loop:
   1. forward solve of the SIMP problem, Eqs. (29)-(30), with the per-cell
-     density theta (``oracle.solve.linear_solve``; the SIMP law of the
-     oracle, reading r11);
+     density theta (``oracle.solve.linear_solve`` with the oracle's SIMP
+     law E(theta) = E_min + theta^p (1 - E_min));
   2. compliance c = f . u (Eq. (31); for a nodal load vector f the boundary
      integral of u^h . t is f . U) and its gradient by the adjoint method
      (``oracle.solve.adjoint_gradient`` with dJ/du = f);

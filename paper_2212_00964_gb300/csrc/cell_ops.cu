@@ -7,6 +7,7 @@
 
 #include "cell_kernels.cuh"
 #include "cell_ops.cuh"
+#include "cell_x2.cuh"
 #include "mesh.cuh"
 
 namespace femgb {
@@ -123,9 +124,27 @@ static void warm_one()
     resident_grid((const void *)apply_brick<T, NH>, BRICK_X * BRICK_Y * BRICK_Z, 0);
 }
 
+static const void *apply_x2_func(bool nh, int mode, int kin, bool batched)
+{
+    if (mode == CM_APPLY)
+        return nh ? (const void *)cell_apply_x2<1, CM_APPLY, 0, false> : (const void *)cell_apply_x2<0, CM_APPLY, 0, false>;
+    if (nh && kin == 3)
+        return batched ? (const void *)cell_apply_x2<1, CM_APPLY_PCG, 3, true>
+                       : (const void *)cell_apply_x2<1, CM_APPLY_PCG, 3, false>;
+    if (nh)
+        return batched ? (const void *)cell_apply_x2<1, CM_APPLY_PCG, 0, true>
+                       : (const void *)cell_apply_x2<1, CM_APPLY_PCG, 0, false>;
+    return batched ? (const void *)cell_apply_x2<0, CM_APPLY_PCG, 0, true>
+                   : (const void *)cell_apply_x2<0, CM_APPLY_PCG, 0, false>;
+}
+
 void warm_occupancy(bool nh)
 {
     device_sms();
+    for (int b = 0; b < 2; ++b) {
+        resident_grid(apply_x2_func(nh, CM_APPLY_PCG, 0, b), CELL_BLOCK, 0);
+        if (nh) resident_grid(apply_x2_func(nh, CM_APPLY_PCG, 3, b), CELL_BLOCK, 0);
+    }
     if (nh) {
         warm_one<float, 1>();
         warm_one<double, 1>();
@@ -134,6 +153,19 @@ void warm_occupancy(bool nh)
         warm_one<double, 0>();
     }
 }
+// CG apply packed over Gauss-point pairs (FP32 only): kin 0 recomputes the
+// kinematics, kin 3 reads the gradient and scalars stored by the diagonal.
+cudaError_t launch_apply_x2(bool nh, int kin, const CellArgs<float> &a, cudaStream_t s)
+{
+    if (kin == 3 && (!nh || !a.kin || a.kin_mode != 3)) return cudaErrorInvalidValue;
+    const bool batched = a.tab != nullptr;
+    auto f = (void (*)(const CellArgs<float>))apply_x2_func(nh, CM_APPLY_PCG, kin, batched);
+    int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, 0));
+    if (g < 1) return cudaSuccess;
+    count_launch();
+    return launch_pdl(f, (int)g, CELL_BLOCK, 0, s, a);  // begins with pdl_wait()
+}
+
 template <typename T>
 cudaError_t launch_apply_brick(bool nh, const CellArgs<T> &a, cudaStream_t s)
 {
@@ -277,10 +309,43 @@ static int residual_t(fem_mesh_t m, const fem_material *mat, const T *u, const T
     return FEM_OK;
 }
 
+// y = mask ? x : 0 (the prescribed rows of the eliminated tangent apply)
+template <typename T>
+__global__ void k_apply_init(T *y, const T *x, const uint8_t *mask, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (mask && mask[i]) ? x[i] : (T)0;
+}
+
+// FP32 tangent apply on an atomic-scatter mesh: the prescribed rows are
+// written first, then one packed cell kernel adds the free rows.
+static int apply_x2_standalone(fem_mesh_t m, const fem_material *mat, const float *u, const float *cp,
+                               const uint8_t *mask, const float *x, float *y, cudaStream_t s)
+{
+    const int64_t D = m->n_dofs();
+    k_apply_init<float><<<vgrid(D), 256, 0, s>>>(y, x, mask, D);
+    count_launch();
+    CellArgs<float> a{};
+    a.d0 = make_desc(m, mat);
+    a.n_tiles = (m->n_cells + CELL_BLOCK - 1) / CELL_BLOCK;
+    a.u = u; a.x = x; a.y = y; a.cell_param = cp; a.mask = mask;
+    const bool nh = mat->kind == FEM_NEOHOOKE;
+    auto f = (void (*)(const CellArgs<float>))apply_x2_func(nh, CM_APPLY, 0, false);
+    int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, 0));
+    if (g >= 1) {
+        count_launch();
+        FEM_CUDA(launch_pdl(f, (int)g, CELL_BLOCK, 0, s, a));  // waits before its first add into y
+    }
+    FEM_CUDA(cudaGetLastError());
+    return FEM_OK;
+}
+
 template <typename T>
 static int apply_t(fem_mesh_t m, const fem_material *mat, const T *u, const T *cp, const uint8_t *mask, const T *x,
                    T *y, cudaStream_t s)
 {
+    if (std::is_same<T, float>::value && !m->det)
+        return apply_x2_standalone(m, mat, (const float *)u, (const float *)cp, mask, (const float *)x, (float *)y, s);
     const int64_t D = m->n_dofs();
     FEM_CUDA(cudaMemsetAsync(y, 0, sizeof(T) * D, s));
     CellArgs<T> a{};

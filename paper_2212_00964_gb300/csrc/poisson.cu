@@ -4,9 +4,9 @@
 // of Eq. (26) with its adjoint gradient.
 //
 // Layout: one value per node, node id = i + (nx+1)(j + (ny+1)k); the mask is
-// per node (1 = u prescribed).  The stencil tables (27 node classes x 27
-// offsets, per operator) are built by one thread on the device and staged
-// in shared memory by every block of the operator kernel.
+// per node (1 = u prescribed).  The operators are applied in the separable
+// form of poisson_core.cuh: products of per-axis 3-point filters, evaluated
+// plane by plane with the y and x filters staged in shared memory.
 //
 // CG (dev_pcg.cuh) keeps its scalars on the device: no launch waits on the
 // host, which reads the residual norms once every 8 iterations.
@@ -31,53 +31,115 @@ constexpr int MAX_ITERS = 1000000;
 
 // workspace slots of this path
 enum {
-    WS_PTAB = 48, WS_PR, WS_PZ, WS_PP, WS_PQ, WS_PDINV, WS_PSC, WS_PRHS, WS_PSMALL,
-    WS_PTAB32, WS_PMSMALL, WS_PR32, WS_PC32, WS_PQ64
+    WS_PR = 49, WS_PZ, WS_PP, WS_PQ, WS_PDINV, WS_PSC, WS_PRHS, WS_PSMALL,
+    WS_PMSMALL = 58, WS_PR32, WS_PC32, WS_PQ64
 };
 
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + PB - 1) / PB, 152 * 8)); }
 
-// Both stencil tables in the value type T: tab[0, TAB) stiffness, [TAB, 2 TAB) mass.
-// Built in double by one thread (a few thousand adds), converted by the block.
-template <typename T>
-__global__ void k_pois_tables(double hx, double hy, double hz, double alpha, T *tab)
-{
-    __shared__ double t[2 * poisson::TAB];
-    __shared__ double scratch[128];
-    if (threadIdx.x == 0) poisson::stencil_tables(hx, hy, hz, alpha, t, scratch);
-    __syncthreads();
-    for (int i = threadIdx.x; i < 2 * poisson::TAB; i += blockDim.x) tab[i] = (T)t[i];
-}
+// Operator kernel in the separable form of poisson_core.cuh (axis_stencils):
+// each block owns a tile of SX x SY node columns (a one-node halo included,
+// so it writes (SX - 2) x (SY - 2) columns) over SZ consecutive planes.
+// Every thread holds the x values of its column for the SZ + 2 planes it
+// needs (all loads issued before any arithmetic), and per output plane
+//   1. filters along z:  a = M_z x, b = K_z x            (its own column)
+//   2. filters along y:  c = M_y a, e = K_y a + M_y b     (shared memory)
+//   3. filters along x:  y = alpha (K_x c + M_x e)  or  M_x c for the mass.
+// One read of x (plus halo re-reads from L2), one of the mask and one write
+// of y per node: HBM-bound.  dot != nullptr adds sum_n x_n y_n (one atomic
+// per block).
+constexpr int SX = 32, SY = 16, SZ = 16;
 
-// y = op x for every node (mode: poisson::OUT_*); with dot != nullptr also
-// adds sum_n x_n y_n to *dot (one atomic per block).
 template <typename T>
-__global__ void __launch_bounds__(PB) k_pois_op(const T *__restrict__ tab, const T *__restrict__ x,
-                                               const uint8_t *__restrict__ mask, int mode, T *__restrict__ y,
-                                               int nx, int ny, int nz, int64_t N, double *dot)
+__global__ void __launch_bounds__(SX * SY) k_pois_sep(const T *__restrict__ x, const uint8_t *__restrict__ mask,
+                                                     int op, int mode, T alpha, T hx, T hy, T hz,
+                                                     T *__restrict__ y, int nx, int ny, int nz, double *dot)
 {
-    __shared__ T st[poisson::TAB];
-    __shared__ double sh[PB / 32];
-    for (int t = threadIdx.x; t < poisson::TAB; t += PB) st[t] = tab[t];
-    __syncthreads();
-    T acc = 0;
-    for (int64_t n = blockIdx.x * (int64_t)PB + threadIdx.x; n < N; n += (int64_t)gridDim.x * PB) {
-        const T v = poisson::operator_row<T, T>(st, x, mask, mode, n, nx, ny, nz);
-        y[n] = v;
-        if (dot) acc += x[n] * v;
+    __shared__ T sa[SY][SX + 1], sb[SY][SX + 1], sc[SY][SX + 1], se[SY][SX + 1];
+    __shared__ double sh[SX * SY / 32];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = (int)blockIdx.x * (SX - 2) - 1 + tx;
+    const int j = (int)blockIdx.y * (SY - 2) - 1 + ty;
+    const int k0 = (int)blockIdx.z * SZ;
+    const int kend = min(k0 + SZ, nz + 1);  // output planes [k0, kend)
+    const bool col = i >= 0 && i <= nx && j >= 0 && j <= ny;
+    const bool out = col && tx >= 1 && tx <= SX - 2 && ty >= 1 && ty <= SY - 2;
+    const int64_t sxn = nx + 1, sxy = (int64_t)(nx + 1) * (ny + 1);
+    const int64_t base = col ? i + sxn * j : 0;
+    // x of this column at planes k0 - 1 .. k0 + SZ (zero outside the box and,
+    // for the eliminated operator, on prescribed nodes); mask bits of the same
+    T xc[SZ + 2];
+    unsigned mbits = 0;
+#pragma unroll
+    for (int t = 0; t < SZ + 2; ++t) {
+        const int kk = k0 - 1 + t;
+        T v = (T)0;
+        if (col && kk >= 0 && kk <= nz && kk <= kend) {
+            const int64_t n = base + sxy * kk;
+            v = x[n];
+            if (mask && mask[n]) {
+                mbits |= 1u << t;
+                if (mode == poisson::OUT_ELIM) v = (T)0;
+            }
+        }
+        xc[t] = v;
+    }
+    T kx[3], mx[3], ky[3], my[3];
+    poisson::axis_stencils<T>(i, nx, hx, kx, mx);
+    poisson::axis_stencils<T>(j, ny, hy, ky, my);
+    if (op == 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            kx[d] *= alpha;
+            mx[d] *= alpha;
+        }
+    }
+    double acc = 0;
+#pragma unroll
+    for (int p = 0; p < SZ; ++p) {
+        const int kk = k0 + p;
+        if (kk >= kend) break;  // uniform per block
+        T kz[3], mz[3];
+        poisson::axis_stencils<T>(kk, nz, hz, kz, mz);
+        sa[ty][tx] = mz[0] * xc[p] + mz[1] * xc[p + 1] + mz[2] * xc[p + 2];
+        sb[ty][tx] = kz[0] * xc[p] + kz[1] * xc[p + 1] + kz[2] * xc[p + 2];
+        __syncthreads();
+        if (ty >= 1 && ty <= SY - 2) {
+            const T a0 = sa[ty - 1][tx], a1 = sa[ty][tx], a2 = sa[ty + 1][tx];
+            sc[ty][tx] = my[0] * a0 + my[1] * a1 + my[2] * a2;
+            if (op == 0)
+                se[ty][tx] = ky[0] * a0 + ky[1] * a1 + ky[2] * a2 + my[0] * sb[ty - 1][tx] + my[1] * sb[ty][tx] +
+                             my[2] * sb[ty + 1][tx];
+        }
+        __syncthreads();
+        if (out) {
+            T v = mx[0] * sc[ty][tx - 1] + mx[1] * sc[ty][tx] + mx[2] * sc[ty][tx + 1];
+            if (op == 0) v = kx[0] * sc[ty][tx - 1] + kx[1] * sc[ty][tx] + kx[2] * sc[ty][tx + 1] + mx[0] * se[ty][tx - 1] +
+                             mx[1] * se[ty][tx] + mx[2] * se[ty][tx + 1];
+            const int64_t n = base + sxy * kk;
+            T xn = xc[p + 1];
+            if ((mbits >> (p + 1)) & 1u) {
+                xn = x[n];
+                if (mode == poisson::OUT_ELIM) v = xn;
+                else if (mode == poisson::OUT_ZERO) v = (T)0;
+            }
+            y[n] = v;
+            if (dot) acc += (double)(xn * v);
+        }
     }
     if (dot) {
-        const double s = block_sum_t<T, PB>(acc, sh);
-        if (threadIdx.x == 0) atomicAdd(dot, s);
+        const double s = block_sum<double, SX * SY>(acc, sh);
+        if (tx == 0 && ty == 0) atomicAdd(dot, s);
     }
 }
 
+// Jacobi diagonal of the eliminated stiffness (separable form)
 template <typename T>
-__global__ void k_pois_dinv(const T *__restrict__ tab, const uint8_t *__restrict__ mask, T *__restrict__ dinv, int nx,
-                            int ny, int nz, int64_t N)
+__global__ void k_pois_dinv(double alpha, double hx, double hy, double hz, const uint8_t *__restrict__ mask,
+                            T *__restrict__ dinv, int nx, int ny, int nz, int64_t N)
 {
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
-        const double d = poisson::diag_row<T>(tab, mask, n, nx, ny, nz);
+        const double d = poisson::sep_diag<double>(alpha, hx, hy, hz, mask, n, nx, ny, nz);
         dinv[n] = d != 0.0 ? (T)(1.0 / d) : (T)0;
     }
 }
@@ -148,27 +210,31 @@ struct Ctx {
     cudaStream_t s;
 };
 
-// Stencil tables for (alpha, the mesh's cell size) in the workspace.
-template <typename T>
-const T *make_tables(const Ctx &c, double alpha, int slot = WS_PTAB)
+// Coefficients of the operators on this mesh: alpha and the cell size.
+struct Coef {
+    double alpha, hx, hy, hz;
+};
+
+Coef coef_of(const Ctx &c, double alpha)
 {
-    T *tab = (T *)c.m->ws.get(slot, sizeof(T) * 2 * poisson::TAB);
-    if (!tab) return nullptr;
-    k_pois_tables<T><<<1, 128, 0, c.s>>>(c.m->lx / c.m->nx, c.m->ly / c.m->ny, c.m->lz / c.m->nz, alpha, tab);
-    count_launch();
-    return tab;
+    return Coef{alpha, c.m->lx / c.m->nx, c.m->ly / c.m->ny, c.m->lz / c.m->nz};
 }
 
+// y = op x (op 0 stiffness, 1 mass; mode: poisson::OUT_*)
 template <typename T>
-void launch_op(const Ctx &c, const T *tab, const T *x, const uint8_t *mask, int mode, T *y, double *dot)
+void launch_op(const Ctx &c, const Coef &k, int op, const T *x, const uint8_t *mask, int mode, T *y, double *dot)
 {
-    k_pois_op<T><<<grid_for(c.N), PB, 0, c.s>>>(tab, x, mask, mode, y, c.m->nx, c.m->ny, c.m->nz, c.N, dot);
+    const fem_mesh_s *m = c.m;
+    const dim3 grid((unsigned)((m->nx + 1 + SX - 3) / (SX - 2)), (unsigned)((m->ny + 1 + SY - 3) / (SY - 2)),
+                    (unsigned)((m->nz + 1 + SZ - 1) / SZ));
+    k_pois_sep<T><<<grid, dim3(SX, SY), 0, c.s>>>(x, mask, op, mode, (T)k.alpha, (T)k.hx, (T)k.hy, (T)k.hz, y, m->nx,
+                                                  m->ny, m->nz, dot);
     count_launch();
 }
 
 // Jacobi-PCG for the eliminated stiffness: A u = b, u in/out.
 template <typename T>
-int cg_solve(const Ctx &c, const T *tabA, const uint8_t *mask, const T *b, T *u, double rtol, int maxit, int *iters,
+int cg_solve(const Ctx &c, const Coef &k, const uint8_t *mask, const T *b, T *u, double rtol, int maxit, int *iters,
              double *rel_res)
 {
     const int64_t N = c.N;
@@ -181,24 +247,23 @@ int cg_solve(const Ctx &c, const T *tabA, const uint8_t *mask, const T *b, T *u,
     w.small = (double *)c.m->ws.get(WS_PSMALL, sizeof(double) * 4);
     T *dinv = (T *)c.m->ws.get(WS_PDINV, sizeof(T) * N);
     if (!w.r || !w.z || !w.p || !w.q || !w.sc || !w.small || !dinv) return FEM_ERR_NOMEM;
-    k_pois_dinv<T><<<grid_for(N), PB, 0, c.s>>>(tabA, mask, dinv, c.m->nx, c.m->ny, c.m->nz, N);
+    k_pois_dinv<T><<<grid_for(N), PB, 0, c.s>>>(k.alpha, k.hx, k.hy, k.hz, mask, dinv, c.m->nx, c.m->ny, c.m->nz, N);
     count_launch();
     auto apply = [&](const T *x, T *y, double *dot) -> int {
-        launch_op<T>(c, tabA, x, mask, poisson::OUT_ELIM, y, dot);
+        launch_op<T>(c, k, 0, x, mask, poisson::OUT_ELIM, y, dot);
         return FEM_OK;
     };
     return dpcg::solve<T>(c.s, N, apply, dinv, b, u, w, rtol, maxit, iters, rel_res, "poisson CG");
 }
 
 // Mixed precision (poisson::refine): FP64 residuals, FP32 CG on the correction.
-int solve_mixed(const Ctx &c, const double *tab64, const float *tab32, const uint8_t *mask, const double *b, double *u,
-                double rtol, int maxit, int *iters, double *rel_res)
+int solve_mixed(const Ctx &c, const Coef &k, const uint8_t *mask, const double *b, double *u, double rtol, int maxit,
+                int *iters, double *rel_res)
 {
     const int64_t N = c.N;
     struct Ops {
         const Ctx &c;
-        const double *tab64;
-        const float *tab32;
+        const Coef &k;
         const uint8_t *mask;
         const double *b;
         double *u, *q64, *acc;
@@ -207,7 +272,7 @@ int solve_mixed(const Ctx &c, const double *tab64, const float *tab32, const uin
         int residual(double *rr, double *bb)
         {
             FEM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * 2, c.s));
-            launch_op<double>(c, tab64, u, mask, poisson::OUT_ELIM, q64, nullptr);
+            launch_op<double>(c, k, 0, u, mask, poisson::OUT_ELIM, q64, nullptr);
             k_pois_refine<<<grid_for(c.N), PB, 0, c.s>>>(b, q64, r32, c.N, acc);
             count_launch();
             FEM_CUDA(cudaGetLastError());
@@ -221,7 +286,7 @@ int solve_mixed(const Ctx &c, const double *tab64, const float *tab32, const uin
         int inner(int maxit_left, int *it)
         {
             FEM_CUDA(cudaMemsetAsync(c32, 0, sizeof(float) * c.N, c.s));
-            return cg_solve<float>(c, tab32, mask, r32, c32, poisson::INNER_RTOL, maxit_left, it, nullptr);
+            return cg_solve<float>(c, k, mask, r32, c32, poisson::INNER_RTOL, maxit_left, it, nullptr);
         }
         int correct()
         {
@@ -232,7 +297,7 @@ int solve_mixed(const Ctx &c, const double *tab64, const float *tab32, const uin
         }
         void fail(const char *what) { set_error(std::string("poisson mixed solve: ") + what); }
     };
-    Ops ops{c, tab64, tab32, mask, b, u,
+    Ops ops{c, k, mask, b, u,
             (double *)c.m->ws.get(WS_PQ64, sizeof(double) * N), (double *)c.m->ws.get(WS_PMSMALL, sizeof(double) * 2),
             (float *)c.m->ws.get(WS_PR32, sizeof(float) * N), (float *)c.m->ws.get(WS_PC32, sizeof(float) * N)};
     if (!ops.q64 || !ops.acc || !ops.r32 || !ops.c32) return FEM_ERR_NOMEM;
@@ -249,11 +314,9 @@ template <typename T>
 int apply_t(fem_mesh_t m, double alpha, int op, const uint8_t *mask, const T *x, T *y, cudaStream_t s)
 {
     Ctx c{m, m->n_nodes, s};
-    const T *tab = make_tables<T>(c, alpha);
-    if (!tab) return FEM_ERR_NOMEM;
     const int mode = op == 0 ? (mask ? poisson::OUT_ELIM : poisson::OUT_PLAIN)
                              : (mask ? poisson::OUT_ZERO : poisson::OUT_PLAIN);
-    launch_op<T>(c, tab + op * poisson::TAB, x, mask, mode, y, nullptr);
+    launch_op<T>(c, coef_of(c, alpha), op, x, mask, mode, y, nullptr);
     FEM_CUDA(cudaGetLastError());
     return FEM_OK;
 }
@@ -263,16 +326,11 @@ int solve_t(fem_mesh_t m, double alpha, const uint8_t *mask, const T *b, T *u, d
             double *rel_res, cudaStream_t s, bool mixed = false)
 {
     Ctx c{m, m->n_nodes, s};
-    const T *tab = make_tables<T>(c, alpha);
-    if (!tab) return FEM_ERR_NOMEM;
+    const Coef k = coef_of(c, alpha);
     if constexpr (std::is_same<T, double>::value) {
-        if (mixed) {
-            const float *tab32 = make_tables<float>(c, alpha, WS_PTAB32);
-            if (!tab32) return FEM_ERR_NOMEM;
-            return solve_mixed(c, tab, tab32, mask, b, u, rtol, maxit, iters, rel_res);
-        }
+        if (mixed) return solve_mixed(c, k, mask, b, u, rtol, maxit, iters, rel_res);
     }
-    return cg_solve<T>(c, tab, mask, b, u, rtol, maxit, iters, rel_res);
+    return cg_solve<T>(c, k, mask, b, u, rtol, maxit, iters, rel_res);
 }
 
 template <typename T>
@@ -282,23 +340,22 @@ int gradient_t(fem_mesh_t m, double alpha, const uint8_t *mask, const T *theta, 
 {
     Ctx c{m, m->n_nodes, s};
     const int64_t N = c.N;
-    const T *tab = make_tables<T>(c, alpha);
+    const Coef k = coef_of(c, alpha);
     T *rhs = (T *)m->ws.get(WS_PRHS, sizeof(T) * N);
-    if (!tab || !rhs) return FEM_ERR_NOMEM;
-    const float *tab32 = nullptr;
-    if (mixed && !(tab32 = make_tables<float>(c, alpha, WS_PTAB32))) return FEM_ERR_NOMEM;
+    if (!rhs) return FEM_ERR_NOMEM;
     auto cg_solve = [&](const uint8_t *mk, const T *bb, T *x, double rt, int mi, int *it, double *rr) -> int {
         if constexpr (std::is_same<T, double>::value) {
-            if (mixed) return solve_mixed(c, tab, tab32, mk, bb, x, rt, mi, it, rr);
+            if (mixed) return solve_mixed(c, k, mk, bb, x, rt, mi, it, rr);
         }
-        return ::femgb::cg_solve<T>(c, tab, mk, bb, x, rt, mi, it, rr);
+        return ::femgb::cg_solve<T>(c, k, mk, bb, x, rt, mi, it, rr);
     };
     double *small = (double *)m->ws.get(WS_PSMALL, sizeof(double) * 4);
     if (!small) return FEM_ERR_NOMEM;
     struct Ops {
         const Ctx &c;
         decltype(cg_solve) &solve;
-        const T *tab, *theta, *u_obs;
+        const Coef &k;
+        const T *theta, *u_obs;
         const uint8_t *mask;
         const int64_t *obs;
         int64_t n_obs;
@@ -310,8 +367,7 @@ int gradient_t(fem_mesh_t m, double alpha, const uint8_t *mask, const T *theta, 
         int load()
         {
             // rhs = M theta (free rows), 0 on masked nodes
-            launch_op<T>(c, tab + poisson::TAB, theta, mask, mask ? poisson::OUT_ZERO : poisson::OUT_PLAIN, rhs,
-                         nullptr);
+            launch_op<T>(c, k, 1, theta, mask, mask ? poisson::OUT_ZERO : poisson::OUT_PLAIN, rhs, nullptr);
             FEM_CUDA(cudaGetLastError());
             return FEM_OK;
         }
@@ -348,14 +404,14 @@ int gradient_t(fem_mesh_t m, double alpha, const uint8_t *mask, const T *theta, 
         int gradient()
         {
             // dJ/dtheta = M^T lambda (M symmetric; lambda vanishes on masked nodes)
-            launch_op<T>(c, tab + poisson::TAB, lam, nullptr, poisson::OUT_PLAIN, grad, nullptr);
+            launch_op<T>(c, k, 1, lam, nullptr, poisson::OUT_PLAIN, grad, nullptr);
             FEM_CUDA(cudaGetLastError());
             FEM_CUDA(cudaStreamSynchronize(c.s));
             return FEM_OK;
         }
         void fail(const char *what) { set_error(std::string("fem_poisson_gradient: ") + what); }
     };
-    Ops ops{c, cg_solve, tab, theta, u_obs, mask, obs, n_obs, rtol, maxit, u, lam, grad, rhs, small};
+    Ops ops{c, cg_solve, k, theta, u_obs, mask, obs, n_obs, rtol, maxit, u, lam, grad, rhs, small};
     const int rc = poisson::objective_gradient(ops, J, iters);
     static_assert((int)poisson::ST_ARG == (int)FEM_ERR_ARG, "argument status");
     return rc;
@@ -369,26 +425,21 @@ int adjoint_t(fem_mesh_t m, double alpha, const uint8_t *mask, const T *dJdu, do
 {
     Ctx c{m, m->n_nodes, s};
     const int64_t N = c.N;
-    const T *tab = make_tables<T>(c, alpha);
+    const Coef k = coef_of(c, alpha);
     T *rhs = (T *)m->ws.get(WS_PRHS, sizeof(T) * N);
-    if (!tab || !rhs) return FEM_ERR_NOMEM;
+    if (!rhs) return FEM_ERR_NOMEM;
     k_pois_free_copy<T><<<grid_for(N), PB, 0, s>>>(dJdu, mask, rhs, N);
     count_launch();
     FEM_CUDA(cudaMemsetAsync(lam, 0, sizeof(T) * N, s));
     int rc;
     if constexpr (std::is_same<T, double>::value) {
-        if (mixed) {
-            const float *tab32 = make_tables<float>(c, alpha, WS_PTAB32);
-            if (!tab32) return FEM_ERR_NOMEM;
-            rc = solve_mixed(c, tab, tab32, mask, rhs, lam, rtol, maxit, iters, nullptr);
-        } else {
-            rc = cg_solve<T>(c, tab, mask, rhs, lam, rtol, maxit, iters, nullptr);
-        }
+        if (mixed) rc = solve_mixed(c, k, mask, rhs, lam, rtol, maxit, iters, nullptr);
+        else rc = cg_solve<T>(c, k, mask, rhs, lam, rtol, maxit, iters, nullptr);
     } else {
-        rc = cg_solve<T>(c, tab, mask, rhs, lam, rtol, maxit, iters, nullptr);
+        rc = cg_solve<T>(c, k, mask, rhs, lam, rtol, maxit, iters, nullptr);
     }
     if (rc != FEM_OK) return rc;
-    launch_op<T>(c, tab + poisson::TAB, lam, nullptr, poisson::OUT_PLAIN, grad, nullptr);
+    launch_op<T>(c, k, 1, lam, nullptr, poisson::OUT_PLAIN, grad, nullptr);
     FEM_CUDA(cudaGetLastError());
     FEM_CUDA(cudaStreamSynchronize(s));
     return FEM_OK;

@@ -153,5 +153,88 @@ POIS_HD double diag_row(const C *tab_stiff, const uint8_t *mask, int64_t n, int 
     return (double)tab_stiff[cls * N_OFF + CENTRE];
 }
 
+// ---- separable form (what the GPU kernel evaluates) ----------------------
+// The cells around a node form a Cartesian product of the cells that exist
+// on each axis, and the element matrices are tensor products of the 1D
+// linear-element matrices, so each 27-point row factorises: with the
+// assembled 1D stencils of axis d at the node's coordinate,
+//   K_d = (-1, 2, -1) / h_d,  M_d = (1, 4, 1) h_d / 6     (interior)
+// and the missing neighbour dropped on a face (K_d = (0, 1, -1) / h_d,
+// M_d = (0, 2, 1) h_d / 6 on the low face, mirrored on the high face),
+//   stiffness row = alpha (K_x M_y M_z + M_x K_y M_z + M_x M_y K_z),
+//   mass row      = M_x M_y M_z,
+// a product of three 3-point filters per term.  Coefficients are those of
+// the output node; entry [d + 1] multiplies the neighbour at offset d.
+template <typename T>
+POIS_HD void axis_stencils(int i, int n, T h, T *k, T *m)
+{
+    const T lo = i > 0 ? (T)1 : (T)0, hi = i < n ? (T)1 : (T)0;
+    const T ih = (T)1 / h, m6 = h / (T)6;
+    k[0] = -lo * ih;
+    k[1] = (lo + hi) * ih;
+    k[2] = -hi * ih;
+    m[0] = lo * m6;
+    m[1] = (T)2 * (lo + hi) * m6;
+    m[2] = hi * m6;
+}
+
+// Operator row (OUT_* modes as operator_row) evaluated in the separable form.
+template <typename T>
+POIS_HD T sep_row(int op, T alpha, T hx, T hy, T hz, const T *x, const uint8_t *mask, int mode, int64_t n, int nx,
+                  int ny, int nz)
+{
+    const int64_t sx = nx + 1, sxy = (int64_t)(nx + 1) * (ny + 1);
+    const int k = (int)(n / sxy);
+    const int64_t rem = n - (int64_t)k * sxy;
+    const int j = (int)(rem / sx);
+    const int i = (int)(rem - (int64_t)j * sx);
+    const bool fixed = mask && mask[n];
+    if (mode == OUT_ELIM && fixed) return x[n];
+    if (mode == OUT_ZERO && fixed) return (T)0;
+    const uint8_t *in_mask = mode == OUT_ELIM ? mask : nullptr;
+    T kx[3], mx[3], ky[3], my[3], kz[3], mz[3];
+    axis_stencils<T>(i, nx, hx, kx, mx);
+    axis_stencils<T>(j, ny, hy, ky, my);
+    axis_stencils<T>(k, nz, hz, kz, mz);
+    T acc = (T)0;
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int kk = k + dz;
+        if (kk < 0 || kk > nz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int jj = j + dy;
+            if (jj < 0 || jj > ny) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int ii = i + dx;
+                if (ii < 0 || ii > nx) continue;
+                const int64_t nb = ii + sx * jj + sxy * kk;
+                const T v = (in_mask && in_mask[nb]) ? (T)0 : x[nb];
+                const T c = op == 0 ? alpha * (kx[dx + 1] * my[dy + 1] * mz[dz + 1] +
+                                               mx[dx + 1] * ky[dy + 1] * mz[dz + 1] +
+                                               mx[dx + 1] * my[dy + 1] * kz[dz + 1])
+                                    : mx[dx + 1] * my[dy + 1] * mz[dz + 1];
+                acc += c * v;
+            }
+        }
+    }
+    return acc;
+}
+
+// Jacobi diagonal of the eliminated stiffness in the separable form.
+template <typename T>
+POIS_HD T sep_diag(T alpha, T hx, T hy, T hz, const uint8_t *mask, int64_t n, int nx, int ny, int nz)
+{
+    if (mask && mask[n]) return (T)1;
+    const int64_t sx = nx + 1, sxy = (int64_t)(nx + 1) * (ny + 1);
+    const int k = (int)(n / sxy);
+    const int64_t rem = n - (int64_t)k * sxy;
+    const int j = (int)(rem / sx);
+    const int i = (int)(rem - (int64_t)j * sx);
+    T kx[3], mx[3], ky[3], my[3], kz[3], mz[3];
+    axis_stencils<T>(i, nx, hx, kx, mx);
+    axis_stencils<T>(j, ny, hy, ky, my);
+    axis_stencils<T>(k, nz, hz, kz, mz);
+    return alpha * (kx[1] * my[1] * mz[1] + mx[1] * ky[1] * mz[1] + mx[1] * my[1] * kz[1]);
+}
+
 }  // namespace poisson
 }  // namespace femgb

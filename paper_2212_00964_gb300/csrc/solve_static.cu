@@ -11,6 +11,14 @@
 // (CG vectors, the FP64 residual, the control block) lives in one file-scope
 // device array of FEM_STATIC_SCRATCH_BYTES.  Every GPU that loads the library
 // holds that array until the process exits.
+//
+// It also makes no synchronisation call: each of its host round trips is a
+// device-to-host copy into pageable host memory, which the CUDA runtime
+// returns from only once the copy is complete.  While another thread holds
+// a global-mode stream capture open, cudaMalloc, cudaStreamSynchronize,
+// cudaStreamQuery and cudaEventSynchronize are refused (and invalidate that
+// capture); kernel launches, memsets and pageable copies on another stream
+// are not.
 #include <cstdio>
 #include <mutex>
 

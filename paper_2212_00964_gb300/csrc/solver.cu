@@ -650,9 +650,9 @@ class Core {
             ca.cell_param = b_.cpT;
             ca.u = b_.uT;
             ca.y = b_.dg;
-            // apply kernels 4 and 5 read the tangent data stored here
-            ca.kin = variant_ >= 4 ? b_.kin : nullptr;
-            ca.kin_mode = variant_ == 7 ? 3 : variant_ - 3;
+            // apply kernels 4-7 and 9 read the tangent data stored here
+            ca.kin_mode = kin_mode_of(variant_);
+            ca.kin = ca.kin_mode ? b_.kin : nullptr;
             if ((e = launch_cell<T>(CM_DIAG_CTL, pb_.nh, ca, s)) != cudaSuccess) return e;
         }
         k_pcg_init<T><<<gv, VEC_BLOCK, 0, s>>>(va_);
@@ -743,9 +743,18 @@ class Core {
         }
         ca.n_tiles = pb_.n_tiles;
         if (variant_ == 3) return launch_apply_cell4<T>(pb_.nh, ca, s);
+        if (variant_ == 8 || variant_ == 9) {
+            ca.kin_mode = kin_mode_of(variant_);
+            ca.kin = ca.kin_mode ? b_.kin : nullptr;
+            if (std::is_same<T, float>::value)
+                return launch_apply_x2(pb_.nh, ca.kin_mode, *(const CellArgs<float> *)&ca, s);
+            // no packed FP64 arithmetic: the scalar kernels of the same data
+            if (variant_ == 9) return launch_apply_kin<T>(pb_.nh, ca, s, false);
+            return launch_cell<T>(CM_APPLY_PCG, pb_.nh, ca, s);
+        }
         if (variant_ >= 4) {
             ca.kin = b_.kin;
-            ca.kin_mode = variant_ == 7 ? 3 : variant_ - 3;
+            ca.kin_mode = kin_mode_of(variant_);
             return launch_apply_kin<T>(pb_.nh, ca, s, variant_ == 7);
         }
         return launch_cell<T>(CM_APPLY_PCG, pb_.nh, ca, s);
@@ -798,20 +807,21 @@ class Core {
             cudaEventDestroy(e0);
             return (cudaGetLastError(), 2);
         }
-        float best = 1e30f, times[7] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
+        float best = 1e30f, times[9] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
         int choice = 1;
-        const int n_var = (pb_.nh && b_.kin) ? 7 : 3;
-        for (int v = 1; v <= n_var; ++v) {
+        const bool stored = pb_.nh && b_.kin, packed = std::is_same<T, float>::value;
+        for (int v = 1; v <= 9; ++v) {
+            if ((v >= 4 && v <= 7 && !stored) || (v == 8 && !packed) || (v == 9 && !(packed && stored))) continue;
             variant_ = v;
             // fresh control blocks for each variant (the apply's epilogue updates them)
             bool ok = cudaMemcpyAsync(b_.tune, tc.data(), sizeof(Ctl) * tc.size(), cudaMemcpyHostToDevice, s) ==
                       cudaSuccess;
-            if (ok && v >= 4) {  // tangent data of the probe state (dg is rebuilt by every head graph)
+            if (ok && kin_mode_of(v)) {  // tangent data of the probe state (dg is rebuilt by every head graph)
                 CellArgs<T> cd = ca;
                 cd.n_tiles = pb_.n_tiles;
                 cd.y = b_.dg;
                 cd.kin = b_.kin;
-                cd.kin_mode = v == 7 ? 3 : v - 3;
+                cd.kin_mode = kin_mode_of(v);
                 ok = launch_cell<T>(CM_DIAG_CTL, pb_.nh, cd, s) == cudaSuccess;
             }
             ok = ok && launch_apply(ca, s) == cudaSuccess;
@@ -838,9 +848,10 @@ class Core {
                 fprintf(stderr,
                         "femgb autotune: D=%lld instances=%d per-cell %.3f ms, bricks %.3f ms, "
                         "per-cell(4 CTA/SM) %.3f ms, stored tangent %.3f ms, stored scalars %.3f ms, "
-                        "stored scalars + gradient %.3f ms (4 CTA/SM %.3f ms) -> %d\n",
+                        "stored scalars + gradient %.3f ms (4 CTA/SM %.3f ms), packed pairs %.3f ms, "
+                        "packed pairs on stored data %.3f ms -> %d\n",
                         (long long)pb_.D, (int)pb_.desc.size(), times[0] / 3, times[1] / 3, times[2] / 3,
-                        times[3] / 3, times[4] / 3, times[5] / 3, times[6] / 3, choice);
+                        times[3] / 3, times[4] / 3, times[5] / 3, times[6] / 3, times[7] / 3, times[8] / 3, choice);
         }
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = choice;
@@ -869,8 +880,9 @@ class Core {
     }
 
     // Same rounds as run(), launched straight onto `s` without graphs,
-    // events or pinned host memory (the counters are read into `hc`, a host
-    // array of 3 ints, with a pageable copy and a stream synchronisation).
+    // events or synchronisation calls: the counters are read into `hc`, a
+    // PAGEABLE host array of at least 3 ints (a device-to-host copy into
+    // pageable memory returns only once the copy has completed).
     int run_direct(cudaStream_t s, double timeout_s, int *hc)
     {
         if (int rc = check_variant()) return rc;
@@ -881,10 +893,11 @@ class Core {
             if (timeout_s <= 0) return false;
             return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > timeout_s;
         };
+        // a copy into pageable host memory returns once the copy is complete,
+        // so no stream synchronisation follows it (one is refused while
+        // another thread holds a global-mode capture open)
         auto read = [&]() -> cudaError_t {
-            cudaError_t e = cudaMemcpyAsync(hc, b_.counter, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            return e;
+            return cudaMemcpyAsync(hc, b_.counter, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
         };
         FEM_CUDA(enqueue_head(s));
         FEM_CUDA(read());
@@ -949,9 +962,9 @@ class Core {
 
     int check_variant() const
     {
-        if (variant_ >= 4 && !(pb_.nh && b_.kin))
-            return (set_error("apply_kernel 4-7 (stored tangent data) needs a Neo-Hookean problem and its buffer "
-                              "(not available in fem_solve_static)"),
+        if (kin_mode_of(variant_) && !(pb_.nh && b_.kin))
+            return (set_error("apply_kernel 4-7 and 9 (stored tangent data) need a Neo-Hookean problem and its "
+                              "buffer (not available in fem_solve_static)"),
                     FEM_ERR_ARG);
         return FEM_OK;
     }
@@ -1005,7 +1018,8 @@ class Core {
     bool fused_ = false;    // CG iterations run as the fused update + apply kernel
     int variant_ = 0;       // CG apply kernel: 0 autotune, 1 per-cell, 2 bricks, 3 per-cell at 4 CTA/SM,
                             // 4 per-cell on stored NH tangent data, 5 on stored NH tangent scalars,
-                            // 6 on stored scalars and displacement gradient, 7 as 6 at 4 CTA/SM
+                            // 6 on stored scalars and displacement gradient, 7 as 6 at 4 CTA/SM,
+                            // 8 as 1 packed over Gauss-point pairs, 9 as 6 packed (FP32 only)
     double apply_ms_ = 0;   // sampled device time of CG applies
     int apply_samples_ = 0;
     double update_ms_ = 0;  // sampled device time of CG vector updates
@@ -1053,7 +1067,7 @@ static int check_options(const fem_options &o)
         return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
     if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
         !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
-        o.apply_kernel < 0 || o.apply_kernel > 7 || o.cg_fused < 0 || o.cg_fused > 1 || o.newton_res32 < 0 ||
+        o.apply_kernel < 0 || o.apply_kernel > 9 || o.cg_fused < 0 || o.cg_fused > 1 || o.newton_res32 < 0 ||
         o.newton_res32 > 1)
         return (set_error("invalid solver options"), FEM_ERR_ARG);
     return FEM_OK;
@@ -1318,6 +1332,12 @@ size_t region_bytes(const InstDesc &d, int precision, bool has_cp)
                                  : region_layout<float>(d, has_cp, nullptr, nullptr);
 }
 
+// Writes one control block from a kernel parameter (no host copy).
+__global__ void k_ctl_set(Ctl *c, const Ctl v)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *c = v;
+}
+
 template <typename T>
 static int solve_region_t(const InstDesc &d, int n_steps, const fem_bc &bc, const double *cp64,
                           const fem_options &o, double *u64, void *region, Ctl &ctl_out, cudaStream_t s)
@@ -1354,15 +1374,16 @@ static int solve_region_t(const InstDesc &d, int n_steps, const fem_bc &bc, cons
     c0.step = std::min(o.step_begin, n_steps);
     c0.need_bc = 1;
     c0.r_ref = -1.0;
-    FEM_CUDA(cudaMemcpyAsync(b.ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    k_ctl_set<<<1, 32, 0, s>>>(b.ctl, c0);
+    count_launch();
+    FEM_CUDA(cudaGetLastError());
     FEM_CUDA(cudaMemsetAsync(b.counter, 0, 4 * sizeof(int), s));
-    int hc[4] = {0, 0, 0, 0};
+    int hc[4] = {0, 0, 0, 0};  // pageable: each read returns once its copy is complete
     Core<T> core(pb, b, SM_NONLINEAR, params_from(o), hc);
     core.max_steps_ = n_steps;
     core.variant_ = o.apply_kernel;
     int rc = core.run_direct(s, o.timeout_s, hc);
     cudaError_t e = cudaMemcpyAsync(&ctl_out, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (rc) return rc;
     FEM_CUDA(e);
     return FEM_OK;

@@ -27,7 +27,8 @@ int tgrid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + T
 
 __device__ __forceinline__ void stage_weights(double rmin, double *w)
 {
-    if (threadIdx.x == 0) topopt::filter_weights(rmin, w);
+    const int R = topopt::filter_radius(rmin), W = 2 * R + 1;
+    for (int t = threadIdx.x; t < W * W * W; t += blockDim.x) w[t] = topopt::filter_weight_at(rmin, R, t);
     __syncthreads();
 }
 

@@ -34,16 +34,19 @@ namespace topopt {
 // w[(di + R) + W (dj + R) + W^2 (dk + R)], W = 2R + 1 (0 beyond rmin).
 TO_HD int filter_radius(double rmin) { return (int)ceil(rmin) - 1; }
 
+// One entry t = (di + R) + W (dj + R) + W^2 (dk + R) of the cone table.
+TO_HD double filter_weight_at(double rmin, int R, int t)
+{
+    const int W = 2 * R + 1;
+    const int di = t % W - R, dj = (t / W) % W - R, dk = t / (W * W) - R;
+    const double v = rmin - sqrt((double)(di * di + dj * dj + dk * dk));
+    return v > 0.0 ? v : 0.0;
+}
+
 TO_HD void filter_weights(double rmin, double *w)
 {
     const int R = filter_radius(rmin), W = 2 * R + 1;
-    for (int dk = -R; dk <= R; ++dk)
-        for (int dj = -R; dj <= R; ++dj)
-            for (int di = -R; di <= R; ++di) {
-                const double d = sqrt((double)(di * di + dj * dj + dk * dk));
-                const double v = rmin - d;
-                w[(di + R) + W * (dj + R) + W * W * (dk + R)] = v > 0.0 ? v : 0.0;
-            }
+    for (int t = 0; t < W * W * W; ++t) w[t] = filter_weight_at(rmin, R, t);
 }
 
 // sum over the in-box neighbours f of cell e of w_ef * val(f)

@@ -32,6 +32,21 @@ void host_apply_f32(int nx, int ny, int nz, const double *tab, int op, int mode,
     for (int64_t n = 0; n < N; ++n) y[n] = operator_row<float, float>(tf + op * TAB, x, mask, mode, n, nx, ny, nz);
 }
 
+void host_apply_sep(int nx, int ny, int nz, double lx, double ly, double lz, double alpha, int op, int mode,
+                    const double *x, const uint8_t *mask, double *y)
+{
+    const int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+    for (int64_t n = 0; n < N; ++n)
+        y[n] = sep_row<double>(op, alpha, lx / nx, ly / ny, lz / nz, x, mask, mode, n, nx, ny, nz);
+}
+
+void host_diag_sep(int nx, int ny, int nz, double lx, double ly, double lz, double alpha, const uint8_t *mask,
+                   double *d)
+{
+    const int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+    for (int64_t n = 0; n < N; ++n) d[n] = sep_diag<double>(alpha, lx / nx, ly / ny, lz / nz, mask, n, nx, ny, nz);
+}
+
 void host_diag(int nx, int ny, int nz, const double *tab, const uint8_t *mask, double *d)
 {
     const int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);

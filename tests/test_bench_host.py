@@ -22,7 +22,7 @@ def test_workload_name_counts_dofs():
 
 def test_traffic_only_for_the_captured_kernel_and_sources():
     b = load_bench()
-    for k in range(1, 8):
+    for k in range(1, 10):
         t = b.apply_traffic(k)
         assert (t is None) == (k not in b.APPLY_TRAFFIC_BYTES)
     k = next(iter(b.APPLY_TRAFFIC_BYTES))
@@ -33,20 +33,19 @@ def test_traffic_only_for_the_captured_kernel_and_sources():
 
 def test_every_apply_kernel_has_a_flop_count_and_name():
     b = load_bench()
-    assert set(b.APPLY_FLOPS_PER_CELL) == set(range(1, 8))
+    assert set(b.APPLY_FLOPS_PER_CELL) == set(range(1, 10))
     assert all(0 < v <= b.NH_APPLY_FLOPS_PER_CELL for v in b.APPLY_FLOPS_PER_CELL.values())
 
 
-def test_gpu_tests_of_unrun_paths_are_collected_last():
-    """The conftest hook orders every gpu_new test after all other GPU tests,
-    so a stop on the first failure cannot hide the established ones."""
+def test_allocation_free_solve_tests_are_collected_last():
+    """The fem_solve_static tests run after every other GPU test, so a stop
+    on the first failure (-x) has already run all the others."""
     import subprocess
     import sys
     out = subprocess.run([sys.executable, "-m", "pytest", "--collect-only", "-q", "-m", "gpu", "-p", "no:cacheprovider",
                           os.path.join(ROOT, "tests")], capture_output=True, text=True, cwd=ROOT).stdout
     ids = [l for l in out.splitlines() if "::" in l]
-    new_files = ("test_gpu_poisson.py", "test_gpu_plasticity.py", "test_gpu_topopt.py")
-    is_new = [any(f in l for f in new_files) for l in ids]
-    assert any(is_new) and not all(is_new)
-    first_new = is_new.index(True)
-    assert all(is_new[first_new:]), "an established GPU test is collected after a gpu_new one"
+    last = [("test_zz_no_alloc.py" in l) for l in ids]
+    assert any(last) and not all(last)
+    first = last.index(True)
+    assert all(last[first:]), "a GPU test is collected after the allocation-free solve tests"

@@ -8,7 +8,7 @@ import torch
 import oracle
 from oracle import solve as osolve
 from paper_2212_00964_gb300 import inputs
-from tests.gpu_common import TOL_ADJ_FD, TOL_ADJ_ORACLE, dev, fem, host, rel_l2
+from tests.gpu_common import TOL_ADJ_FD, TOL_ADJ_ORACLE, TOL_REFINED, dev, fem, host, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -120,7 +120,9 @@ def test_autograd_function_matches_adjoint():
 def test_c2_full_size_compliance_closed_form():
     """128x64x64 SIMP cantilever: the GPU adjoint gradient of the compliance
     equals the self-adjoint closed form -s'(theta_e) u_e^T K0_e u_e at the
-    GPU solution (oracle VJP with lambda = u), and central FD on 4 cells."""
+    GPU solution (oracle VJP with lambda = u), and central FD of the
+    compliance on the 64 cells drawn with seed 7, each side a full-size
+    mixed-precision solve."""
     F = fem()
     w = inputs.c2()
     m = F.fem_mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)
@@ -134,7 +136,9 @@ def test_c2_full_size_compliance_closed_form():
     closed = oracle.vjp(om, omat, host(u), host(u), w.cell_param, w.mask)
     assert rel_l2(host(g), closed) <= TOL_ADJ_ORACLE
     h = 1e-4
-    for e in inputs.fd_cells(om.n_cells, k=4):
+    cells = inputs.fd_cells(om.n_cells, k=64, seed=7)
+    assert cells.size == 64
+    for e in cells:
         tp = w.cell_param.copy()
         tm = w.cell_param.copy()
         tp[e] += h
@@ -151,7 +155,9 @@ def test_c4_full_size_forward_and_adjoint_properties():
     that hold at any size: the oracle's FP64 residual at the mixed-precision
     GPU solution is at the Newton tolerance; the GPU adjoint variable solves
     the oracle's tangent system K(u) lambda = dJ/du on the free DOFs; and the
-    GPU gradient equals the oracle's vector-Jacobian product at that lambda."""
+    GPU gradient equals the oracle's vector-Jacobian product at that lambda;
+    and the mixed-precision solution equals the all-FP64 GPU solution to
+    relative L2 1e-8."""
     F = fem()
     w = inputs.c4()
     m = F.fem_mesh(w.nx, w.ny, w.nz)
@@ -178,3 +184,8 @@ def test_c4_full_size_forward_and_adjoint_properties():
     assert np.linalg.norm((Kl - b)[free]) <= 1e-8 * np.linalg.norm(b[free])
     g_ref = oracle.vjp(om, omat, uh, lh, w.cell_param, w.mask)
     assert rel_l2(host(g), g_ref) <= TOL_ADJ_ORACLE
+    u64 = torch.zeros_like(u)
+    o64 = F.default_options(precision=F.FEM_FP64, newton_rtol=1e-10)
+    st64 = F.fem_solve(m, mat, dev(w.mask), dev(w.u_bar), u64, None, dev(w.cell_param), w.n_steps, o64)
+    assert st64["status"] == 0
+    assert rel_l2(uh, host(u64)) <= TOL_REFINED

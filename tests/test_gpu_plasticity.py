@@ -11,7 +11,7 @@ from oracle import plasticity as pl
 from paper_2212_00964_gb300 import inputs
 from tests.gpu_common import dev, fem, host, rel_l2
 
-pytestmark = [pytest.mark.gpu, pytest.mark.gpu_new]
+pytestmark = pytest.mark.gpu
 
 E, NU, SY = 70e3, 0.3, 250.0
 

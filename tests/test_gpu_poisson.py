@@ -13,7 +13,7 @@ from oracle import poisson as op
 from paper_2212_00964_gb300 import inputs
 from tests.gpu_common import dev, fem, host, rel_l2
 
-pytestmark = [pytest.mark.gpu, pytest.mark.gpu_new]
+pytestmark = pytest.mark.gpu
 
 BOXES = [(3, 4, 2, 1.0, 1.3, 0.4), (1, 2, 1, 0.5, 1.0, 0.2), (37, 5, 3, 2.0, 0.3, 0.9)]
 

@@ -71,12 +71,13 @@ def test_c0_linear_elastic_mixed_refined():
     assert rel_l2(u, ref) <= TOL_REFINED
 
 
-@pytest.mark.parametrize("apply_kernel", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("apply_kernel", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 @pytest.mark.parametrize("n", [4, 8, 9])
 def test_neohooke_load_steps(n, apply_kernel):
     """Every CG apply kernel (per-cell scatter at 3 and 4 CTAs/SM, 8x4x4
-    bricks, per-cell on stored tangent data); 9^3 leaves ragged bricks in
-    every direction and a ragged last cell tile."""
+    bricks, per-cell on stored tangent data, packed Gauss-point pairs with
+    and without stored data; FP64 runs the scalar kernel of the same data);
+    9^3 leaves ragged bricks in every direction and a ragged last cell tile."""
     w = inputs.c1(n=n, n_steps=10)
     ref = oracle_c1(n)
     u64, st64 = gpu_solve(w, 0, newton_rtol=1e-13, pcg_rtol=1e-8, apply_kernel=apply_kernel)
@@ -99,7 +100,7 @@ def test_neohooke_noncubic_with_stiffness_field():
     assert rel_l2(u, ref) <= TOL_REFINED
 
 
-@pytest.mark.parametrize("apply_kernel", [1, 2, 3])
+@pytest.mark.parametrize("apply_kernel", [1, 2, 3, 8])
 def test_simp_cantilever_small(apply_kernel):
     w = inputs.c2(nx=16, ny=8, nz=8)
     ref = oracle_solve(w)

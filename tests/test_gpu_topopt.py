@@ -11,7 +11,7 @@ from oracle import topopt as ot
 from paper_2212_00964_gb300 import inputs
 from tests.gpu_common import dev, fem, host, rel_l2
 
-pytestmark = [pytest.mark.gpu, pytest.mark.gpu_new]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("rmin", [1.0, 1.5, 2.3])
