@@ -346,7 +346,10 @@ typedef struct {
                             8 = as 1 with two Gauss points per instruction (packed
                                 FP32 pairs; FEM_MIXED only, FEM_FP64 runs 1),
                             9 = as 6 with two Gauss points per instruction
-                                (FEM_MIXED only, FEM_FP64 runs 6) */
+                                (FEM_MIXED only, FEM_FP64 runs 6),
+                            10 = as 9 with each tile's stored data copied into
+                                shared memory by a TMA bulk copy issued one tile
+                                ahead (FEM_MIXED only, FEM_FP64 runs 6) */
     int cg_fused;        /* 0: separate CG apply and update kernels; 1: one fused kernel per CG
                             iteration (the vector update of the previous iteration recomputed
                             per node inside the tangent apply) with apply kernels 1 and 5
@@ -356,6 +359,18 @@ typedef struct {
                             load step's first correction and while ||R_free|| > 1e-2 ||R_ref||
                             (far above FP32 rounding; such a residual never decides
                             convergence), FP64 otherwise; 0: always FP64 */
+    int graph_loop;      /* 1 (default): the solve is one CUDA graph launch whose loops over
+                            Newton rounds and CG chunks run on the device (conditional WHILE
+                            nodes, their conditions set by kernels from the solver's counters,
+                            both loops bounded on the device), then one host synchronisation;
+                            falls back to 0 where the runtime refuses the graph, and when
+                            timeout_s > 0 (a wall-clock watchdog needs the host loop).  0: one graph
+                            launch per CG chunk and per Newton round, with a host read of three
+                            counters after each */
+    double pcg_rtol_max; /* 0 (default): the inner CG tolerance is pcg_rtol in every Newton round;
+                            > 0: an adaptive tolerance (the forcing term of Eisenstat and Walker,
+                            choice 2, gamma 0.9) between pcg_rtol and pcg_rtol_max, loose on a load
+                            step's first round and tightening as Newton converges */
 } fem_options;
 
 typedef struct {
@@ -449,9 +464,16 @@ int fem_solve_batched(int n_inst, const fem_instance *inst, const fem_options *o
  * capture.  Every call shares the one array and overwrites what it needs, so
  * calls that overlap on the GPU (other streams, other host threads) race.
  *
- * Execution: kernels launch directly on `stream`, with no CUDA graph, event
- * or pinned host buffer; the call synchronises `stream` to read its
- * counters.  Arguments, results and stats otherwise match fem_solve;
+ * Execution: kernels launch directly on `stream`, with no CUDA graph, event,
+ * pinned host buffer or synchronisation call.  Each host round trip (the
+ * solver's counters, the final control block) is a device-to-host copy into
+ * pageable host memory, which returns only once the copy is complete.  So a
+ * call made after the first one also runs on its own stream while another
+ * host thread holds a global-mode stream capture open (that capture refuses
+ * cudaMalloc, cudaStreamSynchronize, cudaStreamQuery and
+ * cudaEventSynchronize in every thread, and is invalidated by them); the
+ * tests check that case and that a call leaves the device's free memory
+ * unchanged.  Arguments, results and stats otherwise match fem_solve;
  * apply_ms and apply_samples stay 0. */
 #define FEM_STATIC_SCRATCH_BYTES (8u << 20)
 int fem_solve_static(int nx, int ny, int nz, double lx, double ly, double lz, const fem_material *mat,

@@ -42,7 +42,8 @@ def build(force: bool = False) -> str:
         san = ["-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
                "-fno-sanitize-recover=all"] if _SANITIZE else ["-O2"]
         subprocess.check_call(
-            ["gcc"] + san + ["-ffp-contract=off", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+            ["gcc"] + san + ["-ffp-contract=off", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp,
+                             "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -71,6 +72,10 @@ def lib():
         L.oracle_residual.argtypes = [I64, I64, P, P] + mat + [P, P, P, P, P]
         L.oracle_residual.restype = D
         L.oracle_tangent_apply.argtypes = [I64, I64, P, P] + mat + [P, P, P, P, P]
+        L.oracle_residual_mt.argtypes = [I64, P, P] + mat + [P, P, P, P, P, P, P]
+        L.oracle_residual_mt.restype = D
+        L.oracle_tangent_apply_mt.argtypes = [I64, P, P] + mat + [P, P, P, P, P, P, P]
+        L.oracle_threads.restype = I
         L.oracle_element_tangent.argtypes = [P, P] + mat + [P, P, I64, P]
         L.oracle_diag.argtypes = [I64, I64, P, P] + mat + [P, P, P, P]
         L.oracle_assemble.argtypes = [I64, I64, P, P] + mat + [P, P, P, P, P, P, P]
@@ -222,6 +227,35 @@ def tangent_apply(m: Mesh, mat: Material, u, x, cell_param=None, mask=None):
     cp, mk = _f64(cell_param), _u8(mask)
     lib().oracle_tangent_apply(m.n_nodes, m.n_cells, _p(m.conn), _p(m.X), *mat.args(),
                                _p(cp), _p(u), _p(x), _p(mk), _p(y))
+    return y
+
+
+def threads():
+    """Threads the all-cores variants run on."""
+    return lib().oracle_threads()
+
+
+def residual_mt(m: Mesh, mat: Material, u, cell_param=None, f_ext=None, mask=None):
+    """residual() with the cell loop spread over all host cores (colour class
+    by colour class); for the CPU baseline."""
+    u = _f64(u).reshape(-1)
+    R = np.zeros(m.n_dofs)
+    cp, fe, mk = _f64(cell_param), _f64(f_ext), _u8(mask)
+    ptr, perm = colour(m)
+    lib().oracle_residual_mt(m.n_nodes, _p(m.conn), _p(m.X), *mat.args(), _p(cp), _p(u), _p(fe), _p(mk),
+                             _p(ptr), _p(perm), _p(R))
+    return R
+
+
+def tangent_apply_mt(m: Mesh, mat: Material, u, x, cell_param=None, mask=None):
+    """tangent_apply() with the cell loop spread over all host cores."""
+    u = _f64(u).reshape(-1)
+    x = _f64(x).reshape(-1)
+    y = np.zeros(m.n_dofs)
+    cp, mk = _f64(cell_param), _u8(mask)
+    ptr, perm = colour(m)
+    lib().oracle_tangent_apply_mt(m.n_nodes, _p(m.conn), _p(m.X), *mat.args(), _p(cp), _p(u), _p(x), _p(mk),
+                                  _p(ptr), _p(perm), _p(y))
     return y
 
 

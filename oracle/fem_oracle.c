@@ -529,6 +529,78 @@ void oracle_tangent_apply(int64_t n_nodes, int64_t n_cells, const int32_t *conn,
             if (mask[d]) y[d] = x[d];
 }
 
+/* The two operators above with the cell loop spread over the host's cores,
+ * for the all-cores CPU baseline only.  Cells are visited colour class by
+ * colour class (colour_ptr / cell_perm of oracle_colour: cells of one class
+ * share no node), so the scatter within a class is race-free; each cell's
+ * arithmetic is the serial functions' own (element_residual, element_jvp).
+ * The results equal the serial ones up to the order of the additions into
+ * each node.  Built with OpenMP; without it the loops run serially. */
+double oracle_residual_mt(int64_t n_nodes, const int32_t *conn, const double *X, int kind, double E, double nu,
+                          double simp_p, double simp_emin, const double *cell_param, const double *u,
+                          const double *f_ext, const uint8_t *mask, const int32_t *colour_ptr,
+                          const int32_t *cell_perm, double *R)
+{
+    double jmin = 1e300;
+    for (int64_t d = 0; d < 3 * n_nodes; ++d) R[d] = f_ext ? -f_ext[d] : 0.0;
+    for (int c = 0; c < 8; ++c) {
+#pragma omp parallel for schedule(static) reduction(min : jmin)
+        for (int64_t t = colour_ptr[c]; t < colour_ptr[c + 1]; ++t) {
+            const int64_t e = cell_perm[t];
+            double ue[24], Re[24];
+            double Es = E * cell_scale(kind, simp_p, simp_emin, cell_param, e);
+            gather(conn, e, u, ue);
+            double j = element_residual(kind, Es, nu, conn, X, e, ue, Re);
+            if (j < jmin) jmin = j;
+            for (int a = 0; a < 8; ++a)
+                for (int i = 0; i < 3; ++i) R[3 * (int64_t)conn[8 * e + a] + i] += Re[3 * a + i];
+        }
+    }
+    if (mask)
+        for (int64_t d = 0; d < 3 * n_nodes; ++d)
+            if (mask[d]) R[d] = 0.0;
+    return jmin;
+}
+
+void oracle_tangent_apply_mt(int64_t n_nodes, const int32_t *conn, const double *X, int kind, double E, double nu,
+                             double simp_p, double simp_emin, const double *cell_param, const double *u,
+                             const double *x, const uint8_t *mask, const int32_t *colour_ptr,
+                             const int32_t *cell_perm, double *y)
+{
+    for (int64_t d = 0; d < 3 * n_nodes; ++d) y[d] = 0.0;
+    for (int c = 0; c < 8; ++c) {
+#pragma omp parallel for schedule(static)
+        for (int64_t t = colour_ptr[c]; t < colour_ptr[c + 1]; ++t) {
+            const int64_t e = cell_perm[t];
+            double ue[24], xe[24], ye[24];
+            double Es = E * cell_scale(kind, simp_p, simp_emin, cell_param, e);
+            gather(conn, e, u, ue);
+            for (int a = 0; a < 8; ++a)
+                for (int i = 0; i < 3; ++i) {
+                    int64_t d = 3 * (int64_t)conn[8 * e + a] + i;
+                    xe[3 * a + i] = (mask && mask[d]) ? 0.0 : x[d];
+                }
+            element_jvp(kind, Es, nu, conn, X, e, ue, xe, ye);
+            for (int a = 0; a < 8; ++a)
+                for (int i = 0; i < 3; ++i) y[3 * (int64_t)conn[8 * e + a] + i] += ye[3 * a + i];
+        }
+    }
+    if (mask)
+        for (int64_t d = 0; d < 3 * n_nodes; ++d)
+            if (mask[d]) y[d] = x[d];
+}
+
+/* Threads the OpenMP runtime would use (1 without OpenMP). */
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 /* Dense element tangent K_e = dr_e/dU_e (Eq. (9)), column by column as
  * JVPs with unit vectors.  Ke row-major 24x24, Ke[24*r + c]. */
 void oracle_element_tangent(const int32_t *conn, const double *X, int kind, double E, double nu,

@@ -58,4 +58,6 @@ extern "C" void fem_default_options(fem_options *o)
     o->cg_fused = 0;
     o->timeout_s = 0.0;
     o->newton_res32 = 1;
+    o->graph_loop = 1;
+    o->pcg_rtol_max = 0.0;
 }

@@ -124,8 +124,11 @@ static void warm_one()
     resident_grid((const void *)apply_brick<T, NH>, BRICK_X * BRICK_Y * BRICK_Z, 0);
 }
 
-static const void *apply_x2_func(bool nh, int mode, int kin, bool batched)
+static const void *apply_x2_func(bool nh, int mode, int kin, bool batched, bool stage = false)
 {
+    if (stage)
+        return batched ? (const void *)cell_apply_x2<1, CM_APPLY_PCG, 3, true, true>
+                       : (const void *)cell_apply_x2<1, CM_APPLY_PCG, 3, false, true>;
     if (mode == CM_APPLY)
         return nh ? (const void *)cell_apply_x2<1, CM_APPLY, 0, false> : (const void *)cell_apply_x2<0, CM_APPLY, 0, false>;
     if (nh && kin == 3)
@@ -138,12 +141,30 @@ static const void *apply_x2_func(bool nh, int mode, int kin, bool batched)
                    : (const void *)cell_apply_x2<0, CM_APPLY_PCG, 0, false>;
 }
 
+// The staged kernel's dynamic shared memory (above the 48 KB default) is
+// allowed once per process, before any capture.
+static void stage_attributes()
+{
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (int b = 0; b < 2; ++b)
+            if (cudaFuncSetAttribute(apply_x2_func(true, CM_APPLY_PCG, 3, b, true),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KIN3_STAGE_SMEM) != cudaSuccess)
+                cudaGetLastError();
+    });
+}
+
 void warm_occupancy(bool nh)
 {
     device_sms();
     for (int b = 0; b < 2; ++b) {
         resident_grid(apply_x2_func(nh, CM_APPLY_PCG, 0, b), CELL_BLOCK, 0);
         if (nh) resident_grid(apply_x2_func(nh, CM_APPLY_PCG, 3, b), CELL_BLOCK, 0);
+    }
+    if (nh) {
+        stage_attributes();
+        for (int b = 0; b < 2; ++b)
+            resident_grid(apply_x2_func(true, CM_APPLY_PCG, 3, b, true), CELL_BLOCK, KIN3_STAGE_SMEM);
     }
     if (nh) {
         warm_one<float, 1>();
@@ -155,15 +176,18 @@ void warm_occupancy(bool nh)
 }
 // CG apply packed over Gauss-point pairs (FP32 only): kin 0 recomputes the
 // kinematics, kin 3 reads the gradient and scalars stored by the diagonal.
-cudaError_t launch_apply_x2(bool nh, int kin, const CellArgs<float> &a, cudaStream_t s)
+cudaError_t launch_apply_x2(bool nh, int kin, const CellArgs<float> &a, cudaStream_t s, bool stage)
 {
     if (kin == 3 && (!nh || !a.kin || a.kin_mode != 3)) return cudaErrorInvalidValue;
+    if (stage && kin != 3) return cudaErrorInvalidValue;
     const bool batched = a.tab != nullptr;
-    auto f = (void (*)(const CellArgs<float>))apply_x2_func(nh, CM_APPLY_PCG, kin, batched);
-    int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, 0));
+    const size_t smem = stage ? KIN3_STAGE_SMEM : 0;
+    if (stage) stage_attributes();
+    auto f = (void (*)(const CellArgs<float>))apply_x2_func(nh, CM_APPLY_PCG, kin, batched, stage);
+    int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, smem));
     if (g < 1) return cudaSuccess;
     count_launch();
-    return launch_pdl(f, (int)g, CELL_BLOCK, 0, s, a);  // begins with pdl_wait()
+    return launch_pdl(f, (int)g, CELL_BLOCK, smem, s, a);  // waits (pdl_wait) before reading CG vectors
 }
 
 template <typename T>

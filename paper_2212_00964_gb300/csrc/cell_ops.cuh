@@ -21,7 +21,7 @@ cudaError_t launch_apply_cell4(bool nh, const CellArgs<T> &a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_apply_kin(bool nh, const CellArgs<T> &a, cudaStream_t s, bool four_ctas = false);
 
-cudaError_t launch_apply_x2(bool nh, int kin, const CellArgs<float> &a, cudaStream_t s);
+cudaError_t launch_apply_x2(bool nh, int kin, const CellArgs<float> &a, cudaStream_t s, bool stage = false);
 
 // What the diagonal kernel stores for CG apply kernel `variant` (CellArgs::kin_mode):
 // 0 nothing, 1 cof(F) + scalars, 2 scalars, 3 scalars + displacement gradient.
@@ -30,7 +30,7 @@ inline int kin_mode_of(int variant)
     switch (variant) {
     case 4: return 1;
     case 5: return 2;
-    case 6: case 7: case 9: return 3;
+    case 6: case 7: case 9: case 10: return 3;
     }
     return 0;
 }

@@ -184,8 +184,19 @@ __device__ __forceinline__ void nh_point_pair(const float2 H[9], float G, float 
     q.e2 = mul2(dup(-2.0f / 3.0f), k1iJ);
 }
 
-// dP = dk1 F + k1 dF + dbeta cof F + beta dcof(F)[dF] (nh_dstress_c) at a pair.
-__device__ __forceinline__ void nh_dstress_pair(const NHPair &q, const float2 dF[9], float2 dP[9])
+// d cof F along dF at a pair: entry F_a F_b - F_c F_e has derivative
+// F_a dF_b + dF_a F_b + (-F_c) dF_e + dF_c (-F_e), the negated factors read
+// from -F (uses F, nF, dF of the enclosing scope)
+#define FEMGB_DMX2(a, b, c, e) fma2(F[a], dF[b], fma2(dF[a], F[b], fma2(nF[c], dF[e], mul2(dF[c], nF[e]))))
+
+// dP = dk1 F + k1 dF + dbeta cof F + beta dcof(F)[dF] (nh_dstress_c) at a
+// pair, fused with the flux sums of the cell: the x-flux of
+// Gauss pair (be, ga) is summed over its two points into sx[c][be + 2 ga];
+// the y-flux goes to the pair sy[c][ga] (accumulated over be when acc_y),
+// the z-flux to sz[c][be] (accumulated over ga when acc_z).  Accumulating
+// into the previous sum is the last FMA of each chain.
+__device__ __forceinline__ void nh_dstress_acc(const NHPair &q, const float2 dF[9], float sx[3][4], float2 sy[3][2],
+                                               float2 sz[3][2], int be, int ga, bool acc_y, bool acc_z)
 {
     const float2 *F = q.F, *nF = q.nF, *C = q.C;
     float2 dJ = mul2(C[0], dF[0]), fd = mul2(F[0], dF[0]);
@@ -196,16 +207,22 @@ __device__ __forceinline__ void nh_dstress_pair(const NHPair &q, const float2 dF
     }
     const float2 dk1 = mul2(q.e2, dJ);
     const float2 dbeta = fma2(q.e1, dJ, mul2(q.e2, fd));
-    // d cof F: each entry a f_b - f_c f_e of F has derivative
-    // a db + da b - c de - dc e, with -c and -e read from -F
-#define FEMGB_DMX(a, b, c, e) fma2(F[a], dF[b], fma2(dF[a], F[b], fma2(nF[c], dF[e], mul2(dF[c], nF[e]))))
     float2 dC[9];
-    dC[0] = FEMGB_DMX(4, 8, 5, 7); dC[1] = FEMGB_DMX(5, 6, 3, 8); dC[2] = FEMGB_DMX(3, 7, 4, 6);
-    dC[3] = FEMGB_DMX(2, 7, 1, 8); dC[4] = FEMGB_DMX(0, 8, 2, 6); dC[5] = FEMGB_DMX(1, 6, 0, 7);
-    dC[6] = FEMGB_DMX(1, 5, 2, 4); dC[7] = FEMGB_DMX(2, 3, 0, 5); dC[8] = FEMGB_DMX(0, 4, 1, 3);
-#undef FEMGB_DMX
+    dC[0] = FEMGB_DMX2(4, 8, 5, 7); dC[1] = FEMGB_DMX2(5, 6, 3, 8); dC[2] = FEMGB_DMX2(3, 7, 4, 6);
+    dC[3] = FEMGB_DMX2(2, 7, 1, 8); dC[4] = FEMGB_DMX2(0, 8, 2, 6); dC[5] = FEMGB_DMX2(1, 6, 0, 7);
+    dC[6] = FEMGB_DMX2(1, 5, 2, 4); dC[7] = FEMGB_DMX2(2, 3, 0, 5); dC[8] = FEMGB_DMX2(0, 4, 1, 3);
 #pragma unroll
-    for (int t = 0; t < 9; ++t) dP[t] = fma2(dk1, F[t], fma2(q.k1, dF[t], fma2(dbeta, C[t], mul2(q.beta, dC[t]))));
+    for (int c = 0; c < 3; ++c) {
+        const int tx = 3 * c, ty = 3 * c + 1, tz = 3 * c + 2;
+        const float2 px = fma2(dk1, F[tx], fma2(q.k1, dF[tx], fma2(dbeta, C[tx], mul2(q.beta, dC[tx]))));
+        sx[c][be + 2 * ga] = px.x + px.y;
+        const float2 y0 = acc_y ? sy[c][ga] : dup(0.f);
+        sy[c][ga] = acc_y ? fma2(dk1, F[ty], fma2(q.k1, dF[ty], fma2(dbeta, C[ty], fma2(q.beta, dC[ty], y0))))
+                          : fma2(dk1, F[ty], fma2(q.k1, dF[ty], fma2(dbeta, C[ty], mul2(q.beta, dC[ty]))));
+        const float2 z0 = acc_z ? sz[c][be] : dup(0.f);
+        sz[c][be] = acc_z ? fma2(dk1, F[tz], fma2(q.k1, dF[tz], fma2(dbeta, C[tz], fma2(q.beta, dC[tz], z0))))
+                          : fma2(dk1, F[tz], fma2(q.k1, dF[tz], fma2(dbeta, C[tz], mul2(q.beta, dC[tz]))));
+    }
 }
 
 // Linear elasticity at a pair: P = lam tr(H) I + mu (H + H^T).
@@ -221,6 +238,55 @@ __device__ __forceinline__ void le_stress_pair(const float2 H[9], float lam, flo
     P[5] = P[7] = mul2(m1, add2(H[5], H[7]));
 }
 
+// ---- TMA bulk staging of the stored tangent data (apply kernel 10) -------
+// The stored data of one 128-cell tile (kin3 layout: KIN3_CELL values x 128
+// cells, 34,816 bytes) is contiguous in global memory, so one bulk copy
+// (cp.async.bulk, completion counted on an mbarrier) moves it into shared
+// memory.  Two buffers: the copy of the next tile runs while this tile
+// computes.
+constexpr int KIN3_TILE_FLOATS = KIN3_CELL * CELL_BLOCK;
+constexpr unsigned KIN3_TILE_BYTES = KIN3_TILE_FLOATS * 4u;
+constexpr size_t KIN3_STAGE_SMEM = 2 * (size_t)KIN3_TILE_BYTES;
+constexpr int MBAR_SPIN_LIMIT = 1 << 22;  // bounded wait (each try_wait also suspends briefly)
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// One bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+// global -> shared, completing a transaction of that size on `bar`.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    unsigned long long g;
+    asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(src));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(g), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Wait for phase `parity` of `bar` to complete; false after the spin limit.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    const unsigned addr = smem_u32(bar);
+    for (int i = 0; i < MBAR_SPIN_LIMIT; ++i) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 // Stored tangent data read by KIN = 3 (kin3_slot layout, written by the
 // diagonal kernel in kin_mode 3): the 36 displacement-gradient values of the
 // cell and the four scalars (k1, beta, e1, e2) of each Gauss point.
@@ -231,17 +297,42 @@ __device__ __forceinline__ void le_stress_pair(const float2 H[9], float lam, flo
 //   KIN = 3: displacement gradient and tangent scalars read from a.kin.
 // CM_APPLY: x is masked on prescribed DOFs in the gather and nothing is added
 // to prescribed rows (y must hold its prescribed-row values already).
-template <int NH, int MODE, int KIN, bool BATCHED>
-__global__ void __launch_bounds__(CELL_BLOCK, 3) cell_apply_x2(const __grid_constant__ CellArgs<float> a)
+//   STAGE (KIN = 3, CG only): the stored data of each tile is staged into
+//   shared memory by a bulk copy issued one tile ahead (dynamic shared memory
+//   KIN3_STAGE_SMEM).  A copy that does not complete within the bounded wait
+//   sets the instance's status to FEM_ERR_TIMEOUT and ends the block's work.
+#ifndef FEMGB_X2_MINB
+#define FEMGB_X2_MINB 3  // CTAs per SM the register budget is set for
+#endif
+template <int NH, int MODE, int KIN, bool BATCHED, bool STAGE = false>
+__global__ void __launch_bounds__(CELL_BLOCK, FEMGB_X2_MINB) cell_apply_x2(const __grid_constant__ CellArgs<float> a)
 {
     static_assert(MODE == CM_APPLY_PCG || MODE == CM_APPLY, "apply modes only");
     static_assert(KIN == 0 || (KIN == 3 && NH), "KIN 0 or 3 (Neo-Hookean)");
+    static_assert(!STAGE || (KIN == 3 && MODE == CM_APPLY_PCG), "staging serves the stored-data CG apply");
     constexpr bool PCG = (MODE == CM_APPLY_PCG);
     __shared__ double sh[CELL_BLOCK / 32];
+    extern __shared__ __align__(128) float kin_s[];  // STAGE: two tiles of stored data
+    __shared__ __align__(8) unsigned long long kbar[2];
     float part = 0;
     int acc_k = -1, acc_slot = 0;
     int ctl_k = -1, ctl_go = 0, ctl_slot = 0;
     bool worked = false;
+    if (STAGE) {
+        if (threadIdx.x == 0) {
+            mbar_init(&kbar[0], 1);
+            mbar_init(&kbar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        // the stored data is written by the diagonal kernel of an earlier
+        // launch sequence, not by this launch's predecessor: the first copy
+        // may start before the programmatic-serialisation wait
+        if (threadIdx.x == 0 && (int64_t)blockIdx.x < a.n_tiles)
+            bulk_load(kin_s, a.kin + (int64_t)blockIdx.x * KIN3_TILE_FLOATS, KIN3_TILE_BYTES, &kbar[0]);
+    }
+    int it = 0;           // tiles this block has visited
+    int drain0 = -1, drain1 = -1;  // STAGE: iterations whose copies may be in flight at exit
     if (PCG) {
         pdl_wait();
         if (threadIdx.x == 0) kclock_start(a.kclock, 0);
@@ -252,7 +343,15 @@ __global__ void __launch_bounds__(CELL_BLOCK, 3) cell_apply_x2(const __grid_cons
             if (threadIdx.x == 0) kclock_account(a.kclock, 1);
         }
     }
-    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
+        if (STAGE) {
+            // prefetch the next tile into the other buffer (every thread left
+            // it at the barrier that ended the previous iteration)
+            const int64_t nt = tile + gridDim.x;
+            if (threadIdx.x == 0 && nt < a.n_tiles)
+                bulk_load(kin_s + ((it + 1) & 1) * KIN3_TILE_FLOATS, a.kin + nt * KIN3_TILE_FLOATS, KIN3_TILE_BYTES,
+                          &kbar[(it + 1) & 1]);
+        }
         int k = 0;
         InstDesc dcopy;
         const InstDesc *dp = &a.d0;
@@ -262,6 +361,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, 3) cell_apply_x2(const __grid_cons
             dp = &dcopy;
         }
         const InstDesc &d = *dp;
+        bool go_tile = true;
         if (PCG) {
             if (acc_k >= 0 && k != acc_k) {  // uniform per block
                 const double s = block_sum_t<float, CELL_BLOCK>(part, sh);
@@ -280,7 +380,23 @@ __global__ void __launch_bounds__(CELL_BLOCK, 3) cell_apply_x2(const __grid_cons
                 ctl_slot = (__shfl_sync(0xffffffffu, base, 0) + a.iter) & 3;
                 ctl_k = k;
             }
-            if (!ctl_go) continue;  // uniform per block
+            go_tile = ctl_go != 0;  // uniform per block
+        }
+        if (STAGE) {
+            // this tile's stored data (every iteration consumes its copy)
+            const bool ok = __syncthreads_and(mbar_wait(&kbar[it & 1], (it >> 1) & 1) ? 1 : 0) != 0;
+            if (!ok) {  // uniform per block
+                if (threadIdx.x == 0) atomicCAS(&a.ctl[k].status, 0, (int)FEM_ERR_TIMEOUT);
+                drain0 = it;  // not known complete
+                if (tile + gridDim.x < a.n_tiles) drain1 = it + 1;
+                break;
+            }
+        }
+        if (!go_tile) {  // uniform per block
+            if (STAGE) __syncthreads();
+            continue;
+        }
+        if (PCG) {
             acc_k = k;
             acc_slot = ctl_slot;
             worked = true;
@@ -302,7 +418,6 @@ __global__ void __launch_bounds__(CELL_BLOCK, 3) cell_apply_x2(const __grid_cons
         const int nq[4] = {n0, n0 + sy, n0 + sz, n0 + sz + sy};
         const float ihx = d.ihx<float>(), ihy = d.ihy<float>(), ihz = d.ihz<float>();
         const float wdet = d.wdet<float>();
-        const float wl = live ? wdet : 0.f;
         const float *cp = a.cell_param ? a.cell_param + d.cell_off : nullptr;
         const Mat<float> m = cell_mat<float>(d, cp, cell);
         const uint8_t *mb = (MODE == CM_APPLY && a.mask) ? a.mask + d.dof_off : nullptr;
@@ -337,8 +452,13 @@ __global__ void __launch_bounds__(CELL_BLOCK, 3) cell_apply_x2(const __grid_cons
         float ux[3][4], xx[3][4];
         float2 uy[3][2], uz[3][2], xy[3][2], xz[3][2];
         const float *kb = nullptr;
+        // stored data of this cell: value v at kst[v * CELL_BLOCK]
+        const float *kst = nullptr;
+        if (KIN == 3)
+            kst = STAGE ? kin_s + (it & 1) * KIN3_TILE_FLOATS + cell % CELL_BLOCK
+                        : a.kin + kin3_slot(d.tile_off, cell, 0);
         if (KIN == 3) {
-            kb = a.kin + kin3_slot(d.tile_off, cell, 8 * KIN2_VALUES);
+            kb = kst + 8 * KIN2_VALUES * CELL_BLOCK;
             // stored layout of cell_kernel: value (c, dir, j) at ((c * 3 + dir) * 4 + j) * CELL_BLOCK
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -371,6 +491,10 @@ __global__ void __launch_bounds__(CELL_BLOCK, 3) cell_apply_x2(const __grid_cons
                 dH[3 * c + 2] = xz[c][be];
             }
             float2 P[9];
+            // flux sums: the y-flux of (be, ga) adds to the pair of ga over be,
+            // the z-flux of (be, ga) to the pair of be over ga; a second
+            // visit accumulates into the first (acc = true)
+            const bool acc_y = be != 0, acc_z = ga != 0;
             if (NH) {
                 float2 H[9];
 #pragma unroll
@@ -384,8 +508,8 @@ __global__ void __launch_bounds__(CELL_BLOCK, 3) cell_apply_x2(const __grid_cons
                     f_pair(H, q);
                     cof_pair(q);
                     const int g0 = 2 * be + 4 * ga;  // Gauss points g0 (al = 0) and g0 + 1
-                    const float *s0 = a.kin + kin3_slot(d.tile_off, cell, g0 * KIN2_VALUES);
-                    const float *s1 = a.kin + kin3_slot(d.tile_off, cell, (g0 + 1) * KIN2_VALUES);
+                    const float *s0 = kst + g0 * KIN2_VALUES * CELL_BLOCK;
+                    const float *s1 = kst + (g0 + 1) * KIN2_VALUES * CELL_BLOCK;
                     q.k1 = pk(s0[0], s1[0]);
                     q.beta = pk(s0[CELL_BLOCK], s1[CELL_BLOCK]);
                     q.e1 = pk(s0[2 * CELL_BLOCK], s1[2 * CELL_BLOCK]);
@@ -393,24 +517,30 @@ __global__ void __launch_bounds__(CELL_BLOCK, 3) cell_apply_x2(const __grid_cons
                 } else {
                     nh_point_pair(H, m.c1, m.c2, q);
                 }
-                nh_dstress_pair(q, dH, P);
+                nh_dstress_acc(q, dH, sxs, sys, szs, be, ga, acc_y, acc_z);
             } else {
                 le_stress_pair(dH, m.c1, m.c2, P);
-            }
-            if (PCG) {
 #pragma unroll
-                for (int t = 0; t < 9; ++t) pdh = fma2(P[t], dH[t], pdh);
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                sxs[c][be + 2 * ga] = P[3 * c + 0].x + P[3 * c + 0].y;
-                if (be == 0) sys[c][ga] = P[3 * c + 1];
-                else sys[c][ga] = add2(sys[c][ga], P[3 * c + 1]);
-                if (ga == 0) szs[c][be] = P[3 * c + 2];
-                else szs[c][be] = add2(szs[c][be], P[3 * c + 2]);
+                for (int c = 0; c < 3; ++c) {
+                    sxs[c][be + 2 * ga] = P[3 * c + 0].x + P[3 * c + 0].y;
+                    sys[c][ga] = acc_y ? add2(sys[c][ga], P[3 * c + 1]) : P[3 * c + 1];
+                    szs[c][be] = acc_z ? add2(szs[c][be], P[3 * c + 2]) : P[3 * c + 2];
+                }
             }
         }
-        if (PCG) part += wl * (pdh.x + pdh.y);
+        if (PCG) {
+            // x_e . K_e x_e = w detJ sum over Gauss points of dP : dH; the
+            // flux sums share their gradient factor, so the sum runs over them
+            float ps = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) ps += sxs[c][j] * xx[c][j];
+#pragma unroll
+                for (int g = 0; g < 2; ++g) pdh = fma2(sys[c][g], xy[c][g], fma2(szs[c][g], xz[c][g], pdh));
+            }
+            if (live) part += wdet * (ps + pdh.x + pdh.y);
+        }
         float2 Y[3][4];
 #pragma unroll
         for (int c = 0; c < 3; ++c) grad_x2_t(sxs[c], sys[c], szs[c], ihx * wdet, ihy * wdet, ihz * wdet, Y[c]);
@@ -443,6 +573,13 @@ __global__ void __launch_bounds__(CELL_BLOCK, 3) cell_apply_x2(const __grid_cons
                     if (!to_right && !(mb && mb[3 * nq[i] + 3 + c])) red_add(&yb[3 * nq[i] + 3 + c], Y[c][i].y);
                 }
         }
+        if (STAGE) __syncthreads();  // buffer (it & 1) is refilled by the next iteration's prefetch
+    }
+    if (STAGE && drain0 >= 0) {
+        // after a timed-out wait, copies may still be in flight into this
+        // block's shared memory: wait for them (bounded) before the block exits
+        (void)mbar_wait(&kbar[drain0 & 1], (unsigned)((drain0 >> 1) & 1));
+        if (drain1 >= 0) (void)mbar_wait(&kbar[drain1 & 1], (unsigned)((drain1 >> 1) & 1));
     }
     if (PCG) {
         if (acc_k >= 0) {  // uniform per block

@@ -108,6 +108,7 @@ struct Ctl {
     double gamma[4], delta[4], rr[4], alpha[4];
     int go;     // CG runs: set by the CG start, cleared by block 0 of the kernel that stops it
     int res32;  // this round's Newton residual is evaluated in FP32 (far from convergence)
+    double r_prev;  // ||R_free|| of the previous Newton round (adaptive inner tolerance)
 };
 
 // Live kernel-span statistics of the two CG kernels, in device memory: the

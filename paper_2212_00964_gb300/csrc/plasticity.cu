@@ -29,7 +29,7 @@ constexpr int MAX_ITERS = 1000000;
 
 enum { WS_JR = 64, WS_JB, WS_JDU, WS_JD, WS_JDINV, WS_JHN, WS_JCR, WS_JCZ, WS_JCP, WS_JCQ, WS_JSC, WS_JSMALL };
 // FP32 buffers of the mixed-precision correction
-enum { WS_JB32 = 88, WS_JDU32, WS_JDINV32, WS_JCR32, WS_JCZ32, WS_JCP32, WS_JCQ32, WS_JD32 };
+enum { WS_JB32 = 88, WS_JDU32, WS_JDINV32, WS_JCR32, WS_JCZ32, WS_JCP32, WS_JCQ32, WS_JD32, WS_JH32, WS_JU32 };
 
 struct Geo {
     int nx, ny, nz;
@@ -93,9 +93,12 @@ __global__ void __launch_bounds__(CB) k_j2_residual(Geo g, const double *__restr
 }
 
 // y += sum_e K_e(u) x_e with masked entries of x removed, computed in T
-// (double, or float inside the mixed-precision CG) from the FP64 state
-template <typename T>
-__global__ void __launch_bounds__(CB) k_j2_apply(Geo g, const double *__restrict__ u, const double *__restrict__ hist,
+// (double, or float inside the mixed-precision CG) from the state and
+// history in S (FP64, or their FP32 copies: on GB300 a conversion from FP64
+// runs at the FP64 rate, so the mixed CG converts once per Newton iteration,
+// not once per apply)
+template <typename T, typename S = double>
+__global__ void __launch_bounds__(CB) k_j2_apply(Geo g, const S *__restrict__ u, const S *__restrict__ hist,
                                                 const T *__restrict__ x, const uint8_t *__restrict__ mask, T *y)
 {
     for (int64_t e = blockIdx.x * (int64_t)CB + threadIdx.x; e < g.ne; e += (int64_t)gridDim.x * CB) {
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(CB) k_j2_apply(Geo g, const double *__restrict
                 xe[3 * a + t] = (mask && mask[d]) ? (T)0 : x[d];
             }
         }
-        j2::cell_jvp<T, double>(g.c, (T)g.ihx, (T)g.ihy, (T)g.ihz, (T)g.w, ue, xe, hist, g.ne, e, ye);
+        j2::cell_jvp<T, S>(g.c, (T)g.ihx, (T)g.ihy, (T)g.ihz, (T)g.w, ue, xe, hist, g.ne, e, ye);
         for (int a = 0; a < 8; ++a) {
             const int64_t n = j2::cell_node(i, j, k, a, g.nx, g.ny);
             for (int t = 0; t < 3; ++t) atomicAdd(&y[3 * n + t], ye[3 * a + t]);
@@ -119,9 +122,9 @@ __global__ void __launch_bounds__(CB) k_j2_apply(Geo g, const double *__restrict
 }
 
 // d += diagonal of the element tangents (closed form, j2::cell_diag),
-// computed in T from the FP64 state
-template <typename T>
-__global__ void __launch_bounds__(CB) k_j2_diag(Geo g, const double *__restrict__ u, const double *__restrict__ hist,
+// computed in T from the state and history in S
+template <typename T, typename S = double>
+__global__ void __launch_bounds__(CB) k_j2_diag(Geo g, const S *__restrict__ u, const S *__restrict__ hist,
                                                T *d)
 {
     for (int64_t e = blockIdx.x * (int64_t)CB + threadIdx.x; e < g.ne; e += (int64_t)gridDim.x * CB) {
@@ -132,7 +135,7 @@ __global__ void __launch_bounds__(CB) k_j2_diag(Geo g, const double *__restrict_
             const int64_t n = j2::cell_node(i, j, k, a, g.nx, g.ny);
             for (int t = 0; t < 3; ++t) ue[3 * a + t] = (T)u[3 * n + t];
         }
-        j2::cell_diag<T, double>(g.c, (T)g.ihx, (T)g.ihy, (T)g.ihz, (T)g.w, ue, hist, g.ne, e, de);
+        j2::cell_diag<T, S>(g.c, (T)g.ihx, (T)g.ihy, (T)g.ihz, (T)g.w, ue, hist, g.ne, e, de);
         for (int a = 0; a < 8; ++a) {
             const int64_t n = j2::cell_node(i, j, k, a, g.nx, g.ny);
             for (int t = 0; t < 3; ++t) atomicAdd(&d[3 * n + t], de[3 * a + t]);
@@ -215,12 +218,12 @@ int residual_launch(const Geo &g, const uint8_t *mask, const double *u, const do
     return FEM_OK;
 }
 
-template <typename T>
-int apply_launch(const Geo &g, const uint8_t *mask, const double *u, const double *hist, const T *x, T *y, double *dot,
+template <typename T, typename S = double>
+int apply_launch(const Geo &g, const uint8_t *mask, const S *u, const S *hist, const T *x, T *y, double *dot,
                  cudaStream_t s)
 {
     FEM_CUDA(cudaMemsetAsync(y, 0, sizeof(T) * g.dofs, s));
-    k_j2_apply<T><<<cell_grid(g.ne), CB, 0, s>>>(g, u, hist, x, mask, y);
+    k_j2_apply<T, S><<<cell_grid(g.ne), CB, 0, s>>>(g, u, hist, x, mask, y);
     k_j2_fix_dot<T><<<vec_grid(g.dofs), VB, 0, s>>>(x, mask, y, g.dofs, dot);
     count_launch(2);
     FEM_CUDA(cudaGetLastError());
@@ -273,8 +276,19 @@ extern "C" int fem_j2_tangent_apply(fem_mesh_t m, const fem_j2_material *mat, in
     cudaStream_t s = (cudaStream_t)stream;
     if (precision == FEM_FP64)
         return apply_launch<double>(geo(m, mat), mask, u, hist, (const double *)x, (double *)y, nullptr, s);
-    if (precision == FEM_FP32)
-        return apply_launch<float>(geo(m, mat), mask, u, hist, (const float *)x, (float *)y, nullptr, s);
+    if (precision == FEM_FP32) {
+        // FP32 copies of the state and history, then the FP32 apply (the
+        // kernel the mixed-precision CG runs)
+        const Geo g = geo(m, mat);
+        const int64_t nh = 12 * 8 * g.ne;
+        float *u32 = (float *)m->ws.get(WS_JU32, sizeof(float) * g.dofs);
+        float *hist32 = (float *)m->ws.get(WS_JH32, sizeof(float) * (size_t)nh);
+        if (!u32 || !hist32) return FEM_ERR_NOMEM;
+        k_j2_to_f32<<<vec_grid(g.dofs), VB, 0, s>>>(u, u32, g.dofs);
+        k_j2_to_f32<<<vec_grid(nh), VB, 0, s>>>(hist, hist32, nh);
+        count_launch(2);
+        return apply_launch<float, float>(g, mask, u32, hist32, (const float *)x, (float *)y, nullptr, s);
+    }
     return (set_error("fem_j2_tangent_apply: precision must be FEM_FP64 or FEM_FP32"), FEM_ERR_ARG);
 }
 
@@ -312,8 +326,11 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
     if (!R || !b || !du || !dg || !dinv || !hn || !w.r || !w.z || !w.p || !w.q || !w.sc || !small)
         return FEM_ERR_NOMEM;
     dpcg::Buffers<float> w32{};
-    float *b32 = nullptr, *du32 = nullptr, *dinv32 = nullptr, *dg32 = nullptr;
+    float *b32 = nullptr, *du32 = nullptr, *dinv32 = nullptr, *dg32 = nullptr, *u32 = nullptr, *hist32 = nullptr;
     if (mixed) {
+        u32 = (float *)m->ws.get(WS_JU32, sizeof(float) * D);
+        hist32 = (float *)m->ws.get(WS_JH32, hb / 2);
+        if (!u32 || !hist32) return FEM_ERR_NOMEM;
         dg32 = (float *)m->ws.get(WS_JD32, sizeof(float) * D);
         b32 = (float *)m->ws.get(WS_JB32, sizeof(float) * D);
         du32 = (float *)m->ws.get(WS_JDU32, sizeof(float) * D);
@@ -333,7 +350,7 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
         double *u, *hist, *R, *b, *du, *dg, *dinv, *hn, *small;
         const dpcg::Buffers<double> &w;
         const dpcg::Buffers<float> &w32;
-        float *b32, *du32, *dinv32, *dg32;
+        float *b32, *du32, *dinv32, *dg32, *u32, *hist32;
         bool mixed;
         double cg_rtol;
         int cg_maxit;
@@ -367,14 +384,18 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
             // mixed: tangent, CG vectors and du in FP32 (the residual stays FP64)
             int rc;
             if (mixed) {
+                // FP32 copies of the state and history for this iteration's CG
+                const int64_t nh = 12 * 8 * g.ne;
+                k_j2_to_f32<<<vec_grid(g.dofs), VB, 0, s>>>(u, u32, g.dofs);
+                k_j2_to_f32<<<vec_grid(nh), VB, 0, s>>>(hist, hist32, nh);
                 FEM_CUDA(cudaMemsetAsync(dg32, 0, sizeof(float) * g.dofs, s));
-                k_j2_diag<float><<<cell_grid(g.ne), CB, 0, s>>>(g, u, hist, dg32);
+                k_j2_diag<float, float><<<cell_grid(g.ne), CB, 0, s>>>(g, u32, hist32, dg32);
                 k_j2_dinv<float><<<vec_grid(g.dofs), VB, 0, s>>>(dg32, mask, dinv32, g.dofs);
                 k_j2_to_f32<<<vec_grid(g.dofs), VB, 0, s>>>(b, b32, g.dofs);
-                count_launch(3);
+                count_launch(5);
                 FEM_CUDA(cudaMemsetAsync(du32, 0, sizeof(float) * g.dofs, s));
                 auto apply = [&](const float *x, float *y, double *dot) -> int {
-                    return apply_launch<float>(g, mask, u, hist, x, y, dot, s);
+                    return apply_launch<float, float>(g, mask, u32, hist32, x, y, dot, s);
                 };
                 rc = dpcg::solve<float>(s, g.dofs, apply, dinv32, b32, du32, w32, cg_rtol, cg_maxit, cg_it, nullptr,
                                         "fem_j2_step");
@@ -415,7 +436,7 @@ extern "C" int fem_j2_step(fem_mesh_t m, const fem_j2_material *mat, int precisi
         }
         void fail(const char *what) { set_error(std::string("fem_j2_step: ") + what); }
     };
-    Ops ops{g,  mask, u_bar, u, hist, R, b, du, dg, dinv, hn, small, w, w32, b32, du32, dinv32, dg32, mixed, cg_rtol,
+    Ops ops{g,  mask, u_bar, u, hist, R, b, du, dg, dinv, hn, small, w, w32, b32, du32, dinv32, dg32, u32, hist32, mixed, cg_rtol,
             cg_maxit, hb, s};
     const double h = std::min(1.0 / g.ihx, std::min(1.0 / g.ihy, 1.0 / g.ihz));
     return j2::newton_step(ops, mat->sigma_y, h, newton_rtol, newton_maxit, newton_iters, cg_iters, n_yield);

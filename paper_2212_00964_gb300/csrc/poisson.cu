@@ -38,25 +38,44 @@ enum {
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + PB - 1) / PB, 152 * 8)); }
 
 // Operator kernel in the separable form of poisson_core.cuh (axis_stencils):
-// each block owns a tile of SX x SY node columns (a one-node halo included,
-// so it writes (SX - 2) x (SY - 2) columns) over SZ consecutive planes.
-// Every thread holds the x values of its column for the SZ + 2 planes it
-// needs (all loads issued before any arithmetic), and per output plane
-//   1. filters along z:  a = M_z x, b = K_z x            (its own column)
-//   2. filters along y:  c = M_y a, e = K_y a + M_y b     (shared memory)
-//   3. filters along x:  y = alpha (K_x c + M_x e)  or  M_x c for the mass.
-// One read of x (plus halo re-reads from L2), one of the mask and one write
-// of y per node: HBM-bound.  dot != nullptr adds sum_n x_n y_n (one atomic
-// per block).
+// a block of SX x SY threads owns SX x SY node columns, a one-node halo
+// included, so it writes (SX - 2) x (SY - 2) columns, over SZ consecutive
+// planes.  A warp is one row of SX = 32 columns along x.  Each thread holds
+// the x values of its column for the SZ + 2 planes it needs (all loads
+// issued before any arithmetic) and, per output plane,
+//   1. filters along z in registers:  a = M_z x, b = K_z x;
+//   2. filters along y through shared memory (double-buffered by plane, so
+//      one barrier per plane):  c = M_y a, e = K_y a + M_y b;
+//   3. filters along x through warp shuffles:
+//      y = alpha (K_x c + M_x e), or M_x c for the mass.
+// Per node one read of x (halo re-reads come from L2), one of the mask and
+// one write of y: HBM-bound.  With DOT, sum_n x_n y_n is added to *dot (one
+// atomic per block).  ih* = 1/h, m6* = h/6 per axis.
 constexpr int SX = 32, SY = 16, SZ = 16;
 
 template <typename T>
+struct Axis3 {
+    T ih, m6;
+    // 1D stencils (neighbour -1, 0, +1) at node coordinate i of n cells
+    __device__ __forceinline__ void at(int i, int n, T *k, T *m) const
+    {
+        const T lo = i > 0 ? (T)1 : (T)0, hi = i < n ? (T)1 : (T)0;
+        k[0] = -lo * ih;
+        k[1] = (lo + hi) * ih;
+        k[2] = -hi * ih;
+        m[0] = lo * m6;
+        m[1] = (T)2 * (lo + hi) * m6;
+        m[2] = hi * m6;
+    }
+};
+
+template <typename T, int OP, int MODE, bool DOT>
 __global__ void __launch_bounds__(SX * SY) k_pois_sep(const T *__restrict__ x, const uint8_t *__restrict__ mask,
-                                                     int op, int mode, T alpha, T hx, T hy, T hz,
+                                                     T alpha, Axis3<T> ax, Axis3<T> ay, Axis3<T> az,
                                                      T *__restrict__ y, int nx, int ny, int nz, double *dot)
 {
-    __shared__ T sa[SY][SX + 1], sb[SY][SX + 1], sc[SY][SX + 1], se[SY][SX + 1];
-    __shared__ double sh[SX * SY / 32];
+    __shared__ T sa[2][SY][SX], sb[2][SY][SX];
+    __shared__ double sh[SY];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int i = (int)blockIdx.x * (SX - 2) - 1 + tx;
     const int j = (int)blockIdx.y * (SY - 2) - 1 + ty;
@@ -64,8 +83,8 @@ __global__ void __launch_bounds__(SX * SY) k_pois_sep(const T *__restrict__ x, c
     const int kend = min(k0 + SZ, nz + 1);  // output planes [k0, kend)
     const bool col = i >= 0 && i <= nx && j >= 0 && j <= ny;
     const bool out = col && tx >= 1 && tx <= SX - 2 && ty >= 1 && ty <= SY - 2;
-    const int64_t sxn = nx + 1, sxy = (int64_t)(nx + 1) * (ny + 1);
-    const int64_t base = col ? i + sxn * j : 0;
+    const int64_t sxy = (int64_t)(nx + 1) * (ny + 1);
+    const int64_t base = col ? i + (int64_t)(nx + 1) * j : 0;
     // x of this column at planes k0 - 1 .. k0 + SZ (zero outside the box and,
     // for the eliminated operator, on prescribed nodes); mask bits of the same
     T xc[SZ + 2];
@@ -77,59 +96,77 @@ __global__ void __launch_bounds__(SX * SY) k_pois_sep(const T *__restrict__ x, c
         if (col && kk >= 0 && kk <= nz && kk <= kend) {
             const int64_t n = base + sxy * kk;
             v = x[n];
-            if (mask && mask[n]) {
+            if (MODE != poisson::OUT_PLAIN && mask[n]) {
                 mbits |= 1u << t;
-                if (mode == poisson::OUT_ELIM) v = (T)0;
+                if (MODE == poisson::OUT_ELIM) v = (T)0;
             }
         }
         xc[t] = v;
     }
     T kx[3], mx[3], ky[3], my[3];
-    poisson::axis_stencils<T>(i, nx, hx, kx, mx);
-    poisson::axis_stencils<T>(j, ny, hy, ky, my);
-    if (op == 0) {
+    ax.at(i, nx, kx, mx);
+    ay.at(j, ny, ky, my);
+    if (OP == 0) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             kx[d] *= alpha;
             mx[d] *= alpha;
         }
     }
-    double acc = 0;
+    T acc = (T)0;
 #pragma unroll
     for (int p = 0; p < SZ; ++p) {
         const int kk = k0 + p;
         if (kk >= kend) break;  // uniform per block
         T kz[3], mz[3];
-        poisson::axis_stencils<T>(kk, nz, hz, kz, mz);
-        sa[ty][tx] = mz[0] * xc[p] + mz[1] * xc[p + 1] + mz[2] * xc[p + 2];
-        sb[ty][tx] = kz[0] * xc[p] + kz[1] * xc[p + 1] + kz[2] * xc[p + 2];
+        az.at(kk, nz, kz, mz);
+        const int buf = p & 1;
+        const T a = mz[0] * xc[p] + mz[1] * xc[p + 1] + mz[2] * xc[p + 2];
+        const T b = OP == 0 ? kz[0] * xc[p] + kz[1] * xc[p + 1] + kz[2] * xc[p + 2] : (T)0;
+        sa[buf][ty][tx] = a;
+        if (OP == 0) sb[buf][ty][tx] = b;
         __syncthreads();
-        if (ty >= 1 && ty <= SY - 2) {
-            const T a0 = sa[ty - 1][tx], a1 = sa[ty][tx], a2 = sa[ty + 1][tx];
-            sc[ty][tx] = my[0] * a0 + my[1] * a1 + my[2] * a2;
-            if (op == 0)
-                se[ty][tx] = ky[0] * a0 + ky[1] * a1 + ky[2] * a2 + my[0] * sb[ty - 1][tx] + my[1] * sb[ty][tx] +
-                             my[2] * sb[ty + 1][tx];
+        // rows 0 and SY - 1 are halo: their values are read, never filtered
+        const int tym = ty > 0 ? ty - 1 : ty, typ = ty < SY - 1 ? ty + 1 : ty;
+        const T a0 = sa[buf][tym][tx], a2 = sa[buf][typ][tx];
+        const T c = my[0] * a0 + my[1] * a + my[2] * a2;
+        T e = (T)0;
+        if (OP == 0) e = ky[0] * a0 + ky[1] * a + ky[2] * a2 + my[0] * sb[buf][tym][tx] + my[1] * b +
+                         my[2] * sb[buf][typ][tx];
+        const T cm = __shfl_up_sync(0xffffffffu, c, 1), cp = __shfl_down_sync(0xffffffffu, c, 1);
+        T v;
+        if (OP == 0) {
+            const T em = __shfl_up_sync(0xffffffffu, e, 1), ep = __shfl_down_sync(0xffffffffu, e, 1);
+            v = kx[0] * cm + kx[1] * c + kx[2] * cp + mx[0] * em + mx[1] * e + mx[2] * ep;
+        } else {
+            v = mx[0] * cm + mx[1] * c + mx[2] * cp;
         }
-        __syncthreads();
         if (out) {
-            T v = mx[0] * sc[ty][tx - 1] + mx[1] * sc[ty][tx] + mx[2] * sc[ty][tx + 1];
-            if (op == 0) v = kx[0] * sc[ty][tx - 1] + kx[1] * sc[ty][tx] + kx[2] * sc[ty][tx + 1] + mx[0] * se[ty][tx - 1] +
-                             mx[1] * se[ty][tx] + mx[2] * se[ty][tx + 1];
             const int64_t n = base + sxy * kk;
             T xn = xc[p + 1];
-            if ((mbits >> (p + 1)) & 1u) {
-                xn = x[n];
-                if (mode == poisson::OUT_ELIM) v = xn;
-                else if (mode == poisson::OUT_ZERO) v = (T)0;
+            if (MODE != poisson::OUT_PLAIN && ((mbits >> (p + 1)) & 1u)) {
+                if (MODE == poisson::OUT_ELIM) {
+                    xn = x[n];
+                    v = xn;
+                } else {
+                    v = (T)0;
+                }
             }
             y[n] = v;
-            if (dot) acc += (double)(xn * v);
+            if (DOT) acc += xn * v;
         }
     }
-    if (dot) {
-        const double s = block_sum<double, SX * SY>(acc, sh);
-        if (tx == 0 && ty == 0) atomicAdd(dot, s);
+    if (DOT) {  // a row of the block (fixed ty, SX = 32 lanes) is one warp
+        static_assert(SX == 32, "one warp per block row");
+        const T w = warp_sum(acc);
+        if (tx == 0) sh[ty] = (double)w;
+        __syncthreads();
+        if (tx == 0 && ty == 0) {
+            double s = 0;
+#pragma unroll
+            for (int r = 0; r < SY; ++r) s += sh[r];
+            atomicAdd(dot, s);
+        }
     }
 }
 
@@ -227,8 +264,20 @@ void launch_op(const Ctx &c, const Coef &k, int op, const T *x, const uint8_t *m
     const fem_mesh_s *m = c.m;
     const dim3 grid((unsigned)((m->nx + 1 + SX - 3) / (SX - 2)), (unsigned)((m->ny + 1 + SY - 3) / (SY - 2)),
                     (unsigned)((m->nz + 1 + SZ - 1) / SZ));
-    k_pois_sep<T><<<grid, dim3(SX, SY), 0, c.s>>>(x, mask, op, mode, (T)k.alpha, (T)k.hx, (T)k.hy, (T)k.hz, y, m->nx,
-                                                  m->ny, m->nz, dot);
+    const Axis3<T> ax{(T)(1.0 / k.hx), (T)(k.hx / 6.0)}, ay{(T)(1.0 / k.hy), (T)(k.hy / 6.0)},
+        az{(T)(1.0 / k.hz), (T)(k.hz / 6.0)};
+    if (!mask) mode = poisson::OUT_PLAIN;
+    auto f = k_pois_sep<T, 0, poisson::OUT_PLAIN, false>;
+    if (op == 0) {
+        if (mode == poisson::OUT_ELIM) f = dot ? k_pois_sep<T, 0, poisson::OUT_ELIM, true> : k_pois_sep<T, 0, poisson::OUT_ELIM, false>;
+        else if (mode == poisson::OUT_ZERO) f = k_pois_sep<T, 0, poisson::OUT_ZERO, false>;
+        else f = dot ? k_pois_sep<T, 0, poisson::OUT_PLAIN, true> : k_pois_sep<T, 0, poisson::OUT_PLAIN, false>;
+    } else {
+        f = mode == poisson::OUT_ZERO ? k_pois_sep<T, 1, poisson::OUT_ZERO, false>
+                                      : (mode == poisson::OUT_ELIM ? k_pois_sep<T, 1, poisson::OUT_ELIM, false>
+                                                                   : k_pois_sep<T, 1, poisson::OUT_PLAIN, false>);
+    }
+    f<<<grid, dim3(SX, SY), 0, c.s>>>(x, mask, (T)k.alpha, ax, ay, az, y, m->nx, m->ny, m->nz, dot);
     count_launch();
 }
 

@@ -38,6 +38,7 @@ struct SolverParams {
     int pcg_maxit;
     int chunk;
     double res32_tau;  // FP32 Newton residual while ||R|| > res32_tau ||R_ref|| (0: always FP64)
+    double eta_max;    // > 0: adaptive inner tolerance in [eta, eta_max]; 0: eta fixed
 };
 
 enum SolveMode { SM_NONLINEAR = 0, SM_LINEAR = 1 };
@@ -197,7 +198,26 @@ __global__ void k_control(Ctl *ctl, int n_inst, SolverParams prm, int *counter)
     c.pcg_done = 0;
     c.pcg_last = 0;
     c.rr0 = 0;
-    c.eta = prm.eta;
+    // inner CG tolerance: fixed, or the forcing term of Eisenstat and Walker
+    // (1996, choice 2: 0.9 (||R_k|| / ||R_k-1||)^2, safeguarded by
+    // 0.9 eta_k-1^2 when that exceeds 0.1), kept in [eta, eta_max] and, near
+    // the Newton stop, no tighter than half the remaining reduction needs
+    double eta = prm.eta;
+    if (prm.eta_max > 0) {
+        if (lift || !(c.r_prev > 0)) {
+            eta = prm.eta_max;
+        } else {
+            const double q = rn / c.r_prev;
+            eta = 0.9 * q * q;
+            const double safe = 0.9 * c.eta * c.eta;
+            if (safe > 0.1) eta = fmax(eta, safe);
+            const double stop = fmax(prm.rtol * c.r_ref, prm.atol);
+            if (rn > 0) eta = fmax(eta, 0.5 * stop / rn);
+            eta = fmin(fmax(eta, prm.eta), prm.eta_max);
+        }
+    }
+    c.r_prev = rn;
+    c.eta = eta;
     c.go = 0;
     for (int s = 0; s < 4; ++s) c.gamma[s] = c.delta[s] = c.rr[s] = c.alpha[s] = 0;
     atomicAdd(&counter[0], 1);
@@ -525,6 +545,68 @@ struct Buffers {
     T *r2, *s2, *q2, *q3; // second r and s, second and third w of the fused CG kernel (may be null)
 };
 
+// ---- one-graph solve: loop control on the device --------------------------
+// counter[4] Newton rounds, [5] CG chunks of the current round, [6] 1 when
+// the round bound stopped the solve, [7] CG chunks of the whole solve.
+__global__ void k_loop_start(int *counter)
+{
+    if (threadIdx.x == 0) counter[4] = counter[5] = counter[6] = counter[7] = 0;
+}
+
+// Before a round's CG: the chunk loop runs if any instance solves.
+__global__ void k_chunk_gate(cudaGraphConditionalHandle h, int *counter)
+{
+    if (threadIdx.x != 0) return;
+    counter[5] = 0;
+    cudaGraphSetConditional(h, counter[0] > 0 ? 1u : 0u);
+}
+
+// After a chunk: continue while an instance still iterates, at most
+// max_chunks chunks per round (the CG itself is capped at pcg_maxit).
+__global__ void k_chunk_next(cudaGraphConditionalHandle h, int *counter, int max_chunks)
+{
+    if (threadIdx.x != 0) return;
+    const int c = ++counter[5];
+    ++counter[7];
+    cudaGraphSetConditional(h, (counter[1] > 0 && c < max_chunks) ? 1u : 0u);
+}
+
+// After a round: continue while an instance is active, at most max_rounds.
+__global__ void k_round_next(cudaGraphConditionalHandle h, int *counter, int max_rounds)
+{
+    if (threadIdx.x != 0) return;
+    const int r = ++counter[4];
+    unsigned go = counter[2] > 0 ? 1u : 0u;
+    if (go && r >= max_rounds) {
+        go = 0;
+        counter[6] = 1;
+    }
+    cudaGraphSetConditional(h, go);
+}
+
+// Appends a WHILE node on handle h to the capture in progress on s (after
+// everything captured so far) and returns its body graph.
+static cudaError_t append_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t *body)
+{
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np);
+    if (e != cudaSuccess) return e;
+    *body = np.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
 struct Graphs {
     cudaGraphExec_t head = nullptr, chunk = nullptr, tail_head = nullptr;
     int64_t n_head = 0, n_chunk = 0, n_tail_head = 0;
@@ -743,13 +825,13 @@ class Core {
         }
         ca.n_tiles = pb_.n_tiles;
         if (variant_ == 3) return launch_apply_cell4<T>(pb_.nh, ca, s);
-        if (variant_ == 8 || variant_ == 9) {
+        if (variant_ >= 8) {
             ca.kin_mode = kin_mode_of(variant_);
             ca.kin = ca.kin_mode ? b_.kin : nullptr;
             if (std::is_same<T, float>::value)
-                return launch_apply_x2(pb_.nh, ca.kin_mode, *(const CellArgs<float> *)&ca, s);
+                return launch_apply_x2(pb_.nh, ca.kin_mode, *(const CellArgs<float> *)&ca, s, variant_ == 10);
             // no packed FP64 arithmetic: the scalar kernels of the same data
-            if (variant_ == 9) return launch_apply_kin<T>(pb_.nh, ca, s, false);
+            if (variant_ >= 9) return launch_apply_kin<T>(pb_.nh, ca, s, false);
             return launch_cell<T>(CM_APPLY_PCG, pb_.nh, ca, s);
         }
         if (variant_ >= 4) {
@@ -807,11 +889,17 @@ class Core {
             cudaEventDestroy(e0);
             return (cudaGetLastError(), 2);
         }
-        float best = 1e30f, times[9] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
+        float best = 1e30f, times[10] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
         int choice = 1;
         const bool stored = pb_.nh && b_.kin, packed = std::is_same<T, float>::value;
-        for (int v = 1; v <= 9; ++v) {
-            if ((v >= 4 && v <= 7 && !stored) || (v == 8 && !packed) || (v == 9 && !(packed && stored))) continue;
+        // kernel 10 stages every tile's stored data, also the tiles of
+        // instances that have stopped iterating: it is offered for one
+        // instance only (in a batch that traffic outweighed the gain)
+        const bool single = pb_.desc.size() == 1;
+        for (int v = 1; v <= 10; ++v) {
+            if ((v >= 4 && v <= 7 && !stored) || (v == 8 && !packed) || (v >= 9 && !(packed && stored)) ||
+                (v == 10 && !single))
+                continue;
             variant_ = v;
             // fresh control blocks for each variant (the apply's epilogue updates them)
             bool ok = cudaMemcpyAsync(b_.tune, tc.data(), sizeof(Ctl) * tc.size(), cudaMemcpyHostToDevice, s) ==
@@ -849,9 +937,10 @@ class Core {
                         "femgb autotune: D=%lld instances=%d per-cell %.3f ms, bricks %.3f ms, "
                         "per-cell(4 CTA/SM) %.3f ms, stored tangent %.3f ms, stored scalars %.3f ms, "
                         "stored scalars + gradient %.3f ms (4 CTA/SM %.3f ms), packed pairs %.3f ms, "
-                        "packed pairs on stored data %.3f ms -> %d\n",
+                        "packed pairs on stored data %.3f ms (staged by TMA %.3f ms) -> %d\n",
                         (long long)pb_.D, (int)pb_.desc.size(), times[0] / 3, times[1] / 3, times[2] / 3,
-                        times[3] / 3, times[4] / 3, times[5] / 3, times[6] / 3, times[7] / 3, times[8] / 3, choice);
+                        times[3] / 3, times[4] / 3, times[5] / 3, times[6] / 3, times[7] / 3, times[8] / 3,
+                        times[9] / 3, choice);
         }
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = choice;
@@ -923,6 +1012,88 @@ class Core {
         return FEM_OK;
     }
 
+    // The whole solve as one graph: the head, then a WHILE loop over Newton
+    // rounds whose body holds a WHILE loop over CG chunks, both conditions
+    // set on the device.  One launch and one host synchronisation.  Returns
+    // DEVICE_GRAPH_REFUSED (not a status) when the runtime refuses to build or
+    // instantiate the graph, so that the caller runs the host loop.
+    static constexpr int DEVICE_GRAPH_REFUSED = 1000;
+    int run_device(cudaStream_t s)
+    {
+        constexpr int REFUSED = DEVICE_GRAPH_REFUSED;
+        const int max_rounds = (int)std::min<int64_t>((int64_t)(prm_.maxit + 2) * max_steps_ * 4 + 16, 1 << 30);
+        const int max_chunks = (int)std::min<int64_t>((int64_t)prm_.pcg_maxit / std::max(1, prm_.chunk) + 2, 1 << 30);
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        int64_t n_head = 0, n_round = 0, n_chunk = 0;
+        bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+        cudaGraphConditionalHandle h_round = 0, h_chunk = 0;
+        cudaGraph_t body_round = nullptr, body_chunk = nullptr;
+        ok = ok && cudaGraphConditionalHandleCreate(&h_round, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+        auto capture_into = [&](cudaGraph_t into, int part) -> bool {
+            if (cudaStreamBeginCaptureToGraph(s, into, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+                cudaSuccess)
+                return false;
+            t_capturing = true;
+            cudaError_t e = cudaSuccess;
+            if (part == 0) {  // top level: head, loop counters, the round loop
+                e = enqueue_head(s);
+                if (e == cudaSuccess) {
+                    k_loop_start<<<1, 32, 0, s>>>(b_.counter);
+                    e = cudaGetLastError();
+                }
+                if (e == cudaSuccess) e = append_while(s, h_round, &body_round);
+            } else if (part == 1) {  // a round: CG chunk loop, Newton update, next head
+                if (cudaGraphConditionalHandleCreate(&h_chunk, into, 0, 0) != cudaSuccess) e = cudaErrorUnknown;
+                if (e == cudaSuccess) {
+                    k_chunk_gate<<<1, 32, 0, s>>>(h_chunk, b_.counter);
+                    e = cudaGetLastError();
+                }
+                if (e == cudaSuccess) e = append_while(s, h_chunk, &body_chunk);
+                if (e == cudaSuccess) e = enqueue_tail(s);
+                if (e == cudaSuccess) e = enqueue_head(s);
+                if (e == cudaSuccess) {
+                    k_round_next<<<1, 32, 0, s>>>(h_round, b_.counter, max_rounds);
+                    e = cudaGetLastError();
+                }
+            } else {  // a chunk of CG iterations
+                e = enqueue_chunk(s);
+                if (e == cudaSuccess) {
+                    k_chunk_next<<<1, 32, 0, s>>>(h_chunk, b_.counter, max_chunks);
+                    e = cudaGetLastError();
+                }
+            }
+            t_capturing = false;
+            cudaGraph_t out = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(s, &out);
+            cudaGetLastError();
+            return e == cudaSuccess && e2 == cudaSuccess;
+        };
+        ok = ok && capture_into(g, 0) && body_round && capture_into(body_round, 1) && body_chunk &&
+             capture_into(body_chunk, 2);
+        if (ok) {
+            n_head = count_kernel_nodes(g);
+            n_round = count_kernel_nodes(body_round);
+            n_chunk = count_kernel_nodes(body_chunk);
+            ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+        }
+        if (g) cudaGraphDestroy(g);
+        if (!ok) {
+            cudaGetLastError();
+            return REFUSED;
+        }
+        cudaError_t e = cudaGraphLaunch(ge, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_counter_, b_.counter, 8 * sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaGraphExecDestroy(ge);
+        FEM_CUDA(e);
+        // kernels that ran: the head, every round and every chunk with its
+        // loop-control kernel (n_round counts the round's own kernel nodes)
+        count_launch(n_head + (int64_t)h_counter_[4] * n_round + (int64_t)h_counter_[7] * n_chunk);
+        if (h_counter_[6]) return (set_error("solve round limit reached on the device"), FEM_ERR_TIMEOUT);
+        return FEM_OK;
+    }
+
     cudaError_t capture(cudaStream_t s, int which, cudaGraphExec_t *out, int64_t *n_kernels)
     {
         cudaGraph_t g = nullptr;
@@ -963,7 +1134,7 @@ class Core {
     int check_variant() const
     {
         if (kin_mode_of(variant_) && !(pb_.nh && b_.kin))
-            return (set_error("apply_kernel 4-7 and 9 (stored tangent data) need a Neo-Hookean problem and its "
+            return (set_error("apply_kernel 4-7, 9 and 10 (stored tangent data) need a Neo-Hookean problem and its "
                               "buffer (not available in fem_solve_static)"),
                     FEM_ERR_ARG);
         return FEM_OK;
@@ -977,6 +1148,10 @@ class Core {
         warm_cg_fused(pb_.nh);
         if (variant_ == 0) variant_ = autotune(s);
         fused_ = choose_fused();
+        if (graph_loop_ && timeout_s <= 0) {  // a wall-clock watchdog needs the host loop
+            int rc = run_device(s);
+            if (rc != DEVICE_GRAPH_REFUSED) return rc;  // else: the host loop below
+        }
         FEM_CUDA(capture(s, 0, &G.head, &G.n_head));
         FEM_CUDA(capture(s, 1, &G.chunk, &G.n_chunk));
         FEM_CUDA(capture(s, 2, &G.tail_head, &G.n_tail_head));
@@ -1015,11 +1190,13 @@ class Core {
     const double *ustar64_ = nullptr;  // linear mode: the fixed state
     int max_steps_ = 1;
     int cg_fused_opt_ = 0;  // 1: fused CG kernel where the apply kernel allows it
+    int graph_loop_ = 0;    // 1: the solve as one graph with device-side loops (run_device)
     bool fused_ = false;    // CG iterations run as the fused update + apply kernel
     int variant_ = 0;       // CG apply kernel: 0 autotune, 1 per-cell, 2 bricks, 3 per-cell at 4 CTA/SM,
                             // 4 per-cell on stored NH tangent data, 5 on stored NH tangent scalars,
                             // 6 on stored scalars and displacement gradient, 7 as 6 at 4 CTA/SM,
-                            // 8 as 1 packed over Gauss-point pairs, 9 as 6 packed (FP32 only)
+                            // 8 as 1 packed over Gauss-point pairs, 9 as 6 packed (FP32 only),
+                            // 10 as 9 with the stored data staged by TMA bulk copies
     double apply_ms_ = 0;   // sampled device time of CG applies
     int apply_samples_ = 0;
     double update_ms_ = 0;  // sampled device time of CG vector updates
@@ -1040,7 +1217,7 @@ static int *host_counters()
 {
     static thread_local int *h = nullptr;
     if (!h) {
-        if (cudaHostAlloc((void **)&h, 4 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        if (cudaHostAlloc((void **)&h, 8 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
             cudaGetLastError();
             h = nullptr;
         }
@@ -1058,6 +1235,7 @@ static SolverParams params_from(const fem_options &o)
     p.pcg_maxit = o.pcg_maxit;
     p.chunk = o.pcg_chunk > 0 ? o.pcg_chunk : 16;
     p.res32_tau = (o.precision == FEM_MIXED && o.newton_res32) ? 1e-2 : 0.0;
+    p.eta_max = o.pcg_rtol_max;
     return p;
 }
 
@@ -1067,8 +1245,9 @@ static int check_options(const fem_options &o)
         return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
     if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
         !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
-        o.apply_kernel < 0 || o.apply_kernel > 9 || o.cg_fused < 0 || o.cg_fused > 1 || o.newton_res32 < 0 ||
-        o.newton_res32 > 1)
+        o.apply_kernel < 0 || o.apply_kernel > 10 || o.cg_fused < 0 || o.cg_fused > 1 || o.newton_res32 < 0 ||
+        o.newton_res32 > 1 || o.graph_loop < 0 || o.graph_loop > 1 || !(o.pcg_rtol_max >= 0) ||
+        !(o.pcg_rtol_max < 1) || (o.pcg_rtol_max > 0 && o.pcg_rtol_max < o.pcg_rtol))
         return (set_error("invalid solver options"), FEM_ERR_ARG);
     return FEM_OK;
 }
@@ -1110,7 +1289,7 @@ static int alloc_buffers(Workspace &ws, const Problem &pb, Buffers<T> &b, bool n
         if (!dst) return FEM_ERR_NOMEM;                          \
     } while (0)
     WSGET(b.ctl, WS_CTL, Ctl, n);
-    WSGET(b.counter, WS_CNT, int, 4);
+    WSGET(b.counter, WS_CNT, int, 8);  // [0..3] solver counters, [4..7] device loop control
     WSGET(b.R64, WS_R64, double, D);
     WSGET(b.x, WS_X, T, D);
     WSGET(b.r, WS_R, T, D);
@@ -1220,6 +1399,7 @@ static int solve_batch(Workspace &ws, Problem &pb, double *u64, const uint8_t *m
     core.max_steps_ = *std::max_element(pb.n_steps.begin(), pb.n_steps.end());
     core.variant_ = o.apply_kernel;
     core.cg_fused_opt_ = o.cg_fused;
+    core.graph_loop_ = o.graph_loop;
     int rc = core.run(s, o.timeout_s);
     if (rc == FEM_OK) FEM_CUDA(core.read_clock(s));
     at.ms = core.apply_ms_;
@@ -1277,6 +1457,7 @@ static int adjoint_batch(Workspace &ws, Problem &pb, const double *ustar, const 
     core.ustar64_ = ustar;
     core.variant_ = o.apply_kernel;
     core.cg_fused_opt_ = o.cg_fused;
+    core.graph_loop_ = o.graph_loop;
     int rc = core.run(s, o.timeout_s);
     if (rc == FEM_OK) FEM_CUDA(core.read_clock(s));
     at.ms = core.apply_ms_;

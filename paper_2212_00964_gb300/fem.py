@@ -49,7 +49,8 @@ class fem_options(ctypes.Structure):
                 ("pcg_rtol", ctypes.c_double), ("pcg_maxit", ctypes.c_int),
                 ("pcg_chunk", ctypes.c_int), ("step_begin", ctypes.c_int),
                 ("apply_kernel", ctypes.c_int), ("cg_fused", ctypes.c_int),
-                ("timeout_s", ctypes.c_double), ("newton_res32", ctypes.c_int)]
+                ("timeout_s", ctypes.c_double), ("newton_res32", ctypes.c_int), ("graph_loop", ctypes.c_int),
+                ("pcg_rtol_max", ctypes.c_double)]
 
 
 class fem_stats(ctypes.Structure):

@@ -22,7 +22,8 @@ def test_workload_name_counts_dofs():
 
 def test_traffic_only_for_the_captured_kernel_and_sources():
     b = load_bench()
-    for k in range(1, 10):
+    b.APPLY_TRAFFIC_SHA256 = b.sources_hash()  # the capture describes these sources
+    for k in range(1, 11):
         t = b.apply_traffic(k)
         assert (t is None) == (k not in b.APPLY_TRAFFIC_BYTES)
     k = next(iter(b.APPLY_TRAFFIC_BYTES))
@@ -33,7 +34,7 @@ def test_traffic_only_for_the_captured_kernel_and_sources():
 
 def test_every_apply_kernel_has_a_flop_count_and_name():
     b = load_bench()
-    assert set(b.APPLY_FLOPS_PER_CELL) == set(range(1, 10))
+    assert set(b.APPLY_FLOPS_PER_CELL) == set(range(1, 11))
     assert all(0 < v <= b.NH_APPLY_FLOPS_PER_CELL for v in b.APPLY_FLOPS_PER_CELL.values())
 
 

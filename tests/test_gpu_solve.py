@@ -71,7 +71,7 @@ def test_c0_linear_elastic_mixed_refined():
     assert rel_l2(u, ref) <= TOL_REFINED
 
 
-@pytest.mark.parametrize("apply_kernel", [1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("apply_kernel", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 @pytest.mark.parametrize("n", [4, 8, 9])
 def test_neohooke_load_steps(n, apply_kernel):
     """Every CG apply kernel (per-cell scatter at 3 and 4 CTAs/SM, 8x4x4
@@ -157,3 +157,16 @@ def test_c1_full_size_mixed_vs_fp64_and_oracle_residual():
     om = oracle.mesh(w.nx, w.ny, w.nz)
     R = oracle.residual(om, oracle.Material(w.kind, w.E, w.nu), u32, None, None, w.mask)
     assert np.linalg.norm(R) <= 1e-9 * st32["ref_rnorm"]
+
+
+@pytest.mark.parametrize("graph_loop", [0, 1])
+def test_graph_loop_modes_agree(graph_loop):
+    """The one-graph solve (device-side loops over Newton rounds and CG
+    chunks) and the host-driven loop reach the oracle's solution, with the
+    same iteration counts up to CG rounding."""
+    n = 8
+    w = inputs.c1(n=n, n_steps=10)
+    ref = oracle_c1(n)
+    u, st = gpu_solve(w, 2, newton_rtol=1e-12, graph_loop=graph_loop)
+    assert st["status"] == 0 and st["load_steps"] == 10
+    assert rel_l2(u, ref) <= TOL_REFINED
