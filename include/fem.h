@@ -326,7 +326,7 @@ typedef struct {
     double newton_rtol;  /* stop when ||R_free|| <= newton_rtol * ||R_free|| of step 1, it 0 */
     double newton_atol;  /* ... or ||R_free|| <= newton_atol */
     int newton_maxit;    /* Newton iterations per load step before FEM_ERR_NOT_CONVERGED */
-    double pcg_rtol;     /* inner CG: ||r|| <= pcg_rtol ||r_0|| (default 3e-3) */
+    double pcg_rtol;     /* inner CG: ||r|| <= eta ||r_0||, eta >= pcg_rtol (default 3e-4) */
     int pcg_maxit;       /* inner CG iteration cap (the iterate is still used) */
     int pcg_chunk;       /* CG iterations per CUDA-graph launch (0 = default) */
     int step_begin;      /* first load step to run (1 = from the start; k+1 resumes a
@@ -367,10 +367,12 @@ typedef struct {
                             timeout_s > 0 (a wall-clock watchdog needs the host loop).  0: one graph
                             launch per CG chunk and per Newton round, with a host read of three
                             counters after each */
-    double pcg_rtol_max; /* 0 (default): the inner CG tolerance is pcg_rtol in every Newton round;
-                            > 0: an adaptive tolerance (the forcing term of Eisenstat and Walker,
-                            choice 2, gamma 0.9) between pcg_rtol and pcg_rtol_max, loose on a load
-                            step's first round and tightening as Newton converges */
+    double pcg_rtol_max; /* > 0 (default 0.1): the inner CG tolerance eta of each Newton round is the
+                            forcing term of Eisenstat and Walker (choice 2, gamma 0.9, safeguarded)
+                            between pcg_rtol and pcg_rtol_max, pcg_rtol on a load step's first
+                            (lifting) round, tightening as Newton converges, never tighter than half
+                            the reduction the Newton stop still needs; 0: eta = pcg_rtol in every
+                            round */
 } fem_options;
 
 typedef struct {

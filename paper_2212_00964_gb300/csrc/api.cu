@@ -50,7 +50,7 @@ extern "C" void fem_default_options(fem_options *o)
     o->newton_rtol = 1e-10;
     o->newton_atol = 0.0;
     o->newton_maxit = 30;
-    o->pcg_rtol = 3e-3;
+    o->pcg_rtol = 3e-4;
     o->pcg_maxit = 5000;
     o->pcg_chunk = 16;
     o->step_begin = 1;
@@ -59,5 +59,5 @@ extern "C" void fem_default_options(fem_options *o)
     o->timeout_s = 0.0;
     o->newton_res32 = 1;
     o->graph_loop = 1;
-    o->pcg_rtol_max = 0.0;
+    o->pcg_rtol_max = 0.1;
 }

@@ -9,18 +9,23 @@ namespace femgb {
 
 // Named device buffers that grow on demand and are never shrunk.
 // Slots 0..31 belong to the solvers, WS_BICG0.. to the assembled-matrix
-// solver, 48..63 to the scalar Poisson path, 64..79 and 88..96 to J2
+// solver, 48..63 to the scalar Poisson path, 64..79 and 88..97 to J2
 // plasticity, 80..87 to the topology-optimisation step.
 enum { WS_BICG0 = 32 };
 
 struct Workspace {
-    enum { N_SLOTS = 97 };
+    enum { N_SLOTS = 128 };
     void *ptr[N_SLOTS] = {};
     size_t cap[N_SLOTS] = {};
 
-    // Returns nullptr (with the error text set) when cudaMalloc fails.
+    // Returns nullptr (with the error text set) when cudaMalloc fails or the
+    // slot does not exist.
     void *get(int slot, size_t bytes)
     {
+        if (slot < 0 || slot >= N_SLOTS) {
+            set_error("workspace: slot out of range");
+            return nullptr;
+        }
         if (bytes == 0) bytes = 16;
         if (cap[slot] >= bytes) return ptr[slot];
         if (ptr[slot]) cudaFree(ptr[slot]);

@@ -114,12 +114,17 @@ __global__ void __launch_bounds__(SX * SY) k_pois_sep(const T *__restrict__ x, c
         }
     }
     T acc = (T)0;
+    // z stencils of an inner plane; a face plane (k = 0 or nz) takes its own
+    T kzi[3], mzi[3];
+    az.at(1, 2, kzi, mzi);
+    T *yp = y + base + sxy * k0;
+    const T *xp = x + base + sxy * k0;
 #pragma unroll
-    for (int p = 0; p < SZ; ++p) {
+    for (int p = 0; p < SZ; ++p, yp += sxy, xp += sxy) {
         const int kk = k0 + p;
         if (kk >= kend) break;  // uniform per block
-        T kz[3], mz[3];
-        az.at(kk, nz, kz, mz);
+        T kz[3] = {kzi[0], kzi[1], kzi[2]}, mz[3] = {mzi[0], mzi[1], mzi[2]};
+        if (kk == 0 || kk == nz) az.at(kk, nz, kz, mz);  // uniform per block
         const int buf = p & 1;
         const T a = mz[0] * xc[p] + mz[1] * xc[p + 1] + mz[2] * xc[p + 2];
         const T b = OP == 0 ? kz[0] * xc[p] + kz[1] * xc[p + 1] + kz[2] * xc[p + 2] : (T)0;
@@ -142,17 +147,16 @@ __global__ void __launch_bounds__(SX * SY) k_pois_sep(const T *__restrict__ x, c
             v = mx[0] * cm + mx[1] * c + mx[2] * cp;
         }
         if (out) {
-            const int64_t n = base + sxy * kk;
             T xn = xc[p + 1];
             if (MODE != poisson::OUT_PLAIN && ((mbits >> (p + 1)) & 1u)) {
                 if (MODE == poisson::OUT_ELIM) {
-                    xn = x[n];
+                    xn = *xp;
                     v = xn;
                 } else {
                     v = (T)0;
                 }
             }
-            y[n] = v;
+            *yp = v;
             if (DOT) acc += xn * v;
         }
     }

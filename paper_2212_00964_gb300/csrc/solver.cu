@@ -150,6 +150,10 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_res_finish(const VecArgs<T> a)
     VEC_ITEMS_END
 }
 
+#ifndef FEMGB_RES32_TAU
+#define FEMGB_RES32_TAU 1e-2  // FP32 Newton residual while ||R|| > this * ||R_ref||
+#endif
+
 // One thread per instance: read the FP64 residual norm, decide convergence,
 // advance load steps, start the next CG.
 __global__ void k_control(Ctl *ctl, int n_inst, SolverParams prm, int *counter)
@@ -201,11 +205,14 @@ __global__ void k_control(Ctl *ctl, int n_inst, SolverParams prm, int *counter)
     // inner CG tolerance: fixed, or the forcing term of Eisenstat and Walker
     // (1996, choice 2: 0.9 (||R_k|| / ||R_k-1||)^2, safeguarded by
     // 0.9 eta_k-1^2 when that exceeds 0.1), kept in [eta, eta_max] and, near
-    // the Newton stop, no tighter than half the remaining reduction needs
+    // the Newton stop, no tighter than half the remaining reduction needs.
+    // A load step's first (lifting) correction is solved to eta: with no
+    // line search, a loose first correction of a large increment can invert
+    // cells.
     double eta = prm.eta;
     if (prm.eta_max > 0) {
         if (lift || !(c.r_prev > 0)) {
-            eta = prm.eta_max;
+            eta = prm.eta;
         } else {
             const double q = rn / c.r_prev;
             eta = 0.9 * q * q;
@@ -1234,7 +1241,7 @@ static SolverParams params_from(const fem_options &o)
     p.eta = o.pcg_rtol;
     p.pcg_maxit = o.pcg_maxit;
     p.chunk = o.pcg_chunk > 0 ? o.pcg_chunk : 16;
-    p.res32_tau = (o.precision == FEM_MIXED && o.newton_res32) ? 1e-2 : 0.0;
+    p.res32_tau = (o.precision == FEM_MIXED && o.newton_res32) ? FEMGB_RES32_TAU : 0.0;
     p.eta_max = o.pcg_rtol_max;
     return p;
 }
