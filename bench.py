@@ -55,8 +55,14 @@ NH_APPLY_FLOPS_PER_CELL = 3269
 # Kernels 8 and 9 are kernels 1 and 6 evaluated two Gauss points per packed
 # FP32 instruction, 10 is 9 with its stored data staged by TMA: the same
 # algorithmic flops.
+# Kernel 11 is linear-elastic / SIMP only (tensor cores, shared element
+# matrix): its count is the LE one below.
+# Linear-elastic / SIMP apply with the shared element matrix: y_e = s_e K0 x_e
+# 24 x 24 x 2 = 1,152, the scale 24, the p.Kp partial 48.
+LE_APPLY_FLOPS_PER_CELL = 1224
 APPLY_FLOPS_PER_CELL = {1: NH_APPLY_FLOPS_PER_CELL, 2: NH_APPLY_FLOPS_PER_CELL, 3: NH_APPLY_FLOPS_PER_CELL,
-                        4: 2517, 5: 2733, 6: 2445, 7: 2445, 8: NH_APPLY_FLOPS_PER_CELL, 9: 2445, 10: 2445}
+                        4: 2517, 5: 2733, 6: 2445, 7: 2445, 8: NH_APPLY_FLOPS_PER_CELL, 9: 2445, 10: 2445,
+                        11: LE_APPLY_FLOPS_PER_CELL}
 # DRAM bytes (read + write) of one launch of a CG apply kernel, by apply
 # kernel id, from the ncu capture summarised in profiles/ (kernel 9:
 # cg_apply_nh64_kernel9.md; cold caches under ncu, so the 71 MB of stored data
@@ -105,7 +111,8 @@ def parse():
     ap.add_argument("--pcg-rtol", type=float, default=3e-4, help="inner CG relative tolerance (lower bound)")
     ap.add_argument("--apply-kernel", type=int, default=0,
                     help="0 autotuned, 1 per-cell, 2 bricks, 3 per-cell 4 CTA/SM, 4/5/6/7 stored tangent data, "
-                         "8/9 packed Gauss-point pairs (recomputed / stored data), 10 as 9 staged by TMA")
+                         "8/9 packed Gauss-point pairs (recomputed / stored data), 10 as 9 staged by TMA, "
+                         "11 LE/SIMP on the tensor cores (also the CG kernel of --profile-op le_apply, default 8)")
     ap.add_argument("--newton-res32", type=int, default=1,
                     help="0: FP64 Newton residual in every iteration")
     ap.add_argument("--cg-fused", type=int, default=0,
@@ -119,7 +126,7 @@ def parse():
     ap.add_argument("--graph-loop", type=int, default=1,
                     help="1: each solve is one graph launch with device-side loops; 0: host-driven loop")
     ap.add_argument("--profile-op", default=None,
-                    choices=["nh_apply", "le_apply", "poisson_apply", "j2_apply", "filter"],
+                    choices=["nh_apply", "le_apply", "le_apply_tc", "poisson_apply", "j2_apply", "filter"],
                     help="run one operator a few times on its benchmark size and exit (for ncu captures)")
     return ap.parse_args()
 
@@ -332,6 +339,15 @@ def device_time(torch, fn, reps=10, flush=None):
     return float(np.median(times)), mode
 
 
+def measured_hbm_gbs():
+    """The measured HBM copy bandwidth of MEASURED_PEAKS.json (GB/s), or None."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def suite(F, inputs, torch):
     """Secondary measurements of the hot path (each timed once after one
     untimed run): the 256-instance batched Neo-Hookean solve, the SIMP
@@ -400,8 +416,31 @@ def suite(F, inputs, torch):
     out["adjoint_c2"] = {"dofs": w.n_dofs, "cells": w.n_cells, "forward_s": tf, "adjoint_s": ta,
                          "compliance": float(f @ u), "grad_norm": float(torch.linalg.norm(g)),
                          "forward_cg_iters": stf["pcg_iters"], "adjoint_cg_iters": sta["pcg_iters"],
-                         "status": [stf["status"], sta["status"]]}
-    del m, u, g
+                         "apply_kernel": stf["apply_kernel"], "status": [stf["status"], sta["status"]]}
+    # the SIMP CG apply on CUDA cores (packed pairs, kernel 8) against the
+    # tensor cores (shared element matrix, kernel 11): live kernel span per
+    # apply in the same forward solve, against the algorithmic 8 D + 4 Ne bytes
+    hbm_peak = measured_hbm_gbs()
+    le = {"algorithmic_bytes": 8 * w.n_dofs + 4 * w.n_cells,
+          "note": "live span of the CG apply inside the c2 forward solve (vectors L2-resident)"}
+    u_ref = u.clone()
+    for k in (8, 11):
+        ok = F.default_options(newton_rtol=1e-10, apply_kernel=k)
+
+        def fwd_k():
+            u.zero_()
+            return F.fem_solve(m, mat, mask, ubar, u, f, th, 1, ok)
+
+        tk, stk = timed(fwd_k)
+        us = stk["apply_ms"] * 1e3 / max(stk["apply_samples"], 1)
+        gbs = le["algorithmic_bytes"] / (us * 1e-6) / 1e9
+        le[f"kernel_{k}"] = {"solve_s": tk, "cg_iters": stk["pcg_iters"], "apply_us": us,
+                             "gbs_algorithmic": gbs, "hbm_frac_of_measured": gbs / hbm_peak if hbm_peak else None,
+                             "tflops": LE_APPLY_FLOPS_PER_CELL * w.n_cells / (us * 1e-6) / 1e12,
+                             "rel_l2_vs_default": float(torch.linalg.norm(u - u_ref) / torch.linalg.norm(u_ref)),
+                             "status": stk["status"]}
+    out["le_apply_c2"] = le
+    del m, u, g, u_ref
 
     # c4: 128^3 Neo-Hookean, 5 load steps, face-displacement objective
     w = inputs.c4()
@@ -463,13 +502,40 @@ def suite(F, inputs, torch):
             xx = torch.tensor(x0, dtype=dt, device="cuda")
             yy = torch.empty_like(xx)
             cp = torch.tensor(w.cell_param, dtype=dt, device="cuda") if w.cell_param is not None else None
-            t, mode = device_time(torch, lambda: F.fem_tangent_apply(m, mat, uu, xx, cp, mask, yy), 10, flush)
+            call = lambda: F.fem_tangent_apply(m, mat, uu, xx, cp, mask, yy)
+            t, mode = device_time(torch, call, 10, flush)
             flops = NH_APPLY_FLOPS_PER_CELL * w.n_cells / t / 1e12
             peak = FP32_PEAK_TFLOPS if name == "fp32" else FP64_PEAK_TFLOPS
-            out["apply_standalone"][f"{n}^3_{name}"] = {"dofs": w.n_dofs, "time_us": t * 1e6,
-                                                         "gdofs": w.n_dofs / t / 1e9, "tflops": flops,
-                                                         "frac_of_peak": flops / peak, "timing": mode}
+            e = {"dofs": w.n_dofs, "time_us": t * 1e6, "gdofs": w.n_dofs / t / 1e9, "tflops": flops,
+                 "frac_of_peak": flops / peak, "timing": mode, "l2": "flushed"}
+            if name == "fp32":  # the same call with its inputs left in L2 by the previous replay
+                tw, _ = device_time(torch, call, 10, None)
+                e["l2_warm"] = {"time_us": tw * 1e6, "gdofs": w.n_dofs / tw / 1e9,
+                                "frac_of_peak": NH_APPLY_FLOPS_PER_CELL * w.n_cells / tw / 1e12 / peak}
+            out["apply_standalone"][f"{n}^3_{name}"] = e
         del m, uu, xx, yy
+    # the SIMP apply of the c2 cantilever on the CUDA cores (packed pairs)
+    # and on the tensor cores (shared element matrix): algorithmic bytes
+    # 8 D + 4 Ne against the measured HBM peak
+    w = inputs.c2()
+    mat = F.material(w.kind, w.E, w.nu, w.simp_p, w.simp_emin)
+    mask = torch.tensor(w.mask, device="cuda")
+    xx = torch.tensor(np.random.default_rng(12).standard_normal(w.n_dofs), dtype=torch.float32, device="cuda")
+    uu, yy = torch.zeros_like(xx), torch.empty_like(xx)
+    th = torch.tensor(w.cell_param, dtype=torch.float32, device="cuda")
+    hbm_peak = measured_hbm_gbs()
+    for unit, kern in (("cuda_cores", "k_apply_init + cell_apply_x2<LE,CM_APPLY,KIN=0>"),
+                       ("tensor_cores", "k_le_k0 + k_apply_init + cell_apply_le_tc<false>")):
+        m = F.fem_mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, tensor_cores=unit == "tensor_cores")
+        for l2, fl in (("flushed", flush), ("warm", None)):
+            t, mode = device_time(torch, lambda: F.fem_tangent_apply(m, mat, uu, xx, th, mask, yy), 10, fl)
+            gbs = (8 * w.n_dofs + 4 * w.n_cells) / t / 1e9
+            out["apply_standalone"][f"c2_simp_fp32_{unit}_l2_{l2}"] = {
+                "dofs": w.n_dofs, "time_us": t * 1e6, "gdofs": w.n_dofs / t / 1e9, "gbs_algorithmic": gbs,
+                "hbm_frac_of_measured": gbs / hbm_peak if hbm_peak else None,
+                "tflops": LE_APPLY_FLOPS_PER_CELL * w.n_cells / t / 1e12, "timing": mode, "kernels": kern}
+        del m
+    del uu, xx, yy, th
     del flush
 
     # the paper's solve path on the same 64^3 Neo-Hookean box: the tangent at
@@ -519,12 +585,7 @@ def next_suite(F, inputs, torch):
     instead of stopping the benchmark."""
     import numpy as np
     out = {}
-    hbm_peak = None
-    try:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
-            hbm_peak = float(json.load(fh)["hbm_gbs"])
-    except (OSError, KeyError, ValueError):
-        pass
+    hbm_peak = measured_hbm_gbs()
 
     def guarded(name, fn):
         try:
@@ -672,14 +733,16 @@ def standalone_roofline(extra):
     return {"bound": "alu", "kernel": "k_apply_init + cell_apply_x2<NH,CM_APPLY,KIN=0>", "achieved": e["tflops"],
             "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": e["tflops"] / FP32_PEAK_TFLOPS, "traffic": None,
             "time_us": e["time_us"], "gdofs": e["gdofs"], "flop_per_cell": NH_APPLY_FLOPS_PER_CELL,
-            "timing": "graph replay of one fem_tangent_apply call, L2 flushed before each"}
+            "timing": "graph replay of one fem_tangent_apply call, L2 flushed before each",
+            "l2_warm": e.get("l2_warm")}
 
 
 def profile_op(args):
     """A few calls of one operator at its benchmark size (first call warms up),
     for a profiler capture of a single launch: the FP32 Neo-Hookean tangent
     apply at 64^3, the SIMP (linear-elastic) CG apply of the 128x64x64
-    cantilever inside one solve, the Poisson stiffness operator at
+    cantilever inside one solve, the standalone SIMP apply of the same
+    cantilever (tensor cores), the Poisson stiffness operator at
     512x512x128, the FP32 J2 tangent apply at 64^3 (uniaxial state after one
     load step), the cone filter (r_min 1.5) on the 128x64x64 cantilever."""
     import numpy as np
@@ -708,11 +771,20 @@ def profile_op(args):
         u = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
         # host-driven loop: ncu does not profile kernels inside graphs with
         # conditional nodes
-        o = F.default_options(newton_rtol=1e-10, apply_kernel=8, graph_loop=0)
+        o = F.default_options(newton_rtol=1e-10, apply_kernel=args.apply_kernel or 8, graph_loop=0)
 
         def call():
             u.zero_()
             F.fem_solve(m, mat, mask, ubar, u, f, th, 1, o)
+    elif op == "le_apply_tc":
+        w = inputs.c2()
+        m = F.fem_mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, tensor_cores=True)
+        mat = F.material(w.kind, w.E, w.nu, w.simp_p, w.simp_emin)
+        mask = torch.tensor(w.mask, device="cuda")
+        x = torch.tensor(np.random.default_rng(12).standard_normal(w.n_dofs), dtype=torch.float32, device="cuda")
+        u, y = torch.zeros_like(x), torch.empty_like(x)
+        th = torch.tensor(w.cell_param, dtype=torch.float32, device="cuda")
+        call = lambda: F.fem_tangent_apply(m, mat, u, x, th, mask, y)
     elif op == "poisson_apply":
         w = inputs.poisson_inference(512, 512, 128, 1.0, 1.0, 0.2)
         m = F.fem_mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)

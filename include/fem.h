@@ -87,6 +87,12 @@ typedef struct {
                                     on this mesh scatter colour by colour with plain
                                     stores (cells of one colour share no node), so their
                                     results are bit-reproducible; default: atomics */
+#define FEM_MESH_TENSOR_CORES 4 /* FP32 fem_tangent_apply of a linear-elastic or SIMP
+                                   material on this mesh runs on the tensor cores (the
+                                   shared element matrix as split-TF32 tcgen05 MMAs, Sec. 2.3
+                                   Eq. (11)); default: the CUDA-core kernel, which is faster on
+                                   GB300 (see apply_kernel 11). Ignored with
+                                   FEM_MESH_DETERMINISTIC and for other materials/precisions */
 
 /* Build a structured box mesh on the device (the paper's linear hexahedra,
  * Sec. 3.1): connectivity, coordinates, the 8-colour cell colouring and,

@@ -2,11 +2,14 @@
 // tangent apply, diagonal, VJP, CSR assembly) and the cell-kernel launcher
 // shared with the solvers.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 
 #include "cell_kernels.cuh"
 #include "cell_ops.cuh"
+#include "cell_tc.cuh"
 #include "cell_x2.cuh"
 #include "mesh.cuh"
 
@@ -34,7 +37,12 @@ int resident_grid(const void *func, int block, size_t smem)
     int nb;
     if (it == g_occ.end()) {
         nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, block, smem) != cudaSuccess || nb < 1) {
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, block, smem);
+        if (const char *env = getenv("FEMGB_OCC_LOG"))
+            if (env[0] == '1')
+                fprintf(stderr, "femgb occupancy: kernel %p block %d smem %zu -> %d CTAs/SM (%s)\n", func, block, smem,
+                        nb, cudaGetErrorString(e));
+        if (e != cudaSuccess || nb < 1) {
             cudaGetLastError();
             nb = 1;
         }
@@ -190,6 +198,43 @@ cudaError_t launch_apply_x2(bool nh, int kin, const CellArgs<float> &a, cudaStre
     return launch_pdl(f, (int)g, CELL_BLOCK, smem, s, a);  // waits (pdl_wait) before reading CG vectors
 }
 
+// Unit-scale linear-elastic element matrix of the instance (24 x 24 FP32)
+// for the tensor-core apply.
+cudaError_t launch_le_k0(const InstDesc &d, float *k0, cudaStream_t s)
+{
+    if (d.kind == FEM_NEOHOOKE || !k0) return cudaErrorInvalidValue;
+    count_launch();
+    k_le_k0<<<(TC_K * TC_K + 127) / 128, 128, 0, s>>>(d, k0);
+    return cudaGetLastError();
+}
+
+// Apply of one linear-elastic / SIMP instance on the tensor cores: the CG
+// apply (pcg) or the standalone masked apply.
+cudaError_t launch_apply_le_tc(const CellArgs<float> &a, const float *k0, cudaStream_t s, bool pcg)
+{
+    if (a.tab || a.cells || !k0 || a.d0.kind == FEM_NEOHOOKE) return cudaErrorInvalidValue;
+    auto f = pcg ? cell_apply_le_tc<true> : cell_apply_le_tc<false>;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        // 30 KB of static shared memory per CTA: ask for the largest shared
+        // memory carveout, or the default split leaves room for one CTA per SM
+        for (auto k : {cell_apply_le_tc<true>, cell_apply_le_tc<false>}) {
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BYTES) != cudaSuccess)
+                cudaGetLastError();
+            if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+                cudaGetLastError();
+        }
+    });
+    // the register budget (launch bounds) and the shared memory fit
+    // FEMGB_TC_MINB CTAs per SM
+    const int occ = resident_grid((const void *)f, CELL_BLOCK, TC_SMEM_BYTES);
+    int64_t g = std::min<int64_t>(a.n_tiles, std::max<int64_t>(occ, (int64_t)FEMGB_TC_MINB * device_sms()));
+    if (g < 1) return cudaSuccess;
+    count_launch();
+    return launch_pdl(f, (int)g, CELL_BLOCK, TC_SMEM_BYTES, s, a, k0);  // waits (pdl_wait) before reading
+}
+
 template <typename T>
 cudaError_t launch_apply_brick(bool nh, const CellArgs<T> &a, cudaStream_t s)
 {
@@ -333,10 +378,32 @@ static int residual_t(fem_mesh_t m, const fem_material *mat, const T *u, const T
     return FEM_OK;
 }
 
-// y = mask ? x : 0 (the prescribed rows of the eliminated tangent apply)
-template <typename T>
-__global__ void k_apply_init(T *y, const T *x, const uint8_t *mask, int64_t n)
+// This block's share of [p, p + bytes) requested into L2 by one bulk prefetch
+// (16-byte granules; nothing for an unaligned array).
+__device__ __forceinline__ void l2_prefetch_share(const void *p, size_t bytes)
 {
+    if (!p || ((uintptr_t)p & 15)) return;
+    const size_t chunk = ((bytes + gridDim.x - 1) / gridDim.x + 15) & ~(size_t)15;
+    const size_t b0 = (size_t)blockIdx.x * chunk;
+    if (b0 >= bytes) return;
+    const size_t len = (chunk < bytes - b0 ? chunk : bytes - b0) & ~(size_t)15;
+    if (len == 0) return;
+    unsigned long long g;
+    asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"((const char *)p + b0));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g), "r"((unsigned)len) : "memory");
+}
+
+// y = mask ? x : 0 (the prescribed rows of the eliminated tangent apply);
+// with pf0 / pf1 the arrays the apply gathers next (of n values) are
+// prefetched into L2 on the way.
+template <typename T>
+__global__ void k_apply_init(T *y, const T *x, const uint8_t *mask, int64_t n, const T *pf0 = nullptr,
+                             const T *pf1 = nullptr)
+{
+    if (threadIdx.x == 0) {
+        l2_prefetch_share(pf0, sizeof(T) * (size_t)n);
+        l2_prefetch_share(pf1, sizeof(T) * (size_t)n);
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = (mask && mask[i]) ? x[i] : (T)0;
 }
@@ -347,7 +414,7 @@ static int apply_x2_standalone(fem_mesh_t m, const fem_material *mat, const floa
                                const uint8_t *mask, const float *x, float *y, cudaStream_t s)
 {
     const int64_t D = m->n_dofs();
-    k_apply_init<float><<<vgrid(D), 256, 0, s>>>(y, x, mask, D);
+    k_apply_init<float><<<vgrid(D), 256, 0, s>>>(y, x, mask, D, x, u);
     count_launch();
     CellArgs<float> a{};
     a.d0 = make_desc(m, mat);
@@ -364,10 +431,33 @@ static int apply_x2_standalone(fem_mesh_t m, const fem_material *mat, const floa
     return FEM_OK;
 }
 
+// FP32 linear-elastic / SIMP tangent apply on an atomic-scatter mesh on the
+// tensor cores: the element matrix of this material, the prescribed rows,
+// then the masked apply.
+static int apply_le_tc_standalone(fem_mesh_t m, const fem_material *mat, const float *cp, const uint8_t *mask,
+                                  const float *x, float *y, cudaStream_t s)
+{
+    float *k0 = (float *)m->ws.get(WS_APPLY_K0, sizeof(float) * TC_K * TC_K);
+    if (!k0) return FEM_ERR_NOMEM;
+    const int64_t D = m->n_dofs();
+    CellArgs<float> a{};
+    a.d0 = make_desc(m, mat);
+    a.n_tiles = (m->n_cells + CELL_BLOCK - 1) / CELL_BLOCK;
+    a.x = x; a.y = y; a.cell_param = cp; a.mask = mask;
+    FEM_CUDA(launch_le_k0(a.d0, k0, s));
+    k_apply_init<float><<<vgrid(D), 256, 0, s>>>(y, x, mask, D, x);
+    count_launch();
+    FEM_CUDA(launch_apply_le_tc(a, k0, s, false));
+    FEM_CUDA(cudaGetLastError());
+    return FEM_OK;
+}
+
 template <typename T>
 static int apply_t(fem_mesh_t m, const fem_material *mat, const T *u, const T *cp, const uint8_t *mask, const T *x,
                    T *y, cudaStream_t s)
 {
+    if (std::is_same<T, float>::value && !m->det && m->tc && mat->kind != FEM_NEOHOOKE)
+        return apply_le_tc_standalone(m, mat, (const float *)cp, mask, (const float *)x, (float *)y, s);
     if (std::is_same<T, float>::value && !m->det)
         return apply_x2_standalone(m, mat, (const float *)u, (const float *)cp, mask, (const float *)x, (float *)y, s);
     const int64_t D = m->n_dofs();

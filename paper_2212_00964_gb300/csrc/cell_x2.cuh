@@ -426,6 +426,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, FEMGB_X2_MINB) cell_apply_x2(const
         const uint8_t *mb = (MODE == CM_APPLY && a.mask) ? a.mask + d.dof_off : nullptr;
 
         // gathers first (one exposed latency per cell)
+        unsigned mbits = 0;  // CM_APPLY: prescribed DOFs of the cell
         float2 X[3][4];
         float2 U[3][4];
         {
@@ -442,12 +443,20 @@ __global__ void __launch_bounds__(CELL_BLOCK, FEMGB_X2_MINB) cell_apply_x2(const
                     for (int i = 0; i < 4; ++i) U[c][i] = pk(ub[3 * nq[i] + c], ub[3 * nq[i] + 3 + c]);
             }
             if (mb) {
+                // the cell's 24 prescribed flags, read once: bit c + 3 (2 i + p)
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        if (mb[3 * nq[i] + c]) X[c][i].x = 0.f;
-                        if (mb[3 * nq[i] + 3 + c]) X[c][i].y = 0.f;
+                        if (mb[3 * nq[i] + c]) mbits |= 1u << (c + 6 * i);
+                        if (mb[3 * nq[i] + 3 + c]) mbits |= 1u << (c + 6 * i + 3);
+                    }
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (mbits & (1u << (c + 6 * i))) X[c][i].x = 0.f;
+                        if (mbits & (1u << (c + 6 * i + 3))) X[c][i].y = 0.f;
                     }
             }
         }
@@ -572,8 +581,8 @@ __global__ void __launch_bounds__(CELL_BLOCK, FEMGB_X2_MINB) cell_apply_x2(const
             for (int c = 0; c < 3; ++c)
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    if (!(mb && mb[3 * nq[i] + c])) red_add(&yb[3 * nq[i] + c], Y[c][i].x);
-                    if (!to_right && !(mb && mb[3 * nq[i] + 3 + c])) red_add(&yb[3 * nq[i] + 3 + c], Y[c][i].y);
+                    if (!(mbits & (1u << (c + 6 * i)))) red_add(&yb[3 * nq[i] + c], Y[c][i].x);
+                    if (!to_right && !(mbits & (1u << (c + 6 * i + 3)))) red_add(&yb[3 * nq[i] + 3 + c], Y[c][i].y);
                 }
         }
         if (STAGE) __syncthreads();  // buffer (it & 1) is refilled by the next iteration's prefetch

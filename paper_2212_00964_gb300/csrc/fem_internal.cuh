@@ -765,10 +765,11 @@ __device__ __forceinline__ void le_stress(const T *H, const Mat<T> &m, T *P)
             P[3 * i + j] = m.c2 * (H[3 * i + j] + H[3 * j + i]) + (i == j ? tr : (T)0);
 }
 
-// Cell material constants from the instance and the cell parameter, in T
-// only (the unit-scale constants were derived on the host).
+// Stiffness scale s_e of a cell (the SIMP law of the density, or the plain
+// scale) and the cell's material constants, in T only (the unit-scale
+// constants were derived on the host).
 template <typename T>
-__device__ __forceinline__ Mat<T> cell_mat(const InstDesc &d, const T *cell_param, int64_t cell)
+__device__ __forceinline__ T cell_scale(const InstDesc &d, const T *cell_param, int64_t cell)
 {
     T sc = (T)1;
     if (d.kind == FEM_SIMP) {
@@ -779,6 +780,13 @@ __device__ __forceinline__ Mat<T> cell_mat(const InstDesc &d, const T *cell_para
     } else if (cell_param) {
         sc = cell_param[cell];
     }
+    return sc;
+}
+
+template <typename T>
+__device__ __forceinline__ Mat<T> cell_mat(const InstDesc &d, const T *cell_param, int64_t cell)
+{
+    const T sc = cell_scale<T>(d, cell_param, cell);
     Mat<T> m;
     m.c1 = d.c1u<T>() * sc;
     m.c2 = d.c2u<T>() * sc;

@@ -189,6 +189,7 @@ extern "C" int fem_mesh(int nx, int ny, int nz, double lx, double ly, double lz,
     m->lx = lx; m->ly = ly; m->lz = lz;
     m->n_nodes = n_nodes; m->n_cells = n_cells; m->nnz = csr ? nnz : 0;
     m->det = (flags & FEM_MESH_DETERMINISTIC) != 0;
+    m->tc = (flags & FEM_MESH_TENSOR_CORES) != 0;
     auto fail = [&](cudaError_t e, const char *what) {
         int rc = cuda_fail(e, what, __FILE__, __LINE__);
         fem_mesh_destroy(m);

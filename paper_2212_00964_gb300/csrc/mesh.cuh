@@ -10,8 +10,9 @@ namespace femgb {
 // Named device buffers that grow on demand and are never shrunk.
 // Slots 0..31 belong to the solvers, WS_BICG0.. to the assembled-matrix
 // solver, 48..63 to the scalar Poisson path, 64..79 and 88..97 to J2
-// plasticity, 80..87 to the topology-optimisation step.
-enum { WS_BICG0 = 32 };
+// plasticity, 80..87 to the topology-optimisation step, WS_APPLY_K0 to the
+// standalone tensor-core tangent apply.
+enum { WS_BICG0 = 32, WS_APPLY_K0 = 100 };
 
 struct Workspace {
     enum { N_SLOTS = 128 };
@@ -64,6 +65,7 @@ struct fem_mesh_s {
     int32_t *row_ptr = nullptr;
     int32_t *col = nullptr;
     bool det = false;  // FEM_MESH_DETERMINISTIC: colour-ordered cell operators
+    bool tc = false;   // FEM_MESH_TENSOR_CORES: FP32 LE/SIMP applies on the tensor cores
     femgb::Workspace ws;
     std::mutex mu;  // one solve per handle at a time
 

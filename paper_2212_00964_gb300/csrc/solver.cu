@@ -550,6 +550,7 @@ struct Buffers {
     KernelClock *kclock; // live span statistics of the CG kernels (may be null)
     T *kin;              // stored NH tangent data for apply kernels 4, 5 (may be null)
     T *r2, *s2, *q2, *q3; // second r and s, second and third w of the fused CG kernel (may be null)
+    float *k0;           // unit-scale linear-elastic element matrix for apply kernel 11 (may be null)
 };
 
 // ---- one-graph solve: loop control on the device --------------------------
@@ -832,6 +833,10 @@ class Core {
         }
         ca.n_tiles = pb_.n_tiles;
         if (variant_ == 3) return launch_apply_cell4<T>(pb_.nh, ca, s);
+        if (variant_ == 11) {
+            if (!std::is_same<T, float>::value) return launch_cell<T>(CM_APPLY_PCG, pb_.nh, ca, s);
+            return launch_apply_le_tc(*(const CellArgs<float> *)&ca, b_.k0, s);
+        }
         if (variant_ >= 8) {
             ca.kin_mode = kin_mode_of(variant_);
             ca.kin = ca.kin_mode ? b_.kin : nullptr;
@@ -896,16 +901,16 @@ class Core {
             cudaEventDestroy(e0);
             return (cudaGetLastError(), 2);
         }
-        float best = 1e30f, times[10] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
+        float best = 1e30f, times[11] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
         int choice = 1;
         const bool stored = pb_.nh && b_.kin, packed = std::is_same<T, float>::value;
         // kernel 10 stages every tile's stored data, also the tiles of
         // instances that have stopped iterating: it is offered for one
         // instance only (in a batch that traffic outweighed the gain)
         const bool single = pb_.desc.size() == 1;
-        for (int v = 1; v <= 10; ++v) {
-            if ((v >= 4 && v <= 7 && !stored) || (v == 8 && !packed) || (v >= 9 && !(packed && stored)) ||
-                (v == 10 && !single))
+        for (int v = 1; v <= 11; ++v) {
+            if ((v >= 4 && v <= 7 && !stored) || (v == 8 && !packed) || (v >= 9 && v <= 10 && !(packed && stored)) ||
+                (v == 10 && !single) || (v == 11 && !tc_ok()))
                 continue;
             variant_ = v;
             // fresh control blocks for each variant (the apply's epilogue updates them)
@@ -929,7 +934,10 @@ class Core {
                  probe.status == 0 && probe.go == 1;  // the probe kept iterating
             if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
                 times[v - 1] = ms;
-                if (ms < best) {
+                // a later (more specialised) variant replaces the current
+                // choice only when it is faster by more than the probe's
+                // spread of about 2 %
+                if (ms < 0.98f * best) {
                     best = ms;
                     choice = v;
                 }
@@ -944,10 +952,10 @@ class Core {
                         "femgb autotune: D=%lld instances=%d per-cell %.3f ms, bricks %.3f ms, "
                         "per-cell(4 CTA/SM) %.3f ms, stored tangent %.3f ms, stored scalars %.3f ms, "
                         "stored scalars + gradient %.3f ms (4 CTA/SM %.3f ms), packed pairs %.3f ms, "
-                        "packed pairs on stored data %.3f ms (staged by TMA %.3f ms) -> %d\n",
+                        "packed pairs on stored data %.3f ms (staged by TMA %.3f ms), tensor cores %.3f ms -> %d\n",
                         (long long)pb_.D, (int)pb_.desc.size(), times[0] / 3, times[1] / 3, times[2] / 3,
                         times[3] / 3, times[4] / 3, times[5] / 3, times[6] / 3, times[7] / 3, times[8] / 3,
-                        times[9] / 3, choice);
+                        times[9] / 3, times[10] / 3, choice);
         }
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = choice;
@@ -983,6 +991,7 @@ class Core {
     {
         if (int rc = check_variant()) return rc;
         warm_occupancy(pb_.nh);
+        FEM_CUDA(prepare_tc(s));
         if (variant_ == 0) variant_ = 1;  // no probe timing without events: the per-cell kernel
         auto t0 = std::chrono::steady_clock::now();
         auto expired = [&]() {
@@ -1138,8 +1147,22 @@ class Core {
         return cg_fused_opt_ == 1 && (variant_ == 1 || variant_ == 5) && b_.r2 && b_.s2 && b_.q2 && b_.q3;
     }
 
+    // apply kernel 11: one FP32 linear-elastic / SIMP instance with its element matrix buffer
+    bool tc_ok() const { return !pb_.nh && std::is_same<T, float>::value && pb_.desc.size() == 1 && b_.k0; }
+
+    // the element matrix of apply kernel 11, for this solve's material
+    cudaError_t prepare_tc(cudaStream_t s)
+    {
+        if (!tc_ok()) return cudaSuccess;
+        return launch_le_k0(pb_.desc[0], b_.k0, s);
+    }
+
     int check_variant() const
     {
+        if (variant_ == 11 && (pb_.nh || pb_.desc.size() != 1 || (std::is_same<T, float>::value && !b_.k0)))
+            return (set_error("apply_kernel 11 (tensor cores) needs one linear-elastic or SIMP instance in "
+                              "FEM_MIXED precision"),
+                    FEM_ERR_ARG);
         if (kin_mode_of(variant_) && !(pb_.nh && b_.kin))
             return (set_error("apply_kernel 4-7, 9 and 10 (stored tangent data) need a Neo-Hookean problem and its "
                               "buffer (not available in fem_solve_static)"),
@@ -1153,6 +1176,7 @@ class Core {
         Graphs G;
         warm_occupancy(pb_.nh);
         warm_cg_fused(pb_.nh);
+        FEM_CUDA(prepare_tc(s));
         if (variant_ == 0) variant_ = autotune(s);
         fused_ = choose_fused();
         if (graph_loop_ && timeout_s <= 0) {  // a wall-clock watchdog needs the host loop
@@ -1252,7 +1276,7 @@ static int check_options(const fem_options &o)
         return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
     if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
         !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
-        o.apply_kernel < 0 || o.apply_kernel > 10 || o.cg_fused < 0 || o.cg_fused > 1 || o.newton_res32 < 0 ||
+        o.apply_kernel < 0 || o.apply_kernel > 11 || o.cg_fused < 0 || o.cg_fused > 1 || o.newton_res32 < 0 ||
         o.newton_res32 > 1 || o.graph_loop < 0 || o.graph_loop > 1 || !(o.pcg_rtol_max >= 0) ||
         !(o.pcg_rtol_max < 1) || (o.pcg_rtol_max > 0 && o.pcg_rtol_max < o.pcg_rtol))
         return (set_error("invalid solver options"), FEM_ERR_ARG);
@@ -1283,7 +1307,7 @@ static cudaError_t join_streams(cudaStream_t from, cudaStream_t to)
 enum {
     WS_CTL = 0, WS_CNT, WS_R64, WS_UT, WS_X, WS_R, WS_Z, WS_P, WS_Q, WS_DG, WS_LAM, WS_TAB, WS_CPT,
     WS_U64CAT, WS_MASKCAT, WS_UBARCAT, WS_RHSCAT, WS_CP64CAT, WS_G64, WS_S, WS_TUNE, WS_KCLOCK, WS_KIN,
-    WS_R2, WS_S2, WS_Q2, WS_Q3
+    WS_R2, WS_S2, WS_Q2, WS_Q3, WS_K0
 };
 
 template <typename T>
@@ -1315,6 +1339,9 @@ static int alloc_buffers(Workspace &ws, const Problem &pb, Buffers<T> &b, bool n
     b.s2 = (T *)ws.get(WS_S2, sizeof(T) * (size_t)D);
     b.q2 = (T *)ws.get(WS_Q2, sizeof(T) * (size_t)D);
     b.q3 = (T *)ws.get(WS_Q3, sizeof(T) * (size_t)D);
+    // element matrix of the tensor-core apply (one FP32 linear-elastic / SIMP
+    // instance); optional: without it apply kernel 11 is not offered
+    b.k0 = (!pb.nh && sizeof(T) == 4 && n == 1) ? (float *)ws.get(WS_K0, sizeof(float) * 24 * 24) : nullptr;
     if (n > 1) WSGET(b.tab, WS_TAB, InstDesc, n);
     else b.tab = nullptr;
     if (need_uT) WSGET(b.uT, WS_UT, T, D);

@@ -24,6 +24,7 @@ FEM_LINEAR, FEM_SIMP, FEM_NEOHOOKE = 0, 1, 2
 FEM_FP64, FEM_FP32, FEM_MIXED = 0, 1, 2
 FEM_MESH_CSR = 1
 FEM_MESH_DETERMINISTIC = 2
+FEM_MESH_TENSOR_CORES = 4
 FEM_POISSON_STIFFNESS, FEM_POISSON_MASS = 0, 1
 FACES = {"x0": 0, "x1": 1, "y0": 2, "y1": 3, "z0": 4, "z1": 5}
 
@@ -204,9 +205,11 @@ class Mesh:
             pass
 
 
-def fem_mesh(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, csr=False, stream=None, deterministic=False) -> Mesh:
+def fem_mesh(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, csr=False, stream=None, deterministic=False,
+             tensor_cores=False) -> Mesh:
     h = ctypes.c_void_p()
-    flags = (FEM_MESH_CSR if csr else 0) | (FEM_MESH_DETERMINISTIC if deterministic else 0)
+    flags = ((FEM_MESH_CSR if csr else 0) | (FEM_MESH_DETERMINISTIC if deterministic else 0)
+             | (FEM_MESH_TENSOR_CORES if tensor_cores else 0))
     _check(lib().fem_mesh(nx, ny, nz, lx, ly, lz, flags, _stream(stream), ctypes.byref(h)), "fem_mesh")
     return Mesh(h, nx, ny, nz, lx, ly, lz, csr)
 

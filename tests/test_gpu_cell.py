@@ -116,34 +116,70 @@ def test_loads_match_oracle():
     assert rel_l2(host(f), oracle.body_force(om, b)) <= 1e-14
 
 
-def test_full_size_apply_sampled():
-    """64^3 Neo-Hookean FP32 tangent apply in the benchmark configuration:
-    sampled output DOFs against the oracle apply restricted to the cells
-    around each sampled node (computed one by one on a sub-box)."""
+@pytest.mark.parametrize("case", ["c1_nh_64cube", "c2_simp_128x64x64", "c2_simp_128x64x64_tensor_cores"])
+def test_full_size_apply_sampled(case):
+    """FP32 tangent apply in the benchmark configurations (the 64^3
+    Neo-Hookean box on the packed CUDA-core kernel, the 128x64x64 SIMP
+    cantilever on the CUDA cores and on the tensor cores; many cell tiles per
+    CTA): sampled
+    output DOFs against the oracle apply restricted to the cells around each
+    sampled node (computed one by one on a sub-box)."""
     F = fem()
-    n = 64
-    w = inputs.c1(n)
-    m = F.fem_mesh(n, n, n)
-    u = inputs.random_state(w.n_dofs, 1.0 / n, 11, scale=0.05)
+    w = inputs.c1(64) if case.startswith("c1") else inputs.c2()
+    nx, ny, nz = w.nx, w.ny, w.nz
+    hx, hy, hz = w.lx / nx, w.ly / ny, w.lz / nz
+    m = F.fem_mesh(nx, ny, nz, w.lx, w.ly, w.lz, tensor_cores=case.endswith("tensor_cores"))
+    u = inputs.random_state(w.n_dofs, min(hx, hy, hz), 11, scale=0.05)
     x = inputs.random_vector(w.n_dofs, 12)
-    gmat = F.material(w.kind, w.E, w.nu)
-    y = host(F.fem_tangent_apply(m, gmat, dev(u, torch.float32), dev(x, torch.float32), None, dev(w.mask)))
-    omat = oracle.Material(w.kind, w.E, w.nu)
-    a = n + 1
+    cp = w.cell_param
+    gmat = F.material(w.kind, w.E, w.nu, w.simp_p, w.simp_emin)
+    y = host(F.fem_tangent_apply(m, gmat, dev(u, torch.float32), dev(x, torch.float32),
+                                 None if cp is None else dev(cp, torch.float32), dev(w.mask)))
+    omat = oracle.Material(w.kind, w.E, w.nu, w.simp_p, w.simp_emin)
+    ax, ay = nx + 1, ny + 1
     rng = np.random.default_rng(3)
     for node in rng.integers(0, w.n_nodes, 12):
-        I, J, K = node % a, (node // a) % a, node // (a * a)
+        I, J, K = node % ax, (node // ax) % ay, node // (ax * ay)
         i0, j0, k0 = max(I - 1, 0), max(J - 1, 0), max(K - 1, 0)
-        i1, j1, k1 = min(I + 1, n), min(J + 1, n), min(K + 1, n)
-        sub = oracle.mesh(i1 - i0, j1 - j0, k1 - k0, (i1 - i0) / n, (j1 - j0) / n, (k1 - k0) / n)
+        i1, j1, k1 = min(I + 1, nx), min(J + 1, ny), min(K + 1, nz)
+        sub = oracle.mesh(i1 - i0, j1 - j0, k1 - k0, (i1 - i0) * hx, (j1 - j0) * hy, (k1 - k0) * hz)
         II, JJ, KK = np.meshgrid(np.arange(i0, i1 + 1), np.arange(j0, j1 + 1), np.arange(k0, k1 + 1), indexing="ij")
-        gid = (II + a * (JJ + a * KK)).transpose(2, 1, 0).reshape(-1)  # sub-node order x fastest
+        gid = (II + ax * (JJ + ay * KK)).transpose(2, 1, 0).reshape(-1)  # sub-node order x fastest
         dofs = (3 * gid[:, None] + np.arange(3)).reshape(-1)
-        ys = oracle.tangent_apply(sub, omat, u[dofs], x[dofs], None, w.mask[dofs])
+        sub_cp = None
+        if cp is not None:
+            CI, CJ, CK = np.meshgrid(np.arange(i0, i1), np.arange(j0, j1), np.arange(k0, k1), indexing="ij")
+            sub_cp = cp[(CI + nx * (CJ + ny * CK)).transpose(2, 1, 0).reshape(-1)]
+        ys = oracle.tangent_apply(sub, omat, u[dofs], x[dofs], sub_cp, w.mask[dofs])
         loc = int(np.where(gid == node)[0][0])
         ref = ys[3 * loc:3 * loc + 3]
         got = y[3 * node:3 * node + 3]
-        assert np.abs(got - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+        assert np.abs(got - ref).max() <= 3e-5 * np.abs(ys).max(), (node, got, ref)
+
+
+@pytest.mark.parametrize("name", ["le", "simp"])
+def test_tensor_core_apply_as_accurate_as_fp32(name):
+    """On a FEM_MESH_TENSOR_CORES mesh the FP32 linear-elastic / SIMP apply
+    runs on the tensor cores (split-TF32 products of the shared element
+    matrix); it matches the oracle like the other FP32 applies (ragged tiles,
+    masks) and its error against the FP64 apply stays within three times
+    that of the FP32 CUDA-core kernel on the same inputs, and within 1e-6
+    relative L2."""
+    F, _, om, omat, gmat, u, x, cp, mask = setup(name, (17, 9, 5))
+    mt = F.fem_mesh(17, 9, 5, 1.0, 0.8, 1.2, tensor_cores=True)
+    f32 = torch.float32
+    for mk in (mask, None):
+        y_ref = oracle.tangent_apply(om, omat, u, x, cp, mk)
+        y = F.fem_tangent_apply(mt, gmat, dev(u, f32), dev(x, f32), dev(cp, f32), None if mk is None else dev(mk))
+        assert rel_l2(host(y), y_ref) <= TOL_FP32
+    shape = (64, 32, 16)
+    F, m, om, omat, gmat, u, x, cp, mask = setup(name, shape)
+    mt = F.fem_mesh(*shape, 1.0, 0.8, 1.2, tensor_cores=True)
+    y64 = host(F.fem_tangent_apply(m, gmat, dev(u), dev(x), dev(cp), dev(mask)))
+    y_tc = host(F.fem_tangent_apply(mt, gmat, dev(u, f32), dev(x, f32), dev(cp, f32), dev(mask)))
+    y_cc = host(F.fem_tangent_apply(m, gmat, dev(u, f32), dev(x, f32), dev(cp, f32), dev(mask)))
+    e_tc, e_cc = rel_l2(y_tc, y64), rel_l2(y_cc, y64)
+    assert e_tc <= 1e-6 and e_tc <= 3.0 * e_cc, (e_tc, e_cc)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])

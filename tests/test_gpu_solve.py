@@ -100,7 +100,7 @@ def test_neohooke_noncubic_with_stiffness_field():
     assert rel_l2(u, ref) <= TOL_REFINED
 
 
-@pytest.mark.parametrize("apply_kernel", [1, 2, 3, 8])
+@pytest.mark.parametrize("apply_kernel", [1, 2, 3, 8, 11])
 def test_simp_cantilever_small(apply_kernel):
     w = inputs.c2(nx=16, ny=8, nz=8)
     ref = oracle_solve(w)
@@ -109,6 +109,29 @@ def test_simp_cantilever_small(apply_kernel):
     assert rel_l2(u, ref) <= TOL_REFINED
     u64, st64 = gpu_solve(w, 0, newton_rtol=1e-13, pcg_rtol=1e-9, apply_kernel=apply_kernel)
     assert rel_l2(u64, ref) <= TOL_FP64
+
+
+def test_simp_full_size_tensor_core_apply():
+    """The 128x64x64 SIMP cantilever (4,096 cell tiles, several per CTA) with
+    the CG apply on the tensor cores (kernel 11, split-TF32 shared element
+    matrix) and on the CUDA cores (kernel 8): the same FP64-refined solution,
+    and no more refinement sweeps or CG iterations than the FP32 apply needs
+    (an apply less accurate than FP32 would slow both)."""
+    w = inputs.c2()
+    u8, st8 = gpu_solve(w, 2, newton_rtol=1e-10, apply_kernel=8)
+    u11, st11 = gpu_solve(w, 2, newton_rtol=1e-10, apply_kernel=11)
+    assert st8["status"] == 0 and st11["status"] == 0 and st11["apply_kernel"] == 11
+    assert rel_l2(u11, u8) <= 1e-8
+    assert st11["newton_iters"] <= st8["newton_iters"] + 1
+    assert st11["pcg_iters"] <= 1.1 * st8["pcg_iters"]
+
+
+def test_tensor_core_kernel_needs_one_linear_instance():
+    """Apply kernel 11 is refused for a Neo-Hookean problem (argument error)."""
+    F = fem()
+    with pytest.raises(F.FemError) as ei:
+        gpu_solve(inputs.c1(n=4, n_steps=1), 2, apply_kernel=11)
+    assert ei.value.status == -1  # FEM_ERR_ARG
 
 
 @pytest.mark.parametrize("n", [8, 9])
