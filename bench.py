@@ -53,8 +53,8 @@ NH_APPLY_FLOPS_PER_CELL = 3269
 # displacement gradient stored) also skips the 3 x 96 flops of the gradient of
 # u -> 2,445.
 # Kernels 8 and 9 are kernels 1 and 6 evaluated two Gauss points per packed
-# FP32 instruction, 10 is 9 with its stored data staged by TMA: the same
-# algorithmic flops.
+# FP32 instruction, 10 is 9 with its stored data staged by TMA, 12 is 9 with
+# two threads per cell: the same algorithmic flops.
 # Kernel 11 is linear-elastic / SIMP only (tensor cores, shared element
 # matrix): its count is the LE one below.
 # Linear-elastic / SIMP apply with the shared element matrix: y_e = s_e K0 x_e
@@ -62,17 +62,17 @@ NH_APPLY_FLOPS_PER_CELL = 3269
 LE_APPLY_FLOPS_PER_CELL = 1224
 APPLY_FLOPS_PER_CELL = {1: NH_APPLY_FLOPS_PER_CELL, 2: NH_APPLY_FLOPS_PER_CELL, 3: NH_APPLY_FLOPS_PER_CELL,
                         4: 2517, 5: 2733, 6: 2445, 7: 2445, 8: NH_APPLY_FLOPS_PER_CELL, 9: 2445, 10: 2445,
-                        11: LE_APPLY_FLOPS_PER_CELL}
+                        11: LE_APPLY_FLOPS_PER_CELL, 12: 2445}
 # DRAM bytes (read + write) of one launch of a CG apply kernel, by apply
 # kernel id, from the ncu capture summarised in profiles/ (kernel 9:
 # cg_apply_nh64_kernel9.md; cold caches under ncu, so the 71 MB of stored data
 # come from DRAM there, while in the timed solves they stay in L2).  Valid
 # only for the kernel sources the capture was taken on: reported as null once
 # their hash changes.
-APPLY_TRAFFIC_BYTES = {9: 77.92e6 + 1.647e6}
+APPLY_TRAFFIC_BYTES = {9: 77.93e6 + 1.507e6}
 APPLY_TRAFFIC_SOURCES = ("paper_2212_00964_gb300/csrc/cell_kernels.cuh", "paper_2212_00964_gb300/csrc/fem_internal.cuh",
                          "paper_2212_00964_gb300/csrc/cell_x2.cuh")
-APPLY_TRAFFIC_SHA256 = "56a4647f7a4c95a5c5ed97a0c05f53883f40c5ac4c49f6fd4d38b86842464919"
+APPLY_TRAFFIC_SHA256 = "679dfa4943d98dec787e215af70ca7945a92f5ff28c4ddae064cca8fe144159a"
 # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP64 peak: measured on a GB300 with a DFMA throughput loop (1.196 TFLOP/s;
@@ -112,7 +112,8 @@ def parse():
     ap.add_argument("--apply-kernel", type=int, default=0,
                     help="0 autotuned, 1 per-cell, 2 bricks, 3 per-cell 4 CTA/SM, 4/5/6/7 stored tangent data, "
                          "8/9 packed Gauss-point pairs (recomputed / stored data), 10 as 9 staged by TMA, "
-                         "11 LE/SIMP on the tensor cores (also the CG kernel of --profile-op le_apply, default 8)")
+                         "11 LE/SIMP on the tensor cores (also the CG kernel of --profile-op le_apply, default 8), "
+                         "12 as 9 with two threads per cell")
     ap.add_argument("--newton-res32", type=int, default=1,
                     help="0: FP64 Newton residual in every iteration")
     ap.add_argument("--cg-fused", type=int, default=0,
@@ -975,7 +976,9 @@ def run_gb300(args):
                                 7: "cell_kernel<float,NH,CM_APPLY_PCG,4,KIN=3>",
                                 8: "cell_apply_x2<NH,CM_APPLY_PCG,KIN=0>",
                                 9: "cell_apply_x2<NH,CM_APPLY_PCG,KIN=3>",
-                                10: "cell_apply_x2<NH,CM_APPLY_PCG,KIN=3,STAGE>"}.get(st0.get("apply_kernel"), "?"),
+                                10: "cell_apply_x2<NH,CM_APPLY_PCG,KIN=3,STAGE>",
+                                11: "cell_apply_le_tc<PCG>",
+                                12: "cell_apply_x2h<NH,CM_APPLY_PCG,KIN=3>"}.get(st0.get("apply_kernel"), "?"),
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": apply_traffic(st0.get("apply_kernel")),
                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",

@@ -10,6 +10,7 @@
 #include "cell_kernels.cuh"
 #include "cell_ops.cuh"
 #include "cell_tc.cuh"
+#include "cell_x2h.cuh"
 #include "cell_x2.cuh"
 #include "mesh.cuh"
 
@@ -196,6 +197,18 @@ cudaError_t launch_apply_x2(bool nh, int kin, const CellArgs<float> &a, cudaStre
     if (g < 1) return cudaSuccess;
     count_launch();
     return launch_pdl(f, (int)g, CELL_BLOCK, smem, s, a);  // waits (pdl_wait) before reading CG vectors
+}
+
+// CG apply packed over Gauss-point pairs on stored data, two threads per cell
+// (apply kernel 12).
+cudaError_t launch_apply_x2h(const CellArgs<float> &a, cudaStream_t s)
+{
+    if (!a.kin || a.kin_mode != 3 || a.d0.kind != FEM_NEOHOOKE) return cudaErrorInvalidValue;
+    auto f = a.tab ? cell_apply_x2h<true> : cell_apply_x2h<false>;
+    int64_t g = std::min<int64_t>(2 * a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, 0));
+    if (g < 1) return cudaSuccess;
+    count_launch();
+    return launch_pdl(f, (int)g, CELL_BLOCK, 0, s, a);  // waits (pdl_wait) before reading CG vectors
 }
 
 // Unit-scale linear-elastic element matrix of the instance (24 x 24 FP32)

@@ -22,6 +22,7 @@ template <typename T>
 cudaError_t launch_apply_kin(bool nh, const CellArgs<T> &a, cudaStream_t s, bool four_ctas = false);
 
 cudaError_t launch_apply_x2(bool nh, int kin, const CellArgs<float> &a, cudaStream_t s, bool stage = false);
+cudaError_t launch_apply_x2h(const CellArgs<float> &a, cudaStream_t s);
 cudaError_t launch_le_k0(const InstDesc &d, float *k0, cudaStream_t s);
 cudaError_t launch_apply_le_tc(const CellArgs<float> &a, const float *k0, cudaStream_t s, bool pcg = true);
 
@@ -32,7 +33,7 @@ inline int kin_mode_of(int variant)
     switch (variant) {
     case 4: return 1;
     case 5: return 2;
-    case 6: case 7: case 9: case 10: return 3;
+    case 6: case 7: case 9: case 10: case 12: return 3;
     }
     return 0;
 }

@@ -840,6 +840,8 @@ class Core {
         if (variant_ >= 8) {
             ca.kin_mode = kin_mode_of(variant_);
             ca.kin = ca.kin_mode ? b_.kin : nullptr;
+            if (variant_ == 12 && std::is_same<T, float>::value)
+                return launch_apply_x2h(*(const CellArgs<float> *)&ca, s);
             if (std::is_same<T, float>::value)
                 return launch_apply_x2(pb_.nh, ca.kin_mode, *(const CellArgs<float> *)&ca, s, variant_ == 10);
             // no packed FP64 arithmetic: the scalar kernels of the same data
@@ -901,16 +903,17 @@ class Core {
             cudaEventDestroy(e0);
             return (cudaGetLastError(), 2);
         }
-        float best = 1e30f, times[11] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
+        float best = 1e30f, times[12] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
         int choice = 1;
         const bool stored = pb_.nh && b_.kin, packed = std::is_same<T, float>::value;
         // kernel 10 stages every tile's stored data, also the tiles of
         // instances that have stopped iterating: it is offered for one
         // instance only (in a batch that traffic outweighed the gain)
         const bool single = pb_.desc.size() == 1;
-        for (int v = 1; v <= 11; ++v) {
-            if ((v >= 4 && v <= 7 && !stored) || (v == 8 && !packed) || (v >= 9 && v <= 10 && !(packed && stored)) ||
-                (v == 10 && !single) || (v == 11 && !tc_ok()))
+        for (int v = 1; v <= 12; ++v) {
+            if ((v >= 4 && v <= 7 && !stored) || (v == 8 && !packed) ||
+                ((v == 9 || v == 10 || v == 12) && !(packed && stored)) || (v == 10 && !single) ||
+                (v == 11 && !tc_ok()))
                 continue;
             variant_ = v;
             // fresh control blocks for each variant (the apply's epilogue updates them)
@@ -952,10 +955,11 @@ class Core {
                         "femgb autotune: D=%lld instances=%d per-cell %.3f ms, bricks %.3f ms, "
                         "per-cell(4 CTA/SM) %.3f ms, stored tangent %.3f ms, stored scalars %.3f ms, "
                         "stored scalars + gradient %.3f ms (4 CTA/SM %.3f ms), packed pairs %.3f ms, "
-                        "packed pairs on stored data %.3f ms (staged by TMA %.3f ms), tensor cores %.3f ms -> %d\n",
+                        "packed pairs on stored data %.3f ms (staged by TMA %.3f ms), tensor cores %.3f ms, "
+                        "packed pairs on stored data with two threads per cell %.3f ms -> %d\n",
                         (long long)pb_.D, (int)pb_.desc.size(), times[0] / 3, times[1] / 3, times[2] / 3,
                         times[3] / 3, times[4] / 3, times[5] / 3, times[6] / 3, times[7] / 3, times[8] / 3,
-                        times[9] / 3, times[10] / 3, choice);
+                        times[9] / 3, times[10] / 3, times[11] / 3, choice);
         }
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = choice;
@@ -1164,7 +1168,7 @@ class Core {
                               "FEM_MIXED precision"),
                     FEM_ERR_ARG);
         if (kin_mode_of(variant_) && !(pb_.nh && b_.kin))
-            return (set_error("apply_kernel 4-7, 9 and 10 (stored tangent data) need a Neo-Hookean problem and its "
+            return (set_error("apply_kernel 4-7, 9, 10 and 12 (stored tangent data) need a Neo-Hookean problem and its "
                               "buffer (not available in fem_solve_static)"),
                     FEM_ERR_ARG);
         return FEM_OK;
@@ -1276,7 +1280,7 @@ static int check_options(const fem_options &o)
         return (set_error("solver precision must be FEM_MIXED or FEM_FP64"), FEM_ERR_ARG);
     if (!(o.newton_rtol >= 0) || !(o.newton_atol >= 0) || o.newton_maxit < 0 || !(o.pcg_rtol > 0) ||
         !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
-        o.apply_kernel < 0 || o.apply_kernel > 11 || o.cg_fused < 0 || o.cg_fused > 1 || o.newton_res32 < 0 ||
+        o.apply_kernel < 0 || o.apply_kernel > 12 || o.cg_fused < 0 || o.cg_fused > 1 || o.newton_res32 < 0 ||
         o.newton_res32 > 1 || o.graph_loop < 0 || o.graph_loop > 1 || !(o.pcg_rtol_max >= 0) ||
         !(o.pcg_rtol_max < 1) || (o.pcg_rtol_max > 0 && o.pcg_rtol_max < o.pcg_rtol))
         return (set_error("invalid solver options"), FEM_ERR_ARG);

@@ -34,7 +34,7 @@ def test_traffic_only_for_the_captured_kernel_and_sources():
 
 def test_every_apply_kernel_has_a_flop_count_and_name():
     b = load_bench()
-    assert set(b.APPLY_FLOPS_PER_CELL) == set(range(1, 12))
+    assert set(b.APPLY_FLOPS_PER_CELL) == set(range(1, 13))
     assert all(0 < v <= b.NH_APPLY_FLOPS_PER_CELL for v in b.APPLY_FLOPS_PER_CELL.values())
 
 

@@ -25,7 +25,7 @@ def make_instances(F, works):
     return insts
 
 
-@pytest.mark.parametrize("apply_kernel", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("apply_kernel", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12])
 def test_small_batch_vs_oracle_and_single(apply_kernel):
     F = fem()
     works = inputs.c3(n_inst=7, seed=3, lo=2, hi=9, n_steps=3)

@@ -71,7 +71,7 @@ def test_c0_linear_elastic_mixed_refined():
     assert rel_l2(u, ref) <= TOL_REFINED
 
 
-@pytest.mark.parametrize("apply_kernel", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("apply_kernel", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12])
 @pytest.mark.parametrize("n", [4, 8, 9])
 def test_neohooke_load_steps(n, apply_kernel):
     """Every CG apply kernel (per-cell scatter at 3 and 4 CTAs/SM, 8x4x4
