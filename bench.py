@@ -126,6 +126,8 @@ def parse():
                     help="> 0: adaptive inner CG tolerance between --pcg-rtol and this; 0: fixed")
     ap.add_argument("--graph-loop", type=int, default=1,
                     help="1: each solve is one graph launch with device-side loops; 0: host-driven loop")
+    ap.add_argument("--cta-cells", type=int, default=0,
+                    help="cells per block of the packed apply kernels 8 and 9 (64, 128; 0 autotuned)")
     ap.add_argument("--profile-op", default=None,
                     choices=["nh_apply", "le_apply", "le_apply_tc", "poisson_apply", "j2_apply", "filter"],
                     help="run one operator a few times on its benchmark size and exit (for ncu captures)")
@@ -845,7 +847,7 @@ def run_gb300(args):
     ubar = torch.tensor(w.u_bar, device="cuda")
     u = torch.zeros(D, dtype=torch.float64, device="cuda")
     opt = F.default_options(precision=F.FEM_MIXED, newton_rtol=1e-10, pcg_rtol=args.pcg_rtol,
-                            apply_kernel=args.apply_kernel, cg_fused=args.cg_fused,
+                            apply_kernel=args.apply_kernel, cg_fused=args.cg_fused, cta_cells=args.cta_cells,
                             newton_res32=args.newton_res32, graph_loop=args.graph_loop,
                             pcg_rtol_max=args.pcg_rtol_max)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -979,6 +981,7 @@ def run_gb300(args):
                                 10: "cell_apply_x2<NH,CM_APPLY_PCG,KIN=3,STAGE>",
                                 11: "cell_apply_le_tc<PCG>",
                                 12: "cell_apply_x2h<NH,CM_APPLY_PCG,KIN=3>"}.get(st0.get("apply_kernel"), "?"),
+                     "cta_cells": st0.get("cta_cells"),
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": apply_traffic(st0.get("apply_kernel")),
                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",

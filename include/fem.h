@@ -355,7 +355,13 @@ typedef struct {
                                 (FEM_MIXED only, FEM_FP64 runs 6),
                             10 = as 9 with each tile's stored data copied into
                                 shared memory by a TMA bulk copy issued one tile
-                                ahead (FEM_MIXED only, FEM_FP64 runs 6) */
+                                ahead (FEM_MIXED only, FEM_FP64 runs 6),
+                            11 = linear-elastic / SIMP, one instance: the shared
+                                element matrix on the tensor cores (split-TF32
+                                tcgen05 MMAs, TMEM accumulators; FEM_MIXED only,
+                                FEM_FP64 runs 1),
+                            12 = as 9 with two threads per cell, one per
+                                Gauss-point level (FEM_MIXED only, FEM_FP64 runs 6) */
     int cg_fused;        /* 0: separate CG apply and update kernels; 1: one fused kernel per CG
                             iteration (the vector update of the previous iteration recomputed
                             per node inside the tangent apply) with apply kernels 1 and 5
@@ -379,6 +385,9 @@ typedef struct {
                             (lifting) round, tightening as Newton converges, never tighter than half
                             the reduction the Newton stop still needs; 0: eta = pcg_rtol in every
                             round */
+    int cta_cells;       /* cells (threads) per block of the packed CG apply kernels 8 and 9: 64 or
+                            128; 0 (default): timed by the autotuner beside the kernel choice when
+                            apply_kernel = 0, else 128 */
 } fem_options;
 
 typedef struct {
@@ -397,6 +406,7 @@ typedef struct {
     int apply_kernel;    /* CG apply kernel that ran (see fem_options.apply_kernel) */
     double update_ms;    /* the same for the CG vector-update launches (0 with cg_fused) */
     int update_samples;
+    int cta_cells;       /* cells per block of the CG apply kernel that ran (kernels 8 and 9; 128 otherwise) */
 } fem_stats;
 
 typedef struct {

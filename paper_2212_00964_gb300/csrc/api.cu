@@ -60,4 +60,5 @@ extern "C" void fem_default_options(fem_options *o)
     o->newton_res32 = 1;
     o->graph_loop = 1;
     o->pcg_rtol_max = 0.1;
+    o->cta_cells = 0;
 }

@@ -133,21 +133,28 @@ static void warm_one()
     resident_grid((const void *)apply_brick<T, NH>, BRICK_X * BRICK_Y * BRICK_Z, 0);
 }
 
-static const void *apply_x2_func(bool nh, int mode, int kin, bool batched, bool stage = false)
+// CG instantiations of the packed kernel for `nt` cells per block (64 or 128)
+template <int NT>
+static const void *apply_x2_pcg(bool nh, int kin, bool batched)
+{
+    if (nh && kin == 3)
+        return batched ? (const void *)cell_apply_x2<1, CM_APPLY_PCG, 3, true, false, NT>
+                       : (const void *)cell_apply_x2<1, CM_APPLY_PCG, 3, false, false, NT>;
+    if (nh)
+        return batched ? (const void *)cell_apply_x2<1, CM_APPLY_PCG, 0, true, false, NT>
+                       : (const void *)cell_apply_x2<1, CM_APPLY_PCG, 0, false, false, NT>;
+    return batched ? (const void *)cell_apply_x2<0, CM_APPLY_PCG, 0, true, false, NT>
+                   : (const void *)cell_apply_x2<0, CM_APPLY_PCG, 0, false, false, NT>;
+}
+
+static const void *apply_x2_func(bool nh, int mode, int kin, bool batched, bool stage = false, int nt = CELL_BLOCK)
 {
     if (stage)
         return batched ? (const void *)cell_apply_x2<1, CM_APPLY_PCG, 3, true, true>
                        : (const void *)cell_apply_x2<1, CM_APPLY_PCG, 3, false, true>;
     if (mode == CM_APPLY)
         return nh ? (const void *)cell_apply_x2<1, CM_APPLY, 0, false> : (const void *)cell_apply_x2<0, CM_APPLY, 0, false>;
-    if (nh && kin == 3)
-        return batched ? (const void *)cell_apply_x2<1, CM_APPLY_PCG, 3, true>
-                       : (const void *)cell_apply_x2<1, CM_APPLY_PCG, 3, false>;
-    if (nh)
-        return batched ? (const void *)cell_apply_x2<1, CM_APPLY_PCG, 0, true>
-                       : (const void *)cell_apply_x2<1, CM_APPLY_PCG, 0, false>;
-    return batched ? (const void *)cell_apply_x2<0, CM_APPLY_PCG, 0, true>
-                   : (const void *)cell_apply_x2<0, CM_APPLY_PCG, 0, false>;
+    return nt == 64 ? apply_x2_pcg<64>(nh, kin, batched) : apply_x2_pcg<CELL_BLOCK>(nh, kin, batched);
 }
 
 // The staged kernel's dynamic shared memory (above the 48 KB default) is
@@ -166,10 +173,11 @@ static void stage_attributes()
 void warm_occupancy(bool nh)
 {
     device_sms();
-    for (int b = 0; b < 2; ++b) {
-        resident_grid(apply_x2_func(nh, CM_APPLY_PCG, 0, b), CELL_BLOCK, 0);
-        if (nh) resident_grid(apply_x2_func(nh, CM_APPLY_PCG, 3, b), CELL_BLOCK, 0);
-    }
+    for (int b = 0; b < 2; ++b)
+        for (int nt : {64, CELL_BLOCK}) {
+            resident_grid(apply_x2_func(nh, CM_APPLY_PCG, 0, b, false, nt), nt, 0);
+            if (nh) resident_grid(apply_x2_func(nh, CM_APPLY_PCG, 3, b, false, nt), nt, 0);
+        }
     if (nh) {
         stage_attributes();
         for (int b = 0; b < 2; ++b)
@@ -185,18 +193,22 @@ void warm_occupancy(bool nh)
 }
 // CG apply packed over Gauss-point pairs (FP32 only): kin 0 recomputes the
 // kinematics, kin 3 reads the gradient and scalars stored by the diagonal.
-cudaError_t launch_apply_x2(bool nh, int kin, const CellArgs<float> &a, cudaStream_t s, bool stage)
+// nt: cells per block (64 or 128; the staged kernel moves whole 128-cell tiles).
+cudaError_t launch_apply_x2(bool nh, int kin, const CellArgs<float> &a, cudaStream_t s, bool stage, int nt)
 {
     if (kin == 3 && (!nh || !a.kin || a.kin_mode != 3)) return cudaErrorInvalidValue;
     if (stage && kin != 3) return cudaErrorInvalidValue;
+    if (nt != 64 && nt != CELL_BLOCK) return cudaErrorInvalidValue;
+    if (stage) nt = CELL_BLOCK;
     const bool batched = a.tab != nullptr;
     const size_t smem = stage ? KIN3_STAGE_SMEM : 0;
     if (stage) stage_attributes();
-    auto f = (void (*)(const CellArgs<float>))apply_x2_func(nh, CM_APPLY_PCG, kin, batched, stage);
-    int64_t g = std::min<int64_t>(a.n_tiles, resident_grid((const void *)f, CELL_BLOCK, smem));
+    auto f = (void (*)(const CellArgs<float>))apply_x2_func(nh, CM_APPLY_PCG, kin, batched, stage, nt);
+    const int64_t n_iter = a.n_tiles * (CELL_BLOCK / nt);
+    int64_t g = std::min<int64_t>(n_iter, resident_grid((const void *)f, nt, smem));
     if (g < 1) return cudaSuccess;
     count_launch();
-    return launch_pdl(f, (int)g, CELL_BLOCK, smem, s, a);  // waits (pdl_wait) before reading CG vectors
+    return launch_pdl(f, (int)g, nt, smem, s, a);  // waits (pdl_wait) before reading CG vectors
 }
 
 // CG apply packed over Gauss-point pairs on stored data, two threads per cell

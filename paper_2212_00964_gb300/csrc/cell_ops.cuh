@@ -21,7 +21,8 @@ cudaError_t launch_apply_cell4(bool nh, const CellArgs<T> &a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_apply_kin(bool nh, const CellArgs<T> &a, cudaStream_t s, bool four_ctas = false);
 
-cudaError_t launch_apply_x2(bool nh, int kin, const CellArgs<float> &a, cudaStream_t s, bool stage = false);
+cudaError_t launch_apply_x2(bool nh, int kin, const CellArgs<float> &a, cudaStream_t s, bool stage = false,
+                            int nt = CELL_BLOCK);
 cudaError_t launch_apply_x2h(const CellArgs<float> &a, cudaStream_t s);
 cudaError_t launch_le_k0(const InstDesc &d, float *k0, cudaStream_t s);
 cudaError_t launch_apply_le_tc(const CellArgs<float> &a, const float *k0, cudaStream_t s, bool pcg = true);

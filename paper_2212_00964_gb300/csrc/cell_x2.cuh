@@ -307,14 +307,19 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 #ifndef FEMGB_X2_MINB
 #define FEMGB_X2_MINB 3  // CTAs per SM the register budget is set for
 #endif
-template <int NH, int MODE, int KIN, bool BATCHED, bool STAGE = false>
-__global__ void __launch_bounds__(CELL_BLOCK, FEMGB_X2_MINB) cell_apply_x2(const __grid_constant__ CellArgs<float> a)
+//   NT: cells (threads) per block iteration, a divisor of the 128-cell tile of
+//   the stored-data layout; the register budget is the same for every NT.
+template <int NH, int MODE, int KIN, bool BATCHED, bool STAGE = false, int NT = CELL_BLOCK>
+__global__ void __launch_bounds__(NT, FEMGB_X2_MINB *(CELL_BLOCK / NT)) cell_apply_x2(const __grid_constant__ CellArgs<float> a)
 {
+    static_assert(CELL_BLOCK % NT == 0 && NT % 32 == 0, "NT: a multiple of 32 dividing the tile");
+    static_assert(!STAGE || NT == CELL_BLOCK, "staging moves whole tiles");
+    constexpr int SUB = CELL_BLOCK / NT;  // block iterations per 128-cell tile
     static_assert(MODE == CM_APPLY_PCG || MODE == CM_APPLY, "apply modes only");
     static_assert(KIN == 0 || (KIN == 3 && NH), "KIN 0 or 3 (Neo-Hookean)");
     static_assert(!STAGE || (KIN == 3 && MODE == CM_APPLY_PCG), "staging serves the stored-data CG apply");
     constexpr bool PCG = (MODE == CM_APPLY_PCG);
-    __shared__ double sh[CELL_BLOCK / 32];
+    __shared__ double sh[NT / 32];
     extern __shared__ __align__(128) float kin_s[];  // STAGE: two tiles of stored data
     __shared__ __align__(8) unsigned long long kbar[2];
     float part = 0;
@@ -346,7 +351,8 @@ __global__ void __launch_bounds__(CELL_BLOCK, FEMGB_X2_MINB) cell_apply_x2(const
             if (threadIdx.x == 0) kclock_account(a.kclock, 1);
         }
     }
-    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
+    for (int64_t st = blockIdx.x; st < a.n_tiles * SUB; st += gridDim.x, ++it) {
+        const int64_t tile = st / SUB;
         if (STAGE) {
             // prefetch the next tile into the other buffer (every thread left
             // it at the barrier that ended the previous iteration)
@@ -367,7 +373,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, FEMGB_X2_MINB) cell_apply_x2(const
         bool go_tile = true;
         if (PCG) {
             if (acc_k >= 0 && k != acc_k) {  // uniform per block
-                const double s = block_sum_t<float, CELL_BLOCK>(part, sh);
+                const double s = block_sum_t<float, NT>(part, sh);
                 if (threadIdx.x == 0) atomicAdd(&a.ctl[acc_k].delta[acc_slot], s);
                 part = 0;
                 acc_k = -1;
@@ -405,7 +411,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, FEMGB_X2_MINB) cell_apply_x2(const
             worked = true;
         }
         const int ne = (int)d.n_cells();
-        const int local = (int)(tile - d.tile_off) * (int)blockDim.x + (int)threadIdx.x;
+        const int local = (int)(tile - d.tile_off) * CELL_BLOCK + (int)(st % SUB) * NT + (int)threadIdx.x;
         const bool live = local < ne;
         // every lane takes part in the +x lane merge; a lane past the end
         // computes the last cell with zero weight and scatters nothing
@@ -595,7 +601,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, FEMGB_X2_MINB) cell_apply_x2(const
     }
     if (PCG) {
         if (acc_k >= 0) {  // uniform per block
-            const double s = block_sum_t<float, CELL_BLOCK>(part, sh);
+            const double s = block_sum_t<float, NT>(part, sh);
             if (threadIdx.x == 0) atomicAdd(&a.ctl[acc_k].delta[acc_slot], s);
         }
         if (threadIdx.x == 0 && worked) kclock_stop(a.kclock, 0);

@@ -843,7 +843,8 @@ class Core {
             if (variant_ == 12 && std::is_same<T, float>::value)
                 return launch_apply_x2h(*(const CellArgs<float> *)&ca, s);
             if (std::is_same<T, float>::value)
-                return launch_apply_x2(pb_.nh, ca.kin_mode, *(const CellArgs<float> *)&ca, s, variant_ == 10);
+                return launch_apply_x2(pb_.nh, ca.kin_mode, *(const CellArgs<float> *)&ca, s, variant_ == 10,
+                                       variant_ == 10 ? CELL_BLOCK : (cta_ ? cta_ : CELL_BLOCK));
             // no packed FP64 arithmetic: the scalar kernels of the same data
             if (variant_ >= 9) return launch_apply_kin<T>(pb_.nh, ca, s, false);
             return launch_cell<T>(CM_APPLY_PCG, pb_.nh, ca, s);
@@ -859,15 +860,21 @@ class Core {
     // Autotuner: time both apply variants on this problem (scratch control
     // blocks that keep every instance iterating) and keep the faster one.
     // The choice is cached per (law, precision, DOFs, instances).
+    // The packed kernels 8 and 9 are also timed at 64 cells per block (unless
+    // fem_options.cta_cells fixes it); the chosen block size is left in cta_.
     int autotune(cudaStream_t s)
     {
         static std::mutex mu;
-        static std::map<std::tuple<int, int, int64_t, int>, int> cache;
-        const auto key = std::make_tuple((int)pb_.nh, (int)sizeof(T), pb_.D, (int)pb_.desc.size());
+        static std::map<std::tuple<int, int, int64_t, int, int>, std::pair<int, int>> cache;
+        const int req_cta = cta_;
+        const auto key = std::make_tuple((int)pb_.nh, (int)sizeof(T), pb_.D, (int)pb_.desc.size(), req_cta);
         {
             std::lock_guard<std::mutex> lk(mu);
             auto it = cache.find(key);
-            if (it != cache.end()) return it->second;
+            if (it != cache.end()) {
+                cta_ = it->second.second;
+                return it->second.first;
+            }
         }
         if (!b_.tune) return 2;
         std::vector<Ctl> tc(pb_.desc.size());
@@ -910,12 +917,19 @@ class Core {
         // instances that have stopped iterating: it is offered for one
         // instance only (in a batch that traffic outweighed the gain)
         const bool single = pb_.desc.size() == 1;
-        for (int v = 1; v <= 12; ++v) {
+        float times64[2] = {-1.f, -1.f};  // kernels 8 and 9 at 64 cells per block
+        int choice_cta = CELL_BLOCK;
+        for (int v = 1; v <= 12; ++v)
+        for (int nt : {CELL_BLOCK, 64}) {
             if ((v >= 4 && v <= 7 && !stored) || (v == 8 && !packed) ||
                 ((v == 9 || v == 10 || v == 12) && !(packed && stored)) || (v == 10 && !single) ||
                 (v == 11 && !tc_ok()))
                 continue;
+            const bool sized = v == 8 || v == 9;  // kernels with a block-size choice
+            if (nt == 64 && (!sized || req_cta == CELL_BLOCK)) continue;
+            if (nt == CELL_BLOCK && sized && req_cta == 64) continue;
             variant_ = v;
+            cta_ = nt;
             // fresh control blocks for each variant (the apply's epilogue updates them)
             bool ok = cudaMemcpyAsync(b_.tune, tc.data(), sizeof(Ctl) * tc.size(), cudaMemcpyHostToDevice, s) ==
                       cudaSuccess;
@@ -936,13 +950,15 @@ class Core {
             ok = ok && cudaMemcpy(&probe, b_.tune, sizeof(Ctl), cudaMemcpyDeviceToHost) == cudaSuccess &&
                  probe.status == 0 && probe.go == 1;  // the probe kept iterating
             if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
-                times[v - 1] = ms;
+                if (nt == 64) times64[v - 8] = ms;
+                else times[v - 1] = ms;
                 // a later (more specialised) variant replaces the current
                 // choice only when it is faster by more than the probe's
                 // spread of about 2 %
                 if (ms < 0.98f * best) {
                     best = ms;
                     choice = v;
+                    choice_cta = nt;
                 }
             }
             cudaGetLastError();
@@ -956,13 +972,16 @@ class Core {
                         "per-cell(4 CTA/SM) %.3f ms, stored tangent %.3f ms, stored scalars %.3f ms, "
                         "stored scalars + gradient %.3f ms (4 CTA/SM %.3f ms), packed pairs %.3f ms, "
                         "packed pairs on stored data %.3f ms (staged by TMA %.3f ms), tensor cores %.3f ms, "
-                        "packed pairs on stored data with two threads per cell %.3f ms -> %d\n",
+                        "packed pairs on stored data with two threads per cell %.3f ms; 64 cells per block: "
+                        "packed pairs %.3f ms, on stored data %.3f ms -> %d (%d cells per block)\n",
                         (long long)pb_.D, (int)pb_.desc.size(), times[0] / 3, times[1] / 3, times[2] / 3,
                         times[3] / 3, times[4] / 3, times[5] / 3, times[6] / 3, times[7] / 3, times[8] / 3,
-                        times[9] / 3, times[10] / 3, times[11] / 3, choice);
+                        times[9] / 3, times[10] / 3, times[11] / 3, times64[0] / 3, times64[1] / 3, choice,
+                        choice_cta);
         }
         std::lock_guard<std::mutex> lk(mu);
-        cache[key] = choice;
+        cache[key] = std::make_pair(choice, choice_cta);
+        cta_ = choice_cta;
         return choice;
     }
 
@@ -1231,7 +1250,9 @@ class Core {
                             // 4 per-cell on stored NH tangent data, 5 on stored NH tangent scalars,
                             // 6 on stored scalars and displacement gradient, 7 as 6 at 4 CTA/SM,
                             // 8 as 1 packed over Gauss-point pairs, 9 as 6 packed (FP32 only),
-                            // 10 as 9 with the stored data staged by TMA bulk copies
+                            // 10 as 9 with the stored data staged by TMA bulk copies,
+                            // 11 LE/SIMP on the tensor cores, 12 as 9 with two threads per cell
+    int cta_ = 0;           // cells per block of kernels 8 and 9 (64, 128; 0: autotuned or 128)
     double apply_ms_ = 0;   // sampled device time of CG applies
     int apply_samples_ = 0;
     double update_ms_ = 0;  // sampled device time of CG vector updates
@@ -1282,7 +1303,8 @@ static int check_options(const fem_options &o)
         !(o.pcg_rtol < 1) || o.pcg_maxit < 1 || o.pcg_chunk < 0 || o.pcg_chunk > 256 || o.step_begin < 1 ||
         o.apply_kernel < 0 || o.apply_kernel > 12 || o.cg_fused < 0 || o.cg_fused > 1 || o.newton_res32 < 0 ||
         o.newton_res32 > 1 || o.graph_loop < 0 || o.graph_loop > 1 || !(o.pcg_rtol_max >= 0) ||
-        !(o.pcg_rtol_max < 1) || (o.pcg_rtol_max > 0 && o.pcg_rtol_max < o.pcg_rtol))
+        !(o.pcg_rtol_max < 1) || (o.pcg_rtol_max > 0 && o.pcg_rtol_max < o.pcg_rtol) ||
+        (o.cta_cells != 0 && o.cta_cells != 64 && o.cta_cells != CELL_BLOCK))
         return (set_error("invalid solver options"), FEM_ERR_ARG);
     return FEM_OK;
 }
@@ -1372,6 +1394,7 @@ struct ApplyTiming {
     double ms = 0;
     int samples = 0;
     int variant = 0;
+    int cta = CELL_BLOCK;
     double upd_ms = 0;
     int upd_samples = 0;
 };
@@ -1385,6 +1408,7 @@ static void fill_stats(const Ctl &c, fem_stats *st, double ms, const ApplyTiming
     st->apply_kernel = at.variant;
     st->update_ms = at.upd_ms;
     st->update_samples = at.upd_samples;
+    st->cta_cells = at.cta;
     st->status = c.status == 1 ? FEM_OK : (c.status == 0 ? FEM_ERR_NOT_CONVERGED : c.status);
     st->load_steps = c.steps_done;
     st->newton_iters = c.newton_total;
@@ -1436,6 +1460,7 @@ static int solve_batch(Workspace &ws, Problem &pb, double *u64, const uint8_t *m
     Core<T> core(pb, b, SM_NONLINEAR, params_from(o), hc);
     core.max_steps_ = *std::max_element(pb.n_steps.begin(), pb.n_steps.end());
     core.variant_ = o.apply_kernel;
+    core.cta_ = o.cta_cells;
     core.cg_fused_opt_ = o.cg_fused;
     core.graph_loop_ = o.graph_loop;
     int rc = core.run(s, o.timeout_s);
@@ -1443,6 +1468,7 @@ static int solve_batch(Workspace &ws, Problem &pb, double *u64, const uint8_t *m
     at.ms = core.apply_ms_;
     at.samples = core.apply_samples_;
     at.variant = core.variant_;
+    at.cta = (core.variant_ == 8 || core.variant_ == 9) && core.cta_ ? core.cta_ : CELL_BLOCK;
     at.upd_ms = core.update_ms_;
     at.upd_samples = core.update_samples_;
     ctl_out.resize(ctl.size());
@@ -1494,6 +1520,7 @@ static int adjoint_batch(Workspace &ws, Problem &pb, const double *ustar, const 
     Core<T> core(pb, b, SM_LINEAR, prm, hc);
     core.ustar64_ = ustar;
     core.variant_ = o.apply_kernel;
+    core.cta_ = o.cta_cells;
     core.cg_fused_opt_ = o.cg_fused;
     core.graph_loop_ = o.graph_loop;
     int rc = core.run(s, o.timeout_s);
@@ -1501,6 +1528,7 @@ static int adjoint_batch(Workspace &ws, Problem &pb, const double *ustar, const 
     at.ms = core.apply_ms_;
     at.samples = core.apply_samples_;
     at.variant = core.variant_;
+    at.cta = (core.variant_ == 8 || core.variant_ == 9) && core.cta_ ? core.cta_ : CELL_BLOCK;
     cudaError_t e = cudaMemcpyAsync(&ctl_out, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (rc) return rc;
@@ -1601,6 +1629,7 @@ static int solve_region_t(const InstDesc &d, int n_steps, const fem_bc &bc, cons
     Core<T> core(pb, b, SM_NONLINEAR, params_from(o), hc);
     core.max_steps_ = n_steps;
     core.variant_ = o.apply_kernel;
+    core.cta_ = o.cta_cells;
     int rc = core.run_direct(s, o.timeout_s, hc);
     cudaError_t e = cudaMemcpyAsync(&ctl_out, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
     if (rc) return rc;

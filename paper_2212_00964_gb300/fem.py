@@ -51,7 +51,7 @@ class fem_options(ctypes.Structure):
                 ("pcg_chunk", ctypes.c_int), ("step_begin", ctypes.c_int),
                 ("apply_kernel", ctypes.c_int), ("cg_fused", ctypes.c_int),
                 ("timeout_s", ctypes.c_double), ("newton_res32", ctypes.c_int), ("graph_loop", ctypes.c_int),
-                ("pcg_rtol_max", ctypes.c_double)]
+                ("pcg_rtol_max", ctypes.c_double), ("cta_cells", ctypes.c_int)]
 
 
 class fem_stats(ctypes.Structure):
@@ -59,7 +59,8 @@ class fem_stats(ctypes.Structure):
                 ("pcg_iters", ctypes.c_int), ("ref_rnorm", ctypes.c_double),
                 ("final_rnorm", ctypes.c_double), ("time_ms", ctypes.c_double),
                 ("apply_ms", ctypes.c_double), ("apply_samples", ctypes.c_int), ("apply_launches", ctypes.c_int),
-                ("apply_kernel", ctypes.c_int), ("update_ms", ctypes.c_double), ("update_samples", ctypes.c_int)]
+                ("apply_kernel", ctypes.c_int), ("update_ms", ctypes.c_double), ("update_samples", ctypes.c_int),
+                ("cta_cells", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -43,6 +43,22 @@ def test_small_batch_vs_oracle_and_single(apply_kernel):
         assert rel_l2(host(I.u), host(u1)) <= TOL_REFINED
 
 
+@pytest.mark.parametrize("apply_kernel", [8, 9])
+def test_small_batch_at_64_cells_per_block(apply_kernel):
+    """Half-tile block iterations in a batch: the instance of each half tile
+    is found from its 128-cell tile."""
+    F = fem()
+    works = inputs.c3(n_inst=7, seed=3, lo=2, hi=9, n_steps=3)
+    insts = make_instances(F, works)
+    rc, stats = F.fem_solve_batched(insts, F.default_options(newton_rtol=1e-12, apply_kernel=apply_kernel,
+                                                             cta_cells=64))
+    assert rc == 0 and all(s["status"] == 0 for s in stats)
+    for w, I in zip(works, insts):
+        om = oracle.mesh(w.nx, w.ny, w.nz)
+        ref = osolve.newton_solve(om, oracle.Material(w.kind, w.E, w.nu), w.mask, w.u_bar, n_steps=w.n_steps)
+        assert rel_l2(host(I.u), ref) <= TOL_REFINED
+
+
 @pytest.mark.slow
 def test_full_batch_256_instances():
     """The 256-instance workload (edges 8..32): every instance converges; the

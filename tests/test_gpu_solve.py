@@ -88,6 +88,26 @@ def test_neohooke_load_steps(n, apply_kernel):
     assert rel_l2(u32, ref) <= TOL_REFINED
 
 
+@pytest.mark.parametrize("apply_kernel", [8, 9])
+@pytest.mark.parametrize("n", [8, 9])
+def test_packed_kernels_at_64_cells_per_block(n, apply_kernel):
+    """fem_options.cta_cells = 64: the packed CG kernels iterate over half
+    tiles of the stored-data layout (9^3: ragged last half tile); same bar
+    as at 128 cells per block, and the stats report the block size."""
+    w = inputs.c1(n=n, n_steps=10)
+    ref = oracle_c1(n)
+    u32, st32 = gpu_solve(w, 2, newton_rtol=1e-12, apply_kernel=apply_kernel, cta_cells=64)
+    assert st32["status"] == 0 and st32["apply_kernel"] == apply_kernel and st32["cta_cells"] == 64
+    assert rel_l2(u32, ref) <= TOL_REFINED
+
+
+def test_cells_per_block_option_is_checked():
+    F = fem()
+    with pytest.raises(F.FemError) as ei:
+        gpu_solve(inputs.c1(n=4, n_steps=1), 2, cta_cells=96)
+    assert ei.value.status == -1  # FEM_ERR_ARG
+
+
 def test_neohooke_noncubic_with_stiffness_field():
     w = inputs.c1(n=4, n_steps=3)
     w.nx, w.ny, w.nz = 6, 4, 3
