@@ -246,12 +246,19 @@ __device__ __forceinline__ void cg_go_book(Ctl &c, int it, int pcg_maxit)
 // CG keeps the iterate; FEM_ERR_BREAKDOWN in iteration 0) or non-finite dots.
 __device__ __forceinline__ int cg_step(const Ctl &c, int it, double &alpha, double &beta, int &status)
 {
+    // the four ring values in one round of loads (the previous iteration's
+    // slots are not used at it = 0); beta g / alpha_{it-1} as
+    // g (g / (gamma_{it-1} alpha_{it-1})), so that two FP64 divisions, not
+    // three, lie on the dependent chain to alpha
     const double g = __ldcg(&c.gamma[it & 3]);
-    double den = __ldcg(&c.delta[it & 3]);
+    const double dl = __ldcg(&c.delta[it & 3]);
+    const double gp = __ldcg(&c.gamma[(it + 3) & 3]);
+    const double ap = __ldcg(&c.alpha[(it + 3) & 3]);
+    double den = dl;
     beta = 0.0;
     if (it > 0) {
-        beta = g / __ldcg(&c.gamma[(it + 3) & 3]);
-        den -= beta * g / __ldcg(&c.alpha[(it + 3) & 3]);
+        beta = g / gp;
+        den = dl - g * (g / (gp * ap));
     }
     status = 0;
     if (!isfinite(den) || !isfinite(g)) {

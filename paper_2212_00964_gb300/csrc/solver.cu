@@ -274,6 +274,9 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_init(const VecArgs<T> a)
     }
 }
 
+#ifndef FEMGB_UPD_MINB
+#define FEMGB_UPD_MINB 3  // CTAs per SM the FP32 update's register budget is set for
+#endif
 // CG iteration `it` after the tangent apply w = K z_it (w lives in q and
 // delta_it = (w, z_it) was reduced by the apply):
 //   beta = gamma_it / gamma_{it-1}, alpha = gamma_it / (delta_it - beta gamma_it / alpha_{it-1})
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_pcg_init(const VecArgs<T> a)
 // Every block derives alpha and beta from the same reduced scalars; the
 // first block of the instance records alpha and clears the next delta slot.
 template <typename T>
-__global__ void __launch_bounds__(VEC_BLOCK, (sizeof(T) == 4 ? 3 : 2)) k_pcg_update(const VecArgs<T> a)
+__global__ void __launch_bounds__(VEC_BLOCK, (sizeof(T) == 4 ? FEMGB_UPD_MINB : 2)) k_pcg_update(const VecArgs<T> a)
 {
     __shared__ double sh[2 * (VEC_BLOCK / 32)];
     __shared__ int s_go;
@@ -291,9 +294,11 @@ __global__ void __launch_bounds__(VEC_BLOCK, (sizeof(T) == 4 ? 3 : 2)) k_pcg_upd
     if (threadIdx.x == 0) kclock_start(a.kclock, 1);
     if (blockIdx.x == 0) {
         // alpha, beta (or the stop) of this iteration for every instance, from
-        // the dots the apply reduced; book the apply's span
-        for (int kk = threadIdx.x; kk < a.n_inst; kk += blockDim.x)
-            cg_step_book(a.ctl[kk], __ldcg(&a.ctl[kk].pcg_base) + a.iter);
+        // the dots the apply reduced, booked by warps 1.. (thread 0 derives
+        // this block's own scalars meanwhile); book the apply's span
+        if (threadIdx.x >= 32)
+            for (int kk = (int)threadIdx.x - 32; kk < a.n_inst; kk += (int)blockDim.x - 32)
+                cg_step_book(a.ctl[kk], __ldcg(&a.ctl[kk].pcg_base) + a.iter);
         if (threadIdx.x == 0) kclock_account(a.kclock, 0);
     }
     int sk = -1;
@@ -302,9 +307,10 @@ __global__ void __launch_bounds__(VEC_BLOCK, (sizeof(T) == 4 ? 3 : 2)) k_pcg_upd
     if (k != sk) {  // uniform per block: every block derives the same scalars
         __syncthreads();
         if (threadIdx.x == 0) {
-            int go = __ldcg(&c.go), st = 0;
+            const int go0 = __ldcg(&c.go), base = __ldcg(&c.pcg_base);  // one round of loads
+            int go = 0, st = 0;
             double al = 0.0, be = 0.0;
-            if (go) go = cg_step(c, __ldcg(&c.pcg_base) + a.iter, al, be, st);
+            if (go0) go = cg_step(c, base + a.iter, al, be, st);
             s_go = go;
             s_al = al;
             s_be = be;
