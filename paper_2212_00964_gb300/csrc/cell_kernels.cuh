@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, (sizeof(T) == 4 ? MINB : 1))
     if (MODE == CM_APPLY_PCG) {
         pdl_wait();
         if (threadIdx.x == 0) kclock_start(a.kclock, 0);
-        if (blockIdx.x == 0) {
+        if (blockIdx.x == gridDim.x - 1) {  // the block with the fewest tiles books
             // decide, for every instance, whether this CG iteration runs (from
             // the dots the previous update reduced) and book it; book the
             // previous update's span
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(BRICK_X * BRICK_Y * BRICK_Z, (sizeof(T) == 4 ?
     const int tid = threadIdx.x;
     pdl_wait();
     if (tid == 0) kclock_start(a.kclock, 0);
-    if (blockIdx.x == 0) {  // as in cell_kernel<CM_APPLY_PCG>
+    if (blockIdx.x == gridDim.x - 1) {  // as in cell_kernel<CM_APPLY_PCG>
         const int ni = a.tab ? a.n_inst : 1;
         for (int kk = tid; kk < ni; kk += NT) cg_go_book(a.ctl[kk], __ldcg(&a.ctl[kk].pcg_base) + a.iter, a.pcg_maxit);
         if (tid == 0) kclock_account(a.kclock, 1);

@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, FEMGB_TC_MINB)
     }
     pdl_wait();
     if (PCG && threadIdx.x == 0) kclock_start(a.kclock, 0);
-    if (PCG && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (PCG && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {  // the block with the fewest tiles books
         cg_go_book(a.ctl[0], __ldcg(&a.ctl[0].pcg_base) + a.iter, a.pcg_maxit);
         kclock_account(a.kclock, 1);  // the span of the CG update before this launch
     }

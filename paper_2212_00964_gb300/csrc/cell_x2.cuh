@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(NT, FEMGB_X2_MINB *(CELL_BLOCK / NT)) cell_app
     if (PCG) {
         pdl_wait();
         if (threadIdx.x == 0) kclock_start(a.kclock, 0);
-        if (blockIdx.x == 0) {
+        if (blockIdx.x == gridDim.x - 1) {  // the block with the fewest tiles books
             const int ni = a.tab ? a.n_inst : 1;
             for (int kk = threadIdx.x; kk < ni; kk += blockDim.x)
                 cg_go_book(a.ctl[kk], __ldcg(&a.ctl[kk].pcg_base) + a.iter, a.pcg_maxit);

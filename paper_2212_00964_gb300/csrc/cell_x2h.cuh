@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(CELL_BLOCK, FEMGB_X2H_MINB) cell_apply_x2h(con
     const int lane = threadIdx.x & 31;
     pdl_wait();
     if (threadIdx.x == 0) kclock_start(a.kclock, 0);
-    if (blockIdx.x == 0) {
+    if (blockIdx.x == gridDim.x - 1) {  // the block with the fewest tiles books
         const int ni = a.tab ? a.n_inst : 1;
         for (int kk = threadIdx.x; kk < ni; kk += blockDim.x)
             cg_go_book(a.ctl[kk], __ldcg(&a.ctl[kk].pcg_base) + a.iter, a.pcg_maxit);
