@@ -248,8 +248,11 @@ __device__ __forceinline__ int cg_step(const Ctl &c, int it, double &alpha, doub
 {
     // the four ring values in one round of loads (the previous iteration's
     // slots are not used at it = 0); beta g / alpha_{it-1} as
-    // g (g / (gamma_{it-1} alpha_{it-1})), so that two FP64 divisions, not
-    // three, lie on the dependent chain to alpha
+    // g (g / (gamma_{it-1} alpha_{it-1})), and the quotients as products with
+    // correctly rounded FP64 reciprocals (__drcp_rn), so that two short FP64
+    // sequences lie on the dependent chain to alpha (one thread of every
+    // block runs it while the block waits; GB300's FP64 rate makes each step
+    // count)
     const double g = __ldcg(&c.gamma[it & 3]);
     const double dl = __ldcg(&c.delta[it & 3]);
     const double gp = __ldcg(&c.gamma[(it + 3) & 3]);
@@ -257,8 +260,8 @@ __device__ __forceinline__ int cg_step(const Ctl &c, int it, double &alpha, doub
     double den = dl;
     beta = 0.0;
     if (it > 0) {
-        beta = g / gp;
-        den = dl - g * (g / (gp * ap));
+        beta = g * __drcp_rn(gp);
+        den = dl - g * (g * __drcp_rn(gp * ap));
     }
     status = 0;
     if (!isfinite(den) || !isfinite(g)) {
@@ -269,7 +272,7 @@ __device__ __forceinline__ int cg_step(const Ctl &c, int it, double &alpha, doub
         if (it == 0) status = FEM_ERR_BREAKDOWN;
         return 0;
     }
-    alpha = g / den;
+    alpha = g * __drcp_rn(den);
     return 1;
 }
 
@@ -425,27 +428,31 @@ __device__ __forceinline__ double block_sum_f(float v, double *sh)
     return s;
 }
 
-// Two block-wide sums with one pair of barriers (FP32 warp stage, FP64 across
-// warps); results valid in thread 0.
+// Two block-wide sums with one pair of barriers, all in FP32 (the warp
+// partials summed by warp 0 with shuffles, no serial FP64 chain in thread 0);
+// the results, valid in thread 0, are returned in FP64 for the caller's
+// cross-block FP64 accumulation.
 template <int NT>
 __device__ __forceinline__ void block_sum2_f(float a, float b, double *sh, double &ra, double &rb)
 {
+    static_assert(NT / 32 <= 32, "one warp sums the warp partials");
+    float *shf = (float *)sh;  // 2 NT / 32 floats fit in the 2 NT / 32 doubles
     a = warp_sum(a);
     b = warp_sum(b);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
     if (l == 0) {
-        sh[2 * w] = (double)a;
-        sh[2 * w + 1] = (double)b;
+        shf[2 * w] = a;
+        shf[2 * w + 1] = b;
     }
     __syncthreads();
     ra = rb = 0;
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int i = 0; i < NT / 32; ++i) {
-            ra += sh[2 * i];
-            rb += sh[2 * i + 1];
-        }
+    if (w == 0) {
+        float sa = l < NT / 32 ? shf[2 * l] : 0.f, sb = l < NT / 32 ? shf[2 * l + 1] : 0.f;
+        sa = warp_sum(sa);
+        sb = warp_sum(sb);
+        ra = (double)sa;
+        rb = (double)sb;
     }
 }
 
