@@ -69,10 +69,10 @@ APPLY_FLOPS_PER_CELL = {1: NH_APPLY_FLOPS_PER_CELL, 2: NH_APPLY_FLOPS_PER_CELL, 
 # come from DRAM there, while in the timed solves they stay in L2).  Valid
 # only for the kernel sources the capture was taken on: reported as null once
 # their hash changes.
-APPLY_TRAFFIC_BYTES = {9: 77.92e6 + 1.441e6}
+APPLY_TRAFFIC_BYTES = {9: 77.92e6 + 1.395e6}
 APPLY_TRAFFIC_SOURCES = ("paper_2212_00964_gb300/csrc/cell_kernels.cuh", "paper_2212_00964_gb300/csrc/fem_internal.cuh",
                          "paper_2212_00964_gb300/csrc/cell_x2.cuh")
-APPLY_TRAFFIC_SHA256 = "5a735b1c5b284d12e4cc9eb41ac59744fd9862cf6f1500020ebe43bbb08e33d2"
+APPLY_TRAFFIC_SHA256 = "59fce7b64f1c2e7a6b5046604c58dafaf4c61aece9f80a012485baf27389e736"
 # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP64 peak: measured on a GB300 with a DFMA throughput loop (1.196 TFLOP/s;
