@@ -64,9 +64,9 @@ APPLY_FLOPS_PER_CELL = {1: NH_APPLY_FLOPS_PER_CELL, 2: NH_APPLY_FLOPS_PER_CELL, 
                         4: 2517, 5: 2733, 6: 2445, 7: 2445, 8: NH_APPLY_FLOPS_PER_CELL, 9: 2445, 10: 2445,
                         11: LE_APPLY_FLOPS_PER_CELL, 12: 2445}
 # DRAM bytes (read + write) of one launch of a CG apply kernel, by apply
-# kernel id, from the ncu capture summarised in profiles/ (kernel 9:
-# cg_apply_nh64_kernel9.md; cold caches under ncu, so the 71 MB of stored data
-# come from DRAM there, while in the timed solves they stay in L2).  Valid
+# kernel id, from the ncu capture of kernel 9 at 64^3 summarised under
+# profiles/ (cold caches under ncu, so the 71 MB of stored data come from
+# DRAM there, while in the timed solves they stay in L2).  Valid
 # only for the kernel sources the capture was taken on: reported as null once
 # their hash changes.
 APPLY_TRAFFIC_BYTES = {9: 77.92e6 + 1.395e6}
