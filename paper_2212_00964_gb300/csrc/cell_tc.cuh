@@ -8,10 +8,12 @@
 // block of gathered cell directions, which runs as tcgen05.mma:
 //   * X is split into TF32 high and low parts, both rounded to nearest (the
 //     tensor cores would truncate an FP32 low part), K0 likewise, and the
-//     product is X_hi K0_hi + X_hi K0_lo + X_lo K0_hi (X_lo K0_lo is below
-//     2^-24 of |x||K0|): each term within about three units of 2^-24, near
-//     the FP32 CUDA-core apply; nine 128x32x8 MMAs per tile, the cross terms
-//     accumulated before the large ones;
+//     product is X_hi K0_hi + X_hi K0_lo + X_lo K0_hi: each factor is held to
+//     2^-22 of its value and the dropped X_lo K0_lo is below 2^-22 |x||K0|,
+//     so each term is within 3 x 2^-22 of |x||K0| in the worst case (on
+//     random directions about 1.3 times the FP32 CUDA-core apply's error);
+//     nine 128x32x8 MMAs per tile, the cross terms accumulated before the
+//     large ones;
 //   * the product runs on x_e minus the translation of its node 0 (K0
 //     annihilates translations), so its rounding scales with the variation
 //     of x over the cell, as in a gradient form;

@@ -7,7 +7,13 @@ mathematics the CUDA kernels rely on beyond the oracle's own formulation:
   and against the A dF^T A form;
 * the FP64 reciprocal cube root taken as two Newton steps
   r <- r + r (1 - x r^3) / 3 from an FP32-accurate start meets FP64 accuracy
-  for any start within the FP32 approximation's error bound."""
+  for any start within the FP32 approximation's error bound;
+* the tensor-core form of the linear-elastic apply: the shared unit-scale
+  element matrix K0 of a box cell (typed from its definition) is the
+  independent Voigt B^T D B matrix, it annihilates rigid translations (so
+  K0 x = K0 (x - x_0)), the integer TF32 rounding is round-to-nearest with
+  ties away from zero, and the split product X_hi K_hi + X_hi K_lo +
+  X_lo K_hi stays within its worst-case bound."""
 import numpy as np
 
 G, KAPPA = 3.846153846153846, 8.333333333333334  # E = 10, nu = 0.3
@@ -101,3 +107,101 @@ def test_reciprocal_cube_root_two_newton_steps():
         for _ in range(2):
             r = r + (r / 3.0) * (1.0 - x * r * r * r)
         assert np.max(np.abs(r / exact - 1)) <= 4e-16
+
+
+# ---- tensor-core linear-elastic apply -------------------------------------
+
+
+def k0_box(hx, hy, hz, lam, mu):
+    """K0[(a,c),(b,d)] = sum_q w detJ (lam dNa_c dNb_d + mu delta_cd gNa.gNb +
+    mu dNa_d dNb_c) at the 2x2x2 Gauss points; local node a = p + 2q + 4r."""
+    g = 0.5 / np.sqrt(3.0)
+    gp = (0.5 - g, 0.5 + g)
+    off = np.array([[a & 1, (a >> 1) & 1, (a >> 2) & 1] for a in range(8)])
+    h = np.array([hx, hy, hz])
+    K = np.zeros((24, 24))
+    for q in range(8):
+        xi = np.array([gp[q & 1], gp[(q >> 1) & 1], gp[(q >> 2) & 1]])
+        G = np.zeros((8, 3))
+        for a in range(8):
+            for d in range(3):
+                v = (1.0 if off[a, d] else -1.0) / h[d]
+                for o in range(3):
+                    if o != d:
+                        v *= xi[o] if off[a, o] else 1.0 - xi[o]
+                G[a, d] = v
+        for a in range(8):
+            for b in range(8):
+                dot = G[a] @ G[b]
+                for c in range(3):
+                    for e in range(3):
+                        K[3 * a + c, 3 * b + e] += (lam * G[a, c] * G[b, e] + mu * (dot if c == e else 0.0)
+                                                    + mu * G[a, e] * G[b, c])
+    return K * (hx * hy * hz / 8)
+
+
+def test_shared_element_matrix_is_the_voigt_stiffness():
+    from tests import indep
+    hx, hy, hz, E, nu = 0.7, 0.4, 1.3, 70e3, 0.3
+    lam, mu = indep.lame(E, nu)
+    K = k0_box(hx, hy, hz, lam, mu)
+    # VTK corner order of indep: lexicographic node a = p + 2q + 4r is VTK node perm[a]
+    perm = [0, 1, 3, 2, 4, 5, 7, 6]
+    dof = np.array([3 * perm[a] + c for a in range(8) for c in range(3)])
+    Kv = indep.voigt_ke(hx, hy, hz, E, nu)[np.ix_(dof, dof)]
+    assert np.abs(K - Kv).max() <= 1e-12 * np.abs(Kv).max()
+    assert np.abs(K - K.T).max() <= 1e-12 * np.abs(K).max()
+
+
+def test_shared_element_matrix_annihilates_translations():
+    K = k0_box(1.0, 0.8, 1.2, 1.0, 0.6)
+    rng = np.random.default_rng(3)
+    for c in range(3):
+        t = np.zeros(24)
+        t[c::3] = 1.0
+        assert np.abs(K @ t).max() <= 1e-13 * np.abs(K).max()
+    x = 1e3 + rng.standard_normal(24)  # a large common translation
+    xd = x.copy()
+    for c in range(3):
+        xd[c::3] -= x[c]
+    assert np.allclose(K @ x, K @ xd, rtol=0, atol=1e-9 * np.abs(K).max() * np.abs(x).max())
+
+
+def tf32_rna(v):
+    """The kernel's integer rounding: half a TF32 unit added to the FP32 bit
+    pattern's magnitude, then the low 13 bits cleared."""
+    b = np.asarray(v, dtype=np.float32).view(np.uint32)
+    return ((b + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+def test_tf32_integer_rounding_is_nearest_ties_away():
+    rng = np.random.default_rng(4)
+    v = (rng.standard_normal(20000) * 10.0 ** rng.uniform(-20, 20, 20000)).astype(np.float32)
+    # exact ties at the 13th bit: mantissa ending in 1 followed by zeros
+    ties = (np.arange(1, 2001, dtype=np.uint32) << 13 | np.uint32(0x1000)) | np.uint32(0x3F800000)
+    v = np.concatenate([v, ties.view(np.float32), -ties.view(np.float32)])
+    got = tf32_rna(v).astype(np.float64)
+    x = v.astype(np.float64)
+    e = np.floor(np.log2(np.abs(x)))
+    ulp = 2.0 ** (e - 10)  # 11 significant bits
+    ref = np.sign(x) * np.floor(np.abs(x) / ulp + 0.5) * ulp
+    assert np.array_equal(got, ref)
+
+
+def test_split_tf32_product_bound():
+    """Worst case per product term: |x - x_hi - x_lo| <= 2^-22 |x| for each
+    factor, and the dropped X_lo K_lo term below 2^-22 |x||K|: the
+    three-product sum is within 3 * 2^-22 of sum |x||K| (products exact)."""
+    rng = np.random.default_rng(5)
+    K = k0_box(1.0 / 64, 1.0 / 64, 1.0 / 64, 1.35, 0.38).astype(np.float32)
+    kh = tf32_rna(K)
+    kl = tf32_rna(K - kh)
+    for _ in range(200):
+        x = (rng.standard_normal(24) * 10.0 ** rng.uniform(-3, 3)).astype(np.float32)
+        xh = tf32_rna(x)
+        xl = tf32_rna(x - xh)
+        d = np.float64
+        y = kh.astype(d) @ xh.astype(d) + kl.astype(d) @ xh.astype(d) + kh.astype(d) @ xl.astype(d)
+        exact = K.astype(d) @ x.astype(d)
+        bound = 3 * 2.0 ** -22 * (np.abs(K).astype(d) @ np.abs(x).astype(d))
+        assert np.all(np.abs(y - exact) <= bound)
