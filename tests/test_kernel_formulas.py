@@ -13,7 +13,12 @@ mathematics the CUDA kernels rely on beyond the oracle's own formulation:
   independent Voigt B^T D B matrix, it annihilates rigid translations (so
   K0 x = K0 (x - x_0)), the integer TF32 rounding is round-to-nearest with
   ties away from zero, and the split product X_hi K_hi + X_hi K_lo +
-  X_lo K_hi stays within its worst-case bound."""
+  X_lo K_hi stays within its worst-case bound;
+* the two-threads-per-cell split of the packed apply: the gradient at one
+  Gauss level written in the coordinates of the own and the other node
+  level (the z-difference's sign folded into the z scale) is the gradient
+  of the trilinear field, and the two levels' transposed partials sum to
+  the transpose of the whole gradient."""
 import numpy as np
 
 G, KAPPA = 3.846153846153846, 8.333333333333334  # E = 10, nu = 0.3
@@ -205,3 +210,64 @@ def test_split_tf32_product_bound():
         exact = K.astype(d) @ x.astype(d)
         bound = 3 * 2.0 ** -22 * (np.abs(K).astype(d) @ np.abs(x).astype(d))
         assert np.all(np.abs(y - exact) <= bound)
+
+
+# ---- two threads per cell: own / other node level ---------------------------
+
+CA, CB = (1 + 1 / np.sqrt(3)) / 2, (1 - 1 / np.sqrt(3)) / 2  # 1-D shape values at the Gauss points
+
+
+def trilinear_grad(v, h, al, be, ga):
+    """Gradient of the trilinear field with nodal values v[p, q, r] at Gauss
+    point (al, be, ga) of a box cell with sizes h (direct evaluation)."""
+    s = [CA, CB]  # value of the node-0 shape function at Gauss point 0, 1 (node 1: mirrored)
+    N = lambda node, gp: s[gp] if node == 0 else s[1 - gp]
+    g = np.zeros(3)
+    for p in range(2):
+        for q in range(2):
+            for r in range(2):
+                dx = (1 if p else -1) / h[0] * N(q, be) * N(r, ga)
+                dy = N(p, al) * (1 if q else -1) / h[1] * N(r, ga)
+                dz = N(p, al) * N(q, be) * (1 if r else -1) / h[2]
+                g += v[p, q, r] * np.array([dx, dy, dz])
+    return g
+
+
+def grad_own_other(Vo, Vt, ihx, ihy, ihz_s):
+    """The kernel's formulation: Vo[q] = (v(0,q,own), v(1,q,own)), Vt likewise
+    for the other level; returns gx[be], gy (pair over al), gz[be] (pairs)."""
+    do = [Vo[q][1] - Vo[q][0] for q in range(2)]
+    dt = [Vt[q][1] - Vt[q][0] for q in range(2)]
+    gx = []
+    for be in range(2):
+        b0, b1 = (CB, CA) if be else (CA, CB)
+        gx.append(CA * ihx * (b0 * do[0] + b1 * do[1]) + CB * ihx * (b0 * dt[0] + b1 * dt[1]))
+    Z = CA * (Vo[1] - Vo[0]) + CB * (Vt[1] - Vt[0])
+    gy = CA * ihy * Z + CB * ihy * Z[::-1]
+    D0, D1 = Vo[0] - Vt[0], Vo[1] - Vt[1]
+    gz = []
+    for be in range(2):
+        Z = CA * D0 + CB * D1 if be == 0 else CB * D0 + CA * D1
+        gz.append(CA * ihz_s * Z + CB * ihz_s * Z[::-1])
+    return gx, gy, gz
+
+
+def test_own_other_level_gradient():
+    rng = np.random.default_rng(6)
+    h = np.array([0.3, 0.5, 0.7])
+    for _ in range(20):
+        v = rng.standard_normal((2, 2, 2))
+        for lvl in range(2):  # the thread's Gauss level ga = node level r = lvl
+            Vo = [np.array([v[0, q, lvl], v[1, q, lvl]]) for q in range(2)]
+            Vt = [np.array([v[0, q, 1 - lvl], v[1, q, 1 - lvl]]) for q in range(2)]
+            ihz_s = (1 if lvl else -1) / h[2]
+            gx, gy, gz = grad_own_other(Vo, Vt, 1 / h[0], 1 / h[1], ihz_s)
+            for be in range(2):
+                for al in range(2):
+                    ref = trilinear_grad(v, h, al, be, lvl)
+                    assert abs(gx[be] - ref[0]) <= 1e-12
+                    assert abs(gz[be][al] - ref[2]) <= 1e-12
+            # the y-derivative pair is taken at (al, ., lvl): it does not depend on be
+            for al in range(2):
+                assert abs(gy[al] - trilinear_grad(v, h, al, 0, lvl)[1]) <= 1e-12
+                assert abs(gy[al] - trilinear_grad(v, h, al, 1, lvl)[1]) <= 1e-12
