@@ -271,3 +271,56 @@ def test_own_other_level_gradient():
             for al in range(2):
                 assert abs(gy[al] - trilinear_grad(v, h, al, 0, lvl)[1]) <= 1e-12
                 assert abs(gy[al] - trilinear_grad(v, h, al, 1, lvl)[1]) <= 1e-12
+
+
+def grad_own_other_t(sx, sy, sz, scx, scy, scz_s):
+    """The kernel's transpose at one Gauss level: x-flux sums sx[be] (over
+    al), y-flux pair sy (over be), z-flux pairs sz[be]; returns the own and
+    other node levels' sums Yo[q], Yt[q] (pairs over p)."""
+    Yo, Yt = [None, None], [None, None]
+    for q in range(2):
+        b0, b1 = (CB, CA) if q else (CA, CB)
+        t = b0 * sx[0] + b1 * sx[1]
+        wo, wt = CA * scx * t, CB * scx * t
+        Yo[q] = np.array([-wo, wo])
+        Yt[q] = np.array([-wt, wt])
+    T = CA * sy + CB * sy[::-1]
+    Wo, Wt = CA * scy * T, CB * scy * T
+    Yo[1] = Yo[1] + Wo
+    Yo[0] = Yo[0] - Wo
+    Yt[1] = Yt[1] + Wt
+    Yt[0] = Yt[0] - Wt
+    T0 = CA * sz[0] + CB * sz[0][::-1]
+    T1 = CA * sz[1] + CB * sz[1][::-1]
+    W0 = CA * scz_s * T0 + CB * scz_s * T1
+    W1 = CB * scz_s * T0 + CA * scz_s * T1
+    Yo[0], Yt[0] = Yo[0] + W0, Yt[0] - W0
+    Yo[1], Yt[1] = Yo[1] + W1, Yt[1] - W1
+    return Yo, Yt
+
+
+def test_own_other_level_transpose_sums_to_the_full_transpose():
+    rng = np.random.default_rng(7)
+    h = np.array([0.3, 0.5, 0.7])
+    for _ in range(20):
+        f = rng.standard_normal((2, 2, 2, 3))  # flux at Gauss point (al, be, ga)
+        Y = np.zeros((2, 2, 2))                # sum over Gauss points of f . grad N at node (p, q, r)
+        for al in range(2):
+            for be in range(2):
+                for ga in range(2):
+                    for p in range(2):
+                        for q in range(2):
+                            for r in range(2):
+                                e = np.zeros((2, 2, 2))
+                                e[p, q, r] = 1.0
+                                Y[p, q, r] += f[al, be, ga] @ trilinear_grad(e, h, al, be, ga)
+        got = np.zeros((2, 2, 2))
+        for lvl in range(2):
+            sx = [f[:, be, lvl, 0].sum() for be in range(2)]
+            sy = np.array([f[al, :, lvl, 1].sum() for al in range(2)])
+            sz = [np.array([f[al, be, lvl, 2] for al in range(2)]) for be in range(2)]
+            Yo, Yt = grad_own_other_t(sx, sy, sz, 1 / h[0], 1 / h[1], (1 if lvl else -1) / h[2])
+            for q in range(2):
+                got[:, q, lvl] += Yo[q]
+                got[:, q, 1 - lvl] += Yt[q]
+        assert np.abs(got - Y).max() <= 1e-12 * max(1.0, np.abs(Y).max())
