@@ -1033,7 +1033,7 @@ void oracle_j2_tangent_apply(int64_t n_nodes, int64_t n_cells, const int32_t *co
 }
 
 /* Dense element tangent of cell e (24x24 row-major), column c = JVP with
- * the unit vector e_c; no mask (the driver eliminates prescribed DOFs). */
+ * the unit vector e_c; no mask (the caller eliminates prescribed DOFs). */
 void oracle_j2_element_tangent(const int32_t *conn, const double *X, double E, double nu, double sy,
                                const double *hist_eps, const double *hist_sig, const double *u,
                                int64_t e, double *Ke)
