@@ -129,7 +129,8 @@ def parse():
     ap.add_argument("--cta-cells", type=int, default=0,
                     help="cells per block of the packed apply kernels 8 and 9 (64, 128; 0 autotuned)")
     ap.add_argument("--profile-op", default=None,
-                    choices=["nh_apply", "le_apply", "le_apply_tc", "poisson_apply", "j2_apply", "filter"],
+                    choices=["nh_apply", "le_apply", "le_apply_tc", "poisson_apply", "j2_apply", "j2_residual",
+                             "filter"],
                     help="run one operator a few times on its benchmark size and exit (for ncu captures)")
     return ap.parse_args()
 
@@ -664,6 +665,33 @@ def next_suite(F, inputs, torch):
             res[name] = {"us": t * 1e6, "tflops": tf, "timing": mode,
                          "frac_fp32_peak": tf / FP32_PEAK_TFLOPS if name == "fp32" else None,
                          "frac_fp64_peak": tf / FP64_PEAK_TFLOPS if name == "fp64" else None}
+        # the FP64 residual with the returned history, as every Newton
+        # iteration of a load step runs it; the call reads the yield count
+        # back and synchronises, so it is timed directly (events around the
+        # call); algorithmic bytes per cell: the history read and rewritten
+        # (2 x 96 doubles), u and R (3 doubles per node, one node per cell)
+        try:
+            r, hist_new = torch.empty_like(u_it), torch.empty_like(hist)
+            F.fem_j2_residual(m, mat, u_it, hist, mask, r, hist_new)
+            ts = []
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                F.fem_j2_residual(m, mat, u_it, hist, mask, r, hist_new)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            t = float(np.median(ts))
+            gbs = (2 * 96 * 8 + 48) * m.n_cells / t / 1e9
+            hbm_peak = measured_hbm_gbs()
+            res["residual_fp64"] = {"us": t * 1e6, "timing": "direct (includes the yield-count read-back)",
+                                    "algorithmic_bytes_per_cell": 2 * 96 * 8 + 48, "gbs": gbs,
+                                    "hbm_frac_of_measured": gbs / hbm_peak if hbm_peak else None,
+                                    "fp64_flop_per_cell": 3750,
+                                    "fp64_tflops": 3750 * m.n_cells / t / 1e12,
+                                    "frac_fp64_peak": 3750 * m.n_cells / t / 1e12 / FP64_PEAK_TFLOPS}
+        except Exception as e:  # keep the apply figures above
+            res["residual_fp64"] = {"error": f"{type(e).__name__}: {e}"}
         return res
 
     guarded("j2_apply_64cube", j2_apply)
@@ -747,7 +775,9 @@ def profile_op(args):
     cantilever inside one solve, the standalone SIMP apply of the same
     cantilever (tensor cores), the Poisson stiffness operator at
     512x512x128, the FP32 J2 tangent apply at 64^3 (uniaxial state after one
-    load step), the cone filter (r_min 1.5) on the 128x64x64 cantilever."""
+    load step), the FP64 J2 residual with the returned history at the same
+    state (as each Newton iteration of a load step runs it), the cone filter
+    (r_min 1.5) on the 128x64x64 cantilever."""
     import numpy as np
     import torch
     torch.cuda.set_device(0)
@@ -795,7 +825,7 @@ def profile_op(args):
         x = torch.randn(m.n_nodes, dtype=torch.float32, device="cuda")
         y = torch.empty_like(x)
         call = lambda: F.fem_poisson_apply(m, x, 1.0, F.FEM_POISSON_STIFFNESS, mask, y)
-    elif op == "j2_apply":
+    elif op in ("j2_apply", "j2_residual"):
         n = 64
         mask_h, ubars, _, (E, nu, sy) = inputs.j2_uniaxial(n=n)
         m = F.fem_mesh(n, n, n)
@@ -803,20 +833,36 @@ def profile_op(args):
         mask = torch.tensor(mask_h, device="cuda")
         u = torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda")
         hist = F.j2_history(m)
-        # FP64 step, so that the FP32 apply kernel runs only in the calls below
-        F.fem_j2_step(m, mat, mask, torch.tensor(ubars[4], device="cuda"), u, hist, mixed=False)
-        x = torch.randn(m.n_dofs, dtype=torch.float32, device="cuda")
-        y = torch.empty_like(x)
-        call = lambda: F.fem_j2_tangent_apply(m, mat, u, hist, x, mask, y)
+        if op == "j2_apply":
+            # FP64 step, so that the FP32 apply kernel runs only in the calls below
+            F.fem_j2_step(m, mat, mask, torch.tensor(ubars[4], device="cuda"), u, hist, mixed=False)
+            x = torch.randn(m.n_dofs, dtype=torch.float32, device="cuda")
+            y = torch.empty_like(x)
+            call = lambda: F.fem_j2_tangent_apply(m, mat, u, hist, x, mask, y)
+        else:
+            # a homogeneous uniaxial field past first yield (strain 1.5 sigma_y / E
+            # along z, elastic lateral contraction) on the virgin history: every
+            # Gauss point takes the return-mapping branch, and no solve runs
+            # the residual kernel before the calls below
+            eps = 1.5 * sy / E
+            gx = np.arange(n + 1) / n
+            Z, Y, X = np.meshgrid(gx, gx, gx, indexing="ij")  # node index i + (n+1)(j + (n+1)k)
+            uh = np.stack([-nu * eps * X, -nu * eps * Y, eps * Z], axis=-1).reshape(-1)
+            u = torch.tensor(uh, dtype=torch.float64, device="cuda")
+            r, hist_new = torch.empty_like(u), torch.empty_like(hist)
+            call = lambda: F.fem_j2_residual(m, mat, u, hist, mask, r, hist_new)
     else:
         w = inputs.c2()
         m = F.fem_mesh(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz)
         g = torch.randn(w.n_cells, dtype=torch.float64, device="cuda")
         call = lambda: F.fem_density_filter(m, g, 1.5)
     for _ in range(3):
-        call()
+        out = call()
     torch.cuda.synchronize()
-    print(json.dumps({"profile_op": op, "status": "ok"}), flush=True)
+    info = {"profile_op": op, "status": "ok"}
+    if op == "j2_residual":
+        info.update(gauss_points_yielding=int(out[1]), gauss_points=8 * m.n_cells)
+    print(json.dumps(info), flush=True)
     return 0
 
 
