@@ -1,8 +1,9 @@
 """GPU parity of the solvers against the oracle's Newton / spsolve solutions:
 the linear-elastic c0 solve (FP64 and mixed), Neo-Hookean load-stepped
-Newton (FP64 and mixed with FP64 refinement), SIMP solve, and the 64^3
-Neo-Hookean benchmark solve checked by properties that hold at any size
-(mixed vs FP64 GPU solution, oracle FP64 residual at the GPU solution)."""
+Newton (FP64 and mixed with FP64 refinement) up to 17^3, SIMP solve, and
+the 64^3 Neo-Hookean benchmark solve checked by properties that hold at any
+size (mixed vs FP64 GPU solution, oracle FP64 residual at the GPU
+solution)."""
 import functools
 
 import numpy as np
@@ -86,6 +87,25 @@ def test_neohooke_load_steps(n, apply_kernel):
     u32, st32 = gpu_solve(w, 2, newton_rtol=1e-12, apply_kernel=apply_kernel)
     assert st32["status"] == 0 and st32["apply_kernel"] == apply_kernel
     assert rel_l2(u32, ref) <= TOL_REFINED
+
+
+@pytest.mark.slow
+def test_c1_17cube_against_the_oracle():
+    """17^3 Neo-Hookean, 10 load steps (17,496 DOF; 4,913 cells, 38 full
+    cell tiles and a ragged one; many CG chunks per Newton iteration): the
+    default solves (autotuned apply kernel, adaptive inner tolerance, one
+    graph launch with device-side loops) equal the oracle's Newton / spsolve
+    solution, mixed to 1e-8 and all-FP64 to 1e-10 (about two minutes of
+    oracle time on one core)."""
+    n = 17
+    w = inputs.c1(n=n, n_steps=10)
+    ref = oracle_c1(n)
+    u32, st32 = gpu_solve(w, 2, newton_rtol=1e-12)
+    assert st32["status"] == 0 and st32["load_steps"] == 10
+    assert rel_l2(u32, ref) <= TOL_REFINED
+    u64, st64 = gpu_solve(w, 0, newton_rtol=1e-13, pcg_rtol=1e-8)
+    assert st64["status"] == 0 and st64["load_steps"] == 10
+    assert rel_l2(u64, ref) <= TOL_FP64
 
 
 @pytest.mark.parametrize("apply_kernel", [8, 9])
