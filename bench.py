@@ -581,12 +581,14 @@ def suite(F, inputs, torch):
 
 def next_suite(F, inputs, torch):
     """Timings of the scalar Poisson, J2 plasticity and topology-optimisation
-    paths (opt-in): one objective + adjoint gradient of the full-field
-    inference at the paper's 50x50x10 and at 256x256x64, with the stiffness
-    stencil timed alone by CUDA events; the J2 load / unload path on a 16^3
-    box; one topology-optimisation iteration (SIMP solve, adjoint, filter,
-    MMA step) on the 128x64x64 cantilever.  Each entry records its error
-    instead of stopping the benchmark."""
+    paths (part of the default run; --no-next-suite skips them): one
+    objective + adjoint gradient of the full-field inference at the paper's
+    50x50x10 and at 256x256x64, with the stiffness stencil timed alone by
+    CUDA events; the J2 tangent apply (FP64 and FP32) and the FP64 J2
+    residual at 64^3, and the J2 load / unload path on a 16^3 box; one
+    topology-optimisation iteration (SIMP solve, adjoint, filter, MMA step)
+    on the 128x64x64 cantilever.  Each entry records its error instead of
+    stopping the benchmark."""
     import numpy as np
     out = {}
     hbm_peak = measured_hbm_gbs()
@@ -683,7 +685,6 @@ def next_suite(F, inputs, torch):
                 ts.append(e0.elapsed_time(e1) / 1e3)
             t = float(np.median(ts))
             gbs = (2 * 96 * 8 + 48) * m.n_cells / t / 1e9
-            hbm_peak = measured_hbm_gbs()
             res["residual_fp64"] = {"us": t * 1e6, "timing": "direct (includes the yield-count read-back)",
                                     "algorithmic_bytes_per_cell": 2 * 96 * 8 + 48, "gbs": gbs,
                                     "hbm_frac_of_measured": gbs / hbm_peak if hbm_peak else None,
